@@ -1,0 +1,259 @@
+"""ctypes front end of the FP64 CPU oracle (oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
+CPU-baseline leg may import this package; the library under
+``paper_1712_03439_gb300`` never does.  It shares no code with the CUDA path.
+
+Batch arguments are duck-typed: any object with ``num_mics``,
+``num_sources`` (int32 [U]), ``num_samples`` (int64 [U]), ``rir_len``
+(int32 [R]), ``x``, ``rir`` and ``snr_db`` (float32, packed as described in
+the library header) works.  All arithmetic is FP64; FP32 inputs are converted
+exactly.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+_CFLAGS = ["-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-std=c11",
+           "-D_DEFAULT_SOURCE"]
+
+
+def build_library(force: bool = False, extra_flags=()) -> str:
+    """Compiles oracle.c into liboracle.so (gcc, OpenMP).  Returns the path."""
+    out = _LIB_PATH
+    if extra_flags:
+        tag = "_".join(f.strip("-").replace("=", "") for f in extra_flags)
+        out = os.path.join(_HERE, f"liboracle_{tag}.so")
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        cmd = ["gcc", *_CFLAGS, *extra_flags, _SRC, "-o", out, "-lm"]
+        subprocess.run(cmd, check=True)
+    return out
+
+
+def _load(path=None):
+    global _lib
+    if path is not None:
+        return _bind(ctypes.CDLL(path))
+    if _lib is None:
+        override = os.environ.get("ORACLE_LIB")
+        _lib = _bind(ctypes.CDLL(override if override else build_library()))
+    return _lib
+
+
+def _bind(lib):
+    P = ctypes.c_void_p
+    i32, i64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    lib.oracle_cost_td.restype = f64
+    lib.oracle_cost_td.argtypes = [f64, f64, f64, f64]
+    lib.oracle_cost_fft.restype = f64
+    lib.oracle_cost_fft.argtypes = [f64, f64, f64]
+    lib.oracle_cost_ola.restype = f64
+    lib.oracle_cost_ola.argtypes = [f64, f64, f64, f64, f64]
+    lib.oracle_best_ola_n.restype = i64
+    lib.oracle_best_ola_n.argtypes = [f64, f64, f64, f64, ctypes.c_int, ctypes.c_int]
+    lib.oracle_truncate.restype = i64
+    lib.oracle_truncate.argtypes = [P, i64, f64, P, P, P]
+    lib.oracle_gains.restype = ctypes.c_int
+    lib.oracle_gains.argtypes = [P, i64, i32, P, P]
+    lib.oracle_mix_direct.restype = None
+    lib.oracle_mix_direct.argtypes = [P, i64, i32, i32, P, P, P, P, P]
+    lib.oracle_truncate_batch.restype = ctypes.c_int
+    lib.oracle_truncate_batch.argtypes = [i64, P, P, f64, P, P, P, P, ctypes.c_int]
+    lib.oracle_forward_batch.restype = ctypes.c_int
+    lib.oracle_forward_batch.argtypes = [i32, i32, P, P, P, P, P, P, P, ctypes.c_int, P, P,
+                                         ctypes.c_int]
+    lib.oracle_backward_batch.restype = ctypes.c_int
+    lib.oracle_backward_batch.argtypes = [i32, i32, P, P, P, P, P, P, P, P, P, P, P,
+                                          ctypes.c_int]
+    lib.oracle_mix_ola.restype = ctypes.c_int
+    lib.oracle_mix_ola.argtypes = [P, i64, i32, i32, P, P, P, P, i64, P]
+    lib.oracle_forward_ola_batch.restype = ctypes.c_int
+    lib.oracle_forward_ola_batch.argtypes = [i32, i32, P, P, P, P, P, P, P, i64, P,
+                                             ctypes.c_int]
+    lib.oracle_dft_real.restype = None
+    lib.oracle_dft_real.argtypes = [P, i64, i64, P, P]
+    lib.oracle_max_threads.restype = ctypes.c_int
+    lib.oracle_max_threads.argtypes = []
+    return lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _i64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int64))
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+# ---- cost models (Eq. 3, 5, 6) -------------------------------------------------
+def cost_td(I, J, Nx, Nh, lib=None):
+    return (lib or _load()).oracle_cost_td(I, J, Nx, Nh)
+
+
+def cost_fft(I, J, N, lib=None):
+    return (lib or _load()).oracle_cost_fft(I, J, N)
+
+
+def cost_ola(I, J, Nx, Nh, N, lib=None):
+    return (lib or _load()).oracle_cost_ola(I, J, Nx, Nh, N)
+
+
+def best_ola_n(I, J, Nx, Nh, m_lo=6, m_hi=20, lib=None):
+    return int((lib or _load()).oracle_best_ola_n(I, J, Nx, Nh, m_lo, m_hi))
+
+
+def max_threads(lib=None) -> int:
+    return int((lib or _load()).oracle_max_threads())
+
+
+# ---- single-RIR / single-utterance entry points ----------------------------
+def truncate(h, eta_db, lib=None):
+    """Eq. 7-9 on one RIR.  Returns (L, peak, e_tot, e_kept)."""
+    h = _f64(h)
+    pk, et, ek = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    L = (lib or _load()).oracle_truncate(_p(h), h.shape[0], float(eta_db), ctypes.byref(pk),
+                                         ctypes.byref(et), ctypes.byref(ek))
+    if L < 0:
+        raise OracleError("invalid truncation arguments")
+    return int(L), pk.value, et.value, ek.value
+
+
+def gains(x_sources, snr_db, lib=None):
+    """Per-source gains for one utterance.  x_sources: [I, Nx]."""
+    x = _f64(x_sources)
+    I, nx = x.shape
+    snr = _f64(snr_db)
+    alpha = np.zeros(I)
+    rc = (lib or _load()).oracle_gains(_p(x), nx, I, _p(snr), _p(alpha))
+    if rc:
+        raise OracleError("noise source with zero power")
+    return alpha
+
+
+def mix_direct(x_sources, rirs, L, alpha, lib=None):
+    """Eq. 2 for one utterance.  x_sources [I, Nx]; rirs: list of I*J arrays in
+    (i, j) order; L: kept lengths [I*J]; alpha [I].  Returns y [J, Nx]."""
+    x = _f64(x_sources)
+    I, nx = x.shape
+    J = len(rirs) // I
+    off = _i64(np.concatenate([[0], np.cumsum([len(r) for r in rirs])])[:-1])
+    rir = _f64(np.concatenate([np.asarray(r, dtype=np.float64) for r in rirs]))
+    y = np.zeros((J, nx))
+    (lib or _load()).oracle_mix_direct(_p(x), nx, I, J, _p(rir), _p(off), _p(_i64(L)),
+                                       _p(_f64(alpha)), _p(y))
+    return y
+
+
+def mix_ola(x_sources, rirs, L, alpha, fft_n=0, lib=None):
+    """The paper's per-(i, j) OLA filtering, FP64.  Same arguments as mix_direct."""
+    x = _f64(x_sources)
+    I, nx = x.shape
+    J = len(rirs) // I
+    off = _i64(np.concatenate([[0], np.cumsum([len(r) for r in rirs])])[:-1])
+    rir = _f64(np.concatenate([np.asarray(r, dtype=np.float64) for r in rirs]))
+    y = np.zeros((J, nx))
+    rc = (lib or _load()).oracle_mix_ola(_p(x), nx, I, J, _p(rir), _p(off), _p(_i64(L)),
+                                         _p(_f64(alpha)), int(fft_n), _p(y))
+    if rc:
+        raise OracleError("invalid FFT size")
+    return y
+
+
+def dft_real(x, n_fft, lib=None):
+    x = _f64(x)
+    re, im = np.zeros(n_fft), np.zeros(n_fft)
+    (lib or _load()).oracle_dft_real(_p(x), x.shape[0], n_fft, _p(re), _p(im))
+    return re + 1j * im
+
+
+# ---- batch entry points ------------------------------------------------------
+def truncate_batch(batch, eta_db, nthreads=0, lib=None):
+    """Returns dict(L, peak, e_tot, e_kept) over all RIRs of the batch."""
+    lib = lib or _load()
+    R = batch.rir_len.shape[0]
+    L = np.zeros(R, np.int64)
+    pk, et, ek = np.zeros(R), np.zeros(R), np.zeros(R)
+    rir = _f64(batch.rir)
+    rc = lib.oracle_truncate_batch(R, _p(_i32(batch.rir_len)), _p(rir), float(eta_db),
+                                   _p(L), _p(pk), _p(et), _p(ek), nthreads)
+    if rc:
+        raise OracleError("invalid truncation arguments")
+    return dict(L=L, peak=pk, e_tot=et, e_kept=ek)
+
+
+def forward(batch, eta_db=20.0, alpha=None, nthreads=0, lib=None):
+    """Truncation, gains (from batch.snr_db unless alpha is given) and the
+    direct-form mix.  Returns dict(y, alpha, L, e_kept_frac)."""
+    lib = lib or _load()
+    tr = truncate_batch(batch, eta_db, nthreads, lib)
+    S = int(np.sum(batch.num_sources))
+    gain_mode = 0 if alpha is None else 1
+    a = np.zeros(S) if alpha is None else _f64(alpha).copy()
+    y = np.zeros(int(np.sum(batch.num_samples)) * batch.num_mics)
+    x = _f64(batch.x)
+    rir = _f64(batch.rir)
+    rc = lib.oracle_forward_batch(batch.num_sources.shape[0], batch.num_mics,
+                                  _p(_i32(batch.num_sources)), _p(_i64(batch.num_samples)),
+                                  _p(_i32(batch.rir_len)), _p(x), _p(rir), _p(tr["L"]),
+                                  _p(_f64(batch.snr_db)), gain_mode, _p(a), _p(y), nthreads)
+    if rc:
+        raise OracleError("noise source with zero power")
+    frac = np.where(tr["e_tot"] > 0, tr["e_kept"] / np.where(tr["e_tot"] > 0, tr["e_tot"], 1), 1.0)
+    return dict(y=y, alpha=a, L=tr["L"], e_kept_frac=frac)
+
+
+def backward(batch, L, alpha, g, nthreads=0, lib=None):
+    """Adjoint of the mix for fixed L and alpha.  Returns dict(dx, dh, dalpha)."""
+    lib = lib or _load()
+    S = int(np.sum(batch.num_sources))
+    dx = np.zeros(batch.x.shape[0])
+    dh = np.zeros(batch.rir.shape[0])
+    da = np.zeros(S)
+    x = _f64(batch.x)
+    rir = _f64(batch.rir)
+    lib.oracle_backward_batch(batch.num_sources.shape[0], batch.num_mics,
+                              _p(_i32(batch.num_sources)), _p(_i64(batch.num_samples)),
+                              _p(_i32(batch.rir_len)), _p(x), _p(rir), _p(_i64(L)),
+                              _p(_f64(alpha)), _p(_f64(g)), _p(dx), _p(dh), _p(da), nthreads)
+    return dict(dx=dx, dh=dh, dalpha=da)
+
+
+def forward_ola(batch, L, alpha, fft_n=0, nthreads=0, lib=None):
+    """The paper's OLA filtering over a batch (FP64), for given L and alpha."""
+    lib = lib or _load()
+    y = np.zeros(int(np.sum(batch.num_samples)) * batch.num_mics)
+    x = _f64(batch.x)
+    rir = _f64(batch.rir)
+    rc = lib.oracle_forward_ola_batch(batch.num_sources.shape[0], batch.num_mics,
+                                      _p(_i32(batch.num_sources)), _p(_i64(batch.num_samples)),
+                                      _p(_i32(batch.rir_len)), _p(x), _p(rir), _p(_i64(L)),
+                                      _p(_f64(alpha)), int(fft_n), _p(y), nthreads)
+    if rc:
+        raise OracleError("invalid FFT size")
+    return y
+
+
+def eta_is_none(eta_db) -> bool:
+    return math.isinf(eta_db)

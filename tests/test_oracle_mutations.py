@@ -1,0 +1,54 @@
+"""Planted mistakes: each plausible error in the oracle must fail a pin.
+
+A mutated copy of oracle.c is compiled into a temporary library and the pin
+suite is run against it in a subprocess (ORACLE_LIB points the oracle's
+loader at the mutant).  The pins are adequate only if every mutant fails.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "oracle.c")
+
+# (name, original text, planted text)
+MUTANTS = [
+    ("eq9_keeps_one_less", "L = n_c + 2;", "L = n_c + 1;"),
+    ("eq8_non_strict", "if (suffix < p_th) n_c = m;", "if (suffix <= p_th) n_c = m;"),
+    ("eq7_amplitude_threshold", "double p_th = pmax * factor;", "double p_th = pmax * sqrt(factor);"),
+    ("conv_drops_last_tap", "int64_t kmax = (n < Lij - 1) ? n : Lij - 1;\n            for (int64_t k = 0; k <= kmax; ++k) acc += h[k] * xi[n - k];\n            yj[n]",
+     "int64_t kmax = (n < Lij - 1) ? n : Lij - 2;\n            for (int64_t k = 0; k <= kmax; ++k) acc += h[k] * xi[n - k];\n            yj[n]"),
+    ("mix_ignores_gain", "yj[n] += alpha[i] * acc;", "yj[n] += acc;"),
+    ("gain_snr_sign", "pow(10.0, -snr_db[i] / 10.0)", "pow(10.0, snr_db[i] / 10.0)"),
+    ("gain_no_sqrt", "alpha[i] = sqrt(p0 / pi * pow(10.0, -snr_db[i] / 10.0));",
+     "alpha[i] = p0 / pi * pow(10.0, -snr_db[i] / 10.0);"),
+    ("dx_convolves_instead_of_correlates",
+     "for (int64_t k = 0; k < Lij && m + k < n_x; ++k) acc += h[k] * gj[m + k];",
+     "for (int64_t k = 0; k < Lij && m >= k; ++k) acc += h[k] * gj[m - k];"),
+    ("dh_transposed_operands", "acc += gj[n] * xi[n - k];", "acc += gj[n - k] * xi[n];"),
+    ("dh_missing_gain", "dhij[k] = alpha[i] * acc;", "dhij[k] = acc;"),
+    ("ola_hop_aliases", "int64_t hop = N - Lh + 1;", "int64_t hop = N - Lh + 2;"),
+    ("ola_missing_normalisation", "yj[s + n] += alpha[i] * Br[n] / (double)N;",
+     "yj[s + n] += alpha[i] * Br[n];"),
+    ("fft_twiddle_sign", "double ang = sign * 2.0 * M_PI * (double)k / (double)len;",
+     "double ang = -sign * 2.0 * M_PI * (double)k / (double)len;"),
+]
+
+
+@pytest.mark.parametrize("name,orig,planted", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(tmp_path, name, orig, planted):
+    src = open(SRC).read()
+    assert src.count(orig) == 1, f"mutation site for {name} not found exactly once"
+    mpath = tmp_path / "oracle_mutant.c"
+    mpath.write_text(src.replace(orig, planted))
+    lib = tmp_path / "liboracle_mutant.so"
+    subprocess.run(["gcc", "-O1", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                    "-std=c11", "-D_DEFAULT_SOURCE", str(mpath), "-o", str(lib), "-lm"],
+                   check=True)
+    env = dict(os.environ, ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutant {name} passed every pin:\n{r.stdout[-2000:]}"

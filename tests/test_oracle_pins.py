@@ -1,0 +1,377 @@
+"""Pins of the FP64 oracle to facts outside itself (CPU only).
+
+Each check ties the oracle to something it does not compute itself: values
+the paper prints (cost models), closed forms, textbook routines (an explicit
+DFT matrix, numpy's convolution), invariants (linearity, adjoint identities,
+energy bookkeeping) and brute force on tiny inputs.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1712_03439_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rng(seed=1):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+# ---------------------------------------------------------------------------
+# cost models: the numbers the paper prints (Eq. 3, Eq. 5, Eq. 6)
+# ---------------------------------------------------------------------------
+def _golden_costs():
+    out = {}
+    with open(os.path.join(GOLDEN, "cost_model.txt")) as f:
+        for line in f:
+            if not line.strip() or line.startswith("#"):
+                continue
+            name, val, tol = line.split()[:3]
+            out[name] = (float(val), float(tol))
+    return out
+
+
+def test_cost_models_match_paper_numbers():
+    g = _golden_costs()
+    I, J, Nx, Nh = 2.55, 2.0, 116991.0, 3893.0
+    val, tol = g["C_td"]
+    assert abs(oracle.cost_td(I, J, Nx, Nh) / val - 1) <= tol
+    val, tol = g["C_FFT_N2^17"]
+    assert abs(oracle.cost_fft(I, J, 2.0 ** 17) / val - 1) <= tol
+    best = oracle.best_ola_n(I, J, Nx, Nh, 6, 20)
+    assert best == 2 ** int(g["C_OLA_argmin_log2"][0])
+    val, tol = g["C_OLA_min"]
+    assert abs(oracle.cost_ola(I, J, Nx, Nh, best) / val - 1) <= tol
+
+
+def test_cost_ola_floor_reading_would_contradict_paper():
+    # With the printed floor the minimum would not be 50.8 M at 2^14; the
+    # ceiling reading is the one consistent with the paper's number.
+    I, J, Nx, Nh = 2.55, 2.0, 116991.0, 3893.0
+    N = 2.0 ** 14
+    floor_cost = I * J * (math.floor(Nx / (N - Nh + 1)) * (4 * N * 14 + 2 * N) + 2 * N * 14)
+    assert abs(floor_cost / 50.8e6 - 1) > 0.05
+    assert abs(oracle.cost_ola(I, J, Nx, Nh, N) / 50.8e6 - 1) < 0.001
+
+
+# ---------------------------------------------------------------------------
+# Eq. 2 by direct convolution
+# ---------------------------------------------------------------------------
+def _dft_matrix(n):
+    k = np.arange(n)
+    return np.exp(-2j * np.pi * np.outer(k, k) / n)
+
+
+@pytest.mark.parametrize("nx,nh", [(1, 1), (5, 3), (17, 9), (40, 24), (3, 30)])
+def test_direct_conv_equals_brute_force_dft_product(nx, nh):
+    r = _rng(nx * 100 + nh)
+    x = r.standard_normal((1, nx))
+    h = r.standard_normal(nh)
+    y = oracle.mix_direct(x, [h], [nh], [1.0])[0]
+    n = nx + nh - 1
+    F = _dft_matrix(n)
+    xp = np.zeros(n); xp[:nx] = x[0]
+    hp = np.zeros(n); hp[:nh] = h
+    full = np.real(np.conj(F) @ ((F @ xp) * (F @ hp)) / n)
+    np.testing.assert_allclose(y, full[:nx], rtol=0, atol=1e-12 * max(1, np.abs(full).max()))
+
+
+def test_direct_conv_equals_numpy_convolve_multi_source_multi_mic():
+    r = _rng(7)
+    I, J, nx = 3, 2, 500
+    x = r.standard_normal((I, nx))
+    rirs = [r.standard_normal(int(r.integers(1, 120))) for _ in range(I * J)]
+    L = [len(h) - int(r.integers(0, len(h))) for h in rirs]
+    alpha = r.uniform(0.1, 2.0, I)
+    y = oracle.mix_direct(x, rirs, L, alpha)
+    for j in range(J):
+        ref = np.zeros(nx)
+        for i in range(I):
+            ref += alpha[i] * np.convolve(x[i], rirs[i * J + j][:L[i * J + j]])[:nx]
+        np.testing.assert_allclose(y[j], ref, rtol=1e-12, atol=1e-12)
+
+
+def test_delta_rir_gives_shifted_signal():
+    r = _rng(3)
+    nx = 300
+    x = r.standard_normal((1, nx))
+    for d in [0, 1, 17, 299, 350]:
+        h = np.zeros(d + 1); h[d] = 1.0
+        y = oracle.mix_direct(x, [h], [d + 1], [0.75])[0]
+        ref = np.zeros(nx)
+        if d < nx:
+            ref[d:] = 0.75 * x[0, :nx - d]
+        np.testing.assert_array_equal(y, ref)
+
+
+def test_linearity_in_x_h_and_alpha():
+    r = _rng(11)
+    I, J, nx = 2, 2, 200
+    x1, x2 = r.standard_normal((I, nx)), r.standard_normal((I, nx))
+    h1 = [r.standard_normal(40) for _ in range(I * J)]
+    h2 = [r.standard_normal(40) for _ in range(I * J)]
+    L = [40] * (I * J)
+    al = np.array([1.0, 0.5])
+    a, b = 0.3, -1.7
+    y = oracle.mix_direct(a * x1 + b * x2, h1, L, al)
+    ref = a * oracle.mix_direct(x1, h1, L, al) + b * oracle.mix_direct(x2, h1, L, al)
+    np.testing.assert_allclose(y, ref, rtol=1e-12, atol=1e-12)
+    y = oracle.mix_direct(x1, [a * p + b * q for p, q in zip(h1, h2)], L, al)
+    ref = a * oracle.mix_direct(x1, h1, L, al) + b * oracle.mix_direct(x1, h2, L, al)
+    np.testing.assert_allclose(y, ref, rtol=1e-12, atol=1e-12)
+    # alpha enters per source: alpha = e_i picks source i alone
+    y0 = oracle.mix_direct(x1, h1, L, [1.0, 0.0])
+    y1 = oracle.mix_direct(x1, h1, L, [0.0, 1.0])
+    np.testing.assert_allclose(oracle.mix_direct(x1, h1, L, [2.0, -3.0]), 2 * y0 - 3 * y1,
+                               rtol=1e-12, atol=1e-12)
+
+
+def test_commutativity_h_star_x():
+    r = _rng(5)
+    n = 64
+    x = r.standard_normal(n)
+    h = r.standard_normal(n)
+    y1 = oracle.mix_direct(x[None, :], [h], [n], [1.0])[0]
+    y2 = oracle.mix_direct(h[None, :], [x], [n], [1.0])[0]
+    np.testing.assert_allclose(y1, y2, rtol=1e-12, atol=1e-12)
+
+
+def test_truncated_taps_do_not_contribute():
+    r = _rng(6)
+    x = r.standard_normal((1, 100))
+    h = r.standard_normal(50)
+    h2 = h.copy(); h2[20:] = r.standard_normal(30) * 100
+    np.testing.assert_array_equal(oracle.mix_direct(x, [h], [20], [1.0]),
+                                  oracle.mix_direct(x, [h2], [20], [1.0]))
+
+
+def test_pure_python_brute_force_tiny_batch():
+    b = synth.make_batch(99, [37, 23], [2, 3], synth.linear_pair_array(), (0.001, 0.002),
+                         n_taps=11)
+    out = oracle.forward(b, eta_db=math.inf)
+    y = out["y"]
+    al = out["alpha"]
+    J = b.num_mics
+    xo, ro, si, ri, yo = b.x_offsets(), b.rir_offsets(), b.src_index(), b.rir_index(), b.y_offsets()
+    for u in range(b.num_utts):
+        nx = int(b.num_samples[u])
+        for j in range(J):
+            for n in range(nx):
+                acc = 0.0
+                for i in range(int(b.num_sources[u])):
+                    s = si[u] + i
+                    rr = ri[u] + i * J + j
+                    h = b.rir[ro[rr]:ro[rr + 1]].astype(np.float64)
+                    xs = b.x[xo[s]:xo[s + 1]].astype(np.float64)
+                    t = 0.0
+                    for k in range(len(h)):
+                        if 0 <= n - k < nx:
+                            t += float(h[k]) * float(xs[n - k])
+                    acc += al[s] * t
+                assert abs(y[yo[u] + j * nx + n] - acc) <= 1e-12 * max(1.0, abs(acc))
+
+
+# ---------------------------------------------------------------------------
+# O2 (the paper's OLA) equals O1 (direct) for every FFT size
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("fft_n", [0, 256, 512, 1024, 2048, 4096])
+def test_ola_equals_direct_for_every_fft_size(fft_n):
+    r = _rng(21)
+    I, J, nx = 2, 2, 3000
+    x = r.standard_normal((I, nx))
+    rirs = [r.standard_normal(200) for _ in range(I * J)]
+    L = [200, 150, 37, 1]
+    al = [1.0, 0.3]
+    yd = oracle.mix_direct(x, rirs, L, al)
+    yo = oracle.mix_ola(x, rirs, L, al, fft_n)
+    assert np.linalg.norm(yo - yd) <= 1e-12 * np.linalg.norm(yd)
+
+
+def test_oracle_dft_matches_matrix_dft_and_parseval():
+    r = _rng(8)
+    for n in [1, 2, 8, 64]:
+        x = r.standard_normal(n)
+        X = oracle.dft_real(x, n)
+        np.testing.assert_allclose(X, _dft_matrix(n) @ x, atol=1e-12 * n)
+        assert abs(np.sum(np.abs(X) ** 2) / n - np.sum(x ** 2)) < 1e-10
+        # Hermitian symmetry of a real signal's spectrum
+        np.testing.assert_allclose(X[1:][::-1], np.conj(X[1:]), atol=1e-12 * n)
+
+
+# ---------------------------------------------------------------------------
+# Eq. 7-9 truncation
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("eta", [3.0, 10.0, 20.0, 30.0, 47.0, 100.0])
+def test_truncation_closed_form_dyadic_decay(eta):
+    # h[n] = +-2^-n: h^2[n] = 4^-n, peak 1, so h^2[n] >= 10^(-eta/10)
+    # iff n <= eta / (20 log10 2); Eq. 9 keeps one more sample.
+    r = _rng(int(eta))
+    n = 60
+    h = (2.0 ** -np.arange(n)) * r.choice([-1.0, 1.0], n)
+    nc = math.floor(eta / (20 * math.log10(2)))
+    L, pk, et, ek = oracle.truncate(h.astype(np.float32), eta)
+    assert pk == 1.0
+    assert L == min(nc + 2, n)
+
+
+def test_truncation_keeps_sample_exactly_at_threshold():
+    # eta = 0 gives p_th = peak power exactly; a later sample of equal
+    # magnitude is "not below" the threshold and so is kept (Eq. 8 uses <).
+    h = np.array([1.0, 0.5, -1.0, 0.25, 0.1, 0.0], np.float32)
+    L, *_ = oracle.truncate(h, 0.0)
+    assert L == 4            # n_c = 2, keep 0..3
+
+
+def test_truncation_uses_last_crossing_not_first():
+    # a late reflection above threshold after a dip keeps everything up to it
+    h = np.array([1.0, 0.01, 0.01, 0.5, 0.01, 0.01, 0.01, 0.01], np.float32)
+    L, *_ = oracle.truncate(h, 10.0)
+    assert L == 5            # n_c = 3
+
+
+def test_truncation_special_cases():
+    h = np.zeros(100, np.float32)
+    assert oracle.truncate(h, 20.0)[0] == 1                 # all-zero RIR
+    r = _rng(4)
+    h = r.standard_normal(300).astype(np.float32)
+    assert oracle.truncate(h, math.inf)[0] == 300           # no cut-off
+    last_peak = int(np.max(np.nonzero(np.abs(h) == np.max(np.abs(h)))[0]))
+    assert oracle.truncate(h, 0.0)[0] == min(last_peak + 2, 300)
+    assert oracle.truncate(np.array([0.3], np.float32), 20.0)[0] == 1
+    with pytest.raises(oracle.OracleError):
+        oracle.truncate(h, -1.0)
+    with pytest.raises(oracle.OracleError):
+        oracle.truncate(h, float("nan"))
+
+
+def test_truncation_invariants_on_synthetic_rirs():
+    b = synth.config_home(n_utts=6)
+    for eta in [10.0, 20.0, 30.0]:
+        tr = oracle.truncate_batch(b, eta)
+        ro = b.rir_offsets()
+        for r in range(b.num_rirs):
+            h = b.rir[ro[r]:ro[r + 1]].astype(np.float64)
+            p = h * h
+            L = int(tr["L"][r])
+            pth = p.max() * 10.0 ** (-eta / 10.0)
+            nc = L - 2
+            assert 1 <= L <= len(h)
+            if L < len(h):
+                assert np.all(p[nc + 1:] < pth)      # everything dropped is below
+                assert p[nc] >= pth                  # n_c itself is not below
+            assert abs(tr["e_kept"][r] + p[L:].sum() - tr["e_tot"][r]) <= 1e-12 * tr["e_tot"][r]
+            assert abs(tr["e_tot"][r] - p.sum()) <= 1e-12 * p.sum()
+        # larger eta never keeps less
+    l10 = oracle.truncate_batch(b, 10.0)["L"]
+    l30 = oracle.truncate_batch(b, 30.0)["L"]
+    assert np.all(l30 >= l10)
+
+
+# ---------------------------------------------------------------------------
+# gains
+# ---------------------------------------------------------------------------
+def test_gains_realise_requested_snr_on_dry_mix():
+    r = _rng(12)
+    I, nx = 4, 5000
+    x = r.standard_normal((I, nx)) * r.uniform(0.1, 3.0, (I, 1))
+    snr = np.array([0.0, 0.0, 12.5, 30.0])
+    a = oracle.gains(x, snr)
+    assert a[0] == 1.0
+    p = np.mean(x ** 2, axis=1)
+    for i in range(1, I):
+        got = 10 * np.log10(p[0] / (a[i] ** 2 * p[i]))
+        assert abs(got - snr[i]) < 1e-12
+
+
+def test_gains_reject_silent_noise_source():
+    x = np.ones((2, 10))
+    x[1] = 0
+    with pytest.raises(oracle.OracleError):
+        oracle.gains(x, [0.0, 10.0])
+
+
+# ---------------------------------------------------------------------------
+# gradients
+# ---------------------------------------------------------------------------
+def _fd_setup():
+    b = synth.config_fd_subcase()
+    S = int(np.sum(b.num_sources))
+    alpha = np.linspace(0.6, 1.4, S)
+    g = synth.grad_like(5, b.y_size)
+    return b, alpha, g
+
+
+def test_adjoint_identities():
+    b, alpha, g = _fd_setup()
+    L = oracle.truncate_batch(b, math.inf)["L"]
+    y = oracle.forward(b, math.inf, alpha=alpha)["y"]
+    gr = oracle.backward(b, L, alpha, g)
+    lhs = float(np.dot(g, y))
+    # <g, A x> = <A^T g, x>, = sum <dh, h>, = sum alpha_i dalpha_i
+    assert abs(np.dot(gr["dx"], b.x.astype(np.float64)) - lhs) <= 1e-11 * abs(lhs)
+    assert abs(np.dot(gr["dh"], b.rir.astype(np.float64)) - lhs) <= 1e-11 * abs(lhs)
+    assert abs(np.dot(gr["dalpha"], alpha) - lhs) <= 1e-11 * abs(lhs)
+
+
+def test_gradients_match_central_finite_differences():
+    # Loss = 0.5 ||y - t||^2.  y is linear in each of x, h, alpha separately,
+    # so a central difference in FP64 is exact up to rounding.
+    b, alpha, _ = _fd_setup()
+    L = oracle.truncate_batch(b, math.inf)["L"]
+    t = synth.grad_like(6, b.y_size)
+    lib = oracle._load()
+
+    def loss(bb, al):
+        y = oracle.forward(bb, math.inf, alpha=al, lib=lib)["y"]
+        return 0.5 * float(np.sum((y - t) ** 2)), y
+
+    l0, y0 = loss(b, alpha)
+    gr = oracle.backward(b, L, alpha, y0 - t)
+    r = _rng(13)
+
+    class B64:
+        pass
+
+    def with_arrays(x=None, rir=None):
+        c = B64()
+        for k in ("num_mics", "num_sources", "num_samples", "rir_len", "snr_db"):
+            setattr(c, k, getattr(b, k))
+        c.x = b.x.astype(np.float64) if x is None else x
+        c.rir = b.rir.astype(np.float64) if rir is None else rir
+        return c
+
+    for idx in r.integers(0, b.x.shape[0], 6):
+        eps = 1e-3 * float(np.sqrt(np.mean(b.x.astype(np.float64) ** 2)))
+        xp, xm = b.x.astype(np.float64), b.x.astype(np.float64)
+        xp = xp.copy(); xm = xm.copy()
+        xp[idx] += eps; xm[idx] -= eps
+        fd = (loss(with_arrays(x=xp), alpha)[0] - loss(with_arrays(x=xm), alpha)[0]) / (2 * eps)
+        assert abs(fd - gr["dx"][idx]) <= 1e-4 * max(abs(fd), 1e-3 * np.abs(gr["dx"]).max())
+    for idx in r.integers(0, b.rir.shape[0], 6):
+        eps = 1e-3 * float(np.sqrt(np.mean(b.rir.astype(np.float64) ** 2)))
+        hp, hm = b.rir.astype(np.float64).copy(), b.rir.astype(np.float64).copy()
+        hp[idx] += eps; hm[idx] -= eps
+        fd = (loss(with_arrays(rir=hp), alpha)[0] - loss(with_arrays(rir=hm), alpha)[0]) / (2 * eps)
+        assert abs(fd - gr["dh"][idx]) <= 1e-4 * max(abs(fd), 1e-3 * np.abs(gr["dh"]).max())
+    for s in range(alpha.shape[0]):
+        eps = 1e-4
+        ap, am = alpha.copy(), alpha.copy()
+        ap[s] += eps; am[s] -= eps
+        fd = (loss(b, ap)[0] - loss(b, am)[0]) / (2 * eps)
+        assert abs(fd - gr["dalpha"][s]) <= 1e-6 * max(abs(fd), 1.0)
+
+
+def test_rir_gradient_is_zero_beyond_kept_length():
+    b = synth.config_fd_subcase()
+    out = oracle.forward(b, 10.0)
+    g = synth.grad_like(8, b.y_size)
+    gr = oracle.backward(b, out["L"], out["alpha"], g)
+    ro = b.rir_offsets()
+    for r in range(b.num_rirs):
+        L = int(out["L"][r])
+        assert np.all(gr["dh"][ro[r] + L:ro[r + 1]] == 0.0)
+        assert np.any(gr["dh"][ro[r]:ro[r] + L] != 0.0)
