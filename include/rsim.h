@@ -1,0 +1,149 @@
+/*
+ * rsim: GPU room-simulator filter-and-mix (C ABI).
+ *
+ * Computes, for a batch of utterances, the far-field microphone signals of
+ * the room simulator (Kim et al., "Efficient Implementation of the Room
+ * Simulator for Training Deep Neural Network Acoustic Models"):
+ *
+ *   Eq. 7-9  hhat_ij = h_ij cut where its power falls eta dB below its peak
+ *   Eq. 2    y_j[n]  = sum_i alpha_i (hhat_ij * x_i)[n],  n in [0, Nx)
+ *
+ * by overlap-add FFT filtering (Sec. 2.2, Eq. 6), and its adjoint (gradients
+ * with respect to x_i, h_ij and alpha_i).  All arithmetic runs in CUDA
+ * kernels on one GPU; the library has no CPU fallback.
+ *
+ * Packed layouts (all FP32, device memory unless stated otherwise):
+ *   x    [sum_u I_u * Nx_u]            utterance, then source, then sample
+ *   rir  [sum_u sum_{i,j} Nh_uij]      utterance, then source i, then mic j,
+ *                                      then tap; RIR index r = rir0_u + i*J + j
+ *   y    [sum_u J * Nx_u]              utterance, then mic, then sample
+ *   per-source arrays (snr_db, gains)  [sum_u I_u], utterance then source
+ *   per-RIR arrays (trunc_len, ...)    [sum_u I_u * J], RIR index order
+ * Source 0 of every utterance is the target; sources 1.. are noise sources.
+ *
+ * Ownership: every buffer passed to a call belongs to the caller and must
+ * stay valid until the work queued on the call's stream has finished.  The
+ * plan owns its scratch memory (allocated in rsim_plan, freed in
+ * rsim_plan_destroy) and must not be used by two streams at once.
+ *
+ * Errors: every call returns an rsim_status; rsim_last_error() gives a
+ * message for the calling thread's last failure.  Argument errors are found
+ * on the host before any work is queued.  Conditions only the device can see
+ * (a truncated RIR longer than every allowed FFT size permits, a silent noise
+ * source that must meet an SNR) are latched in the plan and reported by
+ * rsim_plan_sync_status().
+ */
+#ifndef RSIM_H_
+#define RSIM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rsim_plan_s *rsim_plan_t;
+
+typedef enum {
+    RSIM_OK = 0,
+    RSIM_E_INVALID = 1,      /* bad argument (shape, pointer, value) */
+    RSIM_E_UNSUPPORTED = 2,  /* valid request outside what the kernels support */
+    RSIM_E_NOMEM = 3,        /* device allocation failed */
+    RSIM_E_CUDA = 4,         /* a CUDA runtime call failed */
+    RSIM_E_DEVICE = 5,       /* error latched by a kernel (see rsim_last_error) */
+    RSIM_E_STATE = 6         /* call out of order (backward before forward) */
+} rsim_status;
+
+/* Shapes and options of a plan (host memory, copied by rsim_plan). */
+typedef struct {
+    int32_t num_utts;              /* U >= 1 */
+    int32_t num_mics;              /* J >= 1, shared by the batch */
+    const int32_t *num_sources;    /* [U], 1 <= I_u <= 16 */
+    const int64_t *num_samples;    /* [U], Nx_u >= 1 */
+    const int32_t *rir_len;        /* [sum_u I_u J], Nh >= 1 (before the cut-off) */
+    double eta_db;                 /* Eq. 7 threshold in dB, >= 0; +INFINITY keeps every tap */
+    int32_t fft_sizes_mask;        /* bit m allows N = 2^m, m in [11, 14]; 0 = all of them */
+    int32_t gain_mode;             /* 0: alpha from SNRs (computed, written to gains);
+                                      1: alpha given by the caller in gains */
+    int64_t segment_len;           /* samples per work tile; 0 = default (65536);
+                                      raised to the largest allowed N */
+    const float *fft_cost;         /* [32] host, relative cost of one real FFT of size 2^m
+                                      used to pick N per utterance; NULL = N log2 N */
+} rsim_plan_desc;
+
+/* Creates a plan for the given shapes on CUDA device `device`.  Validates the
+ * description, allocates scratch and uploads twiddle tables.  On success *out
+ * holds a plan to be released with rsim_plan_destroy. */
+rsim_status rsim_plan(const rsim_plan_desc *desc, int device, rsim_plan_t *out);
+
+/* Forward filter-and-mix (Eq. 7-9 truncation, gains, Eq. 2 by overlap-add).
+ *   stream            cudaStream_t to queue the work on (NULL = legacy default)
+ *   x                 packed sources, read only
+ *   rir               packed RIRs, read only
+ *   snr_db            [sum I_u] SNR of each noise source in dB relative to the
+ *                     utterance's target (dry-signal mean power over [0, Nx));
+ *                     entry of the target ignored.  Used when gain_mode = 0,
+ *                     may be NULL when gain_mode = 1.
+ *   gains             [sum I_u] alpha_i: written when gain_mode = 0 (alpha_0 = 1,
+ *                     alpha_i = sqrt(P_0 / P_i * 10^(-SNR_i/10))), read when 1
+ *   y                 packed output, overwritten
+ *   trunc_len         [R] int32 kept lengths L (Eq. 9), or NULL
+ *   energy_kept_frac  [R] sum_{n<L} h^2 / sum_n h^2, or NULL
+ * The call is asynchronous.  The plan keeps the truncation lengths, the FFT
+ * sizes and the RIR spectra for the next rsim_filter_mix_backward. */
+rsim_status rsim_filter_mix(rsim_plan_t plan, void *stream, const float *x, const float *rir,
+                            const float *snr_db, float *gains, float *y, int32_t *trunc_len,
+                            float *energy_kept_frac);
+
+/* Adjoint of the last rsim_filter_mix on this plan (same x, rir and gains
+ * buffers, unchanged).  With grad_y = dLoss/dy:
+ *   grad_x     [like x]    alpha_i sum_j (hhat_ij correlated with grad_y_j)
+ *   grad_rir   [like rir]  alpha_i (grad_y_j correlated with x_i) for taps < L,
+ *                          0 for taps >= L (the cut-off is a fixed mask)
+ *   grad_gains [sum I_u]   <grad_y_j, hhat_ij * x_i> summed over j; gains are
+ *                          treated as inputs (no gradient flows to the SNRs)
+ * grad_x may be NULL (not computed); grad_rir and grad_gains must be given.
+ * Returns RSIM_E_STATE if no forward ran on the plan.  Asynchronous. */
+rsim_status rsim_filter_mix_backward(rsim_plan_t plan, void *stream, const float *grad_y,
+                                     const float *x, const float *gains, float *grad_x,
+                                     float *grad_rir, float *grad_gains);
+
+/* Waits for the plan's stream work and reports errors latched by kernels
+ * (RSIM_E_UNSUPPORTED: no allowed FFT size fits a truncated RIR;
+ * RSIM_E_INVALID: a noise source has zero power).  Clears the latch. */
+rsim_status rsim_plan_sync_status(rsim_plan_t plan, void *stream);
+
+/* Copies the per-utterance plan chosen on the device by the last forward:
+ * log2 of the FFT size, hop (N - L_max + 1), L_max and block count, each [U]
+ * int32 host arrays (any may be NULL).  Synchronises the stream. */
+rsim_status rsim_plan_query(rsim_plan_t plan, void *stream, int32_t *log2_n, int32_t *hop,
+                            int32_t *l_max, int32_t *num_blocks);
+
+/* Stage timing.  When enabled, later calls record CUDA events on their
+ * stream around each stage; rsim_plan_stage_times() synchronises the plan's
+ * device, adds up the recorded durations (at most the last 64 calls) and
+ * resets them.  Stages, in array order:
+ *   0 truncation (Eq. 7-9)     1 source power       2 planner (N, queues, gains)
+ *   3 RIR spectra              4 OLA forward        5 segment fix-up
+ *   6 OLA backward             7 backward reduction
+ * ms[8] receives milliseconds summed over calls, calls[8] the number of calls
+ * summed (either may be NULL). */
+#define RSIM_NUM_STAGES 8
+rsim_status rsim_plan_set_timing(rsim_plan_t plan, int enable);
+rsim_status rsim_plan_stage_times(rsim_plan_t plan, double *ms, int32_t *calls);
+
+/* Bytes of device scratch owned by the plan. */
+int64_t rsim_plan_scratch_bytes(rsim_plan_t plan);
+
+/* Releases the plan and its device memory (NULL is ignored).  The caller must
+ * make sure no queued work still uses it. */
+void rsim_plan_destroy(rsim_plan_t plan);
+
+/* Message describing the calling thread's last error ("" if none). */
+const char *rsim_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSIM_H_ */

@@ -1,0 +1,19 @@
+"""GPU (sm_103a) overlap-add room-simulator filter-and-mix.
+
+Public API (loaded lazily so that importing the package, or its synthetic
+input generators, does not need a GPU):
+  Plan                 -- a plan for a batch shape (wraps rsim_plan)
+  filter_mix           -- forward with allocated outputs
+  RsimFilterMix        -- torch.autograd.Function with the hand-written adjoint
+  filter_mix_autograd  -- RsimFilterMix.apply
+"""
+_API = ("Plan", "filter_mix", "RsimFilterMix", "filter_mix_autograd")
+
+__all__ = list(_API) + ["synth", "build"]
+
+
+def __getattr__(name):
+    if name in _API:
+        from . import api
+        return getattr(api, name)
+    raise AttributeError(name)

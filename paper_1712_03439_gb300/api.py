@@ -1,0 +1,199 @@
+"""Python front end of the rsim C-ABI.
+
+Argument marshalling only: torch tensors provide device memory and the
+current CUDA stream; every step of the computation runs in librsim.so.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import numpy as np
+import torch
+
+from . import _lib
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _want(t, n, dtype, name):
+    if t is None:
+        return
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{name}: expected a contiguous {dtype} tensor of {n} elements, "
+                         f"got {t.dtype} {tuple(t.shape)}")
+
+
+class Plan:
+    """A plan for a batch shape: utterance lengths, sources per utterance,
+    microphones and RIR lengths (see rsim_plan in include/rsim.h)."""
+
+    def __init__(self, num_sources, num_samples, rir_len, num_mics, eta_db=20.0,
+                 fft_sizes=None, gain_mode=0, segment_len=0, fft_cost=None, device=None):
+        self._lib = _lib.load()
+        self._handle = None
+        self.num_sources = np.ascontiguousarray(num_sources, dtype=np.int32)
+        self.num_samples = np.ascontiguousarray(num_samples, dtype=np.int64)
+        self.rir_len = np.ascontiguousarray(rir_len, dtype=np.int32)
+        self.num_mics = int(num_mics)
+        self.gain_mode = int(gain_mode)
+        self.eta_db = float(eta_db)
+        mask = 0
+        for n in (fft_sizes or []):
+            m = int(round(math.log2(n)))
+            if 1 << m != n:
+                raise ValueError(f"FFT size {n} is not a power of two")
+            mask |= 1 << m
+        self._cost = None
+        if fft_cost is not None:
+            self._cost = np.zeros(32, np.float32)
+            for n, c in dict(fft_cost).items():
+                self._cost[int(round(math.log2(n)))] = c
+        desc = _lib.PlanDesc(
+            num_utts=self.num_sources.shape[0], num_mics=self.num_mics,
+            num_sources=self.num_sources.ctypes.data, num_samples=self.num_samples.ctypes.data,
+            rir_len=self.rir_len.ctypes.data, eta_db=self.eta_db, fft_sizes_mask=mask,
+            gain_mode=self.gain_mode, segment_len=int(segment_len),
+            fft_cost=None if self._cost is None else self._cost.ctypes.data)
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        _lib.check(self._lib, self._lib.rsim_plan(ctypes.byref(desc), self.device, ctypes.byref(h)))
+        self._handle = h
+        self.U = int(self.num_sources.shape[0])
+        self.S = int(self.num_sources.sum())
+        self.R = int(self.rir_len.shape[0])
+        self.x_size = int(np.sum(self.num_sources.astype(np.int64) * self.num_samples))
+        self.y_size = int(np.sum(self.num_samples) * self.num_mics)
+        self.rir_size = int(np.sum(self.rir_len.astype(np.int64)))
+
+    @classmethod
+    def for_batch(cls, batch, **kw):
+        return cls(batch.num_sources, batch.num_samples, batch.rir_len, batch.num_mics, **kw)
+
+    # ------------------------------------------------------------------
+    def filter_mix(self, x, rir, gains, y, snr_db=None, trunc_len=None, energy_kept_frac=None,
+                   stream=None):
+        """rsim_filter_mix: writes y (and gains when gain_mode = 0)."""
+        _want(x, self.x_size, torch.float32, "x")
+        _want(rir, self.rir_size, torch.float32, "rir")
+        _want(gains, self.S, torch.float32, "gains")
+        _want(y, self.y_size, torch.float32, "y")
+        _want(snr_db, self.S, torch.float32, "snr_db")
+        _want(trunc_len, self.R, torch.int32, "trunc_len")
+        _want(energy_kept_frac, self.R, torch.float32, "energy_kept_frac")
+        st = self._lib.rsim_filter_mix(self._handle, _stream(stream), _ptr(x), _ptr(rir),
+                                       _ptr(snr_db), _ptr(gains), _ptr(y), _ptr(trunc_len),
+                                       _ptr(energy_kept_frac))
+        _lib.check(self._lib, st)
+
+    def filter_mix_backward(self, grad_y, x, gains, grad_x, grad_rir, grad_gains, stream=None):
+        """rsim_filter_mix_backward: writes grad_x (if given), grad_rir and grad_gains."""
+        _want(grad_y, self.y_size, torch.float32, "grad_y")
+        _want(x, self.x_size, torch.float32, "x")
+        _want(gains, self.S, torch.float32, "gains")
+        _want(grad_x, self.x_size, torch.float32, "grad_x")
+        _want(grad_rir, self.rir_size, torch.float32, "grad_rir")
+        _want(grad_gains, self.S, torch.float32, "grad_gains")
+        st = self._lib.rsim_filter_mix_backward(self._handle, _stream(stream), _ptr(grad_y), _ptr(x),
+                                                _ptr(gains), _ptr(grad_x), _ptr(grad_rir),
+                                                _ptr(grad_gains))
+        _lib.check(self._lib, st)
+
+    def sync_status(self, stream=None):
+        _lib.check(self._lib, self._lib.rsim_plan_sync_status(self._handle, _stream(stream)))
+
+    def query(self, stream=None):
+        """Per-utterance plan of the last forward: log2 N, hop, L_max, blocks."""
+        out = {k: np.zeros(self.U, np.int32) for k in ("log2_n", "hop", "l_max", "num_blocks")}
+        st = self._lib.rsim_plan_query(self._handle, _stream(stream),
+                                       *(ctypes.c_void_p(out[k].ctypes.data)
+                                         for k in ("log2_n", "hop", "l_max", "num_blocks")))
+        _lib.check(self._lib, st)
+        return out
+
+    def set_timing(self, enable: bool):
+        _lib.check(self._lib, self._lib.rsim_plan_set_timing(self._handle, int(bool(enable))))
+
+    def stage_times(self):
+        """{stage: (total ms, calls)} recorded since the last query (synchronises)."""
+        ms = np.zeros(len(_lib.STAGES), np.float64)
+        calls = np.zeros(len(_lib.STAGES), np.int32)
+        _lib.check(self._lib, self._lib.rsim_plan_stage_times(
+            self._handle, ctypes.c_void_p(ms.ctypes.data), ctypes.c_void_p(calls.ctypes.data)))
+        return {k: (float(ms[i]), int(calls[i])) for i, k in enumerate(_lib.STAGES)}
+
+    @property
+    def scratch_bytes(self) -> int:
+        return int(self._lib.rsim_plan_scratch_bytes(self._handle))
+
+    def close(self):
+        if self._handle is not None:
+            self._lib.rsim_plan_destroy(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# convenience and autograd
+# ---------------------------------------------------------------------------
+def filter_mix(plan: Plan, x, rir, snr_db=None, gains=None, stream=None):
+    """Allocates outputs and runs the forward.  Returns dict(y, gains, trunc_len,
+    energy_kept_frac)."""
+    dev = x.device
+    y = torch.empty(plan.y_size, dtype=torch.float32, device=dev)
+    if gains is None:
+        gains = torch.empty(plan.S, dtype=torch.float32, device=dev)
+    tl = torch.empty(plan.R, dtype=torch.int32, device=dev)
+    ekf = torch.empty(plan.R, dtype=torch.float32, device=dev)
+    plan.filter_mix(x, rir, gains, y, snr_db=snr_db, trunc_len=tl, energy_kept_frac=ekf,
+                    stream=stream)
+    return dict(y=y, gains=gains, trunc_len=tl, energy_kept_frac=ekf)
+
+
+class RsimFilterMix(torch.autograd.Function):
+    """y = filter_mix(x, rir, gains) with the hand-written adjoint.
+
+    The plan must use gain_mode = 1 (gains are an input).  The truncation is
+    a fixed mask: grad_rir is zero beyond each kept length."""
+
+    @staticmethod
+    def forward(ctx, plan, x, rir, gains):
+        if plan.gain_mode != 1:
+            raise ValueError("RsimFilterMix needs a plan with gain_mode=1")
+        x, rir, gains = x.contiguous(), rir.contiguous(), gains.contiguous()
+        y = torch.empty(plan.y_size, dtype=torch.float32, device=x.device)
+        plan.filter_mix(x, rir, gains, y)
+        ctx.plan = plan
+        ctx.save_for_backward(x, gains)
+        return y
+
+    @staticmethod
+    def backward(ctx, grad_y):
+        plan = ctx.plan
+        x, gains = ctx.saved_tensors
+        grad_y = grad_y.contiguous()
+        gx = torch.empty(plan.x_size, dtype=torch.float32, device=x.device) if ctx.needs_input_grad[1] else None
+        gr = torch.empty(plan.rir_size, dtype=torch.float32, device=x.device)
+        gg = torch.empty(plan.S, dtype=torch.float32, device=x.device)
+        plan.filter_mix_backward(grad_y, x, gains, gx, gr, gg)
+        return None, gx, gr, gg
+
+
+def filter_mix_autograd(plan: Plan, x, rir, gains):
+    return RsimFilterMix.apply(plan, x, rir, gains)

@@ -1,0 +1,510 @@
+// C-ABI of the room-simulator filter-and-mix library: plan creation, scratch
+// management, twiddle tables and the launch sequences of the forward and
+// backward passes.  Every step of the computation runs in the kernels of
+// rsim_prep.cu, rsim_forward.cu and rsim_backward.cu.
+#include "rsim.h"
+#include "rsim_fft.cuh"
+#include "rsim_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace rsim;
+
+namespace {
+
+thread_local std::string g_err;
+
+rsim_status fail(rsim_status st, const std::string& msg) {
+    g_err = msg;
+    return st;
+}
+
+rsim_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(RSIM_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+class DeviceGuard {
+  public:
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev_);
+        if (prev_ != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() { cudaSetDevice(prev_); }
+  private:
+    int prev_ = 0;
+};
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// exp(-2 pi i num / den) in FP64, rounded once to FP32
+float2 twiddle(int64_t num, int64_t den) {
+    num %= den;
+    const double ang = -2.0 * M_PI * (double)num / (double)den;
+    return make_float2((float)std::cos(ang), (float)std::sin(ang));
+}
+
+template <int M>
+std::vector<float2> twiddle_table() {
+    using P = FftPlan<M>;
+    std::vector<float2> tw(P::TW_LEN);
+    for (int m = 0; m < 16; ++m)
+        for (int k = 0; k < 16; ++k) tw[P::OFF1 + m * 16 + k] = twiddle((int64_t)m * k, 256);
+    for (int m = 0; m < P::R2; ++m)
+        for (int k = 0; k < 256; ++k) tw[P::OFF2 + m * 256 + k] = twiddle((int64_t)m * k, 256 * P::R2);
+    if (M == 8192)
+        for (int m = 0; m < 2; ++m)
+            for (int k = 0; k < 4096; ++k) tw[P::OFF3 + m * 4096 + k] = twiddle((int64_t)m * k, 8192);
+    for (int k = 0; k <= M / 2; ++k) tw[P::OFF_SPLIT + k] = twiddle(k, 2 * M);
+    return tw;
+}
+
+std::vector<float2> twiddle_table_for(int logN) {
+    switch (logN) {
+        case 11: return twiddle_table<1024>();
+        case 12: return twiddle_table<2048>();
+        case 13: return twiddle_table<4096>();
+        case 14: return twiddle_table<8192>();
+    }
+    return {};
+}
+
+}  // namespace
+
+constexpr int kRing = 64;
+
+struct StageTimer {
+    bool on = false;
+    int count[RSIM_NUM_STAGES] = {};
+    cudaEvent_t ev[RSIM_NUM_STAGES][kRing][2] = {};
+};
+
+struct rsim_plan_s {
+    int device = 0;
+    int sms = 0;
+    DevBatch B{};
+    Queues Q{};
+    double factor = 0.0;
+    int none = 0;
+    int gain_mode = 0;
+    int mask = 0;
+    void* dmem = nullptr;
+    size_t dbytes = 0;
+    float2* Hc = nullptr;
+    float* tails = nullptr;
+    float* dhp = nullptr;
+    float* dap = nullptr;
+    float2* tw[kNumBuckets] = {};
+    int grid_trunc = 1, grid_pow = 1;
+    int grid_spec[kNumBuckets] = {}, grid_fwd[kNumBuckets] = {}, grid_bwd[kNumBuckets] = {};
+    bool fwd_done = false;
+    StageTimer timer;
+};
+
+namespace {
+
+// records the start (end = false) or end of a stage when timing is enabled
+void stage_mark(rsim_plan_t p, int stage, bool end, cudaStream_t st) {
+    if (!p->timer.on) return;
+    const int slot = p->timer.count[stage] % kRing;
+    cudaEvent_t& e = p->timer.ev[stage][slot][end ? 1 : 0];
+    if (!e) cudaEventCreate(&e);
+    cudaEventRecord(e, st);
+    if (end) ++p->timer.count[stage];
+}
+
+}  // namespace
+
+extern "C" const char* rsim_last_error(void) { return g_err.c_str(); }
+
+extern "C" int64_t rsim_plan_scratch_bytes(rsim_plan_t plan) { return plan ? (int64_t)plan->dbytes : 0; }
+
+extern "C" void rsim_plan_destroy(rsim_plan_t plan) {
+    if (!plan) return;
+    {
+        DeviceGuard g(plan->device);
+        for (auto& st : plan->timer.ev)
+            for (auto& sl : st)
+                for (auto& e : sl)
+                    if (e) cudaEventDestroy(e);
+        if (plan->dmem) cudaFree(plan->dmem);
+    }
+    delete plan;
+}
+
+extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_t* out) {
+    g_err.clear();
+    if (!d || !out) return fail(RSIM_E_INVALID, "rsim_plan: NULL argument");
+    *out = nullptr;
+    const int U = d->num_utts, J = d->num_mics;
+    if (U < 1) return fail(RSIM_E_INVALID, "num_utts must be >= 1");
+    if (J < 1 || J > 64) return fail(RSIM_E_INVALID, "num_mics must be in [1, 64]");
+    if (!d->num_sources || !d->num_samples || !d->rir_len)
+        return fail(RSIM_E_INVALID, "num_sources, num_samples and rir_len are required");
+    if (!(d->eta_db >= 0.0)) return fail(RSIM_E_INVALID, "eta_db must be >= 0 or +inf");
+    if (d->gain_mode != 0 && d->gain_mode != 1) return fail(RSIM_E_INVALID, "gain_mode must be 0 or 1");
+    int mask = d->fft_sizes_mask;
+    const int supported = ((1 << (kMaxLog + 1)) - 1) & ~((1 << kMinLog) - 1);
+    if (mask == 0) mask = supported;
+    if (mask & ~supported)
+        return fail(RSIM_E_UNSUPPORTED, "fft_sizes_mask allows sizes outside 2^11 .. 2^14");
+    if (d->segment_len < 0) return fail(RSIM_E_INVALID, "segment_len must be >= 0");
+
+    std::vector<int32_t> src0(U + 1), rir0(U + 1), seg0(U + 1);
+    std::vector<int64_t> yoff(U + 1);
+    int64_t S = 0, R = 0, ysz = 0;
+    int imax = 1;
+    int64_t nx_max = 1;
+    int max_log = kMinLog;
+    for (int m = kMinLog; m <= kMaxLog; ++m)
+        if ((mask >> m) & 1) max_log = m;
+    int64_t seg_len = d->segment_len > 0 ? d->segment_len : 65536;
+    seg_len = std::max<int64_t>(seg_len, (int64_t)1 << max_log);
+    int64_t nseg = 0;
+    for (int u = 0; u < U; ++u) {
+        const int I = d->num_sources[u];
+        const int64_t nx = d->num_samples[u];
+        if (I < 1 || I > kMaxSources) return fail(RSIM_E_INVALID, "num_sources[u] must be in [1, 16]");
+        if (nx < 1) return fail(RSIM_E_INVALID, "num_samples[u] must be >= 1");
+        src0[u] = (int32_t)S;
+        rir0[u] = (int32_t)R;
+        seg0[u] = (int32_t)nseg;
+        yoff[u] = ysz;
+        S += I;
+        R += (int64_t)I * J;
+        ysz += (int64_t)J * nx;
+        nseg += (nx + seg_len - 1) / seg_len;
+        imax = std::max(imax, I);
+        nx_max = std::max(nx_max, nx);
+        if (S > INT32_MAX / 2 || R > INT32_MAX / 2 || nseg * kMaxSources > INT32_MAX / 2)
+            return fail(RSIM_E_UNSUPPORTED, "batch too large");
+    }
+    src0[U] = (int32_t)S;
+    rir0[U] = (int32_t)R;
+    seg0[U] = (int32_t)nseg;
+    yoff[U] = ysz;
+    std::vector<int32_t> rlen(d->rir_len, d->rir_len + R);
+    std::vector<int64_t> roff(R + 1), xoff(S + 1);
+    roff[0] = 0;
+    for (int64_t r = 0; r < R; ++r) {
+        if (rlen[r] < 1) return fail(RSIM_E_INVALID, "rir_len[r] must be >= 1");
+        roff[r + 1] = roff[r] + rlen[r];
+    }
+    {
+        int64_t o = 0;
+        for (int u = 0; u < U; ++u)
+            for (int i = 0; i < d->num_sources[u]; ++i) {
+                xoff[src0[u] + i] = o;
+                o += d->num_samples[u];
+            }
+        xoff[S] = o;
+    }
+    std::vector<int32_t> seg_utt(nseg);
+    std::vector<int64_t> dhp_off(nseg + 1);
+    int64_t dhp_total = 0;
+    for (int u = 0; u < U; ++u) {
+        const int64_t rsum = roff[rir0[u + 1]] - roff[rir0[u]];
+        for (int g = seg0[u]; g < seg0[u + 1]; ++g) {
+            seg_utt[g] = u;
+            dhp_off[g] = dhp_total;
+            dhp_total += rsum;
+        }
+    }
+    dhp_off[nseg] = dhp_total;
+    const int MMAX = 1 << (max_log - 1);
+    const int CH = (int)((nx_max + kPowerChunk - 1) / kPowerChunk);
+
+    rsim_plan_t p = new rsim_plan_s();
+    p->device = device;
+    p->gain_mode = d->gain_mode;
+    p->mask = mask;
+    p->none = std::isinf(d->eta_db) ? 1 : 0;
+    p->factor = p->none ? 0.0 : std::pow(10.0, -d->eta_db / 10.0);
+
+    DeviceGuard guard(device);
+    cudaError_t e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "cudaDeviceGetAttribute");
+    }
+
+    // ---- carve one device allocation
+    struct Piece { void** dst; size_t bytes; };
+    std::vector<Piece> pieces;
+    void *p_nsrc, *p_nx, *p_src0, *p_rir0, *p_seg0, *p_segutt, *p_xoff, *p_yoff, *p_roff, *p_rlen,
+        *p_dhpoff, *p_tuning, *p_L, *p_logN, *p_hop, *p_lmax, *p_nblk, *p_pow, *p_err, *p_list,
+        *p_count, *p_next, *p_Hc, *p_tails, *p_dhp, *p_dap;
+    void* p_tw[kNumBuckets] = {};
+    const int64_t cap = std::max<int64_t>(nseg * kMaxSources, R);
+    pieces.push_back({&p_nsrc, sizeof(int32_t) * U});
+    pieces.push_back({&p_nx, sizeof(int64_t) * U});
+    pieces.push_back({&p_src0, sizeof(int32_t) * (U + 1)});
+    pieces.push_back({&p_rir0, sizeof(int32_t) * (U + 1)});
+    pieces.push_back({&p_seg0, sizeof(int32_t) * (U + 1)});
+    pieces.push_back({&p_segutt, sizeof(int32_t) * std::max<int64_t>(nseg, 1)});
+    pieces.push_back({&p_xoff, sizeof(int64_t) * (S + 1)});
+    pieces.push_back({&p_yoff, sizeof(int64_t) * (U + 1)});
+    pieces.push_back({&p_roff, sizeof(int64_t) * (R + 1)});
+    pieces.push_back({&p_rlen, sizeof(int32_t) * R});
+    pieces.push_back({&p_dhpoff, sizeof(int64_t) * (nseg + 1)});
+    pieces.push_back({&p_tuning, sizeof(float) * 32});
+    pieces.push_back({&p_L, sizeof(int32_t) * R});
+    pieces.push_back({&p_logN, sizeof(int32_t) * U});
+    pieces.push_back({&p_hop, sizeof(int32_t) * U});
+    pieces.push_back({&p_lmax, sizeof(int32_t) * U});
+    pieces.push_back({&p_nblk, sizeof(int32_t) * U});
+    pieces.push_back({&p_pow, sizeof(double) * S * CH});
+    pieces.push_back({&p_err, sizeof(int32_t) * 4});
+    pieces.push_back({&p_list, sizeof(int32_t) * kNumLists * kNumBuckets * cap});
+    pieces.push_back({&p_count, sizeof(int32_t) * kNumLists * kNumBuckets});
+    pieces.push_back({&p_next, sizeof(int32_t) * kNumLists * kNumBuckets});
+    pieces.push_back({&p_Hc, sizeof(float2) * R * MMAX});
+    pieces.push_back({&p_tails, sizeof(float) * nseg * J * MMAX});
+    pieces.push_back({&p_dhp, sizeof(float) * std::max<int64_t>(dhp_total, 1)});
+    pieces.push_back({&p_dap, sizeof(float) * nseg * kMaxSources});
+    std::vector<std::vector<float2>> tws(kNumBuckets);
+    for (int m = kMinLog; m <= kMaxLog; ++m) {
+        if (!((mask >> m) & 1)) continue;
+        tws[m - kMinLog] = twiddle_table_for(m);
+        pieces.push_back({&p_tw[m - kMinLog], sizeof(float2) * tws[m - kMinLog].size()});
+    }
+    size_t total = 0;
+    for (auto& pc : pieces) total = align_up(total, 256) + pc.bytes;
+    total = align_up(total, 256);
+    e = cudaMalloc(&p->dmem, total);
+    if (e != cudaSuccess) {
+        delete p;
+        cudaGetLastError();
+        return fail(RSIM_E_NOMEM, "cudaMalloc of " + std::to_string(total) + " bytes failed");
+    }
+    p->dbytes = total;
+    {
+        size_t off = 0;
+        for (auto& pc : pieces) {
+            off = align_up(off, 256);
+            *pc.dst = (char*)p->dmem + off;
+            off += pc.bytes;
+        }
+    }
+    // ---- uploads
+    std::vector<float> tuning(32, 0.f);
+    for (int m = 0; m < 32; ++m) tuning[m] = d->fft_cost ? d->fft_cost[m] : (float)((double)m * std::ldexp(1.0, m));
+    std::vector<int32_t> nsrc(d->num_sources, d->num_sources + U);
+    std::vector<int64_t> nxv(d->num_samples, d->num_samples + U);
+    struct Up { void* dst; const void* src; size_t bytes; };
+    std::vector<Up> ups = {
+        {p_nsrc, nsrc.data(), sizeof(int32_t) * U},
+        {p_nx, nxv.data(), sizeof(int64_t) * U},
+        {p_src0, src0.data(), sizeof(int32_t) * (U + 1)},
+        {p_rir0, rir0.data(), sizeof(int32_t) * (U + 1)},
+        {p_seg0, seg0.data(), sizeof(int32_t) * (U + 1)},
+        {p_segutt, seg_utt.data(), sizeof(int32_t) * nseg},
+        {p_xoff, xoff.data(), sizeof(int64_t) * (S + 1)},
+        {p_yoff, yoff.data(), sizeof(int64_t) * (U + 1)},
+        {p_roff, roff.data(), sizeof(int64_t) * (R + 1)},
+        {p_rlen, rlen.data(), sizeof(int32_t) * R},
+        {p_dhpoff, dhp_off.data(), sizeof(int64_t) * (nseg + 1)},
+        {p_tuning, tuning.data(), sizeof(float) * 32},
+    };
+    for (int b = 0; b < kNumBuckets; ++b)
+        if (p_tw[b]) ups.push_back({p_tw[b], tws[b].data(), sizeof(float2) * tws[b].size()});
+    for (auto& up : ups) {
+        if (up.bytes == 0) continue;
+        e = cudaMemcpy(up.dst, up.src, up.bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            rsim_plan_destroy(p);
+            return cuda_fail(e, "cudaMemcpy (plan upload)");
+        }
+    }
+    e = cudaMemset(p_err, 0, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) e = cudaMemset(p_count, 0, sizeof(int32_t) * kNumLists * kNumBuckets);
+    if (e != cudaSuccess) {
+        rsim_plan_destroy(p);
+        return cuda_fail(e, "cudaMemset (plan)");
+    }
+
+    DevBatch& B = p->B;
+    B.U = U; B.J = J; B.S = (int32_t)S; B.R = (int32_t)R; B.IMAX = imax;
+    B.NSEG = (int32_t)nseg; B.MMAX = MMAX; B.mask = mask; B.seg_len = seg_len;
+    B.gain_mode = d->gain_mode;
+    B.n_src = (const int32_t*)p_nsrc; B.n_x = (const int64_t*)p_nx;
+    B.src0 = (const int32_t*)p_src0; B.rir0 = (const int32_t*)p_rir0;
+    B.seg0 = (const int32_t*)p_seg0; B.seg_utt = (const int32_t*)p_segutt;
+    B.xoff = (const int64_t*)p_xoff; B.yoff = (const int64_t*)p_yoff;
+    B.roff = (const int64_t*)p_roff; B.rir_len = (const int32_t*)p_rlen;
+    B.dhp_off = (const int64_t*)p_dhpoff; B.tuning = (const float*)p_tuning;
+    B.L = (int32_t*)p_L; B.logN = (int32_t*)p_logN; B.hop = (int32_t*)p_hop;
+    B.Lmax = (int32_t*)p_lmax; B.nblk = (int32_t*)p_nblk;
+    B.pow_part = (double*)p_pow; B.CH = CH; B.err = (int32_t*)p_err;
+    p->Q.list = (int32_t*)p_list; p->Q.count = (int32_t*)p_count; p->Q.next = (int32_t*)p_next;
+    p->Q.cap = (int32_t)cap;
+    p->Hc = (float2*)p_Hc; p->tails = (float*)p_tails; p->dhp = (float*)p_dhp; p->dap = (float*)p_dap;
+    for (int b = 0; b < kNumBuckets; ++b) p->tw[b] = (float2*)p_tw[b];
+
+    // ---- launch shapes
+    p->grid_trunc = (int)std::max<int64_t>(1, std::min<int64_t>(R, (int64_t)p->sms * 8));
+    p->grid_pow = (int)std::max<int64_t>(1, std::min<int64_t>(S * CH, (int64_t)p->sms * 8));
+    for (int m = kMinLog; m <= kMaxLog; ++m) {
+        if (!((mask >> m) & 1)) continue;
+        const int b = m - kMinLog;
+        p->grid_spec[b] = (int)std::max<int64_t>(1, std::min<int64_t>(R, (int64_t)p->sms * occupancy_spectrum(m)));
+        p->grid_fwd[b] = (int)std::max<int64_t>(1, std::min<int64_t>(nseg, (int64_t)p->sms * occupancy_forward(m)));
+        p->grid_bwd[b] = (int)std::max<int64_t>(
+            1, std::min<int64_t>(nseg * imax, (int64_t)p->sms * occupancy_backward(m)));
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        rsim_plan_destroy(p);
+        return cuda_fail(e, "kernel attribute setup");
+    }
+    *out = p;
+    return RSIM_OK;
+}
+
+extern "C" rsim_status rsim_filter_mix(rsim_plan_t p, void* stream, const float* x, const float* rir,
+                                       const float* snr_db, float* gains, float* y, int32_t* trunc_len,
+                                       float* energy_kept_frac) {
+    g_err.clear();
+    if (!p) return fail(RSIM_E_INVALID, "NULL plan");
+    if (!x || !rir || !gains || !y) return fail(RSIM_E_INVALID, "x, rir, gains and y are required");
+    if (p->gain_mode == 0 && !snr_db) return fail(RSIM_E_INVALID, "snr_db is required when gain_mode = 0");
+    DeviceGuard guard(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const DevBatch& B = p->B;
+    stage_mark(p, 0, false, st);
+    launch_truncate(B, rir, p->factor, p->none, energy_kept_frac, p->grid_trunc, st);
+    stage_mark(p, 0, true, st);
+    if (p->gain_mode == 0) {
+        stage_mark(p, 1, false, st);
+        launch_power(B, x, p->grid_pow, st);
+        stage_mark(p, 1, true, st);
+    }
+    stage_mark(p, 2, false, st);
+    launch_plan(B, p->Q, snr_db, gains, st);
+    stage_mark(p, 2, true, st);
+    stage_mark(p, 3, false, st);
+    for (int m = kMinLog; m <= kMaxLog; ++m)
+        if ((p->mask >> m) & 1)
+            launch_spectrum(m, B, p->Q, rir, p->Hc, p->tw[m - kMinLog], p->grid_spec[m - kMinLog], st);
+    stage_mark(p, 3, true, st);
+    stage_mark(p, 4, false, st);
+    for (int m = kMinLog; m <= kMaxLog; ++m)
+        if ((p->mask >> m) & 1)
+            launch_forward(m, B, p->Q, x, gains, p->Hc, y, p->tails, p->tw[m - kMinLog],
+                           p->grid_fwd[m - kMinLog], st);
+    stage_mark(p, 4, true, st);
+    stage_mark(p, 5, false, st);
+    launch_fixup(B, y, p->tails, st);
+    stage_mark(p, 5, true, st);
+    if (trunc_len) {
+        cudaError_t e = cudaMemcpyAsync(trunc_len, B.L, sizeof(int32_t) * B.R, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync (trunc_len)");
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+    p->fwd_done = true;
+    return RSIM_OK;
+}
+
+extern "C" rsim_status rsim_filter_mix_backward(rsim_plan_t p, void* stream, const float* grad_y,
+                                                const float* x, const float* gains, float* grad_x,
+                                                float* grad_rir, float* grad_gains) {
+    g_err.clear();
+    if (!p) return fail(RSIM_E_INVALID, "NULL plan");
+    if (!p->fwd_done) return fail(RSIM_E_STATE, "rsim_filter_mix_backward before rsim_filter_mix");
+    if (!grad_y || !x || !gains || !grad_rir || !grad_gains)
+        return fail(RSIM_E_INVALID, "grad_y, x, gains, grad_rir and grad_gains are required");
+    DeviceGuard guard(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const DevBatch& B = p->B;
+    cudaError_t e = cudaMemsetAsync(p->Q.next + p->Q.idx(kListBwd, 0), 0, sizeof(int32_t) * kNumBuckets, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (queue)");
+    stage_mark(p, 6, false, st);
+    for (int m = kMinLog; m <= kMaxLog; ++m)
+        if ((p->mask >> m) & 1)
+            launch_backward(m, B, p->Q, grad_y, x, gains, p->Hc, grad_x, p->dhp, p->dap,
+                            p->tw[m - kMinLog], p->grid_bwd[m - kMinLog], st);
+    stage_mark(p, 6, true, st);
+    stage_mark(p, 7, false, st);
+    launch_finalize(B, gains, p->dhp, p->dap, grad_rir, grad_gains, st);
+    stage_mark(p, 7, true, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+    return RSIM_OK;
+}
+
+extern "C" rsim_status rsim_plan_sync_status(rsim_plan_t p, void* stream) {
+    g_err.clear();
+    if (!p) return fail(RSIM_E_INVALID, "NULL plan");
+    DeviceGuard guard(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    int32_t err = 0;
+    e = cudaMemcpy(&err, p->B.err, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy (error word)");
+    if (err) {
+        cudaMemset(p->B.err, 0, sizeof(int32_t));
+        if (err & kErrNoFftSize)
+            return fail(RSIM_E_UNSUPPORTED,
+                        "a truncated RIR is longer than N/2+1 for every allowed FFT size N");
+        if (err & kErrZeroPower)
+            return fail(RSIM_E_INVALID, "a noise source has zero power but an SNR to meet");
+        return fail(RSIM_E_DEVICE, "device error " + std::to_string(err));
+    }
+    return RSIM_OK;
+}
+
+extern "C" rsim_status rsim_plan_query(rsim_plan_t p, void* stream, int32_t* log2_n, int32_t* hop,
+                                       int32_t* l_max, int32_t* num_blocks) {
+    g_err.clear();
+    if (!p) return fail(RSIM_E_INVALID, "NULL plan");
+    if (!p->fwd_done) return fail(RSIM_E_STATE, "rsim_plan_query before rsim_filter_mix");
+    DeviceGuard guard(p->device);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    const size_t n = sizeof(int32_t) * p->B.U;
+    if (log2_n && (e = cudaMemcpy(log2_n, p->B.logN, n, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpy");
+    if (hop && (e = cudaMemcpy(hop, p->B.hop, n, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpy");
+    if (l_max && (e = cudaMemcpy(l_max, p->B.Lmax, n, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpy");
+    if (num_blocks && (e = cudaMemcpy(num_blocks, p->B.nblk, n, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpy");
+    return RSIM_OK;
+}
+
+extern "C" rsim_status rsim_plan_set_timing(rsim_plan_t p, int enable) {
+    g_err.clear();
+    if (!p) return fail(RSIM_E_INVALID, "NULL plan");
+    p->timer.on = enable != 0;
+    for (int s = 0; s < RSIM_NUM_STAGES; ++s) p->timer.count[s] = 0;
+    return RSIM_OK;
+}
+
+extern "C" rsim_status rsim_plan_stage_times(rsim_plan_t p, double* ms, int32_t* calls) {
+    g_err.clear();
+    if (!p) return fail(RSIM_E_INVALID, "NULL plan");
+    DeviceGuard guard(p->device);
+    for (int s = 0; s < RSIM_NUM_STAGES; ++s) {
+        const int n = std::min(p->timer.count[s], kRing);
+        double tot = 0.0;
+        for (int k = 0; k < n; ++k) {
+            cudaEvent_t a = p->timer.ev[s][k][0], b = p->timer.ev[s][k][1];
+            cudaError_t e = cudaEventSynchronize(b);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+            float f = 0.f;
+            e = cudaEventElapsedTime(&f, a, b);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+            tot += f;
+        }
+        if (ms) ms[s] = tot;
+        if (calls) calls[s] = n;
+        p->timer.count[s] = 0;
+    }
+    return RSIM_OK;
+}

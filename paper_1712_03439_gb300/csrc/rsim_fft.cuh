@@ -1,0 +1,336 @@
+// Block-level FFT building blocks for the overlap-add filter (sm_103a, FP32).
+//
+// A real N-point transform is computed as a complex M = N/2-point transform of
+// z[n] = x[2n] + i x[2n+1] followed by the even/odd split (the "half spectrum"
+// of Sec. 2.2: only bins 0..N/2 are kept, Hermitian symmetry gives the rest).
+//
+// The complex transform is a Stockham auto-sort FFT: each thread of a CTA of
+// T = M/16 threads holds E = 16 complex values in registers; passes of radix
+// 16 (or 8/4/2 for the last factor) run in registers and exchange through one
+// padded shared-memory buffer.  Between passes thread t holds indices
+// t + s*T, s < E ("strided layout"), which is both the load pattern of every
+// pass and the output pattern of the last pass, so the last pass never touches
+// shared memory.
+//
+// Twiddles come from tables built on the host in FP64 and rounded once to
+// FP32 (no fast-math intrinsics).  The inverse transform is computed as
+// conj(FFT(conj(.))) so one code path serves both directions.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rsim {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+    return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+// a * (-i)
+__device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }
+// a * (+i)
+__device__ __forceinline__ float2 mul_pi(float2 a) { return make_float2(-a.y, a.x); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// ---------------------------------------------------------------------------
+// small DFTs in registers, natural-order output, forward sign (e^{-2 pi i nk/R})
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void dft2(float2& a0, float2& a1) {
+    float2 t = a0;
+    a0 = cadd(t, a1);
+    a1 = csub(t, a1);
+}
+
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+    float2 t0 = cadd(a0, a2), t1 = csub(a0, a2);
+    float2 t2 = cadd(a1, a3), t3 = mul_mi(csub(a1, a3));
+    a0 = cadd(t0, t2);
+    a2 = csub(t0, t2);
+    a1 = cadd(t1, t3);
+    a3 = csub(t1, t3);
+}
+
+// cos and sin of 2*pi*e/16 for e = 1, 2, 3
+#define RSIM_C1 0.92387953251128675613f
+#define RSIM_S1 0.38268343236508977173f
+#define RSIM_R2 0.70710678118654752440f
+
+// multiply by w16^e = e^{-2 pi i e / 16} for the exponents a 16-point
+// transform needs (e in {0, 1, 2, 3, 4, 6, 9})
+template <int e>
+__device__ __forceinline__ float2 w16(float2 a) {
+    if constexpr (e == 0) return a;
+    else if constexpr (e == 1) return cmul(a, make_float2(RSIM_C1, -RSIM_S1));
+    else if constexpr (e == 2) return make_float2(RSIM_R2 * (a.x + a.y), RSIM_R2 * (a.y - a.x));
+    else if constexpr (e == 3) return cmul(a, make_float2(RSIM_S1, -RSIM_C1));
+    else if constexpr (e == 4) return mul_mi(a);
+    else if constexpr (e == 6) return make_float2(RSIM_R2 * (a.y - a.x), -RSIM_R2 * (a.x + a.y));
+    else if constexpr (e == 9) return cmul(a, make_float2(-RSIM_C1, RSIM_S1));
+    else return a;  // unused
+}
+
+__device__ __forceinline__ void dft8(float2 (&a)[8]) {
+    // n = 2 n1 + n2, k = k1 + 4 k2
+    dft4(a[0], a[2], a[4], a[6]);
+    dft4(a[1], a[3], a[5], a[7]);
+    // twiddle w8^{n2 k1} = w16^{2 k1} on the odd half
+    a[3] = w16<2>(a[3]);
+    a[5] = w16<4>(a[5]);
+    a[7] = w16<6>(a[7]);
+    float2 b[8];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        float2 e = a[2 * k1], o = a[2 * k1 + 1];
+        b[k1] = cadd(e, o);
+        b[k1 + 4] = csub(e, o);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = b[k];
+}
+
+__device__ __forceinline__ void dft16(float2 (&a)[16]) {
+    // n = 4 n1 + n2, k = k1 + 4 k2
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4(a[n2], a[n2 + 4], a[n2 + 8], a[n2 + 12]);
+    // now a[n2 + 4 k1] = B[n2][k1]; twiddle by w16^{n2 k1}
+    a[5] = w16<1>(a[5]);
+    a[9] = w16<2>(a[9]);
+    a[13] = w16<3>(a[13]);
+    a[6] = w16<2>(a[6]);
+    a[10] = w16<4>(a[10]);
+    a[14] = w16<6>(a[14]);
+    a[7] = w16<3>(a[7]);
+    a[11] = w16<6>(a[11]);
+    a[15] = w16<9>(a[15]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4(a[4 * k1], a[4 * k1 + 1], a[4 * k1 + 2], a[4 * k1 + 3]);
+    // a[4 k1 + k2] = A[k1 + 4 k2]: transpose the 4x4 index
+    float2 b[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) b[k1 + 4 * k2] = a[4 * k1 + k2];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a[k] = b[k];
+}
+
+template <int R>
+__device__ __forceinline__ void dft(float2 (&u)[R]) {
+    if constexpr (R == 2) dft2(u[0], u[1]);
+    else if constexpr (R == 4) dft4(u[0], u[1], u[2], u[3]);
+    else if constexpr (R == 8) dft8(u);
+    else dft16(u);
+}
+
+// ---------------------------------------------------------------------------
+// FFT plans: T = M/16 threads, E = 16 values per thread
+// ---------------------------------------------------------------------------
+constexpr int kE = 16;
+
+// padded shared-memory index: one spare float2 every 16 keeps both the
+// strided loads and the radix-16 scatter stores free of bank conflicts
+__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int padded_len(int M) { return M + (M >> 4); }
+
+template <int M>
+struct FftPlan {
+    static constexpr int T = M / kE;
+    // radix of the last pass; the others are 16
+    static constexpr int R_LAST = (M == 1024) ? 4 : (M == 2048) ? 8 : (M == 4096) ? 16 : 2;
+    static constexpr int NPASS = (M == 8192) ? 4 : 3;
+    // twiddle table layout: pass p (p >= 1) has LP*R entries at offset OFF_p,
+    // entry [m * LP + k] = exp(-2 pi i m k / (LP R)); then the split table
+    static constexpr int R2 = (M == 8192) ? 16 : R_LAST;   // radix of pass 2
+    static constexpr int OFF1 = 0;                          // LP = 16, R = 16
+    static constexpr int OFF2 = OFF1 + 16 * 16;             // LP = 256, R = R2
+    static constexpr int OFF3 = OFF2 + 256 * R2;            // LP = 4096, R = 2 (M = 8192)
+    static constexpr int OFF_SPLIT = (M == 8192) ? OFF3 + 4096 * 2 : OFF3;
+    static constexpr int TW_LEN = OFF_SPLIT + M / 2 + 1;    // split: exp(-2 pi i k / (2M))
+};
+
+// One Stockham pass of radix R with LP = product of the earlier radices.
+// Input: v in strided layout.  If LAST, the output stays in v (strided);
+// otherwise it is scattered to shared memory.
+template <int M, int R, int LP, bool LAST>
+__device__ __forceinline__ void fft_pass(float2 (&v)[kE], float2* __restrict__ sm,
+                                         const float2* __restrict__ tw, int t) {
+    constexpr int T = M / kE;
+    constexpr int NB = kE / R;  // butterflies per thread
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        float2 u[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) u[m] = v[q + m * NB];
+        const int i = t + q * T;
+        const int k = i & (LP - 1);
+        if constexpr (LP > 1) {
+#pragma unroll
+            for (int m = 1; m < R; ++m) u[m] = cmul(u[m], __ldg(&tw[m * LP + k]));
+        }
+        dft<R>(u);
+        if constexpr (LAST) {
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[q + m * NB] = u[m];
+        } else {
+            const int base = (i - k) * R + k;
+#pragma unroll
+            for (int m = 0; m < R; ++m) sm[pad(base + m * LP)] = u[m];
+        }
+    }
+}
+
+template <int M>
+__device__ __forceinline__ void load_strided(float2 (&v)[kE], const float2* __restrict__ sm, int t) {
+    constexpr int T = M / kE;
+#pragma unroll
+    for (int s = 0; s < kE; ++s) v[s] = sm[pad(t + s * T)];
+}
+
+template <int M>
+__device__ __forceinline__ void store_strided(const float2 (&v)[kE], float2* __restrict__ sm, int t) {
+    constexpr int T = M / kE;
+#pragma unroll
+    for (int s = 0; s < kE; ++s) sm[pad(t + s * T)] = v[s];
+}
+
+// Complex forward FFT of size M.  v: strided input in registers; on return v
+// holds the spectrum in strided layout (natural bin index t + s*T).
+// Starts with a __syncthreads so the caller may still be reading sm.
+template <int M>
+__device__ __forceinline__ void fft_core(float2 (&v)[kE], float2* __restrict__ sm,
+                                         const float2* __restrict__ tw, int t) {
+    using P = FftPlan<M>;
+    __syncthreads();
+    fft_pass<M, 16, 1, false>(v, sm, tw, t);
+    __syncthreads();
+    load_strided<M>(v, sm, t);
+    __syncthreads();
+    fft_pass<M, 16, 16, false>(v, sm, tw + P::OFF1, t);
+    __syncthreads();
+    load_strided<M>(v, sm, t);
+    if constexpr (P::NPASS == 3) {
+        fft_pass<M, P::R_LAST, 256, true>(v, sm, tw + P::OFF2, t);
+    } else {
+        __syncthreads();
+        fft_pass<M, 16, 256, false>(v, sm, tw + P::OFF2, t);
+        __syncthreads();
+        load_strided<M>(v, sm, t);
+        fft_pass<M, 2, 4096, true>(v, sm, tw + P::OFF3, t);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// real-signal helpers
+// ---------------------------------------------------------------------------
+
+// Loads z[n] = x[2n] + i x[2n+1] for the strided indices of thread t from a
+// real segment src[0, len) (zero outside).  src may be unaligned.
+template <int M>
+__device__ __forceinline__ void load_real_strided(float2 (&v)[kE], const float* __restrict__ src,
+                                                  int64_t len, int t) {
+    constexpr int T = M / kE;
+#pragma unroll
+    for (int s = 0; s < kE; ++s) {
+        const int64_t n = 2 * (int64_t)(t + s * T);
+        float a = (n < len) ? __ldg(src + n) : 0.f;
+        float b = (n + 1 < len) ? __ldg(src + n + 1) : 0.f;
+        v[s] = make_float2(a, b);
+    }
+}
+
+// Pair layout of a half spectrum: thread t owns, for s < E/2, bins
+// k_s = t + s*T (k_s < M/2) and their mirrors M - k_s, in P[2s] and P[2s+1].
+// Thread 0, s = 0 owns slot 0 -- (X[0], X[M]) packed as one float2 (both are
+// real) -- in P[0], and the self-mirrored bin M/2 in P[1].
+
+// Split: from Z = FFT_M(z) in shared memory (natural order, padded) to the
+// true half spectrum X of the real 2M-point signal, in pair layout.
+// wsplit[k] = exp(-2 pi i k / (2M)).
+template <int M>
+__device__ __forceinline__ void split_forward(float2 (&P)[kE], const float2* __restrict__ sm,
+                                              const float2* __restrict__ wsplit, int t) {
+    constexpr int T = M / kE;
+#pragma unroll
+    for (int s = 0; s < kE / 2; ++s) {
+        const int k = t + s * T;
+        if (k == 0) {
+            float2 z0 = sm[pad(0)];
+            float2 zh = sm[pad(M / 2)];
+            P[0] = make_float2(z0.x + z0.y, z0.x - z0.y);   // (X[0], X[M])
+            P[1] = conjf2(zh);                               // X[M/2]
+        } else {
+            float2 zk = sm[pad(k)];
+            float2 zm = conjf2(sm[pad(M - k)]);
+            float2 E = cscale(cadd(zk, zm), 0.5f);
+            float2 O = cscale(mul_mi(csub(zk, zm)), 0.5f);   // (zk - zm) / (2i)
+            float2 wO = cmul(__ldg(&wsplit[k]), O);
+            P[2 * s] = cadd(E, wO);                          // X[k]
+            P[2 * s + 1] = conjf2(csub(E, wO));              // X[M-k]
+        }
+    }
+}
+
+// Inverse pre-processing: from a half spectrum Y in pair layout to
+// conj(Z') in shared memory (natural order), where Z' = 2 FFT_M(z) of the
+// signal y = IDFT_{2M}(Y) * 2M.  Running fft_core on it and conjugating gives
+// z[n] = y[2n] + i y[2n+1] scaled by 2M (unnormalised inverse).
+template <int M>
+__device__ __forceinline__ void split_inverse_store(const float2 (&P)[kE], float2* __restrict__ sm,
+                                                    const float2* __restrict__ wsplit, int t) {
+    constexpr int T = M / kE;
+#pragma unroll
+    for (int s = 0; s < kE / 2; ++s) {
+        const int k = t + s * T;
+        if (k == 0) {
+            float2 y = P[0];                                 // (Y[0], Y[M])
+            float2 z0 = make_float2(y.x + y.y, y.x - y.y);
+            sm[pad(0)] = conjf2(z0);
+            sm[pad(M / 2)] = cscale(P[1], 2.f);              // conj(2 conj(Y[M/2]))
+        } else {
+            float2 yk = P[2 * s], ym = conjf2(P[2 * s + 1]);
+            float2 E = cadd(yk, ym);
+            float2 D = csub(yk, ym);
+            float2 O = cmulc(__ldg(&wsplit[k]), D);          // D * conj(w^k)
+            float2 zk = cadd(E, mul_pi(O));                  // E + i O
+            float2 zm = cadd(conjf2(E), mul_pi(conjf2(O)));  // conj(E) + i conj(O)
+            sm[pad(k)] = conjf2(zk);
+            sm[pad(M - k)] = conjf2(zm);
+        }
+    }
+}
+
+// Forward real FFT of src[0, len) zero-padded to 2M, into pair layout P.
+template <int M>
+__device__ __forceinline__ void rfft_pairs(float2 (&P)[kE], const float* __restrict__ src, int64_t len,
+                                           float2* __restrict__ sm, const float2* __restrict__ tw, int t) {
+    using Pl = FftPlan<M>;
+    float2 v[kE];
+    load_real_strided<M>(v, src, len, t);
+    fft_core<M>(v, sm, tw, t);
+    __syncthreads();                 // everyone done with the last pass loads
+    store_strided<M>(v, sm, t);
+    __syncthreads();
+    split_forward<M>(P, sm, tw + Pl::OFF_SPLIT, t);
+}
+
+// Unnormalised inverse real FFT of a half spectrum in pair layout.  On return
+// v[s] holds (y[2n], y[2n+1]) * 2M for n = t + s*T.
+template <int M>
+__device__ __forceinline__ void irfft_pairs(float2 (&v)[kE], const float2 (&P)[kE],
+                                            float2* __restrict__ sm, const float2* __restrict__ tw, int t) {
+    using Pl = FftPlan<M>;
+    __syncthreads();                 // sm may still be read by a previous phase
+    split_inverse_store<M>(P, sm, tw + Pl::OFF_SPLIT, t);
+    __syncthreads();
+    load_strided<M>(v, sm, t);
+    fft_core<M>(v, sm, tw, t);
+#pragma unroll
+    for (int s = 0; s < kE; ++s) v[s] = conjf2(v[s]);
+}
+
+}  // namespace rsim

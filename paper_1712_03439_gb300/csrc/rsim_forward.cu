@@ -1,0 +1,275 @@
+// Forward path: RIR spectra (computed once per RIR, Sec. 2.2), the fused
+// overlap-add filter-and-mix (Eq. 2 evaluated block by block as in Eq. 6),
+// and the fix-up that joins output blocks across tile boundaries.
+#include "rsim_fft.cuh"
+#include "rsim_internal.cuh"
+
+namespace rsim {
+
+// Pops the next job index of a persistent kernel's queue (same value in all
+// threads).  Returns -1 when the queue is drained.
+__device__ __forceinline__ int pop_job(const Queues& Q, int kind, int b, int* slot) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int i = atomicAdd(&Q.next[Q.idx(kind, b)], 1);
+        *slot = (i < Q.count[Q.idx(kind, b)]) ? Q.lst(kind, b)[i] : -1;
+    }
+    __syncthreads();
+    return *slot;
+}
+
+// ---------------------------------------------------------------------------
+// K3: Hc_r = rFFT_N(hhat_r) / N in pair layout order (slot 0 = (H[0], H[N/2]))
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(M / kE)
+k_spectrum(DevBatch B, Queues Q, int bucket, const float* __restrict__ rir, float2* __restrict__ Hc,
+           const float2* __restrict__ tw) {
+    constexpr int T = M / kE;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* sm = reinterpret_cast<float2*>(smem_raw);
+    __shared__ int slot;
+    const int t = threadIdx.x;
+    const float inv_n = 1.0f / (2.0f * M);
+    for (;;) {
+        const int r = pop_job(Q, kListSpec, bucket, &slot);
+        if (r < 0) break;
+        float2 P[kE];
+        rfft_pairs<M>(P, rir + B.roff[r], B.L[r], sm, tw, t);
+        float2* H = Hc + (int64_t)r * B.MMAX;
+#pragma unroll
+        for (int s = 0; s < kE / 2; ++s) {
+            const int k = t + s * T;
+            if (k == 0) {
+                H[0] = cscale(P[0], inv_n);
+                H[M / 2] = cscale(P[1], inv_n);
+            } else {
+                H[k] = cscale(P[2 * s], inv_n);
+                H[M - k] = cscale(P[2 * s + 1], inv_n);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K4: fused overlap-add filter-and-mix, persistent over segment tiles
+// ---------------------------------------------------------------------------
+// For each block b of the tile's segment (hop = N - L_max + 1):
+//   X_i = rFFT_N(x_i[b hop, b hop + hop))                 for every source i
+//   Y_j = sum_i alpha_i Hc_ij X_i                          in registers
+//   y_j block = irFFT_N(Y_j); the first hop samples plus the carried tail of
+//   block b-1 are stored, the last L_max - 1 samples are carried to b+1.
+// The tail leaving the segment's last block is written to `tails`; the tile
+// holding the next segment stored its first block without it, and k_fixup
+// adds it afterwards (one FP32 add, the same one done in-tile, so results do
+// not depend on the segmentation).  Microphones are processed in groups of
+// kJG; the source spectra are recomputed per group.
+template <int M>
+__global__ void __launch_bounds__(M / kE)
+k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
+          const float* __restrict__ gains, const float2* __restrict__ Hc, float* __restrict__ y,
+          float* __restrict__ tails, const float2* __restrict__ tw) {
+    constexpr int T = M / kE;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* sm = reinterpret_cast<float2*>(smem_raw);
+    float (*tl)[M] = reinterpret_cast<float (*)[M]>(smem_raw + sizeof(float2) * padded_len(M));
+    __shared__ int slot;
+    const int t = threadIdx.x;
+    for (;;) {
+        const int g = pop_job(Q, kListFwd, bucket, &slot);
+        if (g < 0) break;
+        const int u = B.seg_utt[g];
+        const int64_t s = g - B.seg0[u];
+        const int64_t nx = B.n_x[u];
+        const int hop = B.hop[u];
+        const int tail_len = B.Lmax[u] - 1;
+        int64_t b0, b1;
+        segment_blocks(s, B.seg_len, hop, B.nblk[u], &b0, &b1);
+        if (b0 >= b1) continue;
+        const int I = B.n_src[u], J = B.J;
+        const int sb = B.src0[u], rb = B.rir0[u];
+        for (int j0 = 0; j0 < J; j0 += kJG) {
+            const int jn = min(kJG, J - j0);
+            __syncthreads();
+            for (int jj = 0; jj < jn; ++jj)
+                for (int n = t; n < tail_len; n += T) tl[jj][n] = 0.f;
+            for (int64_t b = b0; b < b1; ++b) {
+                const int64_t pos = b * hop;
+                const int64_t len = min((int64_t)hop, nx - pos);
+                float2 Y[kJG][kE];
+#pragma unroll
+                for (int jj = 0; jj < kJG; ++jj)
+#pragma unroll
+                    for (int e = 0; e < kE; ++e) Y[jj][e] = make_float2(0.f, 0.f);
+                for (int i = 0; i < I; ++i) {
+                    float2 P[kE];
+                    rfft_pairs<M>(P, x + B.xoff[sb + i] + pos, len, sm, tw, t);
+                    const float a = __ldg(gains + sb + i);
+#pragma unroll
+                    for (int jj = 0; jj < kJG; ++jj) {
+                        if (jj >= jn) break;
+                        const float2* H = Hc + (int64_t)(rb + i * J + j0 + jj) * B.MMAX;
+#pragma unroll
+                        for (int q = 0; q < kE / 2; ++q) {
+                            const int k = t + q * T;
+                            if (k == 0) {
+                                const float2 h0 = __ldg(H), hh = __ldg(H + M / 2);
+                                Y[jj][0].x += a * P[0].x * h0.x;
+                                Y[jj][0].y += a * P[0].y * h0.y;
+                                const float2 p = cmul(P[1], hh);
+                                Y[jj][1].x += a * p.x;
+                                Y[jj][1].y += a * p.y;
+                            } else {
+                                const float2 p0 = cmul(P[2 * q], __ldg(H + k));
+                                const float2 p1 = cmul(P[2 * q + 1], __ldg(H + M - k));
+                                Y[jj][2 * q].x += a * p0.x;
+                                Y[jj][2 * q].y += a * p0.y;
+                                Y[jj][2 * q + 1].x += a * p1.x;
+                                Y[jj][2 * q + 1].y += a * p1.y;
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int jj = 0; jj < kJG; ++jj) {
+                    if (jj >= jn) break;
+                    float2 v[kE];
+                    irfft_pairs<M>(v, Y[jj], sm, tw, t);
+                    float* yj = y + B.yoff[u] + (int64_t)(j0 + jj) * nx + pos;
+                    const int64_t lim = nx - pos;
+                    // owned samples [0, hop) plus the incoming tail
+#pragma unroll
+                    for (int q = 0; q < kE; ++q) {
+                        const int n = 2 * (t + q * T);
+                        if (n < hop && n < lim)
+                            yj[n] = v[q].x + (n < tail_len ? tl[jj][n] : 0.f);
+                        if (n + 1 < hop && n + 1 < lim)
+                            yj[n + 1] = v[q].y + (n + 1 < tail_len ? tl[jj][n + 1] : 0.f);
+                    }
+                    __syncthreads();
+                    // outgoing tail [hop, hop + L_max - 1)
+#pragma unroll
+                    for (int q = 0; q < kE; ++q) {
+                        const int n = 2 * (t + q * T);
+                        if (n >= hop && n - hop < tail_len) tl[jj][n - hop] = v[q].x;
+                        if (n + 1 >= hop && n + 1 - hop < tail_len) tl[jj][n + 1 - hop] = v[q].y;
+                    }
+                }
+            }
+            __syncthreads();
+            for (int jj = 0; jj < jn; ++jj) {
+                float* dst = tails + ((int64_t)g * J + j0 + jj) * B.MMAX;
+                for (int n = t; n < tail_len; n += T) dst[n] = tl[jj][n];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K5: add each segment's incoming tail to its first block
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_fixup(DevBatch B, float* __restrict__ y, const float* __restrict__ tails) {
+    for (int g = blockIdx.x; g < B.NSEG; g += gridDim.x) {
+        const int u = B.seg_utt[g];
+        const int64_t s = g - B.seg0[u];
+        if (s == 0 || B.logN[u] == 0) continue;
+        const int hop = B.hop[u];
+        int64_t b0, b1;
+        segment_blocks(s, B.seg_len, hop, B.nblk[u], &b0, &b1);
+        if (b0 >= b1) continue;
+        const int64_t nx = B.n_x[u];
+        const int64_t pos = b0 * hop;
+        const int tail_len = B.Lmax[u] - 1;
+        for (int j = 0; j < B.J; ++j) {
+            const float* src = tails + ((int64_t)(g - 1) * B.J + j) * B.MMAX;
+            float* yj = y + B.yoff[u] + (int64_t)j * nx + pos;
+            for (int n = threadIdx.x; n < tail_len && pos + n < nx; n += blockDim.x)
+                yj[n] = yj[n] + src[n];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <int M>
+constexpr int smem_spectrum() { return (int)sizeof(float2) * padded_len(M); }
+template <int M>
+constexpr int smem_forward() { return (int)sizeof(float2) * padded_len(M) + (int)sizeof(float) * kJG * M; }
+
+template <int M>
+static void spectrum_m(const DevBatch& B, const Queues& Q, int bucket, const float* rir,
+                       float2* Hc, const float2* tw, int grid, cudaStream_t st) {
+    k_spectrum<M><<<grid, M / kE, smem_spectrum<M>(), st>>>(B, Q, bucket, rir, Hc, tw);
+}
+
+void launch_spectrum(int logN, const DevBatch& B, const Queues& Q, const float* rir, float2* Hc,
+                     const float2* tw, int grid, cudaStream_t st) {
+    const int b = logN - kMinLog;
+    switch (logN) {
+        case 11: spectrum_m<1024>(B, Q, b, rir, Hc, tw, grid, st); break;
+        case 12: spectrum_m<2048>(B, Q, b, rir, Hc, tw, grid, st); break;
+        case 13: spectrum_m<4096>(B, Q, b, rir, Hc, tw, grid, st); break;
+        case 14: spectrum_m<8192>(B, Q, b, rir, Hc, tw, grid, st); break;
+        default: break;
+    }
+}
+
+template <int M>
+static void forward_m(const DevBatch& B, const Queues& Q, int bucket, const float* x,
+                      const float* gains, const float2* Hc, float* y, float* tails,
+                      const float2* tw, int grid, cudaStream_t st) {
+    k_forward<M><<<grid, M / kE, smem_forward<M>(), st>>>(B, Q, bucket, x, gains, Hc, y, tails, tw);
+}
+
+void launch_forward(int logN, const DevBatch& B, const Queues& Q, const float* x, const float* gains,
+                    const float2* Hc, float* y, float* tails, const float2* tw, int grid,
+                    cudaStream_t st) {
+    const int b = logN - kMinLog;
+    switch (logN) {
+        case 11: forward_m<1024>(B, Q, b, x, gains, Hc, y, tails, tw, grid, st); break;
+        case 12: forward_m<2048>(B, Q, b, x, gains, Hc, y, tails, tw, grid, st); break;
+        case 13: forward_m<4096>(B, Q, b, x, gains, Hc, y, tails, tw, grid, st); break;
+        case 14: forward_m<8192>(B, Q, b, x, gains, Hc, y, tails, tw, grid, st); break;
+        default: break;
+    }
+}
+
+void launch_fixup(const DevBatch& B, float* y, const float* tails, cudaStream_t st) {
+    int grid = B.NSEG < 4096 ? B.NSEG : 4096;
+    if (grid < 1) grid = 1;
+    k_fixup<<<grid, 256, 0, st>>>(B, y, tails);
+}
+
+int threads_for(int logN) { return (1 << (logN - 1)) / kE; }
+
+template <typename K>
+static int occ(K kernel, int threads, int smem) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem);
+    return n > 0 ? n : 1;
+}
+
+int occupancy_spectrum(int logN) {
+    switch (logN) {
+        case 11: return occ(k_spectrum<1024>, 64, smem_spectrum<1024>());
+        case 12: return occ(k_spectrum<2048>, 128, smem_spectrum<2048>());
+        case 13: return occ(k_spectrum<4096>, 256, smem_spectrum<4096>());
+        case 14: return occ(k_spectrum<8192>, 512, smem_spectrum<8192>());
+    }
+    return 1;
+}
+
+int occupancy_forward(int logN) {
+    switch (logN) {
+        case 11: return occ(k_forward<1024>, 64, smem_forward<1024>());
+        case 12: return occ(k_forward<2048>, 128, smem_forward<2048>());
+        case 13: return occ(k_forward<4096>, 256, smem_forward<4096>());
+        case 14: return occ(k_forward<8192>, 512, smem_forward<8192>());
+    }
+    return 1;
+}
+
+}  // namespace rsim

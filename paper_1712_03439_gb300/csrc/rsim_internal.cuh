@@ -1,0 +1,103 @@
+// Internal declarations shared by the kernels and the C-ABI layer.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rsim {
+
+// Supported overlap-add FFT sizes N = 2^m, m in [kMinLog, kMaxLog]; the
+// complex transform size is M = N/2.
+constexpr int kMinLog = 11;
+constexpr int kMaxLog = 14;
+constexpr int kNumBuckets = kMaxLog - kMinLog + 1;
+constexpr int kMaxSources = 16;      // sources per utterance (bwd tile encoding)
+constexpr int kJG = 2;               // microphones per group inside a tile
+constexpr int kPowerChunk = 32768;   // samples per partial-power CTA
+
+// device error word bits (latched, read by rsim_plan_sync_status)
+enum : int32_t {
+    kErrNoFftSize = 1,     // a truncated RIR longer than N/2+1 for every allowed N
+    kErrZeroPower = 2,     // a noise source with zero power but an SNR to meet
+};
+
+// list kinds inside the work queues
+enum : int { kListFwd = 0, kListBwd = 1, kListSpec = 2, kNumLists = 3 };
+
+// Batch description and per-call state on the device.  Utterance u has
+// n_src[u] sources (source 0 is the target) and J microphones; it is cut into
+// nseg = ceil(n_x / seg_len) segments, each one tile of work.
+struct DevBatch {
+    int32_t U, J, S, R, IMAX;
+    int32_t NSEG;            // total segments
+    int32_t MMAX;            // largest allowed N/2 (spectrum cache stride)
+    int32_t mask;            // allowed log2 N bitmask
+    int64_t seg_len;         // samples per segment (>= largest allowed N)
+    int32_t gain_mode;
+    const int32_t* n_src;    // [U]
+    const int64_t* n_x;      // [U]
+    const int32_t* src0;     // [U+1] first source of utterance
+    const int32_t* rir0;     // [U+1] first RIR of utterance
+    const int32_t* seg0;     // [U+1] first segment of utterance
+    const int32_t* seg_utt;  // [NSEG] utterance of segment
+    const int64_t* xoff;     // [S+1] offset of source s in x
+    const int64_t* yoff;     // [U+1] offset of utterance u in y
+    const int64_t* roff;     // [R+1] offset of RIR r in rir
+    const int32_t* rir_len;  // [R]
+    const int64_t* dhp_off;  // [NSEG] offset of a segment's dh partials
+    const float* tuning;     // [32] cost per real FFT of size 2^m (any unit)
+    // written on the device during a call
+    int32_t* L;              // [R] kept RIR length (Eq. 9)
+    int32_t* logN;           // [U] chosen log2 N (0 = none fits)
+    int32_t* hop;            // [U]
+    int32_t* Lmax;           // [U]
+    int32_t* nblk;           // [U]
+    double* pow_part;        // [S * CH] partial sums of x^2
+    int32_t CH;              // power chunks per source (max)
+    int32_t* err;            // [1] latched error bits
+};
+
+struct Queues {
+    int32_t* list;     // [kNumLists][kNumBuckets][cap]
+    int32_t* count;    // [kNumLists][kNumBuckets]
+    int32_t* next;     // [kNumLists][kNumBuckets] atomic cursors
+    int32_t cap;       // capacity per (list, bucket)
+    __host__ __device__ int32_t* lst(int kind, int b) const { return list + ((int64_t)kind * kNumBuckets + b) * cap; }
+    __host__ __device__ int idx(int kind, int b) const { return kind * kNumBuckets + b; }
+};
+
+// segment s of an utterance with hop h owns the blocks whose start b*h lies
+// in [s*seg_len, (s+1)*seg_len)
+__host__ __device__ inline void segment_blocks(int64_t s, int64_t seg_len, int64_t hop, int64_t nblk,
+                                               int64_t* b0, int64_t* b1) {
+    int64_t lo = (s * seg_len + hop - 1) / hop;
+    int64_t hi = ((s + 1) * seg_len + hop - 1) / hop;
+    if (hi > nblk) hi = nblk;
+    *b0 = lo;
+    *b1 = hi;
+}
+
+// ---- launchers (defined in the kernel translation units) -------------------
+void launch_truncate(const DevBatch& B, const float* rir, double factor, int none,
+                     float* energy_kept_frac, int grid, cudaStream_t st);
+void launch_power(const DevBatch& B, const float* x, int grid, cudaStream_t st);
+void launch_plan(const DevBatch& B, const Queues& Q, const float* snr_db, float* gains,
+                 cudaStream_t st);
+void launch_spectrum(int logN, const DevBatch& B, const Queues& Q, const float* rir, float2* Hc,
+                     const float2* tw, int grid, cudaStream_t st);
+void launch_forward(int logN, const DevBatch& B, const Queues& Q, const float* x, const float* gains,
+                    const float2* Hc, float* y, float* tails, const float2* tw, int grid,
+                    cudaStream_t st);
+void launch_fixup(const DevBatch& B, float* y, const float* tails, cudaStream_t st);
+void launch_backward(int logN, const DevBatch& B, const Queues& Q, const float* g, const float* x,
+                     const float* gains, const float2* Hc, float* dx, float* dhp, float* dap,
+                     const float2* tw, int grid, cudaStream_t st);
+void launch_finalize(const DevBatch& B, const float* gains, const float* dhp, const float* dap,
+                     float* grad_rir, float* grad_gains, cudaStream_t st);
+
+// occupancy helpers (CTAs per SM) and shared-memory sizes of the tiled kernels
+int occupancy_spectrum(int logN);
+int occupancy_forward(int logN);
+int occupancy_backward(int logN);
+int threads_for(int logN);
+
+}  // namespace rsim

@@ -1,0 +1,293 @@
+// Preparation kernels: RIR tail cut-off (Eq. 7-9), per-source power for the
+// SNR gains (Eq. 2's alpha), and the device-side planner that picks the FFT
+// size per utterance (Eq. 6) and builds the work queues.
+#include "rsim_internal.cuh"
+
+#include <math.h>
+
+namespace rsim {
+
+// ---------------------------------------------------------------------------
+// block reductions
+// ---------------------------------------------------------------------------
+template <typename Tv, typename Op>
+__device__ __forceinline__ Tv warp_reduce(Tv v, Op op) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// result valid in every thread; scratch holds >= 32 elements
+template <typename Tv, typename Op>
+__device__ __forceinline__ Tv block_reduce(Tv v, Op op, Tv* scratch, Tv ident) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    v = warp_reduce(v, op);
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    Tv r = (threadIdx.x < nw) ? scratch[threadIdx.x] : ident;
+    if (wid == 0) r = warp_reduce(r, op);
+    if (threadIdx.x == 0) scratch[0] = r;
+    __syncthreads();
+    r = scratch[0];
+    __syncthreads();
+    return r;
+}
+
+struct OpMaxF { __device__ float operator()(float a, float b) const { return fmaxf(a, b); } };
+struct OpMaxI { __device__ int operator()(int a, int b) const { return a > b ? a : b; } };
+struct OpAddD { __device__ double operator()(double a, double b) const { return a + b; } };
+
+// ---------------------------------------------------------------------------
+// K1: tail cut-off of every RIR (Eq. 7-9)
+// ---------------------------------------------------------------------------
+// p_th = max h^2 * factor, factor = 10^(-eta/10) computed once on the host in
+// FP64.  n_c is the last index whose power is not below p_th (Eq. 8 with its
+// strict "<"), and L = min(n_c + 2, Nh) (Eq. 9 keeps one sample beyond n_c).
+// The comparison h^2 < p_th is decided exactly in FP64 (h^2 of an FP32 value
+// is exact in double and p_th is one rounded product); FP32 bounds settle all
+// taps that are clearly above or below so FP64 is used only near p_th.
+// An all-zero RIR keeps L = 1.
+constexpr int kTruncThreads = 256;
+
+__global__ void __launch_bounds__(kTruncThreads)
+k_truncate(DevBatch B, const float* __restrict__ rir, double factor, int none,
+           float* __restrict__ ekf) {
+    __shared__ float sf[32];
+    __shared__ int si[32];
+    __shared__ double sd[32];
+    const int t = threadIdx.x;
+    for (int r = blockIdx.x; r < B.R; r += gridDim.x) {
+        const float* h = rir + B.roff[r];
+        const int n = B.rir_len[r];
+        float amax = 0.f;
+        for (int i = t; i < n; i += kTruncThreads) amax = fmaxf(amax, fabsf(h[i]));
+        amax = block_reduce(amax, OpMaxF(), sf, 0.f);
+        const double P = __dmul_rn((double)amax, (double)amax);   // exact
+        int L;
+        if (P == 0.0) {
+            L = 1;
+        } else if (none) {
+            L = n;
+        } else {
+            const double pth = __dmul_rn(P, factor);
+            const double st = sqrt(pth);
+            const float tlo = (float)(st * (1.0 - 1e-6));   // |h| < tlo  =>  h^2 < p_th
+            const float thi = (float)(st * (1.0 + 1e-6));   // |h| >= thi =>  h^2 >= p_th
+            int last = -1;
+            for (int i = t; i < n; i += kTruncThreads) {
+                const float a = fabsf(h[i]);
+                bool keep;
+                if (a < tlo) keep = false;
+                else if (a >= thi) keep = true;
+                else keep = !(__dmul_rn((double)a, (double)a) < pth);
+                if (keep) last = i;
+            }
+            last = block_reduce(last, OpMaxI(), si, -1);
+            L = last + 2;
+            if (L > n) L = n;
+        }
+        if (ekf) {
+            float et = 0.f, ek = 0.f;
+            for (int i = t; i < n; i += kTruncThreads) {
+                const float p = h[i] * h[i];
+                et += p;
+                if (i < L) ek += p;
+            }
+            double dt = block_reduce((double)et, OpAddD(), sd, 0.0);
+            double dk = block_reduce((double)ek, OpAddD(), sd, 0.0);
+            if (t == 0) ekf[r] = dt > 0.0 ? (float)(dk / dt) : 1.f;
+        }
+        if (t == 0) B.L[r] = L;
+        __syncthreads();
+    }
+}
+
+void launch_truncate(const DevBatch& B, const float* rir, double factor, int none,
+                     float* energy_kept_frac, int grid, cudaStream_t st) {
+    k_truncate<<<grid, kTruncThreads, 0, st>>>(B, rir, factor, none, energy_kept_frac);
+}
+
+// ---------------------------------------------------------------------------
+// K6a: partial sums of x^2 per source, one CTA per 32768-sample chunk
+// ---------------------------------------------------------------------------
+// Compensated (Kahan) FP32 sums per thread, FP64 across the CTA; the chunk
+// partials are added in a fixed order by the planner, so the result does not
+// depend on scheduling.
+constexpr int kPowThreads = 256;
+
+__global__ void __launch_bounds__(kPowThreads)
+k_power(DevBatch B, const float* __restrict__ x) {
+    __shared__ double sd[32];
+    const int t = threadIdx.x;
+    const int64_t total = (int64_t)B.S * B.CH;
+    for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
+        const int s = (int)(w / B.CH), c = (int)(w % B.CH);
+        // utterance of source s: binary search over src0
+        int lo = 0, hi = B.U - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (B.src0[mid] <= s) lo = mid; else hi = mid - 1;
+        }
+        const int64_t nx = B.n_x[lo];
+        const int64_t c0 = (int64_t)c * kPowerChunk;
+        if (c0 >= nx) continue;                 // uniform across the CTA
+        const int64_t c1 = (c0 + kPowerChunk < nx) ? c0 + kPowerChunk : nx;
+        const float* p = x + B.xoff[s];
+        float sum = 0.f, comp = 0.f;
+        for (int64_t i = c0 + t; i < c1; i += kPowThreads) {
+            const float v = __ldg(p + i);
+            const float yv = fmaf(v, v, -comp);
+            const float tv = sum + yv;
+            comp = (tv - sum) - yv;
+            sum = tv;
+        }
+        double d = block_reduce((double)sum - (double)comp, OpAddD(), sd, 0.0);
+        if (t == 0) B.pow_part[w] = d;
+    }
+}
+
+void launch_power(const DevBatch& B, const float* x, int grid, cudaStream_t st) {
+    k_power<<<grid, kPowThreads, 0, st>>>(B, x);
+}
+
+// ---------------------------------------------------------------------------
+// K2: planner (one CTA)
+// ---------------------------------------------------------------------------
+// Per utterance: gains from SNRs, L_max over its RIRs, and the FFT size N.
+// N minimises the cost of Eq. 6 (ceiling block count, one hop shared by all
+// (i, j) of the utterance: hop = N - L_max + 1) weighted by the per-size cost
+// table; N must satisfy L_max - 1 <= hop so an output block's tail only
+// reaches into the next block.  Then per FFT size it writes the lists of
+// spectrum jobs (RIRs), forward tiles (segments) and backward tiles
+// (segment, source), in utterance order, and resets the queue cursors.
+constexpr int kPlanThreads = 1024;
+
+__device__ __forceinline__ int block_exscan(int v, int* sm, int* total) {
+    // sm: >= 32 ints
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int n = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += n;
+    }
+    __syncthreads();
+    if (lane == 31) sm[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int w = (lane < (int)(blockDim.x >> 5)) ? sm[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int n = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += n;
+        }
+        sm[lane] = wi - w;          // exclusive prefix of warp totals
+        if (lane == 31) sm[32] = wi;
+    }
+    __syncthreads();
+    int r = sm[wid] + incl - v;
+    *total = sm[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kPlanThreads)
+k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict__ gains) {
+    __shared__ int sm[33];
+    const int t = threadIdx.x;
+    // ---- gains (alpha_0 = 1, alpha_i = sqrt(P_0 / P_i 10^(-SNR_i/10)))
+    if (B.gain_mode == 0) {
+        for (int u = t; u < B.U; u += kPlanThreads) {
+            const int s0 = B.src0[u], I = B.n_src[u];
+            const double nx = (double)B.n_x[u];
+            double P0 = 0.0;
+            for (int c = 0; c < B.CH; ++c) P0 += B.pow_part[(int64_t)s0 * B.CH + c];
+            P0 /= nx;
+            gains[s0] = 1.f;
+            for (int i = 1; i < I; ++i) {
+                double Pi = 0.0;
+                for (int c = 0; c < B.CH; ++c) Pi += B.pow_part[(int64_t)(s0 + i) * B.CH + c];
+                Pi /= nx;
+                if (!(Pi > 0.0)) {
+                    atomicOr(B.err, kErrZeroPower);
+                    gains[s0 + i] = 0.f;
+                } else {
+                    gains[s0 + i] = (float)sqrt(P0 / Pi * pow(10.0, -(double)snr_db[s0 + i] / 10.0));
+                }
+            }
+        }
+    }
+    // ---- FFT size per utterance
+    for (int u = t; u < B.U; u += kPlanThreads) {
+        int lmax = 1;
+        for (int r = B.rir0[u]; r < B.rir0[u + 1]; ++r) lmax = max(lmax, B.L[r]);
+        const int64_t nx = B.n_x[u];
+        const int I = B.n_src[u], J = B.J;
+        int best = 0;
+        double best_c = 0.0;
+        for (int m = kMinLog; m <= kMaxLog; ++m) {
+            if (!((B.mask >> m) & 1)) continue;
+            const int64_t N = 1LL << m;
+            const int64_t hop = N - lmax + 1;
+            if (lmax - 1 > hop) continue;              // tail must fit in one hop
+            if (N > B.seg_len) continue;
+            const int64_t nb = (nx + hop - 1) / hop;
+            const double c = ((double)nb * (I + J) + (double)I * J) * (double)B.tuning[m];
+            if (best == 0 || c < best_c) { best = m; best_c = c; }
+        }
+        if (best == 0) atomicOr(B.err, kErrNoFftSize);
+        B.logN[u] = best;
+        B.Lmax[u] = lmax;
+        const int64_t hop = best ? (1LL << best) - lmax + 1 : 1;
+        B.hop[u] = (int)hop;
+        B.nblk[u] = best ? (int)((nx + hop - 1) / hop) : 0;
+    }
+    __syncthreads();
+    // ---- work lists, one contiguous chunk of utterances per thread
+    const int per = (B.U + kPlanThreads - 1) / kPlanThreads;
+    const int u0 = min(B.U, t * per), u1 = min(B.U, u0 + per);
+    for (int b = 0; b < kNumBuckets; ++b) {
+        const int m = kMinLog + b;
+        int cf = 0, cb = 0, cs = 0;
+        for (int u = u0; u < u1; ++u) {
+            if (B.logN[u] != m) continue;
+            const int ns = B.seg0[u + 1] - B.seg0[u];
+            cf += ns;
+            cb += ns * B.n_src[u];
+            cs += B.rir0[u + 1] - B.rir0[u];
+        }
+        int tf, tb, ts;
+        int of = block_exscan(cf, sm, &tf);
+        int ob = block_exscan(cb, sm, &tb);
+        int os = block_exscan(cs, sm, &ts);
+        int32_t* lf = Q.lst(kListFwd, b);
+        int32_t* lb = Q.lst(kListBwd, b);
+        int32_t* ls = Q.lst(kListSpec, b);
+        for (int u = u0; u < u1; ++u) {
+            if (B.logN[u] != m) continue;
+            for (int g = B.seg0[u]; g < B.seg0[u + 1]; ++g) {
+                lf[of++] = g;
+                for (int i = 0; i < B.n_src[u]; ++i) lb[ob++] = g * kMaxSources + i;
+            }
+            for (int r = B.rir0[u]; r < B.rir0[u + 1]; ++r) ls[os++] = r;
+        }
+        if (t == 0) {
+            Q.count[Q.idx(kListFwd, b)] = tf;
+            Q.count[Q.idx(kListBwd, b)] = tb;
+            Q.count[Q.idx(kListSpec, b)] = ts;
+            Q.next[Q.idx(kListFwd, b)] = 0;
+            Q.next[Q.idx(kListBwd, b)] = 0;
+            Q.next[Q.idx(kListSpec, b)] = 0;
+        }
+    }
+}
+
+void launch_plan(const DevBatch& B, const Queues& Q, const float* snr_db, float* gains,
+                 cudaStream_t st) {
+    k_plan<<<1, kPlanThreads, 0, st>>>(B, Q, snr_db, gains);
+}
+
+}  // namespace rsim

@@ -1,0 +1,73 @@
+"""The C-ABI library builds, loads and exports every declared symbol (CPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1712_03439_gb300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "rsim.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rsim_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def test_header_declares_the_expected_entry_points():
+    assert _declared() == sorted(_lib.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def _desc(**kw):
+    import numpy as np
+    ns = np.array(kw.pop("ns", [1]), np.int32)
+    nx = np.array(kw.pop("nx", [100]), np.int64)
+    rl = np.array(kw.pop("rl", [10]), np.int32)
+    d = _lib.PlanDesc(num_utts=kw.pop("U", len(ns)), num_mics=kw.pop("J", 1),
+                      num_sources=ns.ctypes.data, num_samples=nx.ctypes.data,
+                      rir_len=rl.ctypes.data, eta_db=kw.pop("eta", 20.0),
+                      fft_sizes_mask=kw.pop("mask", 0), gain_mode=kw.pop("gm", 0),
+                      segment_len=kw.pop("seg", 0), fft_cost=None)
+    return d, (ns, nx, rl)
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(U=0), 1),
+    (dict(J=0), 1),
+    (dict(eta=-1.0), 1),
+    (dict(eta=float("nan")), 1),
+    (dict(gm=2), 1),
+    (dict(ns=[0]), 1),
+    (dict(ns=[17], rl=[10] * 17), 1),
+    (dict(nx=[0]), 1),
+    (dict(rl=[0]), 1),
+    (dict(mask=1 << 16), 2),
+    (dict(seg=-5), 1),
+])
+def test_plan_rejects_bad_descriptions_on_the_host(lib, kw, status):
+    d, keep = _desc(**kw)
+    h = ctypes.c_void_p()
+    st = lib.rsim_plan(ctypes.byref(d), 0, ctypes.byref(h))
+    assert st == status
+    assert h.value is None
+    assert lib.rsim_last_error().decode() != ""
+
+
+def test_null_plan_calls_fail_cleanly(lib):
+    assert lib.rsim_filter_mix(None, None, None, None, None, None, None, None, None) == 1
+    assert lib.rsim_filter_mix_backward(None, None, None, None, None, None, None, None) == 1
+    assert lib.rsim_plan_scratch_bytes(None) == 0
+    lib.rsim_plan_destroy(None)

@@ -1,0 +1,307 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C-ABI.
+
+Tolerances (fixed by the benchmark spec for this path): per output channel a
+relative L2 error <= 1e-5 and a max-abs error <= 1e-5 x the channel's peak;
+truncation lengths exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1712_03439_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL_L2 = 1e-5
+MAX_ABS = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1712_03439_gb300 import build
+    build.build()
+
+
+def dev(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def gpu_forward(batch, eta=20.0, fft_sizes=None, seg=0, gains=None):
+    from paper_1712_03439_gb300 import Plan, filter_mix
+    plan = Plan.for_batch(batch, eta_db=eta, fft_sizes=fft_sizes,
+                          gain_mode=0 if gains is None else 1, segment_len=seg)
+    x, rir = dev(batch.x), dev(batch.rir)
+    if gains is None:
+        out = filter_mix(plan, x, rir, snr_db=dev(batch.snr_db))
+    else:
+        out = filter_mix(plan, x, rir, gains=dev(gains))
+    plan.sync_status()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    return plan, res, (x, rir, out["gains"])
+
+
+def assert_channels_close(y, ref, batch, rel=REL_L2, mabs=MAX_ABS, what="y"):
+    yo = batch.y_offsets()
+    J = batch.num_mics
+    for u in range(batch.num_utts):
+        nx = int(batch.num_samples[u])
+        for j in range(J):
+            sl = slice(yo[u] + j * nx, yo[u] + (j + 1) * nx)
+            g, r = y[sl].astype(np.float64), ref[sl]
+            peak = np.abs(r).max()
+            err = np.abs(g - r)
+            if peak == 0:
+                assert err.max() == 0, f"{what} u={u} j={j}: nonzero output for a zero reference"
+                continue
+            rl2 = np.linalg.norm(g - r) / np.linalg.norm(r)
+            assert rl2 <= rel, f"{what} u={u} j={j}: rel L2 {rl2:.3e}"
+            assert err.max() <= mabs * peak, f"{what} u={u} j={j}: max abs {err.max() / peak:.3e} x peak"
+
+
+def small_batch(seed=7, lengths=(1, 700, 20011, 50000, 70001), n_src=(1, 2, 3, 4, 2),
+                rt60=(0.1, 0.3), J=2):
+    mics = synth.linear_pair_array() if J == 2 else synth.circular_array(J, 0.05)
+    return synth.make_batch(seed, list(lengths), list(n_src), mics, rt60)
+
+
+# ---------------------------------------------------------------------------
+# truncation (Eq. 7-9): lengths exact
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("eta", [0.0, 10.0, 20.0, 30.0, math.inf])
+def test_truncation_lengths_exact(eta):
+    # without a cut-off the RIR itself must fit the largest FFT size (N/2+1 taps)
+    b = synth.config_home(n_utts=12) if math.isfinite(eta) else small_batch(rt60=(0.1, 0.5))
+    _, res, _ = gpu_forward(b, eta=eta, seg=0)
+    ref = oracle.truncate_batch(b, eta)
+    np.testing.assert_array_equal(res["trunc_len"], ref["L"].astype(np.int32))
+    frac = ref["e_kept"] / ref["e_tot"]
+    np.testing.assert_allclose(res["energy_kept_frac"], frac, rtol=1e-5, atol=0)
+
+
+def _hand_batch(rirs, nx=3000, eta=20.0):
+    """One utterance per RIR, 1 source, 1 mic."""
+    b = synth.make_batch(3, [nx] * len(rirs), [1] * len(rirs), np.zeros((1, 2)), (0.1, 0.1),
+                         n_taps=8)
+    b.rir = np.concatenate([np.asarray(r, np.float32) for r in rirs])
+    b.rir_len = np.array([len(r) for r in rirs], np.int32)
+    return b
+
+
+def test_truncation_special_rirs():
+    r = np.random.Generator(np.random.PCG64(4))
+    dyadic = (2.0 ** -np.arange(60)) * r.choice([-1.0, 1.0], 60)
+    rirs = [np.zeros(100), [0.3], [1.0, 0.5, -1.0, 0.25, 0.1, 0.0],
+            [1.0, 0.01, 0.01, 0.5, 0.01, 0.01, 0.01, 0.01], dyadic, r.standard_normal(700)]
+    for eta in [0.0, 10.0, 20.0, 47.0, math.inf]:
+        b = _hand_batch(rirs)
+        _, res, _ = gpu_forward(b, eta=eta, gains=np.ones(len(rirs), np.float32))
+        ref = oracle.truncate_batch(b, eta)
+        np.testing.assert_array_equal(res["trunc_len"], ref["L"].astype(np.int32), err_msg=f"eta={eta}")
+
+
+# ---------------------------------------------------------------------------
+# gains and forward
+# ---------------------------------------------------------------------------
+def test_gains_match_oracle():
+    b = small_batch()
+    _, res, _ = gpu_forward(b)
+    ref = oracle.forward(b, 20.0)
+    np.testing.assert_allclose(res["gains"], ref["alpha"], rtol=2e-6, atol=0)
+
+
+def test_forward_parity_small_batch():
+    b = small_batch()
+    _, res, _ = gpu_forward(b, eta=20.0)
+    ref = oracle.forward(b, 20.0, alpha=res["gains"].astype(np.float64))
+    assert_channels_close(res["y"], ref["y"], b)
+
+
+@pytest.mark.parametrize("n", [2048, 4096, 8192, 16384])
+def test_forward_parity_each_fft_size(n):
+    # short RIRs (eta = 10 dB) so every size is admissible
+    b = small_batch(seed=11, lengths=(3, 1500, 9000, 33333), n_src=(2, 1, 4, 3), rt60=(0.1, 0.2))
+    tr = oracle.truncate_batch(b, 10.0)
+    if tr["L"].max() > n // 2 + 1:
+        pytest.skip("RIR too long for this size")
+    g = np.linspace(0.5, 1.5, int(b.num_sources.sum())).astype(np.float32)
+    plan, res, _ = gpu_forward(b, eta=10.0, fft_sizes=[n], gains=g)
+    assert np.all(plan.query()["log2_n"] == int(math.log2(n)))
+    ref = oracle.forward(b, 10.0, alpha=g.astype(np.float64))
+    assert_channels_close(res["y"], ref["y"], b)
+
+
+def test_forward_no_truncation_multi_segment():
+    b = small_batch(seed=12, lengths=(40000, 65000), n_src=(3, 2), rt60=(0.2, 0.25))
+    g = np.array([1.0, 0.7, 0.2, 1.0, 0.4], np.float32)
+    _, res, _ = gpu_forward(b, eta=math.inf, seg=16384, gains=g)
+    ref = oracle.forward(b, math.inf, alpha=g.astype(np.float64))
+    assert_channels_close(res["y"], ref["y"], b)
+
+
+def test_forward_edge_cases():
+    # Nx = 1, single-tap RIRs, I = J = 1, a zero RIR, Nx shorter than the hop
+    b = synth.make_batch(5, [1, 2, 17, 5000], [1, 2, 1, 3], np.zeros((1, 2)), (0.05, 0.1))
+    ro = b.rir_offsets()
+    rirs = [b.rir[ro[r]:ro[r + 1]].copy() for r in range(b.num_rirs)]
+    rirs[0] = np.array([0.5], np.float32)
+    rirs[1] = np.zeros(40, np.float32)
+    b.rir = np.concatenate(rirs)
+    b.rir_len = np.array([len(r) for r in rirs], np.int32)
+    g = np.ones(int(b.num_sources.sum()), np.float32)
+    _, res, _ = gpu_forward(b, eta=20.0, gains=g)
+    ref = oracle.forward(b, 20.0, alpha=g.astype(np.float64))
+    assert_channels_close(res["y"], ref["y"], b)
+
+
+def test_results_do_not_depend_on_segmentation():
+    b = small_batch(seed=13, lengths=(90001, 140000, 31000), n_src=(2, 3, 1))
+    ys = []
+    for seg in [16384, 40000, 1 << 30]:
+        _, res, _ = gpu_forward(b, eta=20.0, seg=seg)
+        ys.append(res["y"])
+    np.testing.assert_array_equal(ys[0], ys[1])
+    np.testing.assert_array_equal(ys[0], ys[2])
+
+
+def test_results_do_not_depend_on_utterance_order():
+    b = small_batch(seed=14, lengths=(5000, 70000, 20000, 45000), n_src=(2, 1, 4, 3))
+    perm = [2, 0, 3, 1]
+    bp = b.subset(perm)
+    _, r0, _ = gpu_forward(b)
+    _, r1, _ = gpu_forward(bp)
+    yo, yp = b.y_offsets(), bp.y_offsets()
+    for k, u in enumerate(perm):
+        np.testing.assert_array_equal(r0["y"][yo[u]:yo[u + 1]], r1["y"][yp[k]:yp[k + 1]])
+
+
+def test_full_size_home_workload_sampled_utterances():
+    # the 256-utterance Google-Home-like batch at full size, in the benchmark's
+    # launch configuration; the oracle checks a sample of its utterances
+    b = synth.config_home()
+    _, res, _ = gpu_forward(b, eta=20.0)
+    rng = np.random.Generator(np.random.PCG64(1))
+    pick = sorted(rng.choice(b.num_utts, 3, replace=False).tolist())
+    sub = b.subset(pick)
+    si = b.src_index()
+    alpha = np.concatenate([res["gains"][si[u]:si[u + 1]] for u in pick]).astype(np.float64)
+    ref = oracle.forward(sub, 20.0, alpha=alpha)
+    yo = b.y_offsets()
+    y = np.concatenate([res["y"][yo[u]:yo[u + 1]] for u in pick])
+    assert_channels_close(y, ref["y"], sub)
+    tr = oracle.truncate_batch(b, 20.0)
+    np.testing.assert_array_equal(res["trunc_len"], tr["L"].astype(np.int32))
+
+
+# ---------------------------------------------------------------------------
+# backward
+# ---------------------------------------------------------------------------
+def gpu_backward(batch, eta, gains, gy, seg=0, fft_sizes=None):
+    from paper_1712_03439_gb300 import Plan
+    plan, res, (x, rir, g) = gpu_forward(batch, eta=eta, gains=gains, seg=seg, fft_sizes=fft_sizes)
+    gx = torch.empty_like(x)
+    gr = torch.empty_like(rir)
+    gg = torch.empty_like(g)
+    plan.filter_mix_backward(dev(gy), x, g, gx, gr, gg)
+    plan.sync_status()
+    return res, gx.cpu().numpy(), gr.cpu().numpy(), gg.cpu().numpy()
+
+
+def _close_vec(a, r, rel, what):
+    nr = np.linalg.norm(r)
+    assert np.linalg.norm(a.astype(np.float64) - r) <= rel * max(nr, 1e-30), \
+        f"{what}: rel L2 {np.linalg.norm(a - r) / max(nr, 1e-30):.3e}"
+
+
+@pytest.mark.parametrize("eta,seg", [(20.0, 0), (math.inf, 16384)])
+def test_backward_parity_small_batch(eta, seg):
+    b = small_batch(seed=21, lengths=(900, 20011, 50000, 70001), n_src=(2, 3, 4, 1))
+    S = int(b.num_sources.sum())
+    gains = np.linspace(0.6, 1.3, S).astype(np.float32)
+    gy = synth.grad_like(22, b.y_size)
+    _, gx, gr, gg = gpu_backward(b, eta, gains, gy, seg=seg)
+    L = oracle.truncate_batch(b, eta)["L"]
+    ref = oracle.backward(b, L, gains.astype(np.float64), gy)
+    # per source: dx; per RIR: dh; dalpha elementwise
+    xo = b.x_offsets()
+    for s in range(S):
+        _close_vec(gx[xo[s]:xo[s + 1]], ref["dx"][xo[s]:xo[s + 1]], REL_L2, f"dx[{s}]")
+    ro = b.rir_offsets()
+    for r in range(b.num_rirs):
+        _close_vec(gr[ro[r]:ro[r + 1]], ref["dh"][ro[r]:ro[r + 1]], REL_L2, f"dh[{r}]")
+        assert np.all(gr[ro[r] + L[r]:ro[r + 1]] == 0)
+    np.testing.assert_allclose(gg, ref["dalpha"], rtol=REL_L2, atol=REL_L2 * np.abs(ref["dalpha"]).max())
+
+
+def test_autograd_function_matches_oracle_gradient():
+    from paper_1712_03439_gb300 import Plan, filter_mix_autograd
+    b = synth.config_fd_subcase()
+    S = int(b.num_sources.sum())
+    gains = np.linspace(0.6, 1.4, S).astype(np.float32)
+    t = synth.grad_like(6, b.y_size)
+    plan = Plan.for_batch(b, eta_db=math.inf, gain_mode=1)
+    x = dev(b.x).requires_grad_(True)
+    rir = dev(b.rir).requires_grad_(True)
+    g = dev(gains).requires_grad_(True)
+    y = filter_mix_autograd(plan, x, rir, g)
+    loss = 0.5 * torch.sum((y - dev(t)) ** 2)
+    loss.backward()
+    L = oracle.truncate_batch(b, math.inf)["L"]
+    yref = oracle.forward(b, math.inf, alpha=gains.astype(np.float64))["y"]
+    ref = oracle.backward(b, L, gains.astype(np.float64), yref - t)
+    _close_vec(x.grad.cpu().numpy(), ref["dx"], 1e-5, "dx")
+    _close_vec(rir.grad.cpu().numpy(), ref["dh"], 1e-5, "dh")
+    _close_vec(g.grad.cpu().numpy(), ref["dalpha"], 1e-5, "dalpha")
+
+
+def test_backward_each_fft_size():
+    b = small_batch(seed=31, lengths=(7000, 23000), n_src=(2, 3), rt60=(0.1, 0.15))
+    S = int(b.num_sources.sum())
+    gains = np.linspace(0.5, 1.2, S).astype(np.float32)
+    gy = synth.grad_like(32, b.y_size)
+    L = oracle.truncate_batch(b, 10.0)["L"]
+    ref = oracle.backward(b, L, gains.astype(np.float64), gy)
+    for n in [2048, 4096, 8192, 16384]:
+        if L.max() > n // 2 + 1:
+            continue
+        _, gx, gr, gg = gpu_backward(b, 10.0, gains, gy, fft_sizes=[n])
+        _close_vec(gx, ref["dx"], REL_L2, f"dx N={n}")
+        _close_vec(gr, ref["dh"], REL_L2, f"dh N={n}")
+        np.testing.assert_allclose(gg, ref["dalpha"], rtol=REL_L2, atol=REL_L2 * np.abs(ref["dalpha"]).max())
+
+
+# ---------------------------------------------------------------------------
+# errors
+# ---------------------------------------------------------------------------
+def test_backward_before_forward_is_a_state_error():
+    from paper_1712_03439_gb300 import Plan
+    from paper_1712_03439_gb300._lib import RsimError
+    b = small_batch(seed=41, lengths=(1000,), n_src=(1,))
+    plan = Plan.for_batch(b, gain_mode=1)
+    z = lambda n: torch.zeros(n, device="cuda")
+    with pytest.raises(RsimError) as e:
+        plan.filter_mix_backward(z(plan.y_size), z(plan.x_size), z(plan.S), z(plan.x_size),
+                                 z(plan.rir_size), z(plan.S))
+    assert e.value.status == 6
+
+
+def test_silent_noise_source_is_reported():
+    from paper_1712_03439_gb300._lib import RsimError
+    b = small_batch(seed=42, lengths=(3000,), n_src=(2,))
+    xo = b.x_offsets()
+    b.x[xo[1]:xo[2]] = 0
+    with pytest.raises(RsimError) as e:
+        gpu_forward(b)
+    assert e.value.status == 1
+
+
+def test_rir_too_long_for_allowed_sizes_is_reported():
+    from paper_1712_03439_gb300._lib import RsimError
+    b = small_batch(seed=43, lengths=(3000,), n_src=(1,), rt60=(0.5, 0.5))
+    with pytest.raises(RsimError) as e:
+        gpu_forward(b, eta=math.inf, fft_sizes=[2048], gains=np.ones(1, np.float32))
+    assert e.value.status == 2
