@@ -1,0 +1,470 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the room-simulator filter-and-mix path.
+
+One step = the whole hot path over one batch: RIR cut-off (Eq. 7-9), gains
+from SNRs, per-utterance FFT-size choice (Eq. 6), RIR spectra, the fused
+overlap-add forward (Eq. 2), the segment fix-up, and the adjoint (gradients
+for sources, RIRs and gains).  Workload: 256 utterances of 2-15 s at 16 kHz,
+1 target + 0-3 noise sources, 2 microphones, RT60 0.1-0.9 s, 20 dB cut-off
+(synthetic, seeded).  Metric: simulated (target) audio seconds per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "simulated audio s/sec (fwd, fwd+bwd) at 16 kHz, 1×GB300, % FFT roofline vs plain"
+UNIT = "audio_s/s"
+ETA_DB = 20.0
+WORKLOAD = ("home-256: 256 utterances, lengths U(2,15) s at 16 kHz, 1 target + 0-3 noise "
+            "sources, 2 mics 7.1 cm apart, RT60 U(0.1,0.9) s, SNR U(0,30) dB, eta 20 dB")
+DATA = "synthetic: AR(2) speech stand-ins, white/AR(1) noise, exponential-decay RIRs (seeded)"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work (the minimum the method does at the chosen FFT sizes)
+# ---------------------------------------------------------------------------
+def algorithmic_work(batch, q, L):
+    """FLOPs and HBM bytes of the forward and backward OLA kernels.
+
+    A real N-point transform counts 2.5 N log2 N flops, a complex
+    multiply-add 8.  Forward per block: I + J transforms and I*J spectrum
+    products; bytes: x read once, y written once.  Backward per block:
+    2I + J transforms and 2*I*J products, plus one inverse per RIR for dh;
+    bytes: grad_y and x read once, grad_x written once, dh written once."""
+    ff = fb = bf = bb = 0.0
+    J = batch.num_mics
+    ri = batch.rir_index()
+    for u in range(batch.num_utts):
+        I = int(batch.num_sources[u])
+        nx = int(batch.num_samples[u])
+        m = int(q["log2_n"][u])
+        N = 1 << m
+        B = int(q["num_blocks"][u])
+        tr = 2.5 * N * m
+        mac = 8.0 * (N / 2 + 1)
+        ff += B * ((I + J) * tr + I * J * mac)
+        fb += 4.0 * (I + J) * nx
+        bf += B * ((2 * I + J) * tr + 2 * I * J * mac) + I * J * tr
+        bb += 4.0 * (J + 2 * I) * nx + 4.0 * float(np.sum(L[ri[u]:ri[u + 1]]))
+    return dict(fwd_flops=ff, fwd_bytes=fb, bwd_flops=bf, bwd_bytes=bb)
+
+
+def roofline_entry(flops, nbytes, ms, p_fp32_tflops, hbm_gbs, peak_kind, traffic):
+    t = ms / 1e3
+    t_alu = flops / (p_fp32_tflops * 1e12)
+    t_hbm = nbytes / (hbm_gbs * 1e9)
+    if t_alu >= t_hbm:
+        ach = flops / t / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": p_fp32_tflops, "unit": "TFLOP/s",
+                "frac": ach / p_fp32_tflops, "traffic": traffic,
+                "peak_source": f"derived: SMs x 128 FP32 lanes x 2 flops x max SM clock ({peak_kind} clock)",
+                "hbm_side": {"achieved": nbytes / t / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+                             "frac": nbytes / t / 1e9 / hbm_gbs, "peak_source": peak_kind}}
+    ach = nbytes / t / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": hbm_gbs, "unit": "GB/s", "frac": ach / hbm_gbs,
+            "traffic": traffic, "peak_source": peak_kind,
+            "alu_side": {"achieved": flops / t / 1e12, "peak": p_fp32_tflops, "unit": "TFLOP/s"}}
+
+
+def _traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    source has not changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(kernel)
+    if not d:
+        return None
+    src = os.path.join(ROOT, "paper_1712_03439_gb300", "csrc", d["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if h != d.get("source_sha"):
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(", ") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if len(r) > 3 and r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if len(r) > 3 and r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows if len(r) >= 10
+                          for k in range(4) if r[6 + k].strip() == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# plain per-utterance GPU path (Eq. 4 full-length FFT convolution, torch.fft)
+# ---------------------------------------------------------------------------
+def plain_step(torch, batch, xs, hs, snrs, gys):
+    """One forward + backward of the plain path: a Python loop over
+    utterances, each a full-length torch.fft convolution of every (i, j)."""
+    J = batch.num_mics
+    fac = 10.0 ** (-ETA_DB / 10.0)
+    for u in range(batch.num_utts):
+        x, h, snr, gy = xs[u], hs[u], snrs[u], gys[u]
+        x = x.detach().requires_grad_(True)
+        h = h.detach().requires_grad_(True)
+        I, nx = x.shape
+        nh = h.shape[-1]
+        p = h.detach() ** 2
+        pth = p.amax(-1, keepdim=True) * fac
+        idx = torch.arange(nh, device=h.device)
+        last = torch.where(p >= pth, idx, -1).amax(-1, keepdim=True)
+        keep = (idx < torch.clamp(last + 2, max=nh)).to(h.dtype)
+        hh = h * keep
+        pw = (x.detach() ** 2).mean(-1)
+        a = torch.sqrt(pw[0] / pw * torch.pow(10.0, -snr / 10.0))
+        a = torch.cat([torch.ones_like(a[:1]), a[1:]]).requires_grad_(True)
+        n = 1 << int(math.ceil(math.log2(nx + nh - 1)))
+        X = torch.fft.rfft(x, n)                       # [I, F]
+        H = torch.fft.rfft(hh, n)                      # [I, J, F]
+        Y = torch.einsum("i,if,ijf->jf", a.to(X.dtype), X, H)
+        y = torch.fft.irfft(Y, n)[:, :nx]
+        (y * gy).sum().backward()
+    return None
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle on a bounded sample
+# ---------------------------------------------------------------------------
+def oracle_sample_step(oracle, sub, g):
+    out = oracle.forward(sub, ETA_DB)
+    oracle.backward(sub, out["L"], out["alpha"], g)
+
+
+def run_reference(args):
+    import oracle
+    from paper_1712_03439_gb300 import synth
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    b = synth.config_home()
+    sub = b.subset(range(3))
+    g = synth.grad_like(99, sub.y_size)
+    cores = oracle.max_threads()
+    for _ in range(args.warmup):
+        oracle_sample_step(oracle, sub, g)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_sample_step(oracle, sub, g)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = sub.audio_seconds() / dt
+    sample = (f"utterances 0-2 of the home-256 batch ({sub.audio_seconds():.2f} s of audio, "
+              f"{int(sub.num_sources.sum())} sources), forward + backward, direct FP64")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": DATA, "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1712_03439_gb300 import Plan, build, synth
+    from paper_1712_03439_gb300 import _lib
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    b = synth.config_home()
+    audio_s = b.audio_seconds()
+    plan = Plan.for_batch(b, eta_db=ETA_DB, gain_mode=0, device=dev.index)
+    x = torch.from_numpy(b.x).to(dev)
+    rir = torch.from_numpy(b.rir).to(dev)
+    snr = torch.from_numpy(b.snr_db).to(dev)
+    gy = torch.from_numpy(synth.grad_like(99, b.y_size)).to(dev)
+    gains = torch.empty(plan.S, device=dev)
+    y = torch.empty(plan.y_size, device=dev)
+    gx = torch.empty_like(x)
+    gr = torch.empty_like(rir)
+    gg = torch.empty_like(gains)
+    tl = torch.empty(plan.R, dtype=torch.int32, device=dev)
+
+    def fwd():
+        plan.filter_mix(x, rir, gains, y, snr_db=snr, trunc_len=tl)
+
+    def step():
+        fwd()
+        plan.filter_mix_backward(gy, x, gains, gx, gr, gg)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    plan.sync_status()
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    clock = ClockSampler(dev.index) if rank == 0 else None
+    # ---- timed: K full steps
+    plan.set_timing(True)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    stages = plan.stage_times()
+    plan.set_timing(False)
+    clocks = clock.stop() if clock else None
+    plan.sync_status()
+
+    if args.only_step:
+        args.no_plain = args.no_cpu_baseline = True
+    # ---- forward only (context)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kf = 0 if args.only_step else max(1, args.steps)
+    barrier()
+    f0.record(stream)
+    for _ in range(kf):
+        fwd()
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms_fwd = max_over_ranks(f0.elapsed_time(f1) / kf) if kf else float("nan")
+
+    # ---- end to end through the public API with host buffers
+    pin = lambda t: t.cpu().pin_memory()
+    hx, hrir, hsnr, hgy = pin(x), pin(rir), pin(snr), pin(gy)
+    hy, hgx, hgr, hgg, hgains = (torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+                                 for t in (y, gx, gr, gg, gains))
+    h2d = 4 * (hx.numel() + hrir.numel() + hsnr.numel() + hgy.numel())
+    d2h = 4 * (hy.numel() + hgx.numel() + hgr.numel() + hgg.numel() + hgains.numel())
+
+    def e2e_step():
+        x.copy_(hx, non_blocking=True)
+        rir.copy_(hrir, non_blocking=True)
+        snr.copy_(hsnr, non_blocking=True)
+        gy.copy_(hgy, non_blocking=True)
+        step()
+        hy.copy_(y, non_blocking=True)
+        hgx.copy_(gx, non_blocking=True)
+        hgr.copy_(gr, non_blocking=True)
+        hgg.copy_(gg, non_blocking=True)
+        hgains.copy_(gains, non_blocking=True)
+
+    ke = 0 if args.only_step else max(3, min(args.steps, 20))
+    if ke:
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(ke):
+        e2e_step()
+    g1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = max_over_ranks(g0.elapsed_time(g1) / ke) if ke else float("nan")
+
+    # ---- plain per-utterance GPU path (same step, torch.fft)
+    plain = None
+    if not args.no_plain:
+        xo, ro, si, ri = b.x_offsets(), b.rir_offsets(), b.src_index(), b.rir_index()
+        yo = b.y_offsets()
+        xs, hs, snrs, gys = [], [], [], []
+        for u in range(b.num_utts):
+            I, nx = int(b.num_sources[u]), int(b.num_samples[u])
+            xs.append(x[xo[si[u]]:xo[si[u + 1]]].view(I, nx))
+            lens = b.rir_len[ri[u]:ri[u + 1]]
+            hp = torch.zeros(I * b.num_mics, int(lens.max()), device=dev)
+            for k, r in enumerate(range(ri[u], ri[u + 1])):
+                hp[k, :lens[k]] = rir[ro[r]:ro[r + 1]]
+            hs.append(hp.view(I, b.num_mics, -1))
+            snrs.append(snr[si[u]:si[u + 1]])
+            gys.append(gy[yo[u]:yo[u + 1]].view(b.num_mics, nx))
+        plain_step(torch, b, xs, hs, snrs, gys)
+        torch.cuda.synchronize()
+        kp = 2
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(kp):
+            plain_step(torch, b, xs, hs, snrs, gys)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        ms_plain = max_over_ranks(p0.elapsed_time(p1) / kp)
+        plain = {"value": world * audio_s / (ms_plain / 1e3), "unit": UNIT, "ms_per_step": ms_plain,
+                 "what": "per-utterance Python loop of full-length torch.fft (cuFFT) convolution "
+                         "(Eq. 4) with torch truncation and gains, forward + autograd backward"}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel (from the live stage events)
+    q = plan.query()
+    L = tl.cpu().numpy()
+    work = algorithmic_work(b, q, L)
+    hbm, sm_mhz_max, peak_kind = _peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    p_fp32 = sms * 128 * 2 * sm_mhz_max * 1e6 / 1e12
+    per = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in stages.items()}
+    kern = "backward" if per["backward"] >= per["forward"] else "forward"
+    kname = {"forward": "k_forward", "backward": "k_backward"}[kern]
+    src = {"forward": "rsim_forward.cu", "backward": "rsim_backward.cu"}[kern]
+    n_sizes = plan.num_fft_sizes          # one launch per allowed FFT size
+    w = "fwd" if kern == "forward" else "bwd"
+    roof = roofline_entry(work[f"{w}_flops"], work[f"{w}_bytes"], per[kern], p_fp32, hbm, peak_kind,
+                          _traffic_for(kname))
+    roof.update({"kernel": f"{kname}<M> ({src}), all FFT-size launches of one step",
+                 "stage_ms": per[kern], "launches_per_step": n_sizes,
+                 "algorithmic_flops_per_step": work[f"{w}_flops"],
+                 "algorithmic_bytes_per_step": work[f"{w}_bytes"]})
+    fwd_roof = roofline_entry(work["fwd_flops"], work["fwd_bytes"], per["forward"], p_fp32, hbm,
+                              peak_kind, _traffic_for("k_forward"))
+
+    # ---- CPU oracle baseline on a bounded sample (rank 0, N = 1)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        sub = b.subset(range(16))
+        g = synth.grad_like(99, sub.y_size)
+        t0 = time.perf_counter()
+        oracle_sample_step(oracle, sub, g)
+        dt = time.perf_counter() - t0
+        cpu = {"value": sub.audio_seconds() / dt, "unit": UNIT, "cores": oracle.max_threads(),
+               "kind": "oracle",
+               "sample": f"utterances 0-15 of the home-256 batch ({sub.audio_seconds():.1f} s of audio), "
+                         f"forward + backward, FP64 direct convolution, {dt:.1f} s wall"}
+
+    # truncate, power, plan, spectra, forward, fix-up | backward, finalize
+    kernels_per_step = (3 + 2 * n_sizes + 1) + (n_sizes + 1)
+    line = {
+        "metric": METRIC, "value": world * audio_s / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": DATA,
+        "config": {"workload": WORKLOAD, "global_batch": b.num_utts * world,
+                   "audio_seconds_per_step": audio_s * world,
+                   "step": "forward (cut-off, gains, FFT-size plan, RIR spectra, OLA filter-and-mix, "
+                           "fix-up) + backward (grad x, grad RIR, grad gains)",
+                   "l2": "inputs larger than L2 (x is %.0f MB, grad_y %.0f MB)"
+                         % (x.numel() * 4 / 1e6, gy.numel() * 4 / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "fft_sizes_chosen": {str(1 << int(m)): int(c) for m, c in
+                                        zip(*np.unique(q["log2_n"], return_counts=True))}},
+        "fwd_only": {"value": world * audio_s / (ms_fwd / 1e3), "unit": UNIT, "ms_per_step": ms_fwd,
+                     "roofline": fwd_roof},
+        "stages_ms_per_step": per,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "plain_gpu": plain,
+        "e2e": {"value": world * audio_s / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
+        "gpu_launches": kernels_per_step * args.steps,
+        "clocks": clocks,
+    }
+    if plain:
+        line["vs_plain"] = line["value"] / plain["value"]
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-step", action="store_true",
+                    help="time only the K steps (no forward-only, end-to-end, plain or CPU legs); "
+                         "for profiler runs")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -76,6 +76,8 @@ class Plan:
         self.x_size = int(np.sum(self.num_sources.astype(np.int64) * self.num_samples))
         self.y_size = int(np.sum(self.num_samples) * self.num_mics)
         self.rir_size = int(np.sum(self.rir_len.astype(np.int64)))
+        # FFT sizes the plan may pick (one forward/backward launch each)
+        self.num_fft_sizes = bin(mask).count("1") if mask else 4
 
     @classmethod
     def for_batch(cls, batch, **kw):
