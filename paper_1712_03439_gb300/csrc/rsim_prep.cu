@@ -203,13 +203,16 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
         for (int u = t; u < B.U; u += kPlanThreads) {
             const int s0 = B.src0[u], I = B.n_src[u];
             const double nx = (double)B.n_x[u];
+            // chunks past this utterance's end are never written: sum only
+            // the ones that exist
+            const int nch = (int)((B.n_x[u] + kPowerChunk - 1) / kPowerChunk);
             double P0 = 0.0;
-            for (int c = 0; c < B.CH; ++c) P0 += B.pow_part[(int64_t)s0 * B.CH + c];
+            for (int c = 0; c < nch; ++c) P0 += B.pow_part[(int64_t)s0 * B.CH + c];
             P0 /= nx;
             gains[s0] = 1.f;
             for (int i = 1; i < I; ++i) {
                 double Pi = 0.0;
-                for (int c = 0; c < B.CH; ++c) Pi += B.pow_part[(int64_t)(s0 + i) * B.CH + c];
+                for (int c = 0; c < nch; ++c) Pi += B.pow_part[(int64_t)(s0 + i) * B.CH + c];
                 Pi /= nx;
                 if (!(Pi > 0.0)) {
                     atomicOr(B.err, kErrZeroPower);
