@@ -139,6 +139,41 @@ int64_t rsim_plan_scratch_bytes(rsim_plan_t plan);
  * make sure no queued work still uses it. */
 void rsim_plan_destroy(rsim_plan_t plan);
 
+/* Allocation-free per-source gains.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory when
+ * they need the gains -- code running under a memory manager that owns every
+ * device allocation (a framework's caching allocator, a real-time audio
+ * engine that reserves its memory at start-up) or code where an allocation
+ * would stall the device at the wrong moment.  rsim_plan allocates, so such
+ * callers cannot make a plan.
+ *
+ * Computes, for a batch laid out as for rsim_filter_mix, the gains
+ * rsim_filter_mix writes with gain_mode = 0: alpha_0 = 1 and
+ * alpha_i = sqrt(P_0 / P_i * 10^(-SNR_i/10)), P the mean square of the dry
+ * source over [0, Nx); a noise source with P_i = 0 gets NaN.
+ *   stream       cudaStream_t (NULL = legacy default stream)
+ *   num_utts     U >= 1
+ *   num_sources  [U] host, 1..16 sources per utterance
+ *   num_samples  [U] host, Nx >= 1
+ *   x            packed sources, device, read only
+ *   snr_db       [sum I_u] device (entry of each target ignored)
+ *   gains        [sum I_u] device, written
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  Its scratch
+ * is one fixed 2 MiB device array inside the library, present on every GPU
+ * that loads the library until the process exits; a batch needing more
+ * (about 8 bytes per source per 32768 samples of the longest utterance plus
+ * 24 bytes per source and utterance) is rejected with RSIM_E_UNSUPPORTED and
+ * a message.  Nothing in the scratch has to start at zero: each call writes
+ * every entry it reads.  All calls share that one array, so calls whose work
+ * overlaps on the GPU race; queue them on one stream or wait between them.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  The
+ * host arrays are copied (as pageable memory) before the call returns, and
+ * that copy may wait for earlier work on the stream.  Asynchronous otherwise. */
+rsim_status rsim_source_gains_noalloc(void *stream, int32_t num_utts, const int32_t *num_sources,
+                                      const int64_t *num_samples, const float *x, const float *snr_db,
+                                      float *gains);
+
 /* Message describing the calling thread's last error ("" if none). */
 const char *rsim_last_error(void);
 

@@ -151,6 +151,21 @@ class Plan:
             pass
 
 
+def source_gains_noalloc(num_sources, num_samples, x, snr_db, gains, stream=None):
+    """rsim_source_gains_noalloc: the gain_mode = 0 gains without a plan and
+    without any device allocation (scratch is a fixed array in the library)."""
+    lib = _lib.load()
+    ns = np.ascontiguousarray(num_sources, dtype=np.int32)
+    nx = np.ascontiguousarray(num_samples, dtype=np.int64)
+    S = int(ns.sum())
+    _want(x, int(np.sum(ns.astype(np.int64) * nx)), torch.float32, "x")
+    _want(snr_db, S, torch.float32, "snr_db")
+    _want(gains, S, torch.float32, "gains")
+    st = lib.rsim_source_gains_noalloc(_stream(stream), ns.shape[0], ctypes.c_void_p(ns.ctypes.data),
+                                       ctypes.c_void_p(nx.ctypes.data), _ptr(x), _ptr(snr_db), _ptr(gains))
+    _lib.check(lib, st)
+
+
 # ---------------------------------------------------------------------------
 # convenience and autograd
 # ---------------------------------------------------------------------------

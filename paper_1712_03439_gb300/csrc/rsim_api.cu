@@ -120,6 +120,8 @@ void stage_mark(rsim_plan_t p, int stage, bool end, cudaStream_t st) {
 
 extern "C" const char* rsim_last_error(void) { return g_err.c_str(); }
 
+void rsim::set_last_error(const char* msg) { g_err = msg; }
+
 extern "C" int64_t rsim_plan_scratch_bytes(rsim_plan_t plan) { return plan ? (int64_t)plan->dbytes : 0; }
 
 extern "C" void rsim_plan_destroy(rsim_plan_t plan) {

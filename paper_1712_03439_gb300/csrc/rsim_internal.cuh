@@ -94,6 +94,9 @@ void launch_backward(int logN, const DevBatch& B, const Queues& Q, const float* 
 void launch_finalize(const DevBatch& B, const float* gains, const float* dhp, const float* dap,
                      float* grad_rir, float* grad_gains, cudaStream_t st);
 
+// sets the calling thread's message returned by rsim_last_error()
+void set_last_error(const char* msg);
+
 // occupancy helpers (CTAs per SM) and shared-memory sizes of the tiled kernels
 int occupancy_spectrum(int logN);
 int occupancy_forward(int logN);
