@@ -65,7 +65,9 @@ typedef struct {
     int32_t fft_sizes_mask;        /* bit m allows N = 2^m, m in [11, 14]; 0 = all of them */
     int32_t gain_mode;             /* 0: alpha from SNRs (computed, written to gains);
                                       1: alpha given by the caller in gains */
-    int64_t segment_len;           /* samples per work tile; 0 = default (65536);
+    int64_t segment_len;           /* samples per forward work tile; 0 = default (the largest
+                                      allowed N); raised to the largest allowed N */
+    int64_t bwd_segment_len;       /* samples per backward work tile; 0 = default (65536);
                                       raised to the largest allowed N */
     const float *fft_cost;         /* [32] host, relative cost of one real FFT of size 2^m
                                       used to pick N per utterance; NULL = N log2 N */

@@ -40,6 +40,7 @@ class PlanDesc(ctypes.Structure):
         ("fft_sizes_mask", ctypes.c_int32),
         ("gain_mode", ctypes.c_int32),
         ("segment_len", ctypes.c_int64),
+        ("bwd_segment_len", ctypes.c_int64),
         ("fft_cost", ctypes.c_void_p),
     ]
 

@@ -38,7 +38,8 @@ class Plan:
     microphones and RIR lengths (see rsim_plan in include/rsim.h)."""
 
     def __init__(self, num_sources, num_samples, rir_len, num_mics, eta_db=20.0,
-                 fft_sizes=None, gain_mode=0, segment_len=0, fft_cost=None, device=None):
+                 fft_sizes=None, gain_mode=0, segment_len=0, bwd_segment_len=0, fft_cost=None,
+                 device=None):
         self._lib = _lib.load()
         self._handle = None
         self.num_sources = np.ascontiguousarray(num_sources, dtype=np.int32)
@@ -53,6 +54,19 @@ class Plan:
             if 1 << m != n:
                 raise ValueError(f"FFT size {n} is not a power of two")
             mask |= 1 << m
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = int(device)
+        # measured per-size costs and tile lengths for this GPU, if tuned
+        from .autotune import load_table
+        tuned = load_table(torch.cuda.get_device_name(self.device)) or {}
+        if fft_cost is None and "fft_cost_ns" in tuned:
+            fft_cost = {int(k): float(v) for k, v in tuned["fft_cost_ns"].items()}
+        if not segment_len:
+            segment_len = int(tuned.get("segment_len", 0))
+        if not bwd_segment_len:
+            bwd_segment_len = int(tuned.get("bwd_segment_len", 0))
+        self.tuned = bool(tuned)
         self._cost = None
         if fft_cost is not None:
             self._cost = np.zeros(32, np.float32)
@@ -63,10 +77,8 @@ class Plan:
             num_sources=self.num_sources.ctypes.data, num_samples=self.num_samples.ctypes.data,
             rir_len=self.rir_len.ctypes.data, eta_db=self.eta_db, fft_sizes_mask=mask,
             gain_mode=self.gain_mode, segment_len=int(segment_len),
+            bwd_segment_len=int(bwd_segment_len),
             fft_cost=None if self._cost is None else self._cost.ctypes.data)
-        if device is None:
-            device = torch.cuda.current_device()
-        self.device = int(device)
         h = ctypes.c_void_p()
         _lib.check(self._lib, self._lib.rsim_plan(ctypes.byref(desc), self.device, ctypes.byref(h)))
         self._handle = h

@@ -102,6 +102,10 @@ struct rsim_plan_s {
     int grid_spec[kNumBuckets] = {}, grid_fwd[kNumBuckets] = {}, grid_bwd[kNumBuckets] = {};
     bool fwd_done = false;
     StageTimer timer;
+    // one stream per FFT size so the per-size launches run side by side
+    cudaStream_t bs[kNumBuckets] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[kNumBuckets] = {};
 };
 
 namespace {
@@ -114,6 +118,22 @@ void stage_mark(rsim_plan_t p, int stage, bool end, cudaStream_t st) {
     if (!e) cudaEventCreate(&e);
     cudaEventRecord(e, st);
     if (end) ++p->timer.count[stage];
+}
+
+// Runs launch(logN, stream) for every allowed FFT size on that size's own
+// stream, forked from and joined back into st.  Largest sizes go first: their
+// tiles are the longest.
+template <typename F>
+void fan_out(rsim_plan_t p, cudaStream_t st, F launch) {
+    cudaEventRecord(p->ev_fork, st);
+    for (int m = kMaxLog; m >= kMinLog; --m) {
+        if (!((p->mask >> m) & 1)) continue;
+        const int b = m - kMinLog;
+        cudaStreamWaitEvent(p->bs[b], p->ev_fork, 0);
+        launch(m, p->bs[b]);
+        cudaEventRecord(p->ev_join[b], p->bs[b]);
+        cudaStreamWaitEvent(st, p->ev_join[b], 0);
+    }
 }
 
 }  // namespace
@@ -132,6 +152,11 @@ extern "C" void rsim_plan_destroy(rsim_plan_t plan) {
             for (auto& sl : st)
                 for (auto& e : sl)
                     if (e) cudaEventDestroy(e);
+        for (int b = 0; b < kNumBuckets; ++b) {
+            if (plan->bs[b]) cudaStreamDestroy(plan->bs[b]);
+            if (plan->ev_join[b]) cudaEventDestroy(plan->ev_join[b]);
+        }
+        if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
         if (plan->dmem) cudaFree(plan->dmem);
     }
     delete plan;
@@ -153,9 +178,10 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     if (mask == 0) mask = supported;
     if (mask & ~supported)
         return fail(RSIM_E_UNSUPPORTED, "fft_sizes_mask allows sizes outside 2^11 .. 2^14");
-    if (d->segment_len < 0) return fail(RSIM_E_INVALID, "segment_len must be >= 0");
+    if (d->segment_len < 0 || d->bwd_segment_len < 0)
+        return fail(RSIM_E_INVALID, "segment_len and bwd_segment_len must be >= 0");
 
-    std::vector<int32_t> src0(U + 1), rir0(U + 1), seg0(U + 1);
+    std::vector<int32_t> src0(U + 1), rir0(U + 1), seg0(U + 1), bseg0(U + 1);
     std::vector<int64_t> yoff(U + 1);
     int64_t S = 0, R = 0, ysz = 0;
     int imax = 1;
@@ -163,9 +189,12 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     int max_log = kMinLog;
     for (int m = kMinLog; m <= kMaxLog; ++m)
         if ((mask >> m) & 1) max_log = m;
-    int64_t seg_len = d->segment_len > 0 ? d->segment_len : 65536;
-    seg_len = std::max<int64_t>(seg_len, (int64_t)1 << max_log);
-    int64_t nseg = 0;
+    // forward tiles: short segments balance the load across SMs; backward
+    // tiles: longer ones amortise the per-tile dh transforms
+    int64_t seg_len = std::max<int64_t>(d->segment_len, (int64_t)1 << max_log);
+    int64_t bseg_len = d->bwd_segment_len > 0 ? d->bwd_segment_len : 65536;
+    bseg_len = std::max<int64_t>(bseg_len, (int64_t)1 << max_log);
+    int64_t nseg = 0, nbseg = 0;
     for (int u = 0; u < U; ++u) {
         const int I = d->num_sources[u];
         const int64_t nx = d->num_samples[u];
@@ -174,19 +203,23 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
         src0[u] = (int32_t)S;
         rir0[u] = (int32_t)R;
         seg0[u] = (int32_t)nseg;
+        bseg0[u] = (int32_t)nbseg;
         yoff[u] = ysz;
         S += I;
         R += (int64_t)I * J;
         ysz += (int64_t)J * nx;
         nseg += (nx + seg_len - 1) / seg_len;
+        nbseg += (nx + bseg_len - 1) / bseg_len;
         imax = std::max(imax, I);
         nx_max = std::max(nx_max, nx);
-        if (S > INT32_MAX / 2 || R > INT32_MAX / 2 || nseg * kMaxSources > INT32_MAX / 2)
+        if (S > INT32_MAX / 2 || R > INT32_MAX / 2 || nseg > INT32_MAX / 2 ||
+            nbseg * kMaxSources > INT32_MAX / 2)
             return fail(RSIM_E_UNSUPPORTED, "batch too large");
     }
     src0[U] = (int32_t)S;
     rir0[U] = (int32_t)R;
     seg0[U] = (int32_t)nseg;
+    bseg0[U] = (int32_t)nbseg;
     yoff[U] = ysz;
     std::vector<int32_t> rlen(d->rir_len, d->rir_len + R);
     std::vector<int64_t> roff(R + 1), xoff(S + 1);
@@ -204,18 +237,19 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
             }
         xoff[S] = o;
     }
-    std::vector<int32_t> seg_utt(nseg);
-    std::vector<int64_t> dhp_off(nseg + 1);
+    std::vector<int32_t> seg_utt(std::max<int64_t>(nseg, 1)), bseg_utt(std::max<int64_t>(nbseg, 1));
+    std::vector<int64_t> dhp_off(nbseg + 1);
     int64_t dhp_total = 0;
     for (int u = 0; u < U; ++u) {
         const int64_t rsum = roff[rir0[u + 1]] - roff[rir0[u]];
-        for (int g = seg0[u]; g < seg0[u + 1]; ++g) {
-            seg_utt[g] = u;
+        for (int g = seg0[u]; g < seg0[u + 1]; ++g) seg_utt[g] = u;
+        for (int g = bseg0[u]; g < bseg0[u + 1]; ++g) {
+            bseg_utt[g] = u;
             dhp_off[g] = dhp_total;
             dhp_total += rsum;
         }
     }
-    dhp_off[nseg] = dhp_total;
+    dhp_off[nbseg] = dhp_total;
     const int MMAX = 1 << (max_log - 1);
     const int CH = (int)((nx_max + kPowerChunk - 1) / kPowerChunk);
 
@@ -236,22 +270,25 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     // ---- carve one device allocation
     struct Piece { void** dst; size_t bytes; };
     std::vector<Piece> pieces;
+    void *p_bseg0, *p_bsegutt;
     void *p_nsrc, *p_nx, *p_src0, *p_rir0, *p_seg0, *p_segutt, *p_xoff, *p_yoff, *p_roff, *p_rlen,
         *p_dhpoff, *p_tuning, *p_L, *p_logN, *p_hop, *p_lmax, *p_nblk, *p_pow, *p_err, *p_list,
         *p_count, *p_next, *p_Hc, *p_tails, *p_dhp, *p_dap;
     void* p_tw[kNumBuckets] = {};
-    const int64_t cap = std::max<int64_t>(nseg * kMaxSources, R);
+    const int64_t cap = std::max<int64_t>(std::max<int64_t>(nbseg * kMaxSources, nseg), R);
     pieces.push_back({&p_nsrc, sizeof(int32_t) * U});
     pieces.push_back({&p_nx, sizeof(int64_t) * U});
     pieces.push_back({&p_src0, sizeof(int32_t) * (U + 1)});
     pieces.push_back({&p_rir0, sizeof(int32_t) * (U + 1)});
     pieces.push_back({&p_seg0, sizeof(int32_t) * (U + 1)});
     pieces.push_back({&p_segutt, sizeof(int32_t) * std::max<int64_t>(nseg, 1)});
+    pieces.push_back({&p_bseg0, sizeof(int32_t) * (U + 1)});
+    pieces.push_back({&p_bsegutt, sizeof(int32_t) * std::max<int64_t>(nbseg, 1)});
     pieces.push_back({&p_xoff, sizeof(int64_t) * (S + 1)});
     pieces.push_back({&p_yoff, sizeof(int64_t) * (U + 1)});
     pieces.push_back({&p_roff, sizeof(int64_t) * (R + 1)});
     pieces.push_back({&p_rlen, sizeof(int32_t) * R});
-    pieces.push_back({&p_dhpoff, sizeof(int64_t) * (nseg + 1)});
+    pieces.push_back({&p_dhpoff, sizeof(int64_t) * (nbseg + 1)});
     pieces.push_back({&p_tuning, sizeof(float) * 32});
     pieces.push_back({&p_L, sizeof(int32_t) * R});
     pieces.push_back({&p_logN, sizeof(int32_t) * U});
@@ -266,7 +303,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     pieces.push_back({&p_Hc, sizeof(float2) * R * MMAX});
     pieces.push_back({&p_tails, sizeof(float) * nseg * J * MMAX});
     pieces.push_back({&p_dhp, sizeof(float) * std::max<int64_t>(dhp_total, 1)});
-    pieces.push_back({&p_dap, sizeof(float) * nseg * kMaxSources});
+    pieces.push_back({&p_dap, sizeof(float) * std::max<int64_t>(nbseg, 1) * kMaxSources});
     std::vector<std::vector<float2>> tws(kNumBuckets);
     for (int m = kMinLog; m <= kMaxLog; ++m) {
         if (!((mask >> m) & 1)) continue;
@@ -304,11 +341,13 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
         {p_rir0, rir0.data(), sizeof(int32_t) * (U + 1)},
         {p_seg0, seg0.data(), sizeof(int32_t) * (U + 1)},
         {p_segutt, seg_utt.data(), sizeof(int32_t) * nseg},
+        {p_bseg0, bseg0.data(), sizeof(int32_t) * (U + 1)},
+        {p_bsegutt, bseg_utt.data(), sizeof(int32_t) * nbseg},
         {p_xoff, xoff.data(), sizeof(int64_t) * (S + 1)},
         {p_yoff, yoff.data(), sizeof(int64_t) * (U + 1)},
         {p_roff, roff.data(), sizeof(int64_t) * (R + 1)},
         {p_rlen, rlen.data(), sizeof(int32_t) * R},
-        {p_dhpoff, dhp_off.data(), sizeof(int64_t) * (nseg + 1)},
+        {p_dhpoff, dhp_off.data(), sizeof(int64_t) * (nbseg + 1)},
         {p_tuning, tuning.data(), sizeof(float) * 32},
     };
     for (int b = 0; b < kNumBuckets; ++b)
@@ -331,6 +370,8 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     DevBatch& B = p->B;
     B.U = U; B.J = J; B.S = (int32_t)S; B.R = (int32_t)R; B.IMAX = imax;
     B.NSEG = (int32_t)nseg; B.MMAX = MMAX; B.mask = mask; B.seg_len = seg_len;
+    B.NBSEG = (int32_t)nbseg; B.bseg_len = bseg_len;
+    B.bseg0 = (const int32_t*)p_bseg0; B.bseg_utt = (const int32_t*)p_bsegutt;
     B.gain_mode = d->gain_mode;
     B.n_src = (const int32_t*)p_nsrc; B.n_x = (const int64_t*)p_nx;
     B.src0 = (const int32_t*)p_src0; B.rir0 = (const int32_t*)p_rir0;
@@ -355,7 +396,18 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
         p->grid_spec[b] = (int)std::max<int64_t>(1, std::min<int64_t>(R, (int64_t)p->sms * occupancy_spectrum(m)));
         p->grid_fwd[b] = (int)std::max<int64_t>(1, std::min<int64_t>(nseg, (int64_t)p->sms * occupancy_forward(m)));
         p->grid_bwd[b] = (int)std::max<int64_t>(
-            1, std::min<int64_t>(nseg * imax, (int64_t)p->sms * occupancy_backward(m)));
+            1, std::min<int64_t>(nbseg * imax, (int64_t)p->sms * occupancy_backward(m)));
+    }
+    e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+    for (int m = kMinLog; m <= kMaxLog && e == cudaSuccess; ++m) {
+        if (!((mask >> m) & 1)) continue;
+        const int b = m - kMinLog;
+        e = cudaStreamCreateWithFlags(&p->bs[b], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join[b], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        rsim_plan_destroy(p);
+        return cuda_fail(e, "stream/event creation");
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -388,15 +440,15 @@ extern "C" rsim_status rsim_filter_mix(rsim_plan_t p, void* stream, const float*
     launch_plan(B, p->Q, snr_db, gains, st);
     stage_mark(p, 2, true, st);
     stage_mark(p, 3, false, st);
-    for (int m = kMinLog; m <= kMaxLog; ++m)
-        if ((p->mask >> m) & 1)
-            launch_spectrum(m, B, p->Q, rir, p->Hc, p->tw[m - kMinLog], p->grid_spec[m - kMinLog], st);
+    fan_out(p, st, [&](int m, cudaStream_t s) {
+        launch_spectrum(m, B, p->Q, rir, p->Hc, p->tw[m - kMinLog], p->grid_spec[m - kMinLog], s);
+    });
     stage_mark(p, 3, true, st);
     stage_mark(p, 4, false, st);
-    for (int m = kMinLog; m <= kMaxLog; ++m)
-        if ((p->mask >> m) & 1)
-            launch_forward(m, B, p->Q, x, gains, p->Hc, y, p->tails, p->tw[m - kMinLog],
-                           p->grid_fwd[m - kMinLog], st);
+    fan_out(p, st, [&](int m, cudaStream_t s) {
+        launch_forward(m, B, p->Q, x, gains, p->Hc, y, p->tails, p->tw[m - kMinLog],
+                       p->grid_fwd[m - kMinLog], s);
+    });
     stage_mark(p, 4, true, st);
     stage_mark(p, 5, false, st);
     launch_fixup(B, y, p->tails, st);
@@ -425,10 +477,10 @@ extern "C" rsim_status rsim_filter_mix_backward(rsim_plan_t p, void* stream, con
     cudaError_t e = cudaMemsetAsync(p->Q.next + p->Q.idx(kListBwd, 0), 0, sizeof(int32_t) * kNumBuckets, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (queue)");
     stage_mark(p, 6, false, st);
-    for (int m = kMinLog; m <= kMaxLog; ++m)
-        if ((p->mask >> m) & 1)
-            launch_backward(m, B, p->Q, grad_y, x, gains, p->Hc, grad_x, p->dhp, p->dap,
-                            p->tw[m - kMinLog], p->grid_bwd[m - kMinLog], st);
+    fan_out(p, st, [&](int m, cudaStream_t s) {
+        launch_backward(m, B, p->Q, grad_y, x, gains, p->Hc, grad_x, p->dhp, p->dap,
+                        p->tw[m - kMinLog], p->grid_bwd[m - kMinLog], s);
+    });
     stage_mark(p, 6, true, st);
     stage_mark(p, 7, false, st);
     launch_finalize(B, gains, p->dhp, p->dap, grad_rir, grad_gains, st);

@@ -59,13 +59,13 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
         const int code = pop_job_b(Q, kListBwd, bucket, &slot);
         if (code < 0) break;
         const int g = code / kMaxSources, i = code % kMaxSources;
-        const int u = B.seg_utt[g];
-        const int64_t s = g - B.seg0[u];
+        const int u = B.bseg_utt[g];
+        const int64_t s = g - B.bseg0[u];
         const int64_t nx = B.n_x[u];
         const int hop = B.hop[u];
         const int lmax = B.Lmax[u];
         int64_t b0, b1;
-        segment_blocks(s, B.seg_len, hop, B.nblk[u], &b0, &b1);
+        segment_blocks(s, B.bseg_len, hop, B.nblk[u], &b0, &b1);
         if (b0 >= b1) continue;
         const int J = B.J;
         const int sb = B.src0[u], rb = B.rir0[u];
@@ -195,9 +195,9 @@ k_finalize(DevBatch B, const float* __restrict__ gains, const float* __restrict_
         for (int k = threadIdx.x; k < nh; k += blockDim.x) {
             float acc = 0.f;
             if (k < Lr) {
-                for (int g = B.seg0[u]; g < B.seg0[u + 1]; ++g) {
+                for (int g = B.bseg0[u]; g < B.bseg0[u + 1]; ++g) {
                     int64_t b0, b1;
-                    segment_blocks(g - B.seg0[u], B.seg_len, hop, B.nblk[u], &b0, &b1);
+                    segment_blocks(g - B.bseg0[u], B.bseg_len, hop, B.nblk[u], &b0, &b1);
                     if (b0 >= b1) continue;
                     acc += dhp[B.dhp_off[g] + local + k];
                 }
@@ -215,9 +215,9 @@ k_finalize(DevBatch B, const float* __restrict__ gains, const float* __restrict_
             const int u = lo, i = sidx - B.src0[u];
             float acc = 0.f;
             if (B.logN[u] != 0) {
-                for (int g = B.seg0[u]; g < B.seg0[u + 1]; ++g) {
+                for (int g = B.bseg0[u]; g < B.bseg0[u + 1]; ++g) {
                     int64_t b0, b1;
-                    segment_blocks(g - B.seg0[u], B.seg_len, B.hop[u], B.nblk[u], &b0, &b1);
+                    segment_blocks(g - B.bseg0[u], B.bseg_len, B.hop[u], B.nblk[u], &b0, &b1);
                     if (b0 >= b1) continue;
                     acc += dap[(int64_t)g * kMaxSources + i];
                 }

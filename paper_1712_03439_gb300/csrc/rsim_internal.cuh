@@ -24,8 +24,10 @@ enum : int32_t {
 enum : int { kListFwd = 0, kListBwd = 1, kListSpec = 2, kNumLists = 3 };
 
 // Batch description and per-call state on the device.  Utterance u has
-// n_src[u] sources (source 0 is the target) and J microphones; it is cut into
-// nseg = ceil(n_x / seg_len) segments, each one tile of work.
+// n_src[u] sources (source 0 is the target) and J microphones.  The forward
+// cuts it into ceil(n_x / seg_len) segments and the backward into
+// ceil(n_x / bseg_len) segments; a segment is one tile of work (a backward
+// tile is a segment and one source).
 struct DevBatch {
     int32_t U, J, S, R, IMAX;
     int32_t NSEG;            // total segments
@@ -43,7 +45,11 @@ struct DevBatch {
     const int64_t* yoff;     // [U+1] offset of utterance u in y
     const int64_t* roff;     // [R+1] offset of RIR r in rir
     const int32_t* rir_len;  // [R]
-    const int64_t* dhp_off;  // [NSEG] offset of a segment's dh partials
+    int32_t NBSEG;           // total backward segments
+    int64_t bseg_len;        // samples per backward segment (>= largest allowed N)
+    const int32_t* bseg0;    // [U+1] first backward segment of utterance
+    const int32_t* bseg_utt; // [NBSEG] utterance of backward segment
+    const int64_t* dhp_off;  // [NBSEG] offset of a backward segment's dh partials
     const float* tuning;     // [32] cost per real FFT of size 2^m (any unit)
     // written on the device during a call
     int32_t* L;              // [R] kept RIR length (Eq. 9)

@@ -236,7 +236,7 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
             const int64_t N = 1LL << m;
             const int64_t hop = N - lmax + 1;
             if (lmax - 1 > hop) continue;              // tail must fit in one hop
-            if (N > B.seg_len) continue;
+            if (N > B.seg_len || N > B.bseg_len) continue;
             const int64_t nb = (nx + hop - 1) / hop;
             const double c = ((double)nb * (I + J) + (double)I * J) * (double)B.tuning[m];
             if (best == 0 || c < best_c) { best = m; best_c = c; }
@@ -257,9 +257,8 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
         int cf = 0, cb = 0, cs = 0;
         for (int u = u0; u < u1; ++u) {
             if (B.logN[u] != m) continue;
-            const int ns = B.seg0[u + 1] - B.seg0[u];
-            cf += ns;
-            cb += ns * B.n_src[u];
+            cf += B.seg0[u + 1] - B.seg0[u];
+            cb += (B.bseg0[u + 1] - B.bseg0[u]) * B.n_src[u];
             cs += B.rir0[u + 1] - B.rir0[u];
         }
         int tf, tb, ts;
@@ -271,10 +270,9 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
         int32_t* ls = Q.lst(kListSpec, b);
         for (int u = u0; u < u1; ++u) {
             if (B.logN[u] != m) continue;
-            for (int g = B.seg0[u]; g < B.seg0[u + 1]; ++g) {
-                lf[of++] = g;
+            for (int g = B.seg0[u]; g < B.seg0[u + 1]; ++g) lf[of++] = g;
+            for (int g = B.bseg0[u]; g < B.bseg0[u + 1]; ++g)
                 for (int i = 0; i < B.n_src[u]; ++i) lb[ob++] = g * kMaxSources + i;
-            }
             for (int r = B.rir0[u]; r < B.rir0[u + 1]; ++r) ls[os++] = r;
         }
         if (t == 0) {

@@ -40,7 +40,8 @@ def _desc(**kw):
                       num_sources=ns.ctypes.data, num_samples=nx.ctypes.data,
                       rir_len=rl.ctypes.data, eta_db=kw.pop("eta", 20.0),
                       fft_sizes_mask=kw.pop("mask", 0), gain_mode=kw.pop("gm", 0),
-                      segment_len=kw.pop("seg", 0), fft_cost=None)
+                      segment_len=kw.pop("seg", 0), bwd_segment_len=kw.pop("bseg", 0),
+                      fft_cost=None)
     return d, (ns, nx, rl)
 
 
@@ -56,6 +57,7 @@ def _desc(**kw):
     (dict(rl=[0]), 1),
     (dict(mask=1 << 16), 2),
     (dict(seg=-5), 1),
+    (dict(bseg=-5), 1),
 ])
 def test_plan_rejects_bad_descriptions_on_the_host(lib, kw, status):
     d, keep = _desc(**kw)

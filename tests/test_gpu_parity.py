@@ -31,10 +31,11 @@ def dev(a, dtype=torch.float32):
     return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
 
 
-def gpu_forward(batch, eta=20.0, fft_sizes=None, seg=0, gains=None):
+def gpu_forward(batch, eta=20.0, fft_sizes=None, seg=0, gains=None, bseg=0):
     from paper_1712_03439_gb300 import Plan, filter_mix
     plan = Plan.for_batch(batch, eta_db=eta, fft_sizes=fft_sizes,
-                          gain_mode=0 if gains is None else 1, segment_len=seg)
+                          gain_mode=0 if gains is None else 1, segment_len=seg,
+                          bwd_segment_len=bseg)
     x, rir = dev(batch.x), dev(batch.rir)
     if gains is None:
         out = filter_mix(plan, x, rir, snr_db=dev(batch.snr_db))
@@ -200,9 +201,10 @@ def test_full_size_home_workload_sampled_utterances():
 # ---------------------------------------------------------------------------
 # backward
 # ---------------------------------------------------------------------------
-def gpu_backward(batch, eta, gains, gy, seg=0, fft_sizes=None):
+def gpu_backward(batch, eta, gains, gy, seg=0, fft_sizes=None, bseg=0):
     from paper_1712_03439_gb300 import Plan
-    plan, res, (x, rir, g) = gpu_forward(batch, eta=eta, gains=gains, seg=seg, fft_sizes=fft_sizes)
+    plan, res, (x, rir, g) = gpu_forward(batch, eta=eta, gains=gains, seg=seg, fft_sizes=fft_sizes,
+                                         bseg=bseg)
     gx = torch.empty_like(x)
     gr = torch.empty_like(rir)
     gg = torch.empty_like(g)
@@ -217,13 +219,13 @@ def _close_vec(a, r, rel, what):
         f"{what}: rel L2 {np.linalg.norm(a - r) / max(nr, 1e-30):.3e}"
 
 
-@pytest.mark.parametrize("eta,seg", [(20.0, 0), (math.inf, 16384)])
-def test_backward_parity_small_batch(eta, seg):
+@pytest.mark.parametrize("eta,seg,bseg", [(20.0, 0, 0), (math.inf, 16384, 16384), (20.0, 0, 40000)])
+def test_backward_parity_small_batch(eta, seg, bseg):
     b = small_batch(seed=21, lengths=(900, 20011, 50000, 70001), n_src=(2, 3, 4, 1))
     S = int(b.num_sources.sum())
     gains = np.linspace(0.6, 1.3, S).astype(np.float32)
     gy = synth.grad_like(22, b.y_size)
-    _, gx, gr, gg = gpu_backward(b, eta, gains, gy, seg=seg)
+    _, gx, gr, gg = gpu_backward(b, eta, gains, gy, seg=seg, bseg=bseg)
     L = oracle.truncate_batch(b, eta)["L"]
     ref = oracle.backward(b, L, gains.astype(np.float64), gy)
     # per source: dx; per RIR: dh; dalpha elementwise
