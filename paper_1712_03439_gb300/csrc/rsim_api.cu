@@ -51,13 +51,15 @@ template <int M>
 std::vector<float2> twiddle_table() {
     using P = FftPlan<M>;
     std::vector<float2> tw(P::TW_LEN);
-    for (int m = 0; m < 16; ++m)
-        for (int k = 0; k < 16; ++k) tw[P::OFF1 + m * 16 + k] = twiddle((int64_t)m * k, 256);
-    for (int m = 0; m < P::R2; ++m)
-        for (int k = 0; k < 256; ++k) tw[P::OFF2 + m * 256 + k] = twiddle((int64_t)m * k, 256 * P::R2);
+    // pass 1: LP = 16, R = 16; rows w^(2^j), j < 4
+    for (int j = 0; j < 4; ++j)
+        for (int k = 0; k < 16; ++k) tw[P::OFF1 + j * 16 + k] = twiddle((int64_t)(1 << j) * k, 256);
+    // pass 2: LP = 256, R = R2
+    for (int j = 0; j < Log2R<P::R2>::v; ++j)
+        for (int k = 0; k < 256; ++k) tw[P::OFF2 + j * 256 + k] = twiddle((int64_t)(1 << j) * k, 256 * P::R2);
+    // pass 3 (M = 8192): LP = 4096, R = 2
     if (M == 8192)
-        for (int m = 0; m < 2; ++m)
-            for (int k = 0; k < 4096; ++k) tw[P::OFF3 + m * 4096 + k] = twiddle((int64_t)m * k, 8192);
+        for (int k = 0; k < 4096; ++k) tw[P::OFF3 + k] = twiddle(k, 8192);
     for (int k = 0; k <= M / 2; ++k) tw[P::OFF_SPLIT + k] = twiddle(k, 2 * M);
     return tw;
 }
@@ -97,6 +99,7 @@ struct rsim_plan_s {
     float* tails = nullptr;
     float* dhp = nullptr;
     float* dap = nullptr;
+    float2* Wb[kNumBuckets] = {};   // per-CTA backward accumulators of each FFT size
     float2* tw[kNumBuckets] = {};
     int grid_trunc = 1, grid_pow = 1;
     int grid_spec[kNumBuckets] = {}, grid_fwd[kNumBuckets] = {}, grid_bwd[kNumBuckets] = {};
@@ -275,7 +278,23 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
         *p_dhpoff, *p_tuning, *p_L, *p_logN, *p_hop, *p_lmax, *p_nblk, *p_pow, *p_err, *p_list,
         *p_count, *p_next, *p_Hc, *p_tails, *p_dhp, *p_dap;
     void* p_tw[kNumBuckets] = {};
-    const int64_t cap = std::max<int64_t>(std::max<int64_t>(nbseg * kMaxSources, nseg), R);
+    const int64_t cap = std::max<int64_t>(std::max<int64_t>(nbseg, nseg), R);
+    // launch shapes (persistent grids) decide the per-CTA backward scratch
+    int sms = 0;
+    {
+        DeviceGuard g0(device);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    }
+    if (sms < 1) sms = 1;
+    int grid_spec[kNumBuckets] = {}, grid_fwd[kNumBuckets] = {}, grid_bwd[kNumBuckets] = {};
+    for (int m = kMinLog; m <= kMaxLog; ++m) {
+        if (!((mask >> m) & 1)) continue;
+        const int b = m - kMinLog;
+        DeviceGuard g0(device);
+        grid_spec[b] = (int)std::max<int64_t>(1, std::min<int64_t>(R, (int64_t)sms * occupancy_spectrum(m)));
+        grid_fwd[b] = (int)std::max<int64_t>(1, std::min<int64_t>(nseg, (int64_t)sms * occupancy_forward(m)));
+        grid_bwd[b] = (int)std::max<int64_t>(1, std::min<int64_t>(nbseg, (int64_t)sms * occupancy_backward(m)));
+    }
     pieces.push_back({&p_nsrc, sizeof(int32_t) * U});
     pieces.push_back({&p_nx, sizeof(int64_t) * U});
     pieces.push_back({&p_src0, sizeof(int32_t) * (U + 1)});
@@ -304,6 +323,11 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     pieces.push_back({&p_tails, sizeof(float) * nseg * J * MMAX});
     pieces.push_back({&p_dhp, sizeof(float) * std::max<int64_t>(dhp_total, 1)});
     pieces.push_back({&p_dap, sizeof(float) * std::max<int64_t>(nbseg, 1) * kMaxSources});
+    void* p_W[kNumBuckets] = {};
+    for (int m = kMinLog; m <= kMaxLog; ++m)
+        if ((mask >> m) & 1)
+            pieces.push_back({&p_W[m - kMinLog], sizeof(float2) * (size_t)grid_bwd[m - kMinLog] * imax * J *
+                                                     ((size_t)1 << (m - 1))});
     std::vector<std::vector<float2>> tws(kNumBuckets);
     for (int m = kMinLog; m <= kMaxLog; ++m) {
         if (!((mask >> m) & 1)) continue;
@@ -385,19 +409,15 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     p->Q.list = (int32_t*)p_list; p->Q.count = (int32_t*)p_count; p->Q.next = (int32_t*)p_next;
     p->Q.cap = (int32_t)cap;
     p->Hc = (float2*)p_Hc; p->tails = (float*)p_tails; p->dhp = (float*)p_dhp; p->dap = (float*)p_dap;
-    for (int b = 0; b < kNumBuckets; ++b) p->tw[b] = (float2*)p_tw[b];
-
-    // ---- launch shapes
+    for (int b = 0; b < kNumBuckets; ++b) {
+        p->tw[b] = (float2*)p_tw[b];
+        p->Wb[b] = (float2*)p_W[b];
+        p->grid_spec[b] = grid_spec[b];
+        p->grid_fwd[b] = grid_fwd[b];
+        p->grid_bwd[b] = grid_bwd[b];
+    }
     p->grid_trunc = (int)std::max<int64_t>(1, std::min<int64_t>(R, (int64_t)p->sms * 8));
     p->grid_pow = (int)std::max<int64_t>(1, std::min<int64_t>(S * CH, (int64_t)p->sms * 8));
-    for (int m = kMinLog; m <= kMaxLog; ++m) {
-        if (!((mask >> m) & 1)) continue;
-        const int b = m - kMinLog;
-        p->grid_spec[b] = (int)std::max<int64_t>(1, std::min<int64_t>(R, (int64_t)p->sms * occupancy_spectrum(m)));
-        p->grid_fwd[b] = (int)std::max<int64_t>(1, std::min<int64_t>(nseg, (int64_t)p->sms * occupancy_forward(m)));
-        p->grid_bwd[b] = (int)std::max<int64_t>(
-            1, std::min<int64_t>(nbseg * imax, (int64_t)p->sms * occupancy_backward(m)));
-    }
     e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
     for (int m = kMinLog; m <= kMaxLog && e == cudaSuccess; ++m) {
         if (!((mask >> m) & 1)) continue;
@@ -478,7 +498,7 @@ extern "C" rsim_status rsim_filter_mix_backward(rsim_plan_t p, void* stream, con
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (queue)");
     stage_mark(p, 6, false, st);
     fan_out(p, st, [&](int m, cudaStream_t s) {
-        launch_backward(m, B, p->Q, grad_y, x, gains, p->Hc, grad_x, p->dhp, p->dap,
+        launch_backward(m, B, p->Q, grad_y, x, gains, p->Hc, grad_x, p->dhp, p->dap, p->Wb[m - kMinLog],
                         p->tw[m - kMinLog], p->grid_bwd[m - kMinLog], s);
     });
     stage_mark(p, 6, true, st);

@@ -41,24 +41,44 @@ __device__ __forceinline__ double block_sum_d(double v, double* sd) {
 }
 
 // ---------------------------------------------------------------------------
-// K7: persistent over (segment, source) tiles
+// K7: persistent over backward segments (all sources of a segment per tile)
 // ---------------------------------------------------------------------------
+// Per block b of the segment:
+//   G_j = rFFT_N(g_j[b hop, b hop + hop + L_max - 1))    once per mic, kept in
+//                                                         shared memory (pair layout)
+//   for each source i:
+//     X_i = rFFT_N(x_i block)                             registers (pair layout)
+//     C_i = sum_j conj(Hc_ij) G_j                          registers
+//     W_ij += conj(X_i) G_j                                per-CTA scratch in L2
+//     c_i = irFFT_N(C_i)[0, hop): dx_i = alpha_i c_i, dalpha_i += <c_i, x_i>
+// so a block costs J + 2I transforms.  At the end of the segment
+// dh partial_ij = irFFT_N(W_ij)[0, L_ij).  Each thread owns the same bin pairs
+// in every split, product and pre-processing step, so its slots in G and W
+// are private: no conflicts, no barriers around them.  Microphones go in
+// groups of kJG (the source spectra are recomputed per group; dx of later
+// groups is added to the first group's).
 template <int M>
-__global__ void __launch_bounds__(M / kE)
+__global__ void __launch_bounds__(M / kE, (M <= 4096 ? 2 : 1))
 k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const float* __restrict__ x,
            const float* __restrict__ gains, const float2* __restrict__ Hc, float* __restrict__ dx,
-           float* __restrict__ dhp, float* __restrict__ dap, const float2* __restrict__ tw) {
+           float* __restrict__ dhp, float* __restrict__ dap, float2* __restrict__ Wg,
+           const float2* __restrict__ tw) {
+    using Pl = FftPlan<M>;
     constexpr int T = M / kE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* sm = reinterpret_cast<float2*>(smem_raw);
-    float2* W = reinterpret_cast<float2*>(smem_raw + sizeof(float2) * padded_len(M));
+    float2* Gs = reinterpret_cast<float2*>(smem_raw + sizeof(float2) * padded_len(M)) + threadIdx.x;
     __shared__ double sd[32];
+    __shared__ double dsum[kMaxSources];
     __shared__ int slot;
     const int t = threadIdx.x;
+    const float2* wsplit = tw + Pl::OFF_SPLIT;
+    const int J = B.J;
+    // this CTA's accumulators: W_ij slot e of thread t at ((i J + j) M + e T + t)
+    float2* Wc = Wg + (int64_t)blockIdx.x * B.IMAX * J * M + t;
     for (;;) {
-        const int code = pop_job_b(Q, kListBwd, bucket, &slot);
-        if (code < 0) break;
-        const int g = code / kMaxSources, i = code % kMaxSources;
+        const int g = pop_job_b(Q, kListBwd, bucket, &slot);
+        if (g < 0) break;
         const int u = B.bseg_utt[g];
         const int64_t s = g - B.bseg0[u];
         const int64_t nx = B.n_x[u];
@@ -67,102 +87,115 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
         int64_t b0, b1;
         segment_blocks(s, B.bseg_len, hop, B.nblk[u], &b0, &b1);
         if (b0 >= b1) continue;
-        const int J = B.J;
+        const int I = B.n_src[u];
         const int sb = B.src0[u], rb = B.rir0[u];
-        const float a = __ldg(gains + sb + i);
-        const float* xi = x + B.xoff[sb + i];
-        float* dxi = dx ? dx + B.xoff[sb + i] : nullptr;
-        float da = 0.f, dac = 0.f;   // Kahan sum of c * x
+        if (t < kMaxSources) dsum[t] = 0.0;
+        for (int ij = 0; ij < I * J; ++ij)
+#pragma unroll
+            for (int e = 0; e < kE; ++e) Wc[(int64_t)ij * M + e * T] = make_float2(0.f, 0.f);
         for (int j0 = 0; j0 < J; j0 += kJG) {
             const int jn = min(kJG, J - j0);
-#pragma unroll
-            for (int jj = 0; jj < kJG; ++jj)
-#pragma unroll
-                for (int e = 0; e < kE; ++e) W[(jj * kE + e) * T + t] = make_float2(0.f, 0.f);
             for (int64_t b = b0; b < b1; ++b) {
                 const int64_t pos = b * hop;
                 const int64_t len = min((int64_t)hop, nx - pos);
                 const int64_t wlen = min((int64_t)(hop + lmax - 1), nx - pos);
-                float2 X[kE];
-                rfft_pairs<M>(X, xi + pos, len, sm, tw, t);
-                float2 C[kE];
-#pragma unroll
-                for (int e = 0; e < kE; ++e) C[e] = make_float2(0.f, 0.f);
+                const int64_t lim = nx - pos;
+                // mic spectra of this block
 #pragma unroll
                 for (int jj = 0; jj < kJG; ++jj) {
                     if (jj >= jn) break;
-                    const int j = j0 + jj;
-                    float2 G[kE];
-                    rfft_pairs<M>(G, gy + B.yoff[u] + (int64_t)j * nx + pos, wlen, sm, tw, t);
-                    const float2* H = Hc + (int64_t)(rb + i * J + j) * B.MMAX;
-                    float2* Wj = W + (jj * kE) * T + t;
+                    rfft_to_smem<M>(gy + B.yoff[u] + (int64_t)(j0 + jj) * nx + pos, wlen, sm, tw, t);
 #pragma unroll
-                    for (int q = 0; q < kE / 2; ++q) {
-                        const int k = t + q * T;
-                        float2 w0 = Wj[(2 * q) * T], w1 = Wj[(2 * q + 1) * T];
-                        if (k == 0) {
-                            const float2 h0 = __ldg(H), hh = __ldg(H + M / 2);
-                            C[0].x += h0.x * G[0].x;
-                            C[0].y += h0.y * G[0].y;
-                            C[1] = cadd(C[1], cmulc(hh, G[1]));
-                            w0.x += X[0].x * G[0].x;
-                            w0.y += X[0].y * G[0].y;
-                            w1 = cadd(w1, cmulc(X[1], G[1]));
-                        } else {
-                            C[2 * q] = cadd(C[2 * q], cmulc(__ldg(H + k), G[2 * q]));
-                            C[2 * q + 1] = cadd(C[2 * q + 1], cmulc(__ldg(H + M - k), G[2 * q + 1]));
-                            w0 = cadd(w0, cmulc(X[2 * q], G[2 * q]));
-                            w1 = cadd(w1, cmulc(X[2 * q + 1], G[2 * q + 1]));
-                        }
-                        Wj[(2 * q) * T] = w0;
-                        Wj[(2 * q + 1) * T] = w1;
-                    }
+                    for (int q = 0; q < kE / 2; ++q)
+                        split_pair<M>(sm, wsplit, t + q * T, Gs[(jj * kE + 2 * q) * T],
+                                      Gs[(jj * kE + 2 * q + 1) * T]);
                 }
-                float2 v[kE];
-                irfft_pairs<M>(v, C, sm, tw, t);
-                const int64_t lim = nx - pos;
+                for (int i = 0; i < I; ++i) {
+                    const float* xi = x + B.xoff[sb + i];
+                    float2 X[kE];
+                    rfft_to_smem<M>(xi + pos, len, sm, tw, t);
+                    split_forward<M>(X, sm, wsplit, t);
+                    float2 C[kE];
 #pragma unroll
-                for (int q = 0; q < kE; ++q) {
-                    const int n = 2 * (t + q * T);
+                    for (int e = 0; e < kE; ++e) C[e] = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const int nn = n + e;
-                        if (nn < hop && nn < lim) {
-                            const float c = e ? v[q].y : v[q].x;
-                            if (dxi) {
-                                const float d = a * c;
-                                dxi[pos + nn] = (j0 == 0) ? d : dxi[pos + nn] + d;
+                    for (int jj = 0; jj < kJG; ++jj) {
+                        if (jj >= jn) break;
+                        const float2* H = Hc + (int64_t)(rb + i * J + j0 + jj) * B.MMAX;
+                        float2* W = Wc + (int64_t)(i * J + j0 + jj) * M;
+#pragma unroll
+                        for (int q = 0; q < kE / 2; ++q) {
+                            const int k = t + q * T;
+                            const int kb = (k == 0) ? M / 2 : M - k;
+                            const float2 ga = Gs[(jj * kE + 2 * q) * T], gb = Gs[(jj * kE + 2 * q + 1) * T];
+                            const float2 ha = __ldg(H + k), hb = __ldg(H + kb);
+                            float2 w0 = W[(2 * q) * T], w1 = W[(2 * q + 1) * T];
+                            if (k == 0) {            // slot 0 holds two real bins
+                                C[0].x += ha.x * ga.x;
+                                C[0].y += ha.y * ga.y;
+                                w0.x += X[0].x * ga.x;
+                                w0.y += X[0].y * ga.y;
+                            } else {
+                                C[2 * q] = cadd(C[2 * q], cmulc(ha, ga));
+                                w0 = cadd(w0, cmulc(X[2 * q], ga));
                             }
-                            const float yv = fmaf(c, __ldg(xi + pos + nn), -dac);
-                            const float tv = da + yv;
-                            dac = (tv - da) - yv;
-                            da = tv;
+                            C[2 * q + 1] = cadd(C[2 * q + 1], cmulc(hb, gb));
+                            w1 = cadd(w1, cmulc(X[2 * q + 1], gb));
+                            W[(2 * q) * T] = w0;
+                            W[(2 * q + 1) * T] = w1;
                         }
                     }
-                }
-            }
-            // dh partials of this segment for mics j0 .. j0 + jn - 1
+                    float2 v[kE];
+                    irfft_pairs<M>(v, C, sm, tw, t);
+                    const float a = __ldg(gains + sb + i);
+                    float* dxi = dx ? dx + B.xoff[sb + i] : nullptr;
+                    float da = 0.f, dac = 0.f;   // Kahan sum of c * x over this block
 #pragma unroll
-            for (int jj = 0; jj < kJG; ++jj) {
-                if (jj >= jn) break;
-                float2 Wr[kE];
+                    for (int q = 0; q < kE; ++q) {
+                        const int n = 2 * (t + q * T);
 #pragma unroll
-                for (int e = 0; e < kE; ++e) Wr[e] = W[(jj * kE + e) * T + t];
-                float2 v[kE];
-                irfft_pairs<M>(v, Wr, sm, tw, t);
-                const int r = rb + i * J + j0 + jj;
-                const int Lr = B.L[r];
-                float* out = dhp + B.dhp_off[g] + (B.roff[r] - B.roff[rb]);
-#pragma unroll
-                for (int q = 0; q < kE; ++q) {
-                    const int n = 2 * (t + q * T);
-                    if (n < Lr) out[n] = v[q].x;
-                    if (n + 1 < Lr) out[n + 1] = v[q].y;
+                        for (int e = 0; e < 2; ++e) {
+                            const int nn = n + e;
+                            if (nn < hop && nn < lim) {
+                                const float c = e ? v[q].y : v[q].x;
+                                if (dxi) {
+                                    const float d = a * c;
+                                    dxi[pos + nn] = (j0 == 0) ? d : dxi[pos + nn] + d;
+                                }
+                                const float yv = fmaf(c, __ldg(xi + pos + nn), -dac);
+                                const float tv = da + yv;
+                                dac = (tv - da) - yv;
+                                da = tv;
+                            }
+                        }
+                    }
+                    const double tot = block_sum_d((double)da - (double)dac, sd);
+                    if (t == 0) dsum[i] += tot;
                 }
             }
         }
-        const double tot = block_sum_d((double)da - (double)dac, sd);
-        if (t == 0) dap[(int64_t)g * kMaxSources + i] = (float)tot;
+        // dh partials of this segment
+        for (int ij = 0; ij < I * J; ++ij) {
+            const float2* W = Wc + (int64_t)ij * M;
+            __syncthreads();                 // sm is free
+#pragma unroll 2
+            for (int q = 0; q < kE / 2; ++q)
+                unsplit_pair<M>(sm, wsplit, t + q * T, W[(2 * q) * T], W[(2 * q + 1) * T]);
+            __syncthreads();
+            float2 v[kE];
+            irfft_from_smem<M>(v, sm, tw, t);
+            const int r = rb + ij;
+            const int Lr = B.L[r];
+            float* out = dhp + B.dhp_off[g] + (B.roff[r] - B.roff[rb]);
+#pragma unroll
+            for (int q = 0; q < kE; ++q) {
+                const int n = 2 * (t + q * T);
+                if (n < Lr) out[n] = v[q].x;
+                if (n + 1 < Lr) out[n + 1] = v[q].y;
+            }
+        }
+        __syncthreads();
+        if (t < I) dap[(int64_t)g * kMaxSources + t] = (float)dsum[t];
     }
 }
 
@@ -236,20 +269,20 @@ constexpr int smem_backward() { return (int)sizeof(float2) * (padded_len(M) + kJ
 template <int M>
 static void backward_m(const DevBatch& B, const Queues& Q, int bucket, const float* g, const float* x,
                        const float* gains, const float2* Hc, float* dx, float* dhp, float* dap,
-                       const float2* tw, int grid, cudaStream_t st) {
+                       float2* W, const float2* tw, int grid, cudaStream_t st) {
     k_backward<M><<<grid, M / kE, smem_backward<M>(), st>>>(B, Q, bucket, g, x, gains, Hc, dx, dhp,
-                                                            dap, tw);
+                                                            dap, W, tw);
 }
 
 void launch_backward(int logN, const DevBatch& B, const Queues& Q, const float* g, const float* x,
                      const float* gains, const float2* Hc, float* dx, float* dhp, float* dap,
-                     const float2* tw, int grid, cudaStream_t st) {
+                     float2* W, const float2* tw, int grid, cudaStream_t st) {
     const int b = logN - kMinLog;
     switch (logN) {
-        case 11: backward_m<1024>(B, Q, b, g, x, gains, Hc, dx, dhp, dap, tw, grid, st); break;
-        case 12: backward_m<2048>(B, Q, b, g, x, gains, Hc, dx, dhp, dap, tw, grid, st); break;
-        case 13: backward_m<4096>(B, Q, b, g, x, gains, Hc, dx, dhp, dap, tw, grid, st); break;
-        case 14: backward_m<8192>(B, Q, b, g, x, gains, Hc, dx, dhp, dap, tw, grid, st); break;
+        case 11: backward_m<1024>(B, Q, b, g, x, gains, Hc, dx, dhp, dap, W, tw, grid, st); break;
+        case 12: backward_m<2048>(B, Q, b, g, x, gains, Hc, dx, dhp, dap, W, tw, grid, st); break;
+        case 13: backward_m<4096>(B, Q, b, g, x, gains, Hc, dx, dhp, dap, W, tw, grid, st); break;
+        case 14: backward_m<8192>(B, Q, b, g, x, gains, Hc, dx, dhp, dap, W, tw, grid, st); break;
         default: break;
     }
 }

@@ -13,7 +13,8 @@
 // shared memory.
 //
 // Twiddles come from tables built on the host in FP64 and rounded once to
-// FP32 (no fast-math intrinsics).  The inverse transform is computed as
+// FP32 (no fast-math intrinsics); the tables may sit in global or (copied
+// once per CTA) shared memory.  The inverse transform is computed as
 // conj(FFT(conj(.))) so one code path serves both directions.
 #pragma once
 #include <cuda_runtime.h>
@@ -137,21 +138,61 @@ constexpr int kE = 16;
 __device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int padded_len(int M) { return M + (M >> 4); }
 
+template <int R>
+struct Log2R { static constexpr int v = (R == 2) ? 1 : (R == 4) ? 2 : (R == 8) ? 3 : 4; };
+
 template <int M>
 struct FftPlan {
     static constexpr int T = M / kE;
     // radix of the last pass; the others are 16
     static constexpr int R_LAST = (M == 1024) ? 4 : (M == 2048) ? 8 : (M == 4096) ? 16 : 2;
     static constexpr int NPASS = (M == 8192) ? 4 : 3;
-    // twiddle table layout: pass p (p >= 1) has LP*R entries at offset OFF_p,
-    // entry [m * LP + k] = exp(-2 pi i m k / (LP R)); then the split table
-    static constexpr int R2 = (M == 8192) ? 16 : R_LAST;   // radix of pass 2
+    // Twiddle table: pass p (p >= 1, radix R, LP = product of the earlier
+    // radices) stores log2(R) rows of LP entries, row j holding
+    // w^(2^j) = exp(-2 pi i 2^j k / (LP R)) for k < LP; the other powers are
+    // products of at most four of these.  Then the split table
+    // exp(-2 pi i k / (2M)), k <= M/2.
+    static constexpr int R2 = (M == 8192) ? 16 : R_LAST;    // radix of pass 2
     static constexpr int OFF1 = 0;                          // LP = 16, R = 16
-    static constexpr int OFF2 = OFF1 + 16 * 16;             // LP = 256, R = R2
-    static constexpr int OFF3 = OFF2 + 256 * R2;            // LP = 4096, R = 2 (M = 8192)
-    static constexpr int OFF_SPLIT = (M == 8192) ? OFF3 + 4096 * 2 : OFF3;
-    static constexpr int TW_LEN = OFF_SPLIT + M / 2 + 1;    // split: exp(-2 pi i k / (2M))
+    static constexpr int OFF2 = OFF1 + 16 * 4;              // LP = 256, R = R2
+    static constexpr int OFF3 = OFF2 + 256 * Log2R<R2>::v;  // LP = 4096, R = 2 (M = 8192)
+    static constexpr int OFF_SPLIT = (M == 8192) ? OFF3 + 4096 : OFF3;
+    static constexpr int TW_LEN = OFF_SPLIT + M / 2 + 1;
 };
+
+// u[m] *= w^m, m = 1 .. R-1, from the power rows of a pass table
+template <int R>
+__device__ __forceinline__ void apply_twiddles(float2 (&u)[R], const float2* __restrict__ tab, int LP, int k) {
+    const float2 w1 = tab[k];
+    if constexpr (R == 2) {
+        u[1] = cmul(u[1], w1);
+    } else {
+        const float2 w2 = tab[LP + k];
+        const float2 w3 = cmul(w1, w2);
+        u[1] = cmul(u[1], w1);
+        u[2] = cmul(u[2], w2);
+        u[3] = cmul(u[3], w3);
+        if constexpr (R >= 8) {
+            const float2 w4 = tab[2 * LP + k];
+            u[4] = cmul(u[4], w4);
+            u[5] = cmul(u[5], cmul(w4, w1));
+            u[6] = cmul(u[6], cmul(w4, w2));
+            const float2 w7 = cmul(w4, w3);
+            u[7] = cmul(u[7], w7);
+            if constexpr (R == 16) {
+                const float2 w8 = tab[3 * LP + k];
+                u[8] = cmul(u[8], w8);
+                u[9] = cmul(u[9], cmul(w8, w1));
+                u[10] = cmul(u[10], cmul(w8, w2));
+                u[11] = cmul(u[11], cmul(w8, w3));
+                u[12] = cmul(u[12], cmul(w8, w4));
+                u[13] = cmul(u[13], cmul(w8, cmul(w4, w1)));
+                u[14] = cmul(u[14], cmul(w8, cmul(w4, w2)));
+                u[15] = cmul(u[15], cmul(w8, w7));
+            }
+        }
+    }
+}
 
 // One Stockham pass of radix R with LP = product of the earlier radices.
 // Input: v in strided layout.  If LAST, the output stays in v (strided);
@@ -168,10 +209,7 @@ __device__ __forceinline__ void fft_pass(float2 (&v)[kE], float2* __restrict__ s
         for (int m = 0; m < R; ++m) u[m] = v[q + m * NB];
         const int i = t + q * T;
         const int k = i & (LP - 1);
-        if constexpr (LP > 1) {
-#pragma unroll
-            for (int m = 1; m < R; ++m) u[m] = cmul(u[m], __ldg(&tw[m * LP + k]));
-        }
+        if constexpr (LP > 1) apply_twiddles<R>(u, tw, LP, k);
         dft<R>(u);
         if constexpr (LAST) {
 #pragma unroll
@@ -248,60 +286,147 @@ __device__ __forceinline__ void load_real_strided(float2 (&v)[kE], const float* 
 // Thread 0, s = 0 owns slot 0 -- (X[0], X[M]) packed as one float2 (both are
 // real) -- in P[0], and the self-mirrored bin M/2 in P[1].
 
-// Split: from Z = FFT_M(z) in shared memory (natural order, padded) to the
-// true half spectrum X of the real 2M-point signal, in pair layout.
+// Split of one pair: from Z = FFT_M(z) in shared memory (natural order,
+// padded) to the true half spectrum of the real 2M-point signal:
+// xa = X[k], xb = X[M-k]; for k = 0, xa = (X[0], X[M]) and xb = X[M/2].
 // wsplit[k] = exp(-2 pi i k / (2M)).
+template <int M>
+__device__ __forceinline__ void split_pair(const float2* __restrict__ sm, const float2* __restrict__ wsplit,
+                                           int k, float2& xa, float2& xb) {
+    if (k == 0) {
+        const float2 z0 = sm[pad(0)];
+        const float2 zh = sm[pad(M / 2)];
+        xa = make_float2(z0.x + z0.y, z0.x - z0.y);
+        xb = conjf2(zh);
+    } else {
+        const float2 zk = sm[pad(k)];
+        const float2 zm = conjf2(sm[pad(M - k)]);
+        const float2 E = cscale(cadd(zk, zm), 0.5f);
+        const float2 O = cscale(mul_mi(csub(zk, zm)), 0.5f);   // (zk - zm) / (2i)
+        const float2 wO = cmul(wsplit[k], O);
+        xa = cadd(E, wO);
+        xb = conjf2(csub(E, wO));
+    }
+}
+
+// Split into pair layout registers P[2s] = X[k_s], P[2s+1] = X[M-k_s].
 template <int M>
 __device__ __forceinline__ void split_forward(float2 (&P)[kE], const float2* __restrict__ sm,
                                               const float2* __restrict__ wsplit, int t) {
     constexpr int T = M / kE;
 #pragma unroll
-    for (int s = 0; s < kE / 2; ++s) {
-        const int k = t + s * T;
-        if (k == 0) {
-            float2 z0 = sm[pad(0)];
-            float2 zh = sm[pad(M / 2)];
-            P[0] = make_float2(z0.x + z0.y, z0.x - z0.y);   // (X[0], X[M])
-            P[1] = conjf2(zh);                               // X[M/2]
-        } else {
-            float2 zk = sm[pad(k)];
-            float2 zm = conjf2(sm[pad(M - k)]);
-            float2 E = cscale(cadd(zk, zm), 0.5f);
-            float2 O = cscale(mul_mi(csub(zk, zm)), 0.5f);   // (zk - zm) / (2i)
-            float2 wO = cmul(__ldg(&wsplit[k]), O);
-            P[2 * s] = cadd(E, wO);                          // X[k]
-            P[2 * s + 1] = conjf2(csub(E, wO));              // X[M-k]
-        }
+    for (int s = 0; s < kE / 2; ++s) split_pair<M>(sm, wsplit, t + s * T, P[2 * s], P[2 * s + 1]);
+}
+
+// Inverse pre-processing of one pair: from ya = Y[k], yb = Y[M-k] (for k = 0:
+// (Y[0], Y[M]) and Y[M/2]) of a half spectrum to conj(Z') in shared memory,
+// where Z' = 2 FFT_M(z) of the signal y = IDFT_{2M}(Y) * 2M.  Running
+// fft_core on it and conjugating gives z[n] = y[2n] + i y[2n+1] scaled by
+// 2M (unnormalised inverse).
+template <int M>
+__device__ __forceinline__ void unsplit_pair(float2* __restrict__ sm, const float2* __restrict__ wsplit,
+                                             int k, float2 ya, float2 yb) {
+    if (k == 0) {
+        sm[pad(0)] = conjf2(make_float2(ya.x + ya.y, ya.x - ya.y));
+        sm[pad(M / 2)] = cscale(yb, 2.f);                  // conj(2 conj(Y[M/2]))
+    } else {
+        const float2 ym = conjf2(yb);
+        const float2 E = cadd(ya, ym);
+        const float2 D = csub(ya, ym);
+        const float2 O = cmulc(wsplit[k], D);               // D * conj(w^k)
+        const float2 zk = cadd(E, mul_pi(O));               // E + i O
+        const float2 zm = cadd(conjf2(E), mul_pi(conjf2(O)));
+        sm[pad(k)] = conjf2(zk);
+        sm[pad(M - k)] = conjf2(zm);
     }
 }
 
-// Inverse pre-processing: from a half spectrum Y in pair layout to
-// conj(Z') in shared memory (natural order), where Z' = 2 FFT_M(z) of the
-// signal y = IDFT_{2M}(Y) * 2M.  Running fft_core on it and conjugating gives
-// z[n] = y[2n] + i y[2n+1] scaled by 2M (unnormalised inverse).
 template <int M>
 __device__ __forceinline__ void split_inverse_store(const float2 (&P)[kE], float2* __restrict__ sm,
                                                     const float2* __restrict__ wsplit, int t) {
     constexpr int T = M / kE;
 #pragma unroll
-    for (int s = 0; s < kE / 2; ++s) {
-        const int k = t + s * T;
-        if (k == 0) {
-            float2 y = P[0];                                 // (Y[0], Y[M])
-            float2 z0 = make_float2(y.x + y.y, y.x - y.y);
-            sm[pad(0)] = conjf2(z0);
-            sm[pad(M / 2)] = cscale(P[1], 2.f);              // conj(2 conj(Y[M/2]))
-        } else {
-            float2 yk = P[2 * s], ym = conjf2(P[2 * s + 1]);
-            float2 E = cadd(yk, ym);
-            float2 D = csub(yk, ym);
-            float2 O = cmulc(__ldg(&wsplit[k]), D);          // D * conj(w^k)
-            float2 zk = cadd(E, mul_pi(O));                  // E + i O
-            float2 zm = cadd(conjf2(E), mul_pi(conjf2(O)));  // conj(E) + i conj(O)
-            sm[pad(k)] = conjf2(zk);
-            sm[pad(M - k)] = conjf2(zm);
-        }
+    for (int s = 0; s < kE / 2; ++s) unsplit_pair<M>(sm, wsplit, t + s * T, P[2 * s], P[2 * s + 1]);
+}
+
+// ---------------------------------------------------------------------------
+// asynchronous global -> shared copies (cp.async, completion by groups)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// 4 bytes, zero-filled when !valid (no global read then)
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_addr(dst)), "l"(src),
+                 "r"(valid ? 4 : 0));
+}
+// 16 bytes; both addresses 16-byte aligned
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Queues the copy of the real block src[0, len) into stage[0, 2M), zeros
+// beyond len.  Thread t copies elements t + k*T (coalesced).
+template <int M>
+__device__ __forceinline__ void stage_real_async(float* __restrict__ stage, const float* __restrict__ src,
+                                                 int64_t len, int t) {
+    constexpr int T = M / kE;
+#pragma unroll 8
+    for (int k = 0; k < 2 * kE; ++k) {
+        const int n = t + k * T;
+        const bool ok = n < len;
+        cp_async4(stage + n, ok ? src + n : src, ok);
     }
+}
+
+// z[n] = (stage[2n], stage[2n+1]) for the strided indices of thread t
+template <int M>
+__device__ __forceinline__ void load_staged_strided(float2 (&v)[kE], const float* __restrict__ stage, int t) {
+    constexpr int T = M / kE;
+    const float2* s2 = reinterpret_cast<const float2*>(stage);
+#pragma unroll
+    for (int s = 0; s < kE; ++s) v[s] = s2[t + s * T];
+}
+
+// Forward FFT of a real segment src[0, len) zero-padded to 2M: leaves
+// Z = FFT_M(z) in shared memory, natural order; read pairs with split_pair.
+template <int M>
+__device__ __forceinline__ void rfft_to_smem(const float* __restrict__ src, int64_t len,
+                                             float2* __restrict__ sm, const float2* __restrict__ tw, int t) {
+    float2 v[kE];
+    load_real_strided<M>(v, src, len, t);
+    fft_core<M>(v, sm, tw, t);
+    __syncthreads();                 // everyone done with the last pass loads
+    store_strided<M>(v, sm, t);
+    __syncthreads();
+}
+
+// Forward FFT of a staged real block (stage[0, 2M) in shared memory):
+// leaves Z = FFT_M(z) in sm, natural order.  The caller must have completed
+// the copy into stage and synchronised.
+template <int M>
+__device__ __forceinline__ void rfft_staged_to_smem(const float* __restrict__ stage, float2* __restrict__ sm,
+                                                    const float2* __restrict__ tw, int t) {
+    float2 v[kE];
+    load_staged_strided<M>(v, stage, t);
+    fft_core<M>(v, sm, tw, t);
+    __syncthreads();
+    store_strided<M>(v, sm, t);
+    __syncthreads();
+}
+
+// Inverse real FFT after the caller has written conj(Z') to sm with
+// unsplit_pair (and synchronised): v[s] = (y[2n], y[2n+1]) * 2M, n = t + s*T.
+template <int M>
+__device__ __forceinline__ void irfft_from_smem(float2 (&v)[kE], float2* __restrict__ sm,
+                                                const float2* __restrict__ tw, int t) {
+    load_strided<M>(v, sm, t);
+    fft_core<M>(v, sm, tw, t);
+#pragma unroll
+    for (int s = 0; s < kE; ++s) v[s] = conjf2(v[s]);
 }
 
 // Forward real FFT of src[0, len) zero-padded to 2M, into pair layout P.

@@ -56,25 +56,55 @@ k_spectrum(DevBatch B, Queues Q, int bucket, const float* __restrict__ rir, floa
 // ---------------------------------------------------------------------------
 // For each block b of the tile's segment (hop = N - L_max + 1):
 //   X_i = rFFT_N(x_i[b hop, b hop + hop))                 for every source i
-//   Y_j = sum_i alpha_i Hc_ij X_i                          in registers
+//   Y_j = sum_i alpha_i Hc_ij X_i                          split fused with the
+//                                                          MAC, Y_j in registers
 //   y_j block = irFFT_N(Y_j); the first hop samples plus the carried tail of
 //   block b-1 are stored, the last L_max - 1 samples are carried to b+1.
-// The tail leaving the segment's last block is written to `tails`; the tile
-// holding the next segment stored its first block without it, and k_fixup
-// adds it afterwards (one FP32 add, the same one done in-tile, so results do
-// not depend on the segmentation).  Microphones are processed in groups of
-// kJG; the source spectra are recomputed per group.
+// Global reads are prefetched with cp.async one step ahead so no transform
+// waits on memory: the next source's x block lands in a shared-memory stage
+// while the current one is transformed, and the next source's RIR spectra
+// while the current MAC finishes and the next transform runs.  Twiddles are
+// copied to shared memory once per CTA.  The tail leaving the segment's last
+// block goes to `tails`; the tile of the next segment stored its first block
+// without it and k_fixup adds it afterwards (one FP32 add, the same one done
+// in-tile, so results do not depend on the segmentation).  Microphones are
+// processed in groups of kJG; source spectra are recomputed per group.
 template <int M>
-__global__ void __launch_bounds__(M / kE)
+struct FwdSmem {
+    static constexpr bool kStageH = M <= 4096;   // RIR spectra staged in shared memory
+    static constexpr bool kTwSmem = M <= 4096;   // twiddle tables in shared memory
+    static constexpr size_t a16(size_t v) { return (v + 15) / 16 * 16; }
+    static constexpr size_t o_sm = 0;
+    static constexpr size_t o_xs = a16(o_sm + sizeof(float2) * padded_len(M));
+    static constexpr size_t o_hs = a16(o_xs + sizeof(float) * 2 * M);
+    static constexpr size_t o_tl = a16(o_hs + (kStageH ? sizeof(float2) * kJG * M : 0));
+    static constexpr size_t o_tw = a16(o_tl + sizeof(float) * kJG * M);
+    static constexpr size_t bytes = a16(o_tw + (kTwSmem ? sizeof(float2) * FftPlan<M>::TW_LEN : 0));
+};
+
+template <int M>
+__global__ void __launch_bounds__(M / kE, 1)
 k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
           const float* __restrict__ gains, const float2* __restrict__ Hc, float* __restrict__ y,
-          float* __restrict__ tails, const float2* __restrict__ tw) {
+          float* __restrict__ tails, const float2* __restrict__ twg) {
+    using Pl = FftPlan<M>;
+    using L = FwdSmem<M>;
     constexpr int T = M / kE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* sm = reinterpret_cast<float2*>(smem_raw);
-    float (*tl)[M] = reinterpret_cast<float (*)[M]>(smem_raw + sizeof(float2) * padded_len(M));
+    float2* sm = reinterpret_cast<float2*>(smem_raw + L::o_sm);
+    float* xs = reinterpret_cast<float*>(smem_raw + L::o_xs);
+    float2* hs = reinterpret_cast<float2*>(smem_raw + L::o_hs);
+    float (*tl)[M] = reinterpret_cast<float (*)[M]>(smem_raw + L::o_tl);
     __shared__ int slot;
     const int t = threadIdx.x;
+    const float2* tw = twg;
+    if constexpr (L::kTwSmem) {
+        float2* tws = reinterpret_cast<float2*>(smem_raw + L::o_tw);
+        for (int k = t; k < Pl::TW_LEN; k += T) tws[k] = twg[k];
+        __syncthreads();
+        tw = tws;
+    }
+    const float2* wsplit = tw + Pl::OFF_SPLIT;
     for (;;) {
         const int g = pop_job(Q, kListFwd, bucket, &slot);
         if (g < 0) break;
@@ -90,45 +120,87 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
         const int sb = B.src0[u], rb = B.rir0[u];
         for (int j0 = 0; j0 < J; j0 += kJG) {
             const int jn = min(kJG, J - j0);
-            __syncthreads();
+            // queue the copies of source i's block b and of its spectra
+            auto stage_x = [&](int64_t b, int i) {
+                const int64_t p = b * hop;
+                stage_real_async<M>(xs, x + B.xoff[sb + i] + p, min((int64_t)hop, nx - p), t);
+            };
+            auto stage_h = [&](int i) {
+                if constexpr (L::kStageH) {
+                    for (int jj = 0; jj < jn; ++jj) {
+                        const float2* H = Hc + (int64_t)(rb + i * J + j0 + jj) * B.MMAX;
+#pragma unroll
+                        for (int k = 0; k < M / 2 / T; ++k) {
+                            const int c = t + k * T;
+                            cp_async16(hs + jj * M + 2 * c, H + 2 * c);
+                        }
+                    }
+                }
+            };
+            __syncthreads();                     // stages and tails are free
             for (int jj = 0; jj < jn; ++jj)
                 for (int n = t; n < tail_len; n += T) tl[jj][n] = 0.f;
+            stage_x(b0, 0);
+            cp_async_commit();
+            stage_h(0);
+            cp_async_commit();
             for (int64_t b = b0; b < b1; ++b) {
                 const int64_t pos = b * hop;
-                const int64_t len = min((int64_t)hop, nx - pos);
                 float2 Y[kJG][kE];
 #pragma unroll
                 for (int jj = 0; jj < kJG; ++jj)
 #pragma unroll
                     for (int e = 0; e < kE; ++e) Y[jj][e] = make_float2(0.f, 0.f);
                 for (int i = 0; i < I; ++i) {
-                    float2 P[kE];
-                    rfft_pairs<M>(P, x + B.xoff[sb + i] + pos, len, sm, tw, t);
+                    // x_i is in (only the newest group, H_i, may still be pending)
+                    cp_async_wait<1>();
+                    __syncthreads();
+                    float2 v[kE];
+                    load_staged_strided<M>(v, xs, t);
+                    __syncthreads();             // xs fully read: reuse it
+                    if (i + 1 < I) stage_x(b, i + 1);
+                    else if (b + 1 < b1) stage_x(b + 1, 0);
+                    cp_async_commit();
+                    fft_core<M>(v, sm, tw, t);
+                    __syncthreads();
+                    store_strided<M>(v, sm, t);
+                    cp_async_wait<1>();          // H_i is in
+                    __syncthreads();
                     const float a = __ldg(gains + sb + i);
+                    const float2* H0 = Hc + (int64_t)(rb + i * J + j0) * B.MMAX;
 #pragma unroll
-                    for (int jj = 0; jj < kJG; ++jj) {
-                        if (jj >= jn) break;
-                        const float2* H = Hc + (int64_t)(rb + i * J + j0 + jj) * B.MMAX;
+                    for (int q = 0; q < kE / 2; ++q) {
+                        const int k = t + q * T;
+                        float2 xa, xb;
+                        split_pair<M>(sm, wsplit, k, xa, xb);
+                        xa = cscale(xa, a);
+                        xb = cscale(xb, a);
+                        const int kb = (k == 0) ? M / 2 : M - k;
 #pragma unroll
-                        for (int q = 0; q < kE / 2; ++q) {
-                            const int k = t + q * T;
-                            if (k == 0) {
-                                const float2 h0 = __ldg(H), hh = __ldg(H + M / 2);
-                                Y[jj][0].x += a * P[0].x * h0.x;
-                                Y[jj][0].y += a * P[0].y * h0.y;
-                                const float2 p = cmul(P[1], hh);
-                                Y[jj][1].x += a * p.x;
-                                Y[jj][1].y += a * p.y;
+                        for (int jj = 0; jj < kJG; ++jj) {
+                            if (jj >= jn) break;
+                            float2 ha, hb;
+                            if constexpr (L::kStageH) {
+                                ha = hs[jj * M + k];
+                                hb = hs[jj * M + kb];
                             } else {
-                                const float2 p0 = cmul(P[2 * q], __ldg(H + k));
-                                const float2 p1 = cmul(P[2 * q + 1], __ldg(H + M - k));
-                                Y[jj][2 * q].x += a * p0.x;
-                                Y[jj][2 * q].y += a * p0.y;
-                                Y[jj][2 * q + 1].x += a * p1.x;
-                                Y[jj][2 * q + 1].y += a * p1.y;
+                                const float2* H = H0 + (int64_t)jj * B.MMAX;
+                                ha = __ldg(H + k);
+                                hb = __ldg(H + kb);
                             }
+                            if (k == 0) {            // slot 0 holds two real bins
+                                Y[jj][0].x += xa.x * ha.x;
+                                Y[jj][0].y += xa.y * ha.y;
+                            } else {
+                                Y[jj][2 * q] = cadd(Y[jj][2 * q], cmul(xa, ha));
+                            }
+                            Y[jj][2 * q + 1] = cadd(Y[jj][2 * q + 1], cmul(xb, hb));
                         }
                     }
+                    __syncthreads();             // hs fully read: reuse it
+                    if (i + 1 < I) stage_h(i + 1);
+                    else if (b + 1 < b1 && I > 1) stage_h(0);
+                    cp_async_commit();
                 }
 #pragma unroll
                 for (int jj = 0; jj < kJG; ++jj) {
@@ -163,6 +235,7 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
             }
         }
     }
+    cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
@@ -196,7 +269,7 @@ k_fixup(DevBatch B, float* __restrict__ y, const float* __restrict__ tails) {
 template <int M>
 constexpr int smem_spectrum() { return (int)sizeof(float2) * padded_len(M); }
 template <int M>
-constexpr int smem_forward() { return (int)sizeof(float2) * padded_len(M) + (int)sizeof(float) * kJG * M; }
+constexpr int smem_forward() { return (int)FwdSmem<M>::bytes; }
 
 template <int M>
 static void spectrum_m(const DevBatch& B, const Queues& Q, int bucket, const float* rir,

@@ -26,8 +26,7 @@ enum : int { kListFwd = 0, kListBwd = 1, kListSpec = 2, kNumLists = 3 };
 // Batch description and per-call state on the device.  Utterance u has
 // n_src[u] sources (source 0 is the target) and J microphones.  The forward
 // cuts it into ceil(n_x / seg_len) segments and the backward into
-// ceil(n_x / bseg_len) segments; a segment is one tile of work (a backward
-// tile is a segment and one source).
+// ceil(n_x / bseg_len) segments; a segment is one tile of work.
 struct DevBatch {
     int32_t U, J, S, R, IMAX;
     int32_t NSEG;            // total segments
@@ -94,9 +93,10 @@ void launch_forward(int logN, const DevBatch& B, const Queues& Q, const float* x
                     const float2* Hc, float* y, float* tails, const float2* tw, int grid,
                     cudaStream_t st);
 void launch_fixup(const DevBatch& B, float* y, const float* tails, cudaStream_t st);
+// W: per-CTA dh accumulators, grid * IMAX * J * (N/2) complex
 void launch_backward(int logN, const DevBatch& B, const Queues& Q, const float* g, const float* x,
                      const float* gains, const float2* Hc, float* dx, float* dhp, float* dap,
-                     const float2* tw, int grid, cudaStream_t st);
+                     float2* W, const float2* tw, int grid, cudaStream_t st);
 void launch_finalize(const DevBatch& B, const float* gains, const float* dhp, const float* dap,
                      float* grad_rir, float* grad_gains, cudaStream_t st);
 

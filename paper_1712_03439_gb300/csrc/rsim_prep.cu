@@ -161,7 +161,7 @@ void launch_power(const DevBatch& B, const float* x, int grid, cudaStream_t st) 
 // table; N must satisfy L_max - 1 <= hop so an output block's tail only
 // reaches into the next block.  Then per FFT size it writes the lists of
 // spectrum jobs (RIRs), forward tiles (segments) and backward tiles
-// (segment, source), in utterance order, and resets the queue cursors.
+// (backward segments), in utterance order, and resets the queue cursors.
 constexpr int kPlanThreads = 1024;
 
 __device__ __forceinline__ int block_exscan(int v, int* sm, int* total) {
@@ -258,7 +258,7 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
         for (int u = u0; u < u1; ++u) {
             if (B.logN[u] != m) continue;
             cf += B.seg0[u + 1] - B.seg0[u];
-            cb += (B.bseg0[u + 1] - B.bseg0[u]) * B.n_src[u];
+            cb += B.bseg0[u + 1] - B.bseg0[u];
             cs += B.rir0[u + 1] - B.rir0[u];
         }
         int tf, tb, ts;
@@ -271,8 +271,7 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
         for (int u = u0; u < u1; ++u) {
             if (B.logN[u] != m) continue;
             for (int g = B.seg0[u]; g < B.seg0[u + 1]; ++g) lf[of++] = g;
-            for (int g = B.bseg0[u]; g < B.bseg0[u + 1]; ++g)
-                for (int i = 0; i < B.n_src[u]; ++i) lb[ob++] = g * kMaxSources + i;
+            for (int g = B.bseg0[u]; g < B.bseg0[u + 1]; ++g) lb[ob++] = g;
             for (int r = B.rir0[u]; r < B.rir0[u + 1]; ++r) ls[os++] = r;
         }
         if (t == 0) {
