@@ -47,29 +47,31 @@ float2 twiddle(int64_t num, int64_t den) {
     return make_float2((float)std::cos(ang), (float)std::sin(ang));
 }
 
-template <int M>
+template <int M, int E>
 std::vector<float2> twiddle_table() {
-    using P = FftPlan<M>;
+    using P = FftPlan<M, E>;
     std::vector<float2> tw(P::TW_LEN);
-    // pass 1: LP = 16, R = 16; rows w^(2^j), j < 4
-    for (int j = 0; j < 4; ++j)
-        for (int k = 0; k < 16; ++k) tw[P::OFF1 + j * 16 + k] = twiddle((int64_t)(1 << j) * k, 256);
-    // pass 2: LP = 256, R = R2
-    for (int j = 0; j < Log2R<P::R2>::v; ++j)
-        for (int k = 0; k < 256; ++k) tw[P::OFF2 + j * 256 + k] = twiddle((int64_t)(1 << j) * k, 256 * P::R2);
-    // pass 3 (M = 8192): LP = 4096, R = 2
-    if (M == 8192)
-        for (int k = 0; k < 4096; ++k) tw[P::OFF3 + k] = twiddle(k, 8192);
+    // pass p >= 1: rows w^(2^j), j < log2(radix), of lp(p) entries each
+    for (int p = 1; p < P::NPASS; ++p) {
+        const int R = P::radix(p), LP = P::lp(p);
+        for (int j = 0; j < ilog2(R); ++j)
+            for (int k = 0; k < LP; ++k)
+                tw[P::tw_off(p) + j * LP + k] = twiddle((int64_t)(1 << j) * k, (int64_t)LP * R);
+    }
     for (int k = 0; k <= M / 2; ++k) tw[P::OFF_SPLIT + k] = twiddle(k, 2 * M);
     return tw;
 }
 
-std::vector<float2> twiddle_table_for(int logN) {
-    switch (logN) {
-        case 11: return twiddle_table<1024>();
-        case 12: return twiddle_table<2048>();
-        case 13: return twiddle_table<4096>();
-        case 14: return twiddle_table<8192>();
+std::vector<float2> twiddle_table_for(int logN, int E) {
+    switch (logN * 100 + E) {
+        case 1108: return twiddle_table<1024, 8>();
+        case 1116: return twiddle_table<1024, 16>();
+        case 1208: return twiddle_table<2048, 8>();
+        case 1216: return twiddle_table<2048, 16>();
+        case 1308: return twiddle_table<4096, 8>();
+        case 1316: return twiddle_table<4096, 16>();
+        case 1408: return twiddle_table<8192, 8>();
+        case 1416: return twiddle_table<8192, 16>();
     }
     return {};
 }
@@ -99,8 +101,9 @@ struct rsim_plan_s {
     float* tails = nullptr;
     float* dhp = nullptr;
     float* dap = nullptr;
-    float2* Wb[kNumBuckets] = {};   // per-CTA backward accumulators of each FFT size
-    float2* tw[kNumBuckets] = {};
+    Twiddles tw[kNumBuckets] = {};
+    float2* Gc[kNumBuckets] = {};   // backward mic-spectrum cache per FFT size
+    int gc_blocks[kNumBuckets] = {};
     int grid_trunc = 1, grid_pow = 1;
     int grid_spec[kNumBuckets] = {}, grid_fwd[kNumBuckets] = {}, grid_bwd[kNumBuckets] = {};
     bool fwd_done = false;
@@ -277,7 +280,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     void *p_nsrc, *p_nx, *p_src0, *p_rir0, *p_seg0, *p_segutt, *p_xoff, *p_yoff, *p_roff, *p_rlen,
         *p_dhpoff, *p_tuning, *p_L, *p_logN, *p_hop, *p_lmax, *p_nblk, *p_pow, *p_err, *p_list,
         *p_count, *p_next, *p_Hc, *p_tails, *p_dhp, *p_dap;
-    void* p_tw[kNumBuckets] = {};
+    void* p_tw[2 * kNumBuckets] = {};
     const int64_t cap = std::max<int64_t>(std::max<int64_t>(nbseg, nseg), R);
     // launch shapes (persistent grids) decide the per-CTA backward scratch
     int sms = 0;
@@ -323,16 +326,24 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     pieces.push_back({&p_tails, sizeof(float) * nseg * J * MMAX});
     pieces.push_back({&p_dhp, sizeof(float) * std::max<int64_t>(dhp_total, 1)});
     pieces.push_back({&p_dap, sizeof(float) * std::max<int64_t>(nbseg, 1) * kMaxSources});
-    void* p_W[kNumBuckets] = {};
-    for (int m = kMinLog; m <= kMaxLog; ++m)
-        if ((mask >> m) & 1)
-            pieces.push_back({&p_W[m - kMinLog], sizeof(float2) * (size_t)grid_bwd[m - kMinLog] * imax * J *
-                                                     ((size_t)1 << (m - 1))});
-    std::vector<std::vector<float2>> tws(kNumBuckets);
+    // backward G cache: a segment holds at most ceil(bseg_len / (N/2)) + 1 block starts (hop >= N/2)
+    void* p_Gc[kNumBuckets] = {};
+    int gc_blocks[kNumBuckets] = {};
     for (int m = kMinLog; m <= kMaxLog; ++m) {
         if (!((mask >> m) & 1)) continue;
-        tws[m - kMinLog] = twiddle_table_for(m);
-        pieces.push_back({&p_tw[m - kMinLog], sizeof(float2) * tws[m - kMinLog].size()});
+        const int b = m - kMinLog;
+        const int64_t half = (int64_t)1 << (m - 1);
+        gc_blocks[b] = (int)((bseg_len + half - 1) / half + 1);
+        pieces.push_back({&p_Gc[b], sizeof(float2) * (size_t)grid_bwd[b] * gc_blocks[b] * kJG * half});
+    }
+    std::vector<std::vector<float2>> tws(2 * kNumBuckets);
+    for (int m = kMinLog; m <= kMaxLog; ++m) {
+        if (!((mask >> m) & 1)) continue;
+        for (int e = 0; e < 2; ++e) {
+            const int k = 2 * (m - kMinLog) + e;
+            tws[k] = twiddle_table_for(m, e ? 16 : 8);
+            pieces.push_back({&p_tw[k], sizeof(float2) * tws[k].size()});
+        }
     }
     size_t total = 0;
     for (auto& pc : pieces) total = align_up(total, 256) + pc.bytes;
@@ -374,8 +385,8 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
         {p_dhpoff, dhp_off.data(), sizeof(int64_t) * (nbseg + 1)},
         {p_tuning, tuning.data(), sizeof(float) * 32},
     };
-    for (int b = 0; b < kNumBuckets; ++b)
-        if (p_tw[b]) ups.push_back({p_tw[b], tws[b].data(), sizeof(float2) * tws[b].size()});
+    for (int k = 0; k < 2 * kNumBuckets; ++k)
+        if (p_tw[k]) ups.push_back({p_tw[k], tws[k].data(), sizeof(float2) * tws[k].size()});
     for (auto& up : ups) {
         if (up.bytes == 0) continue;
         e = cudaMemcpy(up.dst, up.src, up.bytes, cudaMemcpyHostToDevice);
@@ -410,8 +421,9 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     p->Q.cap = (int32_t)cap;
     p->Hc = (float2*)p_Hc; p->tails = (float*)p_tails; p->dhp = (float*)p_dhp; p->dap = (float*)p_dap;
     for (int b = 0; b < kNumBuckets; ++b) {
-        p->tw[b] = (float2*)p_tw[b];
-        p->Wb[b] = (float2*)p_W[b];
+        p->tw[b] = Twiddles{(const float2*)p_tw[2 * b], (const float2*)p_tw[2 * b + 1]};
+        p->Gc[b] = (float2*)p_Gc[b];
+        p->gc_blocks[b] = gc_blocks[b];
         p->grid_spec[b] = grid_spec[b];
         p->grid_fwd[b] = grid_fwd[b];
         p->grid_bwd[b] = grid_bwd[b];
@@ -498,8 +510,8 @@ extern "C" rsim_status rsim_filter_mix_backward(rsim_plan_t p, void* stream, con
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (queue)");
     stage_mark(p, 6, false, st);
     fan_out(p, st, [&](int m, cudaStream_t s) {
-        launch_backward(m, B, p->Q, grad_y, x, gains, p->Hc, grad_x, p->dhp, p->dap, p->Wb[m - kMinLog],
-                        p->tw[m - kMinLog], p->grid_bwd[m - kMinLog], s);
+        launch_backward(m, B, p->Q, grad_y, x, gains, p->Hc, grad_x, p->dhp, p->dap, p->Gc[m - kMinLog],
+                        p->gc_blocks[m - kMinLog], p->tw[m - kMinLog], p->grid_bwd[m - kMinLog], s);
     });
     stage_mark(p, 6, true, st);
     stage_mark(p, 7, false, st);

@@ -43,115 +43,196 @@ __device__ __forceinline__ double block_sum_d(double v, double* sd) {
 // ---------------------------------------------------------------------------
 // K7: persistent over backward segments (all sources of a segment per tile)
 // ---------------------------------------------------------------------------
-// Per block b of the segment:
-//   G_j = rFFT_N(g_j[b hop, b hop + hop + L_max - 1))    once per mic, kept in
-//                                                         shared memory (pair layout)
-//   for each source i:
-//     X_i = rFFT_N(x_i block)                             registers (pair layout)
-//     C_i = sum_j conj(Hc_ij) G_j                          registers
-//     W_ij += conj(X_i) G_j                                per-CTA scratch in L2
-//     c_i = irFFT_N(C_i)[0, hop): dx_i = alpha_i c_i, dalpha_i += <c_i, x_i>
-// so a block costs J + 2I transforms.  At the end of the segment
-// dh partial_ij = irFFT_N(W_ij)[0, L_ij).  Each thread owns the same bin pairs
-// in every split, product and pre-processing step, so its slots in G and W
-// are private: no conflicts, no barriers around them.  Microphones go in
-// groups of kJG (the source spectra are recomputed per group; dx of later
-// groups is added to the first group's).
+// Phase 1, per block b of the segment and mic j:
+//   G_jb = rFFT_N(g_j[b hop, b hop + hop + L_max - 1))    stored once in this
+//                                                          CTA's slice of Gc
+// Phase 2, per source i (W_j in registers for the whole segment):
+//   per block b:  X = rFFT_N(x_i block)
+//                 C = sum_j conj(Hc_ij) G_jb               folded straight into
+//                                                          the inverse pre-processing
+//                 W_j += conj(X) G_jb
+//                 c = irFFT_N(C)[0, hop): dx_i = alpha_i c, dalpha_i += <c, x_i>
+//   then dh partial_ij = irFFT_N(W_j)[0, L_ij).
+// A block costs J + 2I transforms.  Each thread owns the same bin pairs in
+// every split and product, so its slots of G are private; x and g blocks, the
+// source's RIR spectra and the block's G are staged with cp.async one step
+// ahead of their use.  Microphones go in groups of kJG (the source spectra
+// are recomputed per group; dx of later groups is added to the first
+// group's).
 template <int M>
-__global__ void __launch_bounds__(M / kE, (M <= 4096 ? 2 : 1))
+struct BwdCfg {
+    static constexpr int E = e_for(M);
+    static constexpr int T = M / E;
+    static constexpr bool kStage = M <= 4096;     // spectra and G staged in shared memory
+    static constexpr bool kTwSmem = M <= 4096;
+    static constexpr int kMinBlocks = M <= 2048 ? 2 : 1;
+    static constexpr size_t a16(size_t v) { return (v + 15) / 16 * 16; }
+    static constexpr size_t o_sm = 0;
+    static constexpr size_t o_xs = a16(o_sm + sizeof(float2) * padded_len(M));
+    static constexpr size_t o_hs = a16(o_xs + sizeof(float) * 2 * M);
+    static constexpr size_t o_gs = a16(o_hs + (kStage ? sizeof(float2) * kJG * M : 0));
+    static constexpr size_t o_tw = a16(o_gs + (kStage ? sizeof(float2) * kJG * M : 0));
+    static constexpr size_t bytes = a16(o_tw + (kTwSmem ? sizeof(float2) * FftPlan<M, E>::TW_LEN : 0));
+};
+
+template <int M>
+__global__ void __launch_bounds__(BwdCfg<M>::T, BwdCfg<M>::kMinBlocks)
 k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const float* __restrict__ x,
            const float* __restrict__ gains, const float2* __restrict__ Hc, float* __restrict__ dx,
-           float* __restrict__ dhp, float* __restrict__ dap, float2* __restrict__ Wg,
-           const float2* __restrict__ tw) {
-    using Pl = FftPlan<M>;
-    constexpr int T = M / kE;
+           float* __restrict__ dhp, float* __restrict__ dap, float2* __restrict__ Gc, int gc_blocks,
+           const float2* __restrict__ twg) {
+    using L = BwdCfg<M>;
+    constexpr int E = L::E;
+    constexpr int T = L::T;
+    using Pl = FftPlan<M, E>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* sm = reinterpret_cast<float2*>(smem_raw);
-    float2* Gs = reinterpret_cast<float2*>(smem_raw + sizeof(float2) * padded_len(M)) + threadIdx.x;
+    float2* sm = reinterpret_cast<float2*>(smem_raw + L::o_sm);
+    float* xs = reinterpret_cast<float*>(smem_raw + L::o_xs);
+    float2* hs = reinterpret_cast<float2*>(smem_raw + L::o_hs);
+    float2* gs = reinterpret_cast<float2*>(smem_raw + L::o_gs);
     __shared__ double sd[32];
     __shared__ double dsum[kMaxSources];
     __shared__ int slot;
     const int t = threadIdx.x;
+    const float2* tw = twg;
+    if constexpr (L::kTwSmem) {
+        float2* tws = reinterpret_cast<float2*>(smem_raw + L::o_tw);
+        for (int k = t; k < Pl::TW_LEN; k += T) tws[k] = twg[k];
+        __syncthreads();
+        tw = tws;
+    }
     const float2* wsplit = tw + Pl::OFF_SPLIT;
-    const int J = B.J;
-    // this CTA's accumulators: W_ij slot e of thread t at ((i J + j) M + e T + t)
-    float2* Wc = Wg + (int64_t)blockIdx.x * B.IMAX * J * M + t;
+    // this CTA's G slice: block bb, mic jj, slot e of thread t at ((bb kJG + jj) E + e) T + t
+    float2* Gcta = Gc + (int64_t)blockIdx.x * gc_blocks * kJG * M;
     for (;;) {
         const int g = pop_job_b(Q, kListBwd, bucket, &slot);
         if (g < 0) break;
         const int u = B.bseg_utt[g];
-        const int64_t s = g - B.bseg0[u];
+        const int64_t sgi = g - B.bseg0[u];
         const int64_t nx = B.n_x[u];
         const int hop = B.hop[u];
         const int lmax = B.Lmax[u];
         int64_t b0, b1;
-        segment_blocks(s, B.bseg_len, hop, B.nblk[u], &b0, &b1);
+        segment_blocks(sgi, B.bseg_len, hop, B.nblk[u], &b0, &b1);
         if (b0 >= b1) continue;
-        const int I = B.n_src[u];
+        const int J = B.J, I = B.n_src[u];
         const int sb = B.src0[u], rb = B.rir0[u];
         if (t < kMaxSources) dsum[t] = 0.0;
-        for (int ij = 0; ij < I * J; ++ij)
-#pragma unroll
-            for (int e = 0; e < kE; ++e) Wc[(int64_t)ij * M + e * T] = make_float2(0.f, 0.f);
+        auto stage_x = [&](int i, int64_t b) {
+            const int64_t p = b * hop;
+            stage_real_async<M, E>(xs, x + B.xoff[sb + i] + p, min((int64_t)hop, nx - p), t);
+        };
+        auto stage_g = [&](int64_t b, int j) {
+            const int64_t p = b * hop;
+            stage_real_async<M, E>(xs, gy + B.yoff[u] + (int64_t)j * nx + p,
+                                   min((int64_t)(hop + lmax - 1), nx - p), t);
+        };
+        auto gslot = [&](int64_t b, int jj) { return Gcta + ((b - b0) * kJG + jj) * (int64_t)M; };
         for (int j0 = 0; j0 < J; j0 += kJG) {
             const int jn = min(kJG, J - j0);
+            // ---- phase 1: mic spectra of every block of the segment
+            __syncthreads();                     // stages are free
+            stage_g(b0, j0);
+            cp_async_commit();
             for (int64_t b = b0; b < b1; ++b) {
-                const int64_t pos = b * hop;
-                const int64_t len = min((int64_t)hop, nx - pos);
-                const int64_t wlen = min((int64_t)(hop + lmax - 1), nx - pos);
-                const int64_t lim = nx - pos;
-                // mic spectra of this block
+                for (int jj = 0; jj < jn; ++jj) {
+                    cp_async_wait<0>();
+                    __syncthreads();
+                    float2 v[E];
+                    load_staged_strided<M, E>(v, xs, t);
+                    __syncthreads();
+                    if (jj + 1 < jn) stage_g(b, j0 + jj + 1);
+                    else if (b + 1 < b1) stage_g(b + 1, j0);
+                    else stage_x(0, b0);             // phase 2 starts with source 0, block b0
+                    cp_async_commit();
+                    rfft_regs_to_smem<M, E>(v, sm, tw, t);
+                    float2* G = gslot(b, jj) + t;
 #pragma unroll
-                for (int jj = 0; jj < kJG; ++jj) {
-                    if (jj >= jn) break;
-                    rfft_to_smem<M>(gy + B.yoff[u] + (int64_t)(j0 + jj) * nx + pos, wlen, sm, tw, t);
-#pragma unroll
-                    for (int q = 0; q < kE / 2; ++q)
-                        split_pair<M>(sm, wsplit, t + q * T, Gs[(jj * kE + 2 * q) * T],
-                                      Gs[(jj * kE + 2 * q + 1) * T]);
+                    for (int q = 0; q < E / 2; ++q)
+                        split_pair<M>(sm, wsplit, t + q * T, G[(2 * q) * T], G[(2 * q + 1) * T]);
                 }
-                for (int i = 0; i < I; ++i) {
-                    const float* xi = x + B.xoff[sb + i];
-                    float2 X[kE];
-                    rfft_to_smem<M>(xi + pos, len, sm, tw, t);
-                    split_forward<M>(X, sm, wsplit, t);
-                    float2 C[kE];
-#pragma unroll
-                    for (int e = 0; e < kE; ++e) C[e] = make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int jj = 0; jj < kJG; ++jj) {
-                        if (jj >= jn) break;
-                        const float2* H = Hc + (int64_t)(rb + i * J + j0 + jj) * B.MMAX;
-                        float2* W = Wc + (int64_t)(i * J + j0 + jj) * M;
-#pragma unroll
-                        for (int q = 0; q < kE / 2; ++q) {
-                            const int k = t + q * T;
-                            const int kb = (k == 0) ? M / 2 : M - k;
-                            const float2 ga = Gs[(jj * kE + 2 * q) * T], gb = Gs[(jj * kE + 2 * q + 1) * T];
-                            const float2 ha = __ldg(H + k), hb = __ldg(H + kb);
-                            float2 w0 = W[(2 * q) * T], w1 = W[(2 * q + 1) * T];
-                            if (k == 0) {            // slot 0 holds two real bins
-                                C[0].x += ha.x * ga.x;
-                                C[0].y += ha.y * ga.y;
-                                w0.x += X[0].x * ga.x;
-                                w0.y += X[0].y * ga.y;
-                            } else {
-                                C[2 * q] = cadd(C[2 * q], cmulc(ha, ga));
-                                w0 = cadd(w0, cmulc(X[2 * q], ga));
-                            }
-                            C[2 * q + 1] = cadd(C[2 * q + 1], cmulc(hb, gb));
-                            w1 = cadd(w1, cmulc(X[2 * q + 1], gb));
-                            W[(2 * q) * T] = w0;
-                            W[(2 * q + 1) * T] = w1;
-                        }
+            }
+            __syncthreads();                     // G written by every thread is visible
+            // ---- phase 2: per source
+            for (int i = 0; i < I; ++i) {
+                const float a = __ldg(gains + sb + i);
+                const float* xi = x + B.xoff[sb + i];
+                float* dxi = dx ? dx + B.xoff[sb + i] : nullptr;
+                float da = 0.f, dac = 0.f;       // Kahan sum of c * x
+                if constexpr (L::kStage) {
+                    for (int jj = 0; jj < jn; ++jj) {
+                        stage_spectrum_async<M, E>(hs + jj * M, Hc + (int64_t)(rb + i * J + j0 + jj) * B.MMAX, t);
+                        stage_spectrum_async<M, E>(gs + jj * M, gslot(b0, jj), t);
                     }
-                    float2 v[kE];
-                    irfft_pairs<M>(v, C, sm, tw, t);
-                    const float a = __ldg(gains + sb + i);
-                    float* dxi = dx ? dx + B.xoff[sb + i] : nullptr;
-                    float da = 0.f, dac = 0.f;   // Kahan sum of c * x over this block
+                    cp_async_commit();
+                }
+                float2 W[kJG][E];
 #pragma unroll
-                    for (int q = 0; q < kE; ++q) {
+                for (int jj = 0; jj < kJG; ++jj)
+#pragma unroll
+                    for (int e = 0; e < E; ++e) W[jj][e] = make_float2(0.f, 0.f);
+                for (int64_t b = b0; b < b1; ++b) {
+                    const int64_t pos = b * hop;
+                    const int64_t lim = nx - pos;
+                    cp_async_wait<0>();
+                    __syncthreads();
+                    float2 v[E];
+                    load_staged_strided<M, E>(v, xs, t);
+                    __syncthreads();
+                    if (b + 1 < b1) stage_x(i, b + 1);
+                    else if (i + 1 < I) stage_x(i + 1, b0);
+                    cp_async_commit();
+                    rfft_regs_to_smem<M, E>(v, sm, tw, t);
+                    float2 X[E];
+                    split_forward<M, E>(X, sm, wsplit, t);
+                    cp_async_wait<1>();          // spectra and G of this block are in
+                    __syncthreads();             // (and every thread is done with sm)
+#pragma unroll
+                    for (int q = 0; q < E / 2; ++q) {
+                        const int k = t + q * T;
+                        const int kb = (k == 0) ? M / 2 : M - k;
+                        float2 ca = make_float2(0.f, 0.f), cb = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int jj = 0; jj < kJG; ++jj) {
+                            if (jj >= jn) break;
+                            float2 ga, gb, ha, hb;
+                            if constexpr (L::kStage) {
+                                ga = gs[jj * M + (2 * q) * T + t];
+                                gb = gs[jj * M + (2 * q + 1) * T + t];
+                                ha = hs[jj * M + k];
+                                hb = hs[jj * M + kb];
+                            } else {
+                                const float2* G = gslot(b, jj) + t;
+                                ga = G[(2 * q) * T];
+                                gb = G[(2 * q + 1) * T];
+                                const float2* H = Hc + (int64_t)(rb + i * J + j0 + jj) * B.MMAX;
+                                ha = __ldg(H + k);
+                                hb = __ldg(H + kb);
+                            }
+                            if (k == 0) {            // slot 0 holds two real bins
+                                ca.x += ha.x * ga.x;
+                                ca.y += ha.y * ga.y;
+                                W[jj][0].x += X[0].x * ga.x;
+                                W[jj][0].y += X[0].y * ga.y;
+                            } else {
+                                ca = cadd(ca, cmulc(ha, ga));
+                                W[jj][2 * q] = cadd(W[jj][2 * q], cmulc(X[2 * q], ga));
+                            }
+                            cb = cadd(cb, cmulc(hb, gb));
+                            W[jj][2 * q + 1] = cadd(W[jj][2 * q + 1], cmulc(X[2 * q + 1], gb));
+                        }
+                        unsplit_pair<M>(sm, wsplit, k, ca, cb);
+                    }
+                    __syncthreads();             // gs fully read, sm fully written
+                    if constexpr (L::kStage) {
+                        if (b + 1 < b1) {
+                            for (int jj = 0; jj < jn; ++jj) stage_spectrum_async<M, E>(gs + jj * M, gslot(b + 1, jj), t);
+                        }
+                        cp_async_commit();
+                    }
+                    irfft_from_smem<M, E>(v, sm, tw, t);
+#pragma unroll
+                    for (int q = 0; q < E; ++q) {
                         const int n = 2 * (t + q * T);
 #pragma unroll
                         for (int e = 0; e < 2; ++e) {
@@ -169,34 +250,31 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
                             }
                         }
                     }
-                    const double tot = block_sum_d((double)da - (double)dac, sd);
-                    if (t == 0) dsum[i] += tot;
                 }
-            }
-        }
-        // dh partials of this segment
-        for (int ij = 0; ij < I * J; ++ij) {
-            const float2* W = Wc + (int64_t)ij * M;
-            __syncthreads();                 // sm is free
-#pragma unroll 2
-            for (int q = 0; q < kE / 2; ++q)
-                unsplit_pair<M>(sm, wsplit, t + q * T, W[(2 * q) * T], W[(2 * q + 1) * T]);
-            __syncthreads();
-            float2 v[kE];
-            irfft_from_smem<M>(v, sm, tw, t);
-            const int r = rb + ij;
-            const int Lr = B.L[r];
-            float* out = dhp + B.dhp_off[g] + (B.roff[r] - B.roff[rb]);
+                // dh partials of source i for mics j0 .. j0 + jn - 1
 #pragma unroll
-            for (int q = 0; q < kE; ++q) {
-                const int n = 2 * (t + q * T);
-                if (n < Lr) out[n] = v[q].x;
-                if (n + 1 < Lr) out[n + 1] = v[q].y;
+                for (int jj = 0; jj < kJG; ++jj) {
+                    if (jj >= jn) break;
+                    float2 v[E];
+                    irfft_pairs<M, E>(v, W[jj], sm, tw, t);
+                    const int r = rb + i * J + j0 + jj;
+                    const int Lr = B.L[r];
+                    float* out = dhp + B.dhp_off[g] + (B.roff[r] - B.roff[rb]);
+#pragma unroll
+                    for (int q = 0; q < E; ++q) {
+                        const int n = 2 * (t + q * T);
+                        if (n < Lr) out[n] = v[q].x;
+                        if (n + 1 < Lr) out[n + 1] = v[q].y;
+                    }
+                }
+                const double tot = block_sum_d((double)da - (double)dac, sd);
+                if (t == 0) dsum[i] += tot;
             }
         }
         __syncthreads();
         if (t < I) dap[(int64_t)g * kMaxSources + t] = (float)dsum[t];
     }
+    cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
@@ -264,27 +342,37 @@ k_finalize(DevBatch B, const float* __restrict__ gains, const float* __restrict_
 // launchers
 // ---------------------------------------------------------------------------
 template <int M>
-constexpr int smem_backward() { return (int)sizeof(float2) * (padded_len(M) + kJG * M); }
+constexpr int smem_backward() { return (int)BwdCfg<M>::bytes; }
 
 template <int M>
 static void backward_m(const DevBatch& B, const Queues& Q, int bucket, const float* g, const float* x,
                        const float* gains, const float2* Hc, float* dx, float* dhp, float* dap,
-                       float2* W, const float2* tw, int grid, cudaStream_t st) {
-    k_backward<M><<<grid, M / kE, smem_backward<M>(), st>>>(B, Q, bucket, g, x, gains, Hc, dx, dhp,
-                                                            dap, W, tw);
+                       float2* Gc, int gc_blocks, Twiddles tw, int grid, cudaStream_t st) {
+    k_backward<M><<<grid, BwdCfg<M>::T, smem_backward<M>(), st>>>(B, Q, bucket, g, x, gains, Hc, dx, dhp,
+                                                                  dap, Gc, gc_blocks, tw.get(BwdCfg<M>::E));
 }
 
 void launch_backward(int logN, const DevBatch& B, const Queues& Q, const float* g, const float* x,
                      const float* gains, const float2* Hc, float* dx, float* dhp, float* dap,
-                     float2* W, const float2* tw, int grid, cudaStream_t st) {
+                     float2* Gc, int gc_blocks, Twiddles tw, int grid, cudaStream_t st) {
     const int b = logN - kMinLog;
     switch (logN) {
-        case 11: backward_m<1024>(B, Q, b, g, x, gains, Hc, dx, dhp, dap, W, tw, grid, st); break;
-        case 12: backward_m<2048>(B, Q, b, g, x, gains, Hc, dx, dhp, dap, W, tw, grid, st); break;
-        case 13: backward_m<4096>(B, Q, b, g, x, gains, Hc, dx, dhp, dap, W, tw, grid, st); break;
-        case 14: backward_m<8192>(B, Q, b, g, x, gains, Hc, dx, dhp, dap, W, tw, grid, st); break;
+        case 11: backward_m<1024>(B, Q, b, g, x, gains, Hc, dx, dhp, dap, Gc, gc_blocks, tw, grid, st); break;
+        case 12: backward_m<2048>(B, Q, b, g, x, gains, Hc, dx, dhp, dap, Gc, gc_blocks, tw, grid, st); break;
+        case 13: backward_m<4096>(B, Q, b, g, x, gains, Hc, dx, dhp, dap, Gc, gc_blocks, tw, grid, st); break;
+        case 14: backward_m<8192>(B, Q, b, g, x, gains, Hc, dx, dhp, dap, Gc, gc_blocks, tw, grid, st); break;
         default: break;
     }
+}
+
+int bwd_threads(int logN) {
+    switch (logN) {
+        case 11: return BwdCfg<1024>::T;
+        case 12: return BwdCfg<2048>::T;
+        case 13: return BwdCfg<4096>::T;
+        case 14: return BwdCfg<8192>::T;
+    }
+    return 1;
 }
 
 void launch_finalize(const DevBatch& B, const float* gains, const float* dhp, const float* dap,
@@ -304,10 +392,10 @@ static int occ_b(K kernel, int threads, int smem) {
 
 int occupancy_backward(int logN) {
     switch (logN) {
-        case 11: return occ_b(k_backward<1024>, 64, smem_backward<1024>());
-        case 12: return occ_b(k_backward<2048>, 128, smem_backward<2048>());
-        case 13: return occ_b(k_backward<4096>, 256, smem_backward<4096>());
-        case 14: return occ_b(k_backward<8192>, 512, smem_backward<8192>());
+        case 11: return occ_b(k_backward<1024>, BwdCfg<1024>::T, smem_backward<1024>());
+        case 12: return occ_b(k_backward<2048>, BwdCfg<2048>::T, smem_backward<2048>());
+        case 13: return occ_b(k_backward<4096>, BwdCfg<4096>::T, smem_backward<4096>());
+        case 14: return occ_b(k_backward<8192>, BwdCfg<8192>::T, smem_backward<8192>());
     }
     return 1;
 }

@@ -4,18 +4,19 @@
 // z[n] = x[2n] + i x[2n+1] followed by the even/odd split (the "half spectrum"
 // of Sec. 2.2: only bins 0..N/2 are kept, Hermitian symmetry gives the rest).
 //
-// The complex transform is a Stockham auto-sort FFT: each thread of a CTA of
-// T = M/16 threads holds E = 16 complex values in registers; passes of radix
-// 16 (or 8/4/2 for the last factor) run in registers and exchange through one
+// The complex transform is a Stockham auto-sort FFT run by a CTA of T = M/E
+// threads, each holding E complex values in registers.  Passes of radix E
+// (the last one possibly smaller) run in registers and exchange through one
 // padded shared-memory buffer.  Between passes thread t holds indices
 // t + s*T, s < E ("strided layout"), which is both the load pattern of every
 // pass and the output pattern of the last pass, so the last pass never touches
 // shared memory.
 //
 // Twiddles come from tables built on the host in FP64 and rounded once to
-// FP32 (no fast-math intrinsics); the tables may sit in global or (copied
-// once per CTA) shared memory.  The inverse transform is computed as
-// conj(FFT(conj(.))) so one code path serves both directions.
+// FP32 (no fast-math intrinsics): each pass stores the powers w^(2^j) and the
+// other powers are products of a few of them.  The tables may sit in global
+// or (copied once per CTA) shared memory.  The inverse transform is computed
+// as conj(FFT(conj(.))) so one code path serves both directions.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -129,35 +130,38 @@ __device__ __forceinline__ void dft(float2 (&u)[R]) {
 }
 
 // ---------------------------------------------------------------------------
-// FFT plans: T = M/16 threads, E = 16 values per thread
+// plans
 // ---------------------------------------------------------------------------
-constexpr int kE = 16;
+__host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
 
-// padded shared-memory index: one spare float2 every 16 keeps both the
-// strided loads and the radix-16 scatter stores free of bank conflicts
-__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
+// values per thread for a complex size M
+__host__ __device__ constexpr int e_for(int M) { return 8; }
+
+// padded shared-memory index: one spare float2 every 16.  With T a multiple
+// of 16 the strided loads and stores are conflict-free, and so are the
+// scatter stores of the radix-16 passes and of the radix-8 passes except
+// the one with LP = 8 (2-way on part of its lanes).
+__host__ __device__ constexpr int pad(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int padded_len(int M) { return M + (M >> 4); }
 
-template <int R>
-struct Log2R { static constexpr int v = (R == 2) ? 1 : (R == 4) ? 2 : (R == 8) ? 3 : 4; };
-
-template <int M>
+template <int M, int E = e_for(M)>
 struct FftPlan {
-    static constexpr int T = M / kE;
-    // radix of the last pass; the others are 16
-    static constexpr int R_LAST = (M == 1024) ? 4 : (M == 2048) ? 8 : (M == 4096) ? 16 : 2;
-    static constexpr int NPASS = (M == 8192) ? 4 : 3;
-    // Twiddle table: pass p (p >= 1, radix R, LP = product of the earlier
-    // radices) stores log2(R) rows of LP entries, row j holding
-    // w^(2^j) = exp(-2 pi i 2^j k / (LP R)) for k < LP; the other powers are
-    // products of at most four of these.  Then the split table
-    // exp(-2 pi i k / (2M)), k <= M/2.
-    static constexpr int R2 = (M == 8192) ? 16 : R_LAST;    // radix of pass 2
-    static constexpr int OFF1 = 0;                          // LP = 16, R = 16
-    static constexpr int OFF2 = OFF1 + 16 * 4;              // LP = 256, R = R2
-    static constexpr int OFF3 = OFF2 + 256 * Log2R<R2>::v;  // LP = 4096, R = 2 (M = 8192)
-    static constexpr int OFF_SPLIT = (M == 8192) ? OFF3 + 4096 : OFF3;
+    static constexpr int T = M / E;
+    static constexpr int LOGE = ilog2(E);
+    static constexpr int LOGM = ilog2(M);
+    static constexpr int NPASS = (LOGM + LOGE - 1) / LOGE;
+    static constexpr int R_LAST = 1 << (LOGM - (NPASS - 1) * LOGE);
+    static constexpr int radix(int p) { return p < NPASS - 1 ? E : R_LAST; }
+    static constexpr int lp(int p) { return 1 << (p * LOGE); }   // product of the earlier radices
+    // Twiddle table: pass p >= 1 stores log2(radix(p)) rows of lp(p) entries,
+    // row j holding w^(2^j) = exp(-2 pi i 2^j k / (lp(p) radix(p))), k < lp(p);
+    // then the split table exp(-2 pi i k / (2M)), k <= M/2.
+    static constexpr int tw_off(int p) {
+        return p <= 1 ? 0 : tw_off(p - 1) + ilog2(radix(p - 1)) * lp(p - 1);
+    }
+    static constexpr int OFF_SPLIT = tw_off(NPASS);
     static constexpr int TW_LEN = OFF_SPLIT + M / 2 + 1;
+    static_assert(T % 16 == 0, "T must be a multiple of 16");
 };
 
 // u[m] *= w^m, m = 1 .. R-1, from the power rows of a pass table
@@ -194,14 +198,23 @@ __device__ __forceinline__ void apply_twiddles(float2 (&u)[R], const float2* __r
     }
 }
 
+// padded offset of element base + m * LP relative to pad(base), for the
+// scatter of a Stockham pass (base = (i - k) R + k with k < LP)
+template <int LP>
+__device__ __forceinline__ constexpr int scatter_off(int m) {
+    if constexpr (LP >= 16) return m * (LP + LP / 16);
+    else if constexpr (LP == 8) return 8 * m + (m >> 1);   // base % 16 = k < 8
+    else return m * LP;                                    // LP = 1: base % 16 + m < 16
+}
+
 // One Stockham pass of radix R with LP = product of the earlier radices.
 // Input: v in strided layout.  If LAST, the output stays in v (strided);
 // otherwise it is scattered to shared memory.
-template <int M, int R, int LP, bool LAST>
-__device__ __forceinline__ void fft_pass(float2 (&v)[kE], float2* __restrict__ sm,
+template <int M, int E, int R, int LP, bool LAST>
+__device__ __forceinline__ void fft_pass(float2 (&v)[E], float2* __restrict__ sm,
                                          const float2* __restrict__ tw, int t) {
-    constexpr int T = M / kE;
-    constexpr int NB = kE / R;  // butterflies per thread
+    constexpr int T = M / E;
+    constexpr int NB = E / R;  // butterflies per thread
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
         float2 u[R];
@@ -215,51 +228,54 @@ __device__ __forceinline__ void fft_pass(float2 (&v)[kE], float2* __restrict__ s
 #pragma unroll
             for (int m = 0; m < R; ++m) v[q + m * NB] = u[m];
         } else {
-            const int base = (i - k) * R + k;
+            float2* dst = sm + pad((i - k) * R + k);
 #pragma unroll
-            for (int m = 0; m < R; ++m) sm[pad(base + m * LP)] = u[m];
+            for (int m = 0; m < R; ++m) dst[scatter_off<LP>(m)] = u[m];
         }
     }
 }
 
-template <int M>
-__device__ __forceinline__ void load_strided(float2 (&v)[kE], const float2* __restrict__ sm, int t) {
-    constexpr int T = M / kE;
+template <int M, int E>
+__device__ __forceinline__ void load_strided(float2 (&v)[E], const float2* __restrict__ sm, int t) {
+    constexpr int T = M / E;
+    const float2* src = sm + t + (t >> 4);
 #pragma unroll
-    for (int s = 0; s < kE; ++s) v[s] = sm[pad(t + s * T)];
+    for (int s = 0; s < E; ++s) v[s] = src[s * (T + T / 16)];
 }
 
-template <int M>
-__device__ __forceinline__ void store_strided(const float2 (&v)[kE], float2* __restrict__ sm, int t) {
-    constexpr int T = M / kE;
+template <int M, int E>
+__device__ __forceinline__ void store_strided(const float2 (&v)[E], float2* __restrict__ sm, int t) {
+    constexpr int T = M / E;
+    float2* dst = sm + t + (t >> 4);
 #pragma unroll
-    for (int s = 0; s < kE; ++s) sm[pad(t + s * T)] = v[s];
+    for (int s = 0; s < E; ++s) dst[s * (T + T / 16)] = v[s];
+}
+
+// passes P .. NPASS-1; entered with v in strided layout and sm free
+template <int M, int E, int P>
+__device__ __forceinline__ void fft_from(float2 (&v)[E], float2* __restrict__ sm,
+                                         const float2* __restrict__ tw, int t) {
+    using Pl = FftPlan<M, E>;
+    constexpr int R = Pl::radix(P), LP = Pl::lp(P);
+    if constexpr (P == Pl::NPASS - 1) {
+        fft_pass<M, E, R, LP, true>(v, sm, tw + Pl::tw_off(P), t);
+    } else {
+        fft_pass<M, E, R, LP, false>(v, sm, tw + Pl::tw_off(P), t);
+        __syncthreads();
+        load_strided<M, E>(v, sm, t);
+        if constexpr (P + 2 < Pl::NPASS) __syncthreads();   // the next pass scatters in place
+        fft_from<M, E, P + 1>(v, sm, tw, t);
+    }
 }
 
 // Complex forward FFT of size M.  v: strided input in registers; on return v
 // holds the spectrum in strided layout (natural bin index t + s*T).
 // Starts with a __syncthreads so the caller may still be reading sm.
-template <int M>
-__device__ __forceinline__ void fft_core(float2 (&v)[kE], float2* __restrict__ sm,
+template <int M, int E>
+__device__ __forceinline__ void fft_core(float2 (&v)[E], float2* __restrict__ sm,
                                          const float2* __restrict__ tw, int t) {
-    using P = FftPlan<M>;
     __syncthreads();
-    fft_pass<M, 16, 1, false>(v, sm, tw, t);
-    __syncthreads();
-    load_strided<M>(v, sm, t);
-    __syncthreads();
-    fft_pass<M, 16, 16, false>(v, sm, tw + P::OFF1, t);
-    __syncthreads();
-    load_strided<M>(v, sm, t);
-    if constexpr (P::NPASS == 3) {
-        fft_pass<M, P::R_LAST, 256, true>(v, sm, tw + P::OFF2, t);
-    } else {
-        __syncthreads();
-        fft_pass<M, 16, 256, false>(v, sm, tw + P::OFF2, t);
-        __syncthreads();
-        load_strided<M>(v, sm, t);
-        fft_pass<M, 2, 4096, true>(v, sm, tw + P::OFF3, t);
-    }
+    fft_from<M, E, 0>(v, sm, tw, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -267,13 +283,13 @@ __device__ __forceinline__ void fft_core(float2 (&v)[kE], float2* __restrict__ s
 // ---------------------------------------------------------------------------
 
 // Loads z[n] = x[2n] + i x[2n+1] for the strided indices of thread t from a
-// real segment src[0, len) (zero outside).  src may be unaligned.
-template <int M>
-__device__ __forceinline__ void load_real_strided(float2 (&v)[kE], const float* __restrict__ src,
+// real segment src[0, len) in global memory (zero outside; src may be unaligned).
+template <int M, int E>
+__device__ __forceinline__ void load_real_strided(float2 (&v)[E], const float* __restrict__ src,
                                                   int64_t len, int t) {
-    constexpr int T = M / kE;
+    constexpr int T = M / E;
 #pragma unroll
-    for (int s = 0; s < kE; ++s) {
+    for (int s = 0; s < E; ++s) {
         const int64_t n = 2 * (int64_t)(t + s * T);
         float a = (n < len) ? __ldg(src + n) : 0.f;
         float b = (n + 1 < len) ? __ldg(src + n + 1) : 0.f;
@@ -310,12 +326,12 @@ __device__ __forceinline__ void split_pair(const float2* __restrict__ sm, const 
 }
 
 // Split into pair layout registers P[2s] = X[k_s], P[2s+1] = X[M-k_s].
-template <int M>
-__device__ __forceinline__ void split_forward(float2 (&P)[kE], const float2* __restrict__ sm,
+template <int M, int E>
+__device__ __forceinline__ void split_forward(float2 (&P)[E], const float2* __restrict__ sm,
                                               const float2* __restrict__ wsplit, int t) {
-    constexpr int T = M / kE;
+    constexpr int T = M / E;
 #pragma unroll
-    for (int s = 0; s < kE / 2; ++s) split_pair<M>(sm, wsplit, t + s * T, P[2 * s], P[2 * s + 1]);
+    for (int s = 0; s < E / 2; ++s) split_pair<M>(sm, wsplit, t + s * T, P[2 * s], P[2 * s + 1]);
 }
 
 // Inverse pre-processing of one pair: from ya = Y[k], yb = Y[M-k] (for k = 0:
@@ -341,12 +357,12 @@ __device__ __forceinline__ void unsplit_pair(float2* __restrict__ sm, const floa
     }
 }
 
-template <int M>
-__device__ __forceinline__ void split_inverse_store(const float2 (&P)[kE], float2* __restrict__ sm,
+template <int M, int E>
+__device__ __forceinline__ void split_inverse_store(const float2 (&P)[E], float2* __restrict__ sm,
                                                     const float2* __restrict__ wsplit, int t) {
-    constexpr int T = M / kE;
+    constexpr int T = M / E;
 #pragma unroll
-    for (int s = 0; s < kE / 2; ++s) unsplit_pair<M>(sm, wsplit, t + s * T, P[2 * s], P[2 * s + 1]);
+    for (int s = 0; s < E / 2; ++s) unsplit_pair<M>(sm, wsplit, t + s * T, P[2 * s], P[2 * s + 1]);
 }
 
 // ---------------------------------------------------------------------------
@@ -370,92 +386,88 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 // Queues the copy of the real block src[0, len) into stage[0, 2M), zeros
 // beyond len.  Thread t copies elements t + k*T (coalesced).
-template <int M>
+template <int M, int E>
 __device__ __forceinline__ void stage_real_async(float* __restrict__ stage, const float* __restrict__ src,
                                                  int64_t len, int t) {
-    constexpr int T = M / kE;
+    constexpr int T = M / E;
 #pragma unroll 8
-    for (int k = 0; k < 2 * kE; ++k) {
+    for (int k = 0; k < 2 * E; ++k) {
         const int n = t + k * T;
         const bool ok = n < len;
         cp_async4(stage + n, ok ? src + n : src, ok);
     }
 }
 
+// Queues the copy of M float2 from 16-byte aligned global memory into
+// 16-byte aligned shared memory.
+template <int M, int E>
+__device__ __forceinline__ void stage_spectrum_async(float2* __restrict__ dst, const float2* __restrict__ src,
+                                                     int t) {
+    constexpr int T = M / E;
+#pragma unroll
+    for (int k = 0; k < M / 2 / T; ++k) {
+        const int c = t + k * T;
+        cp_async16(dst + 2 * c, src + 2 * c);
+    }
+}
+
 // z[n] = (stage[2n], stage[2n+1]) for the strided indices of thread t
-template <int M>
-__device__ __forceinline__ void load_staged_strided(float2 (&v)[kE], const float* __restrict__ stage, int t) {
-    constexpr int T = M / kE;
+template <int M, int E>
+__device__ __forceinline__ void load_staged_strided(float2 (&v)[E], const float* __restrict__ stage, int t) {
+    constexpr int T = M / E;
     const float2* s2 = reinterpret_cast<const float2*>(stage);
 #pragma unroll
-    for (int s = 0; s < kE; ++s) v[s] = s2[t + s * T];
+    for (int s = 0; s < E; ++s) v[s] = s2[t + s * T];
 }
 
-// Forward FFT of a real segment src[0, len) zero-padded to 2M: leaves
-// Z = FFT_M(z) in shared memory, natural order; read pairs with split_pair.
-template <int M>
-__device__ __forceinline__ void rfft_to_smem(const float* __restrict__ src, int64_t len,
-                                             float2* __restrict__ sm, const float2* __restrict__ tw, int t) {
-    float2 v[kE];
-    load_real_strided<M>(v, src, len, t);
-    fft_core<M>(v, sm, tw, t);
+// ---------------------------------------------------------------------------
+// composite real transforms
+// ---------------------------------------------------------------------------
+
+// FFT of strided registers v into sm (natural order); read pairs with
+// split_pair afterwards.
+template <int M, int E>
+__device__ __forceinline__ void rfft_regs_to_smem(float2 (&v)[E], float2* __restrict__ sm,
+                                                  const float2* __restrict__ tw, int t) {
+    fft_core<M, E>(v, sm, tw, t);
     __syncthreads();                 // everyone done with the last pass loads
-    store_strided<M>(v, sm, t);
+    store_strided<M, E>(v, sm, t);
     __syncthreads();
 }
 
-// Forward FFT of a staged real block (stage[0, 2M) in shared memory):
-// leaves Z = FFT_M(z) in sm, natural order.  The caller must have completed
-// the copy into stage and synchronised.
-template <int M>
-__device__ __forceinline__ void rfft_staged_to_smem(const float* __restrict__ stage, float2* __restrict__ sm,
-                                                    const float2* __restrict__ tw, int t) {
-    float2 v[kE];
-    load_staged_strided<M>(v, stage, t);
-    fft_core<M>(v, sm, tw, t);
-    __syncthreads();
-    store_strided<M>(v, sm, t);
-    __syncthreads();
+// Forward real FFT of src[0, len) (global) zero-padded to 2M, into pair layout P.
+template <int M, int E>
+__device__ __forceinline__ void rfft_pairs(float2 (&P)[E], const float* __restrict__ src, int64_t len,
+                                           float2* __restrict__ sm, const float2* __restrict__ tw, int t) {
+    float2 v[E];
+    load_real_strided<M, E>(v, src, len, t);
+    rfft_regs_to_smem<M, E>(v, sm, tw, t);
+    split_forward<M, E>(P, sm, tw + FftPlan<M, E>::OFF_SPLIT, t);
 }
 
 // Inverse real FFT after the caller has written conj(Z') to sm with
-// unsplit_pair (and synchronised): v[s] = (y[2n], y[2n+1]) * 2M, n = t + s*T.
-template <int M>
-__device__ __forceinline__ void irfft_from_smem(float2 (&v)[kE], float2* __restrict__ sm,
+// unsplit_pair and synchronised: v[s] = (y[2n], y[2n+1]) * 2M, n = t + s*T.
+template <int M, int E>
+__device__ __forceinline__ void irfft_from_smem(float2 (&v)[E], float2* __restrict__ sm,
                                                 const float2* __restrict__ tw, int t) {
-    load_strided<M>(v, sm, t);
-    fft_core<M>(v, sm, tw, t);
+    load_strided<M, E>(v, sm, t);
+    fft_core<M, E>(v, sm, tw, t);
 #pragma unroll
-    for (int s = 0; s < kE; ++s) v[s] = conjf2(v[s]);
-}
-
-// Forward real FFT of src[0, len) zero-padded to 2M, into pair layout P.
-template <int M>
-__device__ __forceinline__ void rfft_pairs(float2 (&P)[kE], const float* __restrict__ src, int64_t len,
-                                           float2* __restrict__ sm, const float2* __restrict__ tw, int t) {
-    using Pl = FftPlan<M>;
-    float2 v[kE];
-    load_real_strided<M>(v, src, len, t);
-    fft_core<M>(v, sm, tw, t);
-    __syncthreads();                 // everyone done with the last pass loads
-    store_strided<M>(v, sm, t);
-    __syncthreads();
-    split_forward<M>(P, sm, tw + Pl::OFF_SPLIT, t);
+    for (int s = 0; s < E; ++s) v[s] = conjf2(v[s]);
 }
 
 // Unnormalised inverse real FFT of a half spectrum in pair layout.  On return
 // v[s] holds (y[2n], y[2n+1]) * 2M for n = t + s*T.
-template <int M>
-__device__ __forceinline__ void irfft_pairs(float2 (&v)[kE], const float2 (&P)[kE],
+template <int M, int E>
+__device__ __forceinline__ void irfft_pairs(float2 (&v)[E], const float2 (&P)[E],
                                             float2* __restrict__ sm, const float2* __restrict__ tw, int t) {
-    using Pl = FftPlan<M>;
     __syncthreads();                 // sm may still be read by a previous phase
-    split_inverse_store<M>(P, sm, tw + Pl::OFF_SPLIT, t);
+    split_inverse_store<M, E>(P, sm, tw + FftPlan<M, E>::OFF_SPLIT, t);
     __syncthreads();
-    load_strided<M>(v, sm, t);
-    fft_core<M>(v, sm, tw, t);
+    load_strided<M, E>(v, sm, t);
+    fft_core<M, E>(v, sm, tw, t);
 #pragma unroll
-    for (int s = 0; s < kE; ++s) v[s] = conjf2(v[s]);
+    for (int s = 0; s < E; ++s) v[s] = conjf2(v[s]);
 }
 
 }  // namespace rsim

@@ -22,10 +22,11 @@ __device__ __forceinline__ int pop_job(const Queues& Q, int kind, int b, int* sl
 // K3: Hc_r = rFFT_N(hhat_r) / N in pair layout order (slot 0 = (H[0], H[N/2]))
 // ---------------------------------------------------------------------------
 template <int M>
-__global__ void __launch_bounds__(M / kE)
+__global__ void __launch_bounds__(M / e_for(M))
 k_spectrum(DevBatch B, Queues Q, int bucket, const float* __restrict__ rir, float2* __restrict__ Hc,
            const float2* __restrict__ tw) {
-    constexpr int T = M / kE;
+    constexpr int E = e_for(M);
+    constexpr int T = M / E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* sm = reinterpret_cast<float2*>(smem_raw);
     __shared__ int slot;
@@ -34,11 +35,11 @@ k_spectrum(DevBatch B, Queues Q, int bucket, const float* __restrict__ rir, floa
     for (;;) {
         const int r = pop_job(Q, kListSpec, bucket, &slot);
         if (r < 0) break;
-        float2 P[kE];
-        rfft_pairs<M>(P, rir + B.roff[r], B.L[r], sm, tw, t);
+        float2 P[E];
+        rfft_pairs<M, E>(P, rir + B.roff[r], B.L[r], sm, tw, t);
         float2* H = Hc + (int64_t)r * B.MMAX;
 #pragma unroll
-        for (int s = 0; s < kE / 2; ++s) {
+        for (int s = 0; s < E / 2; ++s) {
             const int k = t + s * T;
             if (k == 0) {
                 H[0] = cscale(P[0], inv_n);
@@ -69,32 +70,41 @@ k_spectrum(DevBatch B, Queues Q, int bucket, const float* __restrict__ rir, floa
 // without it and k_fixup adds it afterwards (one FP32 add, the same one done
 // in-tile, so results do not depend on the segmentation).  Microphones are
 // processed in groups of kJG; source spectra are recomputed per group.
+// Thread shape and shared-memory layout of the forward kernel per size:
+// E values per thread (T = M / E threads), whether the RIR spectra, the
+// carried tails and the twiddles sit in shared memory, and the CTAs per SM
+// the register budget is set for.
 template <int M>
-struct FwdSmem {
-    static constexpr bool kStageH = M <= 4096;   // RIR spectra staged in shared memory
-    static constexpr bool kTwSmem = M <= 4096;   // twiddle tables in shared memory
+struct FwdCfg {
+    static constexpr int E = (M == 4096) ? 16 : 8;
+    static constexpr int T = M / E;
+    static constexpr int kMinBlocks = (M <= 4096) ? 2 : 1;
+    static constexpr bool kStageH = false;
+    static constexpr bool kTailSmem = (M <= 2048);
+    static constexpr bool kTwSmem = (M <= 4096);
     static constexpr size_t a16(size_t v) { return (v + 15) / 16 * 16; }
     static constexpr size_t o_sm = 0;
     static constexpr size_t o_xs = a16(o_sm + sizeof(float2) * padded_len(M));
     static constexpr size_t o_hs = a16(o_xs + sizeof(float) * 2 * M);
     static constexpr size_t o_tl = a16(o_hs + (kStageH ? sizeof(float2) * kJG * M : 0));
-    static constexpr size_t o_tw = a16(o_tl + sizeof(float) * kJG * M);
-    static constexpr size_t bytes = a16(o_tw + (kTwSmem ? sizeof(float2) * FftPlan<M>::TW_LEN : 0));
+    static constexpr size_t o_tw = a16(o_tl + (kTailSmem ? sizeof(float) * kJG * M : 0));
+    static constexpr size_t bytes = a16(o_tw + (kTwSmem ? sizeof(float2) * FftPlan<M, E>::TW_LEN : 0));
 };
 
 template <int M>
-__global__ void __launch_bounds__(M / kE, 1)
+__global__ void __launch_bounds__(FwdCfg<M>::T, FwdCfg<M>::kMinBlocks)
 k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
           const float* __restrict__ gains, const float2* __restrict__ Hc, float* __restrict__ y,
           float* __restrict__ tails, const float2* __restrict__ twg) {
-    using Pl = FftPlan<M>;
-    using L = FwdSmem<M>;
-    constexpr int T = M / kE;
+    using L = FwdCfg<M>;
+    constexpr int E = L::E;
+    constexpr int T = M / E;
+    using Pl = FftPlan<M, E>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* sm = reinterpret_cast<float2*>(smem_raw + L::o_sm);
     float* xs = reinterpret_cast<float*>(smem_raw + L::o_xs);
     float2* hs = reinterpret_cast<float2*>(smem_raw + L::o_hs);
-    float (*tl)[M] = reinterpret_cast<float (*)[M]>(smem_raw + L::o_tl);
+    float* tl_smem = reinterpret_cast<float*>(smem_raw + L::o_tl);
     __shared__ int slot;
     const int t = threadIdx.x;
     const float2* tw = twg;
@@ -123,53 +133,52 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
             // queue the copies of source i's block b and of its spectra
             auto stage_x = [&](int64_t b, int i) {
                 const int64_t p = b * hop;
-                stage_real_async<M>(xs, x + B.xoff[sb + i] + p, min((int64_t)hop, nx - p), t);
+                stage_real_async<M, E>(xs, x + B.xoff[sb + i] + p, min((int64_t)hop, nx - p), t);
             };
             auto stage_h = [&](int i) {
                 if constexpr (L::kStageH) {
-                    for (int jj = 0; jj < jn; ++jj) {
-                        const float2* H = Hc + (int64_t)(rb + i * J + j0 + jj) * B.MMAX;
-#pragma unroll
-                        for (int k = 0; k < M / 2 / T; ++k) {
-                            const int c = t + k * T;
-                            cp_async16(hs + jj * M + 2 * c, H + 2 * c);
-                        }
-                    }
+                    for (int jj = 0; jj < jn; ++jj)
+                        stage_spectrum_async<M, E>(hs + jj * M, Hc + (int64_t)(rb + i * J + j0 + jj) * B.MMAX, t);
                 }
+            };
+            // carried tail of mic jj: shared memory, or this tile's slot of `tails`
+            auto tl = [&](int jj) -> float* {
+                if constexpr (L::kTailSmem) return tl_smem + jj * M;
+                else return tails + ((int64_t)g * J + j0 + jj) * B.MMAX;
             };
             __syncthreads();                     // stages and tails are free
             for (int jj = 0; jj < jn; ++jj)
-                for (int n = t; n < tail_len; n += T) tl[jj][n] = 0.f;
+                for (int n = t; n < tail_len; n += T) tl(jj)[n] = 0.f;
             stage_x(b0, 0);
             cp_async_commit();
             stage_h(0);
             cp_async_commit();
             for (int64_t b = b0; b < b1; ++b) {
                 const int64_t pos = b * hop;
-                float2 Y[kJG][kE];
+                float2 Y[kJG][E];
 #pragma unroll
                 for (int jj = 0; jj < kJG; ++jj)
 #pragma unroll
-                    for (int e = 0; e < kE; ++e) Y[jj][e] = make_float2(0.f, 0.f);
+                    for (int e = 0; e < E; ++e) Y[jj][e] = make_float2(0.f, 0.f);
                 for (int i = 0; i < I; ++i) {
                     // x_i is in (only the newest group, H_i, may still be pending)
                     cp_async_wait<1>();
                     __syncthreads();
-                    float2 v[kE];
-                    load_staged_strided<M>(v, xs, t);
+                    float2 v[E];
+                    load_staged_strided<M, E>(v, xs, t);
                     __syncthreads();             // xs fully read: reuse it
                     if (i + 1 < I) stage_x(b, i + 1);
                     else if (b + 1 < b1) stage_x(b + 1, 0);
                     cp_async_commit();
-                    fft_core<M>(v, sm, tw, t);
+                    fft_core<M, E>(v, sm, tw, t);
                     __syncthreads();
-                    store_strided<M>(v, sm, t);
+                    store_strided<M, E>(v, sm, t);
                     cp_async_wait<1>();          // H_i is in
                     __syncthreads();
                     const float a = __ldg(gains + sb + i);
                     const float2* H0 = Hc + (int64_t)(rb + i * J + j0) * B.MMAX;
 #pragma unroll
-                    for (int q = 0; q < kE / 2; ++q) {
+                    for (int q = 0; q < E / 2; ++q) {
                         const int k = t + q * T;
                         float2 xa, xb;
                         split_pair<M>(sm, wsplit, k, xa, xb);
@@ -205,33 +214,36 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
 #pragma unroll
                 for (int jj = 0; jj < kJG; ++jj) {
                     if (jj >= jn) break;
-                    float2 v[kE];
-                    irfft_pairs<M>(v, Y[jj], sm, tw, t);
+                    float2 v[E];
+                    irfft_pairs<M, E>(v, Y[jj], sm, tw, t);
                     float* yj = y + B.yoff[u] + (int64_t)(j0 + jj) * nx + pos;
+                    float* tlj = tl(jj);
                     const int64_t lim = nx - pos;
                     // owned samples [0, hop) plus the incoming tail
 #pragma unroll
-                    for (int q = 0; q < kE; ++q) {
+                    for (int q = 0; q < E; ++q) {
                         const int n = 2 * (t + q * T);
                         if (n < hop && n < lim)
-                            yj[n] = v[q].x + (n < tail_len ? tl[jj][n] : 0.f);
+                            yj[n] = v[q].x + (n < tail_len ? tlj[n] : 0.f);
                         if (n + 1 < hop && n + 1 < lim)
-                            yj[n + 1] = v[q].y + (n + 1 < tail_len ? tl[jj][n + 1] : 0.f);
+                            yj[n + 1] = v[q].y + (n + 1 < tail_len ? tlj[n + 1] : 0.f);
                     }
                     __syncthreads();
                     // outgoing tail [hop, hop + L_max - 1)
 #pragma unroll
-                    for (int q = 0; q < kE; ++q) {
+                    for (int q = 0; q < E; ++q) {
                         const int n = 2 * (t + q * T);
-                        if (n >= hop && n - hop < tail_len) tl[jj][n - hop] = v[q].x;
-                        if (n + 1 >= hop && n + 1 - hop < tail_len) tl[jj][n + 1 - hop] = v[q].y;
+                        if (n >= hop && n - hop < tail_len) tlj[n - hop] = v[q].x;
+                        if (n + 1 >= hop && n + 1 - hop < tail_len) tlj[n + 1 - hop] = v[q].y;
                     }
                 }
             }
-            __syncthreads();
-            for (int jj = 0; jj < jn; ++jj) {
-                float* dst = tails + ((int64_t)g * J + j0 + jj) * B.MMAX;
-                for (int n = t; n < tail_len; n += T) dst[n] = tl[jj][n];
+            if constexpr (L::kTailSmem) {
+                __syncthreads();
+                for (int jj = 0; jj < jn; ++jj) {
+                    float* dst = tails + ((int64_t)g * J + j0 + jj) * B.MMAX;
+                    for (int n = t; n < tail_len; n += T) dst[n] = tl(jj)[n];
+                }
             }
         }
     }
@@ -269,16 +281,16 @@ k_fixup(DevBatch B, float* __restrict__ y, const float* __restrict__ tails) {
 template <int M>
 constexpr int smem_spectrum() { return (int)sizeof(float2) * padded_len(M); }
 template <int M>
-constexpr int smem_forward() { return (int)FwdSmem<M>::bytes; }
+constexpr int smem_forward() { return (int)FwdCfg<M>::bytes; }
 
 template <int M>
 static void spectrum_m(const DevBatch& B, const Queues& Q, int bucket, const float* rir,
-                       float2* Hc, const float2* tw, int grid, cudaStream_t st) {
-    k_spectrum<M><<<grid, M / kE, smem_spectrum<M>(), st>>>(B, Q, bucket, rir, Hc, tw);
+                       float2* Hc, Twiddles tw, int grid, cudaStream_t st) {
+    k_spectrum<M><<<grid, M / e_for(M), smem_spectrum<M>(), st>>>(B, Q, bucket, rir, Hc, tw.get(e_for(M)));
 }
 
 void launch_spectrum(int logN, const DevBatch& B, const Queues& Q, const float* rir, float2* Hc,
-                     const float2* tw, int grid, cudaStream_t st) {
+                     Twiddles tw, int grid, cudaStream_t st) {
     const int b = logN - kMinLog;
     switch (logN) {
         case 11: spectrum_m<1024>(B, Q, b, rir, Hc, tw, grid, st); break;
@@ -292,12 +304,13 @@ void launch_spectrum(int logN, const DevBatch& B, const Queues& Q, const float* 
 template <int M>
 static void forward_m(const DevBatch& B, const Queues& Q, int bucket, const float* x,
                       const float* gains, const float2* Hc, float* y, float* tails,
-                      const float2* tw, int grid, cudaStream_t st) {
-    k_forward<M><<<grid, M / kE, smem_forward<M>(), st>>>(B, Q, bucket, x, gains, Hc, y, tails, tw);
+                      Twiddles tw, int grid, cudaStream_t st) {
+    k_forward<M><<<grid, FwdCfg<M>::T, smem_forward<M>(), st>>>(B, Q, bucket, x, gains, Hc, y, tails,
+                                                                tw.get(FwdCfg<M>::E));
 }
 
 void launch_forward(int logN, const DevBatch& B, const Queues& Q, const float* x, const float* gains,
-                    const float2* Hc, float* y, float* tails, const float2* tw, int grid,
+                    const float2* Hc, float* y, float* tails, Twiddles tw, int grid,
                     cudaStream_t st) {
     const int b = logN - kMinLog;
     switch (logN) {
@@ -315,7 +328,7 @@ void launch_fixup(const DevBatch& B, float* y, const float* tails, cudaStream_t 
     k_fixup<<<grid, 256, 0, st>>>(B, y, tails);
 }
 
-int threads_for(int logN) { return (1 << (logN - 1)) / kE; }
+int threads_for(int logN) { const int M = 1 << (logN - 1); return M / e_for(M); }
 
 template <typename K>
 static int occ(K kernel, int threads, int smem) {
@@ -327,20 +340,20 @@ static int occ(K kernel, int threads, int smem) {
 
 int occupancy_spectrum(int logN) {
     switch (logN) {
-        case 11: return occ(k_spectrum<1024>, 64, smem_spectrum<1024>());
-        case 12: return occ(k_spectrum<2048>, 128, smem_spectrum<2048>());
-        case 13: return occ(k_spectrum<4096>, 256, smem_spectrum<4096>());
-        case 14: return occ(k_spectrum<8192>, 512, smem_spectrum<8192>());
+        case 11: return occ(k_spectrum<1024>, threads_for(11), smem_spectrum<1024>());
+        case 12: return occ(k_spectrum<2048>, threads_for(12), smem_spectrum<2048>());
+        case 13: return occ(k_spectrum<4096>, threads_for(13), smem_spectrum<4096>());
+        case 14: return occ(k_spectrum<8192>, threads_for(14), smem_spectrum<8192>());
     }
     return 1;
 }
 
 int occupancy_forward(int logN) {
     switch (logN) {
-        case 11: return occ(k_forward<1024>, 64, smem_forward<1024>());
-        case 12: return occ(k_forward<2048>, 128, smem_forward<2048>());
-        case 13: return occ(k_forward<4096>, 256, smem_forward<4096>());
-        case 14: return occ(k_forward<8192>, 512, smem_forward<8192>());
+        case 11: return occ(k_forward<1024>, FwdCfg<1024>::T, smem_forward<1024>());
+        case 12: return occ(k_forward<2048>, FwdCfg<2048>::T, smem_forward<2048>());
+        case 13: return occ(k_forward<4096>, FwdCfg<4096>::T, smem_forward<4096>());
+        case 14: return occ(k_forward<8192>, FwdCfg<8192>::T, smem_forward<8192>());
     }
     return 1;
 }

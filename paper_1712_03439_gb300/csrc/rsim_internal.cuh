@@ -87,16 +87,23 @@ void launch_truncate(const DevBatch& B, const float* rir, double factor, int non
 void launch_power(const DevBatch& B, const float* x, int grid, cudaStream_t st);
 void launch_plan(const DevBatch& B, const Queues& Q, const float* snr_db, float* gains,
                  cudaStream_t st);
+// Twiddle tables of one FFT size for 8 and 16 values per thread; every
+// tiled kernel picks the table of its own thread shape.
+struct Twiddles {
+    const float2* e8;
+    const float2* e16;
+    __host__ __device__ const float2* get(int E) const { return E == 16 ? e16 : e8; }
+};
 void launch_spectrum(int logN, const DevBatch& B, const Queues& Q, const float* rir, float2* Hc,
-                     const float2* tw, int grid, cudaStream_t st);
+                     Twiddles tw, int grid, cudaStream_t st);
 void launch_forward(int logN, const DevBatch& B, const Queues& Q, const float* x, const float* gains,
-                    const float2* Hc, float* y, float* tails, const float2* tw, int grid,
+                    const float2* Hc, float* y, float* tails, Twiddles tw, int grid,
                     cudaStream_t st);
 void launch_fixup(const DevBatch& B, float* y, const float* tails, cudaStream_t st);
-// W: per-CTA dh accumulators, grid * IMAX * J * (N/2) complex
+// Gc: per-CTA cache of the mic spectra of a segment, grid x gc_blocks x kJG x (N/2) complex
 void launch_backward(int logN, const DevBatch& B, const Queues& Q, const float* g, const float* x,
                      const float* gains, const float2* Hc, float* dx, float* dhp, float* dap,
-                     float2* W, const float2* tw, int grid, cudaStream_t st);
+                     float2* Gc, int gc_blocks, Twiddles tw, int grid, cudaStream_t st);
 void launch_finalize(const DevBatch& B, const float* gains, const float* dhp, const float* dap,
                      float* grad_rir, float* grad_gains, cudaStream_t st);
 
@@ -108,5 +115,6 @@ int occupancy_spectrum(int logN);
 int occupancy_forward(int logN);
 int occupancy_backward(int logN);
 int threads_for(int logN);
+int bwd_threads(int logN);
 
 }  // namespace rsim
