@@ -111,7 +111,8 @@ rsim_status rsim_filter_mix_backward(rsim_plan_t plan, void *stream, const float
                                      float *grad_rir, float *grad_gains);
 
 /* Waits for the plan's stream work and reports errors latched by kernels
- * (RSIM_E_UNSUPPORTED: no allowed FFT size fits a truncated RIR;
+ * (RSIM_E_UNSUPPORTED: no allowed FFT size N has N >= 4 (N - L_max + 1), with L_max the
+ * longest truncated RIR of an utterance;
  * RSIM_E_INVALID: a noise source has zero power).  Clears the latch. */
 rsim_status rsim_plan_sync_status(rsim_plan_t plan, void *stream);
 

@@ -102,8 +102,6 @@ struct rsim_plan_s {
     float* dhp = nullptr;
     float* dap = nullptr;
     Twiddles tw[kNumBuckets] = {};
-    float2* Gc[kNumBuckets] = {};   // backward mic-spectrum cache per FFT size
-    int gc_blocks[kNumBuckets] = {};
     int grid_trunc = 1, grid_pow = 1;
     int grid_spec[kNumBuckets] = {}, grid_fwd[kNumBuckets] = {}, grid_bwd[kNumBuckets] = {};
     bool fwd_done = false;
@@ -281,7 +279,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
         *p_dhpoff, *p_tuning, *p_L, *p_logN, *p_hop, *p_lmax, *p_nblk, *p_pow, *p_err, *p_list,
         *p_count, *p_next, *p_Hc, *p_tails, *p_dhp, *p_dap;
     void* p_tw[2 * kNumBuckets] = {};
-    const int64_t cap = std::max<int64_t>(std::max<int64_t>(nbseg, nseg), R);
+    const int64_t cap = std::max<int64_t>(std::max<int64_t>(nbseg * kMaxSources, nseg), R);
     // launch shapes (persistent grids) decide the per-CTA backward scratch
     int sms = 0;
     {
@@ -296,7 +294,8 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
         DeviceGuard g0(device);
         grid_spec[b] = (int)std::max<int64_t>(1, std::min<int64_t>(R, (int64_t)sms * occupancy_spectrum(m)));
         grid_fwd[b] = (int)std::max<int64_t>(1, std::min<int64_t>(nseg, (int64_t)sms * occupancy_forward(m)));
-        grid_bwd[b] = (int)std::max<int64_t>(1, std::min<int64_t>(nbseg, (int64_t)sms * occupancy_backward(m)));
+        grid_bwd[b] = (int)std::max<int64_t>(
+            1, std::min<int64_t>(nbseg * imax, (int64_t)sms * occupancy_backward(m)));
     }
     pieces.push_back({&p_nsrc, sizeof(int32_t) * U});
     pieces.push_back({&p_nx, sizeof(int64_t) * U});
@@ -323,19 +322,9 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     pieces.push_back({&p_count, sizeof(int32_t) * kNumLists * kNumBuckets});
     pieces.push_back({&p_next, sizeof(int32_t) * kNumLists * kNumBuckets});
     pieces.push_back({&p_Hc, sizeof(float2) * R * MMAX});
-    pieces.push_back({&p_tails, sizeof(float) * nseg * J * MMAX});
+    pieces.push_back({&p_tails, sizeof(float) * nseg * J * 2 * MMAX});
     pieces.push_back({&p_dhp, sizeof(float) * std::max<int64_t>(dhp_total, 1)});
     pieces.push_back({&p_dap, sizeof(float) * std::max<int64_t>(nbseg, 1) * kMaxSources});
-    // backward G cache: a segment holds at most ceil(bseg_len / (N/2)) + 1 block starts (hop >= N/2)
-    void* p_Gc[kNumBuckets] = {};
-    int gc_blocks[kNumBuckets] = {};
-    for (int m = kMinLog; m <= kMaxLog; ++m) {
-        if (!((mask >> m) & 1)) continue;
-        const int b = m - kMinLog;
-        const int64_t half = (int64_t)1 << (m - 1);
-        gc_blocks[b] = (int)((bseg_len + half - 1) / half + 1);
-        pieces.push_back({&p_Gc[b], sizeof(float2) * (size_t)grid_bwd[b] * gc_blocks[b] * kJG * half});
-    }
     std::vector<std::vector<float2>> tws(2 * kNumBuckets);
     for (int m = kMinLog; m <= kMaxLog; ++m) {
         if (!((mask >> m) & 1)) continue;
@@ -422,8 +411,6 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     p->Hc = (float2*)p_Hc; p->tails = (float*)p_tails; p->dhp = (float*)p_dhp; p->dap = (float*)p_dap;
     for (int b = 0; b < kNumBuckets; ++b) {
         p->tw[b] = Twiddles{(const float2*)p_tw[2 * b], (const float2*)p_tw[2 * b + 1]};
-        p->Gc[b] = (float2*)p_Gc[b];
-        p->gc_blocks[b] = gc_blocks[b];
         p->grid_spec[b] = grid_spec[b];
         p->grid_fwd[b] = grid_fwd[b];
         p->grid_bwd[b] = grid_bwd[b];
@@ -510,8 +497,8 @@ extern "C" rsim_status rsim_filter_mix_backward(rsim_plan_t p, void* stream, con
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (queue)");
     stage_mark(p, 6, false, st);
     fan_out(p, st, [&](int m, cudaStream_t s) {
-        launch_backward(m, B, p->Q, grad_y, x, gains, p->Hc, grad_x, p->dhp, p->dap, p->Gc[m - kMinLog],
-                        p->gc_blocks[m - kMinLog], p->tw[m - kMinLog], p->grid_bwd[m - kMinLog], s);
+        launch_backward(m, B, p->Q, grad_y, x, gains, p->Hc, grad_x, p->dhp, p->dap,
+                        p->tw[m - kMinLog], p->grid_bwd[m - kMinLog], s);
     });
     stage_mark(p, 6, true, st);
     stage_mark(p, 7, false, st);
@@ -536,7 +523,7 @@ extern "C" rsim_status rsim_plan_sync_status(rsim_plan_t p, void* stream) {
         cudaMemset(p->B.err, 0, sizeof(int32_t));
         if (err & kErrNoFftSize)
             return fail(RSIM_E_UNSUPPORTED,
-                        "a truncated RIR is longer than N/2+1 for every allowed FFT size N");
+                        "a truncated RIR is longer than 3N/4+1 for every allowed FFT size N");
         if (err & kErrZeroPower)
             return fail(RSIM_E_INVALID, "a noise source has zero power but an SNR to meet");
         return fail(RSIM_E_DEVICE, "device error " + std::to_string(err));

@@ -59,8 +59,8 @@ k_spectrum(DevBatch B, Queues Q, int bucket, const float* __restrict__ rir, floa
 //   X_i = rFFT_N(x_i[b hop, b hop + hop))                 for every source i
 //   Y_j = sum_i alpha_i Hc_ij X_i                          split fused with the
 //                                                          MAC, Y_j in registers
-//   y_j block = irFFT_N(Y_j); the first hop samples plus the carried tail of
-//   block b-1 are stored, the last L_max - 1 samples are carried to b+1.
+//   y_j block = irFFT_N(Y_j) plus the carry of the earlier blocks; its first
+//   hop samples are stored, the last L_max - 1 samples are the new carry.
 // Global reads are prefetched with cp.async one step ahead so no transform
 // waits on memory: the next source's x block lands in a shared-memory stage
 // while the current one is transformed, and the next source's RIR spectra
@@ -87,7 +87,7 @@ struct FwdCfg {
     static constexpr size_t o_xs = a16(o_sm + sizeof(float2) * padded_len(M));
     static constexpr size_t o_hs = a16(o_xs + sizeof(float) * 2 * M);
     static constexpr size_t o_tl = a16(o_hs + (kStageH ? sizeof(float2) * kJG * M : 0));
-    static constexpr size_t o_tw = a16(o_tl + (kTailSmem ? sizeof(float) * kJG * M : 0));
+    static constexpr size_t o_tw = a16(o_tl + (kTailSmem ? sizeof(float) * kJG * 2 * M : 0));
     static constexpr size_t bytes = a16(o_tw + (kTwSmem ? sizeof(float2) * FftPlan<M, E>::TW_LEN : 0));
 };
 
@@ -143,8 +143,8 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
             };
             // carried tail of mic jj: shared memory, or this tile's slot of `tails`
             auto tl = [&](int jj) -> float* {
-                if constexpr (L::kTailSmem) return tl_smem + jj * M;
-                else return tails + ((int64_t)g * J + j0 + jj) * B.MMAX;
+                if constexpr (L::kTailSmem) return tl_smem + jj * 2 * M;
+                else return tails + ((int64_t)g * J + j0 + jj) * 2 * B.MMAX;
             };
             __syncthreads();                     // stages and tails are free
             for (int jj = 0; jj < jn; ++jj)
@@ -219,17 +219,18 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
                     float* yj = y + B.yoff[u] + (int64_t)(j0 + jj) * nx + pos;
                     float* tlj = tl(jj);
                     const int64_t lim = nx - pos;
-                    // owned samples [0, hop) plus the incoming tail
+                    // every sample n < N of the block adds the carried sum at n;
+                    // [0, hop) is stored, [hop, N) becomes the new carry (which
+                    // reaches several blocks ahead when L_max - 1 > hop)
 #pragma unroll
                     for (int q = 0; q < E; ++q) {
                         const int n = 2 * (t + q * T);
-                        if (n < hop && n < lim)
-                            yj[n] = v[q].x + (n < tail_len ? tlj[n] : 0.f);
-                        if (n + 1 < hop && n + 1 < lim)
-                            yj[n + 1] = v[q].y + (n + 1 < tail_len ? tlj[n + 1] : 0.f);
+                        if (n < tail_len) v[q].x += tlj[n];
+                        if (n + 1 < tail_len) v[q].y += tlj[n + 1];
+                        if (n < hop && n < lim) yj[n] = v[q].x;
+                        if (n + 1 < hop && n + 1 < lim) yj[n + 1] = v[q].y;
                     }
                     __syncthreads();
-                    // outgoing tail [hop, hop + L_max - 1)
 #pragma unroll
                     for (int q = 0; q < E; ++q) {
                         const int n = 2 * (t + q * T);
@@ -241,7 +242,7 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
             if constexpr (L::kTailSmem) {
                 __syncthreads();
                 for (int jj = 0; jj < jn; ++jj) {
-                    float* dst = tails + ((int64_t)g * J + j0 + jj) * B.MMAX;
+                    float* dst = tails + ((int64_t)g * J + j0 + jj) * 2 * B.MMAX;
                     for (int n = t; n < tail_len; n += T) dst[n] = tl(jj)[n];
                 }
             }
@@ -267,7 +268,7 @@ k_fixup(DevBatch B, float* __restrict__ y, const float* __restrict__ tails) {
         const int64_t pos = b0 * hop;
         const int tail_len = B.Lmax[u] - 1;
         for (int j = 0; j < B.J; ++j) {
-            const float* src = tails + ((int64_t)(g - 1) * B.J + j) * B.MMAX;
+            const float* src = tails + ((int64_t)(g - 1) * B.J + j) * 2 * B.MMAX;
             float* yj = y + B.yoff[u] + (int64_t)j * nx + pos;
             for (int n = threadIdx.x; n < tail_len && pos + n < nx; n += blockDim.x)
                 yj[n] = yj[n] + src[n];

@@ -16,7 +16,7 @@ constexpr int kPowerChunk = 32768;   // samples per partial-power CTA
 
 // device error word bits (latched, read by rsim_plan_sync_status)
 enum : int32_t {
-    kErrNoFftSize = 1,     // a truncated RIR longer than N/2+1 for every allowed N
+    kErrNoFftSize = 1,     // a truncated RIR longer than 3N/4+1 for every allowed N
     kErrZeroPower = 2,     // a noise source with zero power but an SNR to meet
 };
 
@@ -26,7 +26,8 @@ enum : int { kListFwd = 0, kListBwd = 1, kListSpec = 2, kNumLists = 3 };
 // Batch description and per-call state on the device.  Utterance u has
 // n_src[u] sources (source 0 is the target) and J microphones.  The forward
 // cuts it into ceil(n_x / seg_len) segments and the backward into
-// ceil(n_x / bseg_len) segments; a segment is one tile of work.
+// ceil(n_x / bseg_len) segments; a forward tile is a segment, a backward tile
+// a segment and one source.
 struct DevBatch {
     int32_t U, J, S, R, IMAX;
     int32_t NSEG;            // total segments
@@ -100,10 +101,9 @@ void launch_forward(int logN, const DevBatch& B, const Queues& Q, const float* x
                     const float2* Hc, float* y, float* tails, Twiddles tw, int grid,
                     cudaStream_t st);
 void launch_fixup(const DevBatch& B, float* y, const float* tails, cudaStream_t st);
-// Gc: per-CTA cache of the mic spectra of a segment, grid x gc_blocks x kJG x (N/2) complex
 void launch_backward(int logN, const DevBatch& B, const Queues& Q, const float* g, const float* x,
                      const float* gains, const float2* Hc, float* dx, float* dhp, float* dap,
-                     float2* Gc, int gc_blocks, Twiddles tw, int grid, cudaStream_t st);
+                     Twiddles tw, int grid, cudaStream_t st);
 void launch_finalize(const DevBatch& B, const float* gains, const float* dhp, const float* dap,
                      float* grad_rir, float* grad_gains, cudaStream_t st);
 

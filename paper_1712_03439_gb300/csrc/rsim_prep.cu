@@ -62,7 +62,8 @@ k_truncate(DevBatch B, const float* __restrict__ rir, double factor, int none,
         const float* h = rir + B.roff[r];
         const int n = B.rir_len[r];
         float amax = 0.f;
-        for (int i = t; i < n; i += kTruncThreads) amax = fmaxf(amax, fabsf(h[i]));
+#pragma unroll 4
+        for (int i = t; i < n; i += kTruncThreads) amax = fmaxf(amax, fabsf(__ldg(h + i)));
         amax = block_reduce(amax, OpMaxF(), sf, 0.f);
         const double P = __dmul_rn((double)amax, (double)amax);   // exact
         int L;
@@ -76,8 +77,9 @@ k_truncate(DevBatch B, const float* __restrict__ rir, double factor, int none,
             const float tlo = (float)(st * (1.0 - 1e-6));   // |h| < tlo  =>  h^2 < p_th
             const float thi = (float)(st * (1.0 + 1e-6));   // |h| >= thi =>  h^2 >= p_th
             int last = -1;
+#pragma unroll 4
             for (int i = t; i < n; i += kTruncThreads) {
-                const float a = fabsf(h[i]);
+                const float a = fabsf(__ldg(h + i));
                 bool keep;
                 if (a < tlo) keep = false;
                 else if (a >= thi) keep = true;
@@ -135,15 +137,32 @@ k_power(DevBatch B, const float* __restrict__ x) {
         if (c0 >= nx) continue;                 // uniform across the CTA
         const int64_t c1 = (c0 + kPowerChunk < nx) ? c0 + kPowerChunk : nx;
         const float* p = x + B.xoff[s];
-        float sum = 0.f, comp = 0.f;
-        for (int64_t i = c0 + t; i < c1; i += kPowThreads) {
-            const float v = __ldg(p + i);
-            const float yv = fmaf(v, v, -comp);
-            const float tv = sum + yv;
-            comp = (tv - sum) - yv;
-            sum = tv;
+        // four independent compensated sums keep several loads in flight
+        float sum[4] = {0.f, 0.f, 0.f, 0.f}, comp[4] = {0.f, 0.f, 0.f, 0.f};
+        int64_t i = c0 + t;
+        for (; i + 3 * kPowThreads < c1; i += 4 * kPowThreads) {
+            float v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] = __ldg(p + i + k * kPowThreads);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float yv = fmaf(v[k], v[k], -comp[k]);
+                const float tv = sum[k] + yv;
+                comp[k] = (tv - sum[k]) - yv;
+                sum[k] = tv;
+            }
         }
-        double d = block_reduce((double)sum - (double)comp, OpAddD(), sd, 0.0);
+        for (; i < c1; i += kPowThreads) {
+            const float v = __ldg(p + i);
+            const float yv = fmaf(v, v, -comp[0]);
+            const float tv = sum[0] + yv;
+            comp[0] = (tv - sum[0]) - yv;
+            sum[0] = tv;
+        }
+        double part = 0.0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) part += (double)sum[k] - (double)comp[k];
+        double d = block_reduce(part, OpAddD(), sd, 0.0);
         if (t == 0) B.pow_part[w] = d;
     }
 }
@@ -158,10 +177,10 @@ void launch_power(const DevBatch& B, const float* x, int grid, cudaStream_t st) 
 // Per utterance: gains from SNRs, L_max over its RIRs, and the FFT size N.
 // N minimises the cost of Eq. 6 (ceiling block count, one hop shared by all
 // (i, j) of the utterance: hop = N - L_max + 1) weighted by the per-size cost
-// table; N must satisfy L_max - 1 <= hop so an output block's tail only
-// reaches into the next block.  Then per FFT size it writes the lists of
+// table; N must leave hop >= N/4 (a block's tail may then reach several
+// blocks ahead; the forward carries it).  Then per FFT size it writes the lists of
 // spectrum jobs (RIRs), forward tiles (segments) and backward tiles
-// (backward segments), in utterance order, and resets the queue cursors.
+// (backward segment, source), in utterance order, and resets the queue cursors.
 constexpr int kPlanThreads = 1024;
 
 __device__ __forceinline__ int block_exscan(int v, int* sm, int* total) {
@@ -235,7 +254,7 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
             if (!((B.mask >> m) & 1)) continue;
             const int64_t N = 1LL << m;
             const int64_t hop = N - lmax + 1;
-            if (lmax - 1 > hop) continue;              // tail must fit in one hop
+            if (4 * hop < N) continue;                 // hop >= N/4 keeps blocks useful
             if (N > B.seg_len || N > B.bseg_len) continue;
             const int64_t nb = (nx + hop - 1) / hop;
             const double c = ((double)nb * (I + J) + (double)I * J) * (double)B.tuning[m];
@@ -258,7 +277,7 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
         for (int u = u0; u < u1; ++u) {
             if (B.logN[u] != m) continue;
             cf += B.seg0[u + 1] - B.seg0[u];
-            cb += B.bseg0[u + 1] - B.bseg0[u];
+            cb += (B.bseg0[u + 1] - B.bseg0[u]) * B.n_src[u];
             cs += B.rir0[u + 1] - B.rir0[u];
         }
         int tf, tb, ts;
@@ -271,7 +290,8 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
         for (int u = u0; u < u1; ++u) {
             if (B.logN[u] != m) continue;
             for (int g = B.seg0[u]; g < B.seg0[u + 1]; ++g) lf[of++] = g;
-            for (int g = B.bseg0[u]; g < B.bseg0[u + 1]; ++g) lb[ob++] = g;
+            for (int g = B.bseg0[u]; g < B.bseg0[u + 1]; ++g)
+                for (int i = 0; i < B.n_src[u]; ++i) lb[ob++] = g * kMaxSources + i;
             for (int r = B.rir0[u]; r < B.rir0[u + 1]; ++r) ls[os++] = r;
         }
         if (t == 0) {

@@ -75,7 +75,7 @@ def small_batch(seed=7, lengths=(1, 700, 20011, 50000, 70001), n_src=(1, 2, 3, 4
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("eta", [0.0, 10.0, 20.0, 30.0, math.inf])
 def test_truncation_lengths_exact(eta):
-    # without a cut-off the RIR itself must fit the largest FFT size (N/2+1 taps)
+    # without a cut-off the RIR itself must fit the largest FFT size (3N/4+1 taps)
     b = synth.config_home(n_utts=12) if math.isfinite(eta) else small_batch(rt60=(0.1, 0.5))
     _, res, _ = gpu_forward(b, eta=eta, seg=0)
     ref = oracle.truncate_batch(b, eta)
@@ -127,7 +127,7 @@ def test_forward_parity_each_fft_size(n):
     # short RIRs (eta = 10 dB) so every size is admissible
     b = small_batch(seed=11, lengths=(3, 1500, 9000, 33333), n_src=(2, 1, 4, 3), rt60=(0.1, 0.2))
     tr = oracle.truncate_batch(b, 10.0)
-    if tr["L"].max() > n // 2 + 1:
+    if tr["L"].max() > 3 * n // 4 + 1:
         pytest.skip("RIR too long for this size")
     g = np.linspace(0.5, 1.5, int(b.num_sources.sum())).astype(np.float32)
     plan, res, _ = gpu_forward(b, eta=10.0, fft_sizes=[n], gains=g)
@@ -157,6 +157,35 @@ def test_forward_edge_cases():
     _, res, _ = gpu_forward(b, eta=20.0, gains=g)
     ref = oracle.forward(b, 20.0, alpha=g.astype(np.float64))
     assert_channels_close(res["y"], ref["y"], b)
+
+
+def _long_tail_batch():
+    # RIRs of 2.5k-2.9k taps kept whole (eta = inf) with N = 4096: the hop
+    # (about 1.2k) is shorter than the tail, which then spans several blocks
+    return small_batch(seed=15, lengths=(9000, 40000, 70001), n_src=(2, 3, 1), rt60=(0.16, 0.18))
+
+
+def test_forward_tail_spanning_several_blocks():
+    b = _long_tail_batch()
+    g = np.linspace(0.4, 1.2, int(b.num_sources.sum())).astype(np.float32)
+    plan, res, _ = gpu_forward(b, eta=math.inf, fft_sizes=[4096], seg=16384, gains=g)
+    q = plan.query()
+    assert np.all(q["l_max"] - 1 > q["hop"])           # the regime under test
+    ref = oracle.forward(b, math.inf, alpha=g.astype(np.float64))
+    assert_channels_close(res["y"], ref["y"], b)
+
+
+def test_backward_tail_spanning_several_blocks():
+    b = _long_tail_batch()
+    S = int(b.num_sources.sum())
+    gains = np.linspace(0.4, 1.2, S).astype(np.float32)
+    gy = synth.grad_like(23, b.y_size)
+    _, gx, gr, gg = gpu_backward(b, math.inf, gains, gy, seg=16384, fft_sizes=[4096], bseg=16384)
+    L = oracle.truncate_batch(b, math.inf)["L"]
+    ref = oracle.backward(b, L, gains.astype(np.float64), gy)
+    _close_vec(gx, ref["dx"], REL_L2, "dx")
+    _close_vec(gr, ref["dh"], REL_L2, "dh")
+    np.testing.assert_allclose(gg, ref["dalpha"], rtol=REL_L2, atol=REL_L2 * np.abs(ref["dalpha"]).max())
 
 
 def test_results_do_not_depend_on_segmentation():
@@ -268,7 +297,7 @@ def test_backward_each_fft_size():
     L = oracle.truncate_batch(b, 10.0)["L"]
     ref = oracle.backward(b, L, gains.astype(np.float64), gy)
     for n in [2048, 4096, 8192, 16384]:
-        if L.max() > n // 2 + 1:
+        if L.max() > 3 * n // 4 + 1:
             continue
         _, gx, gr, gg = gpu_backward(b, 10.0, gains, gy, fft_sizes=[n])
         _close_vec(gx, ref["dx"], REL_L2, f"dx N={n}")
