@@ -71,6 +71,9 @@ typedef struct {
                                       raised to the largest allowed N */
     const float *fft_cost;         /* [32] host, relative cost of one real FFT of size 2^m
                                       used to pick N per utterance; NULL = N log2 N */
+    int32_t disable_graphs;        /* 0: each call replays a CUDA graph of its launch sequence,
+                                      captured on the first call with a given set of buffer
+                                      pointers; 1: launch eagerly */
 } rsim_plan_desc;
 
 /* Creates a plan for the given shapes on CUDA device `device`.  Validates the
@@ -92,7 +95,11 @@ rsim_status rsim_plan(const rsim_plan_desc *desc, int device, rsim_plan_t *out);
  *   trunc_len         [R] int32 kept lengths L (Eq. 9), or NULL
  *   energy_kept_frac  [R] sum_{n<L} h^2 / sum_n h^2, or NULL
  * The call is asynchronous.  The plan keeps the truncation lengths, the FFT
- * sizes and the RIR spectra for the next rsim_filter_mix_backward. */
+ * sizes and the RIR spectra for the next rsim_filter_mix_backward.  Unless
+ * the plan disables graphs (or stage timing is on), the first call with a
+ * given set of pointers captures the launch sequence into a CUDA graph and
+ * every call replays it on `stream`; the capture itself runs on a stream of
+ * the plan, so `stream` may be the legacy default stream. */
 rsim_status rsim_filter_mix(rsim_plan_t plan, void *stream, const float *x, const float *rir,
                             const float *snr_db, float *gains, float *y, int32_t *trunc_len,
                             float *energy_kept_frac);

@@ -42,6 +42,7 @@ class PlanDesc(ctypes.Structure):
         ("segment_len", ctypes.c_int64),
         ("bwd_segment_len", ctypes.c_int64),
         ("fft_cost", ctypes.c_void_p),
+        ("disable_graphs", ctypes.c_int32),
     ]
 
 

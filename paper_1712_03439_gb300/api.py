@@ -39,7 +39,7 @@ class Plan:
 
     def __init__(self, num_sources, num_samples, rir_len, num_mics, eta_db=20.0,
                  fft_sizes=None, gain_mode=0, segment_len=0, bwd_segment_len=0, fft_cost=None,
-                 device=None):
+                 device=None, graphs=True):
         self._lib = _lib.load()
         self._handle = None
         self.num_sources = np.ascontiguousarray(num_sources, dtype=np.int32)
@@ -78,7 +78,8 @@ class Plan:
             rir_len=self.rir_len.ctypes.data, eta_db=self.eta_db, fft_sizes_mask=mask,
             gain_mode=self.gain_mode, segment_len=int(segment_len),
             bwd_segment_len=int(bwd_segment_len),
-            fft_cost=None if self._cost is None else self._cost.ctypes.data)
+            fft_cost=None if self._cost is None else self._cost.ctypes.data,
+            disable_graphs=0 if graphs else 1)
         h = ctypes.c_void_p()
         _lib.check(self._lib, self._lib.rsim_plan(ctypes.byref(desc), self.device, ctypes.byref(h)))
         self._handle = h

@@ -80,6 +80,11 @@ std::vector<float2> twiddle_table_for(int logN, int E) {
 
 constexpr int kRing = 64;
 
+struct GraphCache {
+    const void* key[8] = {};
+    cudaGraphExec_t exec = nullptr;
+};
+
 struct StageTimer {
     bool on = false;
     int count[RSIM_NUM_STAGES] = {};
@@ -110,6 +115,10 @@ struct rsim_plan_s {
     cudaStream_t bs[kNumBuckets] = {};
     cudaEvent_t ev_fork = nullptr;
     cudaEvent_t ev_join[kNumBuckets] = {};
+    // CUDA graphs of the forward and backward sequences (replayed per call)
+    bool use_graphs = true;
+    cudaStream_t cap = nullptr;     // capture stream
+    GraphCache gfwd, gbwd;
 };
 
 namespace {
@@ -161,6 +170,9 @@ extern "C" void rsim_plan_destroy(rsim_plan_t plan) {
             if (plan->ev_join[b]) cudaEventDestroy(plan->ev_join[b]);
         }
         if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
+        if (plan->gfwd.exec) cudaGraphExecDestroy(plan->gfwd.exec);
+        if (plan->gbwd.exec) cudaGraphExecDestroy(plan->gbwd.exec);
+        if (plan->cap) cudaStreamDestroy(plan->cap);
         if (plan->dmem) cudaFree(plan->dmem);
     }
     delete plan;
@@ -417,7 +429,9 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     }
     p->grid_trunc = (int)std::max<int64_t>(1, std::min<int64_t>(R, (int64_t)p->sms * 8));
     p->grid_pow = (int)std::max<int64_t>(1, std::min<int64_t>(S * CH, (int64_t)p->sms * 8));
-    e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+    p->use_graphs = d->disable_graphs == 0;
+    e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
     for (int m = kMinLog; m <= kMaxLog && e == cudaSuccess; ++m) {
         if (!((mask >> m) & 1)) continue;
         const int b = m - kMinLog;
@@ -437,15 +451,12 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     return RSIM_OK;
 }
 
-extern "C" rsim_status rsim_filter_mix(rsim_plan_t p, void* stream, const float* x, const float* rir,
-                                       const float* snr_db, float* gains, float* y, int32_t* trunc_len,
-                                       float* energy_kept_frac) {
-    g_err.clear();
-    if (!p) return fail(RSIM_E_INVALID, "NULL plan");
-    if (!x || !rir || !gains || !y) return fail(RSIM_E_INVALID, "x, rir, gains and y are required");
-    if (p->gain_mode == 0 && !snr_db) return fail(RSIM_E_INVALID, "snr_db is required when gain_mode = 0");
-    DeviceGuard guard(p->device);
-    cudaStream_t st = (cudaStream_t)stream;
+namespace {
+
+// The forward launch sequence on stream st (eager, or recorded by a capture).
+cudaError_t enqueue_forward(rsim_plan_t p, cudaStream_t st, const float* x, const float* rir,
+                            const float* snr_db, float* gains, float* y, int32_t* trunc_len,
+                            float* energy_kept_frac) {
     const DevBatch& B = p->B;
     stage_mark(p, 0, false, st);
     launch_truncate(B, rir, p->factor, p->none, energy_kept_frac, p->grid_trunc, st);
@@ -474,9 +485,73 @@ extern "C" rsim_status rsim_filter_mix(rsim_plan_t p, void* stream, const float*
     stage_mark(p, 5, true, st);
     if (trunc_len) {
         cudaError_t e = cudaMemcpyAsync(trunc_len, B.L, sizeof(int32_t) * B.R, cudaMemcpyDeviceToDevice, st);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync (trunc_len)");
+        if (e != cudaSuccess) return e;
     }
-    cudaError_t e = cudaGetLastError();
+    return cudaGetLastError();
+}
+
+// The backward launch sequence on stream st.
+cudaError_t enqueue_backward(rsim_plan_t p, cudaStream_t st, const float* grad_y, const float* x,
+                             const float* gains, float* grad_x, float* grad_rir, float* grad_gains) {
+    const DevBatch& B = p->B;
+    cudaError_t e = cudaMemsetAsync(p->Q.next + p->Q.idx(kListBwd, 0), 0, sizeof(int32_t) * kNumBuckets, st);
+    if (e != cudaSuccess) return e;
+    stage_mark(p, 6, false, st);
+    fan_out(p, st, [&](int m, cudaStream_t s) {
+        launch_backward(m, B, p->Q, grad_y, x, gains, p->Hc, grad_x, p->dhp, p->dap,
+                        p->tw[m - kMinLog], p->grid_bwd[m - kMinLog], s);
+    });
+    stage_mark(p, 6, true, st);
+    stage_mark(p, 7, false, st);
+    launch_finalize(B, gains, p->dhp, p->dap, grad_rir, grad_gains, st);
+    stage_mark(p, 7, true, st);
+    return cudaGetLastError();
+}
+
+// Runs `enqueue` through a CUDA graph captured once per set of buffer
+// pointers (key), then replayed on st; eager when graphs are off or stage
+// timing is on.
+template <typename F>
+cudaError_t run_graph(rsim_plan_t p, GraphCache& gc, const void* const (&key)[8], cudaStream_t st, F enqueue) {
+    if (!p->use_graphs || p->timer.on) return enqueue(st);
+    bool hit = gc.exec != nullptr;
+    for (int k = 0; k < 8 && hit; ++k) hit = gc.key[k] == key[k];
+    if (!hit) {
+        if (gc.exec) {
+            cudaGraphExecDestroy(gc.exec);
+            gc.exec = nullptr;
+        }
+        cudaError_t e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        cudaError_t le = enqueue(p->cap);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(p->cap, &graph);
+        if (le != cudaSuccess) e = le;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&gc.exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            gc.exec = nullptr;
+            return e;
+        }
+        for (int k = 0; k < 8; ++k) gc.key[k] = key[k];
+    }
+    return cudaGraphLaunch(gc.exec, st);
+}
+
+}  // namespace
+
+extern "C" rsim_status rsim_filter_mix(rsim_plan_t p, void* stream, const float* x, const float* rir,
+                                       const float* snr_db, float* gains, float* y, int32_t* trunc_len,
+                                       float* energy_kept_frac) {
+    g_err.clear();
+    if (!p) return fail(RSIM_E_INVALID, "NULL plan");
+    if (!x || !rir || !gains || !y) return fail(RSIM_E_INVALID, "x, rir, gains and y are required");
+    if (p->gain_mode == 0 && !snr_db) return fail(RSIM_E_INVALID, "snr_db is required when gain_mode = 0");
+    DeviceGuard guard(p->device);
+    const void* const key[8] = {x, rir, snr_db, gains, y, trunc_len, energy_kept_frac, nullptr};
+    cudaError_t e = run_graph(p, p->gfwd, key, (cudaStream_t)stream, [&](cudaStream_t s) {
+        return enqueue_forward(p, s, x, rir, snr_db, gains, y, trunc_len, energy_kept_frac);
+    });
     if (e != cudaSuccess) return cuda_fail(e, "forward launch");
     p->fwd_done = true;
     return RSIM_OK;
@@ -491,20 +566,10 @@ extern "C" rsim_status rsim_filter_mix_backward(rsim_plan_t p, void* stream, con
     if (!grad_y || !x || !gains || !grad_rir || !grad_gains)
         return fail(RSIM_E_INVALID, "grad_y, x, gains, grad_rir and grad_gains are required");
     DeviceGuard guard(p->device);
-    cudaStream_t st = (cudaStream_t)stream;
-    const DevBatch& B = p->B;
-    cudaError_t e = cudaMemsetAsync(p->Q.next + p->Q.idx(kListBwd, 0), 0, sizeof(int32_t) * kNumBuckets, st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (queue)");
-    stage_mark(p, 6, false, st);
-    fan_out(p, st, [&](int m, cudaStream_t s) {
-        launch_backward(m, B, p->Q, grad_y, x, gains, p->Hc, grad_x, p->dhp, p->dap,
-                        p->tw[m - kMinLog], p->grid_bwd[m - kMinLog], s);
+    const void* const key[8] = {grad_y, x, gains, grad_x, grad_rir, grad_gains, nullptr, nullptr};
+    cudaError_t e = run_graph(p, p->gbwd, key, (cudaStream_t)stream, [&](cudaStream_t s) {
+        return enqueue_backward(p, s, grad_y, x, gains, grad_x, grad_rir, grad_gains);
     });
-    stage_mark(p, 6, true, st);
-    stage_mark(p, 7, false, st);
-    launch_finalize(B, gains, p->dhp, p->dap, grad_rir, grad_gains, st);
-    stage_mark(p, 7, true, st);
-    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "backward launch");
     return RSIM_OK;
 }

@@ -41,7 +41,7 @@ def _desc(**kw):
                       rir_len=rl.ctypes.data, eta_db=kw.pop("eta", 20.0),
                       fft_sizes_mask=kw.pop("mask", 0), gain_mode=kw.pop("gm", 0),
                       segment_len=kw.pop("seg", 0), bwd_segment_len=kw.pop("bseg", 0),
-                      fft_cost=None)
+                      fft_cost=None, disable_graphs=0)
     return d, (ns, nx, rl)
 
 

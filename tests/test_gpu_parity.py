@@ -198,6 +198,29 @@ def test_results_do_not_depend_on_segmentation():
     np.testing.assert_array_equal(ys[0], ys[2])
 
 
+def test_graph_replay_equals_eager_launch():
+    from paper_1712_03439_gb300 import Plan
+    b = small_batch(seed=16, lengths=(5000, 70000, 20000), n_src=(2, 1, 3))
+    S = int(b.num_sources.sum())
+    x, rir, snr = dev(b.x), dev(b.rir), dev(b.snr_db)
+    gy = dev(synth.grad_like(24, b.y_size))
+    outs = []
+    for graphs in (False, True):
+        plan = Plan.for_batch(b, eta_db=20.0, gain_mode=0, graphs=graphs)
+        gains = torch.empty(S, device="cuda")
+        y = torch.empty(b.y_size, device="cuda")
+        gx, gr, gg = torch.empty_like(x), torch.empty_like(rir), torch.empty(S, device="cuda")
+        for _ in range(3):                     # capture once, then replay
+            y.fill_(7.0)
+            gx.fill_(7.0)
+            plan.filter_mix(x, rir, gains, y, snr_db=snr)
+            plan.filter_mix_backward(gy, x, gains, gx, gr, gg)
+        plan.sync_status()
+        outs.append([t.cpu().numpy() for t in (y, gains, gx, gr, gg)])
+    for a, c in zip(*outs):
+        np.testing.assert_array_equal(a, c)
+
+
 def test_results_do_not_depend_on_utterance_order():
     b = small_batch(seed=14, lengths=(5000, 70000, 20000, 45000), n_src=(2, 1, 4, 3))
     perm = [2, 0, 3, 1]
