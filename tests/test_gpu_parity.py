@@ -359,3 +359,23 @@ def test_rir_too_long_for_allowed_sizes_is_reported():
     with pytest.raises(RsimError) as e:
         gpu_forward(b, eta=math.inf, fft_sizes=[2048], gains=np.ones(1, np.float32))
     assert e.value.status == 2
+
+
+# ---------------------------------------------------------------------------
+# microphone groups: J > 2 (8-mic circle as in the long-reverberation
+# workload, shortened) and an odd J
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("J", [3, 8])
+def test_forward_and_backward_many_mics(J):
+    b = small_batch(seed=40 + J, lengths=(20000, 47000), n_src=(4, 2), rt60=(0.1, 0.25), J=J)
+    S = int(b.num_sources.sum())
+    gains = np.linspace(0.5, 1.3, S).astype(np.float32)
+    gy = synth.grad_like(41, b.y_size)
+    res, gx, gr, gg = gpu_backward(b, 20.0, gains, gy, seg=16384, bseg=16384)
+    L = oracle.truncate_batch(b, 20.0)["L"]
+    ref = oracle.forward(b, 20.0, alpha=gains.astype(np.float64))
+    assert_channels_close(res["y"], ref["y"], b)
+    gref = oracle.backward(b, L, gains.astype(np.float64), gy)
+    _close_vec(gx, gref["dx"], REL_L2, "dx")
+    _close_vec(gr, gref["dh"], REL_L2, "dh")
+    np.testing.assert_allclose(gg, gref["dalpha"], rtol=REL_L2, atol=REL_L2 * np.abs(gref["dalpha"]).max())
