@@ -118,6 +118,8 @@ struct rsim_plan_s {
     // CUDA graphs of the forward and backward sequences (replayed per call)
     bool use_graphs = true;
     cudaStream_t cap = nullptr;     // capture stream
+    cudaStream_t aux = nullptr;     // side stream of the forward's first stage
+    cudaEvent_t ev_aux = nullptr;
     GraphCache gfwd, gbwd;
 };
 
@@ -173,6 +175,8 @@ extern "C" void rsim_plan_destroy(rsim_plan_t plan) {
         if (plan->gfwd.exec) cudaGraphExecDestroy(plan->gfwd.exec);
         if (plan->gbwd.exec) cudaGraphExecDestroy(plan->gbwd.exec);
         if (plan->cap) cudaStreamDestroy(plan->cap);
+        if (plan->aux) cudaStreamDestroy(plan->aux);
+        if (plan->ev_aux) cudaEventDestroy(plan->ev_aux);
         if (plan->dmem) cudaFree(plan->dmem);
     }
     delete plan;
@@ -431,6 +435,8 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     p->grid_pow = (int)std::max<int64_t>(1, std::min<int64_t>(S * CH, (int64_t)p->sms * 8));
     p->use_graphs = d->disable_graphs == 0;
     e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_aux, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
     for (int m = kMinLog; m <= kMaxLog && e == cudaSuccess; ++m) {
         if (!((mask >> m) & 1)) continue;
@@ -458,13 +464,23 @@ cudaError_t enqueue_forward(rsim_plan_t p, cudaStream_t st, const float* x, cons
                             const float* snr_db, float* gains, float* y, int32_t* trunc_len,
                             float* energy_kept_frac) {
     const DevBatch& B = p->B;
-    stage_mark(p, 0, false, st);
-    launch_truncate(B, rir, p->factor, p->none, energy_kept_frac, p->grid_trunc, st);
-    stage_mark(p, 0, true, st);
-    if (p->gain_mode == 0) {
-        stage_mark(p, 1, false, st);
-        launch_power(B, x, p->grid_pow, st);
-        stage_mark(p, 1, true, st);
+    if (p->gain_mode == 0 && !p->timer.on) {
+        // source powers (reads x) run beside the RIR scan (reads rir)
+        cudaEventRecord(p->ev_fork, st);
+        cudaStreamWaitEvent(p->aux, p->ev_fork, 0);
+        launch_power(B, x, p->grid_pow, p->aux);
+        cudaEventRecord(p->ev_aux, p->aux);
+        launch_truncate(B, rir, p->factor, p->none, energy_kept_frac, p->grid_trunc, st);
+        cudaStreamWaitEvent(st, p->ev_aux, 0);
+    } else {
+        stage_mark(p, 0, false, st);
+        launch_truncate(B, rir, p->factor, p->none, energy_kept_frac, p->grid_trunc, st);
+        stage_mark(p, 0, true, st);
+        if (p->gain_mode == 0) {
+            stage_mark(p, 1, false, st);
+            launch_power(B, x, p->grid_pow, st);
+            stage_mark(p, 1, true, st);
+        }
     }
     stage_mark(p, 2, false, st);
     launch_plan(B, p->Q, snr_db, gains, st);

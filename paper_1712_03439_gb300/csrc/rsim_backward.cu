@@ -50,7 +50,8 @@ __device__ __forceinline__ double block_sum_d(double v, double* sd) {
 //                                                          pre-processing of the last mic
 //       W_j += conj(X) G_j                                 registers, kept across
 //                                                          the segment
-//   c = irFFT_N(C)[0, hop): dx_i = alpha_i c, dalpha_i += <c, x_i>
+//   c = irFFT_N(C)[0, hop): dx_i = alpha_i c, dalpha_i += <c, x_i> (computed
+//   as sum_k C[k] conj(X[k]) on the spectra, by Parseval)
 // and at the end of the segment dh partial_ij = irFFT_N(W_j)[0, L_ij).
 // Every transform input (x block, g windows) is prefetched with cp.async into
 // a shared-memory stage while the previous transform runs; the source's RIR
@@ -113,7 +114,7 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
         const float a = __ldg(gains + sb + i);
         const float* xi = x + B.xoff[sb + i];
         float* dxi = dx ? dx + B.xoff[sb + i] : nullptr;
-        float da = 0.f, dac = 0.f;   // Kahan sum of c * x
+        float da = 0.f;              // <c, x_i> over the segment
         for (int j0 = 0; j0 < J; j0 += kJG) {
             const int jn = min(kJG, J - j0);
             auto stage_x = [&](int64_t b) {
@@ -193,23 +194,29 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
                         W[jj][2 * q + 1] = cadd(W[jj][2 * q + 1], cmulc(X[2 * q + 1], gb));
                     }
                 }
+                // <c, x_block> by Parseval on the half spectra already in registers
+                // (x_block is zero beyond its length, so only n < hop counts):
+                // sum_n c x = sum_k C[k] conj(X[k]) over all N bins, i.e. bins 0
+                // and N/2 once and every other bin of the half spectrum twice.
+#pragma unroll
+                for (int q = 0; q < E / 2; ++q) {
+                    const int k = t + q * T;
+                    const float p0 = C[2 * q].x * X[2 * q].x + C[2 * q].y * X[2 * q].y;
+                    const float p1 = C[2 * q + 1].x * X[2 * q + 1].x + C[2 * q + 1].y * X[2 * q + 1].y;
+                    da += (k == 0 ? p0 : 2.f * p0) + 2.f * p1;
+                }
                 irfft_pairs<M, E>(v, C, sm, tw, t);
+                if (dxi) {
 #pragma unroll
-                for (int q = 0; q < E; ++q) {
-                    const int n = 2 * (t + q * T);
+                    for (int q = 0; q < E; ++q) {
+                        const int n = 2 * (t + q * T);
 #pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const int nn = n + e;
-                        if (nn < hop && nn < lim) {
-                            const float c = e ? v[q].y : v[q].x;
-                            if (dxi) {
-                                const float d = a * c;
+                        for (int e = 0; e < 2; ++e) {
+                            const int nn = n + e;
+                            if (nn < hop && nn < lim) {
+                                const float d = a * (e ? v[q].y : v[q].x);
                                 dxi[pos + nn] = (j0 == 0) ? d : dxi[pos + nn] + d;
                             }
-                            const float yv = fmaf(c, __ldg(xi + pos + nn), -dac);
-                            const float tv = da + yv;
-                            dac = (tv - da) - yv;
-                            da = tv;
                         }
                     }
                 }
@@ -231,7 +238,7 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
                 }
             }
         }
-        const double tot = block_sum_d((double)da - (double)dac, sd);
+        const double tot = block_sum_d((double)da, sd);
         if (t == 0) dap[(int64_t)g * kMaxSources + i] = (float)tot;
     }
     cp_async_wait<0>();

@@ -136,28 +136,33 @@ k_power(DevBatch B, const float* __restrict__ x) {
         const int64_t c0 = (int64_t)c * kPowerChunk;
         if (c0 >= nx) continue;                 // uniform across the CTA
         const int64_t c1 = (c0 + kPowerChunk < nx) ? c0 + kPowerChunk : nx;
-        const float* p = x + B.xoff[s];
-        // four independent compensated sums keep several loads in flight
+        const float* p = x + B.xoff[s] + c0;
+        const int64_t len = c1 - c0;
+        // scalar head up to 16-byte alignment, float4 body, scalar tail; four
+        // independent compensated sums (one per float4 lane) keep loads in flight
+        int64_t head = (int64_t)(((16u - ((uintptr_t)p & 15u)) & 15u) >> 2);
+        if (head > len) head = len;
+        const int64_t nvec = (len - head) >> 2;
+        const int64_t tail0 = head + 4 * nvec;
         float sum[4] = {0.f, 0.f, 0.f, 0.f}, comp[4] = {0.f, 0.f, 0.f, 0.f};
-        int64_t i = c0 + t;
-        for (; i + 3 * kPowThreads < c1; i += 4 * kPowThreads) {
-            float v[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) v[k] = __ldg(p + i + k * kPowThreads);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float yv = fmaf(v[k], v[k], -comp[k]);
-                const float tv = sum[k] + yv;
-                comp[k] = (tv - sum[k]) - yv;
-                sum[k] = tv;
-            }
+        auto acc = [&](int k, float v) {
+            const float yv = fmaf(v, v, -comp[k]);
+            const float tv = sum[k] + yv;
+            comp[k] = (tv - sum[k]) - yv;
+            sum[k] = tv;
+        };
+        for (int64_t i = t; i < head; i += kPowThreads) acc(0, __ldg(p + i));
+        for (int64_t i = tail0 + t; i < len; i += kPowThreads) acc(1, __ldg(p + i));
+        const float4* p4 = reinterpret_cast<const float4*>(p + head);
+        int64_t j = t;
+        for (; j + kPowThreads < nvec; j += 2 * kPowThreads) {
+            const float4 a = __ldg(p4 + j), b = __ldg(p4 + j + kPowThreads);
+            acc(0, a.x); acc(1, a.y); acc(2, a.z); acc(3, a.w);
+            acc(0, b.x); acc(1, b.y); acc(2, b.z); acc(3, b.w);
         }
-        for (; i < c1; i += kPowThreads) {
-            const float v = __ldg(p + i);
-            const float yv = fmaf(v, v, -comp[0]);
-            const float tv = sum[0] + yv;
-            comp[0] = (tv - sum[0]) - yv;
-            sum[0] = tv;
+        for (; j < nvec; j += kPowThreads) {
+            const float4 a = __ldg(p4 + j);
+            acc(0, a.x); acc(1, a.y); acc(2, a.z); acc(3, a.w);
         }
         double part = 0.0;
 #pragma unroll
