@@ -60,7 +60,7 @@ __device__ __forceinline__ double block_sum_d(double v, double* sd) {
 // per group; dx of later groups is added to the first group's).
 template <int M>
 struct BwdCfg {
-    static constexpr int E = e_for(M);
+    static constexpr int E = M == 4096 ? 16 : e_for(M);
     static constexpr int T = M / E;
     static constexpr bool kStageH = M <= 4096;
     static constexpr bool kTwSmem = M <= 4096;
