@@ -54,21 +54,28 @@ __device__ __forceinline__ double block_sum_d(double v, double* sd) {
 //   as sum_k C[k] conj(X[k]) on the spectra, by Parseval)
 // and at the end of the segment dh partial_ij = irFFT_N(W_j)[0, L_ij).
 // Every transform input (x block, g windows) is prefetched with cp.async into
-// a shared-memory stage while the previous transform runs; the source's RIR
-// spectra are staged once per tile; twiddles are copied to shared memory once
-// per CTA.  Microphones go in groups of kJG (the source spectrum is recomputed
-// per group; dx of later groups is added to the first group's).
+// one of NST shared-memory stages while the previous transform runs; with two
+// stages the copy's completion is folded into the last barrier of that
+// transform.  Transform exchanges alternate between NSM buffers (one barrier
+// per exchange when NSM = 2).  The source's RIR spectra are staged once per
+// tile; twiddles are copied to shared memory once per CTA.  Microphones go in
+// groups of kJG (the source spectrum is recomputed per group; dx of later
+// groups is added to the first group's).
 template <int M>
 struct BwdCfg {
     static constexpr int E = M == 4096 ? 16 : e_for(M);
     static constexpr int T = M / E;
+    static constexpr int NSM = M <= 4096 ? 2 : 1;    // exchange buffers
+    static constexpr int NST = M == 2048 ? 1 : 2;    // input stages
     static constexpr bool kStageH = M <= 4096;
     static constexpr bool kTwSmem = M <= 4096;
     static constexpr int kMinBlocks = M <= 2048 ? 2 : 1;
     static constexpr size_t a16(size_t v) { return (v + 15) / 16 * 16; }
+    static constexpr size_t SM_LEN = a16(sizeof(float2) * padded_len(M));
+    static constexpr size_t ST_LEN = sizeof(float) * 2 * M;
     static constexpr size_t o_sm = 0;
-    static constexpr size_t o_st = a16(o_sm + sizeof(float2) * padded_len(M));
-    static constexpr size_t o_hs = a16(o_st + sizeof(float) * 2 * M);
+    static constexpr size_t o_st = o_sm + NSM * SM_LEN;
+    static constexpr size_t o_hs = a16(o_st + NST * ST_LEN);
     static constexpr size_t o_tw = a16(o_hs + (kStageH ? sizeof(float2) * kJG * M : 0));
     static constexpr size_t bytes = a16(o_tw + (kTwSmem ? sizeof(float2) * FftPlan<M, E>::TW_LEN : 0));
 };
@@ -81,10 +88,13 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
     using L = BwdCfg<M>;
     constexpr int E = L::E;
     constexpr int T = L::T;
+    constexpr int NST = L::NST;
+    constexpr bool kWait = NST == 2;      // stage completion folded into the transforms
     using Pl = FftPlan<M, E>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* sm = reinterpret_cast<float2*>(smem_raw + L::o_sm);
-    float* st = reinterpret_cast<float*>(smem_raw + L::o_st);
+    Exch<L::NSM> ex{reinterpret_cast<float2*>(smem_raw + L::o_sm),
+                    reinterpret_cast<float2*>(smem_raw + L::o_sm + (L::NSM - 1) * L::SM_LEN), 0};
+    float* st0 = reinterpret_cast<float*>(smem_raw + L::o_st);
     float2* hs = reinterpret_cast<float2*>(smem_raw + L::o_hs);
     __shared__ double sd[32];
     __shared__ int slot;
@@ -97,6 +107,8 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
         tw = tws;
     }
     const float2* wsplit = tw + Pl::OFF_SPLIT;
+    int sc = 0;                                  // stage holding the next transform input
+    auto stage = [&](int k) { return st0 + (NST == 2 ? k : 0) * (2 * M); };
     for (;;) {
         const int code = pop_job_b(Q, kListBwd, bucket, &slot);
         if (code < 0) break;
@@ -117,62 +129,65 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
         float da = 0.f;              // <c, x_i> over the segment
         for (int j0 = 0; j0 < J; j0 += kJG) {
             const int jn = min(kJG, J - j0);
-            auto stage_x = [&](int64_t b) {
+            auto stage_x = [&](float* dst, int64_t b) {
                 const int64_t p = b * hop;
-                stage_real_async<M, E>(st, xi + p, min((int64_t)hop, nx - p), t);
+                stage_real_async<M, E>(dst, xi + p, min((int64_t)hop, nx - p), t);
             };
-            auto stage_g = [&](int64_t b, int j) {
+            auto stage_g = [&](float* dst, int64_t b, int j) {
                 const int64_t p = b * hop;
-                stage_real_async<M, E>(st, gy + B.yoff[u] + (int64_t)j * nx + p,
+                stage_real_async<M, E>(dst, gy + B.yoff[u] + (int64_t)j * nx + p,
                                        min((int64_t)(hop + lmax - 1), nx - p), t);
+            };
+            // takes the staged input into v and queues the next one (if any) into the other stage
+            auto next_input = [&](float2 (&v)[E], int64_t b, int nj) {
+                if constexpr (NST == 1) {
+                    cp_async_wait<0>();
+                    __syncthreads();
+                }
+                load_staged_strided<M, E>(v, stage(sc), t);
+                if constexpr (NST == 1) __syncthreads();
+                if (nj >= 0) stage_g(stage(sc ^ 1), b, nj);
+                else if (b + 1 < b1) stage_x(stage(sc ^ 1), b + 1);
+                cp_async_commit();
+                sc ^= (NST - 1);
             };
             float2 W[kJG][E];
 #pragma unroll
             for (int jj = 0; jj < kJG; ++jj)
 #pragma unroll
                 for (int e = 0; e < E; ++e) W[jj][e] = make_float2(0.f, 0.f);
-            __syncthreads();                     // stage and spectra are free
+            __syncthreads();                     // stages and spectra are free
             if constexpr (L::kStageH) {
                 for (int jj = 0; jj < jn; ++jj)
                     stage_spectrum_async<M, E>(hs + jj * M, Hc + (int64_t)(rb + i * J + j0 + jj) * B.MMAX, t);
             }
-            stage_x(b0);
+            stage_x(stage(sc), b0);
             cp_async_commit();
+            cp_async_wait<0>();
+            __syncthreads();
             for (int64_t b = b0; b < b1; ++b) {
                 const int64_t pos = b * hop;
                 const int64_t lim = nx - pos;
                 // source block
-                cp_async_wait<0>();
-                __syncthreads();
                 float2 v[E];
-                load_staged_strided<M, E>(v, st, t);
-                __syncthreads();
-                stage_g(b, j0);
-                cp_async_commit();
-                rfft_regs_to_smem<M, E>(v, sm, tw, t);
+                next_input(v, b, j0);
                 float2 X[E];
-                split_forward<M, E>(X, sm, wsplit, t);
+                split_forward<M, E>(X, rfft_x<M, E, kWait>(v, ex, tw, t), wsplit, t);
                 float2 C[E];
 #pragma unroll
                 for (int e = 0; e < E; ++e) C[e] = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int jj = 0; jj < kJG; ++jj) {
                     if (jj >= jn) break;
-                    cp_async_wait<0>();
-                    __syncthreads();
-                    load_staged_strided<M, E>(v, st, t);
-                    __syncthreads();
-                    if (jj + 1 < jn) stage_g(b, j0 + jj + 1);
-                    else if (b + 1 < b1) stage_x(b + 1);
-                    cp_async_commit();
-                    rfft_regs_to_smem<M, E>(v, sm, tw, t);
+                    next_input(v, b, jj + 1 < jn ? j0 + jj + 1 : -1);
+                    const float2* z = rfft_x<M, E, kWait>(v, ex, tw, t);
                     const float2* Hg = Hc + (int64_t)(rb + i * J + j0 + jj) * B.MMAX;
 #pragma unroll
                     for (int q = 0; q < E / 2; ++q) {
                         const int k = t + q * T;
                         const int kb = (k == 0) ? M / 2 : M - k;
                         float2 ga, gb;
-                        split_pair<M>(sm, wsplit, k, ga, gb);
+                        split_pair<M>(z, wsplit, k, ga, gb);
                         float2 ha, hb;
                         if constexpr (L::kStageH) {
                             ha = hs[jj * M + k];
@@ -205,7 +220,7 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
                     const float p1 = C[2 * q + 1].x * X[2 * q + 1].x + C[2 * q + 1].y * X[2 * q + 1].y;
                     da += (k == 0 ? p0 : 2.f * p0) + 2.f * p1;
                 }
-                irfft_pairs<M, E>(v, C, sm, tw, t);
+                irfft_x<M, E, false>(v, C, ex, tw, t);
                 if (dxi) {
 #pragma unroll
                     for (int q = 0; q < E; ++q) {
@@ -226,7 +241,7 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
             for (int jj = 0; jj < kJG; ++jj) {
                 if (jj >= jn) break;
                 float2 v[E];
-                irfft_pairs<M, E>(v, W[jj], sm, tw, t);
+                irfft_x<M, E, false>(v, W[jj], ex, tw, t);
                 const int r = rb + i * J + j0 + jj;
                 const int Lr = B.L[r];
                 float* out = dhp + B.dhp_off[g] + (B.roff[r] - B.roff[rb]);

@@ -470,4 +470,74 @@ __device__ __forceinline__ void irfft_pairs(float2 (&v)[E], const float2 (&P)[E]
     for (int s = 0; s < E; ++s) v[s] = conjf2(v[s]);
 }
 
+// ---------------------------------------------------------------------------
+// alternating exchange buffers
+// ---------------------------------------------------------------------------
+// Every shared-memory exchange of a transform is "write buffer, barrier, read
+// buffer".  With two buffers used in strict alternation by every exchange of
+// a kernel, the buffer an exchange writes was last read two exchanges earlier,
+// before the previous exchange's barrier, so one barrier per exchange is
+// enough.  With NB = 1 both slots are the same buffer and each exchange adds
+// the barrier that protects its write.
+template <int NB>
+struct Exch {
+    float2* b0;
+    float2* b1;
+    int c;
+    __device__ __forceinline__ float2* begin() {
+        if constexpr (NB == 1) __syncthreads();
+        return c ? b1 : b0;
+    }
+    __device__ __forceinline__ void end() {
+        if constexpr (NB == 2) c ^= 1;
+    }
+};
+
+template <int M, int E, int P, int NB>
+__device__ __forceinline__ void fft_from_x(float2 (&v)[E], Exch<NB>& ex, const float2* __restrict__ tw, int t) {
+    using Pl = FftPlan<M, E>;
+    constexpr int R = Pl::radix(P), LP = Pl::lp(P);
+    if constexpr (P == Pl::NPASS - 1) {
+        fft_pass<M, E, R, LP, true>(v, nullptr, tw + Pl::tw_off(P), t);
+    } else {
+        float2* b = ex.begin();
+        fft_pass<M, E, R, LP, false>(v, b, tw + Pl::tw_off(P), t);
+        __syncthreads();
+        load_strided<M, E>(v, b, t);
+        ex.end();
+        fft_from_x<M, E, P + 1, NB>(v, ex, tw, t);
+    }
+}
+
+// Forward FFT of strided registers v; returns the buffer holding the spectrum
+// in natural order (read it with split_pair before the second exchange after
+// this one).  With WAIT, the caller's outstanding cp.async groups complete
+// before the last barrier, so data staged before the call is visible after it.
+template <int M, int E, bool WAIT, int NB>
+__device__ __forceinline__ const float2* rfft_x(float2 (&v)[E], Exch<NB>& ex, const float2* __restrict__ tw, int t) {
+    fft_from_x<M, E, 0, NB>(v, ex, tw, t);
+    float2* b = ex.begin();
+    store_strided<M, E>(v, b, t);
+    if constexpr (WAIT) cp_async_wait<0>();
+    __syncthreads();
+    ex.end();
+    return b;
+}
+
+// Unnormalised inverse real FFT of a half spectrum in pair layout (see
+// irfft_pairs); WAIT as for rfft_x.
+template <int M, int E, bool WAIT, int NB>
+__device__ __forceinline__ void irfft_x(float2 (&v)[E], const float2 (&P)[E], Exch<NB>& ex,
+                                        const float2* __restrict__ tw, int t) {
+    float2* b = ex.begin();
+    split_inverse_store<M, E>(P, b, tw + FftPlan<M, E>::OFF_SPLIT, t);
+    if constexpr (WAIT) cp_async_wait<0>();
+    __syncthreads();
+    load_strided<M, E>(v, b, t);
+    ex.end();
+    fft_from_x<M, E, 0, NB>(v, ex, tw, t);
+#pragma unroll
+    for (int s = 0; s < E; ++s) v[s] = conjf2(v[s]);
+}
+
 }  // namespace rsim
