@@ -80,6 +80,8 @@ struct BwdCfg {
     static constexpr size_t bytes = a16(o_tw + (kTwSmem ? sizeof(float2) * FftPlan<M, E>::TW_LEN : 0));
 };
 
+static_assert(kJG == 2, "the backward tile loop is written for microphone pairs");
+
 template <int M>
 __global__ void __launch_bounds__(BwdCfg<M>::T, BwdCfg<M>::kMinBlocks)
 k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const float* __restrict__ x,
@@ -90,6 +92,7 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
     constexpr int T = L::T;
     constexpr int NST = L::NST;
     constexpr bool kWait = NST == 2;      // stage completion folded into the transforms
+    constexpr bool kRollSteps = L::NSM == 2;
     using Pl = FftPlan<M, E>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Exch<L::NSM> ex{reinterpret_cast<float2*>(smem_raw + L::o_sm),
@@ -165,49 +168,53 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
             cp_async_commit();
             cp_async_wait<0>();
             __syncthreads();
+            // C += conj(H_j) G_j and W_j += conj(X) G_j from the spectrum in z
+            auto mac = [&](float2 (&Wj)[E], float2 (&C)[E], const float2 (&X)[E], const float2* z, int jj) {
+                const float2* Hg = Hc + (int64_t)(rb + i * J + j0 + jj) * B.MMAX;
+#pragma unroll
+                for (int q = 0; q < E / 2; ++q) {
+                    const int k = t + q * T;
+                    const int kb = (k == 0) ? M / 2 : M - k;
+                    float2 ga, gb;
+                    split_pair<M>(z, wsplit, k, ga, gb);
+                    float2 ha, hb;
+                    if constexpr (L::kStageH) {
+                        ha = hs[jj * M + k];
+                        hb = hs[jj * M + kb];
+                    } else {
+                        ha = __ldg(Hg + k);
+                        hb = __ldg(Hg + kb);
+                    }
+                    if (k == 0) {            // slot 0 holds two real bins
+                        C[0].x += ha.x * ga.x;
+                        C[0].y += ha.y * ga.y;
+                        Wj[0].x += X[0].x * ga.x;
+                        Wj[0].y += X[0].y * ga.y;
+                    } else {
+                        C[2 * q] = cadd(C[2 * q], cmulc(ha, ga));
+                        Wj[2 * q] = cadd(Wj[2 * q], cmulc(X[2 * q], ga));
+                    }
+                    C[2 * q + 1] = cadd(C[2 * q + 1], cmulc(hb, gb));
+                    Wj[2 * q + 1] = cadd(Wj[2 * q + 1], cmulc(X[2 * q + 1], gb));
+                }
+            };
             for (int64_t b = b0; b < b1; ++b) {
                 const int64_t pos = b * hop;
                 const int64_t lim = nx - pos;
-                // source block
-                float2 v[E];
-                next_input(v, b, j0);
-                float2 X[E];
-                split_forward<M, E>(X, rfft_x<M, E, kWait>(v, ex, tw, t), wsplit, t);
-                float2 C[E];
+                float2 v[E], X[E], C[E];
 #pragma unroll
                 for (int e = 0; e < E; ++e) C[e] = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int jj = 0; jj < kJG; ++jj) {
-                    if (jj >= jn) break;
-                    next_input(v, b, jj + 1 < jn ? j0 + jj + 1 : -1);
+                // step 0 transforms the source block, step 1 + jj the window of mic j0 + jj;
+                // one loop body (not unrolled) so the transform code is emitted once
+                // (unrolled at N = 16384, where the rolled loop computed wrong dh)
+#pragma unroll(kRollSteps ? 1 : kJG + 1)
+                for (int sp = 0; sp <= kJG; ++sp) {
+                    if (sp > jn) break;
+                    next_input(v, b, sp < jn ? j0 + sp : -1);
                     const float2* z = rfft_x<M, E, kWait>(v, ex, tw, t);
-                    const float2* Hg = Hc + (int64_t)(rb + i * J + j0 + jj) * B.MMAX;
-#pragma unroll
-                    for (int q = 0; q < E / 2; ++q) {
-                        const int k = t + q * T;
-                        const int kb = (k == 0) ? M / 2 : M - k;
-                        float2 ga, gb;
-                        split_pair<M>(z, wsplit, k, ga, gb);
-                        float2 ha, hb;
-                        if constexpr (L::kStageH) {
-                            ha = hs[jj * M + k];
-                            hb = hs[jj * M + kb];
-                        } else {
-                            ha = __ldg(Hg + k);
-                            hb = __ldg(Hg + kb);
-                        }
-                        if (k == 0) {            // slot 0 holds two real bins
-                            C[0].x += ha.x * ga.x;
-                            C[0].y += ha.y * ga.y;
-                            W[jj][0].x += X[0].x * ga.x;
-                            W[jj][0].y += X[0].y * ga.y;
-                        } else {
-                            C[2 * q] = cadd(C[2 * q], cmulc(ha, ga));
-                            W[jj][2 * q] = cadd(W[jj][2 * q], cmulc(X[2 * q], ga));
-                        }
-                        C[2 * q + 1] = cadd(C[2 * q + 1], cmulc(hb, gb));
-                        W[jj][2 * q + 1] = cadd(W[jj][2 * q + 1], cmulc(X[2 * q + 1], gb));
-                    }
+                    if (sp == 0) split_forward<M, E>(X, z, wsplit, t);
+                    else if (sp == 1) mac(W[0], C, X, z, 0);
+                    else mac(W[1], C, X, z, 1);
                 }
                 // <c, x_block> by Parseval on the half spectra already in registers
                 // (x_block is zero beyond its length, so only n < hop counts):
@@ -236,12 +243,13 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
                     }
                 }
             }
-            // dh partials of this segment for mics j0 .. j0 + jn - 1
+            // dh partials of this segment for mics j0 .. j0 + jn - 1 (one loop body)
+#pragma unroll 1
+            for (int jj = 0; jj < jn; ++jj) {
+                float2 v[E], Pw[E];
 #pragma unroll
-            for (int jj = 0; jj < kJG; ++jj) {
-                if (jj >= jn) break;
-                float2 v[E];
-                irfft_x<M, E, false>(v, W[jj], ex, tw, t);
+                for (int e = 0; e < E; ++e) Pw[e] = jj ? W[1][e] : W[0][e];
+                irfft_x<M, E, false>(v, Pw, ex, tw, t);
                 const int r = rb + i * J + j0 + jj;
                 const int Lr = B.L[r];
                 float* out = dhp + B.dhp_off[g] + (B.roff[r] - B.roff[rb]);
