@@ -71,10 +71,10 @@ def _bind(lib):
     lib.oracle_truncate_batch.argtypes = [i64, P, P, f64, P, P, P, P, ctypes.c_int]
     lib.oracle_forward_batch.restype = ctypes.c_int
     lib.oracle_forward_batch.argtypes = [i32, i32, P, P, P, P, P, P, P, ctypes.c_int, P, P,
-                                         ctypes.c_int]
+                                         ctypes.c_int, ctypes.c_int]
     lib.oracle_backward_batch.restype = ctypes.c_int
     lib.oracle_backward_batch.argtypes = [i32, i32, P, P, P, P, P, P, P, P, P, P, P,
-                                          ctypes.c_int]
+                                          ctypes.c_int, ctypes.c_int]
     lib.oracle_mix_ola.restype = ctypes.c_int
     lib.oracle_mix_ola.argtypes = [P, i64, i32, i32, P, P, P, P, i64, P]
     lib.oracle_forward_ola_batch.restype = ctypes.c_int
@@ -203,29 +203,44 @@ def truncate_batch(batch, eta_db, nthreads=0, lib=None):
     return dict(L=L, peak=pk, e_tot=et, e_kept=ek)
 
 
-def forward(batch, eta_db=20.0, alpha=None, nthreads=0, lib=None):
+def output_lengths(batch, output_mode=0) -> np.ndarray:
+    """Output samples per mic of each utterance: Nx ("same", output_mode 0) or
+    Nx + max Nh - 1 over the utterance's RIRs (full convolution, mode 1)."""
+    nx = np.asarray(batch.num_samples, dtype=np.int64)
+    if not output_mode:
+        return nx.copy()
+    per_utt = np.asarray(batch.num_sources, dtype=np.int64) * batch.num_mics
+    r0 = np.concatenate([[0], np.cumsum(per_utt)])
+    nh = np.asarray(batch.rir_len, dtype=np.int64)
+    return np.array([nx[u] + nh[r0[u]:r0[u + 1]].max() - 1 for u in range(len(nx))], dtype=np.int64)
+
+
+def forward(batch, eta_db=20.0, alpha=None, nthreads=0, lib=None, output_mode=0):
     """Truncation, gains (from batch.snr_db unless alpha is given) and the
-    direct-form mix.  Returns dict(y, alpha, L, e_kept_frac)."""
+    direct-form mix (Eq. 2) over the output range of output_mode.
+    Returns dict(y, alpha, L, e_kept_frac)."""
     lib = lib or _load()
     tr = truncate_batch(batch, eta_db, nthreads, lib)
     S = int(np.sum(batch.num_sources))
     gain_mode = 0 if alpha is None else 1
     a = np.zeros(S) if alpha is None else _f64(alpha).copy()
-    y = np.zeros(int(np.sum(batch.num_samples)) * batch.num_mics)
+    y = np.zeros(int(np.sum(output_lengths(batch, output_mode))) * batch.num_mics)
     x = _f64(batch.x)
     rir = _f64(batch.rir)
     rc = lib.oracle_forward_batch(batch.num_sources.shape[0], batch.num_mics,
                                   _p(_i32(batch.num_sources)), _p(_i64(batch.num_samples)),
                                   _p(_i32(batch.rir_len)), _p(x), _p(rir), _p(tr["L"]),
-                                  _p(_f64(batch.snr_db)), gain_mode, _p(a), _p(y), nthreads)
+                                  _p(_f64(batch.snr_db)), gain_mode, _p(a), _p(y), int(output_mode),
+                                  nthreads)
     if rc:
         raise OracleError("noise source with zero power")
     frac = np.where(tr["e_tot"] > 0, tr["e_kept"] / np.where(tr["e_tot"] > 0, tr["e_tot"], 1), 1.0)
     return dict(y=y, alpha=a, L=tr["L"], e_kept_frac=frac)
 
 
-def backward(batch, L, alpha, g, nthreads=0, lib=None):
-    """Adjoint of the mix for fixed L and alpha.  Returns dict(dx, dh, dalpha)."""
+def backward(batch, L, alpha, g, nthreads=0, lib=None, output_mode=0):
+    """Adjoint of the mix for fixed L and alpha; g has the layout of the
+    output_mode's y.  Returns dict(dx, dh, dalpha)."""
     lib = lib or _load()
     S = int(np.sum(batch.num_sources))
     dx = np.zeros(batch.x.shape[0])
@@ -236,7 +251,8 @@ def backward(batch, L, alpha, g, nthreads=0, lib=None):
     lib.oracle_backward_batch(batch.num_sources.shape[0], batch.num_mics,
                               _p(_i32(batch.num_sources)), _p(_i64(batch.num_samples)),
                               _p(_i32(batch.rir_len)), _p(x), _p(rir), _p(_i64(L)),
-                              _p(_f64(alpha)), _p(_f64(g)), _p(dx), _p(dh), _p(da), nthreads)
+                              _p(_f64(alpha)), _p(_f64(g)), _p(dx), _p(dh), _p(da), int(output_mode),
+                              nthreads)
     return dict(dx=dx, dh=dh, dalpha=da)
 
 

@@ -172,20 +172,23 @@ int oracle_gains(const double *x, int64_t n_x, int32_t I, const double *snr_db,
 
 /* x: [I][n_x]; rir: packed RIRs of this utterance in (i, j) order with
  * offsets rir_off[I*J]; L[I*J]: kept lengths; alpha[I];
- * y: [J][n_x] out.  Mic j only. */
-static void mix_direct_mic(const double *x, int64_t n_x, int32_t I, int32_t J, int32_t j,
+ * yj: [n_y] out, mic j only: y_j[n] = sum_i alpha_i sum_k hhat_ij[k] x_i[n-k]
+ * for n < n_y, with x_i[m] = 0 outside [0, n_x).  n_y = n_x is the "same"
+ * output; n_y = n_x + N_h - 1 the full one. */
+static void mix_direct_mic(const double *x, int64_t n_x, int64_t n_y, int32_t I, int32_t J, int32_t j,
                            const double *rir, const int64_t *rir_off, const int64_t *L,
                            const double *alpha, double *yj)
 {
-    for (int64_t n = 0; n < n_x; ++n) yj[n] = 0.0;
+    for (int64_t n = 0; n < n_y; ++n) yj[n] = 0.0;
     for (int32_t i = 0; i < I; ++i) {
         const double *xi = x + (int64_t)i * n_x;
         const double *h = rir + rir_off[i * J + j];
         int64_t Lij = L[i * J + j];
-        for (int64_t n = 0; n < n_x; ++n) {
+        for (int64_t n = 0; n < n_y; ++n) {
             double acc = 0.0;
             int64_t kmax = (n < Lij - 1) ? n : Lij - 1;
-            for (int64_t k = 0; k <= kmax; ++k) acc += h[k] * xi[n - k];
+            int64_t kmin = (n - n_x + 1 > 0) ? n - n_x + 1 : 0;
+            for (int64_t k = kmin; k <= kmax; ++k) acc += h[k] * xi[n - k];
             yj[n] += alpha[i] * acc;
         }
     }
@@ -196,18 +199,18 @@ void oracle_mix_direct(const double *x, int64_t n_x, int32_t I, int32_t J,
                        const double *alpha, double *y)
 {
     for (int32_t j = 0; j < J; ++j)
-        mix_direct_mic(x, n_x, I, J, j, rir, rir_off, L, alpha, y + (int64_t)j * n_x);
+        mix_direct_mic(x, n_x, n_x, I, J, j, rir, rir_off, L, alpha, y + (int64_t)j * n_x);
 }
 
 /* ------------------------------------------------------------------------ */
 /* Adjoint of Eq. 2 (one utterance, one source)                               */
 /* ------------------------------------------------------------------------ */
 
-/* g: [J][n_x] upstream gradient dLoss/dy.
- * dx_i[m]    = alpha_i sum_j sum_{k<L_ij} hhat_ij[k] g_j[m+k]
+/* g: [J][n_y] upstream gradient dLoss/dy (output length n_y as in mix_direct_mic).
+ * dx_i[m]    = alpha_i sum_j sum_{k<L_ij} hhat_ij[k] g_j[m+k]      (m+k < n_y)
  * dh_ij[k]   = alpha_i sum_n g_j[n] x_i[n-k]   for k < L_ij, 0 for k >= L_ij
  * dalpha_i   = sum_j sum_n g_j[n] (hhat_ij * x_i)[n]                        */
-static void mix_backward_src(const double *x, int64_t n_x, int32_t J, int32_t i,
+static void mix_backward_src(const double *x, int64_t n_x, int64_t n_y, int32_t J, int32_t i,
                              const double *rir, const int64_t *rir_off, const int64_t *rir_len,
                              const int64_t *L, const double *alpha, const double *g,
                              double *dx_i, double *dh, double *dalpha_i)
@@ -216,28 +219,30 @@ static void mix_backward_src(const double *x, int64_t n_x, int32_t J, int32_t i,
     double da = 0.0;
     for (int64_t m = 0; m < n_x; ++m) dx_i[m] = 0.0;
     for (int32_t j = 0; j < J; ++j) {
-        const double *gj = g + (int64_t)j * n_x;
+        const double *gj = g + (int64_t)j * n_y;
         const double *h = rir + rir_off[i * J + j];
         int64_t Lij = L[i * J + j];
         double *dhij = dh + rir_off[i * J + j];
         /* dx */
         for (int64_t m = 0; m < n_x; ++m) {
             double acc = 0.0;
-            for (int64_t k = 0; k < Lij && m + k < n_x; ++k) acc += h[k] * gj[m + k];
+            for (int64_t k = 0; k < Lij && m + k < n_y; ++k) acc += h[k] * gj[m + k];
             dx_i[m] += alpha[i] * acc;
         }
-        /* dh */
+        /* dh: n runs over the output positions where x_i[n-k] exists */
         for (int64_t k = 0; k < rir_len[i * J + j]; ++k) {
             double acc = 0.0;
+            int64_t nend = (n_x + k < n_y) ? n_x + k : n_y;
             if (k < Lij)
-                for (int64_t n = k; n < n_x; ++n) acc += gj[n] * xi[n - k];
+                for (int64_t n = k; n < nend; ++n) acc += gj[n] * xi[n - k];
             dhij[k] = alpha[i] * acc;
         }
         /* dalpha: <g_j, hhat_ij * x_i> */
-        for (int64_t n = 0; n < n_x; ++n) {
+        for (int64_t n = 0; n < n_y; ++n) {
             double acc = 0.0;
             int64_t kmax = (n < Lij - 1) ? n : Lij - 1;
-            for (int64_t k = 0; k <= kmax; ++k) acc += h[k] * xi[n - k];
+            int64_t kmin = (n - n_x + 1 > 0) ? n - n_x + 1 : 0;
+            for (int64_t k = kmin; k <= kmax; ++k) acc += h[k] * xi[n - k];
             da += gj[n] * acc;
         }
     }
@@ -253,20 +258,28 @@ typedef struct {
     int64_t *rir0;     /* [U+1] first RIR of utterance */
     int64_t *xoff;     /* [S]   offset of source s in x */
     int64_t *yoff;     /* [U]   offset of utterance in y */
+    int64_t *n_y;      /* [U]   output samples per mic */
     int64_t *roff;     /* [R]   offset of RIR r in rir */
 } layout_t;
 
+/* output_mode 0: n_y = n_x ("same"); 1: n_y = n_x + max N_h - 1 over the
+ * utterance's RIRs (full convolution length of the untruncated RIRs). */
 static void layout_build(int32_t U, int32_t J, const int32_t *n_src, const int64_t *n_x,
-                         const int32_t *rir_len, layout_t *lo)
+                         const int32_t *rir_len, int output_mode, layout_t *lo)
 {
     lo->src0 = (int64_t *)malloc(sizeof(int64_t) * (U + 1));
     lo->rir0 = (int64_t *)malloc(sizeof(int64_t) * (U + 1));
     lo->yoff = (int64_t *)malloc(sizeof(int64_t) * (U + 1));
+    lo->n_y = (int64_t *)malloc(sizeof(int64_t) * (U + 1));
     lo->src0[0] = 0; lo->rir0[0] = 0; lo->yoff[0] = 0;
     for (int32_t u = 0; u < U; ++u) {
         lo->src0[u + 1] = lo->src0[u] + n_src[u];
         lo->rir0[u + 1] = lo->rir0[u] + (int64_t)n_src[u] * J;
-        lo->yoff[u + 1] = lo->yoff[u] + (int64_t)J * n_x[u];
+        int64_t nh_max = 1;
+        for (int64_t r = lo->rir0[u]; r < lo->rir0[u + 1]; ++r)
+            if (rir_len[r] > nh_max) nh_max = rir_len[r];
+        lo->n_y[u] = output_mode ? n_x[u] + nh_max - 1 : n_x[u];
+        lo->yoff[u + 1] = lo->yoff[u] + (int64_t)J * lo->n_y[u];
     }
     int64_t S = lo->src0[U], R = lo->rir0[U];
     lo->xoff = (int64_t *)malloc(sizeof(int64_t) * (S + 1));
@@ -282,7 +295,7 @@ static void layout_build(int32_t U, int32_t J, const int32_t *n_src, const int64
 
 static void layout_free(layout_t *lo)
 {
-    free(lo->src0); free(lo->rir0); free(lo->xoff); free(lo->yoff); free(lo->roff);
+    free(lo->src0); free(lo->rir0); free(lo->xoff); free(lo->yoff); free(lo->roff); free(lo->n_y);
 }
 
 static void set_threads(int nthreads)
@@ -329,15 +342,16 @@ int oracle_truncate_batch(int64_t R, const int32_t *rir_len, const double *rir, 
 
 /* Forward over a batch.  gain_mode 0: alpha from snr_db (out in alpha);
  * gain_mode 1: alpha given in alpha.  L: [R] kept lengths (in, from
- * oracle_truncate_batch).  y: [sum J*Nx] out. */
+ * oracle_truncate_batch).  y: [sum J*Ny] out, Ny per output_mode (see
+ * layout_build). */
 int oracle_forward_batch(int32_t U, int32_t J, const int32_t *n_src, const int64_t *n_x,
                          const int32_t *rir_len, const double *x, const double *rir,
                          const int64_t *L, const double *snr_db, int gain_mode,
-                         double *alpha, double *y, int nthreads)
+                         double *alpha, double *y, int output_mode, int nthreads)
 {
     set_threads(nthreads);
     layout_t lo;
-    layout_build(U, J, n_src, n_x, rir_len, &lo);
+    layout_build(U, J, n_src, n_x, rir_len, output_mode, &lo);
     int bad = 0;
     if (gain_mode == 0) {
 #pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
@@ -359,9 +373,9 @@ int oracle_forward_batch(int32_t U, int32_t J, const int32_t *n_src, const int64
         for (int64_t uj = 0; uj < UJ; ++uj) {
             int32_t u = (int32_t)(uj / J), j = (int32_t)(uj % J);
             int64_t s0 = lo.src0[u], r0 = lo.rir0[u];
-            mix_direct_mic(x + lo.xoff[s0], n_x[u], n_src[u], J, j,
+            mix_direct_mic(x + lo.xoff[s0], n_x[u], lo.n_y[u], n_src[u], J, j,
                            rir + lo.roff[r0], rel + r0, L + r0, alpha + s0,
-                           y + lo.yoff[u] + (int64_t)j * n_x[u]);
+                           y + lo.yoff[u] + (int64_t)j * lo.n_y[u]);
         }
         free(rel);
     }
@@ -369,16 +383,16 @@ int oracle_forward_batch(int32_t U, int32_t J, const int32_t *n_src, const int64
     return bad ? ORACLE_E_INVALID : ORACLE_OK;
 }
 
-/* Backward over a batch.  g: [sum J*Nx]; dx: [sum I*Nx]; dh: like rir;
- * dalpha: [sum I].  alpha and L as used by the forward. */
+/* Backward over a batch.  g: [sum J*Ny] (Ny per output_mode); dx: [sum I*Nx];
+ * dh: like rir; dalpha: [sum I].  alpha and L as used by the forward. */
 int oracle_backward_batch(int32_t U, int32_t J, const int32_t *n_src, const int64_t *n_x,
                           const int32_t *rir_len, const double *x, const double *rir,
                           const int64_t *L, const double *alpha, const double *g,
-                          double *dx, double *dh, double *dalpha, int nthreads)
+                          double *dx, double *dh, double *dalpha, int output_mode, int nthreads)
 {
     set_threads(nthreads);
     layout_t lo;
-    layout_build(U, J, n_src, n_x, rir_len, &lo);
+    layout_build(U, J, n_src, n_x, rir_len, output_mode, &lo);
     int64_t S = lo.src0[U], R = lo.rir0[U];
     int64_t *rel = (int64_t *)malloc(sizeof(int64_t) * (R + 1));
     int64_t *rlen64 = (int64_t *)malloc(sizeof(int64_t) * (R + 1));
@@ -395,7 +409,7 @@ int oracle_backward_batch(int32_t U, int32_t J, const int32_t *n_src, const int6
         int32_t u = utt_of[s];
         int32_t i = (int32_t)(s - lo.src0[u]);
         int64_t s0 = lo.src0[u], r0 = lo.rir0[u];
-        mix_backward_src(x + lo.xoff[s0], n_x[u], J, i,
+        mix_backward_src(x + lo.xoff[s0], n_x[u], lo.n_y[u], J, i,
                          rir + lo.roff[r0], rel + r0, rlen64 + r0, L + r0, alpha + s0,
                          g + lo.yoff[u], dx + lo.xoff[s], dh + lo.roff[r0], dalpha + s);
     }
@@ -499,7 +513,7 @@ int oracle_forward_ola_batch(int32_t U, int32_t J, const int32_t *n_src, const i
 {
     set_threads(nthreads);
     layout_t lo;
-    layout_build(U, J, n_src, n_x, rir_len, &lo);
+    layout_build(U, J, n_src, n_x, rir_len, 0, &lo);
     int64_t R = lo.rir0[U];
     int64_t *rel = (int64_t *)malloc(sizeof(int64_t) * (R + 1));
     for (int32_t u = 0; u < U; ++u)

@@ -204,6 +204,26 @@ def make_batch(seed: int, lengths, n_sources, mics: np.ndarray, rt60_range,
                  np.asarray(snrs, dtype=np.float32))
 
 
+def trim_rirs(batch: Batch, seed: int, min_frac: float = 0.3) -> Batch:
+    """Cuts every RIR to a seeded length in [min_frac * Nh, Nh], so the RIRs of
+    one utterance differ in length (the longest sets the full output length)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ro = batch.rir_offsets()
+    keep = [max(1, int(rng.integers(int(math.ceil(min_frac * n)), n + 1))) for n in batch.rir_len]
+    rir = np.concatenate([batch.rir[ro[r]:ro[r] + keep[r]] for r in range(batch.num_rirs)])
+    return dataclasses.replace(batch, rir_len=np.asarray(keep, dtype=np.int32), rir=rir.astype(np.float32))
+
+
+def output_lengths(batch: Batch, output_mode: int = 0) -> np.ndarray:
+    """Samples per microphone of each utterance's output: Nx for the "same"
+    output (mode 0), Nx + max Nh - 1 over the utterance's RIRs for the full one."""
+    if not output_mode:
+        return batch.num_samples.astype(np.int64).copy()
+    ri = batch.rir_index()
+    return np.array([int(batch.num_samples[u]) + int(batch.rir_len[ri[u]:ri[u + 1]].max()) - 1
+                     for u in range(batch.num_utts)], dtype=np.int64)
+
+
 def grad_like(seed: int, n: int, scale: float = 0.1) -> np.ndarray:
     """A seeded FP32 vector (an upstream gradient or a regression target)."""
     rng = np.random.Generator(np.random.PCG64(seed))

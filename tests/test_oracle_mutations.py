@@ -18,14 +18,21 @@ MUTANTS = [
     ("eq9_keeps_one_less", "L = n_c + 2;", "L = n_c + 1;"),
     ("eq8_non_strict", "if (suffix < p_th) n_c = m;", "if (suffix <= p_th) n_c = m;"),
     ("eq7_amplitude_threshold", "double p_th = pmax * factor;", "double p_th = pmax * sqrt(factor);"),
-    ("conv_drops_last_tap", "int64_t kmax = (n < Lij - 1) ? n : Lij - 1;\n            for (int64_t k = 0; k <= kmax; ++k) acc += h[k] * xi[n - k];\n            yj[n]",
-     "int64_t kmax = (n < Lij - 1) ? n : Lij - 2;\n            for (int64_t k = 0; k <= kmax; ++k) acc += h[k] * xi[n - k];\n            yj[n]"),
+    ("conv_drops_last_tap", "int64_t kmax = (n < Lij - 1) ? n : Lij - 1;\n            int64_t kmin = (n - n_x + 1 > 0) ? n - n_x + 1 : 0;\n            for (int64_t k = kmin; k <= kmax; ++k) acc += h[k] * xi[n - k];\n            yj[n]",
+     "int64_t kmax = (n < Lij - 1) ? n : Lij - 2;\n            int64_t kmin = (n - n_x + 1 > 0) ? n - n_x + 1 : 0;\n            for (int64_t k = kmin; k <= kmax; ++k) acc += h[k] * xi[n - k];\n            yj[n]"),
+    ("full_output_drops_first_tail_term",
+     "int64_t kmin = (n - n_x + 1 > 0) ? n - n_x + 1 : 0;\n            for (int64_t k = kmin; k <= kmax; ++k) acc += h[k] * xi[n - k];\n            yj[n]",
+     "int64_t kmin = (n - n_x + 2 > 0) ? n - n_x + 2 : 0;\n            for (int64_t k = kmin; k <= kmax; ++k) acc += h[k] * xi[n - k];\n            yj[n]"),
+    ("full_dh_ignores_output_tail", "int64_t nend = (n_x + k < n_y) ? n_x + k : n_y;",
+     "int64_t nend = (n_x < n_y) ? n_x : n_y;"),
+    ("full_length_from_shortest_rir", "if (rir_len[r] > nh_max) nh_max = rir_len[r];",
+     "if (r == lo->rir0[u] || rir_len[r] < nh_max) nh_max = rir_len[r];"),
     ("mix_ignores_gain", "yj[n] += alpha[i] * acc;", "yj[n] += acc;"),
     ("gain_snr_sign", "pow(10.0, -snr_db[i] / 10.0)", "pow(10.0, snr_db[i] / 10.0)"),
     ("gain_no_sqrt", "alpha[i] = sqrt(p0 / pi * pow(10.0, -snr_db[i] / 10.0));",
      "alpha[i] = p0 / pi * pow(10.0, -snr_db[i] / 10.0);"),
     ("dx_convolves_instead_of_correlates",
-     "for (int64_t k = 0; k < Lij && m + k < n_x; ++k) acc += h[k] * gj[m + k];",
+     "for (int64_t k = 0; k < Lij && m + k < n_y; ++k) acc += h[k] * gj[m + k];",
      "for (int64_t k = 0; k < Lij && m >= k; ++k) acc += h[k] * gj[m - k];"),
     ("dh_transposed_operands", "acc += gj[n] * xi[n - k];", "acc += gj[n - k] * xi[n];"),
     ("dh_missing_gain", "dhij[k] = alpha[i] * acc;", "dhij[k] = acc;"),

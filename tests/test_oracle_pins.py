@@ -375,3 +375,107 @@ def test_rir_gradient_is_zero_beyond_kept_length():
         L = int(out["L"][r])
         assert np.all(gr["dh"][ro[r] + L:ro[r + 1]] == 0.0)
         assert np.any(gr["dh"][ro[r]:ro[r] + L] != 0.0)
+
+
+# ---------------------------------------------------------------------------
+# full-length output (output_mode 1): Ny = Nx + max Nh - 1 per utterance
+# ---------------------------------------------------------------------------
+def _full_batch():
+    # uneven RIR lengths inside an utterance, so the longest one sets Ny
+    lengths = np.array([700, 1500, 333])
+    n_src = np.array([2, 1, 3])
+    b = synth.make_batch(91, lengths, n_src, synth.linear_pair_array(), (0.004, 0.012))
+    return synth.trim_rirs(b, 92)
+
+
+def test_full_output_equals_numpy_full_convolution():
+    b = _full_batch()
+    S = int(np.sum(b.num_sources))
+    alpha = np.linspace(0.5, 1.5, S)
+    out = oracle.forward(b, 10.0, alpha=alpha, output_mode=1)
+    L = out["L"]
+    assert np.any(L < b.rir_len)                     # some output tail is exactly zero
+    ny = oracle.output_lengths(b, 1)
+    ri = b.rir_index()
+    assert all(len(set(b.rir_len[ri[u]:ri[u + 1]])) > 1 for u in range(b.num_utts))
+    ro, xo = b.rir_offsets(), b.x_offsets()
+    J = b.num_mics
+    y_off = np.concatenate([[0], np.cumsum(ny * J)])
+    s0 = np.concatenate([[0], np.cumsum(b.num_sources)])
+    r = 0
+    for u in range(len(ny)):
+        I, nx = int(b.num_sources[u]), int(b.num_samples[u])
+        assert ny[u] == nx + b.rir_len[s0[u] * J:(s0[u] + I) * J].max() - 1
+        ref = np.zeros((J, ny[u]))
+        for i in range(I):
+            xi = b.x[xo[s0[u] + i]:xo[s0[u] + i + 1]].astype(np.float64)
+            for j in range(J):
+                rr = (s0[u] + i) * J + j
+                h = b.rir[ro[rr]:ro[rr] + L[rr]].astype(np.float64)
+                c = np.convolve(xi, h)
+                ref[j, :c.shape[0]] += alpha[s0[u] + i] * c
+        got = out["y"][y_off[u]:y_off[u + 1]].reshape(J, ny[u])
+        np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_full_output_starts_with_same_output_and_sums_to_product():
+    b = _full_batch()
+    S = int(np.sum(b.num_sources))
+    alpha = np.linspace(0.7, 1.2, S)
+    full = oracle.forward(b, 20.0, alpha=alpha, output_mode=1)
+    same = oracle.forward(b, 20.0, alpha=alpha)
+    ny, nx, J = oracle.output_lengths(b, 1), b.num_samples, b.num_mics
+    yf = np.concatenate([[0], np.cumsum(ny * J)])
+    ys = np.concatenate([[0], np.cumsum(nx * J)])
+    ro, xo = b.rir_offsets(), b.x_offsets()
+    s0 = np.concatenate([[0], np.cumsum(b.num_sources)])
+    L = full["L"]
+    for u in range(len(nx)):
+        f = full["y"][yf[u]:yf[u + 1]].reshape(J, ny[u])
+        sm = same["y"][ys[u]:ys[u + 1]].reshape(J, nx[u])
+        np.testing.assert_array_equal(f[:, :nx[u]], sm)       # same arithmetic on [0, Nx)
+        for j in range(J):
+            # sum over every output sample of a full convolution = product of the sums
+            ref = 0.0
+            for i in range(int(b.num_sources[u])):
+                rr = (s0[u] + i) * J + j
+                ref += alpha[s0[u] + i] * float(np.sum(b.x[xo[s0[u] + i]:xo[s0[u] + i + 1]], dtype=np.float64)) \
+                    * float(np.sum(b.rir[ro[rr]:ro[rr] + L[rr]], dtype=np.float64))
+            assert abs(float(np.sum(f[j])) - ref) <= 1e-10 * max(1.0, abs(ref))
+
+
+def test_full_output_adjoint_identities_and_numpy_gradients():
+    b = _full_batch()
+    S = int(np.sum(b.num_sources))
+    alpha = np.linspace(0.6, 1.4, S)
+    ny = oracle.output_lengths(b, 1)
+    J = b.num_mics
+    g = synth.grad_like(17, int(np.sum(ny)) * J)
+    out = oracle.forward(b, 10.0, alpha=alpha, output_mode=1)
+    L = out["L"]
+    gr = oracle.backward(b, L, alpha, g, output_mode=1)
+    lhs = float(np.dot(g, out["y"]))
+    hhat = b.rir.astype(np.float64).copy()
+    ro, xo = b.rir_offsets(), b.x_offsets()
+    for rr in range(b.num_rirs):
+        hhat[ro[rr] + L[rr]:ro[rr + 1]] = 0.0
+    assert abs(np.dot(gr["dx"], b.x.astype(np.float64)) - lhs) <= 1e-11 * abs(lhs)
+    assert abs(np.dot(gr["dh"], hhat) - lhs) <= 1e-11 * abs(lhs)
+    assert abs(np.dot(gr["dalpha"], alpha) - lhs) <= 1e-11 * abs(lhs)
+    # element by element against numpy correlations (utterance 1: one source)
+    yf = np.concatenate([[0], np.cumsum(ny * J)])
+    s0 = np.concatenate([[0], np.cumsum(b.num_sources)])
+    u, i = 1, 0
+    s = s0[u] + i
+    xi = b.x[xo[s]:xo[s + 1]].astype(np.float64)
+    nx = xi.shape[0]
+    dx_ref = np.zeros(nx)
+    for j in range(J):
+        gj = g[yf[u] + j * ny[u]:yf[u] + (j + 1) * ny[u]]
+        rr = s * J + j
+        h = b.rir[ro[rr]:ro[rr] + L[rr]].astype(np.float64)
+        dx_ref += alpha[s] * np.convolve(gj, h[::-1])[L[rr] - 1:L[rr] - 1 + nx]
+        dh_ref = alpha[s] * np.convolve(gj, xi[::-1])[nx - 1:nx - 1 + L[rr]]
+        np.testing.assert_allclose(gr["dh"][ro[rr]:ro[rr] + L[rr]], dh_ref, rtol=1e-11,
+                                   atol=1e-11 * np.abs(dh_ref).max())
+    np.testing.assert_allclose(gr["dx"][xo[s]:xo[s + 1]], dx_ref, rtol=1e-11, atol=1e-11 * np.abs(dx_ref).max())
