@@ -6,7 +6,11 @@
  * Simulator for Training Deep Neural Network Acoustic Models"):
  *
  *   Eq. 7-9  hhat_ij = h_ij cut where its power falls eta dB below its peak
- *   Eq. 2    y_j[n]  = sum_i alpha_i (hhat_ij * x_i)[n],  n in [0, Nx)
+ *   Eq. 2    y_j[n]  = sum_i alpha_i (hhat_ij * x_i)[n],  n in [0, Ny)
+ *
+ * with Ny = Nx ("same" output, the default) or Ny = Nx + max_ij Nh_ij - 1
+ * (the full convolution of the untruncated RIR lengths; samples past
+ * Nx + L_max - 1 are zero), chosen per plan by output_mode.
  *
  * by overlap-add FFT filtering (Sec. 2.2, Eq. 6), and its adjoint (gradients
  * with respect to x_i, h_ij and alpha_i).  All arithmetic runs in CUDA
@@ -16,7 +20,7 @@
  *   x    [sum_u I_u * Nx_u]            utterance, then source, then sample
  *   rir  [sum_u sum_{i,j} Nh_uij]      utterance, then source i, then mic j,
  *                                      then tap; RIR index r = rir0_u + i*J + j
- *   y    [sum_u J * Nx_u]              utterance, then mic, then sample
+ *   y    [sum_u J * Ny_u]              utterance, then mic, then sample
  *   per-source arrays (snr_db, gains)  [sum_u I_u], utterance then source
  *   per-RIR arrays (trunc_len, ...)    [sum_u I_u * J], RIR index order
  * Source 0 of every utterance is the target; sources 1.. are noise sources.
@@ -74,6 +78,8 @@ typedef struct {
     int32_t disable_graphs;        /* 0: each call replays a CUDA graph of its launch sequence,
                                       captured on the first call with a given set of buffer
                                       pointers; 1: launch eagerly */
+    int32_t output_mode;           /* 0: "same" output, Ny = Nx; 1: full output,
+                                      Ny = Nx + (longest RIR of the utterance) - 1 */
 } rsim_plan_desc;
 
 /* Creates a plan for the given shapes on CUDA device `device`.  Validates the
@@ -111,6 +117,7 @@ rsim_status rsim_filter_mix(rsim_plan_t plan, void *stream, const float *x, cons
  *                          0 for taps >= L (the cut-off is a fixed mask)
  *   grad_gains [sum I_u]   <grad_y_j, hhat_ij * x_i> summed over j; gains are
  *                          treated as inputs (no gradient flows to the SNRs)
+ * grad_y has the layout of y (Ny samples per mic, per the plan's output_mode).
  * grad_x may be NULL (not computed); grad_rir and grad_gains must be given.
  * Returns RSIM_E_STATE if no forward ran on the plan.  Asynchronous. */
 rsim_status rsim_filter_mix_backward(rsim_plan_t plan, void *stream, const float *grad_y,

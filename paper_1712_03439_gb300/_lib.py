@@ -43,6 +43,7 @@ class PlanDesc(ctypes.Structure):
         ("bwd_segment_len", ctypes.c_int64),
         ("fft_cost", ctypes.c_void_p),
         ("disable_graphs", ctypes.c_int32),
+        ("output_mode", ctypes.c_int32),
     ]
 
 

@@ -39,7 +39,7 @@ class Plan:
 
     def __init__(self, num_sources, num_samples, rir_len, num_mics, eta_db=20.0,
                  fft_sizes=None, gain_mode=0, segment_len=0, bwd_segment_len=0, fft_cost=None,
-                 device=None, graphs=True):
+                 device=None, graphs=True, output_mode=0):
         self._lib = _lib.load()
         self._handle = None
         self.num_sources = np.ascontiguousarray(num_sources, dtype=np.int32)
@@ -47,6 +47,7 @@ class Plan:
         self.rir_len = np.ascontiguousarray(rir_len, dtype=np.int32)
         self.num_mics = int(num_mics)
         self.gain_mode = int(gain_mode)
+        self.output_mode = int(output_mode)
         self.eta_db = float(eta_db)
         mask = 0
         for n in (fft_sizes or []):
@@ -79,7 +80,7 @@ class Plan:
             gain_mode=self.gain_mode, segment_len=int(segment_len),
             bwd_segment_len=int(bwd_segment_len),
             fft_cost=None if self._cost is None else self._cost.ctypes.data,
-            disable_graphs=0 if graphs else 1)
+            disable_graphs=0 if graphs else 1, output_mode=self.output_mode)
         h = ctypes.c_void_p()
         _lib.check(self._lib, self._lib.rsim_plan(ctypes.byref(desc), self.device, ctypes.byref(h)))
         self._handle = h
@@ -87,7 +88,13 @@ class Plan:
         self.S = int(self.num_sources.sum())
         self.R = int(self.rir_len.shape[0])
         self.x_size = int(np.sum(self.num_sources.astype(np.int64) * self.num_samples))
-        self.y_size = int(np.sum(self.num_samples) * self.num_mics)
+        # output samples per mic: Nx, or Nx + (longest RIR of the utterance) - 1
+        self.num_out = self.num_samples.copy()
+        if self.output_mode:
+            r0 = np.concatenate([[0], np.cumsum(self.num_sources.astype(np.int64) * self.num_mics)])
+            self.num_out += np.array([self.rir_len[r0[u]:r0[u + 1]].max() for u in range(self.U)],
+                                     dtype=np.int64) - 1
+        self.y_size = int(np.sum(self.num_out) * self.num_mics)
         self.rir_size = int(np.sum(self.rir_len.astype(np.int64)))
         # FFT sizes the plan may pick (one forward/backward launch each)
         self.num_fft_sizes = bin(mask).count("1") if mask else 4

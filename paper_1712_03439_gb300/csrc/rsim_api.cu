@@ -198,11 +198,12 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     if (mask == 0) mask = supported;
     if (mask & ~supported)
         return fail(RSIM_E_UNSUPPORTED, "fft_sizes_mask allows sizes outside 2^11 .. 2^14");
+    if (d->output_mode != 0 && d->output_mode != 1) return fail(RSIM_E_INVALID, "output_mode must be 0 or 1");
     if (d->segment_len < 0 || d->bwd_segment_len < 0)
         return fail(RSIM_E_INVALID, "segment_len and bwd_segment_len must be >= 0");
 
     std::vector<int32_t> src0(U + 1), rir0(U + 1), seg0(U + 1), bseg0(U + 1);
-    std::vector<int64_t> yoff(U + 1);
+    std::vector<int64_t> yoff(U + 1), nyv(U);
     int64_t S = 0, R = 0, ysz = 0;
     int imax = 1;
     int64_t nx_max = 1;
@@ -225,9 +226,12 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
         seg0[u] = (int32_t)nseg;
         bseg0[u] = (int32_t)nbseg;
         yoff[u] = ysz;
+        int64_t nh_max = 1;
+        for (int64_t r = R; r < R + (int64_t)I * J; ++r) nh_max = std::max<int64_t>(nh_max, d->rir_len[r]);
+        nyv[u] = d->output_mode ? nx + nh_max - 1 : nx;
         S += I;
         R += (int64_t)I * J;
-        ysz += (int64_t)J * nx;
+        ysz += (int64_t)J * nyv[u];
         nseg += (nx + seg_len - 1) / seg_len;
         nbseg += (nx + bseg_len - 1) / bseg_len;
         imax = std::max(imax, I);
@@ -291,7 +295,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     struct Piece { void** dst; size_t bytes; };
     std::vector<Piece> pieces;
     void *p_bseg0, *p_bsegutt;
-    void *p_nsrc, *p_nx, *p_src0, *p_rir0, *p_seg0, *p_segutt, *p_xoff, *p_yoff, *p_roff, *p_rlen,
+    void *p_nsrc, *p_nx, *p_ny, *p_src0, *p_rir0, *p_seg0, *p_segutt, *p_xoff, *p_yoff, *p_roff, *p_rlen,
         *p_dhpoff, *p_tuning, *p_L, *p_logN, *p_hop, *p_lmax, *p_nblk, *p_pow, *p_err, *p_list,
         *p_count, *p_next, *p_Hc, *p_tails, *p_dhp, *p_dap;
     void* p_tw[2 * kNumBuckets] = {};
@@ -315,6 +319,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     }
     pieces.push_back({&p_nsrc, sizeof(int32_t) * U});
     pieces.push_back({&p_nx, sizeof(int64_t) * U});
+    pieces.push_back({&p_ny, sizeof(int64_t) * U});
     pieces.push_back({&p_src0, sizeof(int32_t) * (U + 1)});
     pieces.push_back({&p_rir0, sizeof(int32_t) * (U + 1)});
     pieces.push_back({&p_seg0, sizeof(int32_t) * (U + 1)});
@@ -377,6 +382,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     std::vector<Up> ups = {
         {p_nsrc, nsrc.data(), sizeof(int32_t) * U},
         {p_nx, nxv.data(), sizeof(int64_t) * U},
+        {p_ny, nyv.data(), sizeof(int64_t) * U},
         {p_src0, src0.data(), sizeof(int32_t) * (U + 1)},
         {p_rir0, rir0.data(), sizeof(int32_t) * (U + 1)},
         {p_seg0, seg0.data(), sizeof(int32_t) * (U + 1)},
@@ -413,7 +419,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     B.NBSEG = (int32_t)nbseg; B.bseg_len = bseg_len;
     B.bseg0 = (const int32_t*)p_bseg0; B.bseg_utt = (const int32_t*)p_bsegutt;
     B.gain_mode = d->gain_mode;
-    B.n_src = (const int32_t*)p_nsrc; B.n_x = (const int64_t*)p_nx;
+    B.n_src = (const int32_t*)p_nsrc; B.n_x = (const int64_t*)p_nx; B.n_y = (const int64_t*)p_ny;
     B.src0 = (const int32_t*)p_src0; B.rir0 = (const int32_t*)p_rir0;
     B.seg0 = (const int32_t*)p_seg0; B.seg_utt = (const int32_t*)p_segutt;
     B.xoff = (const int64_t*)p_xoff; B.yoff = (const int64_t*)p_yoff;

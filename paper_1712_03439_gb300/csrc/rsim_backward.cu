@@ -119,6 +119,7 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
         const int u = B.bseg_utt[g];
         const int64_t sgi = g - B.bseg0[u];
         const int64_t nx = B.n_x[u];
+        const int64_t ny = B.n_y[u];
         const int hop = B.hop[u];
         const int lmax = B.Lmax[u];
         int64_t b0, b1;
@@ -138,8 +139,8 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
             };
             auto stage_g = [&](float* dst, int64_t b, int j) {
                 const int64_t p = b * hop;
-                stage_real_async<M, E>(dst, gy + B.yoff[u] + (int64_t)j * nx + p,
-                                       min((int64_t)(hop + lmax - 1), nx - p), t);
+                stage_real_async<M, E>(dst, gy + B.yoff[u] + (int64_t)j * ny + p,
+                                       min((int64_t)(hop + lmax - 1), ny - p), t);
             };
             // takes the staged input into v and queues the next one (if any) into the other stage
             auto next_input = [&](float2 (&v)[E], int64_t b, int nj) {

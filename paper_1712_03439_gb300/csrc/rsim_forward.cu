@@ -121,8 +121,11 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
         const int u = B.seg_utt[g];
         const int64_t s = g - B.seg0[u];
         const int64_t nx = B.n_x[u];
+        const int64_t ny = B.n_y[u];
         const int hop = B.hop[u];
         const int tail_len = B.Lmax[u] - 1;
+        // end of the convolution's support (the full output is zero from here on)
+        const int64_t ye = min(ny, nx + (int64_t)tail_len);
         int64_t b0, b1;
         segment_blocks(s, B.seg_len, hop, B.nblk[u], &b0, &b1);
         if (b0 >= b1) continue;
@@ -216,9 +219,9 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
                     if (jj >= jn) break;
                     float2 v[E];
                     irfft_pairs<M, E>(v, Y[jj], sm, tw, t);
-                    float* yj = y + B.yoff[u] + (int64_t)(j0 + jj) * nx + pos;
+                    float* yj = y + B.yoff[u] + (int64_t)(j0 + jj) * ny + pos;
                     float* tlj = tl(jj);
-                    const int64_t lim = nx - pos;
+                    const int64_t lim = ye - pos;
                     // every sample n < N of the block adds the carried sum at n;
                     // [0, hop) is stored, [hop, N) becomes the new carry (which
                     // reaches several blocks ahead when L_max - 1 > hop)
@@ -246,6 +249,17 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
                     for (int n = t; n < tail_len; n += T) dst[n] = tl(jj)[n];
                 }
             }
+            if (ny > nx && b1 == B.nblk[u]) {
+                // full output: the carry past the last block is the end of the
+                // convolution (up to Nx + L_max - 1), then exact zeros
+                __syncthreads();
+                const int64_t end = b1 * hop;
+                for (int jj = 0; jj < jn; ++jj) {
+                    float* yj = y + B.yoff[u] + (int64_t)(j0 + jj) * ny;
+                    for (int64_t n = min(end, ye) + t; n < ny; n += T)
+                        yj[n] = (n < ye) ? tl(jj)[n - end] : 0.f;
+                }
+            }
         }
     }
     cp_async_wait<0>();
@@ -264,13 +278,14 @@ k_fixup(DevBatch B, float* __restrict__ y, const float* __restrict__ tails) {
         int64_t b0, b1;
         segment_blocks(s, B.seg_len, hop, B.nblk[u], &b0, &b1);
         if (b0 >= b1) continue;
-        const int64_t nx = B.n_x[u];
+        const int64_t ny = B.n_y[u];
         const int64_t pos = b0 * hop;
         const int tail_len = B.Lmax[u] - 1;
+        const int64_t ye = min(ny, B.n_x[u] + (int64_t)tail_len);
         for (int j = 0; j < B.J; ++j) {
             const float* src = tails + ((int64_t)(g - 1) * B.J + j) * 2 * B.MMAX;
-            float* yj = y + B.yoff[u] + (int64_t)j * nx + pos;
-            for (int n = threadIdx.x; n < tail_len && pos + n < nx; n += blockDim.x)
+            float* yj = y + B.yoff[u] + (int64_t)j * ny + pos;
+            for (int n = threadIdx.x; n < tail_len && pos + n < ye; n += blockDim.x)
                 yj[n] = yj[n] + src[n];
         }
     }

@@ -36,7 +36,8 @@ struct DevBatch {
     int64_t seg_len;         // samples per segment (>= largest allowed N)
     int32_t gain_mode;
     const int32_t* n_src;    // [U]
-    const int64_t* n_x;      // [U]
+    const int64_t* n_x;      // [U] input samples
+    const int64_t* n_y;      // [U] output samples per mic (Nx, or the full length)
     const int32_t* src0;     // [U+1] first source of utterance
     const int32_t* rir0;     // [U+1] first RIR of utterance
     const int32_t* seg0;     // [U+1] first segment of utterance

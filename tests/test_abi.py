@@ -41,7 +41,7 @@ def _desc(**kw):
                       rir_len=rl.ctypes.data, eta_db=kw.pop("eta", 20.0),
                       fft_sizes_mask=kw.pop("mask", 0), gain_mode=kw.pop("gm", 0),
                       segment_len=kw.pop("seg", 0), bwd_segment_len=kw.pop("bseg", 0),
-                      fft_cost=None, disable_graphs=0)
+                      fft_cost=None, disable_graphs=0, output_mode=kw.pop("om", 0))
     return d, (ns, nx, rl)
 
 
@@ -58,6 +58,8 @@ def _desc(**kw):
     (dict(mask=1 << 16), 2),
     (dict(seg=-5), 1),
     (dict(bseg=-5), 1),
+    (dict(om=2), 1),
+    (dict(om=-1), 1),
 ])
 def test_plan_rejects_bad_descriptions_on_the_host(lib, kw, status):
     d, keep = _desc(**kw)
