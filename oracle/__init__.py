@@ -80,6 +80,10 @@ def _bind(lib):
     lib.oracle_forward_ola_batch.restype = ctypes.c_int
     lib.oracle_forward_ola_batch.argtypes = [i32, i32, P, P, P, P, P, P, P, i64, P,
                                              ctypes.c_int]
+    lib.oracle_mix_window.restype = None
+    lib.oracle_mix_window.argtypes = [P, i64, i32, i32, P, P, P, P, i64, i64, P]
+    lib.oracle_dx_window.restype = None
+    lib.oracle_dx_window.argtypes = [P, i64, i32, i32, P, P, P, ctypes.c_double, i64, i64, P]
     lib.oracle_dft_real.restype = None
     lib.oracle_dft_real.argtypes = [P, i64, i64, P, P]
     lib.oracle_max_threads.restype = ctypes.c_int
@@ -164,6 +168,33 @@ def mix_direct(x_sources, rirs, L, alpha, lib=None):
     (lib or _load()).oracle_mix_direct(_p(x), nx, I, J, _p(rir), _p(off), _p(_i64(L)),
                                        _p(_f64(alpha)), _p(y))
     return y
+
+
+def mix_window(x_sources, rirs, L, alpha, n0, n1, lib=None):
+    """Eq. 2 for one utterance at output positions [n0, n1) only (positions past
+    Nx are those of the full output).  Arguments as mix_direct; returns [J, n1-n0]."""
+    x = _f64(x_sources)
+    I, nx = x.shape
+    J = len(rirs) // I
+    off = _i64(np.concatenate([[0], np.cumsum([len(r) for r in rirs])])[:-1])
+    rir = _f64(np.concatenate([np.asarray(r, dtype=np.float64) for r in rirs]))
+    y = np.zeros((J, n1 - n0))
+    (lib or _load()).oracle_mix_window(_p(x), nx, I, J, _p(rir), _p(off), _p(_i64(L)), _p(_f64(alpha)),
+                                       int(n0), int(n1), _p(y))
+    return y
+
+
+def dx_window(g_mics, rirs, L, i, alpha_i, m0, m1, lib=None):
+    """Gradient of source i of one utterance at input positions [m0, m1) only.
+    g_mics [J, Ny]: upstream gradient per mic; rirs, L as mix_direct."""
+    g = _f64(g_mics)
+    J, ny = g.shape
+    off = _i64(np.concatenate([[0], np.cumsum([len(r) for r in rirs])])[:-1])
+    rir = _f64(np.concatenate([np.asarray(r, dtype=np.float64) for r in rirs]))
+    dx = np.zeros(m1 - m0)
+    (lib or _load()).oracle_dx_window(_p(g), ny, J, int(i), _p(rir), _p(off), _p(_i64(L)), float(alpha_i),
+                                      int(m0), int(m1), _p(dx))
+    return dx
 
 
 def mix_ola(x_sources, rirs, L, alpha, fft_n=0, lib=None):

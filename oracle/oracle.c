@@ -202,6 +202,54 @@ void oracle_mix_direct(const double *x, int64_t n_x, int32_t I, int32_t J,
         mix_direct_mic(x, n_x, n_x, I, J, j, rir, rir_off, L, alpha, y + (int64_t)j * n_x);
 }
 
+/* Eq. 2 at the output positions n in [n0, n1) only (any n >= 0; positions
+ * past n_x belong to the full output).  y: [J][n1 - n0] out.  Used to check
+ * sampled outputs of long signals without computing every sample. */
+void oracle_mix_window(const double *x, int64_t n_x, int32_t I, int32_t J,
+                       const double *rir, const int64_t *rir_off, const int64_t *L,
+                       const double *alpha, int64_t n0, int64_t n1, double *y)
+{
+    const int64_t w = n1 - n0;
+    for (int32_t j = 0; j < J; ++j) {
+        double *yj = y + (int64_t)j * w;
+        for (int64_t n = n0; n < n1; ++n) {
+            double sum = 0.0;
+            for (int32_t i = 0; i < I; ++i) {
+                const double *xi = x + (int64_t)i * n_x;
+                const double *h = rir + rir_off[i * J + j];
+                int64_t Lij = L[i * J + j];
+                int64_t kmax = (n < Lij - 1) ? n : Lij - 1;
+                int64_t kmin = (n - n_x + 1 > 0) ? n - n_x + 1 : 0;
+                double acc = 0.0;
+                for (int64_t k = kmin; k <= kmax; ++k) acc += h[k] * xi[n - k];
+                sum += alpha[i] * acc;
+            }
+            yj[n - n0] = sum;
+        }
+    }
+}
+
+/* Gradient of source i at input positions m in [m0, m1) only:
+ * dx_i[m] = alpha_i sum_j sum_{k < L_ij, m+k < n_y} hhat_ij[k] g_j[m+k].
+ * g: [J][n_y]; dx: [m1 - m0] out. */
+void oracle_dx_window(const double *g, int64_t n_y, int32_t J, int32_t i,
+                      const double *rir, const int64_t *rir_off, const int64_t *L,
+                      double alpha_i, int64_t m0, int64_t m1, double *dx)
+{
+    for (int64_t m = m0; m < m1; ++m) {
+        double sum = 0.0;
+        for (int32_t j = 0; j < J; ++j) {
+            const double *gj = g + (int64_t)j * n_y;
+            const double *h = rir + rir_off[i * J + j];
+            int64_t Lij = L[i * J + j];
+            double acc = 0.0;
+            for (int64_t k = 0; k < Lij && m + k < n_y; ++k) acc += h[k] * gj[m + k];
+            sum += acc;
+        }
+        dx[m - m0] = alpha_i * sum;
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Adjoint of Eq. 2 (one utterance, one source)                               */
 /* ------------------------------------------------------------------------ */

@@ -479,3 +479,33 @@ def test_full_output_adjoint_identities_and_numpy_gradients():
         np.testing.assert_allclose(gr["dh"][ro[rr]:ro[rr] + L[rr]], dh_ref, rtol=1e-11,
                                    atol=1e-11 * np.abs(dh_ref).max())
     np.testing.assert_allclose(gr["dx"][xo[s]:xo[s + 1]], dx_ref, rtol=1e-11, atol=1e-11 * np.abs(dx_ref).max())
+
+
+# ---------------------------------------------------------------------------
+# sampled-window forms (used on signals too long to compute in full)
+# ---------------------------------------------------------------------------
+def test_windows_equal_numpy_slices():
+    r = _rng(21)
+    I, J, nx = 3, 2, 400
+    x = r.standard_normal((I, nx))
+    rirs = [r.standard_normal(int(r.integers(5, 90))) for _ in range(I * J)]
+    L = [len(h) - int(r.integers(0, len(h) // 2)) for h in rirs]
+    alpha = r.uniform(0.3, 1.7, I)
+    ny = nx + max(len(h) for h in rirs) - 1
+    full = np.zeros((J, ny))
+    for j in range(J):
+        for i in range(I):
+            c = np.convolve(x[i], rirs[i * J + j][:L[i * J + j]])
+            full[j, :c.shape[0]] += alpha[i] * c
+    for n0, n1 in ((0, 50), (123, 400), (390, ny)):
+        np.testing.assert_allclose(oracle.mix_window(x, rirs, L, alpha, n0, n1), full[:, n0:n1],
+                                   rtol=1e-12, atol=1e-12)
+    g = r.standard_normal((J, ny))
+    for i in range(I):
+        ref = np.zeros(nx)
+        for j in range(J):
+            h = rirs[i * J + j][:L[i * J + j]]
+            ref += alpha[i] * np.convolve(g[j], h[::-1])[len(h) - 1:len(h) - 1 + nx]
+        for m0, m1 in ((0, 60), (200, 400)):
+            np.testing.assert_allclose(oracle.dx_window(g, rirs, L, i, alpha[i], m0, m1), ref[m0:m1],
+                                       rtol=1e-12, atol=1e-12)
