@@ -58,6 +58,7 @@ def algorithmic_work(batch, q, L):
     2I + J transforms and 2*I*J products, plus one inverse per RIR for dh;
     bytes: grad_y and x read once, grad_x written once, dh written once."""
     ff = fb = bf = bb = 0.0
+    ff5 = bf5 = 0.0           # the same with 5 N log2 N per transform (complex-FFT count)
     J = batch.num_mics
     ri = batch.rir_index()
     for u in range(batch.num_utts):
@@ -72,7 +73,9 @@ def algorithmic_work(batch, q, L):
         fb += 4.0 * (I + J) * nx
         bf += B * ((2 * I + J) * tr + 2 * I * J * mac) + I * J * tr
         bb += 4.0 * (J + 2 * I) * nx + 4.0 * float(np.sum(L[ri[u]:ri[u + 1]]))
-    return dict(fwd_flops=ff, fwd_bytes=fb, bwd_flops=bf, bwd_bytes=bb)
+        ff5 += B * ((I + J) * 2 * tr + I * J * mac)
+        bf5 += B * ((2 * I + J) * 2 * tr + 2 * I * J * mac) + I * J * 2 * tr
+    return dict(fwd_flops=ff, fwd_bytes=fb, bwd_flops=bf, bwd_bytes=bb, fwd_flops_5n=ff5, bwd_flops_5n=bf5)
 
 
 def roofline_entry(flops, nbytes, ms, p_fp32_tflops, hbm_gbs, peak_kind, traffic):
@@ -90,6 +93,21 @@ def roofline_entry(flops, nbytes, ms, p_fp32_tflops, hbm_gbs, peak_kind, traffic
     return {"bound": "hbm", "achieved": ach, "peak": hbm_gbs, "unit": "GB/s", "frac": ach / hbm_gbs,
             "traffic": traffic, "peak_source": peak_kind,
             "alu_side": {"achieved": flops / t / 1e12, "peak": p_fp32_tflops, "unit": "TFLOP/s"}}
+
+
+def step_roofline(work, ms, p_fp32_tflops, hbm_gbs):
+    """Whole step (forward + backward) against the roof: T_roof = max(bytes /
+    HBM bandwidth, flops / FP32 peak), fraction = T_roof / measured time."""
+    nbytes = work["fwd_bytes"] + work["bwd_bytes"]
+    t_b = nbytes / (hbm_gbs * 1e9)
+    out = {}
+    for key, fl in (("", work["fwd_flops"] + work["bwd_flops"]),
+                    ("_5NlogN", work["fwd_flops_5n"] + work["bwd_flops_5n"])):
+        t_roof = max(t_b, fl / (p_fp32_tflops * 1e12))
+        out["t_roof_ms" + key] = t_roof * 1e3
+        out["frac" + key] = t_roof / (ms / 1e3)
+    out["bound"] = "alu" if out["t_roof_ms"] > t_b * 1e3 else "hbm"
+    return out
 
 
 def _traffic_for(kernel):
@@ -421,7 +439,10 @@ def run_ours(args):
     roof.update({"kernel": f"{kname}<M> ({src}), all FFT-size launches of one step",
                  "stage_ms": per[kern], "launches_per_step": n_sizes,
                  "algorithmic_flops_per_step": work[f"{w}_flops"],
-                 "algorithmic_bytes_per_step": work[f"{w}_bytes"]})
+                 "algorithmic_bytes_per_step": work[f"{w}_bytes"],
+                 "frac_5NlogN": work[f"{w}_flops_5n"] / (per[kern] / 1e3) / 1e12 / p_fp32,
+                 "frac_5NlogN_note": "same kernel, counting 5 N log2 N flops per real N-point "
+                                     "transform (the complex-FFT count) instead of 2.5 N log2 N"})
     fwd_roof = roofline_entry(work["fwd_flops"], work["fwd_bytes"], per["forward"], p_fp32, hbm,
                               peak_kind, _traffic_for("k_forward"))
 
@@ -459,6 +480,7 @@ def run_ours(args):
         "stages_ms_per_step": per,
         "eager_ms_per_step": ms_eager,
         "roofline": roof,
+        "step_roofline": step_roofline(work, ms, p_fp32, hbm),
         "cpu_baseline": cpu,
         "plain_gpu": plain,
         "e2e": {"value": world * audio_s / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -32,8 +32,12 @@ MUTANTS = [
     ("gain_no_sqrt", "alpha[i] = sqrt(p0 / pi * pow(10.0, -snr_db[i] / 10.0));",
      "alpha[i] = p0 / pi * pow(10.0, -snr_db[i] / 10.0);"),
     ("dx_convolves_instead_of_correlates",
-     "for (int64_t k = 0; k < Lij && m + k < n_y; ++k) acc += h[k] * gj[m + k];",
-     "for (int64_t k = 0; k < Lij && m >= k; ++k) acc += h[k] * gj[m - k];"),
+     "for (int64_t k = 0; k < Lij && m + k < n_y; ++k) acc += h[k] * gj[m + k];\n            dx_i[m]",
+     "for (int64_t k = 0; k < Lij && m >= k; ++k) acc += h[k] * gj[m - k];\n            dx_i[m]"),
+    ("window_dx_convolves",
+     "for (int64_t k = 0; k < Lij && m + k < n_y; ++k) acc += h[k] * gj[m + k];\n            sum += acc;",
+     "for (int64_t k = 0; k < Lij && m >= k; ++k) acc += h[k] * gj[m - k];\n            sum += acc;"),
+    ("window_mix_ignores_gain", "sum += alpha[i] * acc;", "sum += acc;"),
     ("dh_transposed_operands", "acc += gj[n] * xi[n - k];", "acc += gj[n - k] * xi[n];"),
     ("dh_missing_gain", "dhij[k] = alpha[i] * acc;", "dhij[k] = acc;"),
     ("ola_hop_aliases", "int64_t hop = N - Lh + 1;", "int64_t hop = N - Lh + 2;"),
