@@ -218,6 +218,30 @@ def plain_step(torch, batch, xs, hs, snrs, gys):
     return None
 
 
+def _plain_inputs(torch, dev, b, x=None, rir=None, snr=None, gy=None):
+    """Per-utterance views (sources [I, Nx], zero-padded RIRs [I, J, Nh_max],
+    SNRs, upstream gradient [J, Nx]) for the plain path."""
+    from paper_1712_03439_gb300 import synth
+    x = torch.from_numpy(b.x).to(dev) if x is None else x
+    rir = torch.from_numpy(b.rir).to(dev) if rir is None else rir
+    snr = torch.from_numpy(b.snr_db).to(dev) if snr is None else snr
+    gy = torch.from_numpy(synth.grad_like(99, b.y_size)).to(dev) if gy is None else gy
+    xo, ro, si, ri = b.x_offsets(), b.rir_offsets(), b.src_index(), b.rir_index()
+    yo = b.y_offsets()
+    xs, hs, snrs, gys = [], [], [], []
+    for u in range(b.num_utts):
+        I, nx = int(b.num_sources[u]), int(b.num_samples[u])
+        xs.append(x[xo[si[u]]:xo[si[u + 1]]].view(I, nx))
+        lens = b.rir_len[ri[u]:ri[u + 1]]
+        hp = torch.zeros(I * b.num_mics, int(lens.max()), device=dev)
+        for k, r in enumerate(range(ri[u], ri[u + 1])):
+            hp[k, :lens[k]] = rir[ro[r]:ro[r + 1]]
+        hs.append(hp.view(I, b.num_mics, -1))
+        snrs.append(snr[si[u]:si[u + 1]])
+        gys.append(gy[yo[u]:yo[u + 1]].view(b.num_mics, nx))
+    return xs, hs, snrs, gys
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the FP64 CPU oracle on a bounded sample
 # ---------------------------------------------------------------------------
@@ -389,19 +413,7 @@ def run_ours(args):
     # ---- plain per-utterance GPU path (same step, torch.fft)
     plain = None
     if not args.no_plain:
-        xo, ro, si, ri = b.x_offsets(), b.rir_offsets(), b.src_index(), b.rir_index()
-        yo = b.y_offsets()
-        xs, hs, snrs, gys = [], [], [], []
-        for u in range(b.num_utts):
-            I, nx = int(b.num_sources[u]), int(b.num_samples[u])
-            xs.append(x[xo[si[u]]:xo[si[u + 1]]].view(I, nx))
-            lens = b.rir_len[ri[u]:ri[u + 1]]
-            hp = torch.zeros(I * b.num_mics, int(lens.max()), device=dev)
-            for k, r in enumerate(range(ri[u], ri[u + 1])):
-                hp[k, :lens[k]] = rir[ro[r]:ro[r + 1]]
-            hs.append(hp.view(I, b.num_mics, -1))
-            snrs.append(snr[si[u]:si[u + 1]])
-            gys.append(gy[yo[u]:yo[u + 1]].view(b.num_mics, nx))
+        xs, hs, snrs, gys = _plain_inputs(torch, dev, b, x=x, rir=rir, snr=snr, gy=gy)
         plain_step(torch, b, xs, hs, snrs, gys)
         torch.cuda.synchronize()
         kp = 2
@@ -496,6 +508,193 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# other workloads (reports beside the headline; not the default line)
+# ---------------------------------------------------------------------------
+def _peaks_fp32(torch, dev):
+    hbm, sm_mhz_max, peak_kind = _peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return hbm, sms * 128 * 2 * sm_mhz_max * 1e6 / 1e12, peak_kind
+
+
+def run_stream(args):
+    """Streaming queue of utterances (log-uniform 0.5-20 s, 1-4 sources, 2 mics)
+    in device-resident batches admitted by a memory budget, forward + backward."""
+    import torch
+    from paper_1712_03439_gb300 import build, synth
+    from paper_1712_03439_gb300.stream import Streamer
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    build.build()
+    b = synth.config_stream(n_utts=args.stream_utts)
+    st = Streamer(budget_bytes=int(args.budget_gb * (1 << 30)), eta_db=ETA_DB, backward=True,
+                  keep_outputs=False)
+    st.run(b.subset(range(min(64, b.num_utts))))          # warm-up (context, code, allocator)
+    clock = ClockSampler(0)
+    t0 = time.perf_counter()
+    res = st.run(b)
+    wall = time.perf_counter() - t0
+    clocks = clock.stop()
+    hbm, p_fp32, peak_kind = _peaks_fp32(torch, dev)
+    flops = nbytes = 0.0
+    off = 0
+    for r in res.records:
+        sub = b.subset(r.utts)
+        w = algorithmic_work(sub, r.query, r.trunc_len)
+        flops += w["fwd_flops"] + w["bwd_flops"]
+        nbytes += w["fwd_bytes"] + w["bwd_bytes"]
+    dev_s = sum(r.device_ms for r in res.records) / 1e3
+    t_roof = max(nbytes / (hbm * 1e9), flops / (p_fp32 * 1e12))
+    plain = None
+    if not args.no_plain:
+        sub = b.subset(range(min(64, b.num_utts)))
+        plain = _plain_rate(torch, dev, sub)
+    wall_sum = sum(r.wall_ms for r in res.records) / 1e3
+    line = {"metric": "simulated audio s/sec (fwd+bwd), streaming batches admitted by memory budget",
+            "value": res.audio_seconds / wall_sum, "unit": UNIT,
+            "value_note": "audio seconds / sum of per-batch wall latencies (batches run one after "
+                          "another); the harness's own host work (forming batches, synthetic "
+                          f"gradients) is outside, {wall:.1f} s in all", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32", "data": DATA,
+            "config": {"workload": f"stream-{b.num_utts}: lengths log-uniform 0.5-20 s, 1-4 sources, "
+                                   f"2 mics, RT60 U(0.1,0.9) s, eta {ETA_DB:g} dB",
+                       "budget_gb": args.budget_gb, "batches": len(res.records),
+                       "audio_seconds": res.audio_seconds},
+            "value_device": res.audio_seconds / dev_s,
+            "latency_ms": {"p50_wall": res.latency_ms(50), "p99_wall": res.latency_ms(99),
+                           "p50_device": res.latency_ms(50, "device_ms"),
+                           "p99_device": res.latency_ms(99, "device_ms"),
+                           "p50_plan": res.latency_ms(50, "plan_ms")},
+            "note": "wall: batch formed on the host to results on the host (pinned staging, plan "
+                    "creation, copies both ways, kernels); device: first copy to last copy on the stream",
+            "roofline": {"t_roof_s": t_roof, "device_s": dev_s, "frac": t_roof / dev_s,
+                         "bound": "alu" if flops / (p_fp32 * 1e12) >= nbytes / (hbm * 1e9) else "hbm",
+                         "peak_fp32_tflops": p_fp32, "peak_hbm_gbs": hbm, "peak_source": peak_kind},
+            "max_footprint_gb": max(r.footprint_bytes for r in res.records) / (1 << 30),
+            "plain_gpu": plain, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _plain_rate(torch, dev, sub):
+    xs, hs, snrs, gys = _plain_inputs(torch, dev, sub)
+    plain_step(torch, sub, xs, hs, snrs, gys)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain_step(torch, sub, xs, hs, snrs, gys)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": sub.audio_seconds() / dt, "unit": UNIT, "sample": f"{sub.num_utts} utterances"}
+
+
+def run_long(args):
+    """Long reverberant multi-mic workload (30 s, 4 sources, 8 mics, RT60 0.8-1.2 s):
+    cut-off sweep with work saved, energy error and forward+backward throughput."""
+    import torch
+    from paper_1712_03439_gb300 import Plan, build, synth
+    from paper_1712_03439_gb300._lib import RsimError
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    build.build()
+    b = synth.config_long(n_utts=args.long_utts)
+    audio_s = b.audio_seconds()
+    x, rir = torch.from_numpy(b.x).to(dev), torch.from_numpy(b.rir).to(dev)
+    snr = torch.from_numpy(b.snr_db).to(dev)
+    gy = torch.from_numpy(synth.grad_like(98, b.y_size)).to(dev)
+    # reference without a cut-off (full-length FFT convolution with torch.fft, FP64) on
+    # two utterances, for the output error each cut-off costs
+    ref_utts = [0, 1] if b.num_utts > 1 else [0]
+    si, xo, yo, ri, ro = b.src_index(), b.x_offsets(), b.y_offsets(), b.rir_index(), b.rir_offsets()
+    rhat = {}
+    for u in ref_utts:
+        I, nx, J = int(b.num_sources[u]), int(b.num_samples[u]), b.num_mics
+        xs = torch.from_numpy(b.x[xo[si[u]]:xo[si[u + 1]]].reshape(I, nx)).to(dev, torch.float64)
+        hs = [torch.from_numpy(b.rir[ro[r]:ro[r + 1]]).to(dev, torch.float64) for r in range(ri[u], ri[u + 1])]
+        n = 1 << int(math.ceil(math.log2(nx + max(h.numel() for h in hs) - 1)))
+        X = torch.fft.rfft(xs, n)
+        rhat[u] = (X, hs, n)
+    sweep = []
+    clock = ClockSampler(0)
+    for eta in (10.0, 20.0, 30.0, math.inf):
+        ent = {"eta_db": None if math.isinf(eta) else eta}
+        plan = Plan.for_batch(b, eta_db=eta, gain_mode=0, device=0)
+        gains, y = torch.empty(plan.S, device=dev), torch.empty(plan.y_size, device=dev)
+        tl = torch.empty(plan.R, dtype=torch.int32, device=dev)
+        ek = torch.empty(plan.R, device=dev)
+        gx, gr, gg = torch.empty_like(x), torch.empty_like(rir), torch.empty_like(gains)
+
+        def step():
+            plan.filter_mix(x, rir, gains, y, snr_db=snr, trunc_len=tl, energy_kept_frac=ek)
+            plan.filter_mix_backward(gy, x, gains, gx, gr, gg)
+        try:
+            step()
+            plan.sync_status()
+        except RsimError as e:
+            L = oracle_free_lengths(b, eta)
+            ent.update(unsupported=str(e), longest_kept_rir=int(L.max()),
+                       work_saved=float(np.sum(b.rir_len - L) / np.sum(b.rir_len)))
+            sweep.append(ent)
+            plan.close()
+            continue
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.long_steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.long_steps
+        L = tl.cpu().numpy().astype(np.int64)
+        a = gains.cpu().numpy().astype(np.float64)
+        errs = []
+        for u in ref_utts:
+            X, hs, n = rhat[u]
+            I, nx, J = int(b.num_sources[u]), int(b.num_samples[u]), b.num_mics
+            H = torch.stack([torch.fft.rfft(h, n) for h in hs]).reshape(I, J, -1)
+            A = torch.from_numpy(a[si[u]:si[u + 1]]).to(dev)
+            yref = torch.fft.irfft(torch.einsum("i,if,ijf->jf", A.to(X.dtype), X, H), n)[:, :nx]
+            yg = y[yo[u]:yo[u + 1]].reshape(J, nx).to(torch.float64)
+            errs.append(float(torch.linalg.norm(yg - yref) / torch.linalg.norm(yref)))
+        q = plan.query()
+        ent.update(value=audio_s / (ms / 1e3), unit=UNIT, ms_per_step=ms,
+                   work_saved=float(np.sum(b.rir_len - L) / np.sum(b.rir_len)),
+                   mean_kept_taps=float(L.mean()), longest_kept_rir=int(L.max()),
+                   energy_kept_frac_mean=float(ek.mean().item()),
+                   output_rel_l2_vs_no_cutoff=float(np.mean(errs)),
+                   fft_sizes={int(k): int(c) for k, c in zip(*np.unique(1 << q["log2_n"].astype(np.int64),
+                                                                        return_counts=True))})
+        sweep.append(ent)
+        plan.close()
+    clocks = clock.stop()
+    line = {"metric": "simulated audio s/sec (fwd+bwd) per cut-off, long reverberant multi-mic",
+            "unit": UNIT, "n_gpus": 1, "dtype": "f32", "data": DATA, "higher_is_better": True,
+            "config": {"workload": f"long-{b.num_utts}: {b.num_utts} x 30 s, 4 sources, 8-mic circle r=5 cm, "
+                                   "RT60 U(0.8,1.2) s", "audio_seconds": audio_s,
+                       "energy_error_reference": "full-length torch.fft FP64 convolution without cut-off, "
+                                                 f"utterances {ref_utts}"},
+            "sweep": sweep, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def oracle_free_lengths(b, eta):
+    """Kept lengths (Eq. 7-9) computed in numpy for the report when the library
+    rejects the batch (FP64 compare, as the kernels do)."""
+    ro = b.rir_offsets()
+    out = np.zeros(b.num_rirs, np.int64)
+    fac = 0.0 if math.isinf(eta) else 10.0 ** (-eta / 10.0)
+    for r in range(b.num_rirs):
+        h2 = b.rir[ro[r]:ro[r + 1]].astype(np.float64) ** 2
+        if math.isinf(eta) or h2.max() == 0:
+            out[r] = h2.size if math.isinf(eta) else 1
+            continue
+        idx = np.nonzero(h2 >= h2.max() * fac)[0]
+        out[r] = min(int(idx[-1]) + 2, h2.size)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -507,9 +706,20 @@ def main():
     ap.add_argument("--only-step", action="store_true",
                     help="time only the K steps (no forward-only, end-to-end, plain or CPU legs); "
                          "for profiler runs")
+    ap.add_argument("--config", choices=["home", "stream", "long"], default="home",
+                    help="home: the headline line; stream / long: reports on the streaming and the "
+                         "long reverberant workloads")
+    ap.add_argument("--stream-utts", type=int, default=4096)
+    ap.add_argument("--budget-gb", type=float, default=2.0)
+    ap.add_argument("--long-utts", type=int, default=32)
+    ap.add_argument("--long-steps", type=int, default=5)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == "stream":
+        return run_stream(args)
+    if args.config == "long":
+        return run_long(args)
     return run_ours(args)
 
 
