@@ -493,6 +493,9 @@ def run_ours(args):
         "eager_ms_per_step": ms_eager,
         "roofline": roof,
         "step_roofline": step_roofline(work, ms, p_fp32, hbm),
+        "fp32_peak_cross_check": {"derived_tflops": p_fp32, "probe": probe_fp32(dev.index),
+                                  "probe_what": "8 independent FMA chains per thread, full occupancy "
+                                                "(paper_1712_03439_gb300/probe/fp32_peak.cu)"},
         "cpu_baseline": cpu,
         "plain_gpu": plain,
         "e2e": {"value": world * audio_s / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -511,6 +514,22 @@ def run_ours(args):
 # ---------------------------------------------------------------------------
 # other workloads (reports beside the headline; not the default line)
 # ---------------------------------------------------------------------------
+def probe_fp32(device=0):
+    """FP32 FMA throughput measured by the probe kernel (TFLOP/s), or None."""
+    import ctypes
+    try:
+        from paper_1712_03439_gb300 import build
+        lib = ctypes.CDLL(build.build_probe())
+    except (OSError, RuntimeError):
+        return None
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    lib.fp32_peak_probe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    if lib.fp32_peak_probe(int(device), 4096, 5, ctypes.byref(tf), ctypes.byref(ms)) != 0:
+        return None
+    return {"tflops": tf.value, "ms": ms.value}
+
+
 def _peaks_fp32(torch, dev):
     hbm, sm_mhz_max, peak_kind = _peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count

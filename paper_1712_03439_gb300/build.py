@@ -38,6 +38,24 @@ def _stale(target, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+PROBE_SRC = os.path.join(PKG, "probe", "fp32_peak.cu")
+PROBE_LIB = os.path.join(PKG, "probe", "libfp32probe.so")
+
+
+def build_probe(force: bool = False) -> str:
+    """The FP32 FMA-throughput probe (a separate library; the benchmark's
+    roofline denominator)."""
+    if not force and not _stale(PROBE_LIB, [PROBE_SRC, __file__]):
+        return PROBE_LIB
+    tmp = PROBE_LIB + ".tmp"
+    r = subprocess.run([_nvcc(), *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+                        PROBE_SRC, "-o", tmp], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for the FP32 probe:\n{r.stderr}")
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     """Compiles every CUDA translation unit for sm_103a and links librsim.so."""
     deps = _deps()
