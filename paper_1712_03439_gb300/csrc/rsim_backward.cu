@@ -230,16 +230,20 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
                 }
                 irfft_x<M, E, false>(v, C, ex, tw, t);
                 if (dxi) {
+                    // samples [0, min(hop, Nx - pos)) of the block; the first mic group
+                    // writes, later groups add; pairs go out as one 8-byte store when aligned
+                    float* dst = dxi + pos;
+                    const int ilim = (int)min((int64_t)hop, lim);
+                    const bool pairs = ((reinterpret_cast<uintptr_t>(dst) & 7) == 0) && j0 == 0;
 #pragma unroll
                     for (int q = 0; q < E; ++q) {
                         const int n = 2 * (t + q * T);
-#pragma unroll
-                        for (int e = 0; e < 2; ++e) {
-                            const int nn = n + e;
-                            if (nn < hop && nn < lim) {
-                                const float d = a * (e ? v[q].y : v[q].x);
-                                dxi[pos + nn] = (j0 == 0) ? d : dxi[pos + nn] + d;
-                            }
+                        const float d0 = a * v[q].x, d1 = a * v[q].y;
+                        if (pairs && n + 1 < ilim) {
+                            *reinterpret_cast<float2*>(dst + n) = make_float2(d0, d1);
+                        } else {
+                            if (n < ilim) dst[n] = (j0 == 0) ? d0 : dst[n] + d0;
+                            if (n + 1 < ilim) dst[n + 1] = (j0 == 0) ? d1 : dst[n + 1] + d1;
                         }
                     }
                 }

@@ -385,16 +385,24 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 // Queues the copy of the real block src[0, len) into stage[0, 2M), zeros
-// beyond len.  Thread t copies elements t + k*T (coalesced).
+// beyond len.  Thread t copies elements t + k*T (coalesced): rows wholly
+// inside the block copy without a per-element predicate, the one ragged row
+// is predicated, and rows past the block are zeroed with plain stores.
 template <int M, int E>
 __device__ __forceinline__ void stage_real_async(float* __restrict__ stage, const float* __restrict__ src,
                                                  int64_t len, int t) {
     constexpr int T = M / E;
-#pragma unroll 8
-    for (int k = 0; k < 2 * E; ++k) {
-        const int n = t + k * T;
-        const bool ok = n < len;
-        cp_async4(stage + n, ok ? src + n : src, ok);
+    const int ilen = (int)(len < 2 * M ? (len > 0 ? len : 0) : 2 * M);
+    const int kfull = ilen / T;                  // rows wholly inside the block
+    float* d = stage + t;
+    const float* s = src + t;
+#pragma unroll 4
+    for (int k = 0; k < kfull; ++k) cp_async4(d + k * T, s + k * T, true);
+    if (kfull < 2 * E) {
+        const bool ok = kfull * T + t < ilen;
+        cp_async4(d + kfull * T, ok ? s + kfull * T : src, ok);
+#pragma unroll 4
+        for (int k = kfull + 1; k < 2 * E; ++k) d[k * T] = 0.f;
     }
 }
 

@@ -225,13 +225,19 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
                     // every sample n < N of the block adds the carried sum at n;
                     // [0, hop) is stored, [hop, N) becomes the new carry (which
                     // reaches several blocks ahead when L_max - 1 > hop)
+                    const int ilim = (int)min((int64_t)hop, lim);
+                    const bool pairs = (reinterpret_cast<uintptr_t>(yj) & 7) == 0;
 #pragma unroll
                     for (int q = 0; q < E; ++q) {
                         const int n = 2 * (t + q * T);
                         if (n < tail_len) v[q].x += tlj[n];
                         if (n + 1 < tail_len) v[q].y += tlj[n + 1];
-                        if (n < hop && n < lim) yj[n] = v[q].x;
-                        if (n + 1 < hop && n + 1 < lim) yj[n + 1] = v[q].y;
+                        if (pairs && n + 1 < ilim) {
+                            *reinterpret_cast<float2*>(yj + n) = v[q];
+                        } else {
+                            if (n < ilim) yj[n] = v[q].x;
+                            if (n + 1 < ilim) yj[n + 1] = v[q].y;
+                        }
                     }
                     __syncthreads();
 #pragma unroll
