@@ -288,11 +288,26 @@ k_fixup(DevBatch B, float* __restrict__ y, const float* __restrict__ tails) {
         const int64_t pos = b0 * hop;
         const int tail_len = B.Lmax[u] - 1;
         const int64_t ye = min(ny, B.n_x[u] + (int64_t)tail_len);
+        const int lim = (int)min((int64_t)tail_len, ye - pos);
+        // four independent read-add-write rounds in flight per thread
+        constexpr int kU = 4;
         for (int j = 0; j < B.J; ++j) {
             const float* src = tails + ((int64_t)(g - 1) * B.J + j) * 2 * B.MMAX;
             float* yj = y + B.yoff[u] + (int64_t)j * ny + pos;
-            for (int n = threadIdx.x; n < tail_len && pos + n < ye; n += blockDim.x)
-                yj[n] = yj[n] + src[n];
+            for (int n0 = threadIdx.x; n0 < lim; n0 += kU * blockDim.x) {
+                float a[kU], c[kU];
+#pragma unroll
+                for (int k = 0; k < kU; ++k) {
+                    const int n = n0 + k * blockDim.x;
+                    a[k] = n < lim ? yj[n] : 0.f;
+                    c[k] = n < lim ? src[n] : 0.f;
+                }
+#pragma unroll
+                for (int k = 0; k < kU; ++k) {
+                    const int n = n0 + k * blockDim.x;
+                    if (n < lim) yj[n] = a[k] + c[k];
+                }
+            }
         }
     }
 }
