@@ -179,7 +179,7 @@ void rsim_plan_destroy(rsim_plan_t plan);
  * is one fixed 2 MiB device array inside the library, present on every GPU
  * that loads the library until the process exits; a batch needing more
  * (about 8 bytes per source per 32768 samples of the longest utterance plus
- * 24 bytes per source and utterance) is rejected with RSIM_E_UNSUPPORTED and
+ * 28 bytes per source and utterance) is rejected with RSIM_E_UNSUPPORTED and
  * a message.  Nothing in the scratch has to start at zero: each call writes
  * every entry it reads.  All calls share that one array, so calls whose work
  * overlaps on the GPU race; queue them on one stream or wait between them.

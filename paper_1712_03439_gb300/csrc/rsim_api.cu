@@ -261,6 +261,11 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
             }
         xoff[S] = o;
     }
+    std::vector<int32_t> src_utt(std::max<int64_t>(S, 1)), rir_utt(std::max<int64_t>(R, 1));
+    for (int u = 0; u < U; ++u) {
+        for (int s = src0[u]; s < src0[u + 1]; ++s) src_utt[s] = u;
+        for (int r = rir0[u]; r < rir0[u + 1]; ++r) rir_utt[r] = u;
+    }
     std::vector<int32_t> seg_utt(std::max<int64_t>(nseg, 1)), bseg_utt(std::max<int64_t>(nbseg, 1));
     std::vector<int64_t> dhp_off(nbseg + 1);
     int64_t dhp_total = 0;
@@ -295,6 +300,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     struct Piece { void** dst; size_t bytes; };
     std::vector<Piece> pieces;
     void *p_bseg0, *p_bsegutt;
+    void *p_srcutt, *p_rirutt;
     void *p_nsrc, *p_nx, *p_ny, *p_src0, *p_rir0, *p_seg0, *p_segutt, *p_xoff, *p_yoff, *p_roff, *p_rlen,
         *p_dhpoff, *p_tuning, *p_L, *p_logN, *p_hop, *p_lmax, *p_nblk, *p_pow, *p_err, *p_list,
         *p_count, *p_next, *p_Hc, *p_tails, *p_dhp, *p_dap;
@@ -330,6 +336,8 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     pieces.push_back({&p_yoff, sizeof(int64_t) * (U + 1)});
     pieces.push_back({&p_roff, sizeof(int64_t) * (R + 1)});
     pieces.push_back({&p_rlen, sizeof(int32_t) * R});
+    pieces.push_back({&p_srcutt, sizeof(int32_t) * std::max<int64_t>(S, 1)});
+    pieces.push_back({&p_rirutt, sizeof(int32_t) * std::max<int64_t>(R, 1)});
     pieces.push_back({&p_dhpoff, sizeof(int64_t) * (nbseg + 1)});
     pieces.push_back({&p_tuning, sizeof(float) * 32});
     pieces.push_back({&p_L, sizeof(int32_t) * R});
@@ -393,6 +401,8 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
         {p_yoff, yoff.data(), sizeof(int64_t) * (U + 1)},
         {p_roff, roff.data(), sizeof(int64_t) * (R + 1)},
         {p_rlen, rlen.data(), sizeof(int32_t) * R},
+        {p_srcutt, src_utt.data(), sizeof(int32_t) * S},
+        {p_rirutt, rir_utt.data(), sizeof(int32_t) * R},
         {p_dhpoff, dhp_off.data(), sizeof(int64_t) * (nbseg + 1)},
         {p_tuning, tuning.data(), sizeof(float) * 32},
     };
@@ -424,6 +434,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     B.seg0 = (const int32_t*)p_seg0; B.seg_utt = (const int32_t*)p_segutt;
     B.xoff = (const int64_t*)p_xoff; B.yoff = (const int64_t*)p_yoff;
     B.roff = (const int64_t*)p_roff; B.rir_len = (const int32_t*)p_rlen;
+    B.src_utt = (const int32_t*)p_srcutt; B.rir_utt = (const int32_t*)p_rirutt;
     B.dhp_off = (const int64_t*)p_dhpoff; B.tuning = (const float*)p_tuning;
     B.L = (int32_t*)p_L; B.logN = (int32_t*)p_logN; B.hop = (int32_t*)p_hop;
     B.Lmax = (int32_t*)p_lmax; B.nblk = (int32_t*)p_nblk;

@@ -287,12 +287,7 @@ k_finalize(DevBatch B, const float* __restrict__ gains, const float* __restrict_
     __shared__ int64_t seg_off[kFinMaxSegs];   // dh-partial offsets of the non-empty segments
     __shared__ int nseg_live;
     for (int r = blockIdx.x; r < B.R; r += gridDim.x) {
-        int lo = 0, hi = B.U - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (B.rir0[mid] <= r) lo = mid; else hi = mid - 1;
-        }
-        const int u = lo;
+        const int u = B.rir_utt[r];
         const int i = (r - B.rir0[u]) / B.J;
         const int Lr = B.L[r], nh = B.rir_len[r];
         float* out = grad_rir + B.roff[r];
@@ -341,12 +336,7 @@ k_finalize(DevBatch B, const float* __restrict__ gains, const float* __restrict_
     }
     if (grad_gains) {
         for (int sidx = blockIdx.x * blockDim.x + threadIdx.x; sidx < B.S; sidx += gridDim.x * blockDim.x) {
-            int lo = 0, hi = B.U - 1;
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (B.src0[mid] <= sidx) lo = mid; else hi = mid - 1;
-            }
-            const int u = lo, i = sidx - B.src0[u];
+            const int u = B.src_utt[sidx], i = sidx - B.src0[u];
             float acc = 0.f;
             if (B.logN[u] != 0) {
                 for (int g = B.bseg0[u]; g < B.bseg0[u + 1]; ++g) {

@@ -46,6 +46,8 @@ struct DevBatch {
     const int64_t* yoff;     // [U+1] offset of utterance u in y
     const int64_t* roff;     // [R+1] offset of RIR r in rir
     const int32_t* rir_len;  // [R]
+    const int32_t* src_utt;  // [S] utterance of source s
+    const int32_t* rir_utt;  // [R] utterance of RIR r
     int32_t NBSEG;           // total backward segments
     int64_t bseg_len;        // samples per backward segment (>= largest allowed N)
     const int32_t* bseg0;    // [U+1] first backward segment of utterance

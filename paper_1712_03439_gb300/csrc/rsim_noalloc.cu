@@ -54,15 +54,17 @@ constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 // Offsets of the packed sources (one thread; the batch is small by the
 // scratch bound): src0[u] = first source of utterance u, xoff[s] = offset of
-// source s in x.
+// source s in x, src_utt[s] = utterance of source s.
 __global__ void k_offsets_noalloc(int U, const int32_t* __restrict__ nsrc, const int64_t* __restrict__ nx,
-                                  int32_t* __restrict__ src0, int64_t* __restrict__ xoff) {
+                                  int32_t* __restrict__ src0, int64_t* __restrict__ xoff,
+                                  int32_t* __restrict__ src_utt) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     int32_t s = 0;
     int64_t o = 0;
     for (int u = 0; u < U; ++u) {
         src0[u] = s;
         for (int i = 0; i < nsrc[u]; ++i) {
+            src_utt[s] = u;
             xoff[s++] = o;
             o += nx[u];
         }
@@ -116,12 +118,13 @@ extern "C" rsim_status rsim_source_gains_noalloc(void* stream, int32_t num_utts,
     }
     const int64_t CH = (nx_max + kPowerChunk - 1) / kPowerChunk;
     // scratch layout: num_sources [U] i32 | n_x [U] i64 | src0 [U+1] i32 |
-    //                 xoff [S+1] i64 | partial sums [S*CH] f64
+    //                 xoff [S+1] i64 | src_utt [S] i32 | partial sums [S*CH] f64
     const size_t o_nsrc = 0;
     const size_t o_nx = align256(o_nsrc + sizeof(int32_t) * U);
     const size_t o_src0 = align256(o_nx + sizeof(int64_t) * U);
     const size_t o_xoff = align256(o_src0 + sizeof(int32_t) * (U + 1));
-    const size_t o_part = align256(o_xoff + sizeof(int64_t) * (S + 1));
+    const size_t o_sutt = align256(o_xoff + sizeof(int64_t) * (S + 1));
+    const size_t o_part = align256(o_sutt + sizeof(int32_t) * S);
     const size_t need = o_part + sizeof(double) * (size_t)S * (size_t)CH;
     if (need > kNoAllocScratchBytes) {
         set_last_error(("rsim_source_gains_noalloc: this batch needs " + std::to_string(need) +
@@ -159,9 +162,11 @@ extern "C" rsim_status rsim_source_gains_noalloc(void* stream, int32_t num_utts,
     B.n_x = reinterpret_cast<const int64_t*>(b + o_nx);
     B.src0 = reinterpret_cast<const int32_t*>(b + o_src0);
     B.xoff = reinterpret_cast<const int64_t*>(b + o_xoff);
+    B.src_utt = reinterpret_cast<const int32_t*>(b + o_sutt);
     B.pow_part = reinterpret_cast<double*>(b + o_part);
     k_offsets_noalloc<<<1, 32, 0, st>>>(U, B.n_src, B.n_x, reinterpret_cast<int32_t*>(b + o_src0),
-                                        reinterpret_cast<int64_t*>(b + o_xoff));
+                                        reinterpret_cast<int64_t*>(b + o_xoff),
+                                        reinterpret_cast<int32_t*>(b + o_sutt));
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(S * CH, (int64_t)std::max(sms, 1) * 8));

@@ -126,13 +126,7 @@ k_power(DevBatch B, const float* __restrict__ x) {
     const int64_t total = (int64_t)B.S * B.CH;
     for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
         const int s = (int)(w / B.CH), c = (int)(w % B.CH);
-        // utterance of source s: binary search over src0
-        int lo = 0, hi = B.U - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (B.src0[mid] <= s) lo = mid; else hi = mid - 1;
-        }
-        const int64_t nx = B.n_x[lo];
+        const int64_t nx = B.n_x[B.src_utt[s]];
         const int64_t c0 = (int64_t)c * kPowerChunk;
         if (c0 >= nx) continue;                 // uniform across the CTA
         const int64_t c1 = (c0 + kPowerChunk < nx) ? c0 + kPowerChunk : nx;
@@ -155,10 +149,14 @@ k_power(DevBatch B, const float* __restrict__ x) {
         for (int64_t i = tail0 + t; i < len; i += kPowThreads) acc(1, __ldg(p + i));
         const float4* p4 = reinterpret_cast<const float4*>(p + head);
         int64_t j = t;
-        for (; j + kPowThreads < nvec; j += 2 * kPowThreads) {
-            const float4 a = __ldg(p4 + j), b = __ldg(p4 + j + kPowThreads);
-            acc(0, a.x); acc(1, a.y); acc(2, a.z); acc(3, a.w);
-            acc(0, b.x); acc(1, b.y); acc(2, b.z); acc(3, b.w);
+        for (; j + 3 * kPowThreads < nvec; j += 4 * kPowThreads) {
+            float4 a[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) a[k] = __ldg(p4 + j + k * kPowThreads);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                acc(0, a[k].x); acc(1, a[k].y); acc(2, a[k].z); acc(3, a[k].w);
+            }
         }
         for (; j < nvec; j += kPowThreads) {
             const float4 a = __ldg(p4 + j);
