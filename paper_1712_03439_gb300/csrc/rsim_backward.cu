@@ -93,6 +93,7 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
     constexpr int NST = L::NST;
     constexpr bool kWait = NST == 2;      // stage completion folded into the transforms
     constexpr bool kRollSteps = L::NSM == 2;
+    constexpr bool kPaired = PairedSplit<M, E>::ok;   // split in registers (paired layout)
     using Pl = FftPlan<M, E>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Exch<L::NSM> ex{reinterpret_cast<float2*>(smem_raw + L::o_sm),
@@ -110,6 +111,8 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
         tw = tws;
     }
     const float2* wsplit = tw + Pl::OFF_SPLIT;
+    // first bin of this thread's pairs: t (pair layout) or its paired butterfly
+    const int kt = kPaired ? paired_butterfly<T>(t) : t;
     int sc = 0;                                  // stage holding the next transform input
     auto stage = [&](int k) { return st0 + (NST == 2 ? k : 0) * (2 * M); };
     for (;;) {
@@ -169,15 +172,22 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
             cp_async_commit();
             cp_async_wait<0>();
             __syncthreads();
-            // C += conj(H_j) G_j and W_j += conj(X) G_j from the spectrum in z
-            auto mac = [&](float2 (&Wj)[E], float2 (&C)[E], const float2 (&X)[E], const float2* z, int jj) {
+            // C += conj(H_j) G_j and W_j += conj(X) G_j; G_j from the spectrum in z
+            // (split here) or already split in registers (paired layout)
+            auto mac = [&](float2 (&Wj)[E], float2 (&C)[E], const float2 (&X)[E], const float2* z,
+                           const float2 (&G)[E], int jj) {
                 const float2* Hg = Hc + (int64_t)(rb + i * J + j0 + jj) * B.MMAX;
 #pragma unroll
                 for (int q = 0; q < E / 2; ++q) {
-                    const int k = t + q * T;
+                    const int k = kt + q * T;
                     const int kb = (k == 0) ? M / 2 : M - k;
                     float2 ga, gb;
-                    split_pair<M>(z, wsplit, k, ga, gb);
+                    if constexpr (kPaired) {
+                        ga = G[2 * q];
+                        gb = G[2 * q + 1];
+                    } else {
+                        split_pair<M>(z, wsplit, k, ga, gb);
+                    }
                     float2 ha, hb;
                     if constexpr (L::kStageH) {
                         ha = hs[jj * M + k];
@@ -212,10 +222,23 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
                 for (int sp = 0; sp <= kJG; ++sp) {
                     if (sp > jn) break;
                     next_input(v, b, sp < jn ? j0 + sp : -1);
-                    const float2* z = rfft_x<M, E, kWait>(v, ex, tw, t);
-                    if (sp == 0) split_forward<M, E>(X, z, wsplit, t);
-                    else if (sp == 1) mac(W[0], C, X, z, 0);
-                    else mac(W[1], C, X, z, 1);
+                    if constexpr (kPaired) {
+                        float2 G[E];
+                        rfft_paired<M, E, kWait>(G, v, ex, tw, t, kt);
+                        if (sp == 0) {
+#pragma unroll
+                            for (int e = 0; e < E; ++e) X[e] = G[e];
+                        } else if (sp == 1) {
+                            mac(W[0], C, X, nullptr, G, 0);
+                        } else {
+                            mac(W[1], C, X, nullptr, G, 1);
+                        }
+                    } else {
+                        const float2* z = rfft_x<M, E, kWait>(v, ex, tw, t);
+                        if (sp == 0) split_forward<M, E>(X, z, wsplit, t);
+                        else if (sp == 1) mac(W[0], C, X, z, v, 0);
+                        else mac(W[1], C, X, z, v, 1);
+                    }
                 }
                 // <c, x_block> by Parseval on the half spectra already in registers
                 // (x_block is zero beyond its length, so only n < hop counts):
@@ -223,12 +246,13 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
                 // and N/2 once and every other bin of the half spectrum twice.
 #pragma unroll
                 for (int q = 0; q < E / 2; ++q) {
-                    const int k = t + q * T;
+                    const int k = kt + q * T;
                     const float p0 = C[2 * q].x * X[2 * q].x + C[2 * q].y * X[2 * q].y;
                     const float p1 = C[2 * q + 1].x * X[2 * q + 1].x + C[2 * q + 1].y * X[2 * q + 1].y;
                     da += (k == 0 ? p0 : 2.f * p0) + 2.f * p1;
                 }
-                irfft_x<M, E, false>(v, C, ex, tw, t);
+                if constexpr (kPaired) irfft_paired<M, E>(v, C, ex, tw, t, kt);
+                else irfft_x<M, E, false>(v, C, ex, tw, t);
                 if (dxi) {
                     // samples [0, min(hop, Nx - pos)) of the block; the first mic group
                     // writes, later groups add; pairs go out as one 8-byte store when aligned
@@ -254,7 +278,8 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
                 float2 v[E], Pw[E];
 #pragma unroll
                 for (int e = 0; e < E; ++e) Pw[e] = jj ? W[1][e] : W[0][e];
-                irfft_x<M, E, false>(v, Pw, ex, tw, t);
+                if constexpr (kPaired) irfft_paired<M, E>(v, Pw, ex, tw, t, kt);
+                else irfft_x<M, E, false>(v, Pw, ex, tw, t);
                 const int r = rb + i * J + j0 + jj;
                 const int Lr = B.L[r];
                 float* out = dhp + B.dhp_off[g] + (B.roff[r] - B.roff[rb]);

@@ -548,4 +548,138 @@ __device__ __forceinline__ void irfft_x(float2 (&v)[E], const float2 (&P)[E], Ex
     for (int s = 0; s < E; ++s) v[s] = conjf2(v[s]);
 }
 
+// ---------------------------------------------------------------------------
+// real split in registers (last pass of full radix)
+// ---------------------------------------------------------------------------
+// When every pass has radix E (M = E^k), the last forward pass can be given to
+// the threads in an order that puts butterflies i and T - i (whose outputs
+// hold the mirror bins k and M - k) in lanes l and l ^ 16 of one warp; the
+// even/odd split then needs one register swap between those lanes instead of
+// a trip through shared memory.  Butterflies 0 and T/2 mirror onto
+// themselves.  The half spectrum comes out in "paired layout": thread t with
+// butterfly i = paired_butterfly(t) holds P[2m] = X[k_m], P[2m+1] = X[M-k_m],
+// k_m = i + T m, m < E/2 (k = 0: P[0] = (X[0], X[M]) packed, P[1] = X[M/2]).
+// The inverse takes the same layout, swaps the mirror halves back and runs
+// its first pass with butterfly i.
+template <int M, int E>
+struct PairedSplit {
+    static constexpr bool ok = FftPlan<M, E>::R_LAST == E && (M / E) % 32 == 0;
+};
+
+template <int T>
+__device__ __forceinline__ int paired_butterfly(int t) {
+    const int w = t >> 5, l = t & 31;
+    if (l < 16) return 16 * w + l;
+    if (w == 0 && l == 16) return T / 2;
+    return T - (16 * w + l - 16);
+}
+
+// forward passes P..; the last one runs butterfly i.  WAIT as for rfft_x,
+// folded into the last exchange.
+template <int M, int E, int P, bool WAIT, int NB>
+__device__ __forceinline__ void fft_from_paired(float2 (&v)[E], Exch<NB>& ex, const float2* __restrict__ tw,
+                                                int t, int i) {
+    using Pl = FftPlan<M, E>;
+    constexpr int R = Pl::radix(P), LP = Pl::lp(P);
+    if constexpr (P == Pl::NPASS - 1) {
+        fft_pass<M, E, R, LP, true>(v, nullptr, tw + Pl::tw_off(P), i);
+    } else {
+        float2* b = ex.begin();
+        fft_pass<M, E, R, LP, false>(v, b, tw + Pl::tw_off(P), t);
+        constexpr bool kLastExchange = P + 1 == Pl::NPASS - 1;
+        if constexpr (WAIT && kLastExchange) cp_async_wait<0>();
+        __syncthreads();
+        load_strided<M, E>(v, b, kLastExchange ? i : t);
+        ex.end();
+        fft_from_paired<M, E, P + 1, WAIT, NB>(v, ex, tw, t, i);
+    }
+}
+
+// Forward real FFT of strided registers v into paired layout P.
+template <int M, int E, bool WAIT, int NB>
+__device__ __forceinline__ void rfft_paired(float2 (&P)[E], float2 (&v)[E], Exch<NB>& ex,
+                                            const float2* __restrict__ tw, int t, int i) {
+    static_assert(PairedSplit<M, E>::ok, "paired split needs M = E^k");
+    constexpr int T = M / E;
+    fft_from_paired<M, E, 0, WAIT, NB>(v, ex, tw, t, i);
+    const float2* wsplit = tw + FftPlan<M, E>::OFF_SPLIT;
+    float2 pw[E / 2];                       // the partner lane's mirror values
+#pragma unroll
+    for (int m = 0; m < E / 2; ++m) {
+        pw[m].x = __shfl_xor_sync(0xffffffffu, v[E - 1 - m].x, 16);
+        pw[m].y = __shfl_xor_sync(0xffffffffu, v[E - 1 - m].y, 16);
+    }
+#pragma unroll
+    for (int m = 0; m < E / 2; ++m) {
+        if (i == 0 && m == 0) {             // bins 0, M and M/2 (all from this thread)
+            const float2 z0 = v[0], zh = v[E / 2];
+            P[0] = make_float2(z0.x + z0.y, z0.x - z0.y);
+            P[1] = conjf2(zh);
+            continue;
+        }
+        const int k = i + T * m;
+        const float2 zk = v[m];
+        const float2 zm = conjf2((i == 0) ? v[E - m] : (i == T / 2 ? v[E - 1 - m] : pw[m]));
+        const float2 Ev = cscale(cadd(zk, zm), 0.5f);
+        const float2 Od = cscale(mul_mi(csub(zk, zm)), 0.5f);   // (zk - zm) / (2i)
+        const float2 wO = cmul(wsplit[k], Od);
+        P[2 * m] = cadd(Ev, wO);
+        P[2 * m + 1] = conjf2(csub(Ev, wO));
+    }
+}
+
+// Unnormalised inverse real FFT of a half spectrum in paired layout; on
+// return v[s] holds (y[2n], y[2n+1]) * 2M for n = t + s*T (as irfft_pairs).
+template <int M, int E, int NB>
+__device__ __forceinline__ void irfft_paired(float2 (&v)[E], const float2 (&P)[E], Exch<NB>& ex,
+                                             const float2* __restrict__ tw, int t, int i) {
+    static_assert(PairedSplit<M, E>::ok, "paired split needs M = E^k");
+    constexpr int T = M / E;
+    using Pl = FftPlan<M, E>;
+    const float2* wsplit = tw + Pl::OFF_SPLIT;
+    float2 mir[E / 2];                      // conj(Z') at the mirror bins M - k_m
+#pragma unroll
+    for (int m = 0; m < E / 2; ++m) {
+        if (i == 0 && m == 0) {
+            const float2 ya = P[0], yb = P[1];
+            v[0] = conjf2(make_float2(ya.x + ya.y, ya.x - ya.y));
+            v[E / 2] = cscale(yb, 2.f);
+            mir[0] = make_float2(0.f, 0.f);
+            continue;
+        }
+        const int k = i + T * m;
+        const float2 ya = P[2 * m], ym = conjf2(P[2 * m + 1]);
+        const float2 Ev = cadd(ya, ym);
+        const float2 O = cmulc(wsplit[k], csub(ya, ym));
+        v[m] = conjf2(cadd(Ev, mul_pi(O)));
+        mir[m] = conjf2(cadd(conjf2(Ev), mul_pi(conjf2(O))));
+    }
+    float2 got[E / 2];
+#pragma unroll
+    for (int m = 0; m < E / 2; ++m) {
+        got[m].x = __shfl_xor_sync(0xffffffffu, mir[m].x, 16);
+        got[m].y = __shfl_xor_sync(0xffffffffu, mir[m].y, 16);
+    }
+    if (i == 0) {
+#pragma unroll
+        for (int m = 1; m < E / 2; ++m) v[E - m] = mir[m];
+    } else if (i == T / 2) {
+#pragma unroll
+        for (int m = 0; m < E / 2; ++m) v[E - 1 - m] = mir[m];
+    } else {
+#pragma unroll
+        for (int m = 0; m < E / 2; ++m) v[E - 1 - m] = got[m];
+    }
+    {
+        float2* b = ex.begin();
+        fft_pass<M, E, Pl::radix(0), 1, false>(v, b, tw, i);
+        __syncthreads();
+        load_strided<M, E>(v, b, t);
+        ex.end();
+    }
+    fft_from_x<M, E, 1, NB>(v, ex, tw, t);
+#pragma unroll
+    for (int s = 0; s < E; ++s) v[s] = conjf2(v[s]);
+}
+
 }  // namespace rsim
