@@ -595,37 +595,49 @@ __device__ __forceinline__ void fft_from_paired(float2 (&v)[E], Exch<NB>& ex, co
     }
 }
 
-// Forward real FFT of strided registers v into paired layout P.
-template <int M, int E, bool WAIT, int NB>
-__device__ __forceinline__ void rfft_paired(float2 (&P)[E], float2 (&v)[E], Exch<NB>& ex,
-                                            const float2* __restrict__ tw, int t, int i) {
-    static_assert(PairedSplit<M, E>::ok, "paired split needs M = E^k");
-    constexpr int T = M / E;
-    fft_from_paired<M, E, 0, WAIT, NB>(v, ex, tw, t, i);
-    const float2* wsplit = tw + FftPlan<M, E>::OFF_SPLIT;
-    float2 pw[E / 2];                       // the partner lane's mirror values
+// The partner lane's mirror values pw[m] = partner's v[E-1-m], m < E/2.
+template <int E>
+__device__ __forceinline__ void paired_swap(float2 (&pw)[E / 2], const float2 (&v)[E]) {
 #pragma unroll
     for (int m = 0; m < E / 2; ++m) {
         pw[m].x = __shfl_xor_sync(0xffffffffu, v[E - 1 - m].x, 16);
         pw[m].y = __shfl_xor_sync(0xffffffffu, v[E - 1 - m].y, 16);
     }
-#pragma unroll
-    for (int m = 0; m < E / 2; ++m) {
-        if (i == 0 && m == 0) {             // bins 0, M and M/2 (all from this thread)
-            const float2 z0 = v[0], zh = v[E / 2];
-            P[0] = make_float2(z0.x + z0.y, z0.x - z0.y);
-            P[1] = conjf2(zh);
-            continue;
-        }
-        const int k = i + T * m;
-        const float2 zk = v[m];
-        const float2 zm = conjf2((i == 0) ? v[E - m] : (i == T / 2 ? v[E - 1 - m] : pw[m]));
-        const float2 Ev = cscale(cadd(zk, zm), 0.5f);
-        const float2 Od = cscale(mul_mi(csub(zk, zm)), 0.5f);   // (zk - zm) / (2i)
-        const float2 wO = cmul(wsplit[k], Od);
-        P[2 * m] = cadd(Ev, wO);
-        P[2 * m + 1] = conjf2(csub(Ev, wO));
+}
+
+// Split of pair m in paired layout: xa = X[k_m], xb = X[M - k_m] (for k = 0:
+// xa = (X[0], X[M]), xb = X[M/2]), from v[m] = Z[k_m] and the mirror value.
+template <int M, int E>
+__device__ __forceinline__ void paired_split_pair(const float2 (&v)[E], const float2 (&pw)[E / 2],
+                                                  const float2* __restrict__ wsplit, int i, int m,
+                                                  float2& xa, float2& xb) {
+    constexpr int T = M / E;
+    if (i == 0 && m == 0) {                 // bins 0, M and M/2 (all from this thread)
+        const float2 z0 = v[0], zh = v[E / 2];
+        xa = make_float2(z0.x + z0.y, z0.x - z0.y);
+        xb = conjf2(zh);
+        return;
     }
+    const float2 zk = v[m];
+    const float2 zm = conjf2((i == 0) ? v[E - m] : (i == T / 2 ? v[E - 1 - m] : pw[m]));
+    const float2 Ev = cscale(cadd(zk, zm), 0.5f);
+    const float2 Od = cscale(mul_mi(csub(zk, zm)), 0.5f);   // (zk - zm) / (2i)
+    const float2 wO = cmul(wsplit[i + T * m], Od);
+    xa = cadd(Ev, wO);
+    xb = conjf2(csub(Ev, wO));
+}
+
+// Forward real FFT of strided registers v into paired layout P.
+template <int M, int E, bool WAIT, int NB>
+__device__ __forceinline__ void rfft_paired(float2 (&P)[E], float2 (&v)[E], Exch<NB>& ex,
+                                            const float2* __restrict__ tw, int t, int i) {
+    static_assert(PairedSplit<M, E>::ok, "paired split needs M = E^k");
+    fft_from_paired<M, E, 0, WAIT, NB>(v, ex, tw, t, i);
+    const float2* wsplit = tw + FftPlan<M, E>::OFF_SPLIT;
+    float2 pw[E / 2];
+    paired_swap<E>(pw, v);
+#pragma unroll
+    for (int m = 0; m < E / 2; ++m) paired_split_pair<M, E>(v, pw, wsplit, i, m, P[2 * m], P[2 * m + 1]);
 }
 
 // Unnormalised inverse real FFT of a half spectrum in paired layout; on
