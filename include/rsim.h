@@ -104,8 +104,12 @@ rsim_status rsim_plan(const rsim_plan_desc *desc, int device, rsim_plan_t *out);
  * sizes and the RIR spectra for the next rsim_filter_mix_backward.  Unless
  * the plan disables graphs (or stage timing is on), the first call with a
  * given set of pointers captures the launch sequence into a CUDA graph and
- * every call replays it on `stream`; the capture itself runs on a stream of
- * the plan, so `stream` may be the legacy default stream. */
+ * every call replays it on `stream` (the plan keeps the graphs of the four
+ * most recently used pointer sets, so alternating between double buffers
+ * replays); the capture itself runs on a stream of the plan, so `stream` may
+ * be the legacy default stream.  Calls on one plan must not overlap on the
+ * GPU (they share the plan's scratch): queue them on one stream, or order
+ * them with events. */
 rsim_status rsim_filter_mix(rsim_plan_t plan, void *stream, const float *x, const float *rir,
                             const float *snr_db, float *gains, float *y, int32_t *trunc_len,
                             float *energy_kept_frac);

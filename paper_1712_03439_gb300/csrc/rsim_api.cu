@@ -80,9 +80,22 @@ std::vector<float2> twiddle_table_for(int logN, int E) {
 
 constexpr int kRing = 64;
 
+// Captured launch sequences, one per set of buffer pointers (a few sets, so
+// callers that alternate buffers -- double-buffered copies -- replay instead of
+// re-capturing); the least recently used one is replaced.
+constexpr int kGraphSlots = 4;
 struct GraphCache {
-    const void* key[8] = {};
-    cudaGraphExec_t exec = nullptr;
+    const void* key[kGraphSlots][8] = {};
+    cudaGraphExec_t exec[kGraphSlots] = {};
+    uint64_t used[kGraphSlots] = {};
+    uint64_t tick = 0;
+    void destroy() {
+        for (int s = 0; s < kGraphSlots; ++s)
+            if (exec[s]) {
+                cudaGraphExecDestroy(exec[s]);
+                exec[s] = nullptr;
+            }
+    }
 };
 
 struct StageTimer {
@@ -172,8 +185,8 @@ extern "C" void rsim_plan_destroy(rsim_plan_t plan) {
             if (plan->ev_join[b]) cudaEventDestroy(plan->ev_join[b]);
         }
         if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
-        if (plan->gfwd.exec) cudaGraphExecDestroy(plan->gfwd.exec);
-        if (plan->gbwd.exec) cudaGraphExecDestroy(plan->gbwd.exec);
+        plan->gfwd.destroy();
+        plan->gbwd.destroy();
         if (plan->cap) cudaStreamDestroy(plan->cap);
         if (plan->aux) cudaStreamDestroy(plan->aux);
         if (plan->ev_aux) cudaEventDestroy(plan->ev_aux);
@@ -547,12 +560,21 @@ cudaError_t enqueue_backward(rsim_plan_t p, cudaStream_t st, const float* grad_y
 template <typename F>
 cudaError_t run_graph(rsim_plan_t p, GraphCache& gc, const void* const (&key)[8], cudaStream_t st, F enqueue) {
     if (!p->use_graphs || p->timer.on) return enqueue(st);
-    bool hit = gc.exec != nullptr;
-    for (int k = 0; k < 8 && hit; ++k) hit = gc.key[k] == key[k];
-    if (!hit) {
-        if (gc.exec) {
-            cudaGraphExecDestroy(gc.exec);
-            gc.exec = nullptr;
+    int slot = -1;
+    for (int s = 0; s < kGraphSlots && slot < 0; ++s) {
+        bool hit = gc.exec[s] != nullptr;
+        for (int k = 0; k < 8 && hit; ++k) hit = gc.key[s][k] == key[k];
+        if (hit) slot = s;
+    }
+    if (slot < 0) {
+        slot = 0;                                   // an empty slot, else the least recently used
+        for (int s = 0; s < kGraphSlots; ++s) {
+            if (!gc.exec[s]) { slot = s; break; }
+            if (gc.used[s] < gc.used[slot]) slot = s;
+        }
+        if (gc.exec[slot]) {
+            cudaGraphExecDestroy(gc.exec[slot]);
+            gc.exec[slot] = nullptr;
         }
         cudaError_t e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return e;
@@ -560,15 +582,16 @@ cudaError_t run_graph(rsim_plan_t p, GraphCache& gc, const void* const (&key)[8]
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(p->cap, &graph);
         if (le != cudaSuccess) e = le;
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&gc.exec, graph, 0);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&gc.exec[slot], graph, 0);
         if (graph) cudaGraphDestroy(graph);
         if (e != cudaSuccess) {
-            gc.exec = nullptr;
+            gc.exec[slot] = nullptr;
             return e;
         }
-        for (int k = 0; k < 8; ++k) gc.key[k] = key[k];
+        for (int k = 0; k < 8; ++k) gc.key[slot][k] = key[k];
     }
-    return cudaGraphLaunch(gc.exec, st);
+    gc.used[slot] = ++gc.tick;
+    return cudaGraphLaunch(gc.exec[slot], st);
 }
 
 }  // namespace

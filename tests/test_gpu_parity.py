@@ -221,6 +221,36 @@ def test_graph_replay_equals_eager_launch():
         np.testing.assert_array_equal(a, c)
 
 
+def test_graph_replay_with_alternating_buffer_sets():
+    # five pointer sets used round-robin (more than the plan keeps graphs for): every
+    # replay or re-capture gives the eager result, and the sets do not leak into each other
+    from paper_1712_03439_gb300 import Plan
+    b = small_batch(seed=17, lengths=(9000, 30000), n_src=(3, 1))
+    S = int(b.num_sources.sum())
+    snr = dev(b.snr_db)
+    ref_plan = Plan.for_batch(b, eta_db=20.0, gain_mode=0, graphs=False)
+    plan = Plan.for_batch(b, eta_db=20.0, gain_mode=0, graphs=True)
+    sets = []
+    for k in range(5):
+        scale = 1.0 + 0.25 * k                    # different inputs per set
+        x, rir = dev(b.x * scale), dev(b.rir)
+        sets.append(dict(x=x, rir=rir, gy=dev(synth.grad_like(30 + k, b.y_size)),
+                         gains=torch.empty(S, device="cuda"), y=torch.empty(b.y_size, device="cuda"),
+                         gx=torch.empty_like(x), gr=torch.empty_like(rir), gg=torch.empty(S, device="cuda")))
+    for rnd in range(3):
+        for k, T in enumerate(sets):
+            T["y"].fill_(7.0)
+            plan.filter_mix(T["x"], T["rir"], T["gains"], T["y"], snr_db=snr)
+            plan.filter_mix_backward(T["gy"], T["x"], T["gains"], T["gx"], T["gr"], T["gg"])
+            if rnd == 2:
+                R = {n: torch.empty_like(v) for n, v in T.items() if n in ("gains", "y", "gx", "gr", "gg")}
+                ref_plan.filter_mix(T["x"], T["rir"], R["gains"], R["y"], snr_db=snr)
+                ref_plan.filter_mix_backward(T["gy"], T["x"], R["gains"], R["gx"], R["gr"], R["gg"])
+                for n in R:
+                    np.testing.assert_array_equal(T[n].cpu().numpy(), R[n].cpu().numpy())
+    plan.sync_status()
+
+
 def test_results_do_not_depend_on_utterance_order():
     b = small_batch(seed=14, lengths=(5000, 70000, 20000, 45000), n_src=(2, 1, 4, 3))
     perm = [2, 0, 3, 1]
