@@ -76,7 +76,7 @@ k_spectrum(DevBatch B, Queues Q, int bucket, const float* __restrict__ rir, floa
 // the register budget is set for.
 template <int M>
 struct FwdCfg {
-    static constexpr int E = (M == 4096) ? 16 : 8;
+    static constexpr int E = (M == 4096 || M == 8192) ? 16 : 8;
     static constexpr int T = M / E;
     static constexpr int kMinBlocks = (M <= 4096) ? 2 : 1;
     static constexpr bool kStageH = false;
