@@ -82,7 +82,10 @@ struct BwdCfg {
 
 static_assert(kJG == 2, "the backward tile loop is written for microphone pairs");
 
-template <int M>
+// MG: more microphones than one group (J > kJG): later groups add their dx to
+// the first group's.  Without it dx is only written, which keeps the
+// read-modify-write path out of the common kernel.
+template <int M, bool MG>
 __global__ void __launch_bounds__(BwdCfg<M>::T, BwdCfg<M>::kMinBlocks)
 k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const float* __restrict__ x,
            const float* __restrict__ gains, const float2* __restrict__ Hc, float* __restrict__ dx,
@@ -265,9 +268,12 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
                         const float d0 = a * v[q].x, d1 = a * v[q].y;
                         if (pairs && n + 1 < ilim) {
                             *reinterpret_cast<float2*>(dst + n) = make_float2(d0, d1);
-                        } else {
+                        } else if constexpr (MG) {
                             if (n < ilim) dst[n] = (j0 == 0) ? d0 : dst[n] + d0;
                             if (n + 1 < ilim) dst[n + 1] = (j0 == 0) ? d1 : dst[n + 1] + d1;
+                        } else {
+                            if (n < ilim) dst[n] = d0;
+                            if (n + 1 < ilim) dst[n + 1] = d1;
                         }
                     }
                 }
@@ -386,7 +392,8 @@ template <int M>
 static void backward_m(const DevBatch& B, const Queues& Q, int bucket, const float* g, const float* x,
                        const float* gains, const float2* Hc, float* dx, float* dhp, float* dap,
                        Twiddles tw, int grid, cudaStream_t st) {
-    k_backward<M><<<grid, BwdCfg<M>::T, smem_backward<M>(), st>>>(B, Q, bucket, g, x, gains, Hc, dx, dhp,
+    auto kern = B.J > kJG ? k_backward<M, true> : k_backward<M, false>;
+    kern<<<grid, BwdCfg<M>::T, smem_backward<M>(), st>>>(B, Q, bucket, g, x, gains, Hc, dx, dhp,
                                                                   dap, tw.get(BwdCfg<M>::E));
 }
 
@@ -428,12 +435,20 @@ static int occ_b(K kernel, int threads, int smem) {
     return n > 0 ? n : 1;
 }
 
+// both microphone-group variants share the launch shape; the smaller occupancy rules
+template <int M>
+static int occ_bb() {
+    const int a = occ_b(k_backward<M, false>, BwdCfg<M>::T, smem_backward<M>());
+    const int b = occ_b(k_backward<M, true>, BwdCfg<M>::T, smem_backward<M>());
+    return a < b ? a : b;
+}
+
 int occupancy_backward(int logN) {
     switch (logN) {
-        case 11: return occ_b(k_backward<1024>, BwdCfg<1024>::T, smem_backward<1024>());
-        case 12: return occ_b(k_backward<2048>, BwdCfg<2048>::T, smem_backward<2048>());
-        case 13: return occ_b(k_backward<4096>, BwdCfg<4096>::T, smem_backward<4096>());
-        case 14: return occ_b(k_backward<8192>, BwdCfg<8192>::T, smem_backward<8192>());
+        case 11: return occ_bb<1024>();
+        case 12: return occ_bb<2048>();
+        case 13: return occ_bb<4096>();
+        case 14: return occ_bb<8192>();
     }
     return 1;
 }
