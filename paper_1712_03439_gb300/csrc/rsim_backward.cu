@@ -183,7 +183,6 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
 #pragma unroll
                 for (int q = 0; q < E / 2; ++q) {
                     const int k = kt + q * T;
-                    const int kb = (k == 0) ? M / 2 : M - k;
                     float2 ga, gb;
                     if constexpr (kPaired) {
                         ga = G[2 * q];
@@ -191,14 +190,9 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
                     } else {
                         split_pair<M>(z, wsplit, k, ga, gb);
                     }
-                    float2 ha, hb;
-                    if constexpr (L::kStageH) {
-                        ha = hs[jj * M + k];
-                        hb = hs[jj * M + kb];
-                    } else {
-                        ha = __ldg(Hg + k);
-                        hb = __ldg(Hg + kb);
-                    }
+                    const float4 hh = L::kStageH ? reinterpret_cast<const float4*>(hs + jj * M)[k]
+                                                 : __ldg(reinterpret_cast<const float4*>(Hg) + k);
+                    const float2 ha = make_float2(hh.x, hh.y), hb = make_float2(hh.z, hh.w);
                     if (k == 0) {            // slot 0 holds two real bins
                         C[0].x += ha.x * ga.x;
                         C[0].y += ha.y * ga.y;

@@ -37,17 +37,13 @@ k_spectrum(DevBatch B, Queues Q, int bucket, const float* __restrict__ rir, floa
         if (r < 0) break;
         float2 P[E];
         rfft_pairs<M, E>(P, rir + B.roff[r], B.L[r], sm, tw, t);
-        float2* H = Hc + (int64_t)r * B.MMAX;
+        // mirror pairs side by side: slot k < M/2 holds (H[k], H[M-k]); slot 0 holds
+        // ((H[0], H[N/2]) packed, H[M/2])
+        float4* H = reinterpret_cast<float4*>(Hc + (int64_t)r * B.MMAX);
 #pragma unroll
         for (int s = 0; s < E / 2; ++s) {
-            const int k = t + s * T;
-            if (k == 0) {
-                H[0] = cscale(P[0], inv_n);
-                H[M / 2] = cscale(P[1], inv_n);
-            } else {
-                H[k] = cscale(P[2 * s], inv_n);
-                H[M - k] = cscale(P[2 * s + 1], inv_n);
-            }
+            const float2 a = cscale(P[2 * s], inv_n), c = cscale(P[2 * s + 1], inv_n);
+            H[t + s * T] = make_float4(a.x, a.y, c.x, c.y);
         }
     }
 }
@@ -187,19 +183,13 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
                         split_pair<M>(sm, wsplit, k, xa, xb);
                         xa = cscale(xa, a);
                         xb = cscale(xb, a);
-                        const int kb = (k == 0) ? M / 2 : M - k;
 #pragma unroll
                         for (int jj = 0; jj < kJG; ++jj) {
                             if (jj >= jn) break;
-                            float2 ha, hb;
-                            if constexpr (L::kStageH) {
-                                ha = hs[jj * M + k];
-                                hb = hs[jj * M + kb];
-                            } else {
-                                const float2* H = H0 + (int64_t)jj * B.MMAX;
-                                ha = __ldg(H + k);
-                                hb = __ldg(H + kb);
-                            }
+                            const float4 hh = L::kStageH
+                                ? reinterpret_cast<const float4*>(hs + jj * M)[k]
+                                : __ldg(reinterpret_cast<const float4*>(H0 + (int64_t)jj * B.MMAX) + k);
+                            const float2 ha = make_float2(hh.x, hh.y), hb = make_float2(hh.z, hh.w);
                             if (k == 0) {            // slot 0 holds two real bins
                                 Y[jj][0].x += xa.x * ha.x;
                                 Y[jj][0].y += xa.y * ha.y;
