@@ -647,6 +647,8 @@ extern "C" rsim_status rsim_plan_sync_status(rsim_plan_t p, void* stream) {
                         "a truncated RIR is longer than 3N/4+1 for every allowed FFT size N");
         if (err & kErrZeroPower)
             return fail(RSIM_E_INVALID, "a noise source has zero power but an SNR to meet");
+        if (err & kErrWaitTimeout)
+            return fail(RSIM_E_DEVICE, "a kernel's bounded wait for a bulk copy ran out; results are invalid");
         return fail(RSIM_E_DEVICE, "device error " + std::to_string(err));
     }
     return RSIM_OK;

@@ -53,11 +53,12 @@ __device__ __forceinline__ double block_sum_d(double v, double* sd) {
 //   c = irFFT_N(C)[0, hop): dx_i = alpha_i c, dalpha_i += <c, x_i> (computed
 //   as sum_k C[k] conj(X[k]) on the spectra, by Parseval)
 // and at the end of the segment dh partial_ij = irFFT_N(W_j)[0, L_ij).
-// Every transform input (x block, g windows) is prefetched with cp.async into
-// one of NST shared-memory stages while the previous transform runs; with two
-// stages the copy's completion is folded into the last barrier of that
-// transform.  Transform exchanges alternate between NSM buffers (one barrier
-// per exchange when NSM = 2).  The source's RIR spectra are staged once per
+// Every transform input (x block, g windows) is prefetched into one of NST
+// shared-memory stages while the previous transform runs: with two stages by
+// one bulk copy per block (the copy engine moves its whole 16-byte chunks and
+// completes an mbarrier the readers wait on, with a bounded wait), with one
+// stage by per-thread cp.async.  Transform exchanges alternate between NSM
+// buffers (one barrier per exchange when NSM = 2).  The source's RIR spectra are staged once per
 // tile; twiddles are copied to shared memory once per CTA.  Microphones go in
 // groups of kJG (the source spectrum is recomputed per group; dx of later
 // groups is added to the first group's).
@@ -72,7 +73,7 @@ struct BwdCfg {
     static constexpr int kMinBlocks = M <= 2048 ? 2 : 1;
     static constexpr size_t a16(size_t v) { return (v + 15) / 16 * 16; }
     static constexpr size_t SM_LEN = a16(sizeof(float2) * padded_len(M));
-    static constexpr size_t ST_LEN = sizeof(float) * 2 * M;
+    static constexpr size_t ST_LEN = sizeof(float) * (2 * M + 8);   // + room for the chunk offset
     static constexpr size_t o_sm = 0;
     static constexpr size_t o_st = o_sm + NSM * SM_LEN;
     static constexpr size_t o_hs = a16(o_st + NST * ST_LEN);
@@ -94,7 +95,7 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
     constexpr int E = L::E;
     constexpr int T = L::T;
     constexpr int NST = L::NST;
-    constexpr bool kWait = NST == 2;      // stage completion folded into the transforms
+    constexpr bool kBulk = NST == 2;      // inputs staged by bulk copies completing on mbarriers
     constexpr bool kRollSteps = L::NSM == 2;
     constexpr bool kPaired = PairedSplit<M, E>::ok;   // split in registers (paired layout)
     using Pl = FftPlan<M, E>;
@@ -105,7 +106,19 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
     float2* hs = reinterpret_cast<float2*>(smem_raw + L::o_hs);
     __shared__ double sd[32];
     __shared__ int slot;
+    __shared__ __align__(8) uint64_t mbar[2];
     const int t = threadIdx.x;
+    if constexpr (kBulk) {
+        if (t == 0) {
+            mbar_init(&mbar[0], 1);
+            mbar_init(&mbar[1], 1);
+            mbar_init_fence();
+        }
+        __syncthreads();
+    }
+    uint32_t ph = 0;                             // bit b: parity of the next phase of stage b
+    int off0 = 0, off1 = 0;                      // float offset of the data in stage 0 / 1
+    bool bad = false;                            // a bounded wait ran out
     const float2* tw = twg;
     if constexpr (L::kTwSmem) {
         float2* tws = reinterpret_cast<float2*>(smem_raw + L::o_tw);
@@ -117,7 +130,7 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
     // first bin of this thread's pairs: t (pair layout) or its paired butterfly
     const int kt = kPaired ? paired_butterfly<T>(t) : t;
     int sc = 0;                                  // stage holding the next transform input
-    auto stage = [&](int k) { return st0 + (NST == 2 ? k : 0) * (2 * M); };
+    auto stage = [&](int k) { return st0 + (NST == 2 ? k : 0) * (2 * M + 8); };
     for (;;) {
         const int code = pop_job_b(Q, kListBwd, bucket, &slot);
         if (code < 0) break;
@@ -139,26 +152,38 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
         float da = 0.f;              // <c, x_i> over the segment
         for (int j0 = 0; j0 < J; j0 += kJG) {
             const int jn = min(kJG, J - j0);
-            auto stage_x = [&](float* dst, int64_t b) {
-                const int64_t p = b * hop;
-                stage_real_async<M, E>(dst, xi + p, min((int64_t)hop, nx - p), t);
+            // queue a real block into stage k (bulk copy + mbarrier, or cp.async)
+            auto stage_in = [&](int k, const float* src, int64_t len) {
+                if constexpr (kBulk) {
+                    const int off = stage_real_bulk<M, E>(stage(k), src, len, &mbar[k], t);
+                    if (k) off1 = off; else off0 = off;
+                } else {
+                    stage_real_async<M, E>(stage(k), src, len, t);
+                }
             };
-            auto stage_g = [&](float* dst, int64_t b, int j) {
+            auto stage_x = [&](int k, int64_t b) {
                 const int64_t p = b * hop;
-                stage_real_async<M, E>(dst, gy + B.yoff[u] + (int64_t)j * ny + p,
-                                       min((int64_t)(hop + lmax - 1), ny - p), t);
+                stage_in(k, xi + p, min((int64_t)hop, nx - p));
+            };
+            auto stage_g = [&](int k, int64_t b, int j) {
+                const int64_t p = b * hop;
+                stage_in(k, gy + B.yoff[u] + (int64_t)j * ny + p, min((int64_t)(hop + lmax - 1), ny - p));
             };
             // takes the staged input into v and queues the next one (if any) into the other stage
             auto next_input = [&](float2 (&v)[E], int64_t b, int nj) {
-                if constexpr (NST == 1) {
+                if constexpr (kBulk) {
+                    bad |= !mbar_wait_bounded(&mbar[sc], (ph >> sc) & 1u);
+                    ph ^= 1u << sc;
+                    load_staged_at<M, E>(v, stage(sc), sc ? off1 : off0, t);
+                } else {
                     cp_async_wait<0>();
                     __syncthreads();
+                    load_staged_strided<M, E>(v, stage(sc), t);
+                    __syncthreads();
                 }
-                load_staged_strided<M, E>(v, stage(sc), t);
-                if constexpr (NST == 1) __syncthreads();
-                if (nj >= 0) stage_g(stage(sc ^ 1), b, nj);
-                else if (b + 1 < b1) stage_x(stage(sc ^ 1), b + 1);
-                cp_async_commit();
+                if (nj >= 0) stage_g(sc ^ (NST - 1), b, nj);
+                else if (b + 1 < b1) stage_x(sc ^ (NST - 1), b + 1);
+                if constexpr (!kBulk) cp_async_commit();
                 sc ^= (NST - 1);
             };
             float2 W[kJG][E];
@@ -171,7 +196,7 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
                 for (int jj = 0; jj < jn; ++jj)
                     stage_spectrum_async<M, E>(hs + jj * M, Hc + (int64_t)(rb + i * J + j0 + jj) * B.MMAX, t);
             }
-            stage_x(stage(sc), b0);
+            stage_x(sc, b0);
             cp_async_commit();
             cp_async_wait<0>();
             __syncthreads();
@@ -221,7 +246,7 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
                     next_input(v, b, sp < jn ? j0 + sp : -1);
                     if constexpr (kPaired) {
                         float2 G[E];
-                        rfft_paired<M, E, kWait>(G, v, ex, tw, t, kt);
+                        rfft_paired<M, E, false>(G, v, ex, tw, t, kt);
                         if (sp == 0) {
 #pragma unroll
                             for (int e = 0; e < E; ++e) X[e] = G[e];
@@ -231,7 +256,7 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
                             mac(W[1], C, X, nullptr, G, 1);
                         }
                     } else {
-                        const float2* z = rfft_x<M, E, kWait>(v, ex, tw, t);
+                        const float2* z = rfft_x<M, E, false>(v, ex, tw, t);
                         if (sp == 0) split_forward<M, E>(X, z, wsplit, t);
                         else if (sp == 1) mac(W[0], C, X, z, v, 0);
                         else mac(W[1], C, X, z, v, 1);
@@ -293,6 +318,12 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
         }
         const double tot = block_sum_d((double)da, sd);
         if (t == 0) dap[(int64_t)g * kMaxSources + i] = (float)tot;
+        if constexpr (kBulk) {
+            if (__syncthreads_or(bad)) {         // a copy never completed: report and stop
+                if (t == 0) atomicOr(B.err, kErrWaitTimeout);
+                break;
+            }
+        }
     }
     cp_async_wait<0>();
 }

@@ -429,6 +429,91 @@ __device__ __forceinline__ void load_staged_strided(float2 (&v)[E], const float*
 }
 
 // ---------------------------------------------------------------------------
+// bulk staging (the copy engine moves a block's whole 16-byte chunks)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t* mb, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(mb)), "r"(count));
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::); }
+// orders this thread's earlier (generic) shared-memory accesses before its later bulk copies
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::); }
+__device__ __forceinline__ void mbar_arrive(uint64_t* mb) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(mb)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mb, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(mb)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mb) {
+    asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(mb))
+                 : "memory");
+}
+// Waits for the phase with the given parity to complete; gives up after a
+// fixed number of polls (each poll may suspend the thread for a while) and
+// returns false then.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mb, uint32_t parity) {
+    for (int it = 0; it < (1 << 20); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_addr(mb)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Queues the real block src[0, len) (zeros after it, len clipped to [0, 2M])
+// into stage at float offset off = (src's float position within its 16-byte
+// chunk), so that the whole chunks can move by one bulk copy (issued by
+// thread 0, completing on mb); the at most three head and three tail floats
+// and the zero fill are plain stores.  Every thread must call it, after a
+// barrier that retired the stage's previous readers.  The stage holds
+// 2M + 8 floats.  Returns off; read with load_staged_at after mb completes
+// and a barrier has passed.
+template <int M, int E>
+__device__ __forceinline__ int stage_real_bulk(float* __restrict__ stage, const float* __restrict__ src,
+                                               int64_t len64, uint64_t* mb, int t) {
+    constexpr int T = M / E;
+    const int len = (int)(len64 < 2 * M ? (len64 > 0 ? len64 : 0) : 2 * M);
+    const int off = (int)((reinterpret_cast<uintptr_t>(src) >> 2) & 3);
+    const int head = off ? min(len, 4 - off) : 0;
+    const int body = ((len - head) >> 2) << 2;
+    if (t == 0) {
+        fence_proxy_async_smem();
+        if (body > 0) {
+            mbar_arrive_expect_tx(mb, (uint32_t)body * 4u);
+            bulk_copy_g2s(stage + off + head, src + head, (uint32_t)body * 4u, mb);
+        } else {
+            mbar_arrive(mb);
+        }
+    }
+    if (t < head) stage[off + t] = __ldg(src + t);
+    const int tail0 = head + body;
+    if (t < len - tail0) stage[off + tail0 + t] = __ldg(src + tail0 + t);
+    for (int n = len + t; n < 2 * M; n += T) stage[off + n] = 0.f;
+    return off;
+}
+
+// z[n] = (stage[off + 2n], stage[off + 2n + 1]) for the strided indices of thread t
+template <int M, int E>
+__device__ __forceinline__ void load_staged_at(float2 (&v)[E], const float* __restrict__ stage, int off, int t) {
+    constexpr int T = M / E;
+    if ((off & 1) == 0) {
+        const float2* s2 = reinterpret_cast<const float2*>(stage + off);
+#pragma unroll
+        for (int s = 0; s < E; ++s) v[s] = s2[t + s * T];
+    } else {
+        const float* s1 = stage + off;
+#pragma unroll
+        for (int s = 0; s < E; ++s) v[s] = make_float2(s1[2 * (t + s * T)], s1[2 * (t + s * T) + 1]);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // composite real transforms
 // ---------------------------------------------------------------------------
 

@@ -18,6 +18,7 @@ constexpr int kPowerChunk = 32768;   // samples per partial-power CTA
 enum : int32_t {
     kErrNoFftSize = 1,     // a truncated RIR longer than 3N/4+1 for every allowed N
     kErrZeroPower = 2,     // a noise source with zero power but an SNR to meet
+    kErrWaitTimeout = 4,   // a kernel gave up waiting for a bulk copy (bounded wait)
 };
 
 // list kinds inside the work queues
