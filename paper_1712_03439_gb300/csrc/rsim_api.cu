@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -452,6 +453,10 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     B.L = (int32_t*)p_L; B.logN = (int32_t*)p_logN; B.hop = (int32_t*)p_hop;
     B.Lmax = (int32_t*)p_lmax; B.nblk = (int32_t*)p_nblk;
     B.pow_part = (double*)p_pow; B.CH = CH; B.err = (int32_t*)p_err;
+    {
+        const char* w = std::getenv("RSIM_TEST_WITHHOLD_BULK_COPY");   // test hook, off by default
+        B.test_withhold = (w && w[0] == '1') ? 1 : 0;
+    }
     p->Q.list = (int32_t*)p_list; p->Q.count = (int32_t*)p_count; p->Q.next = (int32_t*)p_next;
     p->Q.cap = (int32_t)cap;
     p->Hc = (float2*)p_Hc; p->tails = (float*)p_tails; p->dhp = (float*)p_dhp; p->dap = (float*)p_dap;

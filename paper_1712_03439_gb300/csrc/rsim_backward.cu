@@ -118,7 +118,7 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
     }
     uint32_t ph = 0;                             // bit b: parity of the next phase of stage b
     int off0 = 0, off1 = 0;                      // float offset of the data in stage 0 / 1
-    bool bad = false;                            // a bounded wait ran out
+    bool bad = false;                            // a bounded wait ran out (no new copies then)
     const float2* tw = twg;
     if constexpr (L::kTwSmem) {
         float2* tws = reinterpret_cast<float2*>(smem_raw + L::o_tw);
@@ -155,7 +155,7 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
             // queue a real block into stage k (bulk copy + mbarrier, or cp.async)
             auto stage_in = [&](int k, const float* src, int64_t len) {
                 if constexpr (kBulk) {
-                    const int off = stage_real_bulk<M, E>(stage(k), src, len, &mbar[k], t);
+                    const int off = stage_real_bulk<M, E>(stage(k), src, len, &mbar[k], t, B.test_withhold != 0);
                     if (k) off1 = off; else off0 = off;
                 } else {
                     stage_real_async<M, E>(stage(k), src, len, t);
@@ -172,7 +172,12 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
             // takes the staged input into v and queues the next one (if any) into the other stage
             auto next_input = [&](float2 (&v)[E], int64_t b, int nj) {
                 if constexpr (kBulk) {
-                    bad |= !mbar_wait_bounded(&mbar[sc], (ph >> sc) & 1u);
+                    if (!bad && !mbar_wait_bounded(&mbar[sc], (ph >> sc) & 1u)) {
+                        // give the copy one more bounded chance to land before the
+                        // stage is abandoned, so none is left in flight at exit
+                        mbar_wait_bounded(&mbar[sc], (ph >> sc) & 1u, 100000000ull);
+                        bad = true;
+                    }
                     ph ^= 1u << sc;
                     load_staged_at<M, E>(v, stage(sc), sc ? off1 : off0, t);
                 } else {
@@ -181,8 +186,13 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
                     load_staged_strided<M, E>(v, stage(sc), t);
                     __syncthreads();
                 }
-                if (nj >= 0) stage_g(sc ^ (NST - 1), b, nj);
-                else if (b + 1 < b1) stage_x(sc ^ (NST - 1), b + 1);
+                if (kBulk && bad) {
+                    // stop feeding the stages after a wait ran out
+                } else if (nj >= 0) {
+                    stage_g(sc ^ (NST - 1), b, nj);
+                } else if (b + 1 < b1) {
+                    stage_x(sc ^ (NST - 1), b + 1);
+                }
                 if constexpr (!kBulk) cp_async_commit();
                 sc ^= (NST - 1);
             };

@@ -449,21 +449,31 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
                      smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(mb))
                  : "memory");
 }
-// Waits for the phase with the given parity to complete; gives up after a
-// fixed number of polls (each poll may suspend the thread for a while) and
-// returns false then.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mb, uint32_t parity) {
-    for (int it = 0; it < (1 << 20); ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(smem_addr(mb)), "r"(parity)
-            : "memory");
-        if (done) return true;
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t v;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+    return v;
+}
+// Waits for the phase with the given parity to complete; gives up after about
+// limit_ns of wall time and returns false then.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* mb, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(mb)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mb, uint32_t parity,
+                                                  uint64_t limit_ns = 500000000ull) {
+    if (mbar_try_wait(mb, parity)) return true;      // the usual case: the copy is in
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(mb, parity)) return true;
+        if ((it & 63) == 0 && global_ns() - t0 > limit_ns) return false;
     }
-    return false;
 }
 
 // Queues the real block src[0, len) (zeros after it, len clipped to [0, 2M])
@@ -474,9 +484,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mb, uint32_t parity)
 // barrier that retired the stage's previous readers.  The stage holds
 // 2M + 8 floats.  Returns off; read with load_staged_at after mb completes
 // and a barrier has passed.
+// (withhold: test hook -- the barrier is told to expect the bytes but no copy
+// is issued, so the readers' bounded wait runs out)
 template <int M, int E>
 __device__ __forceinline__ int stage_real_bulk(float* __restrict__ stage, const float* __restrict__ src,
-                                               int64_t len64, uint64_t* mb, int t) {
+                                               int64_t len64, uint64_t* mb, int t, bool withhold = false) {
     constexpr int T = M / E;
     const int len = (int)(len64 < 2 * M ? (len64 > 0 ? len64 : 0) : 2 * M);
     const int off = (int)((reinterpret_cast<uintptr_t>(src) >> 2) & 3);
@@ -486,7 +498,7 @@ __device__ __forceinline__ int stage_real_bulk(float* __restrict__ stage, const 
         fence_proxy_async_smem();
         if (body > 0) {
             mbar_arrive_expect_tx(mb, (uint32_t)body * 4u);
-            bulk_copy_g2s(stage + off + head, src + head, (uint32_t)body * 4u, mb);
+            if (!withhold) bulk_copy_g2s(stage + off + head, src + head, (uint32_t)body * 4u, mb);
         } else {
             mbar_arrive(mb);
         }
