@@ -81,7 +81,7 @@ struct FwdCfg {
     static constexpr size_t a16(size_t v) { return (v + 15) / 16 * 16; }
     static constexpr size_t o_sm = 0;
     static constexpr size_t o_xs = a16(o_sm + sizeof(float2) * padded_len(M));
-    static constexpr size_t o_hs = a16(o_xs + sizeof(float) * 2 * M);
+    static constexpr size_t o_hs = a16(o_xs + sizeof(float) * (2 * M + 8));   // + chunk offset room
     static constexpr size_t o_tl = a16(o_hs + (kStageH ? sizeof(float2) * kJG * M : 0));
     static constexpr size_t o_tw = a16(o_tl + (kTailSmem ? sizeof(float) * kJG * 2 * M : 0));
     static constexpr size_t bytes = a16(o_tw + (kTwSmem ? sizeof(float2) * FftPlan<M, E>::TW_LEN : 0));
@@ -102,7 +102,16 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
     float2* hs = reinterpret_cast<float2*>(smem_raw + L::o_hs);
     float* tl_smem = reinterpret_cast<float*>(smem_raw + L::o_tl);
     __shared__ int slot;
+    __shared__ __align__(8) uint64_t mbar;
     const int t = threadIdx.x;
+    if (t == 0) {
+        mbar_init(&mbar, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    uint32_t ph = 0;                             // parity of the stage's next phase
+    int xoff = 0;                                // float offset of the data in the stage
+    bool bad = false;                            // a bounded wait ran out (no new copies then)
     const float2* tw = twg;
     if constexpr (L::kTwSmem) {
         float2* tws = reinterpret_cast<float2*>(smem_raw + L::o_tw);
@@ -130,9 +139,13 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
         for (int j0 = 0; j0 < J; j0 += kJG) {
             const int jn = min(kJG, J - j0);
             // queue the copies of source i's block b and of its spectra
+            // one bulk copy per source block into the stage (whole 16-byte chunks by
+            // the copy engine, completing on mbar; ragged ends and zeros by stores)
             auto stage_x = [&](int64_t b, int i) {
+                if (bad) return;
                 const int64_t p = b * hop;
-                stage_real_async<M, E>(xs, x + B.xoff[sb + i] + p, min((int64_t)hop, nx - p), t);
+                xoff = stage_real_bulk<M, E>(xs, x + B.xoff[sb + i] + p, min((int64_t)hop, nx - p), &mbar, t,
+                                             B.test_withhold != 0);
             };
             auto stage_h = [&](int i) {
                 if constexpr (L::kStageH) {
@@ -162,9 +175,14 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
                 for (int i = 0; i < I; ++i) {
                     // x_i is in (only the newest group, H_i, may still be pending)
                     cp_async_wait<1>();
+                    if (!bad && !mbar_wait_bounded(&mbar, ph)) {
+                        mbar_wait_bounded(&mbar, ph, 100000000ull);   // one more chance to land
+                        bad = true;
+                    }
+                    ph ^= 1u;
                     __syncthreads();
                     float2 v[E];
-                    load_staged_strided<M, E>(v, xs, t);
+                    load_staged_at<M, E>(v, xs, xoff, t);
                     __syncthreads();             // xs fully read: reuse it
                     if (i + 1 < I) stage_x(b, i + 1);
                     else if (b + 1 < b1) stage_x(b + 1, 0);
@@ -256,6 +274,10 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
                         yj[n] = (n < ye) ? tl(jj)[n - end] : 0.f;
                 }
             }
+        }
+        if (__syncthreads_or(bad)) {             // a copy never completed: report and stop
+            if (t == 0) atomicOr(B.err, kErrWaitTimeout);
+            break;
         }
     }
     cp_async_wait<0>();

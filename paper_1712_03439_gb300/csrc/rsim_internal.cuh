@@ -64,7 +64,7 @@ struct DevBatch {
     double* pow_part;        // [S * CH] partial sums of x^2
     int32_t CH;              // power chunks per source (max)
     int32_t* err;            // [1] latched error bits
-    int32_t test_withhold;   // test hook: the backward's bulk copies are not issued, so its
+    int32_t test_withhold;   // test hook: the bulk copies are not issued, so the kernels'
                              // bounded waits run out (set from RSIM_TEST_WITHHOLD_BULK_COPY)
 };
 
