@@ -520,17 +520,27 @@ cudaError_t enqueue_forward(rsim_plan_t p, cudaStream_t st, const float* x, cons
     stage_mark(p, 2, false, st);
     launch_plan(B, p->Q, snr_db, gains, st);
     stage_mark(p, 2, true, st);
-    stage_mark(p, 3, false, st);
-    fan_out(p, st, [&](int m, cudaStream_t s) {
-        launch_spectrum(m, B, p->Q, rir, p->Hc, p->tw[m - kMinLog], p->grid_spec[m - kMinLog], s);
-    });
-    stage_mark(p, 3, true, st);
-    stage_mark(p, 4, false, st);
-    fan_out(p, st, [&](int m, cudaStream_t s) {
-        launch_forward(m, B, p->Q, x, gains, p->Hc, y, p->tails, p->tw[m - kMinLog],
-                       p->grid_fwd[m - kMinLog], s);
-    });
-    stage_mark(p, 4, true, st);
+    if (!p->timer.on) {
+        // each FFT size's spectra then its OLA pass on that size's stream: a size's
+        // forward waits only for its own spectra
+        fan_out(p, st, [&](int m, cudaStream_t s) {
+            launch_spectrum(m, B, p->Q, rir, p->Hc, p->tw[m - kMinLog], p->grid_spec[m - kMinLog], s);
+            launch_forward(m, B, p->Q, x, gains, p->Hc, y, p->tails, p->tw[m - kMinLog],
+                           p->grid_fwd[m - kMinLog], s);
+        });
+    } else {
+        stage_mark(p, 3, false, st);
+        fan_out(p, st, [&](int m, cudaStream_t s) {
+            launch_spectrum(m, B, p->Q, rir, p->Hc, p->tw[m - kMinLog], p->grid_spec[m - kMinLog], s);
+        });
+        stage_mark(p, 3, true, st);
+        stage_mark(p, 4, false, st);
+        fan_out(p, st, [&](int m, cudaStream_t s) {
+            launch_forward(m, B, p->Q, x, gains, p->Hc, y, p->tails, p->tw[m - kMinLog],
+                           p->grid_fwd[m - kMinLog], s);
+        });
+        stage_mark(p, 4, true, st);
+    }
     stage_mark(p, 5, false, st);
     launch_fixup(B, y, p->tails, st);
     stage_mark(p, 5, true, st);
