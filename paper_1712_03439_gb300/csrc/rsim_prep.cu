@@ -185,6 +185,8 @@ void launch_power(const DevBatch& B, const float* x, int grid, cudaStream_t st) 
 // spectrum jobs (RIRs), forward tiles (segments) and backward tiles
 // (backward segment, source), in utterance order, and resets the queue cursors.
 constexpr int kPlanThreads = 1024;
+constexpr float kConsolidateShare = 0.1f;   // a size below this share of the work is a minority
+constexpr float kConsolidateSlack = 0.02f;  // ...and moves if that adds at most this share of the work
 
 __device__ __forceinline__ int block_exscan(int v, int* sm, int* total) {
     // sm: >= 32 ints
@@ -245,30 +247,96 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
             }
         }
     }
-    // ---- FFT size per utterance
+    // ---- FFT size per utterance.  Every thread also tallies, per chosen size m,
+    // the predicted work and, per other size d, how much dearer its utterances
+    // would be at d (or that some cannot use d) -- for the consolidation below.
+    float my_work[kNumBuckets] = {};             // FP32: these only steer a heuristic
+    float my_extra[kNumBuckets][kNumBuckets] = {};
     for (int u = t; u < B.U; u += kPlanThreads) {
         int lmax = 1;
         for (int r = B.rir0[u]; r < B.rir0[u + 1]; ++r) lmax = max(lmax, B.L[r]);
         const int64_t nx = B.n_x[u];
         const int I = B.n_src[u], J = B.J;
+        float cost[kNumBuckets];
         int best = 0;
-        double best_c = 0.0;
+        float best_c = 0.f;
         for (int m = kMinLog; m <= kMaxLog; ++m) {
+            cost[m - kMinLog] = -1.f;                  // not allowed or not admissible
             if (!((B.mask >> m) & 1)) continue;
             const int64_t N = 1LL << m;
             const int64_t hop = N - lmax + 1;
             if (4 * hop < N) continue;                 // hop >= N/4 keeps blocks useful
             if (N > B.seg_len || N > B.bseg_len) continue;
             const int64_t nb = (nx + hop - 1) / hop;
-            const double c = ((double)nb * (I + J) + (double)I * J) * (double)B.tuning[m];
+            const float c = ((float)nb * (I + J) + (float)(I * J)) * B.tuning[m];
+            cost[m - kMinLog] = c;
             if (best == 0 || c < best_c) { best = m; best_c = c; }
         }
         if (best == 0) atomicOr(B.err, kErrNoFftSize);
         B.logN[u] = best;
         B.Lmax[u] = lmax;
-        const int64_t hop = best ? (1LL << best) - lmax + 1 : 1;
+        if (best) {
+#pragma unroll
+            for (int b = 0; b < kNumBuckets; ++b) {
+                if (best != kMinLog + b) continue;
+                my_work[b] += best_c;
+#pragma unroll
+                for (int d = 0; d < kNumBuckets; ++d) my_extra[b][d] += cost[d] < 0.f ? 1e30f : cost[d] - best_c;
+            }
+        }
+    }
+    // fixed-order block sums (warp shuffles, then the warps' partials in order)
+    {
+        constexpr int kVals = kNumBuckets * (kNumBuckets + 1);
+        __shared__ float part[kVals][kPlanThreads / 32];
+        __shared__ float sums[kVals];
+        const int lane = t & 31, wid = t >> 5;
+#pragma unroll
+        for (int q = 0; q < kVals; ++q) {
+            float v = q < kNumBuckets ? my_work[q]
+                                       : my_extra[(q - kNumBuckets) / kNumBuckets][(q - kNumBuckets) % kNumBuckets];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) part[q][wid] = v;
+        }
+        __syncthreads();
+        if (t < kVals) {
+            float v = 0.f;
+            for (int w = 0; w < kPlanThreads / 32; ++w) v += part[t][w];
+            sums[t] = v;
+        }
+        __syncthreads();
+        // consolidation: a size carrying under kConsolidateShare of the predicted work
+        // runs as a small launch beside the dominant one and finishes late (its CTAs
+        // queue behind the persistent ones); all its utterances move to the dominant
+        // size when every one of them fits it and together they cost at most
+        // kConsolidateSlack of the batch's predicted work more there
+        if (t == 0) {
+            int dom = 0;
+            float tot = 0.f;
+            for (int b = 0; b < kNumBuckets; ++b) {
+                tot += sums[b];
+                if (sums[b] > sums[dom]) dom = b;
+            }
+            int moved = 0;
+            for (int b = 0; b < kNumBuckets; ++b)
+                if (b != dom && sums[b] > 0.f && sums[b] < kConsolidateShare * tot &&
+                    sums[kNumBuckets + b * kNumBuckets + dom] < kConsolidateSlack * tot)
+                    moved |= 1 << b;
+            sm[32] = dom;
+            sm[31] = moved;
+        }
+        __syncthreads();
+    }
+    const int dom_m = kMinLog + sm[32], moved = sm[31];
+    for (int u = t; u < B.U; u += kPlanThreads) {
+        int m = B.logN[u];
+        if (m != 0 && ((moved >> (m - kMinLog)) & 1)) m = dom_m;
+        B.logN[u] = m;
+        const int64_t nx = B.n_x[u];
+        const int64_t hop = m ? (1LL << m) - B.Lmax[u] + 1 : 1;
         B.hop[u] = (int)hop;
-        B.nblk[u] = best ? (int)((nx + hop - 1) / hop) : 0;
+        B.nblk[u] = m ? (int)((nx + hop - 1) / hop) : 0;
     }
     __syncthreads();
     // ---- work lists, one contiguous chunk of utterances per thread

@@ -251,6 +251,33 @@ def test_graph_replay_with_alternating_buffer_sets():
     plan.sync_status()
 
 
+def _merge(a, b):
+    return synth.Batch(a.num_mics, np.concatenate([a.num_sources, b.num_sources]),
+                       np.concatenate([a.num_samples, b.num_samples]),
+                       np.concatenate([a.rir_len, b.rir_len]), np.concatenate([a.x, b.x]),
+                       np.concatenate([a.rir, b.rir]), np.concatenate([a.snr_db, b.snr_db]))
+
+
+def test_minority_fft_size_moves_to_the_dominant_one():
+    # two short utterances with short RIRs would pick a small N on their own; beside
+    # thirty long ones they take the batch's dominant size, and the results stay exact
+    from paper_1712_03439_gb300 import Plan
+    big = synth.make_batch(61, [96000] * 30, [2] * 30, synth.linear_pair_array(), (0.3, 0.35))
+    small = synth.make_batch(62, [2500, 3100], [1, 2], synth.linear_pair_array(), (0.02, 0.03))
+    b = _merge(big, small)
+    S = int(b.num_sources.sum())
+    gains = np.linspace(0.8, 1.2, S).astype(np.float32)
+    plan, res, _ = gpu_forward(b, eta=20.0, gains=gains)
+    n = plan.query()["log2_n"]
+    assert len(set(n.tolist())) == 1, n
+    alone, _, _ = gpu_forward(small, eta=20.0, gains=gains[-3:])
+    assert alone.query()["log2_n"].max() < n[0]       # on their own they choose smaller sizes
+    sub = b.subset([30, 31])
+    ref = oracle.forward(sub, 20.0, alpha=gains[-3:].astype(np.float64))
+    yo = b.y_offsets()
+    assert_channels_close(res["y"][yo[30]:yo[32]], ref["y"], sub)
+
+
 def test_results_do_not_depend_on_utterance_order():
     b = small_batch(seed=14, lengths=(5000, 70000, 20000, 45000), n_src=(2, 1, 4, 3))
     perm = [2, 0, 3, 1]
