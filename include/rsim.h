@@ -131,7 +131,12 @@ rsim_status rsim_filter_mix_backward(rsim_plan_t plan, void *stream, const float
 /* Waits for the plan's stream work and reports errors latched by kernels
  * (RSIM_E_UNSUPPORTED: no allowed FFT size N has N >= 4 (N - L_max + 1), with L_max the
  * longest truncated RIR of an utterance;
- * RSIM_E_INVALID: a noise source has zero power).  Clears the latch. */
+ * RSIM_E_INVALID: a noise source has zero power;
+ * RSIM_E_DEVICE: a kernel's bounded wait (about half a second) for one of its own bulk
+ * copies into shared memory ran out; the kernel stopped early and the outputs of that
+ * call are invalid, the context stays usable).  Clears the latch.  For tests only, a plan
+ * made while the environment variable RSIM_TEST_WITHHOLD_BULK_COPY=1 is set issues no
+ * bulk copy, so that path can be exercised without any device fault. */
 rsim_status rsim_plan_sync_status(rsim_plan_t plan, void *stream);
 
 /* Copies the per-utterance plan chosen on the device by the last forward:
