@@ -258,6 +258,34 @@ def _merge(a, b):
                        np.concatenate([a.rir, b.rir]), np.concatenate([a.snr_db, b.snr_db]))
 
 
+@pytest.mark.parametrize("n_fft", [2048, 8192])
+def test_longest_admissible_rir_and_one_tap_more(n_fft):
+    # L_max = 3N/4 + 1 is the longest kept RIR a size admits (hop = N/4, the carry spans
+    # three blocks): exact against the oracle; one tap more is reported unsupported
+    from paper_1712_03439_gb300._lib import RsimError
+    lmax = 3 * n_fft // 4 + 1
+    rng = np.random.Generator(np.random.PCG64(n_fft))
+
+    def batch(nh):
+        b = small_batch(seed=80 + nh % 7, lengths=(3 * n_fft + 77, 5000), n_src=(2, 1))
+        lens = [nh, nh - 5, nh // 2, 17, nh, 3]            # (u0: i0 j0, i0 j1, i1 j0, i1 j1), (u1: ...)
+        rirs = [rng.normal(0, 0.1, L).astype(np.float32) for L in lens]
+        for h in rirs:
+            h[-1] = 0.05                                    # nonzero last tap: L = Nh without cut-off
+        return synth.Batch(b.num_mics, b.num_sources, b.num_samples, np.array(lens, np.int32),
+                           b.x, np.concatenate(rirs), b.snr_db)
+
+    b = batch(lmax)
+    gains = np.array([1.0, 0.7, 1.2], np.float32)
+    plan, res, _ = gpu_forward(b, eta=math.inf, fft_sizes=[n_fft], gains=gains)
+    assert plan.query()["hop"][0] == n_fft // 4
+    ref = oracle.forward(b, math.inf, alpha=gains.astype(np.float64))
+    assert_channels_close(res["y"], ref["y"], b)
+    with pytest.raises(RsimError) as e:
+        gpu_forward(batch(lmax + 1), eta=math.inf, fft_sizes=[n_fft], gains=gains)
+    assert e.value.status == 2
+
+
 def test_minority_fft_size_moves_to_the_dominant_one():
     # two short utterances with short RIRs would pick a small N on their own; beside
     # thirty long ones they take the batch's dominant size, and the results stay exact
