@@ -188,35 +188,6 @@ constexpr int kPlanThreads = 1024;
 constexpr float kConsolidateShare = 0.1f;   // a size below this share of the work is a minority
 constexpr float kConsolidateSlack = 0.02f;  // ...and moves if that adds at most this share of the work
 
-__device__ __forceinline__ int block_exscan(int v, int* sm, int* total) {
-    // sm: >= 32 ints
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int n = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += n;
-    }
-    __syncthreads();
-    if (lane == 31) sm[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-        int w = (lane < (int)(blockDim.x >> 5)) ? sm[lane] : 0;
-        int wi = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int n = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += n;
-        }
-        sm[lane] = wi - w;          // exclusive prefix of warp totals
-        if (lane == 31) sm[32] = wi;
-    }
-    __syncthreads();
-    int r = sm[wid] + incl - v;
-    *total = sm[32];
-    __syncthreads();
-    return r;
-}
 
 __global__ void __launch_bounds__(kPlanThreads)
 k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict__ gains) {
@@ -339,40 +310,85 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
         B.nblk[u] = m ? (int)((nx + hop - 1) / hop) : 0;
     }
     __syncthreads();
-    // ---- work lists, one contiguous chunk of utterances per thread
+    // ---- work lists, one contiguous chunk of utterances per thread.  The three
+    // lists of the four sizes are laid out by one block-wide exclusive scan of
+    // the twelve per-thread counts.
+    constexpr int kNL = 3 * kNumBuckets;           // (list kind, size) pairs
     const int per = (B.U + kPlanThreads - 1) / kPlanThreads;
     const int u0 = min(B.U, t * per), u1 = min(B.U, u0 + per);
-    for (int b = 0; b < kNumBuckets; ++b) {
-        const int m = kMinLog + b;
-        int cf = 0, cb = 0, cs = 0;
-        for (int u = u0; u < u1; ++u) {
-            if (B.logN[u] != m) continue;
-            cf += B.seg0[u + 1] - B.seg0[u];
-            cb += (B.bseg0[u + 1] - B.bseg0[u]) * B.n_src[u];
-            cs += B.rir0[u + 1] - B.rir0[u];
+    int cnt[kNL];
+#pragma unroll
+    for (int q = 0; q < kNL; ++q) cnt[q] = 0;
+    for (int u = u0; u < u1; ++u) {
+        const int m = B.logN[u];
+        if (m == 0) continue;
+        const int b = m - kMinLog;
+#pragma unroll
+        for (int q = 0; q < kNumBuckets; ++q) {
+            if (q != b) continue;
+            cnt[q] += B.seg0[u + 1] - B.seg0[u];
+            cnt[kNumBuckets + q] += (B.bseg0[u + 1] - B.bseg0[u]) * B.n_src[u];
+            cnt[2 * kNumBuckets + q] += B.rir0[u + 1] - B.rir0[u];
         }
-        int tf, tb, ts;
-        int of = block_exscan(cf, sm, &tf);
-        int ob = block_exscan(cb, sm, &tb);
-        int os = block_exscan(cs, sm, &ts);
+    }
+    __shared__ int wtot[kPlanThreads / 32][kNL];
+    __shared__ int ltot[kNL];
+    int off[kNL];
+    {
+        const int lane = t & 31, wid = t >> 5;
+#pragma unroll
+        for (int q = 0; q < kNL; ++q) {
+            int incl = cnt[q];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int n = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += n;
+            }
+            off[q] = incl - cnt[q];
+            if (lane == 31) wtot[wid][q] = incl;
+        }
+        __syncthreads();
+        if (t < kNL) {                            // exclusive scan of the warps' totals
+            int acc = 0;
+            for (int w = 0; w < kPlanThreads / 32; ++w) {
+                const int v = wtot[w][t];
+                wtot[w][t] = acc;
+                acc += v;
+            }
+            ltot[t] = acc;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kNL; ++q) off[q] += wtot[wid][q];
+    }
+    for (int u = u0; u < u1; ++u) {
+        const int m = B.logN[u];
+        if (m == 0) continue;
+        const int b = m - kMinLog;
         int32_t* lf = Q.lst(kListFwd, b);
         int32_t* lb = Q.lst(kListBwd, b);
         int32_t* ls = Q.lst(kListSpec, b);
-        for (int u = u0; u < u1; ++u) {
-            if (B.logN[u] != m) continue;
-            for (int g = B.seg0[u]; g < B.seg0[u + 1]; ++g) lf[of++] = g;
-            for (int g = B.bseg0[u]; g < B.bseg0[u + 1]; ++g)
-                for (int i = 0; i < B.n_src[u]; ++i) lb[ob++] = g * kMaxSources + i;
-            for (int r = B.rir0[u]; r < B.rir0[u + 1]; ++r) ls[os++] = r;
+        int of = 0, ob = 0, os = 0;
+#pragma unroll
+        for (int q = 0; q < kNumBuckets; ++q) {
+            if (q != b) continue;
+            of = off[q]; ob = off[kNumBuckets + q]; os = off[2 * kNumBuckets + q];
+            off[q] += B.seg0[u + 1] - B.seg0[u];
+            off[kNumBuckets + q] += (B.bseg0[u + 1] - B.bseg0[u]) * B.n_src[u];
+            off[2 * kNumBuckets + q] += B.rir0[u + 1] - B.rir0[u];
         }
-        if (t == 0) {
-            Q.count[Q.idx(kListFwd, b)] = tf;
-            Q.count[Q.idx(kListBwd, b)] = tb;
-            Q.count[Q.idx(kListSpec, b)] = ts;
-            Q.next[Q.idx(kListFwd, b)] = 0;
-            Q.next[Q.idx(kListBwd, b)] = 0;
-            Q.next[Q.idx(kListSpec, b)] = 0;
-        }
+        for (int g = B.seg0[u]; g < B.seg0[u + 1]; ++g) lf[of++] = g;
+        for (int g = B.bseg0[u]; g < B.bseg0[u + 1]; ++g)
+            for (int i = 0; i < B.n_src[u]; ++i) lb[ob++] = g * kMaxSources + i;
+        for (int r = B.rir0[u]; r < B.rir0[u + 1]; ++r) ls[os++] = r;
+    }
+    if (t < kNumBuckets) {
+        Q.count[Q.idx(kListFwd, t)] = ltot[t];
+        Q.count[Q.idx(kListBwd, t)] = ltot[kNumBuckets + t];
+        Q.count[Q.idx(kListSpec, t)] = ltot[2 * kNumBuckets + t];
+        Q.next[Q.idx(kListFwd, t)] = 0;
+        Q.next[Q.idx(kListBwd, t)] = 0;
+        Q.next[Q.idx(kListSpec, t)] = 0;
     }
 }
 
