@@ -148,13 +148,14 @@ k_power(DevBatch B, const float* __restrict__ x) {
         for (int64_t i = t; i < head; i += kPowThreads) acc(0, __ldg(p + i));
         for (int64_t i = tail0 + t; i < len; i += kPowThreads) acc(1, __ldg(p + i));
         const float4* p4 = reinterpret_cast<const float4*>(p + head);
+        constexpr int kU = 4;                    // float4 loads in flight per thread
         int64_t j = t;
-        for (; j + 3 * kPowThreads < nvec; j += 4 * kPowThreads) {
-            float4 a[4];
+        for (; j + (kU - 1) * kPowThreads < nvec; j += kU * kPowThreads) {
+            float4 a[kU];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) a[k] = __ldg(p4 + j + k * kPowThreads);
+            for (int k = 0; k < kU; ++k) a[k] = __ldg(p4 + j + k * kPowThreads);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < kU; ++k) {
                 acc(0, a[k].x); acc(1, a[k].y); acc(2, a[k].z); acc(3, a[k].w);
             }
         }
