@@ -57,32 +57,30 @@ k_spectrum(DevBatch B, Queues Q, int bucket, const float* __restrict__ rir, floa
 //                                                          MAC, Y_j in registers
 //   y_j block = irFFT_N(Y_j) plus the carry of the earlier blocks; its first
 //   hop samples are stored, the last L_max - 1 samples are the new carry.
-// Global reads are prefetched with cp.async one step ahead so no transform
-// waits on memory: the next source's x block lands in a shared-memory stage
-// while the current one is transformed, and the next source's RIR spectra
-// while the current MAC finishes and the next transform runs.  Twiddles are
-// copied to shared memory once per CTA.  The tail leaving the segment's last
+// The next source's x block is prefetched one step ahead by one bulk copy
+// into a shared-memory stage (whole 16-byte chunks by the copy engine,
+// completing on an mbarrier the threads wait on with a bounded wait) while the
+// current one is transformed; the RIR spectra are read through L2 as mirror
+// pairs.  Twiddles are copied to shared memory once per CTA (N <= 8192).  The tail leaving the segment's last
 // block goes to `tails`; the tile of the next segment stored its first block
 // without it and k_fixup adds it afterwards (one FP32 add, the same one done
 // in-tile, so results do not depend on the segmentation).  Microphones are
 // processed in groups of kJG; source spectra are recomputed per group.
 // Thread shape and shared-memory layout of the forward kernel per size:
-// E values per thread (T = M / E threads), whether the RIR spectra, the
-// carried tails and the twiddles sit in shared memory, and the CTAs per SM
-// the register budget is set for.
+// E values per thread (T = M / E threads), whether the carried tails and the
+// twiddles sit in shared memory, and the CTAs per SM the register budget is
+// set for.
 template <int M>
 struct FwdCfg {
     static constexpr int E = (M == 4096 || M == 8192) ? 16 : 8;
     static constexpr int T = M / E;
     static constexpr int kMinBlocks = (M <= 4096) ? 2 : 1;
-    static constexpr bool kStageH = false;
     static constexpr bool kTailSmem = (M <= 2048);
     static constexpr bool kTwSmem = (M <= 4096);
     static constexpr size_t a16(size_t v) { return (v + 15) / 16 * 16; }
     static constexpr size_t o_sm = 0;
     static constexpr size_t o_xs = a16(o_sm + sizeof(float2) * padded_len(M));
-    static constexpr size_t o_hs = a16(o_xs + sizeof(float) * (2 * M + 8));   // + chunk offset room
-    static constexpr size_t o_tl = a16(o_hs + (kStageH ? sizeof(float2) * kJG * M : 0));
+    static constexpr size_t o_tl = a16(o_xs + sizeof(float) * (2 * M + 8));   // + chunk offset room
     static constexpr size_t o_tw = a16(o_tl + (kTailSmem ? sizeof(float) * kJG * 2 * M : 0));
     static constexpr size_t bytes = a16(o_tw + (kTwSmem ? sizeof(float2) * FftPlan<M, E>::TW_LEN : 0));
 };
@@ -99,7 +97,6 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* sm = reinterpret_cast<float2*>(smem_raw + L::o_sm);
     float* xs = reinterpret_cast<float*>(smem_raw + L::o_xs);
-    float2* hs = reinterpret_cast<float2*>(smem_raw + L::o_hs);
     float* tl_smem = reinterpret_cast<float*>(smem_raw + L::o_tl);
     __shared__ int slot;
     __shared__ __align__(8) uint64_t mbar;
@@ -138,7 +135,6 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
         const int sb = B.src0[u], rb = B.rir0[u];
         for (int j0 = 0; j0 < J; j0 += kJG) {
             const int jn = min(kJG, J - j0);
-            // queue the copies of source i's block b and of its spectra
             // one bulk copy per source block into the stage (whole 16-byte chunks by
             // the copy engine, completing on mbar; ragged ends and zeros by stores)
             auto stage_x = [&](int64_t b, int i) {
@@ -146,12 +142,6 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
                 const int64_t p = b * hop;
                 xoff = stage_real_bulk<M, E>(xs, x + B.xoff[sb + i] + p, min((int64_t)hop, nx - p), &mbar, t,
                                              B.test_withhold != 0);
-            };
-            auto stage_h = [&](int i) {
-                if constexpr (L::kStageH) {
-                    for (int jj = 0; jj < jn; ++jj)
-                        stage_spectrum_async<M, E>(hs + jj * M, Hc + (int64_t)(rb + i * J + j0 + jj) * B.MMAX, t);
-                }
             };
             // carried tail of mic jj: shared memory, or this tile's slot of `tails`
             auto tl = [&](int jj) -> float* {
@@ -162,9 +152,6 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
             for (int jj = 0; jj < jn; ++jj)
                 for (int n = t; n < tail_len; n += T) tl(jj)[n] = 0.f;
             stage_x(b0, 0);
-            cp_async_commit();
-            stage_h(0);
-            cp_async_commit();
             for (int64_t b = b0; b < b1; ++b) {
                 const int64_t pos = b * hop;
                 float2 Y[kJG][E];
@@ -173,8 +160,7 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
 #pragma unroll
                     for (int e = 0; e < E; ++e) Y[jj][e] = make_float2(0.f, 0.f);
                 for (int i = 0; i < I; ++i) {
-                    // x_i is in (only the newest group, H_i, may still be pending)
-                    cp_async_wait<1>();
+                    // x_i is in
                     if (!bad && !mbar_wait_bounded(&mbar, ph)) {
                         mbar_wait_bounded(&mbar, ph, 100000000ull);   // one more chance to land
                         bad = true;
@@ -186,11 +172,9 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
                     __syncthreads();             // xs fully read: reuse it
                     if (i + 1 < I) stage_x(b, i + 1);
                     else if (b + 1 < b1) stage_x(b + 1, 0);
-                    cp_async_commit();
                     fft_core<M, E>(v, sm, tw, t);
                     __syncthreads();
                     store_strided<M, E>(v, sm, t);
-                    cp_async_wait<1>();          // H_i is in
                     __syncthreads();
                     const float a = __ldg(gains + sb + i);
                     const float2* H0 = Hc + (int64_t)(rb + i * J + j0) * B.MMAX;
@@ -204,9 +188,7 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
 #pragma unroll
                         for (int jj = 0; jj < kJG; ++jj) {
                             if (jj >= jn) break;
-                            const float4 hh = L::kStageH
-                                ? reinterpret_cast<const float4*>(hs + jj * M)[k]
-                                : __ldg(reinterpret_cast<const float4*>(H0 + (int64_t)jj * B.MMAX) + k);
+                            const float4 hh = __ldg(reinterpret_cast<const float4*>(H0 + (int64_t)jj * B.MMAX) + k);
                             const float2 ha = make_float2(hh.x, hh.y), hb = make_float2(hh.z, hh.w);
                             if (k == 0) {            // slot 0 holds two real bins
                                 Y[jj][0].x += xa.x * ha.x;
@@ -217,10 +199,6 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
                             Y[jj][2 * q + 1] = cadd(Y[jj][2 * q + 1], cmul(xb, hb));
                         }
                     }
-                    __syncthreads();             // hs fully read: reuse it
-                    if (i + 1 < I) stage_h(i + 1);
-                    else if (b + 1 < b1 && I > 1) stage_h(0);
-                    cp_async_commit();
                 }
 #pragma unroll
                 for (int jj = 0; jj < kJG; ++jj) {
@@ -280,7 +258,6 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
             break;
         }
     }
-    cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
