@@ -88,6 +88,15 @@ def _bind(lib):
     lib.oracle_dft_real.argtypes = [P, i64, i64, P, P]
     lib.oracle_max_threads.restype = ctypes.c_int
     lib.oracle_max_threads.argtypes = []
+    lib.oracle_image_list.restype = i64
+    lib.oracle_image_list.argtypes = [P, P, P, ctypes.c_float, i32, ctypes.c_float, ctypes.c_float,
+                                      P, P, P, P]
+    lib.oracle_image_rir.restype = i64
+    lib.oracle_image_rir.argtypes = [P, P, P, ctypes.c_float, i32, ctypes.c_float, ctypes.c_float,
+                                     i64, P]
+    lib.oracle_image_rirs.restype = None
+    lib.oracle_image_rirs.argtypes = [i64, P, P, i32, ctypes.c_float, ctypes.c_float, P, P,
+                                      ctypes.c_int]
     return lib
 
 
@@ -300,6 +309,48 @@ def forward_ola(batch, L, alpha, fft_n=0, nthreads=0, lib=None):
     if rc:
         raise OracleError("invalid FFT size")
     return y
+
+
+# ---- Eq. 1: image-method RIRs ------------------------------------------------
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def image_list(room, src, mic, refl, order=8, fs=16000.0, c0=343.0, lib=None):
+    """Every image of one (source, microphone) pair in a room, virtual rooms in
+    (a, b, c) order with c fastest.  Returns dict(pos [V, 3], g, delay, amp)."""
+    V = (2 * int(order) + 1) ** 3
+    pos, amp = np.zeros((V, 3)), np.zeros(V)
+    g, delay = np.zeros(V, np.int32), np.zeros(V, np.int64)
+    n = (lib or _load()).oracle_image_list(_p(_f32(room)), _p(_f32(src)), _p(_f32(mic)), float(refl),
+                                           int(order), float(fs), float(c0), _p(pos), _p(g), _p(delay),
+                                           _p(amp))
+    if n < 0:
+        raise OracleError("invalid image-method arguments")
+    return dict(pos=pos, g=g, delay=delay, amp=amp)
+
+
+def image_rir(room, src, mic, refl, n_h, order=8, fs=16000.0, c0=343.0, lib=None):
+    """Eq. 1 for one (source, microphone) pair: returns (h [n_h] FP64, images landed)."""
+    h = np.zeros(int(n_h))
+    n = (lib or _load()).oracle_image_rir(_p(_f32(room)), _p(_f32(src)), _p(_f32(mic)), float(refl),
+                                          int(order), float(fs), float(c0), int(n_h), _p(h))
+    if n < 0:
+        raise OracleError("invalid image-method arguments")
+    return h, int(n)
+
+
+def image_rirs(geom, rir_len, order=8, fs=16000.0, c0=343.0, nthreads=0, lib=None):
+    """Eq. 1 over a batch.  geom [R, 10] float32 rows (room, source, microphone,
+    r); rir_len [R].  Returns (h packed FP64 [sum rir_len], valid bool [R])."""
+    geom = _f32(geom).reshape(-1, 10)
+    R = geom.shape[0]
+    off = _i64(np.concatenate([[0], np.cumsum(np.asarray(rir_len, dtype=np.int64))]))
+    h = np.zeros(int(off[-1]))
+    valid = np.zeros(R, np.int32)
+    (lib or _load()).oracle_image_rirs(R, _p(geom), _p(off), int(order), float(fs), float(c0), _p(h),
+                                       _p(valid), nthreads)
+    return h, valid.astype(bool)
 
 
 def eta_is_none(eta_db) -> bool:

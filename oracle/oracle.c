@@ -19,7 +19,11 @@
  *   Eq. 6  the paper's overlap-add FFT filtering, one (i, j) at a time, with
  *          its own radix-2 FFT (oracle_mix_ola, used to cross-check and to
  *          give full-batch references quickly)
- *   Eq. 3, 5, 6  the paper's multiplication-count models.
+ *   Eq. 3, 5, 6  the paper's multiplication-count models
+ *   Eq. 1  the image-method room impulse response (Sec. 2), h[n] as the sum
+ *          of r^g_v / d_v delta[n - ceil(d_v fs / c0)] over the images of
+ *          the source in (2K+1)^3 virtual rooms (its readings are listed
+ *          above oracle_image_list).
  *
  * Readings taken where the paper is silent or garbled:
  *   - output length: n in [0, Nx) (Eq. 2 gives no range);
@@ -578,4 +582,159 @@ int oracle_forward_ola_batch(int32_t U, int32_t J, const int32_t *n_src, const i
     free(rel);
     layout_free(&lo);
     return bad ? ORACLE_E_INVALID : ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 1: image-method room impulse response                                 */
+/* ------------------------------------------------------------------------ */
+/*
+ * Readings of Sec. 2 and Eq. 1:
+ *  - the room is the box [0, Lx] x [0, Ly] x [0, Lz] (metres); mirroring it
+ *    across its walls, again and again, tiles space with virtual rooms indexed
+ *    (a, b, c), each index in [-K, K] (K = 8 gives the paper's 17^3 = 4913);
+ *    every virtual room holds one image of the source;
+ *  - along one axis, virtual room a spans [a L, (a + 1) L]; each mirroring
+ *    flips the source coordinate, so the image sits at a L + s for even a and
+ *    at (a + 1) L - s for odd a, and it took |a| reflections to get there;
+ *    g_v = |a| + |b| + |c|;
+ *  - all walls share one reflection coefficient r, 0 <= r < 1 (r = 0 keeps the
+ *    direct path alone, r^0 = 1);
+ *  - the delay ceil(d_v fs / c0) is an integer decision and is taken in FP32,
+ *    the kernel's precision: image coordinate, offset to the microphone, the
+ *    three squares, their sum ((x + y) + z), the square root, d * fs and the
+ *    division by c0 are each one correctly rounded FP32 operation, so both
+ *    implementations put every image on the same sample.  The amplitude
+ *    r^g_v / d_v is FP64, from the same FP32 inputs;
+ *  - an image whose delay is n_h or later lies outside the RIR and is dropped;
+ *  - the source and the microphone lie strictly inside the room, and no image
+ *    may sit at distance zero from the microphone (d_v > 0, Eq. 1).
+ */
+
+static int image_geom_valid(const float *room, const float *src, const float *mic, float refl)
+{
+    for (int k = 0; k < 3; ++k) {
+        if (!(room[k] > 0.0f) || !isfinite(room[k])) return 0;
+        if (!(src[k] > 0.0f && src[k] < room[k])) return 0;
+        if (!(mic[k] > 0.0f && mic[k] < room[k])) return 0;
+    }
+    return refl >= 0.0f && refl < 1.0f;
+}
+
+/* offset from the microphone to the image coordinate of virtual room a, FP32 */
+static float image_offset_f32(int a, float len, float s, float m)
+{
+    float p;
+    if (a % 2 == 0) {
+        float base = (float)a * len;
+        p = base + s;
+    } else {
+        float base = (float)(a + 1) * len;
+        p = base - s;
+    }
+    return p - m;
+}
+
+/* the same in FP64 (for the amplitude) */
+static double image_offset_f64(int a, double len, double s, double m)
+{
+    double p = (a % 2 == 0) ? (double)a * len + s : (double)(a + 1) * len - s;
+    return p - m;
+}
+
+typedef struct {
+    double pos[3];  /* image position (FP64) */
+    int32_t g;      /* reflections */
+    int64_t delay;  /* ceil(d fs / c0), FP32 decision */
+    double amp;     /* r^g / d, FP64 */
+    int ok;         /* 0: the image is at distance zero */
+} image_t;
+
+static image_t image_eval(const float *room, const float *src, const float *mic, float refl,
+                          int a, int b, int c, float fs, float c0)
+{
+    image_t im;
+    const int idx[3] = {a, b, c};
+    float d2 = 0.0f;
+    double e2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        float e = image_offset_f32(idx[k], room[k], src[k], mic[k]);
+        float sq = e * e;
+        d2 = (k == 0) ? sq : d2 + sq;
+        double ed = image_offset_f64(idx[k], room[k], src[k], mic[k]);
+        im.pos[k] = ed + (double)mic[k];
+        e2 += ed * ed;
+    }
+    im.ok = d2 > 0.0f && e2 > 0.0;
+    float d = sqrtf(d2);
+    float num = d * fs;
+    float t = num / c0;
+    im.delay = (int64_t)ceilf(t);
+    im.g = abs(a) + abs(b) + abs(c);
+    im.amp = im.ok ? pow((double)refl, (double)im.g) / sqrt(e2) : 0.0;
+    return im;
+}
+
+/* Every image of one (source, microphone) pair, rooms in (a, b, c) order with
+ * c fastest.  Arrays hold (2K+1)^3 entries.  Returns the count, or -1 if the
+ * arguments are invalid. */
+int64_t oracle_image_list(const float *room, const float *src, const float *mic, float refl,
+                          int32_t order, float fs, float c0, double *pos, int32_t *g,
+                          int64_t *delay, double *amp)
+{
+    if (order < 0 || !(fs > 0.0f) || !(c0 > 0.0f) || !isfinite(fs) || !isfinite(c0)) return -1;
+    if (!image_geom_valid(room, src, mic, refl)) return -1;
+    int64_t v = 0;
+    for (int a = -order; a <= order; ++a)
+        for (int b = -order; b <= order; ++b)
+            for (int c = -order; c <= order; ++c, ++v) {
+                image_t im = image_eval(room, src, mic, refl, a, b, c, fs, c0);
+                if (!im.ok) return -1;
+                for (int k = 0; k < 3; ++k) pos[3 * v + k] = im.pos[k];
+                g[v] = im.g;
+                delay[v] = im.delay;
+                amp[v] = im.amp;
+            }
+    return v;
+}
+
+/* Eq. 1: h[n] = sum_v r^g_v / d_v delta[n - ceil(d_v fs / c0)] for n < n_h.
+ * h is zeroed first.  Returns the number of images that landed in [0, n_h),
+ * or -1 (h left zero) if the arguments are invalid. */
+int64_t oracle_image_rir(const float *room, const float *src, const float *mic, float refl,
+                         int32_t order, float fs, float c0, int64_t n_h, double *h)
+{
+    if (n_h < 0 || n_h > ((int64_t)1 << 24)) return -1;
+    for (int64_t n = 0; n < n_h; ++n) h[n] = 0.0;
+    if (order < 0 || !(fs > 0.0f) || !(c0 > 0.0f) || !isfinite(fs) || !isfinite(c0)) return -1;
+    if (!image_geom_valid(room, src, mic, refl)) return -1;
+    int64_t landed = 0;
+    for (int a = -order; a <= order; ++a)
+        for (int b = -order; b <= order; ++b)
+            for (int c = -order; c <= order; ++c) {
+                image_t im = image_eval(room, src, mic, refl, a, b, c, fs, c0);
+                if (!im.ok) {
+                    for (int64_t n = 0; n < n_h; ++n) h[n] = 0.0;
+                    return -1;
+                }
+                if (im.delay < n_h) {
+                    h[im.delay] += im.amp;
+                    ++landed;
+                }
+            }
+    return landed;
+}
+
+/* Batch form: RIR r has geometry geom[10 r .. 10 r + 9] = room (3), source (3),
+ * microphone (3), r; its taps are h[off[r] .. off[r + 1]).  valid[r] = 1 if its
+ * arguments were valid (an invalid RIR is left zero).  OpenMP across RIRs. */
+void oracle_image_rirs(int64_t R, const float *geom, const int64_t *off, int32_t order, float fs,
+                       float c0, double *h, int32_t *valid, int nthreads)
+{
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t r = 0; r < R; ++r) {
+        const float *gr = geom + 10 * r;
+        valid[r] = oracle_image_rir(gr, gr + 3, gr + 6, gr[9], order, fs, c0, off[r + 1] - off[r],
+                                    h + off[r]) >= 0;
+    }
 }

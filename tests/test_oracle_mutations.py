@@ -48,8 +48,28 @@ MUTANTS = [
 ]
 
 
-@pytest.mark.parametrize("name,orig,planted", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_pins_catch_planted_mistake(tmp_path, name, orig, planted):
+# mistakes in the image-method RIR (Eq. 1), run against its own pin file
+IMAGE_MUTANTS = [
+    ("image_odd_parity_flipped", "if (a % 2 == 0) {", "if (a % 2 != 0) {"),
+    ("image_f64_odd_coordinate", "(double)(a + 1) * len - s", "(double)a * len - s"),
+    ("image_g_drops_axis", "im.g = abs(a) + abs(b) + abs(c);", "im.g = abs(a) + abs(b);"),
+    ("image_delay_floor", "im.delay = (int64_t)ceilf(t);", "im.delay = (int64_t)floorf(t);"),
+    ("image_delay_round", "im.delay = (int64_t)ceilf(t);", "im.delay = (int64_t)roundf(t);"),
+    ("image_amp_inverse_square", "/ sqrt(e2) : 0.0;", "/ e2 : 0.0;"),
+    ("image_fs_c0_swapped", "float num = d * fs;\n    float t = num / c0;",
+     "float num = d * c0;\n    float t = num / fs;"),
+    ("image_loop_short", "for (int c = -order; c <= order; ++c) {\n                image_t im",
+     "for (int c = -order; c < order; ++c) {\n                image_t im"),
+    ("image_drops_last_sample", "if (im.delay < n_h) {", "if (im.delay < n_h - 1) {"),
+    ("image_d2_misses_z", "d2 = (k == 0) ? sq : d2 + sq;", "d2 = (k == 0) ? sq : (k == 1 ? d2 + sq : d2);"),
+]
+
+CASES = [(*m, "test_oracle_pins.py") for m in MUTANTS] + \
+    [(*m, "test_oracle_image_pins.py") for m in IMAGE_MUTANTS]
+
+
+@pytest.mark.parametrize("name,orig,planted,pins", CASES, ids=[c[0] for c in CASES])
+def test_pins_catch_planted_mistake(tmp_path, name, orig, planted, pins):
     src = open(SRC).read()
     assert src.count(orig) == 1, f"mutation site for {name} not found exactly once"
     mpath = tmp_path / "oracle_mutant.c"
@@ -60,6 +80,6 @@ def test_pins_catch_planted_mistake(tmp_path, name, orig, planted):
                    check=True)
     env = dict(os.environ, ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", pins)],
                        env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} passed every pin:\n{r.stdout[-2000:]}"
