@@ -724,6 +724,109 @@ def run_long(args):
     return 0
 
 
+def image_work(geom_rows: int, rir_len, order: int):
+    """Algorithmic work of rsim_image_rirs: every tap written once (zeros
+    included) and each RIR's 40-byte geometry and 8-byte offset read; per
+    image one FP32 add pair, square root, multiply and two divisions (counted
+    as 6 flops), for the (2K+1)^3 images of every RIR."""
+    taps = int(np.sum(np.asarray(rir_len, dtype=np.int64)))
+    nbytes = 4.0 * taps + 48.0 * geom_rows + 8.0
+    flops = 6.0 * geom_rows * (2 * order + 1) ** 3
+    return nbytes, flops
+
+
+def run_rooms(args):
+    """Image-method RIRs (Eq. 1, 17^3 virtual rooms) for the Home mix, made on
+    the device and fed to the filter-and-mix step: the generator's own time and
+    roofline, and the whole step (RIRs + forward + backward)."""
+    import torch
+    from paper_1712_03439_gb300 import Plan, build, image_rirs, synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    build.build()
+    order = 8
+    b, geom = synth.config_home_rooms()
+    lens = b.rir_len.astype(np.int64)
+    off = np.concatenate([[0], np.cumsum(lens)])
+    audio_s = b.audio_seconds()
+    g_d, off_d = torch.from_numpy(geom).to(dev), torch.from_numpy(off).to(dev)
+    rir = torch.empty(int(off[-1]), device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    x, snr = torch.from_numpy(b.x).to(dev), torch.from_numpy(b.snr_db).to(dev)
+    gy = torch.from_numpy(synth.grad_like(97, b.y_size)).to(dev)
+    hbm, p_fp32, peak_kind = _peaks_fp32(torch, dev)
+    # the generator alone: its 41 MB output fits in L2, so L2 is flushed (a 256 MB
+    # write) before every timed launch and each launch is timed on its own
+    flush = torch.empty(64 << 20, device=dev)
+    st = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        image_rirs(g_d, off_d, int(lens.max()), rir, order=order, status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0, "invalid room geometry"
+    n_img = max(args.steps, 20)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_img)]
+    clock = ClockSampler(0)
+    for e0, e1 in evs:
+        flush.fill_(1.0)
+        e0.record(st)
+        image_rirs(g_d, off_d, int(lens.max()), rir, order=order)
+        e1.record(st)
+    torch.cuda.synchronize()
+    img_ms = float(np.mean([a.elapsed_time(z) for a, z in evs]))
+    nbytes, flops = image_work(geom.shape[0], lens, order)
+    img_roof = roofline_entry(flops, nbytes, img_ms, p_fp32, hbm, peak_kind, _traffic_for("k_image_rirs"))
+    # the step: RIRs from the rooms, then forward and backward
+    plan = Plan.for_batch(b, eta_db=ETA_DB, gain_mode=0, device=0)
+    gains, y = torch.empty(plan.S, device=dev), torch.empty(plan.y_size, device=dev)
+    gx, gr, gg = torch.empty_like(x), torch.empty_like(rir), torch.empty_like(gains)
+
+    def step():
+        image_rirs(g_d, off_d, int(lens.max()), rir, order=order)
+        plan.filter_mix(x, rir, gains, y, snr_db=snr)
+        plan.filter_mix_backward(gy, x, gains, gx, gr, gg)
+    for _ in range(max(args.warmup, 3)):
+        step()
+    plan.sync_status()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    clocks = clock.stop()
+    q = plan.query()
+    plan.close()
+    line = {"metric": "simulated audio s/sec (image-method RIRs + fwd + bwd) at 16 kHz, 1xGB300",
+            "value": audio_s / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic: the Home mix's signals with image-method rooms (seeded)",
+            "config": {"workload": f"home-rooms-{b.num_utts}: the Home mix, one cuboid room per utterance "
+                                   "(3-10 x 3-8 x 2.5-5 m, Sabine reflection from RT60 U(0.1,0.9) s), "
+                                   f"{geom.shape[0]} RIRs of ceil(RT60 fs) taps, {(2 * order + 1) ** 3} "
+                                   "virtual rooms each, eta 20 dB",
+                       "audio_seconds": audio_s, "rirs": int(geom.shape[0]), "taps": int(off[-1]),
+                       "fft_sizes": {int(k): int(c) for k, c in zip(*np.unique(
+                           1 << q["log2_n"].astype(np.int64), return_counts=True))},
+                       "l2": "generator timed alone after a 256 MB L2 flush per launch; the step's "
+                             "inputs (x 0.35 GB) are larger than L2"},
+            "image_rirs": {"ms": img_ms, "launches_timed": n_img, "rirs_per_s": geom.shape[0] / (img_ms / 1e3),
+                           "roofline": img_roof},
+            "clocks": clocks}
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.image_rirs(geom[:8], lens[:8], order=order)     # builds and loads the oracle
+        t0 = time.perf_counter()
+        oracle.image_rirs(geom, lens, order=order)
+        cpu_s = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": geom.shape[0] / cpu_s, "unit": "RIRs/s", "cores": oracle.max_threads(),
+                                "kind": "oracle",
+                                "sample": f"all {geom.shape[0]} RIRs of the workload (FP64 amplitudes)"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def oracle_free_lengths(b, eta):
     """Kept lengths (Eq. 7-9) computed in numpy for the report when the library
     rejects the batch (FP64 compare, as the kernels do)."""
@@ -751,9 +854,9 @@ def main():
     ap.add_argument("--only-step", action="store_true",
                     help="time only the K steps (no forward-only, end-to-end, plain or CPU legs); "
                          "for profiler runs")
-    ap.add_argument("--config", choices=["home", "stream", "long"], default="home",
-                    help="home: the headline line; stream / long: reports on the streaming and the "
-                         "long reverberant workloads")
+    ap.add_argument("--config", choices=["home", "stream", "long", "rooms"], default="home",
+                    help="home: the headline line; stream / long / rooms: reports on the streaming, "
+                         "the long reverberant and the image-method-room workloads")
     ap.add_argument("--stream-utts", type=int, default=4096)
     ap.add_argument("--budget-gb", type=float, default=2.0)
     ap.add_argument("--long-utts", type=int, default=32)
@@ -765,6 +868,8 @@ def main():
         return run_stream(args)
     if args.config == "long":
         return run_long(args)
+    if args.config == "rooms":
+        return run_rooms(args)
     return run_ours(args)
 
 

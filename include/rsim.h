@@ -200,6 +200,56 @@ rsim_status rsim_source_gains_noalloc(void *stream, int32_t num_utts, const int3
                                       const int64_t *num_samples, const float *x, const float *snr_db,
                                       float *gains);
 
+/* ---- image-method room impulse responses (Eq. 1, Sec. 2) -------------------
+ *
+ * One RIR per (source, microphone) pair of a cuboid room by the image method:
+ *     h[n] = sum_v r^g_v / d_v * delta[n - ceil(d_v fs / c0)],   0 <= n < n_h,
+ * summed over the images of the source in the (2K+1)^3 virtual rooms (a, b, c),
+ * |a|, |b|, |c| <= K, that mirroring the room across its walls produces (the
+ * paper uses K = 8: 17^3 = 4913 rooms, fs = 16 kHz, c0 = 343 m/s).  The room
+ * is the box [0, Lx] x [0, Ly] x [0, Lz]; along one axis virtual room a spans
+ * [a L, (a+1) L] and holds the image a L + s (a even) or (a+1) L - s (a odd),
+ * reached after |a| reflections, so g_v = |a| + |b| + |c|.  d_v is the image's
+ * distance to the microphone and r the reflection coefficient of every wall.
+ *
+ * The delay is an integer decision made in FP32: image coordinate, offset to
+ * the microphone, squares, their sum (x + y) + z, square root, d * fs and the
+ * division by c0 are each one correctly rounded FP32 operation in that order,
+ * so the delay of every image is reproducible bit for bit.  Amplitudes are
+ * FP32 (r^g by repeated squaring, then one division by d) and summed in shared
+ * memory in no fixed order: taps where images collide can differ in the last
+ * bits from call to call.  An image whose delay is n_h or later is dropped.
+ *
+ * The output has the packed layout rsim_filter_mix reads: RIR r occupies
+ * rir[rir_off[r] .. rir_off[r+1]), so rsim_plan_desc.rir_len[r] must be
+ * rir_off[r+1] - rir_off[r] for the generated RIRs to feed the mix directly.
+ */
+typedef struct {
+    float room[3];   /* Lx, Ly, Lz in metres, each > 0 and finite */
+    float src[3];    /* source position, strictly inside the room */
+    float mic[3];    /* microphone position, strictly inside the room, not at the source */
+    float refl;      /* wall reflection coefficient r, 0 <= r < 1 (r = 0: direct path only) */
+} rsim_image_geom;
+
+/*   stream     cudaStream_t (NULL = legacy default stream)
+ *   num_rirs   R >= 0 (0: nothing but the status reset)
+ *   geom       [R] device, read only
+ *   rir_off    [R+1] device, read only: nondecreasing offsets into rir; every
+ *              length rir_off[r+1] - rir_off[r] at most 2^24 taps
+ *   max_len    host: the longest length, in [0, 2^24]; it sizes the grid only
+ *              (a longer RIR is still written whole)
+ *   order      K in [0, 32]
+ *   fs, c0     sampling rate (Hz) and speed of sound (m/s), finite and > 0
+ *   rir        device, written on [rir_off[0], rir_off[R]) (caller-owned)
+ *   status     device int32 or NULL; set to 0, then bit 1 is set if some
+ *              geometry is invalid (its RIR is written as zeros) and bit 2 if
+ *              some length is negative or above 2^24 (that RIR is not written)
+ * Returns RSIM_E_INVALID for a bad host argument, RSIM_E_CUDA if the launch
+ * fails; asynchronous otherwise.  No allocation; safe to capture in a graph. */
+rsim_status rsim_image_rirs(void *stream, int32_t num_rirs, const rsim_image_geom *geom,
+                            const int64_t *rir_off, int64_t max_len, int32_t order, float fs, float c0,
+                            float *rir, int32_t *status);
+
 /* Message describing the calling thread's last error ("" if none). */
 const char *rsim_last_error(void);
 

@@ -668,7 +668,8 @@ static image_t image_eval(const float *room, const float *src, const float *mic,
     float d = sqrtf(d2);
     float num = d * fs;
     float t = num / c0;
-    im.delay = (int64_t)ceilf(t);
+    /* a travel time beyond any RIR length (huge rooms overflow to +inf) */
+    im.delay = t < 1e18f ? (int64_t)ceilf(t) : INT64_MAX;
     im.g = abs(a) + abs(b) + abs(c);
     im.amp = im.ok ? pow((double)refl, (double)im.g) / sqrt(e2) : 0.0;
     return im;

@@ -6,8 +6,9 @@ input generators, does not need a GPU):
   filter_mix           -- forward with allocated outputs
   RsimFilterMix        -- torch.autograd.Function with the hand-written adjoint
   filter_mix_autograd  -- RsimFilterMix.apply
+  image_rirs           -- image-method RIRs (wraps rsim_image_rirs)
 """
-_API = ("Plan", "filter_mix", "RsimFilterMix", "filter_mix_autograd")
+_API = ("Plan", "filter_mix", "RsimFilterMix", "filter_mix_autograd", "image_rirs")
 
 __all__ = list(_API) + ["synth", "build"]
 

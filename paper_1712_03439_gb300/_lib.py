@@ -19,7 +19,7 @@ STATUS_NAMES = {0: "RSIM_OK", 1: "RSIM_E_INVALID", 2: "RSIM_E_UNSUPPORTED", 3: "
 EXPORTED = ["rsim_plan", "rsim_filter_mix", "rsim_filter_mix_backward", "rsim_plan_sync_status",
             "rsim_plan_query", "rsim_plan_set_timing", "rsim_plan_stage_times",
             "rsim_plan_scratch_bytes", "rsim_plan_destroy", "rsim_source_gains_noalloc",
-            "rsim_last_error"]
+            "rsim_image_rirs", "rsim_last_error"]
 STAGES = ["truncate", "power", "plan", "spectrum", "forward", "fixup", "backward", "finalize"]
 
 
@@ -80,9 +80,10 @@ def load(path: str | None = None):
     lib.rsim_plan_destroy.argtypes = [P]
     lib.rsim_source_gains_noalloc.restype = ctypes.c_int
     lib.rsim_source_gains_noalloc.argtypes = [P, ctypes.c_int32, P, P, P, P, P]
+    lib.rsim_image_rirs.restype = ctypes.c_int
+    lib.rsim_image_rirs.argtypes = [P, i32, P, P, i64, i32, ctypes.c_float, ctypes.c_float, P, P]
     lib.rsim_last_error.restype = ctypes.c_char_p
     lib.rsim_last_error.argtypes = []
-    del i32
     if path is None:
         _lib = lib
     return lib

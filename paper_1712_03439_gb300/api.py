@@ -186,6 +186,34 @@ def source_gains_noalloc(num_sources, num_samples, x, snr_db, gains, stream=None
     _lib.check(lib, st)
 
 
+# image-method RIRs: bits of the status word rsim_image_rirs writes
+IMAGE_BAD_GEOMETRY = 1
+IMAGE_BAD_LENGTH = 2
+
+
+def image_rirs(geom, rir_off, max_len, rir, order=8, fs=16000.0, c0=343.0, status=None, stream=None):
+    """rsim_image_rirs: Eq. 1 RIRs for R (source, microphone) pairs.
+
+    geom      float32 CUDA tensor [R, 10]: room (3), source (3), microphone (3), r
+    rir_off   int64 CUDA tensor [R + 1]: RIR r is rir[rir_off[r]:rir_off[r + 1]]
+    max_len   the longest RIR (host int; sizes the launch)
+    rir       float32 CUDA tensor, written
+    status    optional int32 CUDA tensor [1]: IMAGE_BAD_GEOMETRY / IMAGE_BAD_LENGTH bits"""
+    lib = _lib.load()
+    if not isinstance(geom, torch.Tensor) or not geom.is_cuda or geom.dtype != torch.float32 \
+            or not geom.is_contiguous() or geom.dim() != 2 or geom.shape[1] != 10:
+        raise ValueError("geom must be a contiguous float32 CUDA tensor of shape [R, 10]")
+    R = int(geom.shape[0])
+    _want(rir_off, R + 1, torch.int64, "rir_off")
+    if not isinstance(rir, torch.Tensor) or not rir.is_cuda or rir.dtype != torch.float32 \
+            or not rir.is_contiguous():
+        raise ValueError("rir must be a contiguous float32 CUDA tensor")
+    _want(status, 1, torch.int32, "status")
+    st = lib.rsim_image_rirs(_stream(stream), R, _ptr(geom), _ptr(rir_off), int(max_len), int(order),
+                             float(fs), float(c0), _ptr(rir), _ptr(status))
+    _lib.check(lib, st)
+
+
 # ---------------------------------------------------------------------------
 # convenience and autograd
 # ---------------------------------------------------------------------------

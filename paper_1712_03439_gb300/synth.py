@@ -22,6 +22,19 @@ Recipe (all draws from numpy PCG64):
     n < ceil(RT60 fs), plus a direct impulse 1/r at d0 = round(fs r / 343),
     where r is the source-to-microphone distance;
   * SNR: uniform in [0, 30] dB per noise source.
+
+Rooms for the image-method RIRs (`room_geometry`):
+  * one cuboid room per utterance, Lx ~ U(3, 10), Ly ~ U(3, 8), Lz ~ U(2.5, 5) m;
+  * RT60 ~ U(0.1, 0.9) s; every wall's reflection coefficient follows from
+    Sabine's formula, r = sqrt(1 - a) with a = 0.161 V / (S RT60) clipped to
+    [0.01, 0.99] (V the volume, S the wall area);
+  * the microphone array (the same geometry as above, in the horizontal
+    plane, turned by a random azimuth) is centred at a uniform point at least
+    0.8 m from the side walls, 0.8-1.8 m high; each source sits at a
+    distance U(1, 3) m and azimuth U(0, 2 pi) from the centre, up to 0.5 m
+    above or below it, moved inside the room (0.3 m from every wall) if it
+    falls outside;
+  * every RIR of an utterance has ceil(RT60 fs) taps, as above.
 """
 from __future__ import annotations
 
@@ -230,6 +243,44 @@ def grad_like(seed: int, n: int, scale: float = 0.1) -> np.ndarray:
     return rng.normal(0.0, scale, n).astype(np.float32)
 
 
+def room_geometry(seed: int, num_sources, mics: np.ndarray, rt60_range=(0.1, 0.9),
+                  dist_range=(1.0, 3.0)):
+    """Rooms, positions and wall reflection for the image-method RIRs of a batch
+    shaped by `num_sources` (one room per utterance) and the array `mics`
+    ([J, 2] offsets in metres).  Returns (geom float32 [R, 10] with rows
+    (room, source, microphone, r) in the batch's (u, i, j) RIR order,
+    rir_len int32 [R], rt60 [U])."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    num_sources = np.asarray(num_sources, dtype=np.int64)
+    J = int(mics.shape[0])
+    rows, lens, rt60s = [], [], []
+    margin = 0.3
+    for u in range(num_sources.shape[0]):
+        room = np.array([rng.uniform(3.0, 10.0), rng.uniform(3.0, 8.0), rng.uniform(2.5, 5.0)])
+        rt60 = float(rng.uniform(*rt60_range))
+        vol = float(np.prod(room))
+        area = 2.0 * (room[0] * room[1] + room[0] * room[2] + room[1] * room[2])
+        absorb = min(max(0.161 * vol / (area * rt60), 0.01), 0.99)
+        refl = math.sqrt(1.0 - absorb)
+        centre = np.array([rng.uniform(0.8, room[0] - 0.8), rng.uniform(0.8, room[1] - 0.8),
+                           min(rng.uniform(0.8, 1.8), room[2] - margin)])
+        turn = float(rng.uniform(0.0, 2 * np.pi))
+        rot = np.array([[math.cos(turn), -math.sin(turn)], [math.sin(turn), math.cos(turn)]])
+        mic_pos = [centre + np.append(rot @ mics[j], 0.0) for j in range(J)]
+        n_h = int(math.ceil(rt60 * FS))
+        for _ in range(int(num_sources[u])):
+            dist = float(rng.uniform(*dist_range))
+            phi = float(rng.uniform(0.0, 2 * np.pi))
+            src = centre + np.array([dist * math.cos(phi), dist * math.sin(phi), rng.uniform(-0.5, 0.5)])
+            src = np.clip(src, margin, room - margin)
+            for j in range(J):
+                rows.append(np.concatenate([room, src, mic_pos[j], [refl]]))
+                lens.append(n_h)
+        rt60s.append(rt60)
+    return (np.asarray(rows, dtype=np.float32).reshape(-1, 10), np.asarray(lens, dtype=np.int32),
+            np.asarray(rt60s))
+
+
 # ---------------------------------------------------------------------------
 # the five workloads (sizes as stated for the room-simulator benchmarks)
 # ---------------------------------------------------------------------------
@@ -262,6 +313,15 @@ def config_long(seed: int = SEED_BASE + 3, n_utts: int = 32) -> Batch:
     """32 x 30 s, 4 sources, 8-mic circle of radius 5 cm, RT60 U(0.8, 1.2)."""
     return make_batch(seed, [30 * FS] * n_utts, [4] * n_utts,
                       circular_array(8, 0.05), (0.8, 1.2))
+
+
+def config_home_rooms(seed: int = SEED_BASE + 5, n_utts: int = 256):
+    """The Home mix with image-method rooms in place of the drawn RIRs: returns
+    (batch, geom), the batch's rir zero-filled (to be generated from geom)."""
+    b = config_home(seed, n_utts)
+    geom, rir_len, _ = room_geometry(seed + 3000, b.num_sources, linear_pair_array())
+    return dataclasses.replace(b, rir_len=rir_len, rir=np.zeros(int(rir_len.astype(np.int64).sum()),
+                                                                  np.float32)), geom
 
 
 def config_stream(seed: int = SEED_BASE + 4, n_utts: int = 4096) -> Batch:

@@ -75,3 +75,25 @@ def test_null_plan_calls_fail_cleanly(lib):
     assert lib.rsim_filter_mix_backward(None, None, None, None, None, None, None, None) == 1
     assert lib.rsim_plan_scratch_bytes(None) == 0
     lib.rsim_plan_destroy(None)
+
+
+@pytest.mark.parametrize("args", [
+    dict(R=-1),
+    dict(order=-1),
+    dict(order=33),
+    dict(fs=0.0),
+    dict(fs=float("nan")),
+    dict(c0=-343.0),
+    dict(c0=float("inf")),
+    dict(max_len=-1),
+    dict(max_len=(1 << 24) + 1),
+    dict(R=2, null=True),
+])
+def test_image_rirs_rejects_bad_arguments_on_the_host(lib, args):
+    # every case is refused before any CUDA call, so no GPU is needed
+    R = args.get("R", 0)
+    fake = None if args.get("null") else ctypes.c_void_p(16)
+    st = lib.rsim_image_rirs(None, R, fake, fake, args.get("max_len", 100), args.get("order", 8),
+                             args.get("fs", 16000.0), args.get("c0", 343.0), fake, None)
+    assert st == 1
+    assert "rsim_image_rirs" in lib.rsim_last_error().decode()

@@ -53,8 +53,8 @@ IMAGE_MUTANTS = [
     ("image_odd_parity_flipped", "if (a % 2 == 0) {", "if (a % 2 != 0) {"),
     ("image_f64_odd_coordinate", "(double)(a + 1) * len - s", "(double)a * len - s"),
     ("image_g_drops_axis", "im.g = abs(a) + abs(b) + abs(c);", "im.g = abs(a) + abs(b);"),
-    ("image_delay_floor", "im.delay = (int64_t)ceilf(t);", "im.delay = (int64_t)floorf(t);"),
-    ("image_delay_round", "im.delay = (int64_t)ceilf(t);", "im.delay = (int64_t)roundf(t);"),
+    ("image_delay_floor", "(int64_t)ceilf(t)", "(int64_t)floorf(t)"),
+    ("image_delay_round", "(int64_t)ceilf(t)", "(int64_t)roundf(t)"),
     ("image_amp_inverse_square", "/ sqrt(e2) : 0.0;", "/ e2 : 0.0;"),
     ("image_fs_c0_swapped", "float num = d * fs;\n    float t = num / c0;",
      "float num = d * c0;\n    float t = num / fs;"),
