@@ -212,13 +212,14 @@ rsim_status rsim_source_gains_noalloc(void *stream, int32_t num_utts, const int3
  * reached after |a| reflections, so g_v = |a| + |b| + |c|.  d_v is the image's
  * distance to the microphone and r the reflection coefficient of every wall.
  *
- * The delay is an integer decision made in FP32: image coordinate, offset to
- * the microphone, squares, their sum (x + y) + z, square root, d * fs and the
- * division by c0 are each one correctly rounded FP32 operation in that order,
- * so the delay of every image is reproducible bit for bit.  Amplitudes are
- * FP32 (r^g by repeated squaring, then one division by d) and summed in shared
- * memory in no fixed order: taps where images collide can differ in the last
- * bits from call to call.  An image whose delay is n_h or later is dropped.
+ * The delay is an integer decision made in FP32, as ceil(d * rate) with
+ * rate = fs / c0: image coordinate, offset to the microphone, squares, their
+ * sum (x + y) + z, square root, the rate and the product are each one
+ * correctly rounded FP32 operation, so the delay of every image is
+ * reproducible bit for bit.  Amplitudes are FP32 (r^|a| r^|b| r^|c|, each by
+ * repeated squaring, times an approximate 1/d) and summed in shared memory in
+ * no fixed order: taps where images collide can differ in the last bits from
+ * call to call.  An image whose delay is n_h or later is dropped.
  *
  * The output has the packed layout rsim_filter_mix reads: RIR r occupies
  * rir[rir_off[r] .. rir_off[r+1]), so rsim_plan_desc.rir_len[r] must be

@@ -600,11 +600,12 @@ int oracle_forward_ola_batch(int32_t U, int32_t J, const int32_t *n_src, const i
  *  - all walls share one reflection coefficient r, 0 <= r < 1 (r = 0 keeps the
  *    direct path alone, r^0 = 1);
  *  - the delay ceil(d_v fs / c0) is an integer decision and is taken in FP32,
- *    the kernel's precision: image coordinate, offset to the microphone, the
- *    three squares, their sum ((x + y) + z), the square root, d * fs and the
- *    division by c0 are each one correctly rounded FP32 operation, so both
- *    implementations put every image on the same sample.  The amplitude
- *    r^g_v / d_v is FP64, from the same FP32 inputs;
+ *    the kernel's precision, as ceil(d_v * rate) with rate = fs / c0 rounded
+ *    once: image coordinate, offset to the microphone, the three squares,
+ *    their sum ((x + y) + z), the square root, the rate and the product are
+ *    each one correctly rounded FP32 operation, so both implementations put
+ *    every image on the same sample.  The amplitude r^g_v / d_v is FP64, from
+ *    the same FP32 inputs;
  *  - an image whose delay is n_h or later lies outside the RIR and is dropped;
  *  - the source and the microphone lie strictly inside the room, and no image
  *    may sit at distance zero from the microphone (d_v > 0, Eq. 1).
@@ -666,8 +667,8 @@ static image_t image_eval(const float *room, const float *src, const float *mic,
     }
     im.ok = d2 > 0.0f && e2 > 0.0;
     float d = sqrtf(d2);
-    float num = d * fs;
-    float t = num / c0;
+    float rate = fs / c0;
+    float t = d * rate;
     /* a travel time beyond any RIR length (huge rooms overflow to +inf) */
     im.delay = t < 1e18f ? (int64_t)ceilf(t) : INT64_MAX;
     im.g = abs(a) + abs(b) + abs(c);

@@ -1,17 +1,20 @@
 // Image-method room impulse responses (Eq. 1, Sec. 2).
 //
 // A block owns one window of kImgWindow taps of one RIR and accumulates it in
-// shared memory: every thread walks its share of the (2K+1)^3 images, lands
-// each one whose delay falls inside the window with a shared-memory atomic
-// add, and the block then writes the window out whole (zeros included), so
-// the output is written once and never read.  The per-axis squared offsets of
-// the 2K+1 virtual rooms and the powers r^g are tabulated per block, which
-// leaves two additions, a square root, a multiply and a division per image.
-// Work per image is independent of the RIR length, so the window is as large
-// as static shared memory allows (44 KB; five blocks fit on an SM), which
-// covers most RIRs in one pass.
+// shared memory: each thread takes (a, b) pairs of virtual-room indices and
+// walks the 2K+1 rooms c of each pair, landing every image whose delay falls
+// inside the window with a shared-memory atomic add; the block then writes
+// the window out whole (zeros included) with 16-byte stores, so the output is
+// written once and never read.  The per-axis squared offsets and reflection
+// powers of the 2K+1 virtual rooms are tabulated per block and a pair's x + y
+// part is held in registers, which leaves per image one addition, a square
+// root and a multiply for the delay and two multiplies and a reciprocal square
+// root for the amplitude.  Work per image does not depend on the RIR length, so
+// the window is as large as static shared memory allows (44 KB; four blocks of
+// ten warps fit on an SM) and covers most RIRs in one pass.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <string>
 
 #include "rsim.h"
@@ -20,7 +23,7 @@
 namespace rsim {
 namespace {
 
-constexpr int kImgThreads = 256;
+constexpr int kImgThreads = 320;                  // ten warps: the paper's 17 x 17 (a, b) pairs in one round
 constexpr int kImgWindow = 11264;                 // taps per shared-memory window
 constexpr int kImgMaxOrder = 32;
 constexpr int kImgMaxSide = 2 * kImgMaxOrder + 1;  // virtual rooms per axis
@@ -47,13 +50,15 @@ __device__ __forceinline__ bool geom_valid(const rsim_image_geom& g) {
 }
 
 // grid: R * nw blocks; block b takes RIR b / nw and windows b % nw, b % nw + nw, ...
-__global__ void __launch_bounds__(kImgThreads)
+__global__ void __launch_bounds__(kImgThreads, 4)
 k_image_rirs(int32_t R, int32_t nw, const rsim_image_geom* __restrict__ geom,
              const int64_t* __restrict__ off, int32_t K, float fs, float c0, float* __restrict__ rir,
              int32_t* status) {
-    __shared__ float win[kImgWindow];
-    __shared__ float sq[3][kImgMaxSide];             // squared offset per axis and room index
-    __shared__ float pw[3 * kImgMaxOrder + 1];       // r^g
+    // tap n of the window sits at win[n + lead], lead = the output's offset from a
+    // 16-byte boundary, so that 16-byte chunks of win map onto 16-byte chunks of rir
+    __shared__ __align__(16) float win[kImgWindow + 4];
+    // per axis and virtual-room index: (squared offset, r^|index|)
+    __shared__ float2 tab[3][kImgMaxSide];
     const int t = threadIdx.x;
     const int r = (int)(blockIdx.x / (unsigned)nw);
     const int w_first = (int)(blockIdx.x % (unsigned)nw);
@@ -68,7 +73,6 @@ k_image_rirs(int32_t R, int32_t nw, const rsim_image_geom* __restrict__ geom,
     const rsim_image_geom g = geom[r];
     const bool valid = geom_valid(g);
     const int S = 2 * K + 1;
-    const int V = S * S * S;
     if (t < 3 * S) {
         const int k = t / S, ai = t - k * S;
         // axis k picked by selects (a runtime index into g would go through local memory)
@@ -76,53 +80,61 @@ k_image_rirs(int32_t R, int32_t nw, const rsim_image_geom* __restrict__ geom,
         const float s = k == 0 ? g.src[0] : k == 1 ? g.src[1] : g.src[2];
         const float m = k == 0 ? g.mic[0] : k == 1 ? g.mic[1] : g.mic[2];
         const float e = image_offset(ai - K, len, s, m);
-        sq[k][ai] = __fmul_rn(e, e);
-    }
-    if (t <= 3 * K) {
-        // r^t by repeated squaring
+        // r^|a| by repeated squaring
         float p = 1.f, b = g.refl;
-        for (int e = t; e; e >>= 1) {
-            if (e & 1) p *= b;
+        for (int q = abs(ai - K); q; q >>= 1) {
+            if (q & 1) p *= b;
             b *= b;
         }
-        pw[t] = p;
+        tab[k][ai] = make_float2(__fmul_rn(e, e), p);
     }
-    // digits (base S) of the thread's first image and of the stride between its images
-    const int c_first = t % S, b_first = (t / S) % S, a_first = t / (S * S);
-    const int dc = kImgThreads % S, db = (kImgThreads / S) % S, da = kImgThreads / (S * S);
-    const float nh_f = (float)nh;
+    // samples per metre, one rounding (the same value on every side of the comparison)
+    const float rate = __fdiv_rn(fs, c0);
+    const int P = S * S;
+    float4* win4 = reinterpret_cast<float4*>(win);
     for (int64_t w = w_first; w * kImgWindow < nh; w += nw) {
         const int64_t w0 = w * kImgWindow;
         const int wl = (int)(nh - w0 < kImgWindow ? nh - w0 : (int64_t)kImgWindow);
-        const float w0_f = (float)w0, wl_f = (float)wl;
-        for (int n = t; n < wl; n += kImgThreads) win[n] = 0.f;
-        __syncthreads();   // also publishes sq and pw on the first pass
+        const float w0_f = (float)w0;
+        float* dst = rir + o0 + w0;
+        const int lead = (int)((reinterpret_cast<uintptr_t>(dst) >> 2) & 3);
+        for (int q = t; q < (kImgWindow + 4) / 4; q += kImgThreads) win4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();   // also publishes the tables on the first pass
         bool at_mic = false;
-        int ai = a_first, bi = b_first, ci = c_first;
-        for (int v = t; v < V; v += kImgThreads) {
-            const float d2 = __fadd_rn(__fadd_rn(sq[0][ai], sq[1][bi]), sq[2][ci]);
-            if (d2 > 0.f) {
-                const float d = __fsqrt_rn(d2);
-                const float n_f = ceilf(__fdiv_rn(__fmul_rn(d, fs), c0));
-                // n_f and w0 are integers below 2^24 here, so n_f - w0 is exact
-                if (n_f < nh_f && n_f >= w0_f && n_f - w0_f < wl_f) {
-                    const int gv = abs(ai - K) + abs(bi - K) + abs(ci - K);
-                    atomicAdd(&win[(int)(n_f - w0_f)], __fdiv_rn(pw[gv], d));
-                }
-            } else {
-                at_mic = true;
+        for (int p = t; p < P; p += kImgThreads) {
+            const int ai = p / S, bi = p - ai * S;
+            const float2 ta = tab[0][ai], tb = tab[1][bi];
+            const float sab = __fadd_rn(ta.x, tb.x);   // (x^2 + y^2) + z^2, in that order
+            const float rab = ta.y * tb.y;
+#pragma unroll 4
+            for (int ci = 0; ci < S; ++ci) {
+                const float2 tc = tab[2][ci];
+                const float d2 = __fadd_rn(sab, tc.x);
+                at_mic |= !(d2 > 0.f);   // an image at the microphone (the block is zeroed below)
+                // delay = ceil(d * rate); ceil and w0 are integers, exact below 2^24, so the
+                // offset is exact wherever it can land in the window (wl <= nh - w0)
+                const int i = __float2int_rz(ceilf(__fmul_rn(__fsqrt_rn(d2), rate)) - w0_f);
+                if ((unsigned)i < (unsigned)wl) atomicAdd(&win[i + lead], rab * tc.y * rsqrtf(d2));
             }
-            // next image of this thread: v + kImgThreads in base S
-            ci += dc;
-            if (ci >= S) { ci -= S; ++bi; }
-            bi += db;
-            if (bi >= S) { bi -= S; ++ai; }
-            ai += da;
         }
         const bool bad = __syncthreads_or(at_mic) || !valid;
         if (bad && t == 0 && w == w_first && status) atomicOr(status, kImgBadGeom);
-        float* dst = rir + o0 + w0;
-        for (int n = t; n < wl; n += kImgThreads) dst[n] = bad ? 0.f : win[n];
+        // 16-byte chunks of win [4q, 4q + 4) hold taps 4q - lead .. 4q + 3 - lead; the first
+        // and last chunk may be partial
+        float* dsta = dst - lead;   // 16-byte aligned; its first `lead` floats are not ours
+        const int end = lead + wl;
+        for (int q = t; 4 * q < end; q += kImgThreads) {
+            const int lo = 4 * q;
+            float4 v = bad ? make_float4(0.f, 0.f, 0.f, 0.f) : win4[q];
+            if (lo >= lead && lo + 4 <= end) {
+                *reinterpret_cast<float4*>(dsta + lo) = v;
+            } else {
+                const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (lo + k >= lead && lo + k < end) dsta[lo + k] = e[k];
+            }
+        }
         __syncthreads();   // the window is reused by the next pass
     }
 }

@@ -56,8 +56,7 @@ IMAGE_MUTANTS = [
     ("image_delay_floor", "(int64_t)ceilf(t)", "(int64_t)floorf(t)"),
     ("image_delay_round", "(int64_t)ceilf(t)", "(int64_t)roundf(t)"),
     ("image_amp_inverse_square", "/ sqrt(e2) : 0.0;", "/ e2 : 0.0;"),
-    ("image_fs_c0_swapped", "float num = d * fs;\n    float t = num / c0;",
-     "float num = d * c0;\n    float t = num / fs;"),
+    ("image_fs_c0_swapped", "float rate = fs / c0;", "float rate = c0 / fs;"),
     ("image_loop_short", "for (int c = -order; c <= order; ++c) {\n                image_t im",
      "for (int c = -order; c < order; ++c) {\n                image_t im"),
     ("image_drops_last_sample", "if (im.delay < n_h) {", "if (im.delay < n_h - 1) {"),
