@@ -94,6 +94,21 @@ def _bind(lib):
     lib.oracle_image_rir.restype = i64
     lib.oracle_image_rir.argtypes = [P, P, P, ctypes.c_float, i32, ctypes.c_float, ctypes.c_float,
                                      i64, P]
+    lib.oracle_hz_to_mel.restype = f64
+    lib.oracle_hz_to_mel.argtypes = [f64]
+    lib.oracle_mel_to_hz.restype = f64
+    lib.oracle_mel_to_hz.argtypes = [f64]
+    lib.oracle_mel_filters.restype = None
+    lib.oracle_mel_filters.argtypes = [i32, f64, i32, f64, f64, P]
+    lib.oracle_frame_power.restype = None
+    lib.oracle_frame_power.argtypes = [P, i32, P]
+    lib.oracle_log_mel_rows.restype = i64
+    lib.oracle_log_mel_rows.argtypes = [i64, i32, i32, i32, i32]
+    lib.oracle_log_mel.restype = i64
+    lib.oracle_log_mel.argtypes = [P, i64, i32, i32, f64, i32, f64, f64, f64, i32, i32, P]
+    lib.oracle_log_mel_batch.restype = None
+    lib.oracle_log_mel_batch.argtypes = [i32, i32, P, P, i32, i32, i32, f64, i32, f64, f64, f64, i32, i32, P, P,
+                                         ctypes.c_int]
     lib.oracle_image_rirs.restype = None
     lib.oracle_image_rirs.argtypes = [i64, P, P, i32, ctypes.c_float, ctypes.c_float, P, P,
                                       ctypes.c_int]
@@ -351,6 +366,67 @@ def image_rirs(geom, rir_len, order=8, fs=16000.0, c0=343.0, nthreads=0, lib=Non
     (lib or _load()).oracle_image_rirs(R, _p(geom), _p(off), int(order), float(fs), float(c0), _p(h),
                                        _p(valid), nthreads)
     return h, valid.astype(bool)
+
+
+# ---- Sec. 4: log-Mel front end ------------------------------------------------
+# the paper's features: 32 ms windows every 10 ms at 16 kHz, 128 Mel bands over
+# 125-7500 Hz, four frames stacked, every third stacked frame kept
+MEL_DEFAULTS = dict(n_fft=512, hop=160, fs=16000.0, n_mels=128, f_lo=125.0, f_hi=7500.0, floor=1e-6,
+                    stack=4, stride=3)
+
+
+def hz_to_mel(f, lib=None):
+    return (lib or _load()).oracle_hz_to_mel(float(f))
+
+
+def mel_to_hz(m, lib=None):
+    return (lib or _load()).oracle_mel_to_hz(float(m))
+
+
+def mel_filters(n_fft=512, fs=16000.0, n_mels=128, f_lo=125.0, f_hi=7500.0, lib=None):
+    """Triangular Mel filter weights [n_mels, n_fft/2 + 1]."""
+    W = np.zeros((n_mels, n_fft // 2 + 1))
+    (lib or _load()).oracle_mel_filters(int(n_fft), float(fs), int(n_mels), float(f_lo), float(f_hi), _p(W))
+    return W
+
+
+def frame_power(x, n_fft=512, lib=None):
+    """|X[k]|^2, k = 0 .. n_fft/2, of one Hann-windowed frame of n_fft samples."""
+    x = _f64(x)
+    assert x.shape[0] >= n_fft
+    P = np.zeros(n_fft // 2 + 1)
+    (lib or _load()).oracle_frame_power(_p(x), int(n_fft), _p(P))
+    return P
+
+
+def log_mel_rows(n, n_fft=512, hop=160, stack=4, stride=3, lib=None):
+    return int((lib or _load()).oracle_log_mel_rows(int(n), int(n_fft), int(hop), int(stack), int(stride)))
+
+
+def log_mel(y, lib=None, **kw):
+    """Stacked log-Mel features of one channel: [rows, stack * n_mels]."""
+    p = dict(MEL_DEFAULTS, **kw)
+    y = _f64(y)
+    rows = log_mel_rows(y.shape[0], p["n_fft"], p["hop"], p["stack"], p["stride"], lib)
+    out = np.zeros((rows, p["stack"] * p["n_mels"]))
+    (lib or _load()).oracle_log_mel(_p(y), y.shape[0], p["n_fft"], p["hop"], p["fs"], p["n_mels"], p["f_lo"],
+                                    p["f_hi"], p["floor"], p["stack"], p["stride"], _p(out))
+    return out
+
+
+def log_mel_batch(y, num_out, num_mics, channel=0, nthreads=0, lib=None, **kw):
+    """Features of channel `channel` of every utterance of a mixed output laid
+    out [sum_u J * Ny_u].  Returns (features [rows, stack * n_mels], row offsets [U + 1])."""
+    p = dict(MEL_DEFAULTS, **kw)
+    lib = lib or _load()
+    ny = _i64(num_out)
+    rows = np.array([log_mel_rows(n, p["n_fft"], p["hop"], p["stack"], p["stride"], lib) for n in ny], np.int64)
+    off = _i64(np.concatenate([[0], np.cumsum(rows)]))
+    out = np.zeros((int(off[-1]), p["stack"] * p["n_mels"]))
+    lib.oracle_log_mel_batch(ny.shape[0], int(num_mics), _p(ny), _p(_f64(y)), int(channel), p["n_fft"], p["hop"],
+                             p["fs"], p["n_mels"], p["f_lo"], p["f_hi"], p["floor"], p["stack"], p["stride"],
+                             _p(off), _p(out), nthreads)
+    return out, off
 
 
 def eta_is_none(eta_db) -> bool:

@@ -23,7 +23,9 @@
  *   Eq. 1  the image-method room impulse response (Sec. 2), h[n] as the sum
  *          of r^g_v / d_v delta[n - ceil(d_v fs / c0)] over the images of
  *          the source in (2K+1)^3 virtual rooms (its readings are listed
- *          above oracle_image_list).
+ *          above oracle_image_list)
+ *   Sec. 4 the log-Mel front end applied after mixing (its readings are
+ *          listed above oracle_hz_to_mel).
  *
  * Readings taken where the paper is silent or garbled:
  *   - output length: n in [0, Nx) (Eq. 2 gives no range);
@@ -739,4 +741,117 @@ void oracle_image_rirs(int64_t R, const float *geom, const int64_t *off, int32_t
         valid[r] = oracle_image_rir(gr, gr + 3, gr + 6, gr[9], order, fs, c0, off[r + 1] - off[r],
                                     h + off[r]) >= 0;
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 4: the log-Mel front end after mixing                                */
+/* ------------------------------------------------------------------------ */
+/*
+ * The paper's features: a single channel, 128 log-Mel energies from a 32 ms
+ * window every 10 ms, a Mel filterbank from 125 Hz to 7500 Hz, four frames
+ * stacked and the stacked frames kept every third.  Readings where it is
+ * silent:
+ *  - frame t covers samples [t hop, t hop + n_fft) of the channel, with no
+ *    padding: T = (n - n_fft) / hop + 1 frames (none if n < n_fft);
+ *  - periodic Hann window w[n] = 1/2 - 1/2 cos(2 pi n / n_fft);
+ *  - power spectrum |X[k]|^2 of the windowed frame, k = 0 .. n_fft/2;
+ *  - HTK Mel scale m(f) = 2595 log10(1 + f/700); n_mels + 2 points equally
+ *    spaced in m from m(f_lo) to m(f_hi); filter j is the triangle rising from
+ *    point j to point j+1 and falling to point j+2 (peak 1, no area
+ *    normalisation), sampled at the bin frequencies k fs / n_fft;
+ *  - feature = ln(E + floor) of each filter's energy E;
+ *  - stacked row r holds frames stride r .. stride r + stack - 1 side by side
+ *    (frame-major), for every r whose frames all exist.
+ */
+
+double oracle_hz_to_mel(double f) { return 2595.0 * log10(1.0 + f / 700.0); }
+
+double oracle_mel_to_hz(double m) { return 700.0 * (pow(10.0, m / 2595.0) - 1.0); }
+
+/* weights W[j * (n_fft/2 + 1) + k] of the triangular Mel filters */
+void oracle_mel_filters(int32_t n_fft, double fs, int32_t n_mels, double f_lo, double f_hi, double *W)
+{
+    const int32_t nb = n_fft / 2 + 1;
+    const double m_lo = oracle_hz_to_mel(f_lo), m_hi = oracle_hz_to_mel(f_hi);
+    for (int32_t j = 0; j < n_mels; ++j) {
+        double edge[3];
+        for (int e = 0; e < 3; ++e)
+            edge[e] = oracle_mel_to_hz(m_lo + (m_hi - m_lo) * (double)(j + e) / (double)(n_mels + 1));
+        for (int32_t k = 0; k < nb; ++k) {
+            double f = (double)k * fs / (double)n_fft, w = 0.0;
+            if (f > edge[0] && f < edge[2])
+                w = (f <= edge[1]) ? (f - edge[0]) / (edge[1] - edge[0]) : (edge[2] - f) / (edge[2] - edge[1]);
+            W[(int64_t)j * nb + k] = w;
+        }
+    }
+}
+
+/* power spectrum |X[k]|^2, k = 0 .. n_fft/2, of the Hann-windowed frame */
+void oracle_frame_power(const double *x, int32_t n_fft, double *P)
+{
+    double *re = (double *)malloc(sizeof(double) * n_fft), *im = (double *)malloc(sizeof(double) * n_fft);
+    for (int32_t n = 0; n < n_fft; ++n) {
+        re[n] = x[n] * (0.5 - 0.5 * cos(2.0 * M_PI * (double)n / (double)n_fft));
+        im[n] = 0.0;
+    }
+    fft_radix2(re, im, n_fft, -1);
+    for (int32_t k = 0; k <= n_fft / 2; ++k) P[k] = re[k] * re[k] + im[k] * im[k];
+    free(re);
+    free(im);
+}
+
+/* rows of stacked features from n samples */
+int64_t oracle_log_mel_rows(int64_t n, int32_t n_fft, int32_t hop, int32_t stack, int32_t stride)
+{
+    int64_t T = n >= n_fft ? (n - n_fft) / hop + 1 : 0;
+    return T >= stack ? (T - stack) / stride + 1 : 0;
+}
+
+/* Log-Mel features of one channel of n samples: out[r * stack * n_mels + s * n_mels + j].
+ * Returns the number of rows. */
+int64_t oracle_log_mel(const double *y, int64_t n, int32_t n_fft, int32_t hop, double fs, int32_t n_mels,
+                       double f_lo, double f_hi, double floor_, int32_t stack, int32_t stride, double *out)
+{
+    const int32_t nb = n_fft / 2 + 1;
+    const int64_t rows = oracle_log_mel_rows(n, n_fft, hop, stack, stride);
+    if (rows == 0) return 0;
+    const int64_t frames = (rows - 1) * stride + stack;
+    double *W = (double *)malloc(sizeof(double) * n_mels * nb);
+    double *P = (double *)malloc(sizeof(double) * nb);
+    double *F = (double *)malloc(sizeof(double) * frames * n_mels);
+    oracle_mel_filters(n_fft, fs, n_mels, f_lo, f_hi, W);
+    for (int64_t t = 0; t < frames; ++t) {
+        oracle_frame_power(y + t * hop, n_fft, P);
+        for (int32_t j = 0; j < n_mels; ++j) {
+            double e = 0.0;
+            for (int32_t k = 0; k < nb; ++k) e += W[(int64_t)j * nb + k] * P[k];
+            F[t * n_mels + j] = log(e + floor_);
+        }
+    }
+    for (int64_t r = 0; r < rows; ++r)
+        for (int32_t s = 0; s < stack; ++s)
+            for (int32_t j = 0; j < n_mels; ++j)
+                out[(r * stack + s) * n_mels + j] = F[(r * stride + s) * n_mels + j];
+    free(W);
+    free(P);
+    free(F);
+    return rows;
+}
+
+/* Batch form over utterances: channel `ch` of y laid out [sum_u J * n_y[u]]
+ * (utterance, microphone, sample); rows of utterance u start at row_off[u]
+ * (the prefix sum of oracle_log_mel_rows).  OpenMP across utterances. */
+void oracle_log_mel_batch(int32_t U, int32_t J, const int64_t *n_y, const double *y, int32_t ch, int32_t n_fft,
+                          int32_t hop, double fs, int32_t n_mels, double f_lo, double f_hi, double floor_,
+                          int32_t stack, int32_t stride, const int64_t *row_off, double *out, int nthreads)
+{
+    set_threads(nthreads);
+    int64_t *yoff = (int64_t *)malloc(sizeof(int64_t) * (U + 1));
+    yoff[0] = 0;
+    for (int32_t u = 0; u < U; ++u) yoff[u + 1] = yoff[u] + (int64_t)J * n_y[u];
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t u = 0; u < U; ++u)
+        oracle_log_mel(y + yoff[u] + (int64_t)ch * n_y[u], n_y[u], n_fft, hop, fs, n_mels, f_lo, f_hi, floor_,
+                       stack, stride, out + row_off[u] * (int64_t)stack * n_mels);
+    free(yoff);
 }

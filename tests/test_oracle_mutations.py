@@ -63,8 +63,24 @@ IMAGE_MUTANTS = [
     ("image_d2_misses_z", "d2 = (k == 0) ? sq : d2 + sq;", "d2 = (k == 0) ? sq : (k == 1 ? d2 + sq : d2);"),
 ]
 
+# mistakes in the log-Mel front end, run against its own pin file
+MEL_MUTANTS = [
+    ("mel_symmetric_window", "cos(2.0 * M_PI * (double)n / (double)n_fft)",
+     "cos(2.0 * M_PI * (double)n / (double)(n_fft - 1))"),
+    ("mel_magnitude_not_power", "P[k] = re[k] * re[k] + im[k] * im[k];",
+     "P[k] = sqrt(re[k] * re[k] + im[k] * im[k]);"),
+    ("mel_scale_break_frequency", "2595.0 * log10(1.0 + f / 700.0)", "2595.0 * log10(1.0 + f / 1000.0)"),
+    ("mel_edges_short_of_f_hi", "(double)(j + e) / (double)(n_mels + 1)", "(double)(j + e) / (double)(n_mels + 2)"),
+    ("mel_falling_slope", "(edge[2] - f) / (edge[2] - edge[1])", "(edge[2] - f) / (edge[2] - edge[0])"),
+    ("mel_floor_outside_log", "log(e + floor_)", "log(e) + floor_"),
+    ("mel_stack_stride_confused", "F[(r * stride + s) * n_mels + j]", "F[(r * stack + s) * n_mels + j]"),
+    ("mel_frame_start_shifted", "oracle_frame_power(y + t * hop, n_fft, P);",
+     "oracle_frame_power(y + t * hop + 1, n_fft, P);"),
+]
+
 CASES = [(*m, "test_oracle_pins.py") for m in MUTANTS] + \
-    [(*m, "test_oracle_image_pins.py") for m in IMAGE_MUTANTS]
+    [(*m, "test_oracle_image_pins.py") for m in IMAGE_MUTANTS] + \
+    [(*m, "test_oracle_mel_pins.py") for m in MEL_MUTANTS]
 
 
 @pytest.mark.parametrize("name,orig,planted,pins", CASES, ids=[c[0] for c in CASES])
