@@ -827,6 +827,80 @@ def run_rooms(args):
     return 0
 
 
+def mel_work(num_out, rows_total, frames_total, n_mels=128, stack=4):
+    """Algorithmic work of rsim_plan_log_mel: the channel read once (4 bytes a
+    sample) and the features written once; per frame the window (512
+    multiplies), one real 512-point transform (2.5 N log2 N), the power
+    spectrum (3 per bin) and the filter sums (2 per weighted bin, about two
+    filters per bin)."""
+    nbytes = 4.0 * float(np.sum(num_out)) + 4.0 * rows_total * stack * n_mels
+    flops = frames_total * (512 + 2.5 * 512 * 9 + 3 * 257 + 2 * 2 * 257)
+    return nbytes, flops
+
+
+def run_mel(args):
+    """Log-Mel front end (Sec. 4: 128 filters, 32 ms / 10 ms, 125-7500 Hz, four
+    frames stacked, every third kept) on microphone 0 of the home-256 mix."""
+    import torch
+    from paper_1712_03439_gb300 import Plan, build, synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    build.build()
+    b = synth.config_home()
+    plan = Plan.for_batch(b, eta_db=ETA_DB, gain_mode=0, device=0)
+    x, rir, snr = (torch.from_numpy(a).to(dev) for a in (b.x, b.rir, b.snr_db))
+    gains, y = torch.empty(plan.S, device=dev), torch.empty(plan.y_size, device=dev)
+    plan.filter_mix(x, rir, gains, y, snr_db=snr)
+    rows, total = plan.log_mel_rows()
+    feats = torch.empty((total, 512), device=dev)
+    frames = int(np.sum(np.where(rows > 0, (rows - 1) * 3 + 4, 0)))
+    flush = torch.empty(64 << 20, device=dev)
+    st = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        plan.log_mel(y, feats)
+    torch.cuda.synchronize()
+    n = max(args.steps, 20)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    clock = ClockSampler(0)
+    for e0, e1 in evs:
+        flush.fill_(1.0)
+        e0.record(st)
+        plan.log_mel(y, feats)
+        e1.record(st)
+    torch.cuda.synchronize()
+    clocks = clock.stop()
+    ms = float(np.mean([a.elapsed_time(z) for a, z in evs]))
+    hbm, p_fp32, peak_kind = _peaks_fp32(torch, dev)
+    nbytes, flops = mel_work(plan.num_out, total, frames)
+    audio_s = b.audio_seconds()
+    line = {"metric": "log-Mel features of the mixed output, audio s/sec (1 channel) at 16 kHz, 1xGB300",
+            "value": audio_s / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": n, "warmup": max(args.warmup, 3),
+            "ms_per_step": ms, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic: microphone 0 of the home-256 mix (filter_mix output)",
+            "config": {"workload": "home-256 mixed output, microphone 0: 128 log-Mel filters over 125-7500 Hz, "
+                                   "512-sample Hann frames every 160 samples, 4 frames stacked, every third kept",
+                       "audio_seconds": audio_s, "frames": frames, "rows": total,
+                       "l2": "each timed launch follows a 256 MB L2 flush"},
+            "roofline": roofline_entry(flops, nbytes, ms, p_fp32, hbm, peak_kind, _traffic_for("k_log_mel")),
+            "clocks": clocks}
+    if not args.no_cpu_baseline:
+        import oracle
+        sub = list(range(0, b.num_utts, 64))[:4]
+        yo, yh = b.y_offsets(), y.cpu().numpy()
+        t0 = time.perf_counter()
+        sec = 0.0
+        for u in sub:
+            nu = int(b.num_samples[u])
+            oracle.log_mel(yh[yo[u]:yo[u] + nu])
+            sec += nu / synth.FS
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": sec / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"utterances {sub} ({sec:.1f} audio s), one thread"}
+    plan.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def oracle_free_lengths(b, eta):
     """Kept lengths (Eq. 7-9) computed in numpy for the report when the library
     rejects the batch (FP64 compare, as the kernels do)."""
@@ -854,9 +928,10 @@ def main():
     ap.add_argument("--only-step", action="store_true",
                     help="time only the K steps (no forward-only, end-to-end, plain or CPU legs); "
                          "for profiler runs")
-    ap.add_argument("--config", choices=["home", "stream", "long", "rooms"], default="home",
-                    help="home: the headline line; stream / long / rooms: reports on the streaming, "
-                         "the long reverberant and the image-method-room workloads")
+    ap.add_argument("--config", choices=["home", "stream", "long", "rooms", "mel"], default="home",
+                    help="home: the headline line; stream / long / rooms / mel: reports on the streaming, "
+                         "the long reverberant and the image-method-room workloads and on the log-Mel "
+                         "front end")
     ap.add_argument("--stream-utts", type=int, default=4096)
     ap.add_argument("--budget-gb", type=float, default=2.0)
     ap.add_argument("--long-utts", type=int, default=32)
@@ -870,6 +945,8 @@ def main():
         return run_long(args)
     if args.config == "rooms":
         return run_rooms(args)
+    if args.config == "mel":
+        return run_mel(args)
     return run_ours(args)
 
 

@@ -200,6 +200,51 @@ rsim_status rsim_source_gains_noalloc(void *stream, int32_t num_utts, const int3
                                       const int64_t *num_samples, const float *x, const float *snr_db,
                                       float *gains);
 
+/* ---- log-Mel front end (Sec. 4) ---------------------------------------------
+ *
+ * The features the paper trains on, from one microphone of the mixed output:
+ * frames of 512 samples (32 ms at 16 kHz) every `hop` samples (160: 10 ms),
+ * frame t covering [t hop, t hop + 512) of the utterance's N_y samples with no
+ * padding (T = (N_y - 512) / hop + 1 frames, none if N_y < 512); a periodic
+ * Hann window 1/2 - 1/2 cos(2 pi n / 512); the power spectrum |X[k]|^2,
+ * k = 0 .. 256; n_mels triangular filters whose n_mels + 2 edges are equally
+ * spaced on the HTK Mel scale m(f) = 2595 log10(1 + f / 700) from f_lo to
+ * f_hi (filter j rises from edge j to edge j+1 and falls to edge j+2, peak 1);
+ * v = ln(E + log_floor) per filter; then `stack` consecutive frames side by
+ * side per row, one row every `stride` frames (the paper: 128 filters over
+ * 125-7500 Hz, 4 frames stacked, every third kept).  Row r of an utterance
+ * holds frames stride r .. stride r + stack - 1 (frame-major, n_mels values
+ * each), for every r whose frames all exist: R = (T - stack) / stride + 1
+ * rows (none if T < stack).  feats is [sum_u R_u, stack * n_mels] FP32,
+ * utterances in order.  The filter edges are computed in FP64 on the host and
+ * rounded once; everything else runs in FP32 on the device.
+ */
+typedef struct {
+    int32_t channel;    /* microphone j, 0 <= j < J */
+    int32_t hop;        /* samples between frames, >= 1 */
+    float fs;           /* sampling rate in Hz, > 0 */
+    int32_t n_mels;     /* filters, 1 .. 128 */
+    float f_lo, f_hi;   /* Hz, 0 <= f_lo < f_hi <= fs / 2 */
+    float log_floor;    /* added to each filter energy before the log, > 0 */
+    int32_t stack;      /* frames per row, >= 1 */
+    int32_t stride;     /* frames between rows, >= 1 */
+} rsim_mel_desc;
+
+/* Rows per utterance (rows_per_utt [U] host, may be NULL) and their total
+ * (may be NULL) of the features rsim_plan_log_mel writes for this plan's
+ * output lengths.  Host only; RSIM_E_INVALID for a bad description. */
+rsim_status rsim_plan_log_mel_rows(rsim_plan_t plan, const rsim_mel_desc *desc, int64_t *rows_per_utt,
+                                   int64_t *total_rows);
+
+/* Writes the features of desc->channel of y (laid out as rsim_filter_mix writes
+ * it for this plan, device, read only) into feats (device, caller-owned, the
+ * total rows times stack * n_mels floats; may be NULL when there are no rows).
+ * Uses the plan's scratch for the row
+ * offsets, so calls on one plan must not overlap.  RSIM_E_UNSUPPORTED for more
+ * than 65535 utterances.  Asynchronous; no allocation. */
+rsim_status rsim_plan_log_mel(rsim_plan_t plan, void *stream, const float *y, const rsim_mel_desc *desc,
+                              float *feats);
+
 /* ---- image-method room impulse responses (Eq. 1, Sec. 2) -------------------
  *
  * One RIR per (source, microphone) pair of a cuboid room by the image method:

@@ -19,7 +19,7 @@ STATUS_NAMES = {0: "RSIM_OK", 1: "RSIM_E_INVALID", 2: "RSIM_E_UNSUPPORTED", 3: "
 EXPORTED = ["rsim_plan", "rsim_filter_mix", "rsim_filter_mix_backward", "rsim_plan_sync_status",
             "rsim_plan_query", "rsim_plan_set_timing", "rsim_plan_stage_times",
             "rsim_plan_scratch_bytes", "rsim_plan_destroy", "rsim_source_gains_noalloc",
-            "rsim_image_rirs", "rsim_last_error"]
+            "rsim_image_rirs", "rsim_plan_log_mel", "rsim_plan_log_mel_rows", "rsim_last_error"]
 STAGES = ["truncate", "power", "plan", "spectrum", "forward", "fixup", "backward", "finalize"]
 
 
@@ -44,6 +44,20 @@ class PlanDesc(ctypes.Structure):
         ("fft_cost", ctypes.c_void_p),
         ("disable_graphs", ctypes.c_int32),
         ("output_mode", ctypes.c_int32),
+    ]
+
+
+class MelDesc(ctypes.Structure):
+    _fields_ = [
+        ("channel", ctypes.c_int32),
+        ("hop", ctypes.c_int32),
+        ("fs", ctypes.c_float),
+        ("n_mels", ctypes.c_int32),
+        ("f_lo", ctypes.c_float),
+        ("f_hi", ctypes.c_float),
+        ("log_floor", ctypes.c_float),
+        ("stack", ctypes.c_int32),
+        ("stride", ctypes.c_int32),
     ]
 
 
@@ -82,6 +96,10 @@ def load(path: str | None = None):
     lib.rsim_source_gains_noalloc.argtypes = [P, ctypes.c_int32, P, P, P, P, P]
     lib.rsim_image_rirs.restype = ctypes.c_int
     lib.rsim_image_rirs.argtypes = [P, i32, P, P, i64, i32, ctypes.c_float, ctypes.c_float, P, P]
+    lib.rsim_plan_log_mel.restype = ctypes.c_int
+    lib.rsim_plan_log_mel.argtypes = [P, P, P, ctypes.POINTER(MelDesc), P]
+    lib.rsim_plan_log_mel_rows.restype = ctypes.c_int
+    lib.rsim_plan_log_mel_rows.argtypes = [P, ctypes.POINTER(MelDesc), P, P]
     lib.rsim_last_error.restype = ctypes.c_char_p
     lib.rsim_last_error.argtypes = []
     if path is None:

@@ -155,6 +155,39 @@ class Plan:
             self._handle, ctypes.c_void_p(ms.ctypes.data), ctypes.c_void_p(calls.ctypes.data)))
         return {k: (float(ms[i]), int(calls[i])) for i, k in enumerate(_lib.STAGES)}
 
+    # ------------------------------------------------------------------
+    @staticmethod
+    def mel_desc(channel=0, hop=160, fs=16000.0, n_mels=128, f_lo=125.0, f_hi=7500.0, log_floor=1e-6,
+                 stack=4, stride=3):
+        """The log-Mel description (defaults: the paper's features at 16 kHz)."""
+        return _lib.MelDesc(channel=int(channel), hop=int(hop), fs=float(fs), n_mels=int(n_mels),
+                            f_lo=float(f_lo), f_hi=float(f_hi), log_floor=float(log_floor), stack=int(stack),
+                            stride=int(stride))
+
+    def log_mel_rows(self, **kw):
+        """(rows per utterance [U], total rows) of log_mel's output."""
+        d = self.mel_desc(**kw)
+        rows = np.zeros(self.U, np.int64)
+        total = ctypes.c_int64()
+        _lib.check(self._lib, self._lib.rsim_plan_log_mel_rows(self._handle, ctypes.byref(d),
+                                                               ctypes.c_void_p(rows.ctypes.data),
+                                                               ctypes.byref(total)))
+        return rows, int(total.value)
+
+    def log_mel(self, y, feats=None, stream=None, **kw):
+        """rsim_plan_log_mel: stacked log-Mel features of one microphone of y.
+        Returns feats [rows, stack * n_mels] (allocated if not given)."""
+        d = self.mel_desc(**kw)
+        _want(y, self.y_size, torch.float32, "y")
+        _, total = self.log_mel_rows(**kw)
+        width = d.stack * d.n_mels
+        if feats is None:
+            feats = torch.empty((total, width), dtype=torch.float32, device=y.device)
+        _want(feats.view(-1), total * width, torch.float32, "feats")
+        _lib.check(self._lib, self._lib.rsim_plan_log_mel(self._handle, _stream(stream), _ptr(y), ctypes.byref(d),
+                                                          _ptr(feats)))
+        return feats
+
     @property
     def scratch_bytes(self) -> int:
         return int(self._lib.rsim_plan_scratch_bytes(self._handle))

@@ -14,7 +14,7 @@ OBJ_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(PKG, "librsim.so")
 
 SOURCES = ["rsim_prep.cu", "rsim_forward.cu", "rsim_backward.cu", "rsim_api.cu", "rsim_noalloc.cu",
-           "rsim_image.cu"]
+           "rsim_image.cu", "rsim_mel.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", f"-I{INCLUDE}", f"-I{CSRC}"]

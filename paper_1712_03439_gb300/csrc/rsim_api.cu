@@ -5,6 +5,7 @@
 #include "rsim.h"
 #include "rsim_fft.cuh"
 #include "rsim_internal.cuh"
+#include "rsim_mel.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -135,6 +136,10 @@ struct rsim_plan_s {
     cudaStream_t aux = nullptr;     // side stream of the forward's first stage
     cudaEvent_t ev_aux = nullptr;
     GraphCache gfwd, gbwd;
+    // output samples per microphone of each utterance (host copy) and the row
+    // offsets of the log-Mel features (device, written per call)
+    std::vector<int64_t> h_ny;
+    int64_t* mel_row_off = nullptr;
 };
 
 namespace {
@@ -317,7 +322,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     void *p_srcutt, *p_rirutt;
     void *p_nsrc, *p_nx, *p_ny, *p_src0, *p_rir0, *p_seg0, *p_segutt, *p_xoff, *p_yoff, *p_roff, *p_rlen,
         *p_dhpoff, *p_tuning, *p_L, *p_logN, *p_hop, *p_lmax, *p_nblk, *p_pow, *p_err, *p_list,
-        *p_count, *p_next, *p_Hc, *p_tails, *p_dhp, *p_dap;
+        *p_count, *p_next, *p_Hc, *p_tails, *p_dhp, *p_dap, *p_melrow;
     void* p_tw[2 * kNumBuckets] = {};
     const int64_t cap = std::max<int64_t>(std::max<int64_t>(nbseg * kMaxSources, nseg), R);
     // launch shapes (persistent grids) decide the per-CTA backward scratch
@@ -368,6 +373,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     pieces.push_back({&p_tails, sizeof(float) * nseg * J * 2 * MMAX});
     pieces.push_back({&p_dhp, sizeof(float) * std::max<int64_t>(dhp_total, 1)});
     pieces.push_back({&p_dap, sizeof(float) * std::max<int64_t>(nbseg, 1) * kMaxSources});
+    pieces.push_back({&p_melrow, sizeof(int64_t) * (U + 1)});
     std::vector<std::vector<float2>> tws(2 * kNumBuckets);
     for (int m = kMinLog; m <= kMaxLog; ++m) {
         if (!((mask >> m) & 1)) continue;
@@ -460,6 +466,8 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     p->Q.list = (int32_t*)p_list; p->Q.count = (int32_t*)p_count; p->Q.next = (int32_t*)p_next;
     p->Q.cap = (int32_t)cap;
     p->Hc = (float2*)p_Hc; p->tails = (float*)p_tails; p->dhp = (float*)p_dhp; p->dap = (float*)p_dap;
+    p->mel_row_off = (int64_t*)p_melrow;
+    p->h_ny = nyv;
     for (int b = 0; b < kNumBuckets; ++b) {
         p->tw[b] = Twiddles{(const float2*)p_tw[2 * b], (const float2*)p_tw[2 * b + 1]};
         p->grid_spec[b] = grid_spec[b];
@@ -717,5 +725,90 @@ extern "C" rsim_status rsim_plan_stage_times(rsim_plan_t p, double* ms, int32_t*
         if (calls) calls[s] = n;
         p->timer.count[s] = 0;
     }
+    return RSIM_OK;
+}
+
+// ---- log-Mel front end -------------------------------------------------------
+namespace {
+
+rsim_status mel_params(rsim_plan_t p, const rsim_mel_desc* d, MelParams* out) {
+    if (!p || !d) return fail(RSIM_E_INVALID, "rsim_plan_log_mel: null plan or description");
+    const bool ok = d->channel >= 0 && d->channel < p->B.J && d->hop >= 1 && d->n_mels >= 1 &&
+                    d->n_mels <= kMelMaxMels && std::isfinite(d->fs) && d->fs > 0.f && std::isfinite(d->f_lo) &&
+                    std::isfinite(d->f_hi) && d->f_lo >= 0.f && d->f_lo < d->f_hi && d->f_hi <= 0.5f * d->fs &&
+                    std::isfinite(d->log_floor) && d->log_floor > 0.f && d->stack >= 1 && d->stride >= 1;
+    if (!ok)
+        return fail(RSIM_E_INVALID, "rsim_plan_log_mel: need 0 <= channel < J, hop >= 1, 1 <= n_mels <= 128, "
+                                    "0 <= f_lo < f_hi <= fs / 2, log_floor > 0, stack >= 1, stride >= 1");
+    MelParams& m = *out;
+    m = MelParams{};
+    m.hop = d->hop; m.n_mels = d->n_mels; m.stack = d->stack; m.stride = d->stride;
+    m.floor_ = d->log_floor;
+    // triangles between n_mels + 2 edges equally spaced on the HTK Mel scale, sampled at the
+    // bin frequencies k fs / kMelFft, in FP64; only the nonzero weights are kept
+    const auto mel = [](double f) { return 2595.0 * std::log10(1.0 + f / 700.0); };
+    const auto hz = [](double v) { return 700.0 * (std::pow(10.0, v / 2595.0) - 1.0); };
+    const double m_lo = mel(d->f_lo), m_hi = mel(d->f_hi);
+    int nw = 0;
+    for (int j = 0; j < d->n_mels; ++j) {
+        double e[3];
+        for (int q = 0; q < 3; ++q) e[q] = hz(m_lo + (m_hi - m_lo) * (double)(j + q) / (double)(d->n_mels + 1));
+        m.off[j] = (int16_t)nw;
+        m.first[j] = 0;
+        bool started = false;
+        for (int k = 0; k <= kMelFft / 2; ++k) {
+            const double f = (double)k * (double)d->fs / kMelFft;
+            if (!(f > e[0] && f < e[2])) continue;
+            const double w = f <= e[1] ? (f - e[0]) / (e[1] - e[0]) : (e[2] - f) / (e[2] - e[1]);
+            if (!started) {
+                m.first[j] = (int16_t)k;
+                started = true;
+            }
+            if (nw >= kMelMaxWeights) return fail(RSIM_E_INVALID, "rsim_plan_log_mel: filterbank too dense");
+            m.w[nw++] = (float)w;
+        }
+    }
+    m.off[d->n_mels] = (int16_t)nw;
+    return RSIM_OK;
+}
+
+}  // namespace
+
+extern "C" rsim_status rsim_plan_log_mel_rows(rsim_plan_t p, const rsim_mel_desc* d, int64_t* rows_per_utt,
+                                              int64_t* total_rows) {
+    MelParams mp;
+    const rsim_status st = mel_params(p, d, &mp);
+    if (st != RSIM_OK) return st;
+    int64_t total = 0;
+    for (size_t u = 0; u < p->h_ny.size(); ++u) {
+        int64_t r, f;
+        mel_shape(p->h_ny[u], mp, &r, &f);
+        if (rows_per_utt) rows_per_utt[u] = r;
+        total += r;
+    }
+    if (total_rows) *total_rows = total;
+    return RSIM_OK;
+}
+
+extern "C" rsim_status rsim_plan_log_mel(rsim_plan_t p, void* stream, const float* y, const rsim_mel_desc* d,
+                                         float* feats) {
+    MelParams mp;
+    rsim_status st = mel_params(p, d, &mp);
+    if (st != RSIM_OK) return st;
+    int64_t frames_max = 0;
+    for (int64_t n : p->h_ny) {
+        int64_t r, f;
+        mel_shape(n, mp, &r, &f);
+        frames_max = std::max(frames_max, f);
+    }
+    // with no rows to write, feats may be null (an empty buffer)
+    if (!y || (!feats && frames_max > 0)) return fail(RSIM_E_INVALID, "rsim_plan_log_mel: null y or feats");
+    if (frames_max > 0x7fffffff || p->B.U > 65535)
+        return fail(RSIM_E_UNSUPPORTED, "rsim_plan_log_mel: more than 65535 utterances or too many frames");
+    DeviceGuard guard(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_log_mel(p->B.U, frames_max, y, p->B.yoff, p->B.n_y, d->channel, mp, p->mel_row_off, feats, s);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "log-Mel launch");
     return RSIM_OK;
 }
