@@ -311,6 +311,60 @@ def backward(batch, L, alpha, g, nthreads=0, lib=None, output_mode=0):
     return dict(dx=dx, dh=dh, dalpha=da)
 
 
+# ---- per-(source, microphone) gains (Eq. 2's alpha_ij) ------------------------
+def _scaled_rirs(batch, alpha_rir):
+    """The batch's RIRs each multiplied by its gain alpha_ij (RIR order)."""
+    a = _f64(alpha_rir)
+    assert a.shape[0] == batch.rir_len.shape[0]
+    return _f64(batch.rir) * np.repeat(a, np.asarray(batch.rir_len, dtype=np.int64))
+
+
+def forward_rir_gains(batch, alpha_rir, eta_db=20.0, nthreads=0, lib=None, output_mode=0):
+    """Eq. 2 with one gain per (source, microphone): y_j = sum_i alpha_ij (hhat_ij * x_i).
+    By linearity it is the per-source mix with unit gains of the RIRs scaled by
+    alpha_ij; the cut-off (Eq. 7-9) is taken on the unscaled RIRs.  Returns
+    dict(y, L)."""
+    import dataclasses
+    lib = lib or _load()
+    tr = truncate_batch(batch, eta_db, nthreads, lib)
+    S = int(np.sum(batch.num_sources))
+    scaled = dataclasses.replace(batch, rir=_scaled_rirs(batch, alpha_rir))
+    y = forward_with_lengths(scaled, tr["L"], np.ones(S), nthreads, lib, output_mode)
+    return dict(y=y, L=tr["L"])
+
+
+def backward_rir_gains(batch, L, alpha_rir, g, nthreads=0, lib=None, output_mode=0):
+    """Adjoint of forward_rir_gains for fixed L: dx_i = sum_j alpha_ij (hhat_ij corr g_j),
+    dh_ij = alpha_ij corr(g_j, x_i) (k < L_ij), dalpha_ij = <g_j, hhat_ij * x_i>
+    = sum_k hhat_ij[k] corr(g_j, x_i)[k].  Returns dict(dx, dh, dalpha [R])."""
+    import dataclasses
+    lib = lib or _load()
+    S = int(np.sum(batch.num_sources))
+    a = _f64(alpha_rir)
+    scaled = dataclasses.replace(batch, rir=_scaled_rirs(batch, a))
+    out = backward(scaled, L, np.ones(S), g, nthreads, lib, output_mode)   # dh: corr(g_j, x_i)
+    nh = np.asarray(batch.rir_len, dtype=np.int64)
+    off = np.concatenate([[0], np.cumsum(nh)])
+    corr = out["dh"]
+    rir = _f64(batch.rir)
+    da = np.array([np.dot(rir[off[r]:off[r] + L[r]], corr[off[r]:off[r] + L[r]]) for r in range(nh.shape[0])])
+    return dict(dx=out["dx"], dh=corr * np.repeat(a, nh), dalpha=da)
+
+
+def forward_with_lengths(batch, L, alpha, nthreads=0, lib=None, output_mode=0):
+    """The direct-form mix (Eq. 2) for given kept lengths L and per-source gains."""
+    lib = lib or _load()
+    y = np.zeros(int(np.sum(output_lengths(batch, output_mode))) * batch.num_mics)
+    a = _f64(alpha).copy()
+    rc = lib.oracle_forward_batch(batch.num_sources.shape[0], batch.num_mics,
+                                  _p(_i32(batch.num_sources)), _p(_i64(batch.num_samples)),
+                                  _p(_i32(batch.rir_len)), _p(_f64(batch.x)), _p(_f64(batch.rir)), _p(_i64(L)),
+                                  _p(np.zeros(a.shape[0])), 1, _p(a), _p(y), int(output_mode), nthreads)
+    if rc:
+        raise OracleError("invalid forward arguments")
+    return y
+
+
 def forward_ola(batch, L, alpha, fft_n=0, nthreads=0, lib=None):
     """The paper's OLA filtering over a batch (FP64), for given L and alpha."""
     lib = lib or _load()
