@@ -68,7 +68,9 @@ typedef struct {
     double eta_db;                 /* Eq. 7 threshold in dB, >= 0; +INFINITY keeps every tap */
     int32_t fft_sizes_mask;        /* bit m allows N = 2^m, m in [11, 14]; 0 = all of them */
     int32_t gain_mode;             /* 0: alpha from SNRs (computed, written to gains);
-                                      1: alpha given by the caller in gains */
+                                      1: alpha given by the caller in gains;
+                                      2: one alpha_ij per (source, microphone), Eq. 2's
+                                         general form, given by the caller in gains [R] */
     int64_t segment_len;           /* samples per forward work tile; 0 = default (the largest
                                       allowed N); raised to the largest allowed N */
     int64_t bwd_segment_len;       /* samples per backward work tile; 0 = default (65536);
@@ -94,9 +96,11 @@ rsim_status rsim_plan(const rsim_plan_desc *desc, int device, rsim_plan_t *out);
  *   snr_db            [sum I_u] SNR of each noise source in dB relative to the
  *                     utterance's target (dry-signal mean power over [0, Nx));
  *                     entry of the target ignored.  Used when gain_mode = 0,
- *                     may be NULL when gain_mode = 1.
+ *                     may be NULL otherwise.
  *   gains             [sum I_u] alpha_i: written when gain_mode = 0 (alpha_0 = 1,
- *                     alpha_i = sqrt(P_0 / P_i * 10^(-SNR_i/10))), read when 1
+ *                     alpha_i = sqrt(P_0 / P_i * 10^(-SNR_i/10))), read when 1;
+ *                     gain_mode 2: [R] alpha_ij in RIR order, read (each is folded
+ *                     into its RIR's spectrum; the cut-off uses the unscaled RIR)
  *   y                 packed output, overwritten
  *   trunc_len         [R] int32 kept lengths L (Eq. 9), or NULL
  *   energy_kept_frac  [R] sum_{n<L} h^2 / sum_n h^2, or NULL
@@ -121,6 +125,9 @@ rsim_status rsim_filter_mix(rsim_plan_t plan, void *stream, const float *x, cons
  *                          0 for taps >= L (the cut-off is a fixed mask)
  *   grad_gains [sum I_u]   <grad_y_j, hhat_ij * x_i> summed over j; gains are
  *                          treated as inputs (no gradient flows to the SNRs)
+ * With gain_mode 2, alpha_ij takes the place of alpha_i above, and grad_gains
+ * is [R]: <grad_y_j, hhat_ij * x_i> per RIR (it reads the rir buffer the last
+ * forward was given).
  * grad_y has the layout of y (Ny samples per mic, per the plan's output_mode).
  * grad_x may be NULL (not computed); grad_rir and grad_gains must be given.
  * Returns RSIM_E_STATE if no forward ran on the plan.  Asynchronous. */

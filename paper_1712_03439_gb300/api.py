@@ -96,6 +96,8 @@ class Plan:
                                      dtype=np.int64) - 1
         self.y_size = int(np.sum(self.num_out) * self.num_mics)
         self.rir_size = int(np.sum(self.rir_len.astype(np.int64)))
+        # gains: one per source, or one per (source, microphone) in gain mode 2
+        self.G = self.R if self.gain_mode == 2 else self.S
         # FFT sizes the plan may pick (one forward/backward launch each)
         self.num_fft_sizes = bin(mask).count("1") if mask else 4
 
@@ -109,7 +111,7 @@ class Plan:
         """rsim_filter_mix: writes y (and gains when gain_mode = 0)."""
         _want(x, self.x_size, torch.float32, "x")
         _want(rir, self.rir_size, torch.float32, "rir")
-        _want(gains, self.S, torch.float32, "gains")
+        _want(gains, self.G, torch.float32, "gains")
         _want(y, self.y_size, torch.float32, "y")
         _want(snr_db, self.S, torch.float32, "snr_db")
         _want(trunc_len, self.R, torch.int32, "trunc_len")
@@ -123,10 +125,10 @@ class Plan:
         """rsim_filter_mix_backward: writes grad_x (if given), grad_rir and grad_gains."""
         _want(grad_y, self.y_size, torch.float32, "grad_y")
         _want(x, self.x_size, torch.float32, "x")
-        _want(gains, self.S, torch.float32, "gains")
+        _want(gains, self.G, torch.float32, "gains")
         _want(grad_x, self.x_size, torch.float32, "grad_x")
         _want(grad_rir, self.rir_size, torch.float32, "grad_rir")
-        _want(grad_gains, self.S, torch.float32, "grad_gains")
+        _want(grad_gains, self.G, torch.float32, "grad_gains")
         st = self._lib.rsim_filter_mix_backward(self._handle, _stream(stream), _ptr(grad_y), _ptr(x),
                                                 _ptr(gains), _ptr(grad_x), _ptr(grad_rir),
                                                 _ptr(grad_gains))
@@ -256,7 +258,7 @@ def filter_mix(plan: Plan, x, rir, snr_db=None, gains=None, stream=None):
     dev = x.device
     y = torch.empty(plan.y_size, dtype=torch.float32, device=dev)
     if gains is None:
-        gains = torch.empty(plan.S, dtype=torch.float32, device=dev)
+        gains = torch.empty(plan.G, dtype=torch.float32, device=dev)
     tl = torch.empty(plan.R, dtype=torch.int32, device=dev)
     ekf = torch.empty(plan.R, dtype=torch.float32, device=dev)
     plan.filter_mix(x, rir, gains, y, snr_db=snr_db, trunc_len=tl, energy_kept_frac=ekf,
@@ -267,13 +269,14 @@ def filter_mix(plan: Plan, x, rir, snr_db=None, gains=None, stream=None):
 class RsimFilterMix(torch.autograd.Function):
     """y = filter_mix(x, rir, gains) with the hand-written adjoint.
 
-    The plan must use gain_mode = 1 (gains are an input).  The truncation is
-    a fixed mask: grad_rir is zero beyond each kept length."""
+    The plan must use gain_mode 1 (gains [S], one per source) or 2 (gains [R],
+    one per source and microphone): gains are an input.  The truncation is a
+    fixed mask: grad_rir is zero beyond each kept length."""
 
     @staticmethod
     def forward(ctx, plan, x, rir, gains):
-        if plan.gain_mode != 1:
-            raise ValueError("RsimFilterMix needs a plan with gain_mode=1")
+        if plan.gain_mode not in (1, 2):
+            raise ValueError("RsimFilterMix needs a plan with gain_mode 1 or 2")
         x, rir, gains = x.contiguous(), rir.contiguous(), gains.contiguous()
         y = torch.empty(plan.y_size, dtype=torch.float32, device=x.device)
         plan.filter_mix(x, rir, gains, y)
@@ -288,7 +291,7 @@ class RsimFilterMix(torch.autograd.Function):
         grad_y = grad_y.contiguous()
         gx = torch.empty(plan.x_size, dtype=torch.float32, device=x.device) if ctx.needs_input_grad[1] else None
         gr = torch.empty(plan.rir_size, dtype=torch.float32, device=x.device)
-        gg = torch.empty(plan.S, dtype=torch.float32, device=x.device)
+        gg = torch.empty(plan.G, dtype=torch.float32, device=x.device)
         plan.filter_mix_backward(grad_y, x, gains, gx, gr, gg)
         return None, gx, gr, gg
 

@@ -140,6 +140,10 @@ struct rsim_plan_s {
     // offsets of the log-Mel features (device, written per call)
     std::vector<int64_t> h_ny;
     int64_t* mel_row_off = nullptr;
+    // per-(i, j) gains (gain_mode 2): unit source gains for the kernels, and the RIR
+    // buffer of the last forward (the backward's gain gradient reads it)
+    float* ones = nullptr;
+    const float* fwd_rir = nullptr;
 };
 
 namespace {
@@ -211,7 +215,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     if (!d->num_sources || !d->num_samples || !d->rir_len)
         return fail(RSIM_E_INVALID, "num_sources, num_samples and rir_len are required");
     if (!(d->eta_db >= 0.0)) return fail(RSIM_E_INVALID, "eta_db must be >= 0 or +inf");
-    if (d->gain_mode != 0 && d->gain_mode != 1) return fail(RSIM_E_INVALID, "gain_mode must be 0 or 1");
+    if (d->gain_mode < 0 || d->gain_mode > 2) return fail(RSIM_E_INVALID, "gain_mode must be 0, 1 or 2");
     int mask = d->fft_sizes_mask;
     const int supported = ((1 << (kMaxLog + 1)) - 1) & ~((1 << kMinLog) - 1);
     if (mask == 0) mask = supported;
@@ -322,7 +326,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     void *p_srcutt, *p_rirutt;
     void *p_nsrc, *p_nx, *p_ny, *p_src0, *p_rir0, *p_seg0, *p_segutt, *p_xoff, *p_yoff, *p_roff, *p_rlen,
         *p_dhpoff, *p_tuning, *p_L, *p_logN, *p_hop, *p_lmax, *p_nblk, *p_pow, *p_err, *p_list,
-        *p_count, *p_next, *p_Hc, *p_tails, *p_dhp, *p_dap, *p_melrow;
+        *p_count, *p_next, *p_Hc, *p_tails, *p_dhp, *p_dap, *p_melrow, *p_ones;
     void* p_tw[2 * kNumBuckets] = {};
     const int64_t cap = std::max<int64_t>(std::max<int64_t>(nbseg * kMaxSources, nseg), R);
     // launch shapes (persistent grids) decide the per-CTA backward scratch
@@ -374,6 +378,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     pieces.push_back({&p_dhp, sizeof(float) * std::max<int64_t>(dhp_total, 1)});
     pieces.push_back({&p_dap, sizeof(float) * std::max<int64_t>(nbseg, 1) * kMaxSources});
     pieces.push_back({&p_melrow, sizeof(int64_t) * (U + 1)});
+    pieces.push_back({&p_ones, sizeof(float) * std::max<int64_t>(S, 1)});
     std::vector<std::vector<float2>> tws(2 * kNumBuckets);
     for (int m = kMinLog; m <= kMaxLog; ++m) {
         if (!((mask >> m) & 1)) continue;
@@ -406,6 +411,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     for (int m = 0; m < 32; ++m) tuning[m] = d->fft_cost ? d->fft_cost[m] : (float)((double)m * std::ldexp(1.0, m));
     std::vector<int32_t> nsrc(d->num_sources, d->num_sources + U);
     std::vector<int64_t> nxv(d->num_samples, d->num_samples + U);
+    std::vector<float> ones(std::max<int64_t>(S, 1), 1.f);
     struct Up { void* dst; const void* src; size_t bytes; };
     std::vector<Up> ups = {
         {p_nsrc, nsrc.data(), sizeof(int32_t) * U},
@@ -425,6 +431,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
         {p_rirutt, rir_utt.data(), sizeof(int32_t) * R},
         {p_dhpoff, dhp_off.data(), sizeof(int64_t) * (nbseg + 1)},
         {p_tuning, tuning.data(), sizeof(float) * 32},
+        {p_ones, ones.data(), sizeof(float) * ones.size()},
     };
     for (int k = 0; k < 2 * kNumBuckets; ++k)
         if (p_tw[k]) ups.push_back({p_tw[k], tws[k].data(), sizeof(float2) * tws[k].size()});
@@ -467,6 +474,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     p->Q.cap = (int32_t)cap;
     p->Hc = (float2*)p_Hc; p->tails = (float*)p_tails; p->dhp = (float*)p_dhp; p->dap = (float*)p_dap;
     p->mel_row_off = (int64_t*)p_melrow;
+    p->ones = (float*)p_ones;
     p->h_ny = nyv;
     for (int b = 0; b < kNumBuckets; ++b) {
         p->tw[b] = Twiddles{(const float2*)p_tw[2 * b], (const float2*)p_tw[2 * b + 1]};
@@ -507,6 +515,9 @@ cudaError_t enqueue_forward(rsim_plan_t p, cudaStream_t st, const float* x, cons
                             const float* snr_db, float* gains, float* y, int32_t* trunc_len,
                             float* energy_kept_frac) {
     const DevBatch& B = p->B;
+    // per-(i, j) gains fold into the RIR spectra; the kernels then see unit source gains
+    const float* rir_gain = p->gain_mode == 2 ? gains : nullptr;
+    const float* src_gains = p->gain_mode == 2 ? p->ones : gains;
     if (p->gain_mode == 0 && !p->timer.on) {
         // source powers (reads x) run beside the RIR scan (reads rir)
         cudaEventRecord(p->ev_fork, st);
@@ -532,19 +543,19 @@ cudaError_t enqueue_forward(rsim_plan_t p, cudaStream_t st, const float* x, cons
         // each FFT size's spectra then its OLA pass on that size's stream: a size's
         // forward waits only for its own spectra
         fan_out(p, st, [&](int m, cudaStream_t s) {
-            launch_spectrum(m, B, p->Q, rir, p->Hc, p->tw[m - kMinLog], p->grid_spec[m - kMinLog], s);
-            launch_forward(m, B, p->Q, x, gains, p->Hc, y, p->tails, p->tw[m - kMinLog],
+            launch_spectrum(m, B, p->Q, rir, rir_gain, p->Hc, p->tw[m - kMinLog], p->grid_spec[m - kMinLog], s);
+            launch_forward(m, B, p->Q, x, src_gains, p->Hc, y, p->tails, p->tw[m - kMinLog],
                            p->grid_fwd[m - kMinLog], s);
         });
     } else {
         stage_mark(p, 3, false, st);
         fan_out(p, st, [&](int m, cudaStream_t s) {
-            launch_spectrum(m, B, p->Q, rir, p->Hc, p->tw[m - kMinLog], p->grid_spec[m - kMinLog], s);
+            launch_spectrum(m, B, p->Q, rir, rir_gain, p->Hc, p->tw[m - kMinLog], p->grid_spec[m - kMinLog], s);
         });
         stage_mark(p, 3, true, st);
         stage_mark(p, 4, false, st);
         fan_out(p, st, [&](int m, cudaStream_t s) {
-            launch_forward(m, B, p->Q, x, gains, p->Hc, y, p->tails, p->tw[m - kMinLog],
+            launch_forward(m, B, p->Q, x, src_gains, p->Hc, y, p->tails, p->tw[m - kMinLog],
                            p->grid_fwd[m - kMinLog], s);
         });
         stage_mark(p, 4, true, st);
@@ -563,16 +574,18 @@ cudaError_t enqueue_forward(rsim_plan_t p, cudaStream_t st, const float* x, cons
 cudaError_t enqueue_backward(rsim_plan_t p, cudaStream_t st, const float* grad_y, const float* x,
                              const float* gains, float* grad_x, float* grad_rir, float* grad_gains) {
     const DevBatch& B = p->B;
+    const float* rir_gain = p->gain_mode == 2 ? gains : nullptr;
+    const float* src_gains = p->gain_mode == 2 ? p->ones : gains;
     cudaError_t e = cudaMemsetAsync(p->Q.next + p->Q.idx(kListBwd, 0), 0, sizeof(int32_t) * kNumBuckets, st);
     if (e != cudaSuccess) return e;
     stage_mark(p, 6, false, st);
     fan_out(p, st, [&](int m, cudaStream_t s) {
-        launch_backward(m, B, p->Q, grad_y, x, gains, p->Hc, grad_x, p->dhp, p->dap,
+        launch_backward(m, B, p->Q, grad_y, x, src_gains, p->Hc, grad_x, p->dhp, p->dap,
                         p->tw[m - kMinLog], p->grid_bwd[m - kMinLog], s);
     });
     stage_mark(p, 6, true, st);
     stage_mark(p, 7, false, st);
-    launch_finalize(B, gains, p->dhp, p->dap, grad_rir, grad_gains, st);
+    launch_finalize(B, src_gains, rir_gain, p->fwd_rir, p->dhp, p->dap, grad_rir, grad_gains, st);
     stage_mark(p, 7, true, st);
     return cudaGetLastError();
 }
@@ -633,6 +646,7 @@ extern "C" rsim_status rsim_filter_mix(rsim_plan_t p, void* stream, const float*
     });
     if (e != cudaSuccess) return cuda_fail(e, "forward launch");
     p->fwd_done = true;
+    p->fwd_rir = rir;
     return RSIM_OK;
 }
 
@@ -645,7 +659,9 @@ extern "C" rsim_status rsim_filter_mix_backward(rsim_plan_t p, void* stream, con
     if (!grad_y || !x || !gains || !grad_rir || !grad_gains)
         return fail(RSIM_E_INVALID, "grad_y, x, gains, grad_rir and grad_gains are required");
     DeviceGuard guard(p->device);
-    const void* const key[8] = {grad_y, x, gains, grad_x, grad_rir, grad_gains, nullptr, nullptr};
+    // the RIR buffer of the last forward is part of the key: the gain gradient of
+    // gain mode 2 reads it
+    const void* const key[8] = {grad_y, x, gains, grad_x, grad_rir, grad_gains, p->fwd_rir, nullptr};
     cudaError_t e = run_graph(p, p->gbwd, key, (cudaStream_t)stream, [&](cudaStream_t s) {
         return enqueue_backward(p, s, grad_y, x, gains, grad_x, grad_rir, grad_gains);
     });

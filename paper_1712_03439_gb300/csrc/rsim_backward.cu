@@ -344,14 +344,19 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
 // grad_rir[r][k] = alpha_i / N * sum_segments partial[k] for k < L_r, 0 for
 // L_r <= k < Nh; grad_gains[s] = sum_segments dalpha partial.  Segments are
 // added in order; empty segments (no block starts in them) are skipped.
+// With per-(i, j) gains (rir_gain non-NULL) the spectra already carry alpha_ij,
+// the partials are the plain correlations c_r = corr(g_j, x_i) (times N), so
+// grad_rir[r] = alpha_ij / N c_r and grad_gains[r] = <hhat_r, c_r> / N.
 constexpr int kFinThreads = 256;
 constexpr int kFinMaxSegs = 512;   // backward segments of one utterance handled per pass
 
 __global__ void __launch_bounds__(kFinThreads)
-k_finalize(DevBatch B, const float* __restrict__ gains, const float* __restrict__ dhp,
-           const float* __restrict__ dap, float* __restrict__ grad_rir, float* __restrict__ grad_gains) {
+k_finalize(DevBatch B, const float* __restrict__ gains, const float* __restrict__ rir_gain,
+           const float* __restrict__ rir, const float* __restrict__ dhp, const float* __restrict__ dap,
+           float* __restrict__ grad_rir, float* __restrict__ grad_gains) {
     __shared__ int64_t seg_off[kFinMaxSegs];   // dh-partial offsets of the non-empty segments
     __shared__ int nseg_live;
+    __shared__ float red[kFinThreads / 32];
     for (int r = blockIdx.x; r < B.R; r += gridDim.x) {
         const int u = B.rir_utt[r];
         const int i = (r - B.rir0[u]) / B.J;
@@ -359,9 +364,13 @@ k_finalize(DevBatch B, const float* __restrict__ gains, const float* __restrict_
         float* out = grad_rir + B.roff[r];
         if (B.logN[u] == 0) {
             for (int k = threadIdx.x; k < nh; k += blockDim.x) out[k] = 0.f;
+            if (rir_gain && grad_gains && threadIdx.x == 0) grad_gains[r] = 0.f;
             continue;
         }
-        const float scale = gains[B.src0[u] + i] / (float)(1 << B.logN[u]);
+        const float inv_n = 1.f / (float)(1 << B.logN[u]);
+        const float scale = (rir_gain ? rir_gain[r] : gains[B.src0[u] + i]) * inv_n;
+        const float* h = rir_gain ? rir + B.roff[r] : nullptr;
+        float dot = 0.f;                       // <hhat_r, c_r> (per-(i, j) gains)
         const int64_t local = B.roff[r] - B.roff[B.rir0[u]];
         const int hop = B.hop[u];
         float acc[4];
@@ -397,10 +406,23 @@ k_finalize(DevBatch B, const float* __restrict__ gains, const float* __restrict_
             for (int c = 0; c < 4; ++c) {
                 const int k = threadIdx.x + (c0 + c) * kFinThreads;
                 if (k < nh) out[k] = k < Lr ? scale * acc[c] : 0.f;
+                if (h && k < Lr) dot = fmaf(h[k], acc[c], dot);
             }
         }
+        if (rir_gain && grad_gains) {          // block sum of dot, fixed order
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dot;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                float s = 0.f;
+                for (int w = 0; w < kFinThreads / 32; ++w) s += red[w];
+                grad_gains[r] = s * inv_n;
+            }
+            __syncthreads();
+        }
     }
-    if (grad_gains) {
+    if (grad_gains && !rir_gain) {
         for (int sidx = blockIdx.x * blockDim.x + threadIdx.x; sidx < B.S; sidx += gridDim.x * blockDim.x) {
             const int u = B.src_utt[sidx], i = sidx - B.src0[u];
             float acc = 0.f;
@@ -455,11 +477,12 @@ int bwd_threads(int logN) {
     return 1;
 }
 
-void launch_finalize(const DevBatch& B, const float* gains, const float* dhp, const float* dap,
+void launch_finalize(const DevBatch& B, const float* gains, const float* rir_gain, const float* rir,
+                     const float* dhp, const float* dap,
                      float* grad_rir, float* grad_gains, cudaStream_t st) {
     int grid = B.R < 4096 ? B.R : 4096;
     if (grid < 1) grid = 1;
-    k_finalize<<<grid, kFinThreads, 0, st>>>(B, gains, dhp, dap, grad_rir, grad_gains);
+    k_finalize<<<grid, kFinThreads, 0, st>>>(B, gains, rir_gain, rir, dhp, dap, grad_rir, grad_gains);
 }
 
 template <typename K>

@@ -23,8 +23,8 @@ __device__ __forceinline__ int pop_job(const Queues& Q, int kind, int b, int* sl
 // ---------------------------------------------------------------------------
 template <int M>
 __global__ void __launch_bounds__(M / e_for(M))
-k_spectrum(DevBatch B, Queues Q, int bucket, const float* __restrict__ rir, float2* __restrict__ Hc,
-           const float2* __restrict__ tw) {
+k_spectrum(DevBatch B, Queues Q, int bucket, const float* __restrict__ rir, const float* __restrict__ rir_gain,
+           float2* __restrict__ Hc, const float2* __restrict__ tw) {
     constexpr int E = e_for(M);
     constexpr int T = M / E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -37,12 +37,13 @@ k_spectrum(DevBatch B, Queues Q, int bucket, const float* __restrict__ rir, floa
         if (r < 0) break;
         float2 P[E];
         rfft_pairs<M, E>(P, rir + B.roff[r], B.L[r], sm, tw, t);
+        const float sc = rir_gain ? inv_n * rir_gain[r] : inv_n;   // a per-(i, j) gain folds in here
         // mirror pairs side by side: slot k < M/2 holds (H[k], H[M-k]); slot 0 holds
         // ((H[0], H[N/2]) packed, H[M/2])
         float4* H = reinterpret_cast<float4*>(Hc + (int64_t)r * B.MMAX);
 #pragma unroll
         for (int s = 0; s < E / 2; ++s) {
-            const float2 a = cscale(P[2 * s], inv_n), c = cscale(P[2 * s + 1], inv_n);
+            const float2 a = cscale(P[2 * s], sc), c = cscale(P[2 * s + 1], sc);
             H[t + s * T] = make_float4(a.x, a.y, c.x, c.y);
         }
     }
@@ -310,19 +311,20 @@ template <int M>
 constexpr int smem_forward() { return (int)FwdCfg<M>::bytes; }
 
 template <int M>
-static void spectrum_m(const DevBatch& B, const Queues& Q, int bucket, const float* rir,
+static void spectrum_m(const DevBatch& B, const Queues& Q, int bucket, const float* rir, const float* rir_gain,
                        float2* Hc, Twiddles tw, int grid, cudaStream_t st) {
-    k_spectrum<M><<<grid, M / e_for(M), smem_spectrum<M>(), st>>>(B, Q, bucket, rir, Hc, tw.get(e_for(M)));
+    k_spectrum<M><<<grid, M / e_for(M), smem_spectrum<M>(), st>>>(B, Q, bucket, rir, rir_gain, Hc,
+                                                                  tw.get(e_for(M)));
 }
 
-void launch_spectrum(int logN, const DevBatch& B, const Queues& Q, const float* rir, float2* Hc,
-                     Twiddles tw, int grid, cudaStream_t st) {
+void launch_spectrum(int logN, const DevBatch& B, const Queues& Q, const float* rir, const float* rir_gain,
+                     float2* Hc, Twiddles tw, int grid, cudaStream_t st) {
     const int b = logN - kMinLog;
     switch (logN) {
-        case 11: spectrum_m<1024>(B, Q, b, rir, Hc, tw, grid, st); break;
-        case 12: spectrum_m<2048>(B, Q, b, rir, Hc, tw, grid, st); break;
-        case 13: spectrum_m<4096>(B, Q, b, rir, Hc, tw, grid, st); break;
-        case 14: spectrum_m<8192>(B, Q, b, rir, Hc, tw, grid, st); break;
+        case 11: spectrum_m<1024>(B, Q, b, rir, rir_gain, Hc, tw, grid, st); break;
+        case 12: spectrum_m<2048>(B, Q, b, rir, rir_gain, Hc, tw, grid, st); break;
+        case 13: spectrum_m<4096>(B, Q, b, rir, rir_gain, Hc, tw, grid, st); break;
+        case 14: spectrum_m<8192>(B, Q, b, rir, rir_gain, Hc, tw, grid, st); break;
         default: break;
     }
 }

@@ -101,8 +101,9 @@ struct Twiddles {
     const float2* e16;
     __host__ __device__ const float2* get(int E) const { return E == 16 ? e16 : e8; }
 };
-void launch_spectrum(int logN, const DevBatch& B, const Queues& Q, const float* rir, float2* Hc,
-                     Twiddles tw, int grid, cudaStream_t st);
+// rir_gain: [R] gain of each RIR folded into its spectrum (per-(i, j) gains), or NULL
+void launch_spectrum(int logN, const DevBatch& B, const Queues& Q, const float* rir, const float* rir_gain,
+                     float2* Hc, Twiddles tw, int grid, cudaStream_t st);
 void launch_forward(int logN, const DevBatch& B, const Queues& Q, const float* x, const float* gains,
                     const float2* Hc, float* y, float* tails, Twiddles tw, int grid,
                     cudaStream_t st);
@@ -110,7 +111,9 @@ void launch_fixup(const DevBatch& B, float* y, const float* tails, cudaStream_t 
 void launch_backward(int logN, const DevBatch& B, const Queues& Q, const float* g, const float* x,
                      const float* gains, const float2* Hc, float* dx, float* dhp, float* dap,
                      Twiddles tw, int grid, cudaStream_t st);
-void launch_finalize(const DevBatch& B, const float* gains, const float* dhp, const float* dap,
+// rir_gain non-NULL: per-(i, j) gains; dh scaled per RIR and grad_gains [R] from rir
+void launch_finalize(const DevBatch& B, const float* gains, const float* rir_gain, const float* rir,
+                     const float* dhp, const float* dap,
                      float* grad_rir, float* grad_gains, cudaStream_t st);
 
 // sets the calling thread's message returned by rsim_last_error()

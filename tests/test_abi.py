@@ -50,7 +50,8 @@ def _desc(**kw):
     (dict(J=0), 1),
     (dict(eta=-1.0), 1),
     (dict(eta=float("nan")), 1),
-    (dict(gm=2), 1),
+    (dict(gm=3), 1),
+    (dict(gm=-1), 1),
     (dict(ns=[0]), 1),
     (dict(ns=[17], rl=[10] * 17), 1),
     (dict(nx=[0]), 1),
