@@ -351,6 +351,35 @@ def backward_rir_gains(batch, L, alpha_rir, g, nthreads=0, lib=None, output_mode
     return dict(dx=out["dx"], dh=corr * np.repeat(a, nh), dalpha=da)
 
 
+# ---- gains from SNRs on the reverberant signal (Eq. 2, SNR at a reference mic) ---
+def reverberant_gains(batch, snr_db=None, eta_db=20.0, ref_mic=0, lib=None):
+    """alpha_0 = 1, alpha_i = sqrt(P_0 / P_i 10^(-SNR_i/10)) with P_i the mean square
+    over [0, Nx) of source i filtered by its (cut) RIR to microphone ref_mic, the
+    reverberant signal that microphone receives from it.  Returns (alpha [S], P [S])."""
+    lib = lib or _load()
+    L = truncate_batch(batch, eta_db, 0, lib)["L"]
+    snr = _f64(batch.snr_db if snr_db is None else snr_db)
+    xo, ro, ri, si = batch.x_offsets(), batch.rir_offsets(), batch.rir_index(), batch.src_index()
+    J = batch.num_mics
+    P = np.zeros(int(si[-1]))
+    alpha = np.zeros(int(si[-1]))
+    for u in range(batch.num_utts):
+        nx = int(batch.num_samples[u])
+        for i in range(int(batch.num_sources[u])):
+            s = int(si[u]) + i
+            r = int(ri[u]) + i * J + ref_mic
+            y = mix_direct(batch.x[xo[s]:xo[s + 1]].reshape(1, nx), [batch.rir[ro[r]:ro[r + 1]]], [L[r]], [1.0],
+                           lib)
+            P[s] = float(np.mean(y[0] ** 2))
+        s0 = int(si[u])
+        alpha[s0] = 1.0
+        for i in range(1, int(batch.num_sources[u])):
+            if not P[s0 + i] > 0:
+                raise OracleError("noise source with zero reverberant power")
+            alpha[s0 + i] = math.sqrt(P[s0] / P[s0 + i] * 10.0 ** (-snr[s0 + i] / 10.0))
+    return alpha, P
+
+
 def forward_with_lengths(batch, L, alpha, nthreads=0, lib=None, output_mode=0):
     """The direct-form mix (Eq. 2) for given kept lengths L and per-source gains."""
     lib = lib or _load()
