@@ -67,10 +67,13 @@ typedef struct {
     const int32_t *rir_len;        /* [sum_u I_u J], Nh >= 1 (before the cut-off) */
     double eta_db;                 /* Eq. 7 threshold in dB, >= 0; +INFINITY keeps every tap */
     int32_t fft_sizes_mask;        /* bit m allows N = 2^m, m in [11, 14]; 0 = all of them */
-    int32_t gain_mode;             /* 0: alpha from SNRs (computed, written to gains);
+    int32_t gain_mode;             /* 0: alpha from SNRs on the dry signals (computed,
+                                         written to gains);
                                       1: alpha given by the caller in gains;
                                       2: one alpha_ij per (source, microphone), Eq. 2's
-                                         general form, given by the caller in gains [R] */
+                                         general form, given by the caller in gains [R];
+                                      3: alpha from SNRs on the reverberant signals at
+                                         microphone snr_ref_mic (computed, written) */
     int64_t segment_len;           /* samples per forward work tile; 0 = default (the largest
                                       allowed N); raised to the largest allowed N */
     int64_t bwd_segment_len;       /* samples per backward work tile; 0 = default (65536);
@@ -82,6 +85,8 @@ typedef struct {
                                       pointers; 1: launch eagerly */
     int32_t output_mode;           /* 0: "same" output, Ny = Nx; 1: full output,
                                       Ny = Nx + (longest RIR of the utterance) - 1 */
+    int32_t snr_ref_mic;           /* gain_mode 3: the microphone j (0 <= j < J) whose
+                                      reverberant signal sets the SNRs; ignored otherwise */
 } rsim_plan_desc;
 
 /* Creates a plan for the given shapes on CUDA device `device`.  Validates the
@@ -95,8 +100,10 @@ rsim_status rsim_plan(const rsim_plan_desc *desc, int device, rsim_plan_t *out);
  *   rir               packed RIRs, read only
  *   snr_db            [sum I_u] SNR of each noise source in dB relative to the
  *                     utterance's target (dry-signal mean power over [0, Nx));
- *                     entry of the target ignored.  Used when gain_mode = 0,
- *                     may be NULL otherwise.
+ *                     entry of the target ignored.  Used when gain_mode = 0
+ *                     (P the dry signal's mean square) or 3 (P the mean square
+ *                     over [0, Nx) of the source filtered by its cut RIR to
+ *                     microphone snr_ref_mic); may be NULL otherwise.
  *   gains             [sum I_u] alpha_i: written when gain_mode = 0 (alpha_0 = 1,
  *                     alpha_i = sqrt(P_0 / P_i * 10^(-SNR_i/10))), read when 1;
  *                     gain_mode 2: [R] alpha_ij in RIR order, read (each is folded

@@ -44,6 +44,7 @@ class PlanDesc(ctypes.Structure):
         ("fft_cost", ctypes.c_void_p),
         ("disable_graphs", ctypes.c_int32),
         ("output_mode", ctypes.c_int32),
+        ("snr_ref_mic", ctypes.c_int32),
     ]
 
 

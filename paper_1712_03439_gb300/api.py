@@ -39,7 +39,7 @@ class Plan:
 
     def __init__(self, num_sources, num_samples, rir_len, num_mics, eta_db=20.0,
                  fft_sizes=None, gain_mode=0, segment_len=0, bwd_segment_len=0, fft_cost=None,
-                 device=None, graphs=True, output_mode=0):
+                 device=None, graphs=True, output_mode=0, snr_ref_mic=0):
         self._lib = _lib.load()
         self._handle = None
         self.num_sources = np.ascontiguousarray(num_sources, dtype=np.int32)
@@ -80,7 +80,7 @@ class Plan:
             gain_mode=self.gain_mode, segment_len=int(segment_len),
             bwd_segment_len=int(bwd_segment_len),
             fft_cost=None if self._cost is None else self._cost.ctypes.data,
-            disable_graphs=0 if graphs else 1, output_mode=self.output_mode)
+            disable_graphs=0 if graphs else 1, output_mode=self.output_mode, snr_ref_mic=int(snr_ref_mic))
         h = ctypes.c_void_p()
         _lib.check(self._lib, self._lib.rsim_plan(ctypes.byref(desc), self.device, ctypes.byref(h)))
         self._handle = h

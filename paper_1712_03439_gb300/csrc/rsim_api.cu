@@ -144,7 +144,28 @@ struct rsim_plan_s {
     // buffer of the last forward (the backward's gain gradient reads it)
     float* ones = nullptr;
     const float* fwd_rir = nullptr;
+    // gains from reverberant SNRs (gain_mode 3): a plan over the sources, each its own
+    // one-microphone utterance with its RIR to the reference microphone, whose output
+    // (laid out like x) feeds the source-power scan; the RIRs are gathered for it
+    rsim_plan_t rev = nullptr;
+    const int64_t* rev_src_off = nullptr;   // [S] offset of each source's reference RIR in rir
+    const int64_t* rev_dst_off = nullptr;   // [S + 1] its offset in rev_rir
+    float* rev_rir = nullptr;
+    float* rev_y = nullptr;
 };
+
+namespace {
+// copies RIR s from rir + src_off[s] to dst + dst_off[s] (dst_off[s + 1] - dst_off[s] taps)
+__global__ void k_gather_rirs(int64_t n, const int64_t* __restrict__ src_off, const int64_t* __restrict__ dst_off,
+                              const float* __restrict__ rir, float* __restrict__ dst) {
+    for (int64_t s = blockIdx.x; s < n; s += gridDim.x) {
+        const float* a = rir + src_off[s];
+        float* b = dst + dst_off[s];
+        const int64_t len = dst_off[s + 1] - dst_off[s];
+        for (int64_t k = threadIdx.x; k < len; k += blockDim.x) b[k] = a[k];
+    }
+}
+}  // namespace
 
 namespace {
 
@@ -180,7 +201,9 @@ extern "C" const char* rsim_last_error(void) { return g_err.c_str(); }
 
 void rsim::set_last_error(const char* msg) { g_err = msg; }
 
-extern "C" int64_t rsim_plan_scratch_bytes(rsim_plan_t plan) { return plan ? (int64_t)plan->dbytes : 0; }
+extern "C" int64_t rsim_plan_scratch_bytes(rsim_plan_t plan) {
+    return plan ? (int64_t)plan->dbytes + (plan->rev ? (int64_t)plan->rev->dbytes : 0) : 0;
+}
 
 extern "C" void rsim_plan_destroy(rsim_plan_t plan) {
     if (!plan) return;
@@ -202,6 +225,7 @@ extern "C" void rsim_plan_destroy(rsim_plan_t plan) {
         if (plan->ev_aux) cudaEventDestroy(plan->ev_aux);
         if (plan->dmem) cudaFree(plan->dmem);
     }
+    if (plan->rev) rsim_plan_destroy(plan->rev);
     delete plan;
 }
 
@@ -215,7 +239,9 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     if (!d->num_sources || !d->num_samples || !d->rir_len)
         return fail(RSIM_E_INVALID, "num_sources, num_samples and rir_len are required");
     if (!(d->eta_db >= 0.0)) return fail(RSIM_E_INVALID, "eta_db must be >= 0 or +inf");
-    if (d->gain_mode < 0 || d->gain_mode > 2) return fail(RSIM_E_INVALID, "gain_mode must be 0, 1 or 2");
+    if (d->gain_mode < 0 || d->gain_mode > 3) return fail(RSIM_E_INVALID, "gain_mode must be 0, 1, 2 or 3");
+    if (d->gain_mode == 3 && (d->snr_ref_mic < 0 || d->snr_ref_mic >= J))
+        return fail(RSIM_E_INVALID, "snr_ref_mic must be in [0, num_mics)");
     int mask = d->fft_sizes_mask;
     const int supported = ((1 << (kMaxLog + 1)) - 1) & ~((1 << kMinLog) - 1);
     if (mask == 0) mask = supported;
@@ -326,7 +352,8 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     void *p_srcutt, *p_rirutt;
     void *p_nsrc, *p_nx, *p_ny, *p_src0, *p_rir0, *p_seg0, *p_segutt, *p_xoff, *p_yoff, *p_roff, *p_rlen,
         *p_dhpoff, *p_tuning, *p_L, *p_logN, *p_hop, *p_lmax, *p_nblk, *p_pow, *p_err, *p_list,
-        *p_count, *p_next, *p_Hc, *p_tails, *p_dhp, *p_dap, *p_melrow, *p_ones;
+        *p_count, *p_next, *p_Hc, *p_tails, *p_dhp, *p_dap, *p_melrow, *p_ones, *p_rsrc = nullptr,
+        *p_rdst = nullptr, *p_rrir = nullptr, *p_ry = nullptr;
     void* p_tw[2 * kNumBuckets] = {};
     const int64_t cap = std::max<int64_t>(std::max<int64_t>(nbseg * kMaxSources, nseg), R);
     // launch shapes (persistent grids) decide the per-CTA backward scratch
@@ -379,6 +406,23 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     pieces.push_back({&p_dap, sizeof(float) * std::max<int64_t>(nbseg, 1) * kMaxSources});
     pieces.push_back({&p_melrow, sizeof(int64_t) * (U + 1)});
     pieces.push_back({&p_ones, sizeof(float) * std::max<int64_t>(S, 1)});
+    // gain_mode 3: each source's RIR to the reference microphone, gathered, and the
+    // reverberant sources (laid out like x)
+    std::vector<int64_t> rev_src(S), rev_dst(S + 1, 0);
+    std::vector<int32_t> rev_len(S);
+    if (d->gain_mode == 3) {
+        for (int u = 0; u < U; ++u)
+            for (int i = 0; i < d->num_sources[u]; ++i) {
+                const int64_t s = src0[u] + i, r = rir0[u] + (int64_t)i * J + d->snr_ref_mic;
+                rev_src[s] = roff[r];
+                rev_len[s] = rlen[r];
+                rev_dst[s + 1] = rev_dst[s] + rlen[r];
+            }
+        pieces.push_back({&p_rsrc, sizeof(int64_t) * std::max<int64_t>(S, 1)});
+        pieces.push_back({&p_rdst, sizeof(int64_t) * (S + 1)});
+        pieces.push_back({&p_rrir, sizeof(float) * std::max<int64_t>(rev_dst[S], 1)});
+        pieces.push_back({&p_ry, sizeof(float) * std::max<int64_t>(xoff[S], 1)});
+    }
     std::vector<std::vector<float2>> tws(2 * kNumBuckets);
     for (int m = kMinLog; m <= kMaxLog; ++m) {
         if (!((mask >> m) & 1)) continue;
@@ -433,6 +477,10 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
         {p_tuning, tuning.data(), sizeof(float) * 32},
         {p_ones, ones.data(), sizeof(float) * ones.size()},
     };
+    if (d->gain_mode == 3) {
+        ups.push_back({p_rsrc, rev_src.data(), sizeof(int64_t) * S});
+        ups.push_back({p_rdst, rev_dst.data(), sizeof(int64_t) * (S + 1)});
+    }
     for (int k = 0; k < 2 * kNumBuckets; ++k)
         if (p_tw[k]) ups.push_back({p_tw[k], tws[k].data(), sizeof(float2) * tws[k].size()});
     for (auto& up : ups) {
@@ -455,7 +503,9 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     B.NSEG = (int32_t)nseg; B.MMAX = MMAX; B.mask = mask; B.seg_len = seg_len;
     B.NBSEG = (int32_t)nbseg; B.bseg_len = bseg_len;
     B.bseg0 = (const int32_t*)p_bseg0; B.bseg_utt = (const int32_t*)p_bsegutt;
-    B.gain_mode = d->gain_mode;
+    // the device planner computes gains from the source powers in modes 0 and 3 (in mode 3
+    // the powers are those of the reverberant sources)
+    B.gain_mode = d->gain_mode == 3 ? 0 : d->gain_mode;
     B.n_src = (const int32_t*)p_nsrc; B.n_x = (const int64_t*)p_nx; B.n_y = (const int64_t*)p_ny;
     B.src0 = (const int32_t*)p_src0; B.rir0 = (const int32_t*)p_rir0;
     B.seg0 = (const int32_t*)p_seg0; B.seg_utt = (const int32_t*)p_segutt;
@@ -475,6 +525,10 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     p->Hc = (float2*)p_Hc; p->tails = (float*)p_tails; p->dhp = (float*)p_dhp; p->dap = (float*)p_dap;
     p->mel_row_off = (int64_t*)p_melrow;
     p->ones = (float*)p_ones;
+    p->rev_src_off = (const int64_t*)p_rsrc;
+    p->rev_dst_off = (const int64_t*)p_rdst;
+    p->rev_rir = (float*)p_rrir;
+    p->rev_y = (float*)p_ry;
     p->h_ny = nyv;
     for (int b = 0; b < kNumBuckets; ++b) {
         p->tw[b] = Twiddles{(const float2*)p_tw[2 * b], (const float2*)p_tw[2 * b + 1]};
@@ -504,6 +558,29 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
         rsim_plan_destroy(p);
         return cuda_fail(e, "kernel attribute setup");
     }
+    if (d->gain_mode == 3) {
+        // every source its own utterance, one microphone, its RIR to the reference microphone
+        std::vector<int32_t> ones_i(S, 1);
+        std::vector<int64_t> rev_nx(S);
+        for (int u = 0; u < U; ++u)
+            for (int i = 0; i < d->num_sources[u]; ++i) rev_nx[src0[u] + i] = d->num_samples[u];
+        rsim_plan_desc rd = *d;
+        rd.num_utts = (int32_t)S;
+        rd.num_mics = 1;
+        rd.num_sources = ones_i.data();
+        rd.num_samples = rev_nx.data();
+        rd.rir_len = rev_len.data();
+        rd.gain_mode = 1;
+        rd.output_mode = 0;
+        rd.disable_graphs = 1;
+        rd.snr_ref_mic = 0;
+        const rsim_status rs = rsim_plan(&rd, device, &p->rev);
+        if (rs != RSIM_OK) {
+            const std::string msg = "reverberant-SNR plan: " + g_err;
+            rsim_plan_destroy(p);
+            return fail(rs, msg);
+        }
+    }
     *out = p;
     return RSIM_OK;
 }
@@ -518,7 +595,20 @@ cudaError_t enqueue_forward(rsim_plan_t p, cudaStream_t st, const float* x, cons
     // per-(i, j) gains fold into the RIR spectra; the kernels then see unit source gains
     const float* rir_gain = p->gain_mode == 2 ? gains : nullptr;
     const float* src_gains = p->gain_mode == 2 ? p->ones : gains;
-    if (p->gain_mode == 0 && !p->timer.on) {
+    if (p->gain_mode == 3) {
+        // reverberant sources at the reference microphone (the auxiliary plan, unit gains),
+        // then their powers; the planner turns them into gains as for the dry signals
+        k_gather_rirs<<<(unsigned)std::min<int64_t>(std::max<int64_t>(B.S, 1), 4096), 256, 0, st>>>(
+            B.S, p->rev_src_off, p->rev_dst_off, rir, p->rev_rir);
+        cudaError_t e = enqueue_forward(p->rev, st, x, p->rev_rir, nullptr, p->ones, p->rev_y, nullptr, nullptr);
+        if (e != cudaSuccess) return e;
+        stage_mark(p, 0, false, st);
+        launch_truncate(B, rir, p->factor, p->none, energy_kept_frac, p->grid_trunc, st);
+        stage_mark(p, 0, true, st);
+        stage_mark(p, 1, false, st);
+        launch_power(B, p->rev_y, p->grid_pow, st);
+        stage_mark(p, 1, true, st);
+    } else if (p->gain_mode == 0 && !p->timer.on) {
         // source powers (reads x) run beside the RIR scan (reads rir)
         cudaEventRecord(p->ev_fork, st);
         cudaStreamWaitEvent(p->aux, p->ev_fork, 0);
@@ -638,7 +728,8 @@ extern "C" rsim_status rsim_filter_mix(rsim_plan_t p, void* stream, const float*
     g_err.clear();
     if (!p) return fail(RSIM_E_INVALID, "NULL plan");
     if (!x || !rir || !gains || !y) return fail(RSIM_E_INVALID, "x, rir, gains and y are required");
-    if (p->gain_mode == 0 && !snr_db) return fail(RSIM_E_INVALID, "snr_db is required when gain_mode = 0");
+    if ((p->gain_mode == 0 || p->gain_mode == 3) && !snr_db)
+        return fail(RSIM_E_INVALID, "snr_db is required when gain_mode is 0 or 3");
     DeviceGuard guard(p->device);
     const void* const key[8] = {x, rir, snr_db, gains, y, trunc_len, energy_kept_frac, nullptr};
     cudaError_t e = run_graph(p, p->gfwd, key, (cudaStream_t)stream, [&](cudaStream_t s) {

@@ -41,7 +41,8 @@ def _desc(**kw):
                       rir_len=rl.ctypes.data, eta_db=kw.pop("eta", 20.0),
                       fft_sizes_mask=kw.pop("mask", 0), gain_mode=kw.pop("gm", 0),
                       segment_len=kw.pop("seg", 0), bwd_segment_len=kw.pop("bseg", 0),
-                      fft_cost=None, disable_graphs=0, output_mode=kw.pop("om", 0))
+                      fft_cost=None, disable_graphs=0, output_mode=kw.pop("om", 0),
+                      snr_ref_mic=kw.pop("ref", 0))
     return d, (ns, nx, rl)
 
 
@@ -50,8 +51,10 @@ def _desc(**kw):
     (dict(J=0), 1),
     (dict(eta=-1.0), 1),
     (dict(eta=float("nan")), 1),
-    (dict(gm=3), 1),
+    (dict(gm=4), 1),
     (dict(gm=-1), 1),
+    (dict(gm=3, ref=1), 1),
+    (dict(gm=3, ref=-1), 1),
     (dict(ns=[0]), 1),
     (dict(ns=[17], rl=[10] * 17), 1),
     (dict(nx=[0]), 1),
