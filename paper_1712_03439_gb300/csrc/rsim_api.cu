@@ -152,9 +152,74 @@ struct rsim_plan_s {
     const int64_t* rev_dst_off = nullptr;   // [S + 1] its offset in rev_rir
     float* rev_rir = nullptr;
     float* rev_y = nullptr;
+    // RIRs longer than one block reaches, without a cut-off: uniformly partitioned
+    // convolution.  A plan over virtual sources (i, p) -- source i delayed by p * part_len
+    // samples, filtered by taps [p * part_len, (p + 1) * part_len) of its RIRs -- does the
+    // work; segment copies and sums map x, the RIRs and the gains onto it and its
+    // gradients back.
+    rsim_plan_t part = nullptr;
+    struct Segs { const int64_t *src, *dst, *lead, *copy, *tail; int64_t n; };
+    struct Sums { const int64_t *out, *len, *t0, *src, *tlen; int64_t n; };
+    Segs seg_x{}, seg_h{}, seg_a{}, seg_dh{};
+    Sums sum_dx{}, sum_da{};
+    float *part_x = nullptr, *part_rir = nullptr, *part_a = nullptr;
+    float *part_dx = nullptr, *part_dh = nullptr, *part_da = nullptr;
+    void* part_mem = nullptr;
+    size_t part_bytes = 0;
 };
 
 namespace {
+// segment o: lead[o] zeros, then copy[o] values from in + src[o], then tail[o] zeros,
+// written from out + dst[o]
+__global__ void k_copy_segs(rsim_plan_s::Segs g, const float* __restrict__ in, float* __restrict__ out) {
+    for (int64_t o = blockIdx.x; o < g.n; o += gridDim.x) {
+        float* d = out + g.dst[o];
+        const float* s = in + g.src[o];
+        const int64_t a = g.lead[o], c = g.copy[o], n = a + c + g.tail[o];
+        for (int64_t k = threadIdx.x; k < n; k += blockDim.x) d[k] = (k >= a && k < a + c) ? s[k - a] : 0.f;
+    }
+}
+
+// output o, length len[o]: out[out[o] + m] = sum over terms q in [t0[o], t0[o + 1]) of
+// in[src[q] + m] for m < tlen[q] (terms added in order)
+__global__ void k_sum_segs(rsim_plan_s::Sums g, const float* __restrict__ in, float* __restrict__ out) {
+    for (int64_t o = blockIdx.x; o < g.n; o += gridDim.x) {
+        const int64_t q0 = g.t0[o], q1 = g.t0[o + 1];
+        for (int64_t m = threadIdx.x; m < g.len[o]; m += blockDim.x) {
+            float acc = 0.f;
+            for (int64_t q = q0; q < q1; ++q)
+                if (m < g.tlen[q]) acc += in[g.src[q] + m];
+            out[g.out[o] + m] = acc;
+        }
+    }
+}
+
+// per-source gains from the source powers (alpha_0 = 1, alpha_i = sqrt(P_0 / P_i
+// 10^(-SNR_i/10))) for the partitioned path, where the planner of the plan itself
+// is not run
+__global__ void k_part_gains(DevBatch B, const float* __restrict__ snr_db, float* __restrict__ gains) {
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < B.U; u += gridDim.x * blockDim.x) {
+        const int s0 = B.src0[u], I = B.n_src[u];
+        const double nx = (double)B.n_x[u];
+        const int nch = (int)((B.n_x[u] + kPowerChunk - 1) / kPowerChunk);
+        double P0 = 0.0;
+        for (int c = 0; c < nch; ++c) P0 += B.pow_part[(int64_t)s0 * B.CH + c];
+        P0 /= nx;
+        gains[s0] = 1.f;
+        for (int i = 1; i < I; ++i) {
+            double Pi = 0.0;
+            for (int c = 0; c < nch; ++c) Pi += B.pow_part[(int64_t)(s0 + i) * B.CH + c];
+            Pi /= nx;
+            if (!(Pi > 0.0)) {
+                atomicOr(B.err, kErrZeroPower);
+                gains[s0 + i] = 0.f;
+            } else {
+                gains[s0 + i] = (float)sqrt(P0 / Pi * pow(10.0, -(double)snr_db[s0 + i] / 10.0));
+            }
+        }
+    }
+}
+
 // copies RIR s from rir + src_off[s] to dst + dst_off[s] (dst_off[s + 1] - dst_off[s] taps)
 __global__ void k_gather_rirs(int64_t n, const int64_t* __restrict__ src_off, const int64_t* __restrict__ dst_off,
                               const float* __restrict__ rir, float* __restrict__ dst) {
@@ -202,7 +267,9 @@ extern "C" const char* rsim_last_error(void) { return g_err.c_str(); }
 void rsim::set_last_error(const char* msg) { g_err = msg; }
 
 extern "C" int64_t rsim_plan_scratch_bytes(rsim_plan_t plan) {
-    return plan ? (int64_t)plan->dbytes + (plan->rev ? (int64_t)plan->rev->dbytes : 0) : 0;
+    return plan ? (int64_t)plan->dbytes + (plan->rev ? (int64_t)plan->rev->dbytes : 0) +
+                      (plan->part ? (int64_t)plan->part->dbytes + (int64_t)plan->part_bytes : 0)
+                : 0;
 }
 
 extern "C" void rsim_plan_destroy(rsim_plan_t plan) {
@@ -226,8 +293,151 @@ extern "C" void rsim_plan_destroy(rsim_plan_t plan) {
         if (plan->dmem) cudaFree(plan->dmem);
     }
     if (plan->rev) rsim_plan_destroy(plan->rev);
+    if (plan->part) rsim_plan_destroy(plan->part);
+    if (plan->part_mem) {
+        DeviceGuard g(plan->device);
+        cudaFree(plan->part_mem);
+    }
     delete plan;
 }
+
+namespace {
+
+// Builds the partitioned plan: virtual source (i, p) of an utterance is source i delayed by
+// p * part_len samples, and its RIR to microphone j is taps [p * part_len, (p + 1) * part_len)
+// of h_ij (one zero tap if h_ij is shorter); part_len = N_max / 2, parts = ceil(max Nh / part_len)
+// per utterance.  Also builds the copy and sum tables that map the caller's buffers onto it.
+rsim_status make_partitioned(rsim_plan_t p, const rsim_plan_desc* d, int device, const std::vector<int32_t>& src0,
+                             const std::vector<int32_t>& rir0, const std::vector<int64_t>& xoff,
+                             const std::vector<int64_t>& roff, const std::vector<int32_t>& rlen, int part_log) {
+    const int U = d->num_utts, J = d->num_mics;
+    const int64_t P = (int64_t)1 << (part_log - 1);
+    std::vector<int32_t> ns(U), parts(U), rl;
+    std::vector<int64_t> xs, hs_src, hs_dst, hs_copy, hs_tail, as_src;
+    std::vector<int64_t> xs_src, xs_lead, xs_copy, dh_src, dh_dst, dh_copy;
+    std::vector<int64_t> dx_out, dx_len, dx_t0{0}, dx_src, dx_tlen, da_out, da_len, da_t0{0}, da_src, da_tlen;
+    int64_t xv = 0, rv = 0, sv = 0;
+    for (int u = 0; u < U; ++u) {
+        const int I = d->num_sources[u];
+        const int64_t nx = d->num_samples[u];
+        int64_t nh = 1;
+        for (int r = rir0[u]; r < rir0[u + 1]; ++r) nh = std::max<int64_t>(nh, rlen[r]);
+        const int Pu = (int)((nh + P - 1) / P);
+        if ((int64_t)I * Pu > kMaxSources)
+            return fail(RSIM_E_UNSUPPORTED, "partitioned convolution needs sources x parts <= 16 per utterance");
+        ns[u] = I * Pu;
+        parts[u] = Pu;
+        for (int i = 0; i < I; ++i) {
+            const int64_t s = src0[u] + i;
+            dx_out.push_back(xoff[s]);
+            dx_len.push_back(nx);
+            da_out.push_back(s);
+            da_len.push_back(1);
+            for (int q = 0; q < Pu; ++q) {
+                const int64_t sv_q = sv + (int64_t)i * Pu + q;   // virtual source index
+                const int64_t xv_q = xv + ((int64_t)i * Pu + q) * nx;
+                const int64_t lead = std::min<int64_t>((int64_t)q * P, nx);
+                xs_src.push_back(xoff[s]);
+                xs.push_back(xv_q);
+                xs_lead.push_back(lead);
+                xs_copy.push_back(nx - lead);
+                as_src.push_back(s);
+                dx_src.push_back(xv_q + lead);
+                dx_tlen.push_back(nx - lead);
+                da_src.push_back(sv_q);
+                da_tlen.push_back(1);
+            }
+            dx_t0.push_back((int64_t)dx_src.size());
+            da_t0.push_back((int64_t)da_src.size());
+        }
+        // virtual RIRs in (virtual source, microphone) order
+        for (int i = 0; i < I; ++i)
+            for (int q = 0; q < Pu; ++q)
+                for (int j = 0; j < J; ++j) {
+                    const int64_t r = rir0[u] + (int64_t)i * J + j;
+                    const int64_t valid = std::max<int64_t>(0, std::min<int64_t>(P, rlen[r] - (int64_t)q * P));
+                    const int64_t len = std::max<int64_t>(valid, 1);
+                    rl.push_back((int32_t)len);
+                    hs_src.push_back(roff[r] + (int64_t)q * P);
+                    hs_dst.push_back(rv);
+                    hs_copy.push_back(valid);
+                    hs_tail.push_back(len - valid);
+                    dh_src.push_back(rv);
+                    dh_dst.push_back(roff[r] + (int64_t)q * P);
+                    dh_copy.push_back(valid);
+                    rv += len;
+                }
+        xv += (int64_t)I * Pu * nx;
+        sv += (int64_t)I * Pu;
+    }
+    rsim_plan_desc pd = *d;
+    pd.num_sources = ns.data();
+    pd.rir_len = rl.data();
+    pd.gain_mode = 1;
+    pd.output_mode = 0;
+    pd.disable_graphs = 1;
+    pd.snr_ref_mic = 0;
+    rsim_status st = rsim_plan(&pd, device, &p->part);
+    if (st != RSIM_OK) return fail(st, "partitioned plan: " + g_err);
+    // one allocation: tables, then the virtual buffers
+    std::vector<int64_t> zeros(std::max<size_t>({xs.size(), hs_src.size(), dh_src.size(), (size_t)1}), 0);
+    std::vector<int64_t> ones_v(std::max<size_t>(as_src.size(), 1), 1);
+    std::vector<int64_t> seq(sv);
+    for (int64_t k = 0; k < sv; ++k) seq[k] = k;
+    struct Arr { const std::vector<int64_t>* v; size_t n; const int64_t** dst; };
+    const size_t nS = xs.size(), nR = hs_src.size(), nO = dx_out.size();
+    std::vector<Arr> arrs = {
+        {&xs_src, nS, &p->seg_x.src}, {&xs, nS, &p->seg_x.dst}, {&xs_lead, nS, &p->seg_x.lead},
+        {&xs_copy, nS, &p->seg_x.copy}, {&zeros, nS, &p->seg_x.tail},
+        {&hs_src, nR, &p->seg_h.src}, {&hs_dst, nR, &p->seg_h.dst}, {&zeros, nR, &p->seg_h.lead},
+        {&hs_copy, nR, &p->seg_h.copy}, {&hs_tail, nR, &p->seg_h.tail},
+        {&as_src, nS, &p->seg_a.src}, {&seq, nS, &p->seg_a.dst}, {&zeros, nS, &p->seg_a.lead},
+        {&ones_v, nS, &p->seg_a.copy}, {&zeros, nS, &p->seg_a.tail},
+        {&dh_src, nR, &p->seg_dh.src}, {&dh_dst, nR, &p->seg_dh.dst}, {&zeros, nR, &p->seg_dh.lead},
+        {&dh_copy, nR, &p->seg_dh.copy}, {&zeros, nR, &p->seg_dh.tail},
+        {&dx_out, nO, &p->sum_dx.out}, {&dx_len, nO, &p->sum_dx.len}, {&dx_t0, nO + 1, &p->sum_dx.t0},
+        {&dx_src, dx_src.size(), &p->sum_dx.src}, {&dx_tlen, dx_tlen.size(), &p->sum_dx.tlen},
+        {&da_out, nO, &p->sum_da.out}, {&da_len, nO, &p->sum_da.len}, {&da_t0, nO + 1, &p->sum_da.t0},
+        {&da_src, da_src.size(), &p->sum_da.src}, {&da_tlen, da_tlen.size(), &p->sum_da.tlen},
+    };
+    size_t total = 0;
+    for (auto& a : arrs) total = align_up(total, 256) + sizeof(int64_t) * std::max<size_t>(a.n, 1);
+    const size_t f_off = align_up(total, 256);
+    const int64_t fl[6] = {xv, rv, sv, xv, rv, sv};   // x, rir, gains, dx, dh, dalpha
+    total = f_off;
+    for (int k = 0; k < 6; ++k) total = align_up(total, 256) + sizeof(float) * std::max<int64_t>(fl[k], 1);
+    DeviceGuard guard(device);
+    cudaError_t e = cudaMalloc(&p->part_mem, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(RSIM_E_NOMEM, "cudaMalloc of " + std::to_string(total) + " bytes (partitioned) failed");
+    }
+    p->part_bytes = total;
+    size_t off = 0;
+    for (auto& a : arrs) {
+        off = align_up(off, 256);
+        int64_t* dst = (int64_t*)((char*)p->part_mem + off);
+        if (a.n) {
+            e = cudaMemcpy(dst, a.v->data(), sizeof(int64_t) * a.n, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy (partitioned tables)");
+        }
+        *a.dst = dst;
+        off += sizeof(int64_t) * std::max<size_t>(a.n, 1);
+    }
+    float** bufs[6] = {&p->part_x, &p->part_rir, &p->part_a, &p->part_dx, &p->part_dh, &p->part_da};
+    off = f_off;
+    for (int k = 0; k < 6; ++k) {
+        off = align_up(off, 256);
+        *bufs[k] = (float*)((char*)p->part_mem + off);
+        off += sizeof(float) * std::max<int64_t>(fl[k], 1);
+    }
+    p->seg_x.n = p->seg_a.n = (int64_t)nS;
+    p->seg_h.n = p->seg_dh.n = (int64_t)nR;
+    p->sum_dx.n = p->sum_da.n = (int64_t)nO;
+    return RSIM_OK;
+}
+
+}  // namespace
 
 extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_t* out) {
     g_err.clear();
@@ -250,6 +460,21 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     if (d->output_mode != 0 && d->output_mode != 1) return fail(RSIM_E_INVALID, "output_mode must be 0 or 1");
     if (d->segment_len < 0 || d->bwd_segment_len < 0)
         return fail(RSIM_E_INVALID, "segment_len and bwd_segment_len must be >= 0");
+    // without a cut-off, an RIR longer than the largest allowed FFT size reaches (hop >= N/4:
+    // 3N/4 + 1 taps) goes through uniformly partitioned convolution
+    int part_log = kMinLog;
+    for (int m = kMinLog; m <= kMaxLog; ++m)
+        if ((mask >> m) & 1) part_log = m;
+    bool partitioned = false;
+    if (std::isinf(d->eta_db)) {
+        int64_t nh_all = 0, r_all = 0;
+        for (int u = 0; u < U; ++u) r_all += (int64_t)std::max(d->num_sources[u], 0) * J;
+        for (int64_t r = 0; r < r_all; ++r) nh_all = std::max<int64_t>(nh_all, d->rir_len[r]);
+        partitioned = nh_all > 3 * ((int64_t)1 << part_log) / 4 + 1;
+    }
+    if (partitioned && (d->output_mode != 0 || d->gain_mode > 1))
+        return fail(RSIM_E_UNSUPPORTED, "RIRs longer than the largest FFT size reaches (partitioned "
+                                        "convolution) need output_mode 0 and gain_mode 0 or 1");
 
     std::vector<int32_t> src0(U + 1), rir0(U + 1), seg0(U + 1), bseg0(U + 1);
     std::vector<int64_t> yoff(U + 1), nyv(U);
@@ -558,6 +783,14 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
         rsim_plan_destroy(p);
         return cuda_fail(e, "kernel attribute setup");
     }
+    if (partitioned) {
+        const rsim_status ps = make_partitioned(p, d, device, src0, rir0, xoff, roff, rlen, part_log);
+        if (ps != RSIM_OK) {
+            const std::string msg = g_err;
+            rsim_plan_destroy(p);
+            return fail(ps, msg);
+        }
+    }
     if (d->gain_mode == 3) {
         // every source its own utterance, one microphone, its RIR to the reference microphone
         std::vector<int32_t> ones_i(S, 1);
@@ -587,11 +820,38 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
 
 namespace {
 
+void copy_segs(const rsim_plan_s::Segs& g, const float* in, float* out, cudaStream_t st) {
+    if (g.n > 0) k_copy_segs<<<(unsigned)std::min<int64_t>(g.n, 4096), 256, 0, st>>>(g, in, out);
+}
+void sum_segs(const rsim_plan_s::Sums& g, const float* in, float* out, cudaStream_t st) {
+    if (g.n > 0) k_sum_segs<<<(unsigned)std::min<int64_t>(g.n, 4096), 256, 0, st>>>(g, in, out);
+}
+
 // The forward launch sequence on stream st (eager, or recorded by a capture).
 cudaError_t enqueue_forward(rsim_plan_t p, cudaStream_t st, const float* x, const float* rir,
                             const float* snr_db, float* gains, float* y, int32_t* trunc_len,
                             float* energy_kept_frac) {
     const DevBatch& B = p->B;
+    if (p->part) {
+        // partitioned: lengths (no cut-off) and gains here, the filtering on the plan over the
+        // virtual sources
+        launch_truncate(B, rir, p->factor, p->none, energy_kept_frac, p->grid_trunc, st);
+        if (p->gain_mode == 0) {
+            launch_power(B, x, p->grid_pow, st);
+            k_part_gains<<<(B.U + 255) / 256, 256, 0, st>>>(B, snr_db, gains);
+        }
+        copy_segs(p->seg_x, x, p->part_x, st);
+        copy_segs(p->seg_h, rir, p->part_rir, st);
+        copy_segs(p->seg_a, gains, p->part_a, st);
+        cudaError_t e = enqueue_forward(p->part, st, p->part_x, p->part_rir, nullptr, p->part_a, y, nullptr,
+                                        nullptr);
+        if (e != cudaSuccess) return e;
+        if (trunc_len) {
+            e = cudaMemcpyAsync(trunc_len, B.L, sizeof(int32_t) * B.R, cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaGetLastError();
+    }
     // per-(i, j) gains fold into the RIR spectra; the kernels then see unit source gains
     const float* rir_gain = p->gain_mode == 2 ? gains : nullptr;
     const float* src_gains = p->gain_mode == 2 ? p->ones : gains;
@@ -664,6 +924,17 @@ cudaError_t enqueue_forward(rsim_plan_t p, cudaStream_t st, const float* x, cons
 cudaError_t enqueue_backward(rsim_plan_t p, cudaStream_t st, const float* grad_y, const float* x,
                              const float* gains, float* grad_x, float* grad_rir, float* grad_gains) {
     const DevBatch& B = p->B;
+    if (p->part) {
+        // the plan over the virtual sources, then its gradients folded back: dx_i sums the
+        // delayed copies, dh_ij gathers the parts, dalpha_i sums over the parts
+        cudaError_t e = enqueue_backward(p->part, st, grad_y, p->part_x, p->part_a, grad_x ? p->part_dx : nullptr,
+                                         p->part_dh, p->part_da);
+        if (e != cudaSuccess) return e;
+        if (grad_x) sum_segs(p->sum_dx, p->part_dx, grad_x, st);
+        copy_segs(p->seg_dh, p->part_dh, grad_rir, st);
+        sum_segs(p->sum_da, p->part_da, grad_gains, st);
+        return cudaGetLastError();
+    }
     const float* rir_gain = p->gain_mode == 2 ? gains : nullptr;
     const float* src_gains = p->gain_mode == 2 ? p->ones : gains;
     cudaError_t e = cudaMemsetAsync(p->Q.next + p->Q.idx(kListBwd, 0), 0, sizeof(int32_t) * kNumBuckets, st);
@@ -760,15 +1031,11 @@ extern "C" rsim_status rsim_filter_mix_backward(rsim_plan_t p, void* stream, con
     return RSIM_OK;
 }
 
-extern "C" rsim_status rsim_plan_sync_status(rsim_plan_t p, void* stream) {
-    g_err.clear();
-    if (!p) return fail(RSIM_E_INVALID, "NULL plan");
-    DeviceGuard guard(p->device);
-    cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+namespace {
+// reads and clears the error word of one plan (after the stream was synchronised)
+rsim_status check_device_error(rsim_plan_t p) {
     int32_t err = 0;
-    e = cudaMemcpy(&err, p->B.err, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    cudaError_t e = cudaMemcpy(&err, p->B.err, sizeof(int32_t), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy (error word)");
     if (err) {
         cudaMemset(p->B.err, 0, sizeof(int32_t));
@@ -783,6 +1050,21 @@ extern "C" rsim_status rsim_plan_sync_status(rsim_plan_t p, void* stream) {
     }
     return RSIM_OK;
 }
+}  // namespace
+
+extern "C" rsim_status rsim_plan_sync_status(rsim_plan_t p, void* stream) {
+    g_err.clear();
+    if (!p) return fail(RSIM_E_INVALID, "NULL plan");
+    DeviceGuard guard(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    // the plan's own word, and those of the plans it runs (reverberant gains, partitions)
+    rsim_status s = check_device_error(p);
+    if (s == RSIM_OK && p->rev) s = check_device_error(p->rev);
+    if (s == RSIM_OK && p->part) s = check_device_error(p->part);
+    return s;
+}
 
 extern "C" rsim_status rsim_plan_query(rsim_plan_t p, void* stream, int32_t* log2_n, int32_t* hop,
                                        int32_t* l_max, int32_t* num_blocks) {
@@ -790,6 +1072,7 @@ extern "C" rsim_status rsim_plan_query(rsim_plan_t p, void* stream, int32_t* log
     if (!p) return fail(RSIM_E_INVALID, "NULL plan");
     if (!p->fwd_done) return fail(RSIM_E_STATE, "rsim_plan_query before rsim_filter_mix");
     DeviceGuard guard(p->device);
+    if (p->part) p = p->part;   // the FFT sizes and blocks of the partitioned filtering
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     const size_t n = sizeof(int32_t) * p->B.U;

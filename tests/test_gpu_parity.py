@@ -261,8 +261,8 @@ def _merge(a, b):
 @pytest.mark.parametrize("n_fft", [2048, 8192])
 def test_longest_admissible_rir_and_one_tap_more(n_fft):
     # L_max = 3N/4 + 1 is the longest kept RIR a size admits (hop = N/4, the carry spans
-    # three blocks): exact against the oracle; one tap more is reported unsupported
-    from paper_1712_03439_gb300._lib import RsimError
+    # three blocks): exact against the oracle; one tap more (no cut-off) goes through the
+    # partitioned convolution, exact as well
     lmax = 3 * n_fft // 4 + 1
     rng = np.random.Generator(np.random.PCG64(n_fft))
 
@@ -281,9 +281,9 @@ def test_longest_admissible_rir_and_one_tap_more(n_fft):
     assert plan.query()["hop"][0] == n_fft // 4
     ref = oracle.forward(b, math.inf, alpha=gains.astype(np.float64))
     assert_channels_close(res["y"], ref["y"], b)
-    with pytest.raises(RsimError) as e:
-        gpu_forward(batch(lmax + 1), eta=math.inf, fft_sizes=[n_fft], gains=gains)
-    assert e.value.status == 2
+    b1 = batch(lmax + 1)
+    _, res1, _ = gpu_forward(b1, eta=math.inf, fft_sizes=[n_fft], gains=gains)
+    assert_channels_close(res1["y"], oracle.forward(b1, math.inf, alpha=gains.astype(np.float64))["y"], b1)
 
 
 def test_minority_fft_size_moves_to_the_dominant_one():
@@ -439,10 +439,14 @@ def test_silent_noise_source_is_reported():
 
 
 def test_rir_too_long_for_allowed_sizes_is_reported():
+    # with a cut-off the kept lengths are known on the device only: a kept RIR beyond
+    # 3N/4 + 1 taps for every allowed N is reported (without a cut-off such RIRs go
+    # through the partitioned convolution)
     from paper_1712_03439_gb300._lib import RsimError
     b = small_batch(seed=43, lengths=(3000,), n_src=(1,), rt60=(0.5, 0.5))
+    assert oracle.truncate_batch(b, 60.0)["L"].max() > 3 * 2048 // 4 + 1
     with pytest.raises(RsimError) as e:
-        gpu_forward(b, eta=math.inf, fft_sizes=[2048], gains=np.ones(1, np.float32))
+        gpu_forward(b, eta=60.0, fft_sizes=[2048], gains=np.ones(1, np.float32))
     assert e.value.status == 2
 
 
