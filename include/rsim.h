@@ -91,7 +91,17 @@ typedef struct {
 
 /* Creates a plan for the given shapes on CUDA device `device`.  Validates the
  * description, allocates scratch and uploads twiddle tables.  On success *out
- * holds a plan to be released with rsim_plan_destroy. */
+ * holds a plan to be released with rsim_plan_destroy.
+ *
+ * Without a cut-off (eta_db = +INFINITY), when some RIR is longer than one block
+ * of the largest allowed FFT size N reaches (3N/4 + 1 taps), the plan filters by
+ * uniformly partitioned convolution: source i delayed by p * N/2 samples is
+ * filtered by taps [p N/2, (p+1) N/2) of its RIRs, for p < ceil(longest RIR of
+ * the utterance / (N/2)), and the parts are summed (the same Eq. 2, computed in
+ * pieces).  This needs output_mode 0, gain_mode 0 or 1, and at most 16 sources
+ * times parts per utterance (RSIM_E_UNSUPPORTED otherwise); its scratch holds the
+ * delayed copies of x.  With gain_mode 3 the plan also filters every source to
+ * the reference microphone (a second, one-microphone plan inside this one). */
 rsim_status rsim_plan(const rsim_plan_desc *desc, int device, rsim_plan_t *out);
 
 /* Forward filter-and-mix (Eq. 7-9 truncation, gains, Eq. 2 by overlap-add).
@@ -155,7 +165,9 @@ rsim_status rsim_plan_sync_status(rsim_plan_t plan, void *stream);
 
 /* Copies the per-utterance plan chosen on the device by the last forward:
  * log2 of the FFT size, hop (N - L_max + 1), L_max and block count, each [U]
- * int32 host arrays (any may be NULL).  Synchronises the stream. */
+ * int32 host arrays (any may be NULL); for a partitioned plan, those of the
+ * partitioned filtering (L_max is then the longest part).  Synchronises the
+ * stream. */
 rsim_status rsim_plan_query(rsim_plan_t plan, void *stream, int32_t *log2_n, int32_t *hop,
                             int32_t *l_max, int32_t *num_blocks);
 
