@@ -101,3 +101,29 @@ def test_image_rirs_rejects_bad_arguments_on_the_host(lib, args):
                              args.get("fs", 16000.0), args.get("c0", 343.0), fake, None)
     assert st == 1
     assert "rsim_image_rirs" in lib.rsim_last_error().decode()
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes structures of the binding have the header's field offsets and sizes
+    (compiled with the host C compiler against include/rsim.h)."""
+    import subprocess
+    structs = {"rsim_plan_desc": _lib.PlanDesc, "rsim_mel_desc": _lib.MelDesc}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "rsim.h"', 'int main(void) {']
+    for cname, cls in structs.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'    printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append('    printf("rsim_image_geom size %zu\\n", sizeof(rsim_image_geom));')
+    lines.append('    return 0;\n}')
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, f"{cname}.{fname}"
+    # the image geometry rows the binding passes: 10 floats
+    assert got[("rsim_image_geom", "size")] == 40
