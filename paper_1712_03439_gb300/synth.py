@@ -105,6 +105,17 @@ class Batch:
         """Target-utterance seconds in the batch (not multiplied by I or J)."""
         return float(np.sum(self.num_samples)) / FS
 
+    def excerpt(self, n_max: int) -> "Batch":
+        """The same batch with every utterance cut to its first min(Nx, n_max)
+        samples (all its sources alike; RIRs and SNRs unchanged)."""
+        xo, si = self.x_offsets(), self.src_index()
+        n_new = np.minimum(self.num_samples, int(n_max)).astype(np.int64)
+        xs = []
+        for u in range(self.num_utts):
+            for s in range(si[u], si[u + 1]):
+                xs.append(self.x[xo[s]:xo[s] + n_new[u]])
+        return dataclasses.replace(self, num_samples=n_new, x=np.concatenate(xs).astype(np.float32))
+
     def subset(self, utts) -> "Batch":
         """A batch made of the given utterance indices (in that order)."""
         utts = list(utts)
