@@ -111,3 +111,42 @@ def test_algorithmic_work_counts_transforms_and_bytes():
           + 7 * ((4 + J) * tr(12) + 4 * J * mac(12)) + 2 * J * tr(12))
     assert w["bwd_flops"] == pytest.approx(bf)
     assert w["fwd_flops_5n"] > w["fwd_flops"]
+
+
+def test_room_recipe_keeps_everything_inside_the_room():
+    b = synth.config_stream(n_utts=40)
+    geom, rir_len, rt60 = synth.room_geometry(5, b.num_sources, synth.linear_pair_array())
+    assert geom.shape == (b.num_rirs, 10) and rir_len.shape == (b.num_rirs,)
+    room, src, mic, refl = geom[:, :3], geom[:, 3:6], geom[:, 6:9], geom[:, 9]
+    assert np.all((src > 0) & (src < room)) and np.all((mic > 0) & (mic < room))
+    assert np.all((refl >= 0) & (refl < 1))
+    # one room per utterance, every RIR of it ceil(RT60 fs) taps, the pair 7.1 cm apart
+    ri = b.rir_index()
+    for u in range(b.num_utts):
+        rows = geom[ri[u]:ri[u + 1]]
+        assert np.all(rows[:, :3] == rows[0, :3]) and np.all(rows[:, 9] == rows[0, 9])
+        assert np.all(rir_len[ri[u]:ri[u + 1]] == math.ceil(rt60[u] * synth.FS))
+        m = rows[:, 6:9].reshape(-1, b.num_mics, 3)[0]
+        assert np.linalg.norm(m[0] - m[1]) == pytest.approx(0.071, abs=1e-5)
+
+
+def test_excerpt_cuts_every_source_alike():
+    b = synth.make_batch(3, [1000, 400, 2500], [2, 1, 3], synth.linear_pair_array(), (0.1, 0.1))
+    e = b.excerpt(600)
+    np.testing.assert_array_equal(e.num_samples, [600, 400, 600])
+    xo, eo = b.x_offsets(), e.x_offsets()
+    for s in range(int(b.num_sources.sum())):
+        n = eo[s + 1] - eo[s]
+        np.testing.assert_array_equal(e.x[eo[s]:eo[s + 1]], b.x[xo[s]:xo[s] + n])
+    np.testing.assert_array_equal(e.rir, b.rir)
+    np.testing.assert_array_equal(e.snr_db, b.snr_db)
+
+
+def test_generator_and_front_end_work_counts():
+    bench = _bench()
+    nbytes, flops = bench.image_work(3, [100, 200, 300], 8)
+    assert nbytes == 4.0 * 600 + 48.0 * 3 + 8.0
+    assert flops == 6.0 * 3 * 17 ** 3
+    nbytes, flops = bench.mel_work(np.array([16000, 8000]), 45, 141)
+    assert nbytes == 4.0 * 24000 + 4.0 * 45 * 4 * 128
+    assert flops == 141 * (512 + 2.5 * 512 * 9 + 3 * 257 + 2 * 2 * 257)
