@@ -7,6 +7,10 @@ input generators, does not need a GPU):
   RsimFilterMix        -- torch.autograd.Function with the hand-written adjoint
   filter_mix_autograd  -- RsimFilterMix.apply
   image_rirs           -- image-method RIRs (wraps rsim_image_rirs)
+Plan also carries the log-Mel front end (Plan.log_mel, Plan.log_mel_rows) and
+the gain modes: 0 gains from SNRs on the dry signals, 1 given per source,
+2 given per (source, microphone), 3 from SNRs on the reverberant signal at
+microphone snr_ref_mic.
 """
 _API = ("Plan", "filter_mix", "RsimFilterMix", "filter_mix_autograd", "image_rirs")
 
