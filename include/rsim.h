@@ -13,7 +13,10 @@
  * Nx + L_max - 1 are zero), chosen per plan by output_mode.
  *
  * by overlap-add FFT filtering (Sec. 2.2, Eq. 6), and its adjoint (gradients
- * with respect to x_i, h_ij and alpha_i).  All arithmetic runs in CUDA
+ * with respect to x_i, h_ij and alpha_i; gain mode 2 takes Eq. 2's general
+ * alpha_ij, one gain per source and microphone).  The library also generates
+ * image-method RIRs (Eq. 1, rsim_image_rirs) and computes the log-Mel features
+ * the paper trains on (Sec. 4, rsim_plan_log_mel).  All arithmetic runs in CUDA
  * kernels on one GPU; the library has no CPU fallback.
  *
  * Packed layouts (all FP32, device memory unless stated otherwise):
