@@ -917,6 +917,55 @@ def run_mel(args):
     return 0
 
 
+def run_gains(args):
+    """Forward + backward on the home-256 mix under each gain mode: 0 (SNRs on the
+    dry signals), 2 (one gain per source and microphone) and 3 (SNRs on the
+    reverberant signal at microphone 0, one more filtering pass per source)."""
+    import torch
+    from paper_1712_03439_gb300 import Plan, build, synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    build.build()
+    b = synth.config_home()
+    audio_s = b.audio_seconds()
+    x, rir, snr = (torch.from_numpy(a).to(dev) for a in (b.x, b.rir, b.snr_db))
+    gy = torch.from_numpy(synth.grad_like(95, b.y_size)).to(dev)
+    steps = max(args.steps // 10, 10)
+    out = {}
+    clock = ClockSampler(0)
+    for mode in (0, 2, 3):
+        plan = Plan.for_batch(b, eta_db=ETA_DB, gain_mode=mode, device=0)
+        gains = (torch.from_numpy(np.repeat(np.linspace(0.5, 1.0, plan.S), b.num_mics).astype(np.float32)).to(dev)
+                 if mode == 2 else torch.empty(plan.G, device=dev))
+        y = torch.empty(plan.y_size, device=dev)
+        gx, gr, gg = torch.empty_like(x), torch.empty_like(rir), torch.empty(plan.G, device=dev)
+
+        def step():
+            plan.filter_mix(x, rir, gains, y, snr_db=None if mode == 2 else snr)
+            plan.filter_mix_backward(gy, x, gains, gx, gr, gg)
+        for _ in range(3):
+            step()
+        plan.sync_status()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[str(mode)] = {"ms_per_step": ms, "value": audio_s / (ms / 1e3), "unit": UNIT}
+        plan.close()
+    line = {"metric": "simulated audio s/sec (fwd+bwd) per gain mode, home-256", "unit": UNIT, "n_gpus": 1,
+            "dtype": "f32", "data": DATA, "higher_is_better": True, "steps": steps,
+            "config": {"workload": WORKLOAD, "gain_modes": {"0": "SNRs on the dry signals",
+                                                             "2": "one gain per source and microphone",
+                                                             "3": "SNRs on the reverberant signal at mic 0"}},
+            "modes": out, "clocks": clock.stop()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def oracle_free_lengths(b, eta):
     """Kept lengths (Eq. 7-9) computed in numpy for the report when the library
     rejects the batch (FP64 compare, as the kernels do)."""
@@ -944,7 +993,7 @@ def main():
     ap.add_argument("--only-step", action="store_true",
                     help="time only the K steps (no forward-only, end-to-end, plain or CPU legs); "
                          "for profiler runs")
-    ap.add_argument("--config", choices=["home", "stream", "long", "rooms", "mel"], default="home",
+    ap.add_argument("--config", choices=["home", "stream", "long", "rooms", "mel", "gains"], default="home",
                     help="home: the headline line; stream / long / rooms / mel: reports on the streaming, "
                          "the long reverberant and the image-method-room workloads and on the log-Mel "
                          "front end")
@@ -963,6 +1012,8 @@ def main():
         return run_rooms(args)
     if args.config == "mel":
         return run_mel(args)
+    if args.config == "gains":
+        return run_gains(args)
     return run_ours(args)
 
 
