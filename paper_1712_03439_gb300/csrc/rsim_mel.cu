@@ -1,4 +1,4 @@
-// Log-Mel front end (Sec. 4): stacked log-Mel features of one microphone of
+// Log-Mel front end (Sec. 3): stacked log-Mel features of one microphone of
 // the mixed output.
 //
 // One warp per frame.  The 512 windowed samples are read as 256 complex

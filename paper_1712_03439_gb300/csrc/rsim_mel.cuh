@@ -5,7 +5,7 @@
 
 namespace rsim {
 
-// log-Mel front end (Sec. 4): frames of kMelFft samples every hop samples,
+// log-Mel front end (Sec. 3): frames of kMelFft samples every hop samples,
 // n_mels triangular filters, ln(E + floor), stack frames per row, rows every
 // stride frames
 constexpr int kMelFft = 512;

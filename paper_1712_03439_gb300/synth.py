@@ -7,7 +7,7 @@ no filtering), so both the CUDA path and the FP64 oracle can be fed from it.
 
 Workload shapes follow the paper's statistics:
   * utterances are 16 kHz, mean length 7.31 s (Sec. 2.2);
-  * J = 2 microphones 7.1 cm apart (Sec. 4);
+  * J = 2 microphones 7.1 cm apart (Sec. 3);
   * 0-3 noise sources besides the target, mean I = 2.55 (Sec. 2.1);
   * reverberation times around 0.48 s (Table 4).
 The paper's data sets are not available; these generators stand in for them.

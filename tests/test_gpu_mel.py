@@ -1,4 +1,4 @@
-"""Log-Mel front end (Sec. 4 features): CUDA path vs the FP64 oracle.
+"""Log-Mel front end (Sec. 3 features): CUDA path vs the FP64 oracle.
 
 The frame and row bookkeeping is integer work and must match exactly (row
 counts, which frame lands in which row and slot).  Values are compared in the

@@ -1,4 +1,4 @@
-"""Pins of the oracle's log-Mel front end (Sec. 4 features) against facts that
+"""Pins of the oracle's log-Mel front end (Sec. 3 features) against facts that
 do not come from the oracle itself:
 
 * the HTK Mel scale maps 1000 Hz to 1000 Mel (the property it is built on) and
