@@ -100,6 +100,9 @@ class Plan:
         self.G = self.R if self.gain_mode == 2 else self.S
         # FFT sizes the plan may pick (one forward/backward launch each)
         self.num_fft_sizes = bin(mask).count("1") if mask else 4
+        # forwards run on this plan so far: the backward uses the state (cut-off
+        # lengths, RIR spectra, the RIR buffer) of the most recent one
+        self.forward_count = 0
 
     @classmethod
     def for_batch(cls, batch, **kw):
@@ -120,6 +123,7 @@ class Plan:
                                        _ptr(snr_db), _ptr(gains), _ptr(y), _ptr(trunc_len),
                                        _ptr(energy_kept_frac))
         _lib.check(self._lib, st)
+        self.forward_count += 1
 
     def filter_mix_backward(self, grad_y, x, gains, grad_x, grad_rir, grad_gains, stream=None):
         """rsim_filter_mix_backward: writes grad_x (if given), grad_rir and grad_gains."""
@@ -271,7 +275,15 @@ class RsimFilterMix(torch.autograd.Function):
 
     The plan must use gain_mode 1 (gains [S], one per source) or 2 (gains [R],
     one per source and microphone): gains are an input.  The truncation is a
-    fixed mask: grad_rir is zero beyond each kept length."""
+    fixed mask: grad_rir is zero beyond each kept length.
+
+    The library's backward reuses the state of the plan's most recent forward
+    (cut-off lengths, cached RIR spectra and, with per-(i, j) gains, the RIR
+    buffer that forward read).  The tensors this forward used (x, the
+    contiguous rir, gains) are saved, so that buffer stays alive; when another
+    forward ran on the same plan in between (gradient accumulation, a second
+    branch), the backward first re-runs this call's forward on the saved
+    tensors to restore that state."""
 
     @staticmethod
     def forward(ctx, plan, x, rir, gains):
@@ -281,13 +293,18 @@ class RsimFilterMix(torch.autograd.Function):
         y = torch.empty(plan.y_size, dtype=torch.float32, device=x.device)
         plan.filter_mix(x, rir, gains, y)
         ctx.plan = plan
-        ctx.save_for_backward(x, gains)
+        ctx.forward_count = plan.forward_count
+        ctx.save_for_backward(x, rir, gains)
         return y
 
     @staticmethod
     def backward(ctx, grad_y):
         plan = ctx.plan
-        x, gains = ctx.saved_tensors
+        x, rir, gains = ctx.saved_tensors
+        if plan.forward_count != ctx.forward_count:
+            # a later forward replaced the plan's state: rebuild this call's
+            plan.filter_mix(x, rir, gains, torch.empty(plan.y_size, dtype=torch.float32, device=x.device))
+            ctx.forward_count = plan.forward_count
         grad_y = grad_y.contiguous()
         gx = torch.empty(plan.x_size, dtype=torch.float32, device=x.device) if ctx.needs_input_grad[1] else None
         gr = torch.empty(plan.rir_size, dtype=torch.float32, device=x.device)

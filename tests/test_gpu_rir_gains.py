@@ -9,6 +9,7 @@ import pytest
 
 import oracle
 from paper_1712_03439_gb300 import synth
+from parity_checks import close_vec, grads_close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -29,11 +30,7 @@ def dev(a):
 
 
 def close(a, r, what):
-    a = np.asarray(a, np.float64)
-    nr = np.linalg.norm(r)
-    assert np.linalg.norm(a - r) <= REL * max(nr, 1e-30), f"{what}: rel L2 {np.linalg.norm(a - r) / nr:.3e}"
-    if nr > 0:
-        assert np.max(np.abs(a - r)) <= REL * np.max(np.abs(r)) * 10, f"{what}: max abs"
+    close_vec(a, r, what)
 
 
 def channels_close(y, ref, b):
@@ -78,12 +75,7 @@ def test_rir_gains_match_oracle(J, eta):
     np.testing.assert_array_equal(got["L"], ref["L"])
     channels_close(got["y"], ref["y"], b)
     bw = oracle.backward_rir_gains(b, ref["L"], alpha_r.astype(np.float64), gy.astype(np.float64))
-    xo, ro = b.x_offsets(), b.rir_offsets()
-    for s in range(int(b.num_sources.sum())):
-        close(got["dx"][xo[s]:xo[s + 1]], bw["dx"][xo[s]:xo[s + 1]], f"dx[{s}]")
-    for r in range(b.num_rirs):
-        close(got["dh"][ro[r]:ro[r + 1]], bw["dh"][ro[r]:ro[r + 1]], f"dh[{r}]")
-    np.testing.assert_allclose(got["da"], bw["dalpha"], rtol=REL, atol=REL * np.abs(bw["dalpha"]).max())
+    grads_close(b, bw, ref["L"], dx=got["dx"], dh=got["dh"], dalpha=got["da"])
 
 
 def test_per_source_gains_given_per_rir_reproduce_mode_1():
@@ -144,6 +136,62 @@ def test_autograd_with_rir_gains():
     (0.5 * torch.sum((y - dev(t)) ** 2)).backward()
     ref = oracle.forward_rir_gains(b, alpha_r.astype(np.float64), math.inf)
     bw = oracle.backward_rir_gains(b, ref["L"], alpha_r.astype(np.float64), ref["y"] - t)
-    close(x.grad.cpu().numpy(), bw["dx"], "dx")
-    close(rir.grad.cpu().numpy(), bw["dh"], "dh")
-    close(g.grad.cpu().numpy(), bw["dalpha"], "dalpha")
+    grads_close(b, bw, ref["L"], dx=x.grad.cpu().numpy(), dh=rir.grad.cpu().numpy(), dalpha=g.grad.cpu().numpy())
+
+
+def test_autograd_with_rir_gains_and_a_non_contiguous_rir():
+    # the forward makes a contiguous copy of rir; the gain gradient reads that copy
+    # in the backward, so it must outlive the forward call
+    from paper_1712_03439_gb300 import Plan, filter_mix_autograd
+    b = synth.config_fd_subcase()
+    alpha_r = np.linspace(-0.8, 1.2, b.num_rirs).astype(np.float32)
+    t = synth.grad_like(92, b.y_size)
+    plan = Plan.for_batch(b, eta_db=math.inf, gain_mode=2)
+    x = dev(b.x).requires_grad_(True)
+    wide = torch.zeros((b.rir.shape[0], 2), device="cuda")
+    wide[:, 0] = dev(b.rir)
+    wide.requires_grad_(True)
+    rir = wide[:, 0]                              # stride 2: not contiguous
+    assert not rir.is_contiguous()
+    g = dev(alpha_r).requires_grad_(True)
+    y = filter_mix_autograd(plan, x, rir, g)
+    junk = [torch.full((b.rir.shape[0],), 9.0, device="cuda") for _ in range(4)]   # reuse freed blocks
+    (0.5 * torch.sum((y - dev(t)) ** 2)).backward()
+    del junk
+    ref = oracle.forward_rir_gains(b, alpha_r.astype(np.float64), math.inf)
+    bw = oracle.backward_rir_gains(b, ref["L"], alpha_r.astype(np.float64), ref["y"] - t)
+    grads_close(b, bw, ref["L"], dx=x.grad.cpu().numpy(), dh=wide.grad[:, 0].cpu().numpy(),
+                dalpha=g.grad.cpu().numpy())
+
+
+@pytest.mark.parametrize("gain_mode", [1, 2])
+def test_autograd_two_forwards_then_two_backwards(gain_mode):
+    # gradient accumulation on one plan: both forwards run before either backward;
+    # each backward must see its own forward's RIRs, cut-off and spectra
+    from paper_1712_03439_gb300 import Plan, filter_mix_autograd
+    b = synth.make_batch(93, [6000, 15000], [2, 3], synth.linear_pair_array(), (0.1, 0.3))
+    G = b.num_rirs if gain_mode == 2 else int(b.num_sources.sum())
+    alpha = np.linspace(0.5, 1.4, G).astype(np.float32)
+    plan = Plan.for_batch(b, eta_db=20.0, gain_mode=gain_mode)
+    t = synth.grad_like(94, b.y_size)
+    grads = []
+    for scale in (1.0, 0.5):
+        x = dev(b.x).requires_grad_(True)
+        rir = dev(scale * b.rir).requires_grad_(True)
+        g = dev(alpha).requires_grad_(True)
+        grads.append((x, rir, g))
+    ys = [filter_mix_autograd(plan, *v) for v in grads]
+    for y in ys:
+        (0.5 * torch.sum((y - dev(t)) ** 2)).backward()
+    for (x, rir, g), scale in zip(grads, (1.0, 0.5)):
+        bs = synth.Batch(b.num_mics, b.num_sources, b.num_samples, b.rir_len, b.x,
+                         (scale * b.rir).astype(np.float32), b.snr_db)
+        L = oracle.truncate_batch(bs, 20.0)["L"]
+        if gain_mode == 2:
+            ref = oracle.forward_rir_gains(bs, alpha.astype(np.float64), 20.0)
+            bw = oracle.backward_rir_gains(bs, ref["L"], alpha.astype(np.float64), ref["y"] - t)
+        else:
+            ref = oracle.forward(bs, 20.0, alpha=alpha.astype(np.float64))
+            bw = oracle.backward(bs, L, alpha.astype(np.float64), ref["y"] - t)
+        grads_close(bs, bw, L, dx=x.grad.cpu().numpy(), dh=rir.grad.cpu().numpy(), dalpha=g.grad.cpu().numpy(),
+                    what=f"scale {scale} ")
