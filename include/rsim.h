@@ -16,7 +16,7 @@
  * with respect to x_i, h_ij and alpha_i; gain mode 2 takes Eq. 2's general
  * alpha_ij, one gain per source and microphone).  The library also generates
  * image-method RIRs (Eq. 1, rsim_image_rirs) and computes the log-Mel features
- * the paper trains on (Sec. 4, rsim_plan_log_mel).  All arithmetic runs in CUDA
+ * the paper trains on (Sec. 3, rsim_plan_log_mel).  All arithmetic runs in CUDA
  * kernels on one GPU; the library has no CPU fallback.
  *
  * Packed layouts (all FP32, device memory unless stated otherwise):
@@ -222,14 +222,19 @@ void rsim_plan_destroy(rsim_plan_t plan);
  * every entry it reads.  All calls share that one array, so calls whose work
  * overlaps on the GPU race; queue them on one stream or wait between them.
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  The
- * host arrays are copied (as pageable memory) before the call returns, and
- * that copy may wait for earlier work on the stream.  Asynchronous otherwise. */
+ * device current) and keeps it for the life of the process; make that first
+ * call before any stream capture, and do not call this entry point again on a
+ * device after cudaDeviceReset has been called for it (the kept address would
+ * be stale).  num_sources and num_samples are copied to the device on
+ * `stream` with cudaMemcpyAsync: from pageable host memory that copy is
+ * finished when the call returns (it may wait for earlier work on the
+ * stream); from pinned host memory it is not, and the arrays must stay
+ * unchanged until the stream has reached the call.  Asynchronous otherwise. */
 rsim_status rsim_source_gains_noalloc(void *stream, int32_t num_utts, const int32_t *num_sources,
                                       const int64_t *num_samples, const float *x, const float *snr_db,
                                       float *gains);
 
-/* ---- log-Mel front end (Sec. 4) ---------------------------------------------
+/* ---- log-Mel front end (Sec. 3) ---------------------------------------------
  *
  * The features the paper trains on, from one microphone of the mixed output:
  * frames of 512 samples (32 ms at 16 kHz) every `hop` samples (160: 10 ms),

@@ -6,13 +6,15 @@ an allocation would stall the device at the wrong moment), so they cannot
 make a plan.  Its scratch is a fixed array inside the library that every
 call reuses; these tests call it through the C-ABI twice in a row, on two
 different batches, and check each result against the gains rsim_filter_mix
-computes with gain_mode = 0.  This file is collected last on purpose.
+computes with gain_mode = 0 and against the FP64 oracle's gains.  This file
+is collected last on purpose.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_1712_03439_gb300 import synth
 
 torch = pytest.importorskip("torch")
@@ -65,6 +67,53 @@ def test_noalloc_gains_match_the_plan_path_on_two_calls_in_a_row(lib):
     np.testing.assert_allclose(got_small, ref_small, rtol=RTOL, atol=0)
     # and the same batch twice in a row
     np.testing.assert_allclose(_noalloc_gains(lib, small), ref_small, rtol=RTOL, atol=0)
+
+
+def _oracle_gains(b):
+    si, xo = b.src_index(), b.x_offsets()
+    out = []
+    for u in range(b.num_utts):
+        nx = int(b.num_samples[u])
+        xs = b.x[xo[si[u]]:xo[si[u + 1]]].reshape(-1, nx)
+        out.append(oracle.gains(xs, b.snr_db[si[u]:si[u + 1]]))
+    return np.concatenate(out)
+
+
+def test_noalloc_gains_match_the_oracle(lib):
+    b = synth.make_batch(78, [900, 40000, 70001, 12345], [2, 4, 1, 3], synth.linear_pair_array(), (0.1, 0.3))
+    np.testing.assert_allclose(_noalloc_gains(lib, b), _oracle_gains(b), rtol=RTOL, atol=0)
+
+
+def test_noalloc_silent_noise_source_gets_nan_and_the_others_stay_finite(lib):
+    # the plan path reports a silent noise source as an error; this entry point has
+    # no plan to latch it in and writes NaN for that source only
+    b = synth.make_batch(79, [3000, 5000], [3, 2], synth.linear_pair_array(), (0.1, 0.3))
+    xo = b.x_offsets()
+    b.x[xo[1]:xo[2]] = 0                   # utterance 0, noise source 1
+    got = _noalloc_gains(lib, b)
+    assert np.isnan(got[1])
+    assert np.all(np.isfinite(got[[0, 2, 3, 4]]))
+    # source 2 of utterance 0: the oracle on that utterance without the silent source
+    nx = int(b.num_samples[0])
+    xs = np.stack([b.x[xo[0]:xo[1]], b.x[xo[2]:xo[3]]]).reshape(2, nx)
+    a02 = oracle.gains(xs, np.array([0.0, b.snr_db[2]], np.float32))[1]
+    np.testing.assert_allclose(got[2], a02, rtol=RTOL)
+    assert got[0] == 1.0
+    np.testing.assert_allclose(got[3:], _oracle_gains(b.subset([1])), rtol=RTOL)
+
+
+def test_noalloc_python_wrapper_on_a_side_stream(lib):
+    from paper_1712_03439_gb300 import api
+    b = synth.make_batch(80, [20000, 7000], [2, 3], synth.linear_pair_array(), (0.1, 0.3))
+    side = torch.cuda.Stream()
+    x = torch.from_numpy(b.x).cuda()
+    snr = torch.from_numpy(b.snr_db).cuda()
+    gains = torch.full((int(b.num_sources.sum()),), -1.0, device="cuda")
+    side.wait_stream(torch.cuda.current_stream())   # the inputs' copies are done
+    with torch.cuda.stream(side):
+        api.source_gains_noalloc(b.num_sources, b.num_samples, x, snr, gains, stream=side)
+    side.synchronize()
+    np.testing.assert_allclose(gains.cpu().numpy(), _oracle_gains(b), rtol=RTOL, atol=0)
 
 
 def test_noalloc_rejects_a_batch_beyond_its_fixed_scratch(lib):
