@@ -82,6 +82,8 @@ def _bind(lib):
                                              ctypes.c_int]
     lib.oracle_mix_window.restype = None
     lib.oracle_mix_window.argtypes = [P, i64, i32, i32, P, P, P, P, i64, i64, P]
+    lib.oracle_dh_window.restype = None
+    lib.oracle_dh_window.argtypes = [P, i64, P, i64, i64, ctypes.c_double, i64, i64, P]
     lib.oracle_dx_window.restype = None
     lib.oracle_dx_window.argtypes = [P, i64, i32, i32, P, P, P, ctypes.c_double, i64, i64, P]
     lib.oracle_dft_real.restype = None
@@ -90,7 +92,7 @@ def _bind(lib):
     lib.oracle_max_threads.argtypes = []
     lib.oracle_image_list.restype = i64
     lib.oracle_image_list.argtypes = [P, P, P, ctypes.c_float, i32, ctypes.c_float, ctypes.c_float,
-                                      P, P, P, P]
+                                      P, P, P, P, P]
     lib.oracle_image_rir.restype = i64
     lib.oracle_image_rir.argtypes = [P, P, P, ctypes.c_float, i32, ctypes.c_float, ctypes.c_float,
                                      i64, P]
@@ -219,6 +221,17 @@ def dx_window(g_mics, rirs, L, i, alpha_i, m0, m1, lib=None):
     (lib or _load()).oracle_dx_window(_p(g), ny, J, int(i), _p(rir), _p(off), _p(_i64(L)), float(alpha_i),
                                       int(m0), int(m1), _p(dx))
     return dx
+
+
+def dh_window(x_i, g_j, L_ij, alpha_i, k0, k1, lib=None):
+    """Gradient of one RIR at taps [k0, k1): dh[k] = alpha_i sum_n g_j[n] x_i[n - k]
+    for k < L_ij, 0 beyond (x_i [Nx], g_j [Ny], any Ny)."""
+    x = _f64(x_i)
+    g = _f64(g_j)
+    out = np.zeros(int(k1) - int(k0))
+    (lib or _load()).oracle_dh_window(_p(x), x.shape[0], _p(g), g.shape[0], int(L_ij), float(alpha_i),
+                                      int(k0), int(k1), _p(out))
+    return out
 
 
 def mix_ola(x_sources, rirs, L, alpha, fft_n=0, lib=None):
@@ -416,16 +429,17 @@ def _f32(a) -> np.ndarray:
 
 def image_list(room, src, mic, refl, order=8, fs=16000.0, c0=343.0, lib=None):
     """Every image of one (source, microphone) pair in a room, virtual rooms in
-    (a, b, c) order with c fastest.  Returns dict(pos [V, 3], g, delay, amp)."""
+    (a, b, c) order with c fastest.  Returns dict(pos [V, 3], g, delay, amp,
+    travel): travel is d fs / c0 in samples (FP64) and delay = ceil(travel)."""
     V = (2 * int(order) + 1) ** 3
-    pos, amp = np.zeros((V, 3)), np.zeros(V)
+    pos, amp, travel = np.zeros((V, 3)), np.zeros(V), np.zeros(V)
     g, delay = np.zeros(V, np.int32), np.zeros(V, np.int64)
     n = (lib or _load()).oracle_image_list(_p(_f32(room)), _p(_f32(src)), _p(_f32(mic)), float(refl),
                                            int(order), float(fs), float(c0), _p(pos), _p(g), _p(delay),
-                                           _p(amp))
+                                           _p(amp), _p(travel))
     if n < 0:
         raise OracleError("invalid image-method arguments")
-    return dict(pos=pos, g=g, delay=delay, amp=amp)
+    return dict(pos=pos, g=g, delay=delay, amp=amp, travel=travel)
 
 
 def image_rir(room, src, mic, refl, n_h, order=8, fs=16000.0, c0=343.0, lib=None):
@@ -451,7 +465,7 @@ def image_rirs(geom, rir_len, order=8, fs=16000.0, c0=343.0, nthreads=0, lib=Non
     return h, valid.astype(bool)
 
 
-# ---- Sec. 4: log-Mel front end ------------------------------------------------
+# ---- Sec. 3: log-Mel front end ------------------------------------------------
 # the paper's features: 32 ms windows every 10 ms at 16 kHz, 128 Mel bands over
 # 125-7500 Hz, four frames stacked, every third stacked frame kept
 MEL_DEFAULTS = dict(n_fft=512, hop=160, fs=16000.0, n_mels=128, f_lo=125.0, f_hi=7500.0, floor=1e-6,

@@ -24,7 +24,7 @@
  *          of r^g_v / d_v delta[n - ceil(d_v fs / c0)] over the images of
  *          the source in (2K+1)^3 virtual rooms (its readings are listed
  *          above oracle_image_list)
- *   Sec. 4 the log-Mel front end applied after mixing (its readings are
+ *   Sec. 3 the log-Mel front end applied after mixing (its readings are
  *          listed above oracle_hz_to_mel).
  *
  * Readings taken where the paper is silent or garbled:
@@ -253,6 +253,22 @@ void oracle_dx_window(const double *g, int64_t n_y, int32_t J, int32_t i,
             sum += acc;
         }
         dx[m - m0] = alpha_i * sum;
+    }
+}
+
+/* Gradient of one RIR at taps k in [k0, k1) only:
+ * dh_ij[k] = alpha_i sum_{n < n_y} g_j[n] x_i[n - k] for k < L_ij, 0 for k >= L_ij
+ * (x_i[m] = 0 outside [0, n_x)).  x_i: [n_x]; g_j: [n_y]; dh: [k1 - k0] out. */
+void oracle_dh_window(const double *x_i, int64_t n_x, const double *g_j, int64_t n_y,
+                      int64_t L_ij, double alpha_i, int64_t k0, int64_t k1, double *dh)
+{
+    for (int64_t k = k0; k < k1; ++k) {
+        double acc = 0.0;
+        if (k < L_ij) {
+            int64_t nmax = n_x + k < n_y ? n_x + k : n_y;   /* n - k < n_x */
+            for (int64_t n = k; n < nmax; ++n) acc += g_j[n] * x_i[n - k];
+        }
+        dh[k - k0] = alpha_i * acc;
     }
 }
 
@@ -601,13 +617,14 @@ int oracle_forward_ola_batch(int32_t U, int32_t J, const int32_t *n_src, const i
  *    g_v = |a| + |b| + |c|;
  *  - all walls share one reflection coefficient r, 0 <= r < 1 (r = 0 keeps the
  *    direct path alone, r^0 = 1);
- *  - the delay ceil(d_v fs / c0) is an integer decision and is taken in FP32,
- *    the kernel's precision, as ceil(d_v * rate) with rate = fs / c0 rounded
- *    once: image coordinate, offset to the microphone, the three squares,
- *    their sum ((x + y) + z), the square root, the rate and the product are
- *    each one correctly rounded FP32 operation, so both implementations put
- *    every image on the same sample.  The amplitude r^g_v / d_v is FP64, from
- *    the same FP32 inputs;
+ *  - the delay is ceil(t_v) with t_v = d_v fs / c0 the travel time in
+ *    samples, evaluated in FP64 from the FP32 geometry (image coordinate,
+ *    offset to the microphone, distance, travel time), as is the amplitude
+ *    r^g_v / d_v.  Eq. 1 fixes no precision; where t_v lies within a few
+ *    FP32 rounding errors of an integer, an FP32 evaluation of the same real
+ *    number may land the image one sample later or earlier, and both taps
+ *    are readings of Eq. 1 (the travel time is returned so a caller can tell
+ *    those images apart);
  *  - an image whose delay is n_h or later lies outside the RIR and is dropped;
  *  - the source and the microphone lie strictly inside the room, and no image
  *    may sit at distance zero from the microphone (d_v > 0, Eq. 1).
@@ -623,21 +640,7 @@ static int image_geom_valid(const float *room, const float *src, const float *mi
     return refl >= 0.0f && refl < 1.0f;
 }
 
-/* offset from the microphone to the image coordinate of virtual room a, FP32 */
-static float image_offset_f32(int a, float len, float s, float m)
-{
-    float p;
-    if (a % 2 == 0) {
-        float base = (float)a * len;
-        p = base + s;
-    } else {
-        float base = (float)(a + 1) * len;
-        p = base - s;
-    }
-    return p - m;
-}
-
-/* the same in FP64 (for the amplitude) */
+/* offset from the microphone to the image coordinate of virtual room a */
 static double image_offset_f64(int a, double len, double s, double m)
 {
     double p = (a % 2 == 0) ? (double)a * len + s : (double)(a + 1) * len - s;
@@ -647,7 +650,8 @@ static double image_offset_f64(int a, double len, double s, double m)
 typedef struct {
     double pos[3];  /* image position (FP64) */
     int32_t g;      /* reflections */
-    int64_t delay;  /* ceil(d fs / c0), FP32 decision */
+    double travel;  /* d fs / c0 in samples (FP64) */
+    int64_t delay;  /* ceil(travel) */
     double amp;     /* r^g / d, FP64 */
     int ok;         /* 0: the image is at distance zero */
 } image_t;
@@ -657,24 +661,19 @@ static image_t image_eval(const float *room, const float *src, const float *mic,
 {
     image_t im;
     const int idx[3] = {a, b, c};
-    float d2 = 0.0f;
     double e2 = 0.0;
     for (int k = 0; k < 3; ++k) {
-        float e = image_offset_f32(idx[k], room[k], src[k], mic[k]);
-        float sq = e * e;
-        d2 = (k == 0) ? sq : d2 + sq;
         double ed = image_offset_f64(idx[k], room[k], src[k], mic[k]);
         im.pos[k] = ed + (double)mic[k];
         e2 += ed * ed;
     }
-    im.ok = d2 > 0.0f && e2 > 0.0;
-    float d = sqrtf(d2);
-    float rate = fs / c0;
-    float t = d * rate;
-    /* a travel time beyond any RIR length (huge rooms overflow to +inf) */
-    im.delay = t < 1e18f ? (int64_t)ceilf(t) : INT64_MAX;
+    im.ok = e2 > 0.0;
+    const double d = sqrt(e2);
+    im.travel = d * (double)fs / (double)c0;
+    /* a travel time beyond any RIR length */
+    im.delay = im.travel < 1e18 ? (int64_t)ceil(im.travel) : INT64_MAX;
     im.g = abs(a) + abs(b) + abs(c);
-    im.amp = im.ok ? pow((double)refl, (double)im.g) / sqrt(e2) : 0.0;
+    im.amp = im.ok ? pow((double)refl, (double)im.g) / d : 0.0;
     return im;
 }
 
@@ -683,7 +682,7 @@ static image_t image_eval(const float *room, const float *src, const float *mic,
  * arguments are invalid. */
 int64_t oracle_image_list(const float *room, const float *src, const float *mic, float refl,
                           int32_t order, float fs, float c0, double *pos, int32_t *g,
-                          int64_t *delay, double *amp)
+                          int64_t *delay, double *amp, double *travel)
 {
     if (order < 0 || !(fs > 0.0f) || !(c0 > 0.0f) || !isfinite(fs) || !isfinite(c0)) return -1;
     if (!image_geom_valid(room, src, mic, refl)) return -1;
@@ -697,6 +696,7 @@ int64_t oracle_image_list(const float *room, const float *src, const float *mic,
                 g[v] = im.g;
                 delay[v] = im.delay;
                 amp[v] = im.amp;
+                travel[v] = im.travel;
             }
     return v;
 }
@@ -744,7 +744,7 @@ void oracle_image_rirs(int64_t R, const float *geom, const int64_t *off, int32_t
 }
 
 /* ------------------------------------------------------------------------ */
-/* Sec. 4: the log-Mel front end after mixing                                */
+/* Sec. 3: the log-Mel front end after mixing                                */
 /* ------------------------------------------------------------------------ */
 /*
  * The paper's features: a single channel, 128 log-Mel energies from a 32 ms

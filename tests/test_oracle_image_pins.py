@@ -5,8 +5,8 @@ come from the oracle itself:
   a time (the construction Sec. 2 describes), gives every image position and
   its reflection count;
 * the paper's count of 17 x 17 x 17 = 4913 virtual rooms;
-* Eq. 1's ceiling delay, checked against FP64 distances from that lattice and
-  on geometries where d fs / c0 is an exact number;
+* Eq. 1's ceiling delay, the ceiling of the FP64 travel time d fs / c0 from
+  that lattice, and exact on geometries where d fs / c0 is an exact number;
 * closed forms: r = 0 leaves a single delta 1/d at ceil(d fs / c0);
 * reciprocity (source and microphone swapped give the same response) on
   geometries whose coordinates are exact in FP32;
@@ -90,13 +90,13 @@ def test_delays_are_ceilings_of_the_travel_time(fs, c0):
     lst = oracle.image_list(room, src, mic, 0.6, order=order, fs=fs, c0=c0)
     m = _f32(mic)
     t = np.array([np.linalg.norm(lat[k][0] - m) * _f32([fs])[0] / _f32([c0])[0] for k in _rooms(order)])
+    # the oracle's FP64 travel time is the lattice's (up to FP64 rounding of two
+    # different constructions) and its delay is that travel time's ceiling
+    np.testing.assert_allclose(lst["travel"], t, rtol=1e-13, atol=0)
     d = lst["delay"]
-    # the decision is FP32: allow a slack of a few FP32 ulps of t around integers
-    tol = 8 * np.finfo(np.float32).eps * t
-    assert np.all(d - 1 < t + tol) and np.all(t - tol <= d)
     exact = d == np.ceil(t)
-    assert np.all(exact | (np.abs(t - np.round(t)) <= tol))
-    assert exact.mean() > 0.99
+    assert np.all(exact | (np.abs(t - np.round(t)) <= 1e-9 * t))
+    assert exact.mean() > 0.9999
 
 
 def test_amplitudes_are_reflection_power_over_distance():

@@ -37,6 +37,8 @@ MUTANTS = [
     ("window_dx_convolves",
      "for (int64_t k = 0; k < Lij && m + k < n_y; ++k) acc += h[k] * gj[m + k];\n            sum += acc;",
      "for (int64_t k = 0; k < Lij && m >= k; ++k) acc += h[k] * gj[m - k];\n            sum += acc;"),
+    ("window_dh_drops_first_term", "for (int64_t n = k; n < nmax; ++n)", "for (int64_t n = k + 1; n < nmax; ++n)"),
+    ("window_dh_ignores_cut", "        if (k < L_ij) {\n            int64_t nmax", "        if (1) {\n            int64_t nmax"),
     ("window_mix_ignores_gain", "sum += alpha[i] * acc;", "sum += acc;"),
     ("dh_transposed_operands", "acc += gj[n] * xi[n - k];", "acc += gj[n - k] * xi[n];"),
     ("dh_missing_gain", "dhij[k] = alpha[i] * acc;", "dhij[k] = acc;"),
@@ -50,17 +52,17 @@ MUTANTS = [
 
 # mistakes in the image-method RIR (Eq. 1), run against its own pin file
 IMAGE_MUTANTS = [
-    ("image_odd_parity_flipped", "if (a % 2 == 0) {", "if (a % 2 != 0) {"),
+    ("image_odd_parity_flipped", "(a % 2 == 0) ? (double)a", "(a % 2 != 0) ? (double)a"),
     ("image_f64_odd_coordinate", "(double)(a + 1) * len - s", "(double)a * len - s"),
     ("image_g_drops_axis", "im.g = abs(a) + abs(b) + abs(c);", "im.g = abs(a) + abs(b);"),
-    ("image_delay_floor", "(int64_t)ceilf(t)", "(int64_t)floorf(t)"),
-    ("image_delay_round", "(int64_t)ceilf(t)", "(int64_t)roundf(t)"),
-    ("image_amp_inverse_square", "/ sqrt(e2) : 0.0;", "/ e2 : 0.0;"),
-    ("image_fs_c0_swapped", "float rate = fs / c0;", "float rate = c0 / fs;"),
+    ("image_delay_floor", "(int64_t)ceil(im.travel)", "(int64_t)floor(im.travel)"),
+    ("image_delay_round", "(int64_t)ceil(im.travel)", "(int64_t)round(im.travel)"),
+    ("image_amp_inverse_square", "(double)im.g) / d : 0.0;", "(double)im.g) / e2 : 0.0;"),
+    ("image_fs_c0_swapped", "d * (double)fs / (double)c0;", "d * (double)c0 / (double)fs;"),
     ("image_loop_short", "for (int c = -order; c <= order; ++c) {\n                image_t im",
      "for (int c = -order; c < order; ++c) {\n                image_t im"),
     ("image_drops_last_sample", "if (im.delay < n_h) {", "if (im.delay < n_h - 1) {"),
-    ("image_d2_misses_z", "d2 = (k == 0) ? sq : d2 + sq;", "d2 = (k == 0) ? sq : (k == 1 ? d2 + sq : d2);"),
+    ("image_d2_misses_z", "e2 += ed * ed;", "if (k < 2) e2 += ed * ed;"),
 ]
 
 # mistakes in the log-Mel front end, run against its own pin file

@@ -509,3 +509,19 @@ def test_windows_equal_numpy_slices():
         for m0, m1 in ((0, 60), (200, 400)):
             np.testing.assert_allclose(oracle.dx_window(g, rirs, L, i, alpha[i], m0, m1), ref[m0:m1],
                                        rtol=1e-12, atol=1e-12)
+
+
+def test_dh_window_equals_numpy_correlate_slices():
+    # dh[k] = alpha sum_n g[n] x[n - k]: numpy.correlate(g, x, "full") holds
+    # sum_n g[n + l] x[n] at index l + len(x) - 1, so lag k is at k + nx - 1
+    r = _rng(22)
+    for nx, ny in ((300, 300), (300, 380), (257, 257)):
+        x = r.standard_normal(nx)
+        g = r.standard_normal(ny)
+        L, alpha = 120, 0.83
+        c = np.correlate(g, x, "full")
+        ref = np.zeros(ny)
+        ref[:L] = alpha * c[nx - 1:nx - 1 + L]
+        for k0, k1 in ((0, 40), (100, 130), (115, 200)):
+            np.testing.assert_allclose(oracle.dh_window(x, g, L, alpha, k0, k1), ref[k0:k1],
+                                       rtol=1e-12, atol=1e-12)
