@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 from paper_1712_03439_gb300 import synth
+from parity_checks import close_vec, grads_close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -100,17 +101,7 @@ def test_full_output_backward_matches_oracle(eta, seg, bseg, fft_sizes):
     L = oracle.truncate_batch(b, eta)["L"]
     ref = oracle.backward(b, L, gains.astype(np.float64), gy, output_mode=1)
 
-    def close(a, r, what):
-        nr = np.linalg.norm(r)
-        assert np.linalg.norm(a.astype(np.float64) - r) <= REL_L2 * max(nr, 1e-30), what
-
-    xo, ro = b.x_offsets(), b.rir_offsets()
-    for s in range(S):
-        close(got["dx"][xo[s]:xo[s + 1]], ref["dx"][xo[s]:xo[s + 1]], f"dx[{s}]")
-    for r in range(b.num_rirs):
-        close(got["dh"][ro[r]:ro[r + 1]], ref["dh"][ro[r]:ro[r + 1]], f"dh[{r}]")
-        assert np.all(got["dh"][ro[r] + L[r]:ro[r + 1]] == 0)
-    np.testing.assert_allclose(got["da"], ref["dalpha"], rtol=REL_L2, atol=REL_L2 * np.abs(ref["dalpha"]).max())
+    grads_close(b, ref, L, dx=got["dx"], dh=got["dh"], dalpha=got["da"])
 
 
 def test_full_output_prefix_is_the_same_output():

@@ -9,6 +9,7 @@ import pytest
 
 import oracle
 from paper_1712_03439_gb300 import synth
+from parity_checks import close_vec, grads_close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -72,13 +73,7 @@ def test_partitioned_forward_and_backward_match_oracle(gain_mode, fft_sizes):
     plan.filter_mix_backward(dev(gy), x, gains, gx, gr, gg)
     plan.sync_status()
     bw = oracle.backward(b, b.rir_len.astype(np.int64), alpha, gy.astype(np.float64))
-    xo, ro = b.x_offsets(), b.rir_offsets()
-    gxv, grv = gx.cpu().numpy(), gr.cpu().numpy()
-    for s in range(S):
-        assert rel_l2(gxv[xo[s]:xo[s + 1]], bw["dx"][xo[s]:xo[s + 1]]) <= REL, f"dx[{s}]"
-    for r in range(b.num_rirs):
-        assert rel_l2(grv[ro[r]:ro[r + 1]], bw["dh"][ro[r]:ro[r + 1]]) <= REL, f"dh[{r}]"
-    np.testing.assert_allclose(gg.cpu().numpy(), bw["dalpha"], rtol=REL, atol=REL * np.abs(bw["dalpha"]).max())
+    grads_close(b, bw, b.rir_len, dx=gx.cpu().numpy(), dh=gr.cpu().numpy(), dalpha=gg.cpu().numpy())
     q = plan.query()
     assert np.all(q["log2_n"] > 0)
 

@@ -7,6 +7,7 @@ import pytest
 
 import oracle
 from paper_1712_03439_gb300 import synth
+from parity_checks import close_vec, grads_close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -64,10 +65,9 @@ def test_stream_batches_cover_queue_within_budget_and_match_oracle():
         close(out["y"][yo[k]:yo[k + 1]], ref["y"], f"y batch {bi}")
         gref = oracle.backward(one, ref["L"], out["gains"][si[k]:si[k + 1]].astype(np.float64),
                                grads[bi][yo[k]:yo[k + 1]])
-        close(out["grad_x"][xo[si[k]]:xo[si[k + 1]]], gref["dx"], f"dx batch {bi}")
-        close(out["grad_rir"][ro[ri[k]]:ro[ri[k + 1]]], gref["dh"], f"dh batch {bi}")
-        np.testing.assert_allclose(out["grad_gains"][si[k]:si[k + 1]], gref["dalpha"], rtol=REL_L2,
-                                   atol=REL_L2 * np.abs(gref["dalpha"]).max())
+        grads_close(one, gref, ref["L"], dx=out["grad_x"][xo[si[k]]:xo[si[k + 1]]],
+                    dh=out["grad_rir"][ro[ri[k]]:ro[ri[k + 1]]], dalpha=out["grad_gains"][si[k]:si[k + 1]],
+                    what=f"batch {bi} ")
 
 
 def test_admission_estimate_bounds_the_real_footprint():

@@ -5,8 +5,9 @@
   autograd function with an L2 loss; the oracle checks sampled utterances;
 * long reverberant multi-mic: 30 s utterances, 4 sources, 8 mics, RT60
   0.8-1.2 s, cut-offs of 10, 20 and 30 dB and none (two utterances of that shape);
-  lengths exact, outputs and dx on sampled windows against the oracle's
-  window forms, gradients by the adjoint identities over the whole batch;
+  lengths exact, outputs, dx and dh (sampled RIRs) on sampled windows
+  against the oracle's window forms, and the adjoint identities over the
+  whole batch;
   without a cut-off (RIRs up to 19200 taps, beyond what one block of the
   largest FFT size reaches) through the partitioned convolution.
 """
@@ -161,3 +162,13 @@ def test_long_reverberant_multimic(long_batch, eta):
                 s = si[u] + i
                 dxw = oracle.dx_window(gu, rirs, Lu, i, a_u[i], m0, m0 + W)
                 close_channel(gxv[xo[s] + m0:xo[s] + m0 + W], dxw, f"dx u={u} i={i} m0={m0}")
+        # dh of sampled RIRs element by element on tap windows: the start, the middle,
+        # the window across the cut-off (zero from L on) and the last taps
+        WH = 256
+        for q in sorted({0, 5, 13, I * J - 1}):
+            r, i, j = ri[u] + q, q // J, q % J
+            nh, Lr = int(b.rir_len[r]), int(L[r])
+            for k0 in sorted({0, Lr // 2, max(Lr - WH // 2, 0), max(nh - WH, 0)}):
+                k1 = min(k0 + WH, nh)
+                dhw = oracle.dh_window(xs[i], gu[j], Lr, a_u[i], k0, k1)
+                close_channel(grv[ro[r] + k0:ro[r] + k1], dhw, f"dh u={u} r={q} k0={k0}")
