@@ -159,7 +159,7 @@ class ClockSampler:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.FIELDS}",
-                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                       "--format=csv,noheader,nounits", "-lms", "20"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
@@ -246,6 +246,26 @@ def _plain_inputs(torch, dev, b, x=None, rir=None, snr=None, gy=None):
 # ---------------------------------------------------------------------------
 # reference arm: the FP64 CPU oracle on a bounded sample
 # ---------------------------------------------------------------------------
+def host_cpu() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def oracle_sample_step(oracle, sub, g):
     out = oracle.forward(sub, ETA_DB)
     oracle.backward(sub, out["L"], out["alpha"], g)
@@ -258,9 +278,13 @@ def run_reference(args):
     if rank != 0:
         return 0
     b = synth.config_home()
-    utts = b.subset(range(3))
     cores = oracle.max_threads()
-    # the sample per step: the first T seconds of utterances 0-2 (all sources, whole RIRs),
+    # as many utterances as the oracle has threads (at least 16): its forward runs one
+    # work item per (utterance, microphone) and its backward one per source, so every
+    # core has work
+    n_utts = min(b.num_utts, max(16, cores))
+    utts = b.subset(range(n_utts))
+    # the sample per step: the first T seconds of those utterances (all sources, whole RIRs),
     # T chosen from a one-second calibration so that the K + W steps take about REF_BUDGET_S
     # (the direct form's cost grows linearly with T)
     cal = utts.excerpt(synth.FS)
@@ -279,14 +303,16 @@ def run_reference(args):
         oracle_sample_step(oracle, sub, g)
     dt = (time.perf_counter() - t0) / args.steps
     v = sub.audio_seconds() / dt
-    sample = (f"the first {n / synth.FS:.2f} s of utterances 0-2 of the home-256 batch "
+    sample = (f"the first {n / synth.FS:.2f} s of utterances 0-{n_utts - 1} of the home-256 batch "
               f"({sub.audio_seconds():.2f} s of audio, {int(sub.num_sources.sum())} sources, whole RIRs), "
-              f"forward + backward, direct FP64; the excerpt length keeps the run near {REF_BUDGET_S:.0f} s")
+              f"forward + backward, direct FP64 on {cores} threads of {host_cpu()}; "
+              f"the excerpt length keeps the run near {REF_BUDGET_S:.0f} s")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": DATA, "config": {"workload": WORKLOAD, "sample": sample},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "nproc": os.cpu_count(), "cpu_model": host_cpu()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -503,15 +529,17 @@ def run_ours(args):
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         import oracle
-        sub = b.subset(range(16))
+        cores = oracle.max_threads()
+        n_cpu = min(b.num_utts, max(16, cores))
+        sub = b.subset(range(n_cpu))
         g = synth.grad_like(99, sub.y_size)
         t0 = time.perf_counter()
         oracle_sample_step(oracle, sub, g)
         dt = time.perf_counter() - t0
-        cpu = {"value": sub.audio_seconds() / dt, "unit": UNIT, "cores": oracle.max_threads(),
-               "kind": "oracle",
-               "sample": f"utterances 0-15 of the home-256 batch ({sub.audio_seconds():.1f} s of audio), "
-                         f"forward + backward, FP64 direct convolution, {dt:.1f} s wall"}
+        cpu = {"value": sub.audio_seconds() / dt, "unit": UNIT, "cores": cores,
+               "kind": "oracle", "nproc": os.cpu_count(), "cpu_model": host_cpu(),
+               "sample": f"utterances 0-{n_cpu - 1} of the home-256 batch ({sub.audio_seconds():.1f} s of audio), "
+                         f"forward + backward, FP64 direct convolution on {cores} threads, {dt:.1f} s wall"}
 
     # truncate, power, plan, spectra, forward, fix-up | backward, finalize
     kernels_per_step = (3 + 2 * n_sizes + 1) + (n_sizes + 1)
@@ -855,7 +883,7 @@ def mel_work(num_out, rows_total, frames_total, n_mels=128, stack=4):
 
 
 def run_mel(args):
-    """Log-Mel front end (Sec. 4: 128 filters, 32 ms / 10 ms, 125-7500 Hz, four
+    """Log-Mel front end (Sec. 3: 128 filters, 32 ms / 10 ms, 125-7500 Hz, four
     frames stacked, every third kept) on microphone 0 of the home-256 mix."""
     import torch
     from paper_1712_03439_gb300 import Plan, build, synth
