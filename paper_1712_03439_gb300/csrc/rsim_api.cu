@@ -485,9 +485,10 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     for (int m = kMinLog; m <= kMaxLog; ++m)
         if ((mask >> m) & 1) max_log = m;
     // forward tiles: short segments balance the load across SMs; backward
-    // tiles: longer ones amortise the per-tile dh transforms
+    // tile slots: an utterance may be cut into at most one backward tile per
+    // bseg_len samples (the planner picks how many on the device)
     int64_t seg_len = std::max<int64_t>(d->segment_len, (int64_t)1 << max_log);
-    int64_t bseg_len = d->bwd_segment_len > 0 ? d->bwd_segment_len : 65536;
+    int64_t bseg_len = d->bwd_segment_len > 0 ? d->bwd_segment_len : 16384;
     bseg_len = std::max<int64_t>(bseg_len, (int64_t)1 << max_log);
     int64_t nseg = 0, nbseg = 0;
     for (int u = 0; u < U; ++u) {
@@ -577,7 +578,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     void *p_srcutt, *p_rirutt;
     void *p_nsrc, *p_nx, *p_ny, *p_src0, *p_rir0, *p_seg0, *p_segutt, *p_xoff, *p_yoff, *p_roff, *p_rlen,
         *p_dhpoff, *p_tuning, *p_L, *p_logN, *p_hop, *p_lmax, *p_nblk, *p_pow, *p_err, *p_list,
-        *p_count, *p_next, *p_Hc, *p_tails, *p_dhp, *p_dap, *p_melrow, *p_ones, *p_rsrc = nullptr,
+        *p_count, *p_next, *p_Hc, *p_tails, *p_dhp, *p_dap, *p_melrow, *p_ones, *p_bnt, *p_rsrc = nullptr,
         *p_rdst = nullptr, *p_rrir = nullptr, *p_ry = nullptr;
     void* p_tw[2 * kNumBuckets] = {};
     const int64_t cap = std::max<int64_t>(std::max<int64_t>(nbseg * kMaxSources, nseg), R);
@@ -620,6 +621,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     pieces.push_back({&p_hop, sizeof(int32_t) * U});
     pieces.push_back({&p_lmax, sizeof(int32_t) * U});
     pieces.push_back({&p_nblk, sizeof(int32_t) * U});
+    pieces.push_back({&p_bnt, sizeof(int32_t) * U});
     pieces.push_back({&p_pow, sizeof(double) * S * CH});
     pieces.push_back({&p_err, sizeof(int32_t) * 4});
     pieces.push_back({&p_list, sizeof(int32_t) * kNumLists * kNumBuckets * cap});
@@ -739,7 +741,8 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     B.src_utt = (const int32_t*)p_srcutt; B.rir_utt = (const int32_t*)p_rirutt;
     B.dhp_off = (const int64_t*)p_dhpoff; B.tuning = (const float*)p_tuning;
     B.L = (int32_t*)p_L; B.logN = (int32_t*)p_logN; B.hop = (int32_t*)p_hop;
-    B.Lmax = (int32_t*)p_lmax; B.nblk = (int32_t*)p_nblk;
+    B.Lmax = (int32_t*)p_lmax; B.nblk = (int32_t*)p_nblk; B.bnt = (int32_t*)p_bnt;
+    for (int b = 0; b < kNumBuckets; ++b) B.bgrid[b] = grid_bwd[b];
     B.pow_part = (double*)p_pow; B.CH = CH; B.err = (int32_t*)p_err;
     {
         const char* w = std::getenv("RSIM_TEST_WITHHOLD_BULK_COPY");   // test hook, off by default

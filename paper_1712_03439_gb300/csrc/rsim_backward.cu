@@ -10,6 +10,7 @@
 // Neither wraps around: lags and positions stay below hop + L_max - 1 = N.
 #include "rsim_fft.cuh"
 #include "rsim_internal.cuh"
+#include "rsim_tmem.cuh"
 
 namespace rsim {
 
@@ -136,13 +137,12 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
         if (code < 0) break;
         const int g = code / kMaxSources, i = code % kMaxSources;
         const int u = B.bseg_utt[g];
-        const int64_t sgi = g - B.bseg0[u];
         const int64_t nx = B.n_x[u];
         const int64_t ny = B.n_y[u];
         const int hop = B.hop[u];
         const int lmax = B.Lmax[u];
         int64_t b0, b1;
-        segment_blocks(sgi, B.bseg_len, hop, B.nblk[u], &b0, &b1);
+        tile_blocks(B, g, u, &b0, &b1);
         if (b0 >= b1) continue;
         const int J = B.J;
         const int sb = B.src0[u], rb = B.rir0[u];
@@ -339,23 +339,322 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
 }
 
 // ---------------------------------------------------------------------------
+// K7 (N <= 8192): persistent over (block run, source group) tiles, RIR-gradient
+// accumulators in TMEM
+// ---------------------------------------------------------------------------
+// A tile is a run of consecutive blocks [b0, b1) of one utterance (chosen by
+// the planner so that tiles cost about the same) and up to IG of its sources.
+// Per block b and microphone group j0 .. j0 + jn - 1:
+//   G_j = rFFT_N(g_j[b hop, b hop + N))          once per microphone, registers
+//   for each source i of the tile:
+//     X_i = rFFT_N(x_i block)                     once per source
+//     W_ij += conj(X_i) G_j                       accumulators in TMEM
+//     C_i = sum_j conj(Hc_ij) G_j                 RIR spectra from L2
+//     dalpha_i += <c_i, x_i block> = sum_k C_i conj(X_i) (Parseval)
+//     dx_i block = alpha_i irFFT_N(C_i)[0, hop)  (added to earlier groups')
+// and at the end of the run dh partial_ij = irFFT_N(W_ij)[0, L_ij).  That is
+// 2I + J transforms per block, the method's minimum (a per-source tile
+// recomputes every G_j per source: I (J + 2)).  The I x jn accumulators of a
+// tile do not fit in registers: each is a half spectrum spread over the CTA
+// like the transforms (2E floats per thread), held in TMEM columns of the
+// thread's own lane and read and written once per block with tcgen05.ld/st.
+// Transform inputs are staged as in the per-source kernel: one bulk copy per
+// input into one of two shared-memory stages, completing on an mbarrier with
+// a bounded wait, issued while the previous transform runs; exchanges
+// alternate between two buffers (one barrier each).
+template <int M>
+struct BwdTmCfg {
+    static constexpr int E = M == 4096 ? 16 : e_for(M);
+    static constexpr int T = M / E;
+    static constexpr int kMinBlocks = M <= 2048 ? 2 : 1;
+    static constexpr int kWCols = 2 * E * (T / 128);          // TMEM columns per accumulator
+    static constexpr int kCols = kMinBlocks == 2 ? 256 : 512;  // TMEM columns per CTA
+    static constexpr int IG = kCols / (kWCols * kJG);          // sources per tile
+    static constexpr size_t a16(size_t v) { return (v + 15) / 16 * 16; }
+    static constexpr size_t SM_LEN = a16(sizeof(float2) * padded_len(M));
+    static constexpr size_t ST_LEN = sizeof(float) * (2 * M + 8);   // + room for the chunk offset
+    static constexpr size_t o_sm = 0;
+    static constexpr size_t o_st = o_sm + 2 * SM_LEN;
+    static constexpr size_t o_tw = a16(o_st + 2 * ST_LEN);
+    static constexpr size_t bytes = a16(o_tw + sizeof(float2) * FftPlan<M, E>::TW_LEN);
+    static_assert(T % 128 == 0, "every TMEM lane quadrant holds whole runs of columns");
+    static_assert(IG >= 1 && IG <= kMaxSources, "source group");
+};
+
+template <int M, bool MG>
+__global__ void __launch_bounds__(BwdTmCfg<M>::T, BwdTmCfg<M>::kMinBlocks)
+k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const float* __restrict__ x,
+              const float* __restrict__ gains, const float2* __restrict__ Hc, float* __restrict__ dx,
+              float* __restrict__ dhp, float* __restrict__ dap, const float2* __restrict__ twg) {
+    using L = BwdTmCfg<M>;
+    constexpr int E = L::E;
+    constexpr int T = L::T;
+    constexpr int IG = L::IG;
+    constexpr bool kPaired = PairedSplit<M, E>::ok;   // split in registers (paired layout)
+    static_assert(IG == bwd_src_group(ilog2(M) + 1), "the planner's source groups");
+    using Pl = FftPlan<M, E>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Exch<2> ex{reinterpret_cast<float2*>(smem_raw + L::o_sm),
+               reinterpret_cast<float2*>(smem_raw + L::o_sm + L::SM_LEN), 0};
+    float* st0 = reinterpret_cast<float*>(smem_raw + L::o_st);
+    __shared__ double sd[32];
+    __shared__ int slot;
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_base;
+    const int t = threadIdx.x;
+    if (t < 32) {                                // warp 0 takes the CTA's TMEM columns
+        tmem_alloc(&tmem_base, L::kCols);
+        tmem_relinquish();
+    }
+    if (t == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        mbar_init_fence();
+    }
+    float2* tws = reinterpret_cast<float2*>(smem_raw + L::o_tw);
+    for (int k = t; k < Pl::TW_LEN; k += T) tws[k] = twg[k];
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const float2* tw = tws;
+    const float2* wsplit = tw + Pl::OFF_SPLIT;
+    // accumulator s of this thread: columns s * kWCols + (its run) of its lane
+    const uint32_t tacc = tmem_thread_addr<E>(tmem_base, t);
+    auto wslot = [&](int s) { return tacc + (uint32_t)(s * L::kWCols); };
+    uint32_t ph = 0;                             // bit b: parity of the next phase of stage b
+    int off0 = 0, off1 = 0;                      // float offset of the data in stage 0 / 1
+    bool bad = false;                            // a bounded wait ran out (no new copies then)
+    // first bin of this thread's pairs: t (pair layout) or its paired butterfly
+    const int kt = kPaired ? paired_butterfly<T>(t) : t;
+    int sc = 0;                                  // stage holding the next transform input
+    auto stage = [&](int k) { return st0 + k * (2 * M + 8); };
+    for (;;) {
+        const int code = pop_job_b(Q, kListBwd, bucket, &slot);
+        if (code < 0) break;
+        const int g = code / kMaxSources, i0 = code % kMaxSources;
+        const int u = B.bseg_utt[g];
+        const int64_t nx = B.n_x[u];
+        const int64_t ny = B.n_y[u];
+        const int hop = B.hop[u];
+        const int lmax = B.Lmax[u];
+        int64_t b0, b1;
+        tile_blocks(B, g, u, &b0, &b1);
+        if (b0 >= b1) continue;
+        const int J = B.J;
+        const int I = min(IG, B.n_src[u] - i0);
+        const int sb = B.src0[u] + i0, rb = B.rir0[u];
+        float da[IG];                            // <c_i, x_i> over the run, per source
+#pragma unroll
+        for (int q = 0; q < IG; ++q) da[q] = 0.f;
+        for (int j0 = 0; j0 < J; j0 += kJG) {
+            const int jn = min(kJG, J - j0);
+            const int nsteps = jn + I;           // transforms per block: the G_j, then the X_i
+            // queue the input of step k of block b into stage kk
+            auto stage_step = [&](int kk, int64_t b, int k) {
+                const int64_t p = b * hop;
+                const float* src;
+                int64_t len;
+                if (k < jn) {
+                    src = gy + B.yoff[u] + (int64_t)(j0 + k) * ny + p;
+                    len = min((int64_t)(hop + lmax - 1), ny - p);
+                } else {
+                    src = x + B.xoff[sb + k - jn] + p;
+                    len = min((int64_t)hop, nx - p);
+                }
+                const int off = stage_real_bulk<M, E>(stage(kk), src, len, &mbar[kk], t, B.test_withhold != 0);
+                if (kk) off1 = off; else off0 = off;
+            };
+            // takes the staged input of step k into v and queues the next step's
+            auto next_input = [&](float2 (&v)[E], int64_t b, int k) {
+                if (!bad && !mbar_wait_bounded(&mbar[sc], (ph >> sc) & 1u)) {
+                    // give the copy one more bounded chance to land before the
+                    // stage is abandoned, so none is left in flight at exit
+                    mbar_wait_bounded(&mbar[sc], (ph >> sc) & 1u, 100000000ull);
+                    bad = true;
+                }
+                ph ^= 1u << sc;
+                load_staged_at<M, E>(v, stage(sc), sc ? off1 : off0, t);
+                if (!bad) {
+                    if (k + 1 < nsteps) stage_step(sc ^ 1, b, k + 1);
+                    else if (b + 1 < b1) stage_step(sc ^ 1, b + 1, 0);
+                }
+                sc ^= 1;
+            };
+            // zero this group's accumulators (no other thread reads this thread's columns)
+            {
+                float2 z[E];
+#pragma unroll
+                for (int e = 0; e < E; ++e) z[e] = make_float2(0.f, 0.f);
+                for (int s2 = 0; s2 < I * kJG; ++s2) tmem_store<E>(wslot(s2), z);
+            }
+            __syncthreads();                     // stages are free
+            stage_step(sc, b0, 0);
+            // the stage's ragged ends and zero fill are plain stores by every thread:
+            // visible to all readers after this barrier (later inputs are staged a whole
+            // transform, barriers included, before they are read)
+            __syncthreads();
+            for (int64_t b = b0; b < b1; ++b) {
+                const int64_t pos = b * hop;
+                float2 G[kJG][E];
+                // one loop body for every transform of the block (the transform code
+                // is emitted once)
+#pragma unroll 1
+                for (int k = 0; k < nsteps; ++k) {
+                    float2 v[E], Z[E];
+                    next_input(v, b, k);
+                    if constexpr (kPaired) {
+                        rfft_paired<M, E, false>(Z, v, ex, tw, t, kt);
+                    } else {
+                        const float2* z = rfft_x<M, E, false>(v, ex, tw, t);
+                        split_forward<M, E>(Z, z, wsplit, t);
+                    }
+                    if (k < jn) {
+                        if (k == 0) {
+#pragma unroll
+                            for (int e = 0; e < E; ++e) G[0][e] = Z[e];
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < E; ++e) G[1][e] = Z[e];
+                        }
+                        continue;
+                    }
+                    const int i = k - jn;        // source of the tile; Z holds X_i
+                    // W_ij += conj(X_i) G_j
+#pragma unroll 1
+                    for (int jj = 0; jj < jn; ++jj) {
+                        float2 Wv[E];
+                        tmem_load<E>(Wv, wslot(i * kJG + jj));
+#pragma unroll
+                        for (int q = 0; q < E / 2; ++q) {
+                            const float2 ga = jj ? G[1][2 * q] : G[0][2 * q];
+                            const float2 gb = jj ? G[1][2 * q + 1] : G[0][2 * q + 1];
+                            if (kt + q * T == 0) {   // slot 0 holds two real bins
+                                Wv[0].x += Z[0].x * ga.x;
+                                Wv[0].y += Z[0].y * ga.y;
+                            } else {
+                                Wv[2 * q] = cadd(Wv[2 * q], cmulc(Z[2 * q], ga));
+                            }
+                            Wv[2 * q + 1] = cadd(Wv[2 * q + 1], cmulc(Z[2 * q + 1], gb));
+                        }
+                        tmem_store<E>(wslot(i * kJG + jj), Wv);
+                    }
+                    // C = sum_j conj(H_ij) G_j
+                    float2 C[E];
+#pragma unroll
+                    for (int e = 0; e < E; ++e) C[e] = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int jj = 0; jj < kJG; ++jj) {
+                        if (jj >= jn) break;
+                        const float4* Hg = reinterpret_cast<const float4*>(
+                            Hc + (int64_t)(rb + (i0 + i) * J + j0 + jj) * B.MMAX);
+#pragma unroll
+                        for (int q = 0; q < E / 2; ++q) {
+                            const int kb = kt + q * T;
+                            const float4 hh = __ldg(Hg + kb);
+                            const float2 ha = make_float2(hh.x, hh.y), hb = make_float2(hh.z, hh.w);
+                            const float2 ga = jj ? G[1][2 * q] : G[0][2 * q];
+                            const float2 gb = jj ? G[1][2 * q + 1] : G[0][2 * q + 1];
+                            if (kb == 0) {
+                                C[0].x += ha.x * ga.x;
+                                C[0].y += ha.y * ga.y;
+                            } else {
+                                C[2 * q] = cadd(C[2 * q], cmulc(ha, ga));
+                            }
+                            C[2 * q + 1] = cadd(C[2 * q + 1], cmulc(hb, gb));
+                        }
+                    }
+                    // <c, x_block> by Parseval on the half spectra (x_block is zero
+                    // beyond its length): bins 0 and N/2 once, every other bin twice
+                    float p = 0.f;
+#pragma unroll
+                    for (int q = 0; q < E / 2; ++q) {
+                        const int kb = kt + q * T;
+                        const float p0 = C[2 * q].x * Z[2 * q].x + C[2 * q].y * Z[2 * q].y;
+                        const float p1 = C[2 * q + 1].x * Z[2 * q + 1].x + C[2 * q + 1].y * Z[2 * q + 1].y;
+                        p += (kb == 0 ? p0 : 2.f * p0) + 2.f * p1;
+                    }
+#pragma unroll
+                    for (int q = 0; q < IG; ++q) da[q] += (q == i) ? p : 0.f;
+                    if constexpr (kPaired) irfft_paired<M, E>(v, C, ex, tw, t, kt);
+                    else irfft_x<M, E, false>(v, C, ex, tw, t);
+                    if (dx) {
+                        // samples [0, min(hop, Nx - pos)) of the block; the first microphone
+                        // group writes, later groups add; pairs go out as one 8-byte store
+                        const float a = __ldg(gains + sb + i);
+                        float* dst = dx + B.xoff[sb + i] + pos;
+                        const int ilim = (int)min((int64_t)hop, nx - pos);
+                        const bool pairs = ((reinterpret_cast<uintptr_t>(dst) & 7) == 0) && j0 == 0;
+#pragma unroll
+                        for (int q = 0; q < E; ++q) {
+                            const int n = 2 * (t + q * T);
+                            const float d0 = a * v[q].x, d1 = a * v[q].y;
+                            if (pairs && n + 1 < ilim) {
+                                *reinterpret_cast<float2*>(dst + n) = make_float2(d0, d1);
+                            } else if constexpr (MG) {
+                                if (n < ilim) dst[n] = (j0 == 0) ? d0 : dst[n] + d0;
+                                if (n + 1 < ilim) dst[n + 1] = (j0 == 0) ? d1 : dst[n + 1] + d1;
+                            } else {
+                                if (n < ilim) dst[n] = d0;
+                                if (n + 1 < ilim) dst[n + 1] = d1;
+                            }
+                        }
+                    }
+                }
+            }
+            // dh partials of this run for the tile's sources and this microphone group
+#pragma unroll 1
+            for (int s2 = 0; s2 < I * jn; ++s2) {
+                const int i = s2 / jn, jj = s2 - i * jn;
+                float2 v[E], Wv[E];
+                tmem_load<E>(Wv, wslot(i * kJG + jj));
+                if constexpr (kPaired) irfft_paired<M, E>(v, Wv, ex, tw, t, kt);
+                else irfft_x<M, E, false>(v, Wv, ex, tw, t);
+                const int r = rb + (i0 + i) * J + j0 + jj;
+                const int Lr = B.L[r];
+                float* out = dhp + B.dhp_off[g] + (B.roff[r] - B.roff[rb]);
+#pragma unroll
+                for (int q = 0; q < E; ++q) {
+                    const int n = 2 * (t + q * T);
+                    if (n < Lr) out[n] = v[q].x;
+                    if (n + 1 < Lr) out[n + 1] = v[q].y;
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < IG; ++q) {
+            if (q >= I) break;
+            const double tot = block_sum_d((double)da[q], sd);
+            if (t == 0) dap[(int64_t)g * kMaxSources + i0 + q] = (float)tot;
+        }
+        if (__syncthreads_or(bad)) {             // a copy never completed: report and stop
+            if (t == 0) atomicOr(B.err, kErrWaitTimeout);
+            break;
+        }
+    }
+    // every thread's TMEM accesses are complete (each store waited); order them
+    // before warp 0 frees the columns
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (t < 32) tmem_dealloc(tmem_base, L::kCols);
+}
+
+// ---------------------------------------------------------------------------
 // K8: deterministic reduction of the per-segment partials
 // ---------------------------------------------------------------------------
-// grad_rir[r][k] = alpha_i / N * sum_segments partial[k] for k < L_r, 0 for
-// L_r <= k < Nh; grad_gains[s] = sum_segments dalpha partial.  Segments are
-// added in order; empty segments (no block starts in them) are skipped.
-// With per-(i, j) gains (rir_gain non-NULL) the spectra already carry alpha_ij,
-// the partials are the plain correlations c_r = corr(g_j, x_i) (times N), so
-// grad_rir[r] = alpha_ij / N c_r and grad_gains[r] = <hhat_r, c_r> / N.
+// grad_rir[r][k] = alpha_i / N * sum_tiles partial[k] for k < L_r, 0 for
+// L_r <= k < Nh; grad_gains[s] = sum_tiles dalpha partial.  The utterance's
+// backward tiles (bnt[u] of them, each holding its partials in its slot) are
+// added in order.  With per-(i, j) gains (rir_gain non-NULL) the spectra
+// already carry alpha_ij, the partials are the plain correlations
+// c_r = corr(g_j, x_i) (times N), so grad_rir[r] = alpha_ij / N c_r and
+// grad_gains[r] = <hhat_r, c_r> / N.
 constexpr int kFinThreads = 256;
-constexpr int kFinMaxSegs = 512;   // backward segments of one utterance handled per pass
 
 __global__ void __launch_bounds__(kFinThreads)
 k_finalize(DevBatch B, const float* __restrict__ gains, const float* __restrict__ rir_gain,
            const float* __restrict__ rir, const float* __restrict__ dhp, const float* __restrict__ dap,
            float* __restrict__ grad_rir, float* __restrict__ grad_gains) {
-    __shared__ int64_t seg_off[kFinMaxSegs];   // dh-partial offsets of the non-empty segments
-    __shared__ int nseg_live;
     __shared__ float red[kFinThreads / 32];
     for (int r = blockIdx.x; r < B.R; r += gridDim.x) {
         const int u = B.rir_utt[r];
@@ -372,34 +671,19 @@ k_finalize(DevBatch B, const float* __restrict__ gains, const float* __restrict_
         const float* h = rir_gain ? rir + B.roff[r] : nullptr;
         float dot = 0.f;                       // <hhat_r, c_r> (per-(i, j) gains)
         const int64_t local = B.roff[r] - B.roff[B.rir0[u]];
-        const int hop = B.hop[u];
+        const int g0 = B.bseg0[u], nt = B.bnt[u];
         float acc[4];
         // taps of this thread: k = threadIdx.x + c * blockDim.x
         const int ntap_passes = (nh + kFinThreads - 1) / kFinThreads;
         for (int c0 = 0; c0 < ntap_passes; c0 += 4) {
 #pragma unroll
             for (int c = 0; c < 4; ++c) acc[c] = 0.f;
-            // segments in order; the list of non-empty ones is built once per chunk
-            for (int gb = B.bseg0[u]; gb < B.bseg0[u + 1]; gb += kFinMaxSegs) {
-                const int ge = min(B.bseg0[u + 1], gb + kFinMaxSegs);
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    int n = 0;
-                    for (int g = gb; g < ge; ++g) {
-                        int64_t b0, b1;
-                        segment_blocks(g - B.bseg0[u], B.bseg_len, hop, B.nblk[u], &b0, &b1);
-                        if (b0 < b1) seg_off[n++] = B.dhp_off[g] + local;
-                    }
-                    nseg_live = n;
-                }
-                __syncthreads();
-                for (int q = 0; q < nseg_live; ++q) {
-                    const float* src = dhp + seg_off[q];
+            for (int q = 0; q < nt; ++q) {
+                const float* src = dhp + B.dhp_off[g0 + q] + local;
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const int k = threadIdx.x + (c0 + c) * kFinThreads;
-                        if (k < Lr) acc[c] += src[k];
-                    }
+                for (int c = 0; c < 4; ++c) {
+                    const int k = threadIdx.x + (c0 + c) * kFinThreads;
+                    if (k < Lr) acc[c] += src[k];
                 }
             }
 #pragma unroll
@@ -427,12 +711,7 @@ k_finalize(DevBatch B, const float* __restrict__ gains, const float* __restrict_
             const int u = B.src_utt[sidx], i = sidx - B.src0[u];
             float acc = 0.f;
             if (B.logN[u] != 0) {
-                for (int g = B.bseg0[u]; g < B.bseg0[u + 1]; ++g) {
-                    int64_t b0, b1;
-                    segment_blocks(g - B.bseg0[u], B.bseg_len, B.hop[u], B.nblk[u], &b0, &b1);
-                    if (b0 >= b1) continue;
-                    acc += dap[(int64_t)g * kMaxSources + i];
-                }
+                for (int q = 0; q < B.bnt[u]; ++q) acc += dap[(int64_t)(B.bseg0[u] + q) * kMaxSources + i];
             }
             grad_gains[sidx] = acc;
         }
@@ -444,14 +723,25 @@ k_finalize(DevBatch B, const float* __restrict__ gains, const float* __restrict_
 // ---------------------------------------------------------------------------
 template <int M>
 constexpr int smem_backward() { return (int)BwdCfg<M>::bytes; }
+template <int M>
+constexpr int smem_backward_tm() { return (int)BwdTmCfg<M>::bytes; }
 
+// N <= 8192: the TMEM-accumulator kernel over (block run, source group) tiles;
+// N = 16384: the per-source kernel (three spectra per thread at 16 values per
+// thread would not fit its 128 registers)
 template <int M>
 static void backward_m(const DevBatch& B, const Queues& Q, int bucket, const float* g, const float* x,
                        const float* gains, const float2* Hc, float* dx, float* dhp, float* dap,
                        Twiddles tw, int grid, cudaStream_t st) {
-    auto kern = B.J > kJG ? k_backward<M, true> : k_backward<M, false>;
-    kern<<<grid, BwdCfg<M>::T, smem_backward<M>(), st>>>(B, Q, bucket, g, x, gains, Hc, dx, dhp,
-                                                                  dap, tw.get(BwdCfg<M>::E));
+    if constexpr (M <= 4096) {
+        auto kern = B.J > kJG ? k_backward_tm<M, true> : k_backward_tm<M, false>;
+        kern<<<grid, BwdTmCfg<M>::T, smem_backward_tm<M>(), st>>>(B, Q, bucket, g, x, gains, Hc, dx, dhp,
+                                                                  dap, tw.get(BwdTmCfg<M>::E));
+    } else {
+        auto kern = B.J > kJG ? k_backward<M, true> : k_backward<M, false>;
+        kern<<<grid, BwdCfg<M>::T, smem_backward<M>(), st>>>(B, Q, bucket, g, x, gains, Hc, dx, dhp,
+                                                                      dap, tw.get(BwdCfg<M>::E));
+    }
 }
 
 void launch_backward(int logN, const DevBatch& B, const Queues& Q, const float* g, const float* x,
@@ -469,9 +759,9 @@ void launch_backward(int logN, const DevBatch& B, const Queues& Q, const float* 
 
 int bwd_threads(int logN) {
     switch (logN) {
-        case 11: return BwdCfg<1024>::T;
-        case 12: return BwdCfg<2048>::T;
-        case 13: return BwdCfg<4096>::T;
+        case 11: return BwdTmCfg<1024>::T;
+        case 12: return BwdTmCfg<2048>::T;
+        case 13: return BwdTmCfg<4096>::T;
         case 14: return BwdCfg<8192>::T;
     }
     return 1;
@@ -500,12 +790,21 @@ static int occ_bb() {
     const int b = occ_b(k_backward<M, true>, BwdCfg<M>::T, smem_backward<M>());
     return a < b ? a : b;
 }
+// the TMEM kernels: also no more CTAs per SM than the SM's 512 TMEM columns hold
+// (a CTA beyond that would wait in its allocation until another one exits)
+template <int M>
+static int occ_tm() {
+    const int a = occ_b(k_backward_tm<M, false>, BwdTmCfg<M>::T, smem_backward_tm<M>());
+    const int b = occ_b(k_backward_tm<M, true>, BwdTmCfg<M>::T, smem_backward_tm<M>());
+    const int c = 512 / BwdTmCfg<M>::kCols;
+    return a < b ? (a < c ? a : c) : (b < c ? b : c);
+}
 
 int occupancy_backward(int logN) {
     switch (logN) {
-        case 11: return occ_bb<1024>();
-        case 12: return occ_bb<2048>();
-        case 13: return occ_bb<4096>();
+        case 11: return occ_tm<1024>();
+        case 12: return occ_tm<2048>();
+        case 13: return occ_tm<4096>();
         case 14: return occ_bb<8192>();
     }
     return 1;

@@ -49,11 +49,15 @@ struct DevBatch {
     const int32_t* rir_len;  // [R]
     const int32_t* src_utt;  // [S] utterance of source s
     const int32_t* rir_utt;  // [R] utterance of RIR r
-    int32_t NBSEG;           // total backward segments
-    int64_t bseg_len;        // samples per backward segment (>= largest allowed N)
-    const int32_t* bseg0;    // [U+1] first backward segment of utterance
-    const int32_t* bseg_utt; // [NBSEG] utterance of backward segment
-    const int64_t* dhp_off;  // [NBSEG] offset of a backward segment's dh partials
+    int32_t NBSEG;           // total backward tile slots
+    int64_t bseg_len;        // samples per backward tile slot (>= largest allowed N): an
+                             // utterance has ceil(n_x / bseg_len) slots, the most tiles
+                             // its backward may be cut into
+    const int32_t* bseg0;    // [U+1] first backward tile slot of utterance
+    const int32_t* bseg_utt; // [NBSEG] utterance of backward tile slot
+    const int64_t* dhp_off;  // [NBSEG] offset of a backward tile's dh partials
+    int32_t* bnt;            // [U] backward tiles of the utterance (device-written, <= its slots)
+    int32_t bgrid[4];        // CTAs of each FFT size's backward launch (the planner sizes tiles by it)
     const float* tuning;     // [32] cost per real FFT of size 2^m (any unit)
     // written on the device during a call
     int32_t* L;              // [R] kept RIR length (Eq. 9)
@@ -76,6 +80,23 @@ struct Queues {
     __host__ __device__ int32_t* lst(int kind, int b) const { return list + ((int64_t)kind * kNumBuckets + b) * cap; }
     __host__ __device__ int idx(int kind, int b) const { return kind * kNumBuckets + b; }
 };
+
+// Backward tile t of utterance u (slot bseg0[u] + t, t < bnt[u]) owns blocks
+// [t nblk / bnt, (t + 1) nblk / bnt): bnt[u] near-equal runs of consecutive blocks
+// (bnt <= nblk, so none is empty).
+__host__ __device__ inline void tile_blocks(const DevBatch& B, int g, int u, int64_t* b0, int64_t* b1) {
+    const int64_t t = g - B.bseg0[u];
+    const int64_t n = B.bnt[u], nb = B.nblk[u];
+    *b0 = t < n ? nb * t / n : nb;
+    *b1 = t < n ? nb * (t + 1) / n : nb;
+}
+
+// Sources per backward tile of each FFT size: the TMEM-accumulator kernels
+// (N <= 8192) keep the RIR-gradient spectra of that many sources times two
+// microphones in TMEM; the N = 16384 kernel takes one source per tile.
+__host__ __device__ constexpr int bwd_src_group(int logN) {
+    return logN == 11 ? 8 : logN == 12 ? 4 : logN == 13 ? 4 : 1;
+}
 
 // segment s of an utterance with hop h owns the blocks whose start b*h lies
 // in [s*seg_len, (s+1)*seg_len)
@@ -122,7 +143,7 @@ void set_last_error(const char* msg);
 // occupancy helpers (CTAs per SM) and shared-memory sizes of the tiled kernels
 int occupancy_spectrum(int logN);
 int occupancy_forward(int logN);
-int occupancy_backward(int logN);
+int occupancy_backward(int logN);   // CTAs per SM that may run at once (TMEM included)
 int threads_for(int logN);
 int bwd_threads(int logN);
 

@@ -186,6 +186,7 @@ void launch_power(const DevBatch& B, const float* x, int grid, cudaStream_t st) 
 // spectrum jobs (RIRs), forward tiles (segments) and backward tiles
 // (backward segment, source), in utterance order, and resets the queue cursors.
 constexpr int kPlanThreads = 1024;
+constexpr float kTilesPerCta = 3.f;          // backward tiles per CTA of a launch (load balance)
 constexpr float kConsolidateShare = 0.1f;   // a size below this share of the work is a minority
 constexpr float kConsolidateSlack = 0.02f;  // ...and moves if that adds at most this share of the work
 
@@ -311,12 +312,78 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
         B.nblk[u] = m ? (int)((nx + hop - 1) / hop) : 0;
     }
     __syncthreads();
-    // ---- work lists, one contiguous chunk of utterances per thread.  The three
-    // lists of the four sizes are laid out by one block-wide exclusive scan of
-    // the twelve per-thread counts.
-    constexpr int kNL = 3 * kNumBuckets;           // (list kind, size) pairs
+    // ---- backward tiles.  A tile is a run of consecutive blocks of one utterance
+    // and a group of its sources; its cost is counted in transforms,
+    // c_u = nblk (groups(J) 2 I + J) per utterance.  Each utterance is cut into
+    // ceil(c_u / target) near-equal runs (at least one, at most one per tile slot
+    // and per block), target = the size's total over kTilesPerCta tiles per CTA of
+    // its launch: tiles then cost about the same and every CTA pulls a few.
+    {
+        __shared__ float cpart[kNumBuckets][kPlanThreads / 32];
+        __shared__ float ctot[kNumBuckets];
+        const int ngrp = (B.J + kJG - 1) / kJG;
+        float my_cost[kNumBuckets];
+#pragma unroll
+        for (int q = 0; q < kNumBuckets; ++q) my_cost[q] = 0.f;
+        for (int u = t; u < B.U; u += kPlanThreads) {
+            const int m = B.logN[u];
+            if (m == 0) continue;
+            const float c = (float)B.nblk[u] * (float)(ngrp * 2 * B.n_src[u] + B.J);
+#pragma unroll
+            for (int q = 0; q < kNumBuckets; ++q)
+                if (q == m - kMinLog) my_cost[q] += c;
+        }
+        const int lane = t & 31, wid = t >> 5;
+#pragma unroll
+        for (int q = 0; q < kNumBuckets; ++q) {
+            float v = my_cost[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) cpart[q][wid] = v;
+        }
+        __syncthreads();
+        if (t < kNumBuckets) {
+            float v = 0.f;
+            for (int w = 0; w < kPlanThreads / 32; ++w) v += cpart[t][w];
+            ctot[t] = v;
+        }
+        __syncthreads();
+        for (int u = t; u < B.U; u += kPlanThreads) {
+            const int m = B.logN[u];
+            int nt = 0;
+            if (m != 0) {
+                const int b = m - kMinLog;
+                const float target = fmaxf(ctot[b] / (kTilesPerCta * (float)max(B.bgrid[b], 1)), 1.f);
+                const float c = (float)B.nblk[u] * (float)(ngrp * 2 * B.n_src[u] + B.J);
+                const int slots = B.bseg0[u + 1] - B.bseg0[u];
+                nt = (int)fminf(ceilf(c / target), (float)min(slots, B.nblk[u]));
+                nt = max(nt, 1);
+            }
+            B.bnt[u] = nt;
+        }
+        if (t < kNumBuckets) sm[t] = __float_as_int(ctot[t]);   // the sizes' totals, for the order below
+        __syncthreads();
+    }
+    // ---- work lists, one contiguous chunk of utterances per thread.  The lists of
+    // the four sizes -- forward tiles, backward tiles of at least half the target
+    // cost, the other backward tiles, spectrum jobs -- are laid out by one
+    // block-wide exclusive scan of the sixteen per-thread counts; the backward
+    // list holds the larger tiles first, then the small ones (short utterances),
+    // which fill in at the end of the launch.
+    constexpr int kNL = 4 * kNumBuckets;           // (list kind, size) pairs
     const int per = (B.U + kPlanThreads - 1) / kPlanThreads;
     const int u0 = min(B.U, t * per), u1 = min(B.U, u0 + per);
+    const int ngrp_j = (B.J + kJG - 1) / kJG;
+    // backward tiles of utterance u and whether they are "big"
+    auto bwd_tiles = [&](int u, int b, bool* big) {
+        const int m = kMinLog + b;
+        const int sg = bwd_src_group(m);
+        const int nt = B.bnt[u];
+        const float target = fmaxf(__int_as_float(sm[b]) / (kTilesPerCta * (float)max(B.bgrid[b], 1)), 1.f);
+        const float c = (float)B.nblk[u] * (float)(ngrp_j * 2 * B.n_src[u] + B.J);
+        *big = c / (float)nt >= 0.5f * target;
+        return nt * ((B.n_src[u] + sg - 1) / sg);
+    };
     int cnt[kNL];
 #pragma unroll
     for (int q = 0; q < kNL; ++q) cnt[q] = 0;
@@ -327,9 +394,11 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
 #pragma unroll
         for (int q = 0; q < kNumBuckets; ++q) {
             if (q != b) continue;
+            bool big;
+            const int nb = bwd_tiles(u, q, &big);
             cnt[q] += B.seg0[u + 1] - B.seg0[u];
-            cnt[kNumBuckets + q] += (B.bseg0[u + 1] - B.bseg0[u]) * B.n_src[u];
-            cnt[2 * kNumBuckets + q] += B.rir0[u + 1] - B.rir0[u];
+            cnt[(big ? 1 : 2) * kNumBuckets + q] += nb;
+            cnt[3 * kNumBuckets + q] += B.rir0[u + 1] - B.rir0[u];
         }
     }
     __shared__ int wtot[kPlanThreads / 32][kNL];
@@ -361,6 +430,9 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < kNL; ++q) off[q] += wtot[wid][q];
+        // the small backward tiles follow all the big ones of their size
+#pragma unroll
+        for (int q = 0; q < kNumBuckets; ++q) off[2 * kNumBuckets + q] += ltot[kNumBuckets + q];
     }
     for (int u = u0; u < u1; ++u) {
         const int m = B.logN[u];
@@ -369,24 +441,28 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
         int32_t* lf = Q.lst(kListFwd, b);
         int32_t* lb = Q.lst(kListBwd, b);
         int32_t* ls = Q.lst(kListSpec, b);
-        int of = 0, ob = 0, os = 0;
+        int of = 0, ob = 0, os = 0, nbt = 0;
 #pragma unroll
         for (int q = 0; q < kNumBuckets; ++q) {
             if (q != b) continue;
-            of = off[q]; ob = off[kNumBuckets + q]; os = off[2 * kNumBuckets + q];
+            bool big;
+            nbt = bwd_tiles(u, q, &big);
+            const int kb = (big ? 1 : 2) * kNumBuckets + q;
+            of = off[q]; ob = off[kb]; os = off[3 * kNumBuckets + q];
             off[q] += B.seg0[u + 1] - B.seg0[u];
-            off[kNumBuckets + q] += (B.bseg0[u + 1] - B.bseg0[u]) * B.n_src[u];
-            off[2 * kNumBuckets + q] += B.rir0[u + 1] - B.rir0[u];
+            off[kb] += nbt;
+            off[3 * kNumBuckets + q] += B.rir0[u + 1] - B.rir0[u];
         }
         for (int g = B.seg0[u]; g < B.seg0[u + 1]; ++g) lf[of++] = g;
-        for (int g = B.bseg0[u]; g < B.bseg0[u + 1]; ++g)
-            for (int i = 0; i < B.n_src[u]; ++i) lb[ob++] = g * kMaxSources + i;
+        const int sg = bwd_src_group(m);
+        for (int q = 0; q < B.bnt[u]; ++q)
+            for (int i0 = 0; i0 < B.n_src[u]; i0 += sg) lb[ob++] = (B.bseg0[u] + q) * kMaxSources + i0;
         for (int r = B.rir0[u]; r < B.rir0[u + 1]; ++r) ls[os++] = r;
     }
     if (t < kNumBuckets) {
         Q.count[Q.idx(kListFwd, t)] = ltot[t];
-        Q.count[Q.idx(kListBwd, t)] = ltot[kNumBuckets + t];
-        Q.count[Q.idx(kListSpec, t)] = ltot[2 * kNumBuckets + t];
+        Q.count[Q.idx(kListBwd, t)] = ltot[kNumBuckets + t] + ltot[2 * kNumBuckets + t];
+        Q.count[Q.idx(kListSpec, t)] = ltot[3 * kNumBuckets + t];
         Q.next[Q.idx(kListFwd, t)] = 0;
         Q.next[Q.idx(kListBwd, t)] = 0;
         Q.next[Q.idx(kListSpec, t)] = 0;

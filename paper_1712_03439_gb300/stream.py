@@ -33,7 +33,7 @@ PLAN_FIXED_BYTES = 2 << 20
 
 def utterance_bytes(nx: int, n_src: int, n_mics: int, rir_sum: int, nh_max: int, *,
                     backward: bool = True, output_mode: int = 0, seg_len: int = 16384,
-                    bwd_seg_len: int = 65536) -> int:
+                    bwd_seg_len: int = 16384) -> int:
     """Device bytes one utterance adds to a batch: its buffers plus its share of
     the plan's scratch (an estimate of the library's allocation)."""
     ny = nx + (nh_max - 1 if output_mode else 0)
@@ -47,6 +47,7 @@ def utterance_bytes(nx: int, n_src: int, n_mics: int, rir_sum: int, nh_max: int,
     scratch += 4 * nbseg * rir_sum                       # dh partials
     scratch += 8 * n_src * (-(-nx // _POWER_CHUNK))      # power partial sums
     scratch += 4 * 3 * 4 * max(nbseg * 16, nseg, n_src * n_mics) + 256
+    scratch += 4                                         # backward tiles of the utterance
     return int(buf + scratch)
 
 
