@@ -79,8 +79,9 @@ typedef struct {
                                          microphone snr_ref_mic (computed, written) */
     int64_t segment_len;           /* samples per forward work tile; 0 = default (the largest
                                       allowed N); raised to the largest allowed N */
-    int64_t bwd_segment_len;       /* samples per backward work tile; 0 = default (65536);
-                                      raised to the largest allowed N */
+    int64_t bwd_segment_len;       /* unused (kept for the layout): the backward of each FFT
+                                      size is cut on the device into one contiguous run of
+                                      blocks of equal cost per CTA of its launch */
     const float *fft_cost;         /* [32] host, relative cost of one real FFT of size 2^m
                                       used to pick N per utterance; NULL = N log2 N */
     int32_t disable_graphs;        /* 0: each call replays a CUDA graph of its launch sequence,

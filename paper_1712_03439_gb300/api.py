@@ -65,8 +65,6 @@ class Plan:
             fft_cost = {int(k): float(v) for k, v in tuned["fft_cost_ns"].items()}
         if not segment_len:
             segment_len = int(tuned.get("segment_len", 0))
-        if not bwd_segment_len:
-            bwd_segment_len = int(tuned.get("bwd_segment_len", 0))
         self.tuned = bool(tuned)
         self._cost = None
         if fft_cost is not None:

@@ -6,7 +6,7 @@ per-size costs).  This module measures cost[N] on the device: for each
 allowed N it runs the forward and backward on a workload where every size is
 admissible, reads the kernels' CUDA-event stage times and divides by the
 number of block transforms.  It then times the benchmark-shaped workload for
-a few forward/backward tile lengths.  The result is stored as JSON keyed by
+a few forward tile lengths.  The result is stored as JSON keyed by
 the GPU name in ``tuning.json`` next to this file; ``Plan`` loads it when no
 cost table is given.
 
@@ -83,7 +83,8 @@ def measure_fft_costs(device=0, sizes=SIZES, reps=5):
 
 
 def measure_tiles(costs, device=0, reps=5):
-    """Best (forward, backward) segment lengths on the Home-like workload."""
+    """Best forward segment length on the Home-like workload (the backward is
+    partitioned on the device, one equal-cost chunk per CTA)."""
     import torch
     from . import synth
     from .api import Plan
@@ -92,15 +93,12 @@ def measure_tiles(costs, device=0, reps=5):
     bufs = _buffers(b, dev)
     best = None
     for fseg in (16384, 32768, 65536):
-        for bseg in (32768, 65536, 131072):
-            plan = Plan.for_batch(b, eta_db=20.0, gain_mode=1, segment_len=fseg, bwd_segment_len=bseg,
-                                  fft_cost=costs, device=device)
-            t = _time_plan(plan, *bufs, reps)
-            tot = t["forward"] + t["backward"]
-            plan.close()
-            if best is None or tot < best[0]:
-                best = (tot, fseg, bseg)
-    return {"segment_len": best[1], "bwd_segment_len": best[2]}
+        plan = Plan.for_batch(b, eta_db=20.0, gain_mode=1, segment_len=fseg, fft_cost=costs, device=device)
+        t = _time_plan(plan, *bufs, reps)
+        plan.close()
+        if best is None or t["forward"] < best[0]:
+            best = (t["forward"], fseg)
+    return {"segment_len": best[1]}
 
 
 def autotune(device=0, out=TABLE):

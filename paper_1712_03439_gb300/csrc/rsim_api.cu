@@ -476,7 +476,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
         return fail(RSIM_E_UNSUPPORTED, "RIRs longer than the largest FFT size reaches (partitioned "
                                         "convolution) need output_mode 0 and gain_mode 0 or 1");
 
-    std::vector<int32_t> src0(U + 1), rir0(U + 1), seg0(U + 1), bseg0(U + 1);
+    std::vector<int32_t> src0(U + 1), rir0(U + 1), seg0(U + 1);
     std::vector<int64_t> yoff(U + 1), nyv(U);
     int64_t S = 0, R = 0, ysz = 0;
     int imax = 1;
@@ -484,13 +484,10 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     int max_log = kMinLog;
     for (int m = kMinLog; m <= kMaxLog; ++m)
         if ((mask >> m) & 1) max_log = m;
-    // forward tiles: short segments balance the load across SMs; backward
-    // tile slots: an utterance may be cut into at most one backward tile per
-    // bseg_len samples (the planner picks how many on the device)
+    // forward tiles: short segments balance the load across SMs (the backward is
+    // cut on the device into one equal-cost chunk per CTA)
     int64_t seg_len = std::max<int64_t>(d->segment_len, (int64_t)1 << max_log);
-    int64_t bseg_len = d->bwd_segment_len > 0 ? d->bwd_segment_len : 16384;
-    bseg_len = std::max<int64_t>(bseg_len, (int64_t)1 << max_log);
-    int64_t nseg = 0, nbseg = 0;
+    int64_t nseg = 0;
     for (int u = 0; u < U; ++u) {
         const int I = d->num_sources[u];
         const int64_t nx = d->num_samples[u];
@@ -499,7 +496,6 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
         src0[u] = (int32_t)S;
         rir0[u] = (int32_t)R;
         seg0[u] = (int32_t)nseg;
-        bseg0[u] = (int32_t)nbseg;
         yoff[u] = ysz;
         int64_t nh_max = 1;
         for (int64_t r = R; r < R + (int64_t)I * J; ++r) nh_max = std::max<int64_t>(nh_max, d->rir_len[r]);
@@ -508,17 +504,14 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
         R += (int64_t)I * J;
         ysz += (int64_t)J * nyv[u];
         nseg += (nx + seg_len - 1) / seg_len;
-        nbseg += (nx + bseg_len - 1) / bseg_len;
         imax = std::max(imax, I);
         nx_max = std::max(nx_max, nx);
-        if (S > INT32_MAX / 2 || R > INT32_MAX / 2 || nseg > INT32_MAX / 2 ||
-            nbseg * kMaxSources > INT32_MAX / 2)
+        if (S > INT32_MAX / 2 || R > INT32_MAX / 2 || nseg > INT32_MAX / 2)
             return fail(RSIM_E_UNSUPPORTED, "batch too large");
     }
     src0[U] = (int32_t)S;
     rir0[U] = (int32_t)R;
     seg0[U] = (int32_t)nseg;
-    bseg0[U] = (int32_t)nbseg;
     yoff[U] = ysz;
     std::vector<int32_t> rlen(d->rir_len, d->rir_len + R);
     std::vector<int64_t> roff(R + 1), xoff(S + 1);
@@ -541,19 +534,12 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
         for (int s = src0[u]; s < src0[u + 1]; ++s) src_utt[s] = u;
         for (int r = rir0[u]; r < rir0[u + 1]; ++r) rir_utt[r] = u;
     }
-    std::vector<int32_t> seg_utt(std::max<int64_t>(nseg, 1)), bseg_utt(std::max<int64_t>(nbseg, 1));
-    std::vector<int64_t> dhp_off(nbseg + 1);
-    int64_t dhp_total = 0;
+    std::vector<int32_t> seg_utt(std::max<int64_t>(nseg, 1));
+    int64_t utt_taps_max = 0;                    // RIR taps of the utterance with the most
     for (int u = 0; u < U; ++u) {
-        const int64_t rsum = roff[rir0[u + 1]] - roff[rir0[u]];
+        utt_taps_max = std::max<int64_t>(utt_taps_max, roff[rir0[u + 1]] - roff[rir0[u]]);
         for (int g = seg0[u]; g < seg0[u + 1]; ++g) seg_utt[g] = u;
-        for (int g = bseg0[u]; g < bseg0[u + 1]; ++g) {
-            bseg_utt[g] = u;
-            dhp_off[g] = dhp_total;
-            dhp_total += rsum;
-        }
     }
-    dhp_off[nbseg] = dhp_total;
     const int MMAX = 1 << (max_log - 1);
     const int CH = (int)((nx_max + kPowerChunk - 1) / kPowerChunk);
 
@@ -574,14 +560,14 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     // ---- carve one device allocation
     struct Piece { void** dst; size_t bytes; };
     std::vector<Piece> pieces;
-    void *p_bseg0, *p_bsegutt;
+    void *p_sord, *p_spre, *p_nstream, *p_ctasp, *p_ctab, *p_ctap, *p_piecedh, *p_sfirst, *p_slast;
     void *p_srcutt, *p_rirutt;
     void *p_nsrc, *p_nx, *p_ny, *p_src0, *p_rir0, *p_seg0, *p_segutt, *p_xoff, *p_yoff, *p_roff, *p_rlen,
-        *p_dhpoff, *p_tuning, *p_L, *p_logN, *p_hop, *p_lmax, *p_nblk, *p_pow, *p_err, *p_list,
-        *p_count, *p_next, *p_Hc, *p_tails, *p_dhp, *p_dap, *p_melrow, *p_ones, *p_bnt, *p_rsrc = nullptr,
+        *p_tuning, *p_L, *p_logN, *p_hop, *p_lmax, *p_nblk, *p_pow, *p_err, *p_list,
+        *p_count, *p_next, *p_Hc, *p_tails, *p_dhp, *p_dap, *p_melrow, *p_ones, *p_rsrc = nullptr,
         *p_rdst = nullptr, *p_rrir = nullptr, *p_ry = nullptr;
     void* p_tw[2 * kNumBuckets] = {};
-    const int64_t cap = std::max<int64_t>(std::max<int64_t>(nbseg * kMaxSources, nseg), R);
+    const int64_t cap = std::max<int64_t>(nseg, R);
     // launch shapes (persistent grids) decide the per-CTA backward scratch
     int sms = 0;
     {
@@ -596,9 +582,18 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
         DeviceGuard g0(device);
         grid_spec[b] = (int)std::max<int64_t>(1, std::min<int64_t>(R, (int64_t)sms * occupancy_spectrum(m)));
         grid_fwd[b] = (int)std::max<int64_t>(1, std::min<int64_t>(nseg, (int64_t)sms * occupancy_forward(m)));
-        grid_bwd[b] = (int)std::max<int64_t>(
-            1, std::min<int64_t>(nbseg * imax, (int64_t)sms * occupancy_backward(m)));
+        grid_bwd[b] = (int)std::max<int64_t>(1, (int64_t)sms * occupancy_backward(m));
     }
+    // backward partition: at most one piece per stream plus one per CTA boundary; the
+    // RIR-gradient partials of the pieces fit all RIR taps plus one utterance's per CTA
+    int pmax = 1;
+    int64_t ctas = 0;
+    for (int b = 0; b < kNumBuckets; ++b) {
+        pmax = std::max(pmax, grid_bwd[b]);
+        ctas += grid_bwd[b];
+    }
+    const int64_t npiece = S + ctas;
+    const int64_t dhp_total = roff[R] + ctas * utt_taps_max;
     pieces.push_back({&p_nsrc, sizeof(int32_t) * U});
     pieces.push_back({&p_nx, sizeof(int64_t) * U});
     pieces.push_back({&p_ny, sizeof(int64_t) * U});
@@ -606,22 +601,27 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     pieces.push_back({&p_rir0, sizeof(int32_t) * (U + 1)});
     pieces.push_back({&p_seg0, sizeof(int32_t) * (U + 1)});
     pieces.push_back({&p_segutt, sizeof(int32_t) * std::max<int64_t>(nseg, 1)});
-    pieces.push_back({&p_bseg0, sizeof(int32_t) * (U + 1)});
-    pieces.push_back({&p_bsegutt, sizeof(int32_t) * std::max<int64_t>(nbseg, 1)});
+    pieces.push_back({&p_sord, sizeof(int32_t) * kNumBuckets * std::max<int64_t>(S, 1)});
+    pieces.push_back({&p_spre, sizeof(int64_t) * kNumBuckets * (S + 1)});
+    pieces.push_back({&p_nstream, sizeof(int32_t) * kNumBuckets});
+    pieces.push_back({&p_ctasp, sizeof(int32_t) * kNumBuckets * (pmax + 1)});
+    pieces.push_back({&p_ctab, sizeof(int32_t) * kNumBuckets * (pmax + 1)});
+    pieces.push_back({&p_ctap, sizeof(int32_t) * kNumBuckets * (pmax + 1)});
+    pieces.push_back({&p_piecedh, sizeof(int64_t) * npiece});
+    pieces.push_back({&p_sfirst, sizeof(int32_t) * std::max<int64_t>(S, 1)});
+    pieces.push_back({&p_slast, sizeof(int32_t) * std::max<int64_t>(S, 1)});
     pieces.push_back({&p_xoff, sizeof(int64_t) * (S + 1)});
     pieces.push_back({&p_yoff, sizeof(int64_t) * (U + 1)});
     pieces.push_back({&p_roff, sizeof(int64_t) * (R + 1)});
     pieces.push_back({&p_rlen, sizeof(int32_t) * R});
     pieces.push_back({&p_srcutt, sizeof(int32_t) * std::max<int64_t>(S, 1)});
     pieces.push_back({&p_rirutt, sizeof(int32_t) * std::max<int64_t>(R, 1)});
-    pieces.push_back({&p_dhpoff, sizeof(int64_t) * (nbseg + 1)});
     pieces.push_back({&p_tuning, sizeof(float) * 32});
     pieces.push_back({&p_L, sizeof(int32_t) * R});
     pieces.push_back({&p_logN, sizeof(int32_t) * U});
     pieces.push_back({&p_hop, sizeof(int32_t) * U});
     pieces.push_back({&p_lmax, sizeof(int32_t) * U});
     pieces.push_back({&p_nblk, sizeof(int32_t) * U});
-    pieces.push_back({&p_bnt, sizeof(int32_t) * U});
     pieces.push_back({&p_pow, sizeof(double) * S * CH});
     pieces.push_back({&p_err, sizeof(int32_t) * 4});
     pieces.push_back({&p_list, sizeof(int32_t) * kNumLists * kNumBuckets * cap});
@@ -630,7 +630,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     pieces.push_back({&p_Hc, sizeof(float2) * R * MMAX});
     pieces.push_back({&p_tails, sizeof(float) * nseg * J * 2 * MMAX});
     pieces.push_back({&p_dhp, sizeof(float) * std::max<int64_t>(dhp_total, 1)});
-    pieces.push_back({&p_dap, sizeof(float) * std::max<int64_t>(nbseg, 1) * kMaxSources});
+    pieces.push_back({&p_dap, sizeof(float) * npiece * kMaxSources});
     pieces.push_back({&p_melrow, sizeof(int64_t) * (U + 1)});
     pieces.push_back({&p_ones, sizeof(float) * std::max<int64_t>(S, 1)});
     // gain_mode 3: each source's RIR to the reference microphone, gathered, and the
@@ -692,15 +692,12 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
         {p_rir0, rir0.data(), sizeof(int32_t) * (U + 1)},
         {p_seg0, seg0.data(), sizeof(int32_t) * (U + 1)},
         {p_segutt, seg_utt.data(), sizeof(int32_t) * nseg},
-        {p_bseg0, bseg0.data(), sizeof(int32_t) * (U + 1)},
-        {p_bsegutt, bseg_utt.data(), sizeof(int32_t) * nbseg},
         {p_xoff, xoff.data(), sizeof(int64_t) * (S + 1)},
         {p_yoff, yoff.data(), sizeof(int64_t) * (U + 1)},
         {p_roff, roff.data(), sizeof(int64_t) * (R + 1)},
         {p_rlen, rlen.data(), sizeof(int32_t) * R},
         {p_srcutt, src_utt.data(), sizeof(int32_t) * S},
         {p_rirutt, rir_utt.data(), sizeof(int32_t) * R},
-        {p_dhpoff, dhp_off.data(), sizeof(int64_t) * (nbseg + 1)},
         {p_tuning, tuning.data(), sizeof(float) * 32},
         {p_ones, ones.data(), sizeof(float) * ones.size()},
     };
@@ -728,8 +725,10 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     DevBatch& B = p->B;
     B.U = U; B.J = J; B.S = (int32_t)S; B.R = (int32_t)R; B.IMAX = imax;
     B.NSEG = (int32_t)nseg; B.MMAX = MMAX; B.mask = mask; B.seg_len = seg_len;
-    B.NBSEG = (int32_t)nbseg; B.bseg_len = bseg_len;
-    B.bseg0 = (const int32_t*)p_bseg0; B.bseg_utt = (const int32_t*)p_bsegutt;
+    B.PMAX = pmax; B.NPIECE = (int32_t)npiece;
+    B.sord = (int32_t*)p_sord; B.spre = (int64_t*)p_spre; B.nstream = (int32_t*)p_nstream;
+    B.cta_sp = (int32_t*)p_ctasp; B.cta_b = (int32_t*)p_ctab; B.cta_p = (int32_t*)p_ctap;
+    B.piece_dh = (int64_t*)p_piecedh; B.s_first = (int32_t*)p_sfirst; B.s_last = (int32_t*)p_slast;
     // the device planner computes gains from the source powers in modes 0 and 3 (in mode 3
     // the powers are those of the reverberant sources)
     B.gain_mode = d->gain_mode == 3 ? 0 : d->gain_mode;
@@ -739,9 +738,9 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     B.xoff = (const int64_t*)p_xoff; B.yoff = (const int64_t*)p_yoff;
     B.roff = (const int64_t*)p_roff; B.rir_len = (const int32_t*)p_rlen;
     B.src_utt = (const int32_t*)p_srcutt; B.rir_utt = (const int32_t*)p_rirutt;
-    B.dhp_off = (const int64_t*)p_dhpoff; B.tuning = (const float*)p_tuning;
+    B.tuning = (const float*)p_tuning;
     B.L = (int32_t*)p_L; B.logN = (int32_t*)p_logN; B.hop = (int32_t*)p_hop;
-    B.Lmax = (int32_t*)p_lmax; B.nblk = (int32_t*)p_nblk; B.bnt = (int32_t*)p_bnt;
+    B.Lmax = (int32_t*)p_lmax; B.nblk = (int32_t*)p_nblk;
     for (int b = 0; b < kNumBuckets; ++b) B.bgrid[b] = grid_bwd[b];
     B.pow_part = (double*)p_pow; B.CH = CH; B.err = (int32_t*)p_err;
     {

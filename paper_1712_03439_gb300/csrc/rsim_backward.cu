@@ -14,16 +14,6 @@
 
 namespace rsim {
 
-__device__ __forceinline__ int pop_job_b(const Queues& Q, int kind, int b, int* slot) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int i = atomicAdd(&Q.next[Q.idx(kind, b)], 1);
-        *slot = (i < Q.count[Q.idx(kind, b)]) ? Q.lst(kind, b)[i] : -1;
-    }
-    __syncthreads();
-    return *slot;
-}
-
 __device__ __forceinline__ double block_sum_d(double v, double* sd) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = (blockDim.x + 31) >> 5;
@@ -106,7 +96,6 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
     float* st0 = reinterpret_cast<float*>(smem_raw + L::o_st);
     float2* hs = reinterpret_cast<float2*>(smem_raw + L::o_hs);
     __shared__ double sd[32];
-    __shared__ int slot;
     __shared__ __align__(8) uint64_t mbar[2];
     const int t = threadIdx.x;
     if constexpr (kBulk) {
@@ -132,18 +121,13 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
     const int kt = kPaired ? paired_butterfly<T>(t) : t;
     int sc = 0;                                  // stage holding the next transform input
     auto stage = [&](int k) { return st0 + (NST == 2 ? k : 0) * (2 * M + 8); };
-    for (;;) {
-        const int code = pop_job_b(Q, kListBwd, bucket, &slot);
-        if (code < 0) break;
-        const int g = code / kMaxSources, i = code % kMaxSources;
-        const int u = B.bseg_utt[g];
+    bool stop = false;                           // a wait ran out: the remaining pieces are skipped
+    for_each_piece(B, bucket, blockIdx.x, [&](int pc, int, int u, int i, int64_t b0, int64_t b1) {
+        if (stop) return;
         const int64_t nx = B.n_x[u];
         const int64_t ny = B.n_y[u];
         const int hop = B.hop[u];
         const int lmax = B.Lmax[u];
-        int64_t b0, b1;
-        tile_blocks(B, g, u, &b0, &b1);
-        if (b0 >= b1) continue;
         const int J = B.J;
         const int sb = B.src0[u], rb = B.rir0[u];
         const float a = __ldg(gains + sb + i);
@@ -317,7 +301,7 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
                 else irfft_x<M, E, false>(v, Pw, ex, tw, t);
                 const int r = rb + i * J + j0 + jj;
                 const int Lr = B.L[r];
-                float* out = dhp + B.dhp_off[g] + (B.roff[r] - B.roff[rb]);
+                float* out = dhp + B.piece_dh[pc] + (B.roff[r] - B.roff[rb + i * J]);
 #pragma unroll
                 for (int q = 0; q < E; ++q) {
                     const int n = 2 * (t + q * T);
@@ -327,14 +311,14 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
             }
         }
         const double tot = block_sum_d((double)da, sd);
-        if (t == 0) dap[(int64_t)g * kMaxSources + i] = (float)tot;
+        if (t == 0) dap[(int64_t)pc * kMaxSources] = (float)tot;
         if constexpr (kBulk) {
             if (__syncthreads_or(bad)) {         // a copy never completed: report and stop
                 if (t == 0) atomicOr(B.err, kErrWaitTimeout);
-                break;
+                stop = true;
             }
         }
-    }
+    });
     cp_async_wait<0>();
 }
 
@@ -398,10 +382,10 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
                reinterpret_cast<float2*>(smem_raw + L::o_sm + L::SM_LEN), 0};
     float* st0 = reinterpret_cast<float*>(smem_raw + L::o_st);
     __shared__ double sd[32];
-    __shared__ int slot;
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_base;
     const int t = threadIdx.x;
+    if (chunk_empty(B, bucket, blockIdx.x)) return;   // before any TMEM is taken
     if (t < 32) {                                // warp 0 takes the CTA's TMEM columns
         tmem_alloc(&tmem_base, L::kCols);
         tmem_relinquish();
@@ -428,18 +412,13 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
     const int kt = kPaired ? paired_butterfly<T>(t) : t;
     int sc = 0;                                  // stage holding the next transform input
     auto stage = [&](int k) { return st0 + k * (2 * M + 8); };
-    for (;;) {
-        const int code = pop_job_b(Q, kListBwd, bucket, &slot);
-        if (code < 0) break;
-        const int g = code / kMaxSources, i0 = code % kMaxSources;
-        const int u = B.bseg_utt[g];
+    bool stop = false;                           // a wait ran out: the remaining pieces are skipped
+    for_each_piece(B, bucket, blockIdx.x, [&](int pc, int, int u, int i0, int64_t b0, int64_t b1) {
+        if (stop) return;
         const int64_t nx = B.n_x[u];
         const int64_t ny = B.n_y[u];
         const int hop = B.hop[u];
         const int lmax = B.Lmax[u];
-        int64_t b0, b1;
-        tile_blocks(B, g, u, &b0, &b1);
-        if (b0 >= b1) continue;
         const int J = B.J;
         const int I = min(IG, B.n_src[u] - i0);
         const int sb = B.src0[u] + i0, rb = B.rir0[u];
@@ -611,7 +590,7 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
                 else irfft_x<M, E, false>(v, Wv, ex, tw, t);
                 const int r = rb + (i0 + i) * J + j0 + jj;
                 const int Lr = B.L[r];
-                float* out = dhp + B.dhp_off[g] + (B.roff[r] - B.roff[rb]);
+                float* out = dhp + B.piece_dh[pc] + (B.roff[r] - B.roff[rb + i0 * J]);
 #pragma unroll
                 for (int q = 0; q < E; ++q) {
                     const int n = 2 * (t + q * T);
@@ -624,13 +603,13 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
         for (int q = 0; q < IG; ++q) {
             if (q >= I) break;
             const double tot = block_sum_d((double)da[q], sd);
-            if (t == 0) dap[(int64_t)g * kMaxSources + i0 + q] = (float)tot;
+            if (t == 0) dap[(int64_t)pc * kMaxSources + q] = (float)tot;
         }
         if (__syncthreads_or(bad)) {             // a copy never completed: report and stop
             if (t == 0) atomicOr(B.err, kErrWaitTimeout);
-            break;
+            stop = true;
         }
-    }
+    });
     // every thread's TMEM accesses are complete (each store waited); order them
     // before warp 0 frees the columns
     tmem_fence_before();
@@ -642,11 +621,11 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
 // ---------------------------------------------------------------------------
 // K8: deterministic reduction of the per-segment partials
 // ---------------------------------------------------------------------------
-// grad_rir[r][k] = alpha_i / N * sum_tiles partial[k] for k < L_r, 0 for
-// L_r <= k < Nh; grad_gains[s] = sum_tiles dalpha partial.  The utterance's
-// backward tiles (bnt[u] of them, each holding its partials in its slot) are
-// added in order.  With per-(i, j) gains (rir_gain non-NULL) the spectra
-// already carry alpha_ij, the partials are the plain correlations
+// grad_rir[r][k] = alpha_i / N * sum_pieces partial[k] for k < L_r, 0 for
+// L_r <= k < Nh; grad_gains[s] = sum_pieces dalpha partial.  The pieces of
+// the stream holding source i (s_first .. s_last, consecutive blocks of the
+// utterance) are added in order.  With per-(i, j) gains (rir_gain non-NULL)
+// the spectra already carry alpha_ij, the partials are the plain correlations
 // c_r = corr(g_j, x_i) (times N), so grad_rir[r] = alpha_ij / N c_r and
 // grad_gains[r] = <hhat_r, c_r> / N.
 constexpr int kFinThreads = 256;
@@ -670,16 +649,20 @@ k_finalize(DevBatch B, const float* __restrict__ gains, const float* __restrict_
         const float scale = (rir_gain ? rir_gain[r] : gains[B.src0[u] + i]) * inv_n;
         const float* h = rir_gain ? rir + B.roff[r] : nullptr;
         float dot = 0.f;                       // <hhat_r, c_r> (per-(i, j) gains)
-        const int64_t local = B.roff[r] - B.roff[B.rir0[u]];
-        const int g0 = B.bseg0[u], nt = B.bnt[u];
+        // the stream of source i: its first source, and the offset of RIR r in its partials
+        const int sg = bwd_src_group(B.logN[u]);
+        const int i0 = i / sg * sg;
+        const int sidx = B.src0[u] + i0;
+        const int64_t local = B.roff[r] - B.roff[B.rir0[u] + i0 * B.J];
+        const int p0 = B.s_first[sidx], p1 = B.s_last[sidx];
         float acc[4];
         // taps of this thread: k = threadIdx.x + c * blockDim.x
         const int ntap_passes = (nh + kFinThreads - 1) / kFinThreads;
         for (int c0 = 0; c0 < ntap_passes; c0 += 4) {
 #pragma unroll
             for (int c = 0; c < 4; ++c) acc[c] = 0.f;
-            for (int q = 0; q < nt; ++q) {
-                const float* src = dhp + B.dhp_off[g0 + q] + local;
+            for (int q = p0; q <= p1; ++q) {
+                const float* src = dhp + B.piece_dh[q] + local;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     const int k = threadIdx.x + (c0 + c) * kFinThreads;
@@ -711,7 +694,10 @@ k_finalize(DevBatch B, const float* __restrict__ gains, const float* __restrict_
             const int u = B.src_utt[sidx], i = sidx - B.src0[u];
             float acc = 0.f;
             if (B.logN[u] != 0) {
-                for (int q = 0; q < B.bnt[u]; ++q) acc += dap[(int64_t)(B.bseg0[u] + q) * kMaxSources + i];
+                const int sg = bwd_src_group(B.logN[u]);
+                const int i0 = i / sg * sg;
+                const int st = B.src0[u] + i0;
+                for (int q = B.s_first[st]; q <= B.s_last[st]; ++q) acc += dap[(int64_t)q * kMaxSources + i - i0];
             }
             grad_gains[sidx] = acc;
         }

@@ -26,9 +26,8 @@ enum : int { kListFwd = 0, kListBwd = 1, kListSpec = 2, kNumLists = 3 };
 
 // Batch description and per-call state on the device.  Utterance u has
 // n_src[u] sources (source 0 is the target) and J microphones.  The forward
-// cuts it into ceil(n_x / seg_len) segments and the backward into
-// ceil(n_x / bseg_len) segments; a forward tile is a segment, a backward tile
-// a segment and one source.
+// cuts it into ceil(n_x / seg_len) segments, one tile each; the backward of
+// each FFT size is cut into one contiguous chunk per CTA (for_each_piece).
 struct DevBatch {
     int32_t U, J, S, R, IMAX;
     int32_t NSEG;            // total segments
@@ -49,15 +48,19 @@ struct DevBatch {
     const int32_t* rir_len;  // [R]
     const int32_t* src_utt;  // [S] utterance of source s
     const int32_t* rir_utt;  // [R] utterance of RIR r
-    int32_t NBSEG;           // total backward tile slots
-    int64_t bseg_len;        // samples per backward tile slot (>= largest allowed N): an
-                             // utterance has ceil(n_x / bseg_len) slots, the most tiles
-                             // its backward may be cut into
-    const int32_t* bseg0;    // [U+1] first backward tile slot of utterance
-    const int32_t* bseg_utt; // [NBSEG] utterance of backward tile slot
-    const int64_t* dhp_off;  // [NBSEG] offset of a backward tile's dh partials
-    int32_t* bnt;            // [U] backward tiles of the utterance (device-written, <= its slots)
-    int32_t bgrid[4];        // CTAs of each FFT size's backward launch (the planner sizes tiles by it)
+    // backward partition (written by the planner; see for_each_piece below)
+    int32_t PMAX;            // most CTAs of one FFT size's backward launch
+    int32_t NPIECE;          // capacity of the piece arrays (S + sum of the launches' CTAs)
+    int32_t bgrid[4];        // CTAs of each FFT size's backward launch
+    int32_t* sord;           // [4][S] streams of each size in batch order (first source of the group)
+    int64_t* spre;           // [4][S + 1] cost of the size's streams before each one (transforms)
+    int32_t* nstream;        // [4] streams of each size
+    int32_t* cta_sp;         // [4][PMAX + 1] first stream position of each CTA's chunk
+    int32_t* cta_b;          // [4][PMAX + 1] first block in that stream
+    int32_t* cta_p;          // [4][PMAX + 1] first piece of each chunk
+    int64_t* piece_dh;       // [NPIECE] offset of each piece's RIR-gradient partials
+    int32_t* s_first;        // [S] first piece of the stream that starts at source s
+    int32_t* s_last;         // [S] last piece of that stream
     const float* tuning;     // [32] cost per real FFT of size 2^m (any unit)
     // written on the device during a call
     int32_t* L;              // [R] kept RIR length (Eq. 9)
@@ -81,19 +84,43 @@ struct Queues {
     __host__ __device__ int idx(int kind, int b) const { return kind * kNumBuckets + b; }
 };
 
-// Backward tile t of utterance u (slot bseg0[u] + t, t < bnt[u]) owns blocks
-// [t nblk / bnt, (t + 1) nblk / bnt): bnt[u] near-equal runs of consecutive blocks
-// (bnt <= nblk, so none is empty).
-__host__ __device__ inline void tile_blocks(const DevBatch& B, int g, int u, int64_t* b0, int64_t* b1) {
-    const int64_t t = g - B.bseg0[u];
-    const int64_t n = B.bnt[u], nb = B.nblk[u];
-    *b0 = t < n ? nb * t / n : nb;
-    *b1 = t < n ? nb * (t + 1) / n : nb;
+// The backward work of one FFT size is a sequence of streams -- (utterance, group
+// of up to bwd_src_group(log2 N) of its sources), in batch order, each the
+// utterance's nblk blocks long -- and each block of a stream costs
+// groups(J) * 2 I_g + J transforms (I_g sources in the group).  The planner cuts
+// the sequence at block boundaries into one chunk per CTA of the launch, of
+// equal cost; a chunk is a list of pieces, the parts of the streams it covers
+// (piece p: stream s, blocks [b0, b1)).  Pieces are numbered in sequence
+// order, so a stream's pieces are consecutive (s_first[s] .. s_last[s]).
+// Calls f(p, s, u, i0, b0, b1) for every piece of CTA k of size bucket b, in
+// order (s = first source of the group, i0 = its index in the utterance).
+template <typename F>
+__device__ __forceinline__ void for_each_piece(const DevBatch& B, int b, int k, F f) {
+    const int32_t* sp = B.cta_sp + (int64_t)b * (B.PMAX + 1);
+    const int32_t* sb = B.cta_b + (int64_t)b * (B.PMAX + 1);
+    const int pos0 = sp[k], blk0 = sb[k], pos1 = sp[k + 1], blk1 = sb[k + 1];
+    int p = B.cta_p[(int64_t)b * (B.PMAX + 1) + k];
+    for (int pos = pos0; pos <= pos1; ++pos) {
+        if (pos == pos1 && blk1 == 0) break;
+        const int s = B.sord[(int64_t)b * B.S + pos];
+        const int u = B.src_utt[s];
+        const int64_t lo = pos == pos0 ? blk0 : 0;
+        const int64_t hi = pos == pos1 ? blk1 : B.nblk[u];
+        if (lo >= hi) continue;
+        f(p, s, u, s - B.src0[u], lo, hi);
+        ++p;
+    }
 }
 
-// Sources per backward tile of each FFT size: the TMEM-accumulator kernels
+// True when CTA k of size bucket b has no work.
+__device__ __forceinline__ bool chunk_empty(const DevBatch& B, int b, int k) {
+    const int64_t o = (int64_t)b * (B.PMAX + 1) + k;
+    return B.cta_sp[o] == B.cta_sp[o + 1] && B.cta_b[o] >= B.cta_b[o + 1];
+}
+
+// Sources per backward stream of each FFT size: the TMEM-accumulator kernels
 // (N <= 8192) keep the RIR-gradient spectra of that many sources times two
-// microphones in TMEM; the N = 16384 kernel takes one source per tile.
+// microphones in TMEM; the N = 16384 kernel takes one source at a time.
 __host__ __device__ constexpr int bwd_src_group(int logN) {
     return logN == 11 ? 8 : logN == 12 ? 4 : logN == 13 ? 4 : 1;
 }

@@ -186,7 +186,6 @@ void launch_power(const DevBatch& B, const float* x, int grid, cudaStream_t st) 
 // spectrum jobs (RIRs), forward tiles (segments) and backward tiles
 // (backward segment, source), in utterance order, and resets the queue cursors.
 constexpr int kPlanThreads = 1024;
-constexpr float kTilesPerCta = 3.f;          // backward tiles per CTA of a launch (load balance)
 constexpr float kConsolidateShare = 0.1f;   // a size below this share of the work is a minority
 constexpr float kConsolidateSlack = 0.02f;  // ...and moves if that adds at most this share of the work
 
@@ -239,7 +238,7 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
             const int64_t N = 1LL << m;
             const int64_t hop = N - lmax + 1;
             if (4 * hop < N) continue;                 // hop >= N/4 keeps blocks useful
-            if (N > B.seg_len || N > B.bseg_len) continue;
+            if (N > B.seg_len) continue;
             const int64_t nb = (nx + hop - 1) / hop;
             const float c = ((float)nb * (I + J) + (float)(I * J)) * B.tuning[m];
             cost[m - kMinLog] = c;
@@ -312,78 +311,194 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
         B.nblk[u] = m ? (int)((nx + hop - 1) / hop) : 0;
     }
     __syncthreads();
-    // ---- backward tiles.  A tile is a run of consecutive blocks of one utterance
-    // and a group of its sources; its cost is counted in transforms,
-    // c_u = nblk (groups(J) 2 I + J) per utterance.  Each utterance is cut into
-    // ceil(c_u / target) near-equal runs (at least one, at most one per tile slot
-    // and per block), target = the size's total over kTilesPerCta tiles per CTA of
-    // its launch: tiles then cost about the same and every CTA pulls a few.
-    {
-        __shared__ float cpart[kNumBuckets][kPlanThreads / 32];
-        __shared__ float ctot[kNumBuckets];
-        const int ngrp = (B.J + kJG - 1) / kJG;
-        float my_cost[kNumBuckets];
-#pragma unroll
-        for (int q = 0; q < kNumBuckets; ++q) my_cost[q] = 0.f;
-        for (int u = t; u < B.U; u += kPlanThreads) {
-            const int m = B.logN[u];
-            if (m == 0) continue;
-            const float c = (float)B.nblk[u] * (float)(ngrp * 2 * B.n_src[u] + B.J);
-#pragma unroll
-            for (int q = 0; q < kNumBuckets; ++q)
-                if (q == m - kMinLog) my_cost[q] += c;
-        }
-        const int lane = t & 31, wid = t >> 5;
-#pragma unroll
-        for (int q = 0; q < kNumBuckets; ++q) {
-            float v = my_cost[q];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) cpart[q][wid] = v;
-        }
-        __syncthreads();
-        if (t < kNumBuckets) {
-            float v = 0.f;
-            for (int w = 0; w < kPlanThreads / 32; ++w) v += cpart[t][w];
-            ctot[t] = v;
-        }
-        __syncthreads();
-        for (int u = t; u < B.U; u += kPlanThreads) {
-            const int m = B.logN[u];
-            int nt = 0;
-            if (m != 0) {
-                const int b = m - kMinLog;
-                const float target = fmaxf(ctot[b] / (kTilesPerCta * (float)max(B.bgrid[b], 1)), 1.f);
-                const float c = (float)B.nblk[u] * (float)(ngrp * 2 * B.n_src[u] + B.J);
-                const int slots = B.bseg0[u + 1] - B.bseg0[u];
-                nt = (int)fminf(ceilf(c / target), (float)min(slots, B.nblk[u]));
-                nt = max(nt, 1);
-            }
-            B.bnt[u] = nt;
-        }
-        if (t < kNumBuckets) sm[t] = __float_as_int(ctot[t]);   // the sizes' totals, for the order below
-        __syncthreads();
-    }
-    // ---- work lists, one contiguous chunk of utterances per thread.  The lists of
-    // the four sizes -- forward tiles, backward tiles of at least half the target
-    // cost, the other backward tiles, spectrum jobs -- are laid out by one
-    // block-wide exclusive scan of the sixteen per-thread counts; the backward
-    // list holds the larger tiles first, then the small ones (short utterances),
-    // which fill in at the end of the launch.
-    constexpr int kNL = 4 * kNumBuckets;           // (list kind, size) pairs
     const int per = (B.U + kPlanThreads - 1) / kPlanThreads;
     const int u0 = min(B.U, t * per), u1 = min(B.U, u0 + per);
     const int ngrp_j = (B.J + kJG - 1) / kJG;
-    // backward tiles of utterance u and whether they are "big"
-    auto bwd_tiles = [&](int u, int b, bool* big) {
-        const int m = kMinLog + b;
-        const int sg = bwd_src_group(m);
-        const int nt = B.bnt[u];
-        const float target = fmaxf(__int_as_float(sm[b]) / (kTilesPerCta * (float)max(B.bgrid[b], 1)), 1.f);
-        const float c = (float)B.nblk[u] * (float)(ngrp_j * 2 * B.n_src[u] + B.J);
-        *big = c / (float)nt >= 0.5f * target;
-        return nt * ((B.n_src[u] + sg - 1) / sg);
+    const int lane = t & 31, wid = t >> 5;
+    // ---- backward partition, step 1: the streams of each size in batch order and the
+    // exclusive prefix of their costs (utterances in contiguous chunks per thread)
+    {
+        int ns[kNumBuckets];
+        long long cs[kNumBuckets];
+#pragma unroll
+        for (int q = 0; q < kNumBuckets; ++q) { ns[q] = 0; cs[q] = 0; }
+        for (int u = u0; u < u1; ++u) {
+            const int m = B.logN[u];
+            if (m == 0) continue;
+            const int sg = bwd_src_group(m), I = B.n_src[u];
+#pragma unroll
+            for (int q = 0; q < kNumBuckets; ++q) {
+                if (q != m - kMinLog) continue;
+                for (int i0 = 0; i0 < I; i0 += sg) {
+                    ns[q] += 1;
+                    cs[q] += (long long)B.nblk[u] * (ngrp_j * 2 * min(sg, I - i0) + B.J);
+                }
+            }
+        }
+        __shared__ int wn[kPlanThreads / 32][kNumBuckets];
+        __shared__ long long wc[kPlanThreads / 32][kNumBuckets];
+        int on[kNumBuckets];
+        long long oc[kNumBuckets];
+#pragma unroll
+        for (int q = 0; q < kNumBuckets; ++q) {
+            int in = ns[q];
+            long long ic = cs[q];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int n1 = __shfl_up_sync(0xffffffffu, in, o);
+                const long long c1 = __shfl_up_sync(0xffffffffu, ic, o);
+                if (lane >= o) { in += n1; ic += c1; }
+            }
+            on[q] = in - ns[q];
+            oc[q] = ic - cs[q];
+            if (lane == 31) { wn[wid][q] = in; wc[wid][q] = ic; }
+        }
+        __syncthreads();
+        if (t < kNumBuckets) {                    // exclusive scan of the warps' totals
+            int an = 0;
+            long long ac = 0;
+            for (int w = 0; w < kPlanThreads / 32; ++w) {
+                const int vn = wn[w][t];
+                const long long vc = wc[w][t];
+                wn[w][t] = an;
+                wc[w][t] = ac;
+                an += vn;
+                ac += vc;
+            }
+            B.nstream[t] = an;
+            B.spre[(int64_t)t * (B.S + 1) + an] = ac;   // the size's total cost
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kNumBuckets; ++q) { on[q] += wn[wid][q]; oc[q] += wc[wid][q]; }
+        for (int u = u0; u < u1; ++u) {
+            const int m = B.logN[u];
+            if (m == 0) continue;
+            const int sg = bwd_src_group(m), I = B.n_src[u];
+#pragma unroll
+            for (int q = 0; q < kNumBuckets; ++q) {
+                if (q != m - kMinLog) continue;
+                for (int i0 = 0; i0 < I; i0 += sg) {
+                    B.sord[(int64_t)q * B.S + on[q]] = B.src0[u] + i0;
+                    B.spre[(int64_t)q * (B.S + 1) + on[q]] = oc[q];
+                    on[q] += 1;
+                    oc[q] += (long long)B.nblk[u] * (ngrp_j * 2 * min(sg, I - i0) + B.J);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // per-block cost of the stream at position pos of size q
+    auto stream_cost = [&](int q, int pos, int* u_out) {
+        const int sidx = B.sord[(int64_t)q * B.S + pos];
+        const int u = B.src_utt[sidx];
+        const int sg = bwd_src_group(kMinLog + q);
+        *u_out = u;
+        return ngrp_j * 2 * min(sg, B.n_src[u] - (sidx - B.src0[u])) + B.J;
     };
+    // ---- step 2: where each CTA's chunk starts.  CTA k of size q starts at the first
+    // block whose cost position is at least ceil(k T / P); the end sentinel k = P is
+    // (streams, 0)
+    const int PM = B.PMAX + 1;
+    for (int idx = t; idx < kNumBuckets * PM; idx += kPlanThreads) {
+        const int q = idx / PM, k = idx - q * PM;
+        const int P = B.bgrid[q];
+        if (k > P) continue;
+        const int n = B.nstream[q];
+        const int64_t* pre = B.spre + (int64_t)q * (B.S + 1);
+        int pos = n, blk = 0;
+        if (k < P && n > 0) {
+            const long long T = pre[n];
+            const long long x = (T * k + P - 1) / P;
+            int lo = 0, hi = n;                   // largest pos < n with pre[pos] <= x
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (pre[mid] <= x) lo = mid; else hi = mid;
+            }
+            int u;
+            const int c = stream_cost(q, lo, &u);
+            const long long bk = (x - pre[lo] + c - 1) / c;
+            if (bk >= B.nblk[u]) { pos = lo + 1; blk = 0; }
+            else { pos = lo; blk = (int)bk; }
+        }
+        B.cta_sp[(int64_t)q * PM + k] = pos;
+        B.cta_b[(int64_t)q * PM + k] = blk;
+    }
+    __syncthreads();
+    // ---- step 3: pieces.  Every thread takes a contiguous run of (size, CTA) entries,
+    // counts their chunks' pieces and the RIR-gradient partials they hold; a
+    // block-wide scan in (size, CTA) order numbers them; each thread then writes its
+    // pieces' partial offsets and marks the first and last piece of every stream
+    {
+        const int NE = kNumBuckets * PM;
+        const int pe = (NE + kPlanThreads - 1) / kPlanThreads;
+        const int e0 = min(NE, t * pe), e1 = min(NE, e0 + pe);
+        auto walk = [&](int q, int k, auto visit) {
+            const int pos0 = B.cta_sp[(int64_t)q * PM + k], blk0 = B.cta_b[(int64_t)q * PM + k];
+            const int pos1 = B.cta_sp[(int64_t)q * PM + k + 1], blk1 = B.cta_b[(int64_t)q * PM + k + 1];
+            for (int pos = pos0; pos <= pos1; ++pos) {
+                if (pos == pos1 && blk1 == 0) break;
+                const int sidx = B.sord[(int64_t)q * B.S + pos];
+                const int u = B.src_utt[sidx];
+                const int lo = pos == pos0 ? blk0 : 0;
+                const int hi = pos == pos1 ? blk1 : B.nblk[u];
+                if (lo >= hi) continue;
+                const int i0 = sidx - B.src0[u];
+                const int ig = min(bwd_src_group(kMinLog + q), B.n_src[u] - i0);
+                const int r0 = B.rir0[u] + i0 * B.J;
+                const long long taps = B.roff[r0 + ig * B.J] - B.roff[r0];
+                visit(sidx, lo == 0, hi == B.nblk[u], taps);
+            }
+        };
+        int np = 0;
+        long long nd = 0;
+        for (int e = e0; e < e1; ++e) {
+            const int q = e / PM, k = e - q * PM;
+            if (k < B.bgrid[q]) walk(q, k, [&](int, bool, bool, long long taps) { np += 1; nd += taps; });
+        }
+        __shared__ int pw[kPlanThreads / 32];
+        __shared__ long long dw[kPlanThreads / 32];
+        int ip = np;
+        long long id = nd;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int n1 = __shfl_up_sync(0xffffffffu, ip, o);
+            const long long d1 = __shfl_up_sync(0xffffffffu, id, o);
+            if (lane >= o) { ip += n1; id += d1; }
+        }
+        if (lane == 31) { pw[wid] = ip; dw[wid] = id; }
+        __syncthreads();
+        if (t == 0) {
+            int an = 0;
+            long long ad = 0;
+            for (int w = 0; w < kPlanThreads / 32; ++w) {
+                const int vn = pw[w];
+                const long long vd = dw[w];
+                pw[w] = an;
+                dw[w] = ad;
+                an += vn;
+                ad += vd;
+            }
+        }
+        __syncthreads();
+        int p = ip - np + pw[wid];
+        long long d = id - nd + dw[wid];
+        for (int e = e0; e < e1; ++e) {
+            const int q = e / PM, k = e - q * PM;
+            if (k >= B.bgrid[q]) continue;
+            B.cta_p[(int64_t)q * PM + k] = p;
+            walk(q, k, [&](int sidx, bool first, bool last, long long taps) {
+                B.piece_dh[p] = d;
+                if (first) B.s_first[sidx] = p;
+                if (last) B.s_last[sidx] = p;
+                p += 1;
+                d += taps;
+            });
+        }
+    }
+    // ---- work lists of the forward and the spectra, one contiguous chunk of utterances
+    // per thread, laid out by one block-wide exclusive scan of the per-thread counts
+    constexpr int kNL = 2 * kNumBuckets;           // (list kind, size) pairs
     int cnt[kNL];
 #pragma unroll
     for (int q = 0; q < kNL; ++q) cnt[q] = 0;
@@ -394,18 +509,14 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
 #pragma unroll
         for (int q = 0; q < kNumBuckets; ++q) {
             if (q != b) continue;
-            bool big;
-            const int nb = bwd_tiles(u, q, &big);
             cnt[q] += B.seg0[u + 1] - B.seg0[u];
-            cnt[(big ? 1 : 2) * kNumBuckets + q] += nb;
-            cnt[3 * kNumBuckets + q] += B.rir0[u + 1] - B.rir0[u];
+            cnt[kNumBuckets + q] += B.rir0[u + 1] - B.rir0[u];
         }
     }
     __shared__ int wtot[kPlanThreads / 32][kNL];
     __shared__ int ltot[kNL];
     int off[kNL];
     {
-        const int lane = t & 31, wid = t >> 5;
 #pragma unroll
         for (int q = 0; q < kNL; ++q) {
             int incl = cnt[q];
@@ -430,39 +541,28 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < kNL; ++q) off[q] += wtot[wid][q];
-        // the small backward tiles follow all the big ones of their size
-#pragma unroll
-        for (int q = 0; q < kNumBuckets; ++q) off[2 * kNumBuckets + q] += ltot[kNumBuckets + q];
     }
     for (int u = u0; u < u1; ++u) {
         const int m = B.logN[u];
         if (m == 0) continue;
         const int b = m - kMinLog;
         int32_t* lf = Q.lst(kListFwd, b);
-        int32_t* lb = Q.lst(kListBwd, b);
         int32_t* ls = Q.lst(kListSpec, b);
-        int of = 0, ob = 0, os = 0, nbt = 0;
+        int of = 0, os = 0;
 #pragma unroll
         for (int q = 0; q < kNumBuckets; ++q) {
             if (q != b) continue;
-            bool big;
-            nbt = bwd_tiles(u, q, &big);
-            const int kb = (big ? 1 : 2) * kNumBuckets + q;
-            of = off[q]; ob = off[kb]; os = off[3 * kNumBuckets + q];
+            of = off[q]; os = off[kNumBuckets + q];
             off[q] += B.seg0[u + 1] - B.seg0[u];
-            off[kb] += nbt;
-            off[3 * kNumBuckets + q] += B.rir0[u + 1] - B.rir0[u];
+            off[kNumBuckets + q] += B.rir0[u + 1] - B.rir0[u];
         }
         for (int g = B.seg0[u]; g < B.seg0[u + 1]; ++g) lf[of++] = g;
-        const int sg = bwd_src_group(m);
-        for (int q = 0; q < B.bnt[u]; ++q)
-            for (int i0 = 0; i0 < B.n_src[u]; i0 += sg) lb[ob++] = (B.bseg0[u] + q) * kMaxSources + i0;
         for (int r = B.rir0[u]; r < B.rir0[u + 1]; ++r) ls[os++] = r;
     }
     if (t < kNumBuckets) {
         Q.count[Q.idx(kListFwd, t)] = ltot[t];
-        Q.count[Q.idx(kListBwd, t)] = ltot[kNumBuckets + t] + ltot[2 * kNumBuckets + t];
-        Q.count[Q.idx(kListSpec, t)] = ltot[3 * kNumBuckets + t];
+        Q.count[Q.idx(kListSpec, t)] = ltot[kNumBuckets + t];
+        Q.count[Q.idx(kListBwd, t)] = 0;
         Q.next[Q.idx(kListFwd, t)] = 0;
         Q.next[Q.idx(kListBwd, t)] = 0;
         Q.next[Q.idx(kListSpec, t)] = 0;

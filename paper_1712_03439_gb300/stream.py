@@ -9,8 +9,9 @@ copied back.  Per batch the host wall time from admission to results on the
 host, and the device time between its first copy and its last, are recorded.
 
 The footprint estimate follows the plan's scratch layout (RIR spectra at the
-largest allowed FFT size, per-segment carries and dh partials); after the plan
-is made its real scratch size replaces the estimate in the record.
+largest allowed FFT size, per-segment carries, the backward partition and its
+RIR-gradient partials); after the plan is made its real scratch size replaces
+the estimate in the record.
 """
 from __future__ import annotations
 
@@ -31,39 +32,66 @@ _POWER_CHUNK = 32768
 PLAN_FIXED_BYTES = 2 << 20
 
 
+# CTAs of the backward launches of all FFT sizes together (the partition allots
+# one chunk to each): SMs x (2 + 2 + 1 + 1) on a 152-SM GB300
+PART_CTAS = 152 * 6
+
+
 def utterance_bytes(nx: int, n_src: int, n_mics: int, rir_sum: int, nh_max: int, *,
-                    backward: bool = True, output_mode: int = 0, seg_len: int = 16384,
-                    bwd_seg_len: int = 16384) -> int:
+                    backward: bool = True, output_mode: int = 0, seg_len: int = 16384) -> int:
     """Device bytes one utterance adds to a batch: its buffers plus its share of
-    the plan's scratch (an estimate of the library's allocation)."""
+    the plan's scratch (an estimate of the library's allocation; the backward
+    partition's per-CTA share is in partition_bytes)."""
     ny = nx + (nh_max - 1 if output_mode else 0)
     buf = 4 * (n_src * nx + rir_sum + n_mics * ny) + 8 * n_src
     if backward:
         buf += 4 * (n_mics * ny + n_src * nx + rir_sum) + 4 * n_src
     nseg = -(-nx // max(seg_len, 1 << _MAX_LOG))
-    nbseg = -(-nx // max(bwd_seg_len, 1 << _MAX_LOG))
     scratch = 8 * n_src * n_mics * _MMAX                 # RIR spectra
     scratch += 4 * nseg * n_mics * 2 * _MMAX             # segment carries
-    scratch += 4 * nbseg * rir_sum                       # dh partials
+    scratch += 4 * rir_sum                               # RIR-gradient partials (one piece per stream)
     scratch += 8 * n_src * (-(-nx // _POWER_CHUNK))      # power partial sums
-    scratch += 4 * 3 * 4 * max(nbseg * 16, nseg, n_src * n_mics) + 256
-    scratch += 4                                         # backward tiles of the utterance
+    scratch += 4 * 3 * 4 * max(nseg, n_src * n_mics) + 256
+    # backward streams: order and cost prefix per size, first and last piece, one piece
+    # with its partial offset and source-gain partials
+    scratch += n_src * (4 * 4 + 8 * 4 + 4 + 4 + 8 + 4 * 16)
     return int(buf + scratch)
+
+
+def partition_bytes(utt_taps_max: int, ctas: int = PART_CTAS) -> int:
+    """The backward partition's per-CTA scratch: one extra piece per CTA boundary
+    (partial offset, source-gain partials, RIR-gradient partials of up to the
+    largest utterance's taps) and the chunk starts."""
+    return int(ctas * (8 + 4 * 16 + 4 * utt_taps_max + 3 * 4))
+
+
+def group_bytes(batch: synth.Batch, utts, **kw) -> int:
+    """Estimated device footprint of a batch made of the given utterances."""
+    ri = batch.rir_index()
+    total, taps_max = PLAN_FIXED_BYTES, 0
+    for u in utts:
+        lens = batch.rir_len[ri[u]:ri[u + 1]]
+        total += utterance_bytes(int(batch.num_samples[u]), int(batch.num_sources[u]), batch.num_mics,
+                                 int(lens.sum()), int(lens.max()), **kw)
+        taps_max = max(taps_max, int(lens.sum()))
+    return int(total + partition_bytes(taps_max))
 
 
 def admit(batch: synth.Batch, budget_bytes: int, **kw) -> list[range]:
     """Consecutive groups of utterances whose estimated footprint fits the budget
     (an utterance larger than the budget forms a group of its own)."""
     ri = batch.rir_index()
-    groups, start, used = [], 0, PLAN_FIXED_BYTES
+    groups, start, used, taps_max = [], 0, PLAN_FIXED_BYTES, 0
     for u in range(batch.num_utts):
         lens = batch.rir_len[ri[u]:ri[u + 1]]
         b = utterance_bytes(int(batch.num_samples[u]), int(batch.num_sources[u]), batch.num_mics,
                             int(lens.sum()), int(lens.max()), **kw)
-        if u > start and used + b > budget_bytes:
+        taps = int(lens.sum())
+        if u > start and used + b + partition_bytes(max(taps_max, taps)) > budget_bytes:
             groups.append(range(start, u))
-            start, used = u, PLAN_FIXED_BYTES
+            start, used, taps_max = u, PLAN_FIXED_BYTES, 0
         used += b
+        taps_max = max(taps_max, taps)
     if start < batch.num_utts:
         groups.append(range(start, batch.num_utts))
     return groups

@@ -72,12 +72,9 @@ def test_stream_batches_cover_queue_within_budget_and_match_oracle():
 
 def test_admission_estimate_bounds_the_real_footprint():
     # the estimate the batcher admits by is an upper bound of buffers + real scratch
-    from paper_1712_03439_gb300.stream import PLAN_FIXED_BYTES, Streamer, admit, utterance_bytes
+    from paper_1712_03439_gb300.stream import Streamer, admit, group_bytes
     b = synth.config_stream(seed=171203443 + 7, n_utts=40)
-    ri = b.rir_index()
-    est = PLAN_FIXED_BYTES + sum(utterance_bytes(int(b.num_samples[u]), int(b.num_sources[u]), b.num_mics,
-                              int(b.rir_len[ri[u]:ri[u + 1]].sum()), int(b.rir_len[ri[u]:ri[u + 1]].max()))
-              for u in range(b.num_utts))
+    est = group_bytes(b, range(b.num_utts))
     st = Streamer(budget_bytes=1 << 40, keep_outputs=False)
     res = st.run(b, groups=[range(b.num_utts)])
     assert res.records[0].footprint_bytes <= est

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from paper_1712_03439_gb300 import synth
-from paper_1712_03439_gb300.stream import PLAN_FIXED_BYTES, admit, utterance_bytes
+from paper_1712_03439_gb300.stream import admit, group_bytes, utterance_bytes
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -34,12 +34,12 @@ def test_admission_covers_the_queue_in_order_within_budget(budget_mb):
     groups = admit(b, budget)
     assert [u for g in groups for u in g] == list(range(b.num_utts))
     for g in groups:
-        need = PLAN_FIXED_BYTES + sum(_utt_bytes(b, u) for u in g)
+        need = group_bytes(b, g)
         # a group fits, or it is a single utterance too large for any group
         assert need <= budget or len(g) == 1
         # greedy: the next utterance would not have fitted
         if g.stop < b.num_utts:
-            assert need + _utt_bytes(b, g.stop) > budget
+            assert group_bytes(b, range(g.start, g.stop + 1)) > budget
 
 
 def test_admission_counts_the_backward_and_the_full_output():
