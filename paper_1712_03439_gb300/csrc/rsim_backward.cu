@@ -360,8 +360,13 @@ struct BwdTmCfg {
     static constexpr size_t o_sm = 0;
     static constexpr size_t o_st = o_sm + 2 * SM_LEN;
     static constexpr size_t o_tw = a16(o_st + 2 * ST_LEN);
-    static constexpr size_t bytes = a16(o_tw + sizeof(float2) * FftPlan<M, E>::TW_LEN);
+    // the current source's RIR spectra (one microphone group), staged by bulk copies
+    // issued before its forward transform: where one CTA per SM leaves the room
+    static constexpr bool kStageH = kMinBlocks == 1;
+    static constexpr size_t o_hs = a16(o_tw + sizeof(float2) * FftPlan<M, E>::TW_LEN);
+    static constexpr size_t bytes = a16(o_hs + (kStageH ? sizeof(float2) * kJG * M : 0));
     static_assert(T % 128 == 0, "every TMEM lane quadrant holds whole runs of columns");
+    static_assert(bytes <= 227 * 1024 - 1024, "shared memory of one CTA");
     static_assert(IG >= 1 && IG <= kMaxSources, "source group");
 };
 
@@ -381,8 +386,9 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
     Exch<2> ex{reinterpret_cast<float2*>(smem_raw + L::o_sm),
                reinterpret_cast<float2*>(smem_raw + L::o_sm + L::SM_LEN), 0};
     float* st0 = reinterpret_cast<float*>(smem_raw + L::o_st);
+    float2* hs = reinterpret_cast<float2*>(smem_raw + L::o_hs);
     __shared__ double sd[32];
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t mbar[3];      // two input stages, the RIR spectra
     __shared__ uint32_t tmem_base;
     const int t = threadIdx.x;
     if (chunk_empty(B, bucket, blockIdx.x)) return;   // before any TMEM is taken
@@ -393,6 +399,7 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
     if (t == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
+        mbar_init(&mbar[2], 1);
         mbar_init_fence();
     }
     float2* tws = reinterpret_cast<float2*>(smem_raw + L::o_tw);
@@ -405,13 +412,23 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
     // accumulator s of this thread: columns s * kWCols + (its run) of its lane
     const uint32_t tacc = tmem_thread_addr<E>(tmem_base, t);
     auto wslot = [&](int s) { return tacc + (uint32_t)(s * L::kWCols); };
-    uint32_t ph = 0;                             // bit b: parity of the next phase of stage b
+    uint32_t ph = 0;                             // bit b: parity of the next phase of barrier b
     int off0 = 0, off1 = 0;                      // float offset of the data in stage 0 / 1
     bool bad = false;                            // a bounded wait ran out (no new copies then)
     // first bin of this thread's pairs: t (pair layout) or its paired butterfly
     const int kt = kPaired ? paired_butterfly<T>(t) : t;
     int sc = 0;                                  // stage holding the next transform input
     auto stage = [&](int k) { return st0 + k * (2 * M + 8); };
+    // waits (bounded) for barrier b's current phase; a wait that runs out marks the
+    // CTA bad after one more bounded chance for the copy to land
+    auto wait_bar = [&](int b) {
+        if (!bad && !mbar_wait_bounded(&mbar[b], (ph >> b) & 1u)) {
+            mbar_wait_bounded(&mbar[b], (ph >> b) & 1u, 100000000ull);
+            bad = true;
+        }
+        ph ^= 1u << b;
+    };
+    bool h_pending = false;                      // a spectrum copy was issued and not yet waited for
     bool stop = false;                           // a wait ran out: the remaining pieces are skipped
     for_each_piece(B, bucket, blockIdx.x, [&](int pc, int, int u, int i0, int64_t b0, int64_t b1) {
         if (stop) return;
@@ -445,13 +462,7 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
             };
             // takes the staged input of step k into v and queues the next step's
             auto next_input = [&](float2 (&v)[E], int64_t b, int k) {
-                if (!bad && !mbar_wait_bounded(&mbar[sc], (ph >> sc) & 1u)) {
-                    // give the copy one more bounded chance to land before the
-                    // stage is abandoned, so none is left in flight at exit
-                    mbar_wait_bounded(&mbar[sc], (ph >> sc) & 1u, 100000000ull);
-                    bad = true;
-                }
-                ph ^= 1u << sc;
+                wait_bar(sc);
                 load_staged_at<M, E>(v, stage(sc), sc ? off1 : off0, t);
                 if (!bad) {
                     if (k + 1 < nsteps) stage_step(sc ^ 1, b, k + 1);
@@ -480,6 +491,19 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
 #pragma unroll 1
                 for (int k = 0; k < nsteps; ++k) {
                     float2 v[E], Z[E];
+                    if constexpr (L::kStageH) {
+                        // a source step: its RIR spectra move into hs while its forward
+                        // transform runs (the previous source's readers of hs passed the
+                        // barriers of its inverse transform)
+                        if (k >= jn && !bad) h_pending = true;
+                        if (k >= jn && t == 0 && !bad) {
+                            fence_proxy_async_smem();
+                            mbar_arrive_expect_tx(&mbar[2], (uint32_t)(jn * M * sizeof(float2)));
+                            for (int jj = 0; jj < jn; ++jj)
+                                bulk_copy_g2s(hs + jj * M, Hc + (int64_t)(rb + (i0 + k - jn) * J + j0 + jj) * B.MMAX,
+                                              (uint32_t)(M * sizeof(float2)), &mbar[2]);
+                        }
+                    }
                     next_input(v, b, k);
                     if constexpr (kPaired) {
                         rfft_paired<M, E, false>(Z, v, ex, tw, t, kt);
@@ -521,15 +545,26 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
                     float2 C[E];
 #pragma unroll
                     for (int e = 0; e < E; ++e) C[e] = make_float2(0.f, 0.f);
+                    if constexpr (L::kStageH) {
+                        if (h_pending && bad) {
+                            // a stage wait ran out after this copy was issued: still let it land
+                            mbar_wait_bounded(&mbar[2], (ph >> 2) & 1u, 100000000ull);
+                            ph ^= 1u << 2;
+                        } else if (h_pending) {
+                            wait_bar(2);
+                        }
+                        h_pending = false;
+                    }
 #pragma unroll
                     for (int jj = 0; jj < kJG; ++jj) {
                         if (jj >= jn) break;
-                        const float4* Hg = reinterpret_cast<const float4*>(
-                            Hc + (int64_t)(rb + (i0 + i) * J + j0 + jj) * B.MMAX);
+                        const float4* Hg = L::kStageH ? reinterpret_cast<const float4*>(hs + jj * M)
+                                                      : reinterpret_cast<const float4*>(
+                                                            Hc + (int64_t)(rb + (i0 + i) * J + j0 + jj) * B.MMAX);
 #pragma unroll
                         for (int q = 0; q < E / 2; ++q) {
                             const int kb = kt + q * T;
-                            const float4 hh = __ldg(Hg + kb);
+                            const float4 hh = L::kStageH ? Hg[kb] : __ldg(Hg + kb);
                             const float2 ha = make_float2(hh.x, hh.y), hb = make_float2(hh.z, hh.w);
                             const float2 ga = jj ? G[1][2 * q] : G[0][2 * q];
                             const float2 gb = jj ? G[1][2 * q + 1] : G[0][2 * q + 1];

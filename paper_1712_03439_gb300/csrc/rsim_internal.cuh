@@ -87,9 +87,9 @@ struct Queues {
 // The backward work of one FFT size is a sequence of streams -- (utterance, group
 // of up to bwd_src_group(log2 N) of its sources), in batch order, each the
 // utterance's nblk blocks long -- and each block of a stream costs
-// groups(J) * 2 I_g + J transforms (I_g sources in the group).  The planner cuts
-// the sequence at block boundaries into one chunk per CTA of the launch, of
-// equal cost; a chunk is a list of pieces, the parts of the streams it covers
+// kCostMic J + kCostSrc groups(J) I_g (I_g sources in the group), plus the
+// stream's flush at its end.  The planner cuts the sequence at block boundaries
+// into one chunk per CTA of the launch, of equal cost; a chunk is a list of pieces, the parts of the streams it covers
 // (piece p: stream s, blocks [b0, b1)).  Pieces are numbered in sequence
 // order, so a stream's pieces are consecutive (s_first[s] .. s_last[s]).
 // Calls f(p, s, u, i0, b0, b1) for every piece of CTA k of size bucket b, in
@@ -117,6 +117,16 @@ __device__ __forceinline__ bool chunk_empty(const DevBatch& B, int b, int k) {
     const int64_t o = (int64_t)b * (B.PMAX + 1) + k;
     return B.cta_sp[o] == B.cta_sp[o + 1] && B.cta_b[o] >= B.cta_b[o + 1];
 }
+
+// Backward cost model of the partition (relative units measured on GB300 at N =
+// 8192, per-CTA times fitted to 2%): a microphone step (one forward transform)
+// costs kCostMic, a source step (forward transform, RIR-gradient update, spectral
+// products, inverse and dx stores) kCostSrc; a stream also pays kCostFlush per
+// RIR-gradient inverse at its end and kCostPiece once.
+constexpr int kCostMic = 235;
+constexpr int kCostSrc = 607;
+constexpr int kCostFlush = 318;
+constexpr int kCostPiece = 183;
 
 // Sources per backward stream of each FFT size: the TMEM-accumulator kernels
 // (N <= 8192) keep the RIR-gradient spectra of that many sources times two

@@ -315,6 +315,12 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
     const int u0 = min(B.U, t * per), u1 = min(B.U, u0 + per);
     const int ngrp_j = (B.J + kJG - 1) / kJG;
     const int lane = t & 31, wid = t >> 5;
+    // cost of one block of a stream of ig sources, and of the whole stream (its
+    // blocks, then the flush of its RIR-gradient accumulators)
+    auto block_cost = [&](int ig) { return kCostMic * B.J + kCostSrc * ngrp_j * ig; };
+    auto stream_total = [&](int nb, int ig) {
+        return (long long)nb * block_cost(ig) + (long long)kCostFlush * ig * B.J + kCostPiece;
+    };
     // ---- backward partition, step 1: the streams of each size in batch order and the
     // exclusive prefix of their costs (utterances in contiguous chunks per thread)
     {
@@ -331,7 +337,7 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
                 if (q != m - kMinLog) continue;
                 for (int i0 = 0; i0 < I; i0 += sg) {
                     ns[q] += 1;
-                    cs[q] += (long long)B.nblk[u] * (ngrp_j * 2 * min(sg, I - i0) + B.J);
+                    cs[q] += stream_total(B.nblk[u], min(sg, I - i0));
                 }
             }
         }
@@ -382,7 +388,7 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
                     B.sord[(int64_t)q * B.S + on[q]] = B.src0[u] + i0;
                     B.spre[(int64_t)q * (B.S + 1) + on[q]] = oc[q];
                     on[q] += 1;
-                    oc[q] += (long long)B.nblk[u] * (ngrp_j * 2 * min(sg, I - i0) + B.J);
+                    oc[q] += stream_total(B.nblk[u], min(sg, I - i0));
                 }
             }
         }
@@ -394,11 +400,11 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
         const int u = B.src_utt[sidx];
         const int sg = bwd_src_group(kMinLog + q);
         *u_out = u;
-        return ngrp_j * 2 * min(sg, B.n_src[u] - (sidx - B.src0[u])) + B.J;
+        return block_cost(min(sg, B.n_src[u] - (sidx - B.src0[u])));
     };
     // ---- step 2: where each CTA's chunk starts.  CTA k of size q starts at the first
-    // block whose cost position is at least ceil(k T / P); the end sentinel k = P is
-    // (streams, 0)
+    // block whose cost position is at least ceil(k T / P) (a position inside a
+    // stream's flush is its end); the end sentinel k = P is (streams, 0)
     const int PM = B.PMAX + 1;
     for (int idx = t; idx < kNumBuckets * PM; idx += kPlanThreads) {
         const int q = idx / PM, k = idx - q * PM;
