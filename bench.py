@@ -839,9 +839,29 @@ def run_rooms(args):
     e1.record(st)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    clocks = clock.stop()
     q = plan.query()
     plan.close()
+    # the fused step: RIRs made where they are consumed (generation and cut-off in one
+    # kernel, only the kept taps written), then forward and backward
+    fplan = Plan.for_batch(b, eta_db=ETA_DB, gain_mode=0, device=0, rooms=True)
+    fgains, fy = torch.empty(fplan.S, device=dev), torch.empty(fplan.y_size, device=dev)
+    fgx, fgr, fgg = torch.empty_like(x), torch.empty_like(rir), torch.empty_like(fgains)
+
+    def fused_step():
+        fplan.filter_mix_rooms(x, g_d, fgains, fy, snr_db=snr, order=order)
+        fplan.filter_mix_backward(gy, x, fgains, fgx, fgr, fgg)
+    for _ in range(max(args.warmup, 3)):
+        fused_step()
+    fplan.sync_status()
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(args.steps):
+        fused_step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    fms = e0.elapsed_time(e1) / args.steps
+    fplan.close()
+    clocks = clock.stop()
     line = {"metric": "simulated audio s/sec (image-method RIRs + fwd + bwd) at 16 kHz, 1xGB300",
             "value": audio_s / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "dtype": "f32",
@@ -857,6 +877,11 @@ def run_rooms(args):
                              "inputs (x 0.35 GB) are larger than L2"},
             "image_rirs": {"ms": img_ms, "launches_timed": n_img, "rirs_per_s": geom.shape[0] / (img_ms / 1e3),
                            "roofline": img_roof},
+            "fused": {"value": audio_s / (fms / 1e3), "unit": UNIT, "ms_per_step": fms,
+                      "what": "rsim_filter_mix_rooms: each RIR's images land in shared memory, the cut-off "
+                              "is taken there and only the kept taps are written; then the spectra, "
+                              "forward and backward (the headline value above is the two-call step: "
+                              "rsim_image_rirs writes every tap, rsim_filter_mix reads them)"},
             "clocks": clocks}
     if not args.no_cpu_baseline:
         import oracle

@@ -91,6 +91,11 @@ typedef struct {
                                       Ny = Nx + (longest RIR of the utterance) - 1 */
     int32_t snr_ref_mic;           /* gain_mode 3: the microphone j (0 <= j < J) whose
                                       reverberant signal sets the SNRs; ignored otherwise */
+    int32_t rooms;                 /* 1: the plan also serves rsim_filter_mix_rooms (RIRs made
+                                      from room geometry on the device; reserves the kept taps,
+                                      sum Nh floats); needs gain_mode 0, 1 or 2, every Nh at
+                                      most 40960 and an RIR within the largest FFT size's
+                                      reach (no partitioned convolution); 0: not */
 } rsim_plan_desc;
 
 /* Creates a plan for the given shapes on CUDA device `device`.  Validates the
@@ -330,6 +335,32 @@ typedef struct {
 rsim_status rsim_image_rirs(void *stream, int32_t num_rirs, const rsim_image_geom *geom,
                             const int64_t *rir_off, int64_t max_len, int32_t order, float fs, float c0,
                             float *rir, int32_t *status);
+
+/* ---- RIRs generated where they are consumed (Eq. 1 into Eq. 7-9 and Eq. 2) --
+ *
+ * The forward of rsim_filter_mix with the RIRs made on the device from room
+ * geometry instead of read from the caller: one kernel per call lands every
+ * image of each RIR (Eq. 1, as rsim_image_rirs computes it, the plan's
+ * rir_len[r] taps) in on-chip shared memory, takes the Eq. 7-9 cut-off there
+ * with the same decision as rsim_filter_mix, and writes only the kept taps
+ * [0, L) to the plan's scratch, from which the RIR spectra are taken; the full
+ * RIRs never pass through device memory unless rir_out asks for them.  The plan
+ * must have been made with rooms = 1.
+ *   geom       [R] device, one room geometry per RIR in RIR index order (the
+ *              room, source and microphone of RIR r = rir0_u + i J + j)
+ *   order      K in [0, 32]: (2K + 1)^3 virtual rooms
+ *   fs, c0     sampling rate (Hz) and speed of sound (m/s), finite and > 0
+ *   rir_out    [sum Nh] device or NULL: if given, receives every tap of the
+ *              generated RIRs (as rsim_image_rirs would write them)
+ *   the other arguments as rsim_filter_mix.
+ * A geometry that is invalid or puts an image at the microphone gives that
+ * RIR all zeros (L = 1) and is reported as RSIM_E_INVALID by
+ * rsim_plan_sync_status.  A later rsim_filter_mix_backward on the plan is the
+ * adjoint of this forward, with dh over the generated RIRs' taps.
+ * Asynchronous; graphs as for rsim_filter_mix. */
+rsim_status rsim_filter_mix_rooms(rsim_plan_t plan, void *stream, const float *x, const rsim_image_geom *geom,
+                                  int32_t order, float fs, float c0, const float *snr_db, float *gains,
+                                  float *y, int32_t *trunc_len, float *energy_kept_frac, float *rir_out);
 
 /* Message describing the calling thread's last error ("" if none). */
 const char *rsim_last_error(void);

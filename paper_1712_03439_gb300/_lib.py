@@ -19,7 +19,8 @@ STATUS_NAMES = {0: "RSIM_OK", 1: "RSIM_E_INVALID", 2: "RSIM_E_UNSUPPORTED", 3: "
 EXPORTED = ["rsim_plan", "rsim_filter_mix", "rsim_filter_mix_backward", "rsim_plan_sync_status",
             "rsim_plan_query", "rsim_plan_set_timing", "rsim_plan_stage_times",
             "rsim_plan_scratch_bytes", "rsim_plan_destroy", "rsim_source_gains_noalloc",
-            "rsim_image_rirs", "rsim_plan_log_mel", "rsim_plan_log_mel_rows", "rsim_last_error"]
+            "rsim_image_rirs", "rsim_plan_log_mel", "rsim_plan_log_mel_rows", "rsim_filter_mix_rooms",
+            "rsim_last_error"]
 STAGES = ["truncate", "power", "plan", "spectrum", "forward", "fixup", "backward", "finalize"]
 
 
@@ -45,6 +46,7 @@ class PlanDesc(ctypes.Structure):
         ("disable_graphs", ctypes.c_int32),
         ("output_mode", ctypes.c_int32),
         ("snr_ref_mic", ctypes.c_int32),
+        ("rooms", ctypes.c_int32),
     ]
 
 
@@ -79,6 +81,8 @@ def load(path: str | None = None):
     lib.rsim_plan.argtypes = [ctypes.POINTER(PlanDesc), ctypes.c_int, ctypes.POINTER(P)]
     lib.rsim_filter_mix.restype = ctypes.c_int
     lib.rsim_filter_mix.argtypes = [P, P, P, P, P, P, P, P, P]
+    lib.rsim_filter_mix_rooms.restype = ctypes.c_int
+    lib.rsim_filter_mix_rooms.argtypes = [P, P, P, P, i32, ctypes.c_float, ctypes.c_float, P, P, P, P, P, P]
     lib.rsim_filter_mix_backward.restype = ctypes.c_int
     lib.rsim_filter_mix_backward.argtypes = [P, P, P, P, P, P, P, P]
     lib.rsim_plan_sync_status.restype = ctypes.c_int

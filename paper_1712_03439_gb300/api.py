@@ -39,7 +39,7 @@ class Plan:
 
     def __init__(self, num_sources, num_samples, rir_len, num_mics, eta_db=20.0,
                  fft_sizes=None, gain_mode=0, segment_len=0, bwd_segment_len=0, fft_cost=None,
-                 device=None, graphs=True, output_mode=0, snr_ref_mic=0):
+                 device=None, graphs=True, output_mode=0, snr_ref_mic=0, rooms=False):
         self._lib = _lib.load()
         self._handle = None
         self.num_sources = np.ascontiguousarray(num_sources, dtype=np.int32)
@@ -78,7 +78,8 @@ class Plan:
             gain_mode=self.gain_mode, segment_len=int(segment_len),
             bwd_segment_len=int(bwd_segment_len),
             fft_cost=None if self._cost is None else self._cost.ctypes.data,
-            disable_graphs=0 if graphs else 1, output_mode=self.output_mode, snr_ref_mic=int(snr_ref_mic))
+            disable_graphs=0 if graphs else 1, output_mode=self.output_mode, snr_ref_mic=int(snr_ref_mic),
+            rooms=1 if rooms else 0)
         h = ctypes.c_void_p()
         _lib.check(self._lib, self._lib.rsim_plan(ctypes.byref(desc), self.device, ctypes.byref(h)))
         self._handle = h
@@ -120,6 +121,27 @@ class Plan:
         st = self._lib.rsim_filter_mix(self._handle, _stream(stream), _ptr(x), _ptr(rir),
                                        _ptr(snr_db), _ptr(gains), _ptr(y), _ptr(trunc_len),
                                        _ptr(energy_kept_frac))
+        _lib.check(self._lib, st)
+        self.forward_count += 1
+
+    def filter_mix_rooms(self, x, geom, gains, y, snr_db=None, trunc_len=None, energy_kept_frac=None,
+                         rir_out=None, order=8, fs=16000.0, c0=343.0, stream=None):
+        """rsim_filter_mix_rooms: the forward with the RIRs made on the device from
+        room geometry (geom: float32 CUDA tensor [R, 10], rows of room (3),
+        source (3), microphone (3), r); needs a plan made with rooms=True."""
+        _want(x, self.x_size, torch.float32, "x")
+        if not isinstance(geom, torch.Tensor) or not geom.is_cuda or geom.dtype != torch.float32 \
+                or not geom.is_contiguous() or tuple(geom.shape) != (self.R, 10):
+            raise ValueError(f"geom must be a contiguous float32 CUDA tensor of shape [{self.R}, 10]")
+        _want(gains, self.G, torch.float32, "gains")
+        _want(y, self.y_size, torch.float32, "y")
+        _want(snr_db, self.S, torch.float32, "snr_db")
+        _want(trunc_len, self.R, torch.int32, "trunc_len")
+        _want(energy_kept_frac, self.R, torch.float32, "energy_kept_frac")
+        _want(rir_out, self.rir_size, torch.float32, "rir_out")
+        st = self._lib.rsim_filter_mix_rooms(self._handle, _stream(stream), _ptr(x), _ptr(geom), int(order),
+                                             float(fs), float(c0), _ptr(snr_db), _ptr(gains), _ptr(y),
+                                             _ptr(trunc_len), _ptr(energy_kept_frac), _ptr(rir_out))
         _lib.check(self._lib, st)
         self.forward_count += 1
 

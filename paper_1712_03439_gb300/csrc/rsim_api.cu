@@ -144,6 +144,13 @@ struct rsim_plan_s {
     // buffer of the last forward (the backward's gain gradient reads it)
     float* ones = nullptr;
     const float* fwd_rir = nullptr;
+    // RIRs from room geometry (rsim_filter_mix_rooms): the kept taps, the launch shape of
+    // the fused generation and cut-off, its graphs and the scalar arguments they hold
+    float* rir_kept = nullptr;
+    int nh_max = 1, grid_cut = 1;
+    GraphCache grooms;
+    int32_t rooms_order = -1;
+    float rooms_fs = 0.f, rooms_c0 = 0.f;
     // gains from reverberant SNRs (gain_mode 3): a plan over the sources, each its own
     // one-microphone utterance with its RIR to the reference microphone, whose output
     // (laid out like x) feeds the source-power scan; the RIRs are gathered for it
@@ -287,6 +294,7 @@ extern "C" void rsim_plan_destroy(rsim_plan_t plan) {
         if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
         plan->gfwd.destroy();
         plan->gbwd.destroy();
+        plan->grooms.destroy();
         if (plan->cap) cudaStreamDestroy(plan->cap);
         if (plan->aux) cudaStreamDestroy(plan->aux);
         if (plan->ev_aux) cudaEventDestroy(plan->ev_aux);
@@ -377,6 +385,7 @@ rsim_status make_partitioned(rsim_plan_t p, const rsim_plan_desc* d, int device,
     pd.output_mode = 0;
     pd.disable_graphs = 1;
     pd.snr_ref_mic = 0;
+    pd.rooms = 0;
     rsim_status st = rsim_plan(&pd, device, &p->part);
     if (st != RSIM_OK) return fail(st, "partitioned plan: " + g_err);
     // one allocation: tables, then the virtual buffers
@@ -472,6 +481,10 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
         for (int64_t r = 0; r < r_all; ++r) nh_all = std::max<int64_t>(nh_all, d->rir_len[r]);
         partitioned = nh_all > 3 * ((int64_t)1 << part_log) / 4 + 1;
     }
+    if (d->rooms != 0 && d->rooms != 1) return fail(RSIM_E_INVALID, "rooms must be 0 or 1");
+    if (d->rooms && (partitioned || d->gain_mode == 3))
+        return fail(RSIM_E_UNSUPPORTED, "rooms = 1 needs gain_mode 0, 1 or 2 and every RIR within the "
+                                        "largest FFT size's reach (no partitioned convolution)");
     if (partitioned && (d->output_mode != 0 || d->gain_mode > 1))
         return fail(RSIM_E_UNSUPPORTED, "RIRs longer than the largest FFT size reaches (partitioned "
                                         "convolution) need output_mode 0 and gain_mode 0 or 1");
@@ -514,6 +527,10 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     seg0[U] = (int32_t)nseg;
     yoff[U] = ysz;
     std::vector<int32_t> rlen(d->rir_len, d->rir_len + R);
+    int nh_max = 1;
+    for (int64_t r = 0; r < R; ++r) nh_max = std::max(nh_max, rlen[r]);
+    if (d->rooms && nh_max > kCutMaxTaps)
+        return fail(RSIM_E_UNSUPPORTED, "rooms = 1 holds each RIR in shared memory: rir_len must be at most 40960");
     std::vector<int64_t> roff(R + 1), xoff(S + 1);
     roff[0] = 0;
     for (int64_t r = 0; r < R; ++r) {
@@ -560,6 +577,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     // ---- carve one device allocation
     struct Piece { void** dst; size_t bytes; };
     std::vector<Piece> pieces;
+    void* p_kept = nullptr;
     void *p_sord, *p_spre, *p_nstream, *p_ctasp, *p_ctab, *p_ctap, *p_piecedh, *p_sfirst, *p_slast;
     void *p_srcutt, *p_rirutt;
     void *p_nsrc, *p_nx, *p_ny, *p_src0, *p_rir0, *p_seg0, *p_segutt, *p_xoff, *p_yoff, *p_roff, *p_rlen,
@@ -633,6 +651,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     pieces.push_back({&p_dap, sizeof(float) * npiece * kMaxSources});
     pieces.push_back({&p_melrow, sizeof(int64_t) * (U + 1)});
     pieces.push_back({&p_ones, sizeof(float) * std::max<int64_t>(S, 1)});
+    if (d->rooms) pieces.push_back({&p_kept, sizeof(float) * std::max<int64_t>(roff[R], 1)});
     // gain_mode 3: each source's RIR to the reference microphone, gathered, and the
     // reverberant sources (laid out like x)
     std::vector<int64_t> rev_src(S), rev_dst(S + 1, 0);
@@ -752,6 +771,12 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     p->Hc = (float2*)p_Hc; p->tails = (float*)p_tails; p->dhp = (float*)p_dhp; p->dap = (float*)p_dap;
     p->mel_row_off = (int64_t*)p_melrow;
     p->ones = (float*)p_ones;
+    p->rir_kept = (float*)p_kept;
+    p->nh_max = nh_max;
+    if (d->rooms) {
+        DeviceGuard g0(device);
+        p->grid_cut = image_cut_grid(nh_max, (int)R, p->sms);
+    }
     p->rev_src_off = (const int64_t*)p_rsrc;
     p->rev_dst_off = (const int64_t*)p_rdst;
     p->rev_rir = (float*)p_rrir;
@@ -809,6 +834,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
         rd.output_mode = 0;
         rd.disable_graphs = 1;
         rd.snr_ref_mic = 0;
+        rd.rooms = 0;
         const rsim_status rs = rsim_plan(&rd, device, &p->rev);
         if (rs != RSIM_OK) {
             const std::string msg = "reverberant-SNR plan: " + g_err;
@@ -829,10 +855,19 @@ void sum_segs(const rsim_plan_s::Sums& g, const float* in, float* out, cudaStrea
     if (g.n > 0) k_sum_segs<<<(unsigned)std::min<int64_t>(g.n, 4096), 256, 0, st>>>(g, in, out);
 }
 
+// Room geometry of rsim_filter_mix_rooms: the RIRs are made on the device with
+// the cut-off fused (their kept taps land in p->rir_kept)
+struct RoomsCall {
+    const rsim_image_geom* geom;
+    int order;
+    float fs, c0;
+    float* rir_out;
+};
+
 // The forward launch sequence on stream st (eager, or recorded by a capture).
 cudaError_t enqueue_forward(rsim_plan_t p, cudaStream_t st, const float* x, const float* rir,
                             const float* snr_db, float* gains, float* y, int32_t* trunc_len,
-                            float* energy_kept_frac) {
+                            float* energy_kept_frac, const RoomsCall* rooms = nullptr) {
     const DevBatch& B = p->B;
     if (p->part) {
         // partitioned: lengths (no cut-off) and gains here, the filtering on the plan over the
@@ -854,6 +889,16 @@ cudaError_t enqueue_forward(rsim_plan_t p, cudaStream_t st, const float* x, cons
         }
         return cudaGetLastError();
     }
+    // the cut-off: the scan of the caller's RIRs, or the RIRs made from room geometry
+    // with the cut-off fused, whose kept taps then stand in for the caller's RIRs
+    auto cut = [&](cudaStream_t s) {
+        if (rooms)
+            launch_image_cut(B, rooms->geom, rooms->order, rooms->fs, rooms->c0, p->factor, p->none, p->nh_max,
+                             p->rir_kept, rooms->rir_out, energy_kept_frac, p->grid_cut, s);
+        else
+            launch_truncate(B, rir, p->factor, p->none, energy_kept_frac, p->grid_trunc, s);
+    };
+    if (rooms) rir = p->rir_kept;
     // per-(i, j) gains fold into the RIR spectra; the kernels then see unit source gains
     const float* rir_gain = p->gain_mode == 2 ? gains : nullptr;
     const float* src_gains = p->gain_mode == 2 ? p->ones : gains;
@@ -876,11 +921,11 @@ cudaError_t enqueue_forward(rsim_plan_t p, cudaStream_t st, const float* x, cons
         cudaStreamWaitEvent(p->aux, p->ev_fork, 0);
         launch_power(B, x, p->grid_pow, p->aux);
         cudaEventRecord(p->ev_aux, p->aux);
-        launch_truncate(B, rir, p->factor, p->none, energy_kept_frac, p->grid_trunc, st);
+        cut(st);
         cudaStreamWaitEvent(st, p->ev_aux, 0);
     } else {
         stage_mark(p, 0, false, st);
-        launch_truncate(B, rir, p->factor, p->none, energy_kept_frac, p->grid_trunc, st);
+        cut(st);
         stage_mark(p, 0, true, st);
         if (p->gain_mode == 0) {
             stage_mark(p, 1, false, st);
@@ -1014,6 +1059,36 @@ extern "C" rsim_status rsim_filter_mix(rsim_plan_t p, void* stream, const float*
     return RSIM_OK;
 }
 
+extern "C" rsim_status rsim_filter_mix_rooms(rsim_plan_t p, void* stream, const float* x,
+                                             const rsim_image_geom* geom, int32_t order, float fs, float c0,
+                                             const float* snr_db, float* gains, float* y, int32_t* trunc_len,
+                                             float* energy_kept_frac, float* rir_out) {
+    g_err.clear();
+    if (!p) return fail(RSIM_E_INVALID, "NULL plan");
+    if (!p->rir_kept) return fail(RSIM_E_STATE, "rsim_filter_mix_rooms needs a plan made with rooms = 1");
+    if (!x || !geom || !gains || !y) return fail(RSIM_E_INVALID, "x, geom, gains and y are required");
+    if (order < 0 || order > 32 || !(fs > 0.f) || !(c0 > 0.f) || !std::isfinite(fs) || !std::isfinite(c0))
+        return fail(RSIM_E_INVALID, "need order in [0, 32] and finite fs, c0 > 0");
+    if (p->gain_mode == 0 && !snr_db) return fail(RSIM_E_INVALID, "snr_db is required when gain_mode is 0");
+    DeviceGuard guard(p->device);
+    // the graphs hold order, fs and c0 by value: other values need new captures
+    if (order != p->rooms_order || fs != p->rooms_fs || c0 != p->rooms_c0) {
+        p->grooms.destroy();
+        p->rooms_order = order;
+        p->rooms_fs = fs;
+        p->rooms_c0 = c0;
+    }
+    const RoomsCall rc{geom, order, fs, c0, rir_out};
+    const void* const key[8] = {x, geom, snr_db, gains, y, trunc_len, energy_kept_frac, rir_out};
+    cudaError_t e = run_graph(p, p->grooms, key, (cudaStream_t)stream, [&](cudaStream_t s) {
+        return enqueue_forward(p, s, x, nullptr, snr_db, gains, y, trunc_len, energy_kept_frac, &rc);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "forward launch (rooms)");
+    p->fwd_done = true;
+    p->fwd_rir = p->rir_kept;
+    return RSIM_OK;
+}
+
 extern "C" rsim_status rsim_filter_mix_backward(rsim_plan_t p, void* stream, const float* grad_y,
                                                 const float* x, const float* gains, float* grad_x,
                                                 float* grad_rir, float* grad_gains) {
@@ -1048,6 +1123,9 @@ rsim_status check_device_error(rsim_plan_t p) {
             return fail(RSIM_E_INVALID, "a noise source has zero power but an SNR to meet");
         if (err & kErrWaitTimeout)
             return fail(RSIM_E_DEVICE, "a kernel's bounded wait for a bulk copy ran out; results are invalid");
+        if (err & kErrBadGeometry)
+            return fail(RSIM_E_INVALID, "a room geometry is invalid or puts an image at the microphone "
+                                        "(that RIR was taken as all zeros)");
         return fail(RSIM_E_DEVICE, "device error " + std::to_string(err));
     }
     return RSIM_OK;

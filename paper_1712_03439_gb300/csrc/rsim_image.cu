@@ -49,6 +49,57 @@ __device__ __forceinline__ bool geom_valid(const rsim_image_geom& g) {
     return ok;
 }
 
+// Per axis and virtual-room index a - K: (squared offset to the microphone, r^|a - K|),
+// built by the block's first 3 (2K + 1) threads (the caller synchronises).
+__device__ __forceinline__ void image_tables(const rsim_image_geom& g, int K, float2 (*tab)[kImgMaxSide]) {
+    const int t = threadIdx.x;
+    const int S = 2 * K + 1;
+    if (t < 3 * S) {
+        const int k = t / S, ai = t - k * S;
+        // axis k picked by selects (a runtime index into g would go through local memory)
+        const float len = k == 0 ? g.room[0] : k == 1 ? g.room[1] : g.room[2];
+        const float s = k == 0 ? g.src[0] : k == 1 ? g.src[1] : g.src[2];
+        const float m = k == 0 ? g.mic[0] : k == 1 ? g.mic[1] : g.mic[2];
+        const float e = image_offset(ai - K, len, s, m);
+        // r^|a| by repeated squaring
+        float p = 1.f, b = g.refl;
+        for (int q = abs(ai - K); q; q >>= 1) {
+            if (q & 1) p *= b;
+            b *= b;
+        }
+        tab[k][ai] = make_float2(__fmul_rn(e, e), p);
+    }
+}
+
+// Lands every image whose delay falls in [w0, w0 + wl) at win[delay - w0 + lead]
+// (shared memory, zeroed by the caller) with shared-memory atomics; threads take
+// (a, b) pairs of virtual rooms and walk the rooms c.  Returns true in a thread
+// that met an image at distance zero (the caller combines them).
+__device__ __forceinline__ bool land_images(const float2 (*tab)[kImgMaxSide], int K, float rate, int64_t w0,
+                                            int wl, int lead, float* win) {
+    const int S = 2 * K + 1;
+    const int P = S * S;
+    const float w0_f = (float)w0;
+    bool at_mic = false;
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        const int ai = p / S, bi = p - ai * S;
+        const float2 ta = tab[0][ai], tb = tab[1][bi];
+        const float sab = __fadd_rn(ta.x, tb.x);   // (x^2 + y^2) + z^2, in that order
+        const float rab = ta.y * tb.y;
+#pragma unroll 4
+        for (int ci = 0; ci < S; ++ci) {
+            const float2 tc = tab[2][ci];
+            const float d2 = __fadd_rn(sab, tc.x);
+            at_mic |= !(d2 > 0.f);   // an image at the microphone
+            // delay = ceil(d * rate); ceil and w0 are integers, exact below 2^24, so the
+            // offset is exact wherever it can land in the window (wl <= nh - w0)
+            const int i = __float2int_rz(ceilf(__fmul_rn(__fsqrt_rn(d2), rate)) - w0_f);
+            if ((unsigned)i < (unsigned)wl) atomicAdd(&win[i + lead], rab * tc.y * rsqrtf(d2));
+        }
+    }
+    return at_mic;
+}
+
 // grid: R * nw blocks; block b takes RIR b / nw and windows b % nw, b % nw + nw, ...
 __global__ void __launch_bounds__(kImgThreads, 4)
 k_image_rirs(int32_t R, int32_t nw, const rsim_image_geom* __restrict__ geom,
@@ -72,51 +123,18 @@ k_image_rirs(int32_t R, int32_t nw, const rsim_image_geom* __restrict__ geom,
     if ((int64_t)w_first * kImgWindow >= nh) return;
     const rsim_image_geom g = geom[r];
     const bool valid = geom_valid(g);
-    const int S = 2 * K + 1;
-    if (t < 3 * S) {
-        const int k = t / S, ai = t - k * S;
-        // axis k picked by selects (a runtime index into g would go through local memory)
-        const float len = k == 0 ? g.room[0] : k == 1 ? g.room[1] : g.room[2];
-        const float s = k == 0 ? g.src[0] : k == 1 ? g.src[1] : g.src[2];
-        const float m = k == 0 ? g.mic[0] : k == 1 ? g.mic[1] : g.mic[2];
-        const float e = image_offset(ai - K, len, s, m);
-        // r^|a| by repeated squaring
-        float p = 1.f, b = g.refl;
-        for (int q = abs(ai - K); q; q >>= 1) {
-            if (q & 1) p *= b;
-            b *= b;
-        }
-        tab[k][ai] = make_float2(__fmul_rn(e, e), p);
-    }
+    image_tables(g, K, tab);
     // samples per metre, one rounding (the same value on every side of the comparison)
     const float rate = __fdiv_rn(fs, c0);
-    const int P = S * S;
     float4* win4 = reinterpret_cast<float4*>(win);
     for (int64_t w = w_first; w * kImgWindow < nh; w += nw) {
         const int64_t w0 = w * kImgWindow;
         const int wl = (int)(nh - w0 < kImgWindow ? nh - w0 : (int64_t)kImgWindow);
-        const float w0_f = (float)w0;
         float* dst = rir + o0 + w0;
         const int lead = (int)((reinterpret_cast<uintptr_t>(dst) >> 2) & 3);
         for (int q = t; q < (kImgWindow + 4) / 4; q += kImgThreads) win4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();   // also publishes the tables on the first pass
-        bool at_mic = false;
-        for (int p = t; p < P; p += kImgThreads) {
-            const int ai = p / S, bi = p - ai * S;
-            const float2 ta = tab[0][ai], tb = tab[1][bi];
-            const float sab = __fadd_rn(ta.x, tb.x);   // (x^2 + y^2) + z^2, in that order
-            const float rab = ta.y * tb.y;
-#pragma unroll 4
-            for (int ci = 0; ci < S; ++ci) {
-                const float2 tc = tab[2][ci];
-                const float d2 = __fadd_rn(sab, tc.x);
-                at_mic |= !(d2 > 0.f);   // an image at the microphone (the block is zeroed below)
-                // delay = ceil(d * rate); ceil and w0 are integers, exact below 2^24, so the
-                // offset is exact wherever it can land in the window (wl <= nh - w0)
-                const int i = __float2int_rz(ceilf(__fmul_rn(__fsqrt_rn(d2), rate)) - w0_f);
-                if ((unsigned)i < (unsigned)wl) atomicAdd(&win[i + lead], rab * tc.y * rsqrtf(d2));
-            }
-        }
+        const bool at_mic = land_images(tab, K, rate, w0, wl, lead, win);
         const bool bad = __syncthreads_or(at_mic) || !valid;
         if (bad && t == 0 && w == w_first && status) atomicOr(status, kImgBadGeom);
         // 16-byte chunks of win [4q, 4q + 4) hold taps 4q - lead .. 4q + 3 - lead; the first
@@ -139,7 +157,69 @@ k_image_rirs(int32_t R, int32_t nw, const rsim_image_geom* __restrict__ geom,
     }
 }
 
+// K1 fused with Eq. 1, for plans fed by room geometry (rsim_filter_mix_rooms): one
+// block per RIR (grid-stride) lands every image of the RIR in shared memory (the
+// whole RIR, Nh_max floats of dynamic shared memory), takes the cut-off there with
+// the same decision as the standalone scan (cut_rir), and writes only the kept taps
+// [0, L) to `kept` (plan scratch in the packed RIR layout, read by the spectrum
+// kernel); with `full` non-NULL every tap also goes there.  An invalid geometry or
+// an image at the microphone gives an all-zero RIR (L = 1) and latches
+// kErrBadGeometry.
+constexpr int kCutThreads = 320;
+
+__global__ void __launch_bounds__(kCutThreads)
+k_image_cut(DevBatch B, const rsim_image_geom* __restrict__ geom, int32_t K, float fs, float c0, double factor,
+            int none, float* __restrict__ kept, float* __restrict__ full, float* __restrict__ ekf) {
+    extern __shared__ __align__(16) float hwin[];
+    __shared__ float2 tab[3][kImgMaxSide];
+    __shared__ CutScratch cs;
+    const int t = threadIdx.x;
+    const float rate = __fdiv_rn(fs, c0);
+    for (int r = blockIdx.x; r < B.R; r += gridDim.x) {
+        const int nh = B.rir_len[r];
+        const int64_t o0 = B.roff[r];
+        const rsim_image_geom g = geom[r];
+        const bool valid = geom_valid(g);
+        __syncthreads();                         // the previous RIR's readers are done
+        image_tables(g, K, tab);
+        for (int i = t; i < nh; i += kCutThreads) hwin[i] = 0.f;
+        __syncthreads();
+        const bool at_mic = land_images(tab, K, rate, 0, nh, 0, hwin);
+        if (__syncthreads_or(at_mic) || !valid) {
+            for (int i = t; i < nh; i += kCutThreads) hwin[i] = 0.f;
+            if (t == 0) atomicOr(B.err, kErrBadGeometry);
+            __syncthreads();
+        }
+        float frac = 1.f;
+        const int L = cut_rir([&](int i) { return hwin[i]; }, nh, factor, none, ekf != nullptr, &frac, cs);
+        for (int i = t; i < L; i += kCutThreads) kept[o0 + i] = hwin[i];
+        if (full)
+            for (int i = t; i < nh; i += kCutThreads) full[o0 + i] = hwin[i];
+        if (t == 0) {
+            B.L[r] = L;
+            if (ekf) ekf[r] = frac;
+        }
+    }
+}
+
 }  // namespace
+
+int image_cut_smem(int nh_max) { return (int)sizeof(float) * std::max(nh_max, 1); }
+
+int image_cut_grid(int nh_max, int R, int sms) {
+    const int smem = image_cut_smem(nh_max);
+    cudaFuncSetAttribute(k_image_cut, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_image_cut, kCutThreads, smem);
+    return std::max(1, std::min(R, std::max(occ, 1) * std::max(sms, 1)));
+}
+
+void launch_image_cut(const DevBatch& B, const rsim_image_geom* geom, int K, float fs, float c0, double factor,
+                      int none, int nh_max, float* kept, float* full, float* ekf, int grid, cudaStream_t st) {
+    k_image_cut<<<grid, kCutThreads, image_cut_smem(nh_max), st>>>(B, geom, K, fs, c0, factor, none, kept, full,
+                                                                   ekf);
+}
+
 }  // namespace rsim
 
 using namespace rsim;

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "rsim.h"
+
 namespace rsim {
 
 // Supported overlap-add FFT sizes N = 2^m, m in [kMinLog, kMaxLog]; the
@@ -19,6 +21,7 @@ enum : int32_t {
     kErrNoFftSize = 1,     // a truncated RIR longer than 3N/4+1 for every allowed N
     kErrZeroPower = 2,     // a noise source with zero power but an SNR to meet
     kErrWaitTimeout = 4,   // a kernel gave up waiting for a bulk copy (bounded wait)
+    kErrBadGeometry = 8,   // a room geometry is invalid or puts an image at the microphone
 };
 
 // list kinds inside the work queues
@@ -123,10 +126,10 @@ __device__ __forceinline__ bool chunk_empty(const DevBatch& B, int b, int k) {
 // costs kCostMic, a source step (forward transform, RIR-gradient update, spectral
 // products, inverse and dx stores) kCostSrc; a stream also pays kCostFlush per
 // RIR-gradient inverse at its end and kCostPiece once.
-constexpr int kCostMic = 235;
-constexpr int kCostSrc = 607;
-constexpr int kCostFlush = 318;
-constexpr int kCostPiece = 183;
+constexpr int kCostMic = 243;
+constexpr int kCostSrc = 562;
+constexpr int kCostFlush = 272;
+constexpr int kCostPiece = 48;
 
 // Sources per backward stream of each FFT size: the TMEM-accumulator kernels
 // (N <= 8192) keep the RIR-gradient spectra of that many sources times two
@@ -144,6 +147,106 @@ __host__ __device__ inline void segment_blocks(int64_t s, int64_t seg_len, int64
     if (hi > nblk) hi = nblk;
     *b0 = lo;
     *b1 = hi;
+}
+
+// ---------------------------------------------------------------------------
+// block reductions (device code of the kernel translation units)
+// ---------------------------------------------------------------------------
+template <typename Tv, typename Op>
+__device__ __forceinline__ Tv warp_reduce(Tv v, Op op) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// result valid in every thread; scratch holds >= 32 elements
+template <typename Tv, typename Op>
+__device__ __forceinline__ Tv block_reduce(Tv v, Op op, Tv* scratch, Tv ident) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    v = warp_reduce(v, op);
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    Tv r = (threadIdx.x < nw) ? scratch[threadIdx.x] : ident;
+    if (wid == 0) r = warp_reduce(r, op);
+    if (threadIdx.x == 0) scratch[0] = r;
+    __syncthreads();
+    r = scratch[0];
+    __syncthreads();
+    return r;
+}
+
+struct OpMaxF { __device__ float operator()(float a, float b) const { return fmaxf(a, b); } };
+struct OpMaxI { __device__ int operator()(int a, int b) const { return a > b ? a : b; } };
+struct OpAddD { __device__ double operator()(double a, double b) const { return a + b; } };
+
+// ---------------------------------------------------------------------------
+// Eq. 7-9: the cut-off of one RIR by one CTA
+// ---------------------------------------------------------------------------
+// p_th = max h^2 * factor, factor = 10^(-eta/10) computed once on the host in
+// FP64.  n_c is the last index whose power is not below p_th (Eq. 8 with its
+// strict "<"), and L = min(n_c + 2, Nh) (Eq. 9 keeps one sample beyond n_c).
+// The comparison h^2 < p_th is decided exactly in FP64 (h^2 of an FP32 value
+// is exact in double and p_th is one rounded product); FP32 bounds settle all
+// taps that are clearly above or below so FP64 is used only near p_th.  An
+// all-zero RIR keeps L = 1; none != 0 keeps every tap.  tap(i) returns tap i
+// (any memory); every thread of the CTA calls it, the result is valid in all
+// threads, and with want_frac *frac (valid in thread 0) is the kept share of the
+// RIR's energy.  The standalone scan and the fused image-method path both use
+// this one function, so they decide alike for equal taps.
+struct CutScratch {
+    float f[32];
+    int i[32];
+    double d[32];
+};
+
+template <typename Tap>
+__device__ __forceinline__ int cut_rir(Tap tap, int n, double factor, int none, bool want_frac, float* frac,
+                                       CutScratch& cs) {
+    const int t = threadIdx.x, nt = blockDim.x;
+    float amax = 0.f;
+#pragma unroll 4
+    for (int i = t; i < n; i += nt) amax = fmaxf(amax, fabsf(tap(i)));
+    amax = block_reduce(amax, OpMaxF(), cs.f, 0.f);
+    const double P = __dmul_rn((double)amax, (double)amax);   // exact
+    int L;
+    if (P == 0.0) {
+        L = 1;
+    } else if (none) {
+        L = n;
+    } else {
+        const double pth = __dmul_rn(P, factor);
+        const double st = sqrt(pth);
+        const float tlo = (float)(st * (1.0 - 1e-6));   // |h| < tlo  =>  h^2 < p_th
+        const float thi = (float)(st * (1.0 + 1e-6));   // |h| >= thi =>  h^2 >= p_th
+        int last = -1;
+#pragma unroll 4
+        for (int i = t; i < n; i += nt) {
+            const float a = fabsf(tap(i));
+            bool keep;
+            if (a < tlo) keep = false;
+            else if (a >= thi) keep = true;
+            else keep = !(__dmul_rn((double)a, (double)a) < pth);
+            if (keep) last = i;
+        }
+        last = block_reduce(last, OpMaxI(), cs.i, -1);
+        L = last + 2;
+        if (L > n) L = n;
+    }
+    if (want_frac) {
+        float et = 0.f, ek = 0.f;
+        for (int i = t; i < n; i += nt) {
+            const float v = tap(i);
+            const float p = v * v;
+            et += p;
+            if (i < L) ek += p;
+        }
+        const double dt = block_reduce((double)et, OpAddD(), cs.d, 0.0);
+        const double dk = block_reduce((double)ek, OpAddD(), cs.d, 0.0);
+        *frac = dt > 0.0 ? (float)(dk / dt) : 1.f;
+    }
+    return L;
 }
 
 // ---- launchers (defined in the kernel translation units) -------------------
@@ -166,6 +269,11 @@ void launch_forward(int logN, const DevBatch& B, const Queues& Q, const float* x
                     const float2* Hc, float* y, float* tails, Twiddles tw, int grid,
                     cudaStream_t st);
 void launch_fixup(const DevBatch& B, float* y, const float* tails, cudaStream_t st);
+// Eq. 1 and the cut-off fused (plans fed by room geometry); see rsim_image.cu
+constexpr int kCutMaxTaps = 40960;     // longest RIR the fused path holds in shared memory
+int image_cut_grid(int nh_max, int R, int sms);
+void launch_image_cut(const DevBatch& B, const rsim_image_geom* geom, int K, float fs, float c0, double factor,
+                      int none, int nh_max, float* kept, float* full, float* ekf, int grid, cudaStream_t st);
 void launch_backward(int logN, const DevBatch& B, const Queues& Q, const float* g, const float* x,
                      const float* gains, const float2* Hc, float* dx, float* dhp, float* dap,
                      Twiddles tw, int grid, cudaStream_t st);

@@ -8,100 +8,23 @@
 namespace rsim {
 
 // ---------------------------------------------------------------------------
-// block reductions
+// K1: tail cut-off of every RIR (Eq. 7-9), one CTA per RIR (cut_rir)
 // ---------------------------------------------------------------------------
-template <typename Tv, typename Op>
-__device__ __forceinline__ Tv warp_reduce(Tv v, Op op) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-// result valid in every thread; scratch holds >= 32 elements
-template <typename Tv, typename Op>
-__device__ __forceinline__ Tv block_reduce(Tv v, Op op, Tv* scratch, Tv ident) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nw = (blockDim.x + 31) >> 5;
-    v = warp_reduce(v, op);
-    __syncthreads();
-    if (lane == 0) scratch[wid] = v;
-    __syncthreads();
-    Tv r = (threadIdx.x < nw) ? scratch[threadIdx.x] : ident;
-    if (wid == 0) r = warp_reduce(r, op);
-    if (threadIdx.x == 0) scratch[0] = r;
-    __syncthreads();
-    r = scratch[0];
-    __syncthreads();
-    return r;
-}
-
-struct OpMaxF { __device__ float operator()(float a, float b) const { return fmaxf(a, b); } };
-struct OpMaxI { __device__ int operator()(int a, int b) const { return a > b ? a : b; } };
-struct OpAddD { __device__ double operator()(double a, double b) const { return a + b; } };
-
-// ---------------------------------------------------------------------------
-// K1: tail cut-off of every RIR (Eq. 7-9)
-// ---------------------------------------------------------------------------
-// p_th = max h^2 * factor, factor = 10^(-eta/10) computed once on the host in
-// FP64.  n_c is the last index whose power is not below p_th (Eq. 8 with its
-// strict "<"), and L = min(n_c + 2, Nh) (Eq. 9 keeps one sample beyond n_c).
-// The comparison h^2 < p_th is decided exactly in FP64 (h^2 of an FP32 value
-// is exact in double and p_th is one rounded product); FP32 bounds settle all
-// taps that are clearly above or below so FP64 is used only near p_th.
-// An all-zero RIR keeps L = 1.
 constexpr int kTruncThreads = 256;
 
 __global__ void __launch_bounds__(kTruncThreads)
 k_truncate(DevBatch B, const float* __restrict__ rir, double factor, int none,
            float* __restrict__ ekf) {
-    __shared__ float sf[32];
-    __shared__ int si[32];
-    __shared__ double sd[32];
-    const int t = threadIdx.x;
+    __shared__ CutScratch cs;
     for (int r = blockIdx.x; r < B.R; r += gridDim.x) {
         const float* h = rir + B.roff[r];
         const int n = B.rir_len[r];
-        float amax = 0.f;
-#pragma unroll 4
-        for (int i = t; i < n; i += kTruncThreads) amax = fmaxf(amax, fabsf(__ldg(h + i)));
-        amax = block_reduce(amax, OpMaxF(), sf, 0.f);
-        const double P = __dmul_rn((double)amax, (double)amax);   // exact
-        int L;
-        if (P == 0.0) {
-            L = 1;
-        } else if (none) {
-            L = n;
-        } else {
-            const double pth = __dmul_rn(P, factor);
-            const double st = sqrt(pth);
-            const float tlo = (float)(st * (1.0 - 1e-6));   // |h| < tlo  =>  h^2 < p_th
-            const float thi = (float)(st * (1.0 + 1e-6));   // |h| >= thi =>  h^2 >= p_th
-            int last = -1;
-#pragma unroll 4
-            for (int i = t; i < n; i += kTruncThreads) {
-                const float a = fabsf(__ldg(h + i));
-                bool keep;
-                if (a < tlo) keep = false;
-                else if (a >= thi) keep = true;
-                else keep = !(__dmul_rn((double)a, (double)a) < pth);
-                if (keep) last = i;
-            }
-            last = block_reduce(last, OpMaxI(), si, -1);
-            L = last + 2;
-            if (L > n) L = n;
+        float frac;
+        const int L = cut_rir([&](int i) { return __ldg(h + i); }, n, factor, none, ekf != nullptr, &frac, cs);
+        if (threadIdx.x == 0) {
+            B.L[r] = L;
+            if (ekf) ekf[r] = frac;
         }
-        if (ekf) {
-            float et = 0.f, ek = 0.f;
-            for (int i = t; i < n; i += kTruncThreads) {
-                const float p = h[i] * h[i];
-                et += p;
-                if (i < L) ek += p;
-            }
-            double dt = block_reduce((double)et, OpAddD(), sd, 0.0);
-            double dk = block_reduce((double)ek, OpAddD(), sd, 0.0);
-            if (t == 0) ekf[r] = dt > 0.0 ? (float)(dk / dt) : 1.f;
-        }
-        if (t == 0) B.L[r] = L;
         __syncthreads();
     }
 }

@@ -42,7 +42,7 @@ def _desc(**kw):
                       fft_sizes_mask=kw.pop("mask", 0), gain_mode=kw.pop("gm", 0),
                       segment_len=kw.pop("seg", 0), bwd_segment_len=kw.pop("bseg", 0),
                       fft_cost=None, disable_graphs=0, output_mode=kw.pop("om", 0),
-                      snr_ref_mic=kw.pop("ref", 0))
+                      snr_ref_mic=kw.pop("ref", 0), rooms=kw.pop("rooms", 0))
     return d, (ns, nx, rl)
 
 
@@ -64,6 +64,10 @@ def _desc(**kw):
     (dict(bseg=-5), 1),
     (dict(om=2), 1),
     (dict(om=-1), 1),
+    (dict(rooms=2), 1),
+    (dict(rooms=1, gm=3), 2),
+    (dict(rooms=1, rl=[40961]), 2),
+    (dict(rooms=1, eta=float("inf"), rl=[20000]), 2),
 ])
 def test_plan_rejects_bad_descriptions_on_the_host(lib, kw, status):
     d, keep = _desc(**kw)
@@ -77,6 +81,8 @@ def test_plan_rejects_bad_descriptions_on_the_host(lib, kw, status):
 def test_null_plan_calls_fail_cleanly(lib):
     assert lib.rsim_filter_mix(None, None, None, None, None, None, None, None, None) == 1
     assert lib.rsim_filter_mix_backward(None, None, None, None, None, None, None, None) == 1
+    assert lib.rsim_filter_mix_rooms(None, None, None, None, 8, 16000.0, 343.0, None, None, None, None, None,
+                                     None) == 1
     assert lib.rsim_plan_scratch_bytes(None) == 0
     lib.rsim_plan_destroy(None)
 
