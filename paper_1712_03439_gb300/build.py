@@ -57,16 +57,17 @@ def build_probe(force: bool = False) -> str:
     return PROBE_LIB
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+def build(force: bool = False, verbose: bool = False, extra_flags=(), lib_path: str = LIB_PATH,
+          obj_dir: str = OBJ_DIR) -> str:
     """Compiles every CUDA translation unit for sm_103a and links librsim.so."""
     deps = _deps()
-    if not force and not _stale(LIB_PATH, deps):
-        return LIB_PATH
-    os.makedirs(OBJ_DIR, exist_ok=True)
+    if not force and not _stale(lib_path, deps):
+        return lib_path
+    os.makedirs(obj_dir, exist_ok=True)
     nvcc = _nvcc()
 
     def compile_one(src):
-        obj = os.path.join(OBJ_DIR, os.path.splitext(src)[0] + ".o")
+        obj = os.path.join(obj_dir, os.path.splitext(src)[0] + ".o")
         cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
@@ -81,12 +82,24 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         for _, log in results:
             print(log)
     objs = [o for o, _ in results]
-    tmp = LIB_PATH + ".tmp"
+    tmp = lib_path + ".tmp"
     r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib_path)
+    return lib_path
+
+
+CHECKED_LIB_PATH = os.path.join(PKG, "librsim_checked.so")
+
+
+def build_checked(force: bool = False) -> str:
+    """The bounds-checked variant (-DRSIM_BOUNDS_CHECK): every kernel store is
+    checked against its buffer's extent, an element outside latches an error
+    that rsim_plan_sync_status reports, and the store is skipped.  Built beside
+    librsim.so as librsim_checked.so, for debugging and tests."""
+    return build(force=force, extra_flags=("-DRSIM_BOUNDS_CHECK",), lib_path=CHECKED_LIB_PATH,
+                 obj_dir=os.path.join(PKG, "_build_checked"))
 
 
 if __name__ == "__main__":

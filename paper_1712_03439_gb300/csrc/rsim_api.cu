@@ -602,6 +602,13 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
         grid_fwd[b] = (int)std::max<int64_t>(1, std::min<int64_t>(nseg, (int64_t)sms * occupancy_forward(m)));
         grid_bwd[b] = (int)std::max<int64_t>(1, (int64_t)sms * occupancy_backward(m));
     }
+    {
+        // test hook, off by default: every persistent launch with one CTA (the work
+        // lists and the backward partition then go to a single CTA)
+        const char* o = std::getenv("RSIM_TEST_ONE_CTA");
+        if (o && o[0] == '1')
+            for (int b = 0; b < kNumBuckets; ++b) grid_spec[b] = grid_fwd[b] = grid_bwd[b] = 1;
+    }
     // backward partition: at most one piece per stream plus one per CTA boundary; the
     // RIR-gradient partials of the pieces fit all RIR taps plus one utterance's per CTA
     int pmax = 1;
@@ -744,7 +751,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     DevBatch& B = p->B;
     B.U = U; B.J = J; B.S = (int32_t)S; B.R = (int32_t)R; B.IMAX = imax;
     B.NSEG = (int32_t)nseg; B.MMAX = MMAX; B.mask = mask; B.seg_len = seg_len;
-    B.PMAX = pmax; B.NPIECE = (int32_t)npiece;
+    B.PMAX = pmax; B.NPIECE = (int32_t)npiece; B.NDHP = dhp_total;
     B.sord = (int32_t*)p_sord; B.spre = (int64_t*)p_spre; B.nstream = (int32_t*)p_nstream;
     B.cta_sp = (int32_t*)p_ctasp; B.cta_b = (int32_t*)p_ctab; B.cta_p = (int32_t*)p_ctap;
     B.piece_dh = (int64_t*)p_piecedh; B.s_first = (int32_t*)p_sfirst; B.s_last = (int32_t*)p_slast;
@@ -1123,6 +1130,8 @@ rsim_status check_device_error(rsim_plan_t p) {
             return fail(RSIM_E_INVALID, "a noise source has zero power but an SNR to meet");
         if (err & kErrWaitTimeout)
             return fail(RSIM_E_DEVICE, "a kernel's bounded wait for a bulk copy ran out; results are invalid");
+        if (err & kErrBounds)
+            return fail(RSIM_E_DEVICE, "bounds-checked build: a kernel store fell outside its buffer (skipped)");
         if (err & kErrBadGeometry)
             return fail(RSIM_E_INVALID, "a room geometry is invalid or puts an image at the microphone "
                                         "(that RIR was taken as all zeros)");

@@ -280,13 +280,16 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
                         const int n = 2 * (t + q * T);
                         const float d0 = a * v[q].x, d1 = a * v[q].y;
                         if (pairs && n + 1 < ilim) {
-                            *reinterpret_cast<float2*>(dst + n) = make_float2(d0, d1);
+                            if (RSIM_STORE_OK(B, dst + n + 1, dx, RSIM_X_BYTES(B)))
+                                *reinterpret_cast<float2*>(dst + n) = make_float2(d0, d1);
                         } else if constexpr (MG) {
-                            if (n < ilim) dst[n] = (j0 == 0) ? d0 : dst[n] + d0;
-                            if (n + 1 < ilim) dst[n + 1] = (j0 == 0) ? d1 : dst[n + 1] + d1;
+                            if (n < ilim && RSIM_STORE_OK(B, dst + n, dx, RSIM_X_BYTES(B)))
+                                dst[n] = (j0 == 0) ? d0 : dst[n] + d0;
+                            if (n + 1 < ilim && RSIM_STORE_OK(B, dst + n + 1, dx, RSIM_X_BYTES(B)))
+                                dst[n + 1] = (j0 == 0) ? d1 : dst[n + 1] + d1;
                         } else {
-                            if (n < ilim) dst[n] = d0;
-                            if (n + 1 < ilim) dst[n + 1] = d1;
+                            if (n < ilim && RSIM_STORE_OK(B, dst + n, dx, RSIM_X_BYTES(B))) dst[n] = d0;
+                            if (n + 1 < ilim && RSIM_STORE_OK(B, dst + n + 1, dx, RSIM_X_BYTES(B))) dst[n + 1] = d1;
                         }
                     }
                 }
@@ -305,8 +308,8 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
 #pragma unroll
                 for (int q = 0; q < E; ++q) {
                     const int n = 2 * (t + q * T);
-                    if (n < Lr) out[n] = v[q].x;
-                    if (n + 1 < Lr) out[n + 1] = v[q].y;
+                    if (n < Lr && RSIM_STORE_OK(B, out + n, dhp, B.NDHP * 4)) out[n] = v[q].x;
+                    if (n + 1 < Lr && RSIM_STORE_OK(B, out + n + 1, dhp, B.NDHP * 4)) out[n + 1] = v[q].y;
                 }
             }
         }
@@ -603,13 +606,16 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
                             const int n = 2 * (t + q * T);
                             const float d0 = a * v[q].x, d1 = a * v[q].y;
                             if (pairs && n + 1 < ilim) {
-                                *reinterpret_cast<float2*>(dst + n) = make_float2(d0, d1);
+                                if (RSIM_STORE_OK(B, dst + n + 1, dx, RSIM_X_BYTES(B)))
+                                    *reinterpret_cast<float2*>(dst + n) = make_float2(d0, d1);
                             } else if constexpr (MG) {
-                                if (n < ilim) dst[n] = (j0 == 0) ? d0 : dst[n] + d0;
-                                if (n + 1 < ilim) dst[n + 1] = (j0 == 0) ? d1 : dst[n + 1] + d1;
+                                if (n < ilim && RSIM_STORE_OK(B, dst + n, dx, RSIM_X_BYTES(B)))
+                                    dst[n] = (j0 == 0) ? d0 : dst[n] + d0;
+                                if (n + 1 < ilim && RSIM_STORE_OK(B, dst + n + 1, dx, RSIM_X_BYTES(B)))
+                                    dst[n + 1] = (j0 == 0) ? d1 : dst[n + 1] + d1;
                             } else {
-                                if (n < ilim) dst[n] = d0;
-                                if (n + 1 < ilim) dst[n + 1] = d1;
+                                if (n < ilim && RSIM_STORE_OK(B, dst + n, dx, RSIM_X_BYTES(B))) dst[n] = d0;
+                                if (n + 1 < ilim && RSIM_STORE_OK(B, dst + n + 1, dx, RSIM_X_BYTES(B))) dst[n + 1] = d1;
                             }
                         }
                     }
@@ -629,8 +635,8 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
 #pragma unroll
                 for (int q = 0; q < E; ++q) {
                     const int n = 2 * (t + q * T);
-                    if (n < Lr) out[n] = v[q].x;
-                    if (n + 1 < Lr) out[n + 1] = v[q].y;
+                    if (n < Lr && RSIM_STORE_OK(B, out + n, dhp, B.NDHP * 4)) out[n] = v[q].x;
+                    if (n + 1 < Lr && RSIM_STORE_OK(B, out + n + 1, dhp, B.NDHP * 4)) out[n + 1] = v[q].y;
                 }
             }
         }
@@ -676,8 +682,10 @@ k_finalize(DevBatch B, const float* __restrict__ gains, const float* __restrict_
         const int Lr = B.L[r], nh = B.rir_len[r];
         float* out = grad_rir + B.roff[r];
         if (B.logN[u] == 0) {
-            for (int k = threadIdx.x; k < nh; k += blockDim.x) out[k] = 0.f;
-            if (rir_gain && grad_gains && threadIdx.x == 0) grad_gains[r] = 0.f;
+            for (int k = threadIdx.x; k < nh; k += blockDim.x)
+                if (RSIM_STORE_OK(B, out + k, grad_rir, RSIM_RIR_BYTES(B))) out[k] = 0.f;
+            if (rir_gain && grad_gains && threadIdx.x == 0 && RSIM_STORE_OK(B, grad_gains + r, grad_gains, 4 * B.R))
+                grad_gains[r] = 0.f;
             continue;
         }
         const float inv_n = 1.f / (float)(1 << B.logN[u]);
@@ -707,7 +715,7 @@ k_finalize(DevBatch B, const float* __restrict__ gains, const float* __restrict_
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const int k = threadIdx.x + (c0 + c) * kFinThreads;
-                if (k < nh) out[k] = k < Lr ? scale * acc[c] : 0.f;
+                if (k < nh && RSIM_STORE_OK(B, out + k, grad_rir, RSIM_RIR_BYTES(B))) out[k] = k < Lr ? scale * acc[c] : 0.f;
                 if (h && k < Lr) dot = fmaf(h[k], acc[c], dot);
             }
         }
@@ -719,7 +727,7 @@ k_finalize(DevBatch B, const float* __restrict__ gains, const float* __restrict_
             if (threadIdx.x == 0) {
                 float s = 0.f;
                 for (int w = 0; w < kFinThreads / 32; ++w) s += red[w];
-                grad_gains[r] = s * inv_n;
+                if (RSIM_STORE_OK(B, grad_gains + r, grad_gains, 4 * B.R)) grad_gains[r] = s * inv_n;
             }
             __syncthreads();
         }
@@ -734,7 +742,7 @@ k_finalize(DevBatch B, const float* __restrict__ gains, const float* __restrict_
                 const int st = B.src0[u] + i0;
                 for (int q = B.s_first[st]; q <= B.s_last[st]; ++q) acc += dap[(int64_t)q * kMaxSources + i - i0];
             }
-            grad_gains[sidx] = acc;
+            if (RSIM_STORE_OK(B, grad_gains + sidx, grad_gains, 4 * B.S)) grad_gains[sidx] = acc;
         }
     }
 }

@@ -44,7 +44,8 @@ k_spectrum(DevBatch B, Queues Q, int bucket, const float* __restrict__ rir, cons
 #pragma unroll
         for (int s = 0; s < E / 2; ++s) {
             const float2 a = cscale(P[2 * s], sc), c = cscale(P[2 * s + 1], sc);
-            H[t + s * T] = make_float4(a.x, a.y, c.x, c.y);
+            if (RSIM_STORE_OK(B, &H[t + s * T], Hc, (int64_t)B.R * B.MMAX * sizeof(float2)))
+                H[t + s * T] = make_float4(a.x, a.y, c.x, c.y);
         }
     }
 }
@@ -149,9 +150,17 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
                 if constexpr (L::kTailSmem) return tl_smem + jj * 2 * M;
                 else return tails + ((int64_t)g * J + j0 + jj) * 2 * B.MMAX;
             };
+            const int64_t tails_bytes = (int64_t)B.NSEG * J * 2 * B.MMAX * sizeof(float);
+            // a store into a carried tail: shared memory, or checked against `tails`
+            auto tail_ok = [&](const float* q) {
+                if constexpr (L::kTailSmem) return true;
+                else return RSIM_STORE_OK(B, q, tails, tails_bytes);
+            };
+            const int64_t y_bytes = RSIM_Y_BYTES(B);
             __syncthreads();                     // stages and tails are free
             for (int jj = 0; jj < jn; ++jj)
-                for (int n = t; n < tail_len; n += T) tl(jj)[n] = 0.f;
+                for (int n = t; n < tail_len; n += T)
+                    if (tail_ok(tl(jj) + n)) tl(jj)[n] = 0.f;
             stage_x(b0, 0);
             for (int64_t b = b0; b < b1; ++b) {
                 const int64_t pos = b * hop;
@@ -220,18 +229,19 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
                         if (n < tail_len) v[q].x += tlj[n];
                         if (n + 1 < tail_len) v[q].y += tlj[n + 1];
                         if (pairs && n + 1 < ilim) {
-                            *reinterpret_cast<float2*>(yj + n) = v[q];
+                            if (RSIM_STORE_OK(B, yj + n + 1, y, y_bytes)) *reinterpret_cast<float2*>(yj + n) = v[q];
                         } else {
-                            if (n < ilim) yj[n] = v[q].x;
-                            if (n + 1 < ilim) yj[n + 1] = v[q].y;
+                            if (n < ilim && RSIM_STORE_OK(B, yj + n, y, y_bytes)) yj[n] = v[q].x;
+                            if (n + 1 < ilim && RSIM_STORE_OK(B, yj + n + 1, y, y_bytes)) yj[n + 1] = v[q].y;
                         }
                     }
                     __syncthreads();
 #pragma unroll
                     for (int q = 0; q < E; ++q) {
                         const int n = 2 * (t + q * T);
-                        if (n >= hop && n - hop < tail_len) tlj[n - hop] = v[q].x;
-                        if (n + 1 >= hop && n + 1 - hop < tail_len) tlj[n + 1 - hop] = v[q].y;
+                        if (n >= hop && n - hop < tail_len && tail_ok(tlj + n - hop)) tlj[n - hop] = v[q].x;
+                        if (n + 1 >= hop && n + 1 - hop < tail_len && tail_ok(tlj + n + 1 - hop))
+                            tlj[n + 1 - hop] = v[q].y;
                     }
                 }
             }
@@ -239,7 +249,8 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
                 __syncthreads();
                 for (int jj = 0; jj < jn; ++jj) {
                     float* dst = tails + ((int64_t)g * J + j0 + jj) * 2 * B.MMAX;
-                    for (int n = t; n < tail_len; n += T) dst[n] = tl(jj)[n];
+                    for (int n = t; n < tail_len; n += T)
+                        if (RSIM_STORE_OK(B, dst + n, tails, tails_bytes)) dst[n] = tl(jj)[n];
                 }
             }
             if (ny > nx && b1 == B.nblk[u]) {
@@ -250,7 +261,7 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
                 for (int jj = 0; jj < jn; ++jj) {
                     float* yj = y + B.yoff[u] + (int64_t)(j0 + jj) * ny;
                     for (int64_t n = min(end, ye) + t; n < ny; n += T)
-                        yj[n] = (n < ye) ? tl(jj)[n - end] : 0.f;
+                        if (RSIM_STORE_OK(B, yj + n, y, y_bytes)) yj[n] = (n < ye) ? tl(jj)[n - end] : 0.f;
                 }
             }
         }
@@ -295,7 +306,7 @@ k_fixup(DevBatch B, float* __restrict__ y, const float* __restrict__ tails) {
 #pragma unroll
                 for (int k = 0; k < kU; ++k) {
                     const int n = n0 + k * blockDim.x;
-                    if (n < lim) yj[n] = a[k] + c[k];
+                    if (n < lim && RSIM_STORE_OK(B, yj + n, y, RSIM_Y_BYTES(B))) yj[n] = a[k] + c[k];
                 }
             }
         }

@@ -22,6 +22,7 @@ enum : int32_t {
     kErrZeroPower = 2,     // a noise source with zero power but an SNR to meet
     kErrWaitTimeout = 4,   // a kernel gave up waiting for a bulk copy (bounded wait)
     kErrBadGeometry = 8,   // a room geometry is invalid or puts an image at the microphone
+    kErrBounds = 16,       // bounds-checked build: a store fell outside its buffer (skipped)
 };
 
 // list kinds inside the work queues
@@ -76,6 +77,7 @@ struct DevBatch {
     int32_t* err;            // [1] latched error bits
     int32_t test_withhold;   // test hook: the bulk copies are not issued, so the kernels'
                              // bounded waits run out (set from RSIM_TEST_WITHHOLD_BULK_COPY)
+    int64_t NDHP;            // floats of the RIR-gradient partials (bounds-checked build)
 };
 
 struct Queues {
@@ -248,6 +250,30 @@ __device__ __forceinline__ int cut_rir(Tap tap, int n, double factor, int none, 
     }
     return L;
 }
+
+// ---------------------------------------------------------------------------
+// Bounds-checked build (-DRSIM_BOUNDS_CHECK): every store of the kernels' outputs
+// and scratch checks its element against the extent of its buffer; an element
+// outside latches kErrBounds in the plan's error word (rsim_plan_sync_status
+// reports it) and the store is skipped rather than trapping.  The release build
+// compiles the checks away.
+// ---------------------------------------------------------------------------
+#ifdef RSIM_BOUNDS_CHECK
+__device__ __forceinline__ bool store_ok(const DevBatch& B, const void* p, const void* base, int64_t bytes) {
+    const char* c = static_cast<const char*>(p);
+    const char* b = static_cast<const char*>(base);
+    const bool ok = b != nullptr && c >= b && c < b + bytes;
+    if (!ok) atomicOr(B.err, kErrBounds);
+    return ok;
+}
+#define RSIM_STORE_OK(B, p, base, bytes) ::rsim::store_ok((B), (p), (base), (int64_t)(bytes))
+#else
+#define RSIM_STORE_OK(B, p, base, bytes) true
+#endif
+// extents (bytes) of the buffers the kernels write
+#define RSIM_Y_BYTES(B) (4 * (B).yoff[(B).U])
+#define RSIM_X_BYTES(B) (4 * (B).xoff[(B).S])
+#define RSIM_RIR_BYTES(B) (4 * (B).roff[(B).R])
 
 // ---- launchers (defined in the kernel translation units) -------------------
 void launch_truncate(const DevBatch& B, const float* rir, double factor, int none,
