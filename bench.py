@@ -617,7 +617,7 @@ def run_stream(args):
     build.build()
     b = synth.config_stream(n_utts=args.stream_utts)
     st = Streamer(budget_bytes=int(args.budget_gb * (1 << 30)), eta_db=ETA_DB, backward=True,
-                  keep_outputs=False)
+                  keep_outputs=False, class_plan=not args.stream_plan_per_batch)
     st.run(b.subset(range(min(64, b.num_utts))))          # warm-up (context, code, allocator)
     clock = ClockSampler(0)
     t0 = time.perf_counter()
@@ -653,9 +653,13 @@ def run_stream(args):
             "latency_ms": {"p50_wall": res.latency_ms(50), "p99_wall": res.latency_ms(99),
                            "p50_device": res.latency_ms(50, "device_ms"),
                            "p99_device": res.latency_ms(99, "device_ms"),
-                           "p50_plan": res.latency_ms(50, "plan_ms")},
-            "note": "wall: batch formed on the host to results on the host (pinned staging, plan "
-                    "creation, copies both ways, kernels); device: first copy to last copy on the stream",
+                           "p50_plan": res.latency_ms(50, "plan_ms"),
+                           "p50_staging": res.latency_ms(50, "staging_ms")},
+            "batches_on_the_shape_class_plan": int(sum(r.reshaped for r in res.records)),
+            "note": "wall: batch inputs in pinned host memory to results on the host (re-planning the "
+                    "shape-class plan, copies both ways, kernels); staging: the host copy of a batch's "
+                    "inputs into pinned memory, done on a host thread while the previous batch runs; "
+                    "device: first copy to last copy on the stream",
             "roofline": {"t_roof_s": t_roof, "device_s": dev_s, "frac": t_roof / dev_s,
                          "bound": "alu" if flops / (p_fp32 * 1e12) >= nbytes / (hbm * 1e9) else "hbm",
                          "peak_fp32_tflops": p_fp32, "peak_hbm_gbs": hbm, "peak_source": peak_kind},
@@ -1052,6 +1056,8 @@ def main():
                          "front end")
     ap.add_argument("--stream-utts", type=int, default=4096)
     ap.add_argument("--budget-gb", type=float, default=2.0)
+    ap.add_argument("--stream-plan-per-batch", action="store_true",
+                    help="stream: a plan made for every batch instead of one re-planned shape-class plan")
     ap.add_argument("--long-utts", type=int, default=32)
     ap.add_argument("--long-steps", type=int, default=5)
     args = ap.parse_args()

@@ -196,6 +196,22 @@ rsim_status rsim_plan_stage_times(rsim_plan_t plan, double *ms, int32_t *calls);
 /* Bytes of device scratch owned by the plan. */
 int64_t rsim_plan_scratch_bytes(rsim_plan_t plan);
 
+/* Upper-bound plans: re-plans `plan` for another batch shape in place, without
+ * new device memory, streams or events (SURVEY's shape classes; Sec. 1 draws
+ * fresh rooms and utterances every epoch, so a training loop meets a new shape
+ * on every batch).  A plan made for the largest batch of a class serves every
+ * batch whose scratch pieces each fit the class's: fewer or shorter
+ * utterances, fewer sources, shorter RIRs.  Only num_utts, num_sources,
+ * num_samples, rir_len and fft_cost may differ from the plan's description;
+ * plans with partitioned convolution or gain_mode 3 are not reshaped.  Waits
+ * for the device to finish the plan's earlier work, then uploads the new
+ * tables; the captured graphs of the old shape are dropped and a backward
+ * needs a forward of the new shape first.
+ * Errors: RSIM_E_INVALID (a fixed field differs), RSIM_E_UNSUPPORTED (the
+ * batch does not fit the class, or needs partitioned convolution: make a new
+ * plan); on error the plan keeps its old shape. */
+rsim_status rsim_plan_reshape(rsim_plan_t plan, const rsim_plan_desc *desc);
+
 /* Releases the plan and its device memory (NULL is ignored).  The caller must
  * make sure no queued work still uses it. */
 void rsim_plan_destroy(rsim_plan_t plan);

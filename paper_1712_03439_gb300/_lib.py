@@ -20,7 +20,7 @@ EXPORTED = ["rsim_plan", "rsim_filter_mix", "rsim_filter_mix_backward", "rsim_pl
             "rsim_plan_query", "rsim_plan_set_timing", "rsim_plan_stage_times",
             "rsim_plan_scratch_bytes", "rsim_plan_destroy", "rsim_source_gains_noalloc",
             "rsim_image_rirs", "rsim_plan_log_mel", "rsim_plan_log_mel_rows", "rsim_filter_mix_rooms",
-            "rsim_last_error"]
+            "rsim_plan_reshape", "rsim_last_error"]
 STAGES = ["truncate", "power", "plan", "spectrum", "forward", "fixup", "backward", "finalize"]
 
 
@@ -79,6 +79,8 @@ def load(path: str | None = None):
     P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
     lib.rsim_plan.restype = ctypes.c_int
     lib.rsim_plan.argtypes = [ctypes.POINTER(PlanDesc), ctypes.c_int, ctypes.POINTER(P)]
+    lib.rsim_plan_reshape.restype = ctypes.c_int
+    lib.rsim_plan_reshape.argtypes = [P, ctypes.POINTER(PlanDesc)]
     lib.rsim_filter_mix.restype = ctypes.c_int
     lib.rsim_filter_mix.argtypes = [P, P, P, P, P, P, P, P, P]
     lib.rsim_filter_mix_rooms.restype = ctypes.c_int

@@ -71,18 +71,23 @@ class Plan:
             self._cost = np.zeros(32, np.float32)
             for n, c in dict(fft_cost).items():
                 self._cost[int(round(math.log2(n)))] = c
-        desc = _lib.PlanDesc(
-            num_utts=self.num_sources.shape[0], num_mics=self.num_mics,
-            num_sources=self.num_sources.ctypes.data, num_samples=self.num_samples.ctypes.data,
-            rir_len=self.rir_len.ctypes.data, eta_db=self.eta_db, fft_sizes_mask=mask,
-            gain_mode=self.gain_mode, segment_len=int(segment_len),
-            bwd_segment_len=int(bwd_segment_len),
-            fft_cost=None if self._cost is None else self._cost.ctypes.data,
-            disable_graphs=0 if graphs else 1, output_mode=self.output_mode, snr_ref_mic=int(snr_ref_mic),
-            rooms=1 if rooms else 0)
+        self._fixed = dict(num_mics=self.num_mics, eta_db=self.eta_db, fft_sizes_mask=mask,
+                           gain_mode=self.gain_mode, segment_len=int(segment_len),
+                           bwd_segment_len=int(bwd_segment_len), disable_graphs=0 if graphs else 1,
+                           output_mode=self.output_mode, snr_ref_mic=int(snr_ref_mic), rooms=1 if rooms else 0)
         h = ctypes.c_void_p()
-        _lib.check(self._lib, self._lib.rsim_plan(ctypes.byref(desc), self.device, ctypes.byref(h)))
+        _lib.check(self._lib, self._lib.rsim_plan(ctypes.byref(self._desc()), self.device, ctypes.byref(h)))
         self._handle = h
+        self._set_shape()
+        # FFT sizes the plan may pick (one forward/backward launch each)
+        self.num_fft_sizes = bin(mask).count("1") if mask else 4
+
+    def _desc(self):
+        return _lib.PlanDesc(num_utts=self.num_sources.shape[0], num_sources=self.num_sources.ctypes.data,
+                             num_samples=self.num_samples.ctypes.data, rir_len=self.rir_len.ctypes.data,
+                             fft_cost=None if self._cost is None else self._cost.ctypes.data, **self._fixed)
+
+    def _set_shape(self):
         self.U = int(self.num_sources.shape[0])
         self.S = int(self.num_sources.sum())
         self.R = int(self.rir_len.shape[0])
@@ -97,11 +102,27 @@ class Plan:
         self.rir_size = int(np.sum(self.rir_len.astype(np.int64)))
         # gains: one per source, or one per (source, microphone) in gain mode 2
         self.G = self.R if self.gain_mode == 2 else self.S
-        # FFT sizes the plan may pick (one forward/backward launch each)
-        self.num_fft_sizes = bin(mask).count("1") if mask else 4
         # forwards run on this plan so far: the backward uses the state (cut-off
         # lengths, RIR spectra, the RIR buffer) of the most recent one
         self.forward_count = 0
+
+    def reshape(self, num_sources, num_samples, rir_len):
+        """rsim_plan_reshape: this plan, re-planned in place for another batch shape
+        that fits its shape class (raises RsimError with status 2 when it does not;
+        the plan then keeps its shape)."""
+        old = (self.num_sources, self.num_samples, self.rir_len)
+        self.num_sources = np.ascontiguousarray(num_sources, dtype=np.int32)
+        self.num_samples = np.ascontiguousarray(num_samples, dtype=np.int64)
+        self.rir_len = np.ascontiguousarray(rir_len, dtype=np.int32)
+        try:
+            _lib.check(self._lib, self._lib.rsim_plan_reshape(self._handle, ctypes.byref(self._desc())))
+        except Exception:
+            self.num_sources, self.num_samples, self.rir_len = old
+            raise
+        self._set_shape()
+
+    def reshape_for(self, batch):
+        self.reshape(batch.num_sources, batch.num_samples, batch.rir_len)
 
     @classmethod
     def for_batch(cls, batch, **kw):

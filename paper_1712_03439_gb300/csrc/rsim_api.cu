@@ -148,6 +148,10 @@ struct rsim_plan_s {
     // the fused generation and cut-off, its graphs and the scalar arguments they hold
     float* rir_kept = nullptr;
     int nh_max = 1, grid_cut = 1;
+    // the allocation's pieces (bytes each, in carving order): a reshape fits the new
+    // shape's pieces into them at the same offsets
+    std::vector<size_t> piece_cap;
+    rsim_plan_desc desc_fixed{};     // the fields a reshape must keep (pointers cleared)
     GraphCache grooms;
     int32_t rooms_order = -1;
     float rooms_fs = 0.f, rooms_c0 = 0.f;
@@ -448,8 +452,11 @@ rsim_status make_partitioned(rsim_plan_t p, const rsim_plan_desc* d, int device,
 
 }  // namespace
 
-extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_t* out) {
-    g_err.clear();
+namespace {
+// Builds a plan for description d.  With `borrow` non-NULL the plan takes no new
+// device memory, streams or events: its pieces must fit borrow's (same carving
+// order, each no larger), which are used at the same offsets (a reshape).
+rsim_status plan_build(const rsim_plan_desc* d, int device, rsim_plan_t* out, rsim_plan_t borrow) {
     if (!d || !out) return fail(RSIM_E_INVALID, "rsim_plan: NULL argument");
     *out = nullptr;
     const int U = d->num_utts, J = d->num_mics;
@@ -578,6 +585,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     struct Piece { void** dst; size_t bytes; };
     std::vector<Piece> pieces;
     void* p_kept = nullptr;
+    void* p_lpre = nullptr;
     void *p_sord, *p_spre, *p_nstream, *p_ctasp, *p_ctab, *p_ctap, *p_piecedh, *p_sfirst, *p_slast;
     void *p_srcutt, *p_rirutt;
     void *p_nsrc, *p_nx, *p_ny, *p_src0, *p_rir0, *p_seg0, *p_segutt, *p_xoff, *p_yoff, *p_roff, *p_rlen,
@@ -610,7 +618,8 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
             for (int b = 0; b < kNumBuckets; ++b) grid_spec[b] = grid_fwd[b] = grid_bwd[b] = 1;
     }
     // backward partition: at most one piece per stream plus one per CTA boundary; the
-    // RIR-gradient partials of the pieces fit all RIR taps plus one utterance's per CTA
+    // RIR-gradient partials hold twice the batch's RIR taps (the planner packs the pieces
+    // by kept taps and cuts fewer chunks when they would not fit)
     int pmax = 1;
     int64_t ctas = 0;
     for (int b = 0; b < kNumBuckets; ++b) {
@@ -618,7 +627,8 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
         ctas += grid_bwd[b];
     }
     const int64_t npiece = S + ctas;
-    const int64_t dhp_total = roff[R] + ctas * utt_taps_max;
+    const int64_t dhp_total = 2 * roff[R] + 1024;
+    (void)utt_taps_max;
     pieces.push_back({&p_nsrc, sizeof(int32_t) * U});
     pieces.push_back({&p_nx, sizeof(int64_t) * U});
     pieces.push_back({&p_ny, sizeof(int64_t) * U});
@@ -633,6 +643,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     pieces.push_back({&p_ctab, sizeof(int32_t) * kNumBuckets * (pmax + 1)});
     pieces.push_back({&p_ctap, sizeof(int32_t) * kNumBuckets * (pmax + 1)});
     pieces.push_back({&p_piecedh, sizeof(int64_t) * npiece});
+    pieces.push_back({&p_lpre, sizeof(int64_t) * (R + 1)});
     pieces.push_back({&p_sfirst, sizeof(int32_t) * std::max<int64_t>(S, 1)});
     pieces.push_back({&p_slast, sizeof(int32_t) * std::max<int64_t>(S, 1)});
     pieces.push_back({&p_xoff, sizeof(int64_t) * (S + 1)});
@@ -685,22 +696,36 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
             pieces.push_back({&p_tw[k], sizeof(float2) * tws[k].size()});
         }
     }
-    size_t total = 0;
-    for (auto& pc : pieces) total = align_up(total, 256) + pc.bytes;
-    total = align_up(total, 256);
-    e = cudaMalloc(&p->dmem, total);
-    if (e != cudaSuccess) {
-        delete p;
-        cudaGetLastError();
-        return fail(RSIM_E_NOMEM, "cudaMalloc of " + std::to_string(total) + " bytes failed");
+    if (borrow) {
+        // a reshape: every piece must fit the shape class's
+        bool fits = pieces.size() == borrow->piece_cap.size();
+        for (size_t k = 0; fits && k < pieces.size(); ++k) fits = pieces[k].bytes <= borrow->piece_cap[k];
+        if (!fits) {
+            delete p;
+            return fail(RSIM_E_UNSUPPORTED, "the batch does not fit the plan's shape class (make a new plan)");
+        }
+        p->dmem = borrow->dmem;
+        p->dbytes = borrow->dbytes;
+        p->piece_cap = borrow->piece_cap;
+    } else {
+        size_t total = 0;
+        for (auto& pc : pieces) total = align_up(total, 256) + pc.bytes;
+        total = align_up(total, 256);
+        e = cudaMalloc(&p->dmem, total);
+        if (e != cudaSuccess) {
+            delete p;
+            cudaGetLastError();
+            return fail(RSIM_E_NOMEM, "cudaMalloc of " + std::to_string(total) + " bytes failed");
+        }
+        p->dbytes = total;
+        for (auto& pc : pieces) p->piece_cap.push_back(pc.bytes);
     }
-    p->dbytes = total;
     {
         size_t off = 0;
-        for (auto& pc : pieces) {
+        for (size_t k = 0; k < pieces.size(); ++k) {
             off = align_up(off, 256);
-            *pc.dst = (char*)p->dmem + off;
-            off += pc.bytes;
+            *pieces[k].dst = (char*)p->dmem + off;
+            off += p->piece_cap[k];
         }
     }
     // ---- uploads
@@ -755,6 +780,7 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     B.sord = (int32_t*)p_sord; B.spre = (int64_t*)p_spre; B.nstream = (int32_t*)p_nstream;
     B.cta_sp = (int32_t*)p_ctasp; B.cta_b = (int32_t*)p_ctab; B.cta_p = (int32_t*)p_ctap;
     B.piece_dh = (int64_t*)p_piecedh; B.s_first = (int32_t*)p_sfirst; B.s_last = (int32_t*)p_slast;
+    B.lpre = (int64_t*)p_lpre;
     // the device planner computes gains from the source powers in modes 0 and 3 (in mode 3
     // the powers are those of the reverberant sources)
     B.gain_mode = d->gain_mode == 3 ? 0 : d->gain_mode;
@@ -798,15 +824,33 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
     p->grid_trunc = (int)std::max<int64_t>(1, std::min<int64_t>(R, (int64_t)p->sms * 8));
     p->grid_pow = (int)std::max<int64_t>(1, std::min<int64_t>(S * CH, (int64_t)p->sms * 8));
     p->use_graphs = d->disable_graphs == 0;
-    e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_aux, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
-    for (int m = kMinLog; m <= kMaxLog && e == cudaSuccess; ++m) {
-        if (!((mask >> m) & 1)) continue;
-        const int b = m - kMinLog;
-        e = cudaStreamCreateWithFlags(&p->bs[b], cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join[b], cudaEventDisableTiming);
+    p->desc_fixed = *d;
+    p->desc_fixed.num_utts = 0;
+    p->desc_fixed.num_sources = nullptr;
+    p->desc_fixed.num_samples = nullptr;
+    p->desc_fixed.rir_len = nullptr;
+    p->desc_fixed.fft_cost = nullptr;
+    if (borrow) {
+        // the streams and events of the shape class (moved over by the reshape)
+        p->cap = borrow->cap;
+        p->aux = borrow->aux;
+        p->ev_aux = borrow->ev_aux;
+        p->ev_fork = borrow->ev_fork;
+        for (int b = 0; b < kNumBuckets; ++b) {
+            p->bs[b] = borrow->bs[b];
+            p->ev_join[b] = borrow->ev_join[b];
+        }
+    } else {
+        e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_aux, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+        for (int m = kMinLog; m <= kMaxLog && e == cudaSuccess; ++m) {
+            if (!((mask >> m) & 1)) continue;
+            const int b = m - kMinLog;
+            e = cudaStreamCreateWithFlags(&p->bs[b], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join[b], cudaEventDisableTiming);
+        }
     }
     if (e != cudaSuccess) {
         rsim_plan_destroy(p);
@@ -850,6 +894,67 @@ extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_
         }
     }
     *out = p;
+    return RSIM_OK;
+}
+
+}  // namespace
+
+extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_t* out) {
+    g_err.clear();
+    return plan_build(d, device, out, nullptr);
+}
+
+extern "C" rsim_status rsim_plan_reshape(rsim_plan_t p, const rsim_plan_desc* d) {
+    g_err.clear();
+    if (!p || !d) return fail(RSIM_E_INVALID, "rsim_plan_reshape: NULL argument");
+    if (p->part || p->rev)
+        return fail(RSIM_E_UNSUPPORTED, "plans with partitioned convolution or reverberant-SNR gains "
+                                        "cannot be reshaped");
+    const rsim_plan_desc& f = p->desc_fixed;
+    if (d->num_mics != f.num_mics || d->eta_db != f.eta_db || d->fft_sizes_mask != f.fft_sizes_mask ||
+        d->gain_mode != f.gain_mode || d->output_mode != f.output_mode || d->snr_ref_mic != f.snr_ref_mic ||
+        d->rooms != f.rooms || d->segment_len != f.segment_len || d->disable_graphs != f.disable_graphs)
+        return fail(RSIM_E_INVALID, "rsim_plan_reshape: only the batch shape may change (num_utts, "
+                                    "num_sources, num_samples, rir_len, fft_cost)");
+    DeviceGuard guard(p->device);
+    rsim_plan_t np = nullptr;
+    const rsim_status st = plan_build(d, p->device, &np, p);
+    if (st != RSIM_OK) return st;                // p is unchanged
+    if (np->part || np->rev) {
+        // the new shape needs a sub-plan: keep the old state
+        np->dmem = nullptr;
+        np->cap = np->aux = nullptr;
+        np->ev_aux = np->ev_fork = nullptr;
+        for (int b = 0; b < kNumBuckets; ++b) {
+            np->bs[b] = nullptr;
+            np->ev_join[b] = nullptr;
+        }
+        rsim_plan_destroy(np);
+        return fail(RSIM_E_UNSUPPORTED, "the new shape needs partitioned convolution: make a new plan");
+    }
+    // no work of the old shape may still read the tables being replaced
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        np->dmem = nullptr;
+        np->cap = np->aux = nullptr;
+        np->ev_aux = np->ev_fork = nullptr;
+        for (int b = 0; b < kNumBuckets; ++b) {
+            np->bs[b] = nullptr;
+            np->ev_join[b] = nullptr;
+        }
+        rsim_plan_destroy(np);
+        return cuda_fail(e, "cudaDeviceSynchronize (reshape)");
+    }
+    // the old state (graphs, timer) goes; the memory, streams and events stay with p
+    std::swap(*p, *np);
+    np->dmem = nullptr;
+    np->cap = np->aux = nullptr;
+    np->ev_aux = np->ev_fork = nullptr;
+    for (int b = 0; b < kNumBuckets; ++b) {
+        np->bs[b] = nullptr;
+        np->ev_join[b] = nullptr;
+    }
+    rsim_plan_destroy(np);
     return RSIM_OK;
 }
 

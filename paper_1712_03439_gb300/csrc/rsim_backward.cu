@@ -304,7 +304,7 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
                 else irfft_x<M, E, false>(v, Pw, ex, tw, t);
                 const int r = rb + i * J + j0 + jj;
                 const int Lr = B.L[r];
-                float* out = dhp + B.piece_dh[pc] + (B.roff[r] - B.roff[rb + i * J]);
+                float* out = dhp + B.piece_dh[pc] + (B.lpre[r] - B.lpre[rb + i * J]);
 #pragma unroll
                 for (int q = 0; q < E; ++q) {
                     const int n = 2 * (t + q * T);
@@ -631,7 +631,7 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
                 else irfft_x<M, E, false>(v, Wv, ex, tw, t);
                 const int r = rb + (i0 + i) * J + j0 + jj;
                 const int Lr = B.L[r];
-                float* out = dhp + B.piece_dh[pc] + (B.roff[r] - B.roff[rb + i0 * J]);
+                float* out = dhp + B.piece_dh[pc] + (B.lpre[r] - B.lpre[rb + i0 * J]);
 #pragma unroll
                 for (int q = 0; q < E; ++q) {
                     const int n = 2 * (t + q * T);
@@ -696,7 +696,7 @@ k_finalize(DevBatch B, const float* __restrict__ gains, const float* __restrict_
         const int sg = bwd_src_group(B.logN[u]);
         const int i0 = i / sg * sg;
         const int sidx = B.src0[u] + i0;
-        const int64_t local = B.roff[r] - B.roff[B.rir0[u] + i0 * B.J];
+        const int64_t local = B.lpre[r] - B.lpre[B.rir0[u] + i0 * B.J];
         const int p0 = B.s_first[sidx], p1 = B.s_last[sidx];
         float acc[4];
         // taps of this thread: k = threadIdx.x + c * blockDim.x

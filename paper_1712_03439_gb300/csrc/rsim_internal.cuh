@@ -63,6 +63,8 @@ struct DevBatch {
     int32_t* cta_b;          // [4][PMAX + 1] first block in that stream
     int32_t* cta_p;          // [4][PMAX + 1] first piece of each chunk
     int64_t* piece_dh;       // [NPIECE] offset of each piece's RIR-gradient partials
+    int64_t* lpre;           // [R + 1] kept taps of the RIRs before each one (the partials of a
+                             // piece hold its stream's kept taps, RIR after RIR)
     int32_t* s_first;        // [S] first piece of the stream that starts at source s
     int32_t* s_last;         // [S] last piece of that stream
     const float* tuning;     // [32] cost per real FFT of size 2^m (any unit)
@@ -77,7 +79,7 @@ struct DevBatch {
     int32_t* err;            // [1] latched error bits
     int32_t test_withhold;   // test hook: the bulk copies are not issued, so the kernels'
                              // bounded waits run out (set from RSIM_TEST_WITHHOLD_BULK_COPY)
-    int64_t NDHP;            // floats of the RIR-gradient partials (bounds-checked build)
+    int64_t NDHP;            // floats of the RIR-gradient partials (the planner fits the pieces in)
 };
 
 struct Queues {
@@ -182,6 +184,7 @@ __device__ __forceinline__ Tv block_reduce(Tv v, Op op, Tv* scratch, Tv ident) {
 struct OpMaxF { __device__ float operator()(float a, float b) const { return fmaxf(a, b); } };
 struct OpMaxI { __device__ int operator()(int a, int b) const { return a > b ? a : b; } };
 struct OpAddD { __device__ double operator()(double a, double b) const { return a + b; } };
+struct OpAddLL { __device__ long long operator()(long long a, long long b) const { return a + b; } };
 
 // ---------------------------------------------------------------------------
 // Eq. 7-9: the cut-off of one RIR by one CTA

@@ -116,6 +116,7 @@ constexpr float kConsolidateSlack = 0.02f;  // ...and moves if that adds at most
 __global__ void __launch_bounds__(kPlanThreads)
 k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict__ gains) {
     __shared__ int sm[33];
+    __shared__ long long pw_scratch[32];
     const int t = threadIdx.x;
     // ---- gains (alpha_0 = 1, alpha_i = sqrt(P_0 / P_i 10^(-SNR_i/10)))
     if (B.gain_mode == 0) {
@@ -325,60 +326,123 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
         *u_out = u;
         return block_cost(min(sg, B.n_src[u] - (sidx - B.src0[u])));
     };
-    // ---- step 2: where each CTA's chunk starts.  CTA k of size q starts at the first
-    // block whose cost position is at least ceil(k T / P) (a position inside a
-    // stream's flush is its end); the end sentinel k = P is (streams, 0)
-    const int PM = B.PMAX + 1;
-    for (int idx = t; idx < kNumBuckets * PM; idx += kPlanThreads) {
-        const int q = idx / PM, k = idx - q * PM;
-        const int P = B.bgrid[q];
-        if (k > P) continue;
-        const int n = B.nstream[q];
-        const int64_t* pre = B.spre + (int64_t)q * (B.S + 1);
-        int pos = n, blk = 0;
-        if (k < P && n > 0) {
-            const long long T = pre[n];
-            const long long x = (T * k + P - 1) / P;
-            int lo = 0, hi = n;                   // largest pos < n with pre[pos] <= x
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (pre[mid] <= x) lo = mid; else hi = mid;
-            }
-            int u;
-            const int c = stream_cost(q, lo, &u);
-            const long long bk = (x - pre[lo] + c - 1) / c;
-            if (bk >= B.nblk[u]) { pos = lo + 1; blk = 0; }
-            else { pos = lo; blk = (int)bk; }
+    // ---- step 2: the kept taps of the RIRs before each one (exclusive prefix over the
+    // batch, RIRs in contiguous chunks per thread): a piece's RIR-gradient partials
+    // hold its stream's kept taps
+    {
+        const int rper = (B.R + kPlanThreads - 1) / kPlanThreads;
+        const int r0t = min(B.R, t * rper), r1t = min(B.R, r0t + rper);
+        long long mine = 0;
+        for (int r = r0t; r < r1t; ++r) mine += B.L[r];
+        __shared__ long long lw[kPlanThreads / 32];
+        long long incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
         }
-        B.cta_sp[(int64_t)q * PM + k] = pos;
-        B.cta_b[(int64_t)q * PM + k] = blk;
+        if (lane == 31) lw[wid] = incl;
+        __syncthreads();
+        if (t == 0) {
+            long long acc = 0;
+            for (int w = 0; w < kPlanThreads / 32; ++w) {
+                const long long v = lw[w];
+                lw[w] = acc;
+                acc += v;
+            }
+            B.lpre[B.R] = acc;
+        }
+        __syncthreads();
+        long long run = incl - mine + lw[wid];
+        for (int r = r0t; r < r1t; ++r) {
+            B.lpre[r] = run;
+            run += B.L[r];
+        }
     }
     __syncthreads();
-    // ---- step 3: pieces.  Every thread takes a contiguous run of (size, CTA) entries,
-    // counts their chunks' pieces and the RIR-gradient partials they hold; a
-    // block-wide scan in (size, CTA) order numbers them; each thread then writes its
-    // pieces' partial offsets and marks the first and last piece of every stream
-    {
-        const int NE = kNumBuckets * PM;
-        const int pe = (NE + kPlanThreads - 1) / kPlanThreads;
-        const int e0 = min(NE, t * pe), e1 = min(NE, e0 + pe);
-        auto walk = [&](int q, int k, auto visit) {
-            const int pos0 = B.cta_sp[(int64_t)q * PM + k], blk0 = B.cta_b[(int64_t)q * PM + k];
-            const int pos1 = B.cta_sp[(int64_t)q * PM + k + 1], blk1 = B.cta_b[(int64_t)q * PM + k + 1];
-            for (int pos = pos0; pos <= pos1; ++pos) {
-                if (pos == pos1 && blk1 == 0) break;
-                const int sidx = B.sord[(int64_t)q * B.S + pos];
-                const int u = B.src_utt[sidx];
-                const int lo = pos == pos0 ? blk0 : 0;
-                const int hi = pos == pos1 ? blk1 : B.nblk[u];
-                if (lo >= hi) continue;
-                const int i0 = sidx - B.src0[u];
-                const int ig = min(bwd_src_group(kMinLog + q), B.n_src[u] - i0);
-                const int r0 = B.rir0[u] + i0 * B.J;
-                const long long taps = B.roff[r0 + ig * B.J] - B.roff[r0];
-                visit(sidx, lo == 0, hi == B.nblk[u], taps);
+    // ---- steps 3 and 4, repeated until the partials fit: where each CTA's chunk
+    // starts, then the pieces.  CTA k of size q (k < P, P the CTAs that take work)
+    // starts at the first block whose cost position is at least ceil(k T / P) (a
+    // position inside a stream's flush is its end); CTAs from P on, and the end
+    // sentinel, get (streams, 0).  Every CTA boundary inside a stream adds a piece
+    // holding a copy of the stream's partials; when all of them exceed the
+    // RIR-gradient partials, every size's P is halved and the cut is redone (at
+    // P = 1 the pieces are the streams, which always fit).
+    const int PM = B.PMAX + 1;
+    __shared__ int peff[kNumBuckets];
+    __shared__ long long dtot;
+    if (t < kNumBuckets) peff[t] = B.bgrid[t];
+    __syncthreads();
+    auto walk = [&](int q, int k, auto visit) {
+        const int pos0 = B.cta_sp[(int64_t)q * PM + k], blk0 = B.cta_b[(int64_t)q * PM + k];
+        const int pos1 = B.cta_sp[(int64_t)q * PM + k + 1], blk1 = B.cta_b[(int64_t)q * PM + k + 1];
+        for (int pos = pos0; pos <= pos1; ++pos) {
+            if (pos == pos1 && blk1 == 0) break;
+            const int sidx = B.sord[(int64_t)q * B.S + pos];
+            const int u = B.src_utt[sidx];
+            const int lo = pos == pos0 ? blk0 : 0;
+            const int hi = pos == pos1 ? blk1 : B.nblk[u];
+            if (lo >= hi) continue;
+            const int i0 = sidx - B.src0[u];
+            const int ig = min(bwd_src_group(kMinLog + q), B.n_src[u] - i0);
+            const int r0 = B.rir0[u] + i0 * B.J;
+            const long long taps = B.lpre[r0 + ig * B.J] - B.lpre[r0];
+            visit(sidx, lo == 0, hi == B.nblk[u], taps);
+        }
+    };
+    const int NE = kNumBuckets * PM;
+    const int pe = (NE + kPlanThreads - 1) / kPlanThreads;
+    const int e0 = min(NE, t * pe), e1 = min(NE, e0 + pe);
+    for (;;) {
+        // step 3: chunk starts
+        for (int idx = t; idx < kNumBuckets * PM; idx += kPlanThreads) {
+            const int q = idx / PM, k = idx - q * PM;
+            const int P = peff[q];
+            if (k > B.bgrid[q]) continue;
+            const int n = B.nstream[q];
+            const int64_t* pre = B.spre + (int64_t)q * (B.S + 1);
+            int pos = n, blk = 0;
+            if (k < P && n > 0) {
+                const long long T = pre[n];
+                const long long x = (T * k + P - 1) / P;
+                int lo = 0, hi = n;               // largest pos < n with pre[pos] <= x
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (pre[mid] <= x) lo = mid; else hi = mid;
+                }
+                int u;
+                const int c = stream_cost(q, lo, &u);
+                const long long bk = (x - pre[lo] + c - 1) / c;
+                if (bk >= B.nblk[u]) { pos = lo + 1; blk = 0; }
+                else { pos = lo; blk = (int)bk; }
             }
-        };
+            B.cta_sp[(int64_t)q * PM + k] = pos;
+            B.cta_b[(int64_t)q * PM + k] = blk;
+        }
+        __syncthreads();
+        // step 4a: the partials all pieces need
+        long long nd = 0;
+        for (int e = e0; e < e1; ++e) {
+            const int q = e / PM, k = e - q * PM;
+            if (k < B.bgrid[q]) walk(q, k, [&](int, bool, bool, long long taps) { nd += taps; });
+        }
+        nd = block_reduce(nd, OpAddLL(), reinterpret_cast<long long*>(pw_scratch), 0LL);
+        if (t == 0) dtot = nd;
+        __syncthreads();
+        bool done = dtot <= B.NDHP;
+        if (!done) {
+            bool all_one = true;
+            for (int q = 0; q < kNumBuckets; ++q) all_one = all_one && peff[q] <= 1;
+            done = all_one;                       // cannot happen: single chunks fit
+        }
+        if (done) break;
+        __syncthreads();
+        if (t < kNumBuckets) peff[t] = max(1, peff[t] / 2);
+        __syncthreads();
+    }
+    // step 4b: number the pieces in (size, CTA) order, write their partial offsets and
+    // mark the first and last piece of every stream
+    {
         int np = 0;
         long long nd = 0;
         for (int e = e0; e < e1; ++e) {
