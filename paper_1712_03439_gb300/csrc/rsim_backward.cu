@@ -87,7 +87,6 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
     constexpr int T = L::T;
     constexpr int NST = L::NST;
     constexpr bool kBulk = NST == 2;      // inputs staged by bulk copies completing on mbarriers
-    constexpr bool kRollSteps = L::NSM == 2;
     constexpr bool kPaired = PairedSplit<M, E>::ok;   // split in registers (paired layout)
     using Pl = FftPlan<M, E>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -233,8 +232,7 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
                 for (int e = 0; e < E; ++e) C[e] = make_float2(0.f, 0.f);
                 // step 0 transforms the source block, step 1 + jj the window of mic j0 + jj;
                 // one loop body (not unrolled) so the transform code is emitted once
-                // (unrolled at N = 16384, where the rolled loop computed wrong dh)
-#pragma unroll(kRollSteps ? 1 : kJG + 1)
+#pragma unroll 1
                 for (int sp = 0; sp <= kJG; ++sp) {
                     if (sp > jn) break;
                     next_input(v, b, sp < jn ? j0 + sp : -1);
@@ -251,7 +249,9 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
                         }
                     } else {
                         const float2* z = rfft_x<M, E, false>(v, ex, tw, t);
-                        if (sp == 0) split_forward<M, E>(X, z, wsplit, t);
+                        // X is kept while the next steps' transforms rewrite z (with one
+                        // exchange buffer z is the same address at every step)
+                        if (sp == 0) split_forward_now<M, E>(X, z, wsplit, t);
                         else if (sp == 1) mac(W[0], C, X, z, v, 0);
                         else mac(W[1], C, X, z, v, 1);
                     }

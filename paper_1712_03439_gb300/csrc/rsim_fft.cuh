@@ -306,23 +306,32 @@ __device__ __forceinline__ void load_real_strided(float2 (&v)[E], const float* _
 // padded) to the true half spectrum of the real 2M-point signal:
 // xa = X[k], xb = X[M-k]; for k = 0, xa = (X[0], X[M]) and xb = X[M/2].
 // wsplit[k] = exp(-2 pi i k / (2M)).
+// The mirror slot the split of bin k reads besides k itself: Z[M/2] for k = 0.
 template <int M>
-__device__ __forceinline__ void split_pair(const float2* __restrict__ sm, const float2* __restrict__ wsplit,
-                                           int k, float2& xa, float2& xb) {
+__host__ __device__ constexpr int split_mirror(int k) { return k == 0 ? M / 2 : M - k; }
+
+// The split arithmetic on zk = Z[k] and zq = Z[split_mirror(k)].
+template <int M>
+__device__ __forceinline__ void split_values(float2 zk, float2 zq, const float2* __restrict__ wsplit,
+                                             int k, float2& xa, float2& xb) {
     if (k == 0) {
-        const float2 z0 = sm[pad(0)];
-        const float2 zh = sm[pad(M / 2)];
-        xa = make_float2(z0.x + z0.y, z0.x - z0.y);
-        xb = conjf2(zh);
+        xa = make_float2(zk.x + zk.y, zk.x - zk.y);
+        xb = conjf2(zq);
     } else {
-        const float2 zk = sm[pad(k)];
-        const float2 zm = conjf2(sm[pad(M - k)]);
+        const float2 zm = conjf2(zq);
         const float2 E = cscale(cadd(zk, zm), 0.5f);
         const float2 O = cscale(mul_mi(csub(zk, zm)), 0.5f);   // (zk - zm) / (2i)
         const float2 wO = cmul(wsplit[k], O);
         xa = cadd(E, wO);
         xb = conjf2(csub(E, wO));
     }
+}
+
+template <int M>
+__device__ __forceinline__ void split_pair(const float2* __restrict__ sm, const float2* __restrict__ wsplit,
+                                           int k, float2& xa, float2& xb) {
+    if (k == 0) split_values<M>(sm[pad(0)], sm[pad(M / 2)], wsplit, 0, xa, xb);
+    else split_values<M>(sm[pad(k)], sm[pad(M - k)], wsplit, k, xa, xb);
 }
 
 // Split into pair layout registers P[2s] = X[k_s], P[2s+1] = X[M-k_s].
@@ -332,6 +341,27 @@ __device__ __forceinline__ void split_forward(float2 (&P)[E], const float2* __re
     constexpr int T = M / E;
 #pragma unroll
     for (int s = 0; s < E / 2; ++s) split_pair<M>(sm, wsplit, t + s * T, P[2 * s], P[2 * s + 1]);
+}
+
+// split_forward reading the buffer with volatile loads, for a spectrum kept in
+// registers while later transforms of a rolled loop rewrite the same buffer
+// (one exchange buffer: every transform's spectrum lands at the same address).
+// With plain loads the compiled code was seen to produce, where the kept values
+// are used, the split of what the buffer holds at that point -- as if the reads
+// of one address in different iterations were one value across the barriers
+// between them.  Volatile loads are each performed where they stand.
+template <int M, int E>
+__device__ __forceinline__ void split_forward_now(float2 (&P)[E], const float2* sm,
+                                                  const float2* __restrict__ wsplit, int t) {
+    constexpr int T = M / E;
+    const volatile float2* vs = sm;
+#pragma unroll
+    for (int s = 0; s < E / 2; ++s) {
+        const int k = t + s * T;
+        const int a = pad(k), b = pad(split_mirror<M>(k));
+        split_values<M>(make_float2(vs[a].x, vs[a].y), make_float2(vs[b].x, vs[b].y), wsplit, k,
+                        P[2 * s], P[2 * s + 1]);
+    }
 }
 
 // Inverse pre-processing of one pair: from ya = Y[k], yb = Y[M-k] (for k = 0:
