@@ -96,21 +96,35 @@ typedef struct {
                                       sum Nh floats); needs gain_mode 0, 1 or 2, every Nh at
                                       most 40960 and an RIR within the largest FFT size's
                                       reach (no partitioned convolution); 0: not */
+    int32_t long_rirs;             /* with a cut-off (finite eta_db): 1 gives every utterance
+                                      whose untruncated RIRs reach beyond one block of the
+                                      largest allowed FFT size a partitioned path (see
+                                      rsim_plan), taken on the device when its kept RIRs do
+                                      too; 0: a kept RIR beyond that reach is reported by
+                                      rsim_plan_sync_status (RSIM_E_UNSUPPORTED).  Without a
+                                      cut-off those utterances always take the partitioned
+                                      path, whatever this field says. */
 } rsim_plan_desc;
 
 /* Creates a plan for the given shapes on CUDA device `device`.  Validates the
  * description, allocates scratch and uploads twiddle tables.  On success *out
  * holds a plan to be released with rsim_plan_destroy.
  *
- * Without a cut-off (eta_db = +INFINITY), when some RIR is longer than one block
- * of the largest allowed FFT size N reaches (3N/4 + 1 taps), the plan filters by
- * uniformly partitioned convolution: source i delayed by p * N/2 samples is
+ * One block of the largest allowed FFT size N reaches RIRs of 3N/4 + 1 taps
+ * (hop >= N/4).  An utterance whose untruncated RIRs are longer (without a
+ * cut-off, or with one and long_rirs = 1) also gets a partitioned path
+ * (Sec. 2.2, Eq. 6, computed in pieces): source i delayed by p * N/2 samples is
  * filtered by taps [p N/2, (p+1) N/2) of its RIRs, for p < ceil(longest RIR of
- * the utterance / (N/2)), and the parts are summed (the same Eq. 2, computed in
- * pieces).  This needs output_mode 0, gain_mode 0 or 1, and at most 16 sources
- * times parts per utterance (RSIM_E_UNSUPPORTED otherwise); its scratch holds the
- * delayed copies of x.  With gain_mode 3 the plan also filters every source to
- * the reference microphone (a second, one-microphone plan inside this one). */
+ * the utterance / (N/2)), and the parts are summed -- the same Eq. 2.  The
+ * planner on the device sends an utterance there when its kept RIRs do not fit
+ * one block (always without a cut-off); the parts of a kept RIR are zero from
+ * its kept length L on, so the result is the mix with the cut RIRs.  Every
+ * output range and gain mode is served; at most 64 sources times parts per
+ * utterance (RSIM_E_UNSUPPORTED otherwise).  Its scratch holds the delayed
+ * copies of those utterances' sources over the output range.  With gain_mode 3
+ * the plan also filters every source to the reference microphone (a second,
+ * one-microphone plan inside this one).  A plan with a partitioned path cannot
+ * be reshaped. */
 rsim_status rsim_plan(const rsim_plan_desc *desc, int device, rsim_plan_t *out);
 
 /* Forward filter-and-mix (Eq. 7-9 truncation, gains, Eq. 2 by overlap-add).
@@ -174,9 +188,9 @@ rsim_status rsim_plan_sync_status(rsim_plan_t plan, void *stream);
 
 /* Copies the per-utterance plan chosen on the device by the last forward:
  * log2 of the FFT size, hop (N - L_max + 1), L_max and block count, each [U]
- * int32 host arrays (any may be NULL); for a partitioned plan, those of the
- * partitioned filtering (L_max is then the longest part).  Synchronises the
- * stream. */
+ * int32 host arrays (any may be NULL); for an utterance the planner sent to
+ * its partitioned path, the size, hop and blocks of that filtering (L_max
+ * stays the longest kept RIR).  Synchronises the stream. */
 rsim_status rsim_plan_query(rsim_plan_t plan, void *stream, int32_t *log2_n, int32_t *hop,
                             int32_t *l_max, int32_t *num_blocks);
 

@@ -47,6 +47,7 @@ class PlanDesc(ctypes.Structure):
         ("output_mode", ctypes.c_int32),
         ("snr_ref_mic", ctypes.c_int32),
         ("rooms", ctypes.c_int32),
+        ("long_rirs", ctypes.c_int32),
     ]
 
 

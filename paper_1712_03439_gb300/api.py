@@ -39,7 +39,7 @@ class Plan:
 
     def __init__(self, num_sources, num_samples, rir_len, num_mics, eta_db=20.0,
                  fft_sizes=None, gain_mode=0, segment_len=0, bwd_segment_len=0, fft_cost=None,
-                 device=None, graphs=True, output_mode=0, snr_ref_mic=0, rooms=False):
+                 device=None, graphs=True, output_mode=0, snr_ref_mic=0, rooms=False, long_rirs=False):
         self._lib = _lib.load()
         self._handle = None
         self.num_sources = np.ascontiguousarray(num_sources, dtype=np.int32)
@@ -74,7 +74,8 @@ class Plan:
         self._fixed = dict(num_mics=self.num_mics, eta_db=self.eta_db, fft_sizes_mask=mask,
                            gain_mode=self.gain_mode, segment_len=int(segment_len),
                            bwd_segment_len=int(bwd_segment_len), disable_graphs=0 if graphs else 1,
-                           output_mode=self.output_mode, snr_ref_mic=int(snr_ref_mic), rooms=1 if rooms else 0)
+                           output_mode=self.output_mode, snr_ref_mic=int(snr_ref_mic), rooms=1 if rooms else 0,
+                           long_rirs=1 if long_rirs else 0)
         h = ctypes.c_void_p()
         _lib.check(self._lib, self._lib.rsim_plan(ctypes.byref(self._desc()), self.device, ctypes.byref(h)))
         self._handle = h

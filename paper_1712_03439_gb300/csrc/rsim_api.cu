@@ -163,70 +163,60 @@ struct rsim_plan_s {
     const int64_t* rev_dst_off = nullptr;   // [S + 1] its offset in rev_rir
     float* rev_rir = nullptr;
     float* rev_y = nullptr;
-    // RIRs longer than one block reaches, without a cut-off: uniformly partitioned
-    // convolution.  A plan over virtual sources (i, p) -- source i delayed by p * part_len
-    // samples, filtered by taps [p * part_len, (p + 1) * part_len) of its RIRs -- does the
-    // work; segment copies and sums map x, the RIRs and the gains onto it and its
-    // gradients back.
+    // Utterances whose RIRs may reach beyond one block of the largest size: uniformly
+    // partitioned convolution.  A plan over those utterances, in which virtual source
+    // (i, q) is source i delayed by q * part_len samples and filtered by taps
+    // [q * part_len, (q + 1) * part_len) of its RIRs, does the work for the ones the
+    // planner sends there (defer); segment copies and sums map x, the RIRs, the gains and
+    // grad_y onto it and its outputs and gradients back, for those utterances only.
     rsim_plan_t part = nullptr;
-    struct Segs { const int64_t *src, *dst, *lead, *copy, *tail; int64_t n; };
-    struct Sums { const int64_t *out, *len, *t0, *src, *tlen; int64_t n; };
-    Segs seg_x{}, seg_h{}, seg_a{}, seg_dh{};
+    struct Segs {
+        const int64_t *src, *dst, *lead, *copy, *tail;
+        const int64_t* utt;               // utterance of the partitioned plan (skip unless deferred)
+        const int64_t *lim_r, *lim_off;   // copy at most L[lim_r] - lim_off values (NULL: all)
+        int64_t n;
+        int64_t out_n;                    // floats of the destination buffer
+    };
+    struct Sums { const int64_t *out, *len, *t0, *src, *tlen, *utt; int64_t n, out_n; };
+    Segs seg_x{}, seg_h{}, seg_a{}, seg_dh{}, seg_y{}, seg_gy{};
     Sums sum_dx{}, sum_da{};
-    float *part_x = nullptr, *part_rir = nullptr, *part_a = nullptr;
+    float *part_x = nullptr, *part_rir = nullptr, *part_a = nullptr, *part_y = nullptr;
     float *part_dx = nullptr, *part_dh = nullptr, *part_da = nullptr;
+    uint8_t* defer = nullptr;             // [utterances of the partitioned plan]
+    std::vector<int32_t> part_utt;        // its utterance k is utterance part_utt[k] here
     void* part_mem = nullptr;
     size_t part_bytes = 0;
 };
 
 namespace {
-// segment o: lead[o] zeros, then copy[o] values from in + src[o], then tail[o] zeros,
-// written from out + dst[o]
-__global__ void k_copy_segs(rsim_plan_s::Segs g, const float* __restrict__ in, float* __restrict__ out) {
+// segment o of a deferred utterance: lead[o] zeros, then copy[o] values from in + src[o]
+// (at most L[lim_r[o]] - lim_off[o] of them: a part of a cut RIR, or of its gradient; zeros
+// in place of the rest), then tail[o] zeros, written from out + dst[o]
+// (B: the outer plan, whose planner set the deferral flags and whose cut-off set L)
+__global__ void k_copy_segs(DevBatch B, rsim_plan_s::Segs g, const float* __restrict__ in, float* __restrict__ out) {
     for (int64_t o = blockIdx.x; o < g.n; o += gridDim.x) {
+        if (!B.defer[g.utt[o]]) continue;
         float* d = out + g.dst[o];
         const float* s = in + g.src[o];
-        const int64_t a = g.lead[o], c = g.copy[o], n = a + c + g.tail[o];
-        for (int64_t k = threadIdx.x; k < n; k += blockDim.x) d[k] = (k >= a && k < a + c) ? s[k - a] : 0.f;
+        const int64_t a = g.lead[o], n = a + g.copy[o] + g.tail[o];
+        int64_t c = g.copy[o];
+        if (g.lim_r) c = max((int64_t)0, min(c, (int64_t)B.L[g.lim_r[o]] - g.lim_off[o]));
+        for (int64_t k = threadIdx.x; k < n; k += blockDim.x)
+            if (RSIM_STORE_OK(B, d + k, out, 4 * g.out_n)) d[k] = (k >= a && k < a + c) ? s[k - a] : 0.f;
     }
 }
 
-// output o, length len[o]: out[out[o] + m] = sum over terms q in [t0[o], t0[o + 1]) of
-// in[src[q] + m] for m < tlen[q] (terms added in order)
-__global__ void k_sum_segs(rsim_plan_s::Sums g, const float* __restrict__ in, float* __restrict__ out) {
+// output o of a deferred utterance, length len[o]: out[out[o] + m] = sum over terms q in
+// [t0[o], t0[o + 1]) of in[src[q] + m] for m < tlen[q] (terms added in order)
+__global__ void k_sum_segs(DevBatch B, rsim_plan_s::Sums g, const float* __restrict__ in, float* __restrict__ out) {
     for (int64_t o = blockIdx.x; o < g.n; o += gridDim.x) {
+        if (!B.defer[g.utt[o]]) continue;
         const int64_t q0 = g.t0[o], q1 = g.t0[o + 1];
         for (int64_t m = threadIdx.x; m < g.len[o]; m += blockDim.x) {
             float acc = 0.f;
             for (int64_t q = q0; q < q1; ++q)
                 if (m < g.tlen[q]) acc += in[g.src[q] + m];
-            out[g.out[o] + m] = acc;
-        }
-    }
-}
-
-// per-source gains from the source powers (alpha_0 = 1, alpha_i = sqrt(P_0 / P_i
-// 10^(-SNR_i/10))) for the partitioned path, where the planner of the plan itself
-// is not run
-__global__ void k_part_gains(DevBatch B, const float* __restrict__ snr_db, float* __restrict__ gains) {
-    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < B.U; u += gridDim.x * blockDim.x) {
-        const int s0 = B.src0[u], I = B.n_src[u];
-        const double nx = (double)B.n_x[u];
-        const int nch = (int)((B.n_x[u] + kPowerChunk - 1) / kPowerChunk);
-        double P0 = 0.0;
-        for (int c = 0; c < nch; ++c) P0 += B.pow_part[(int64_t)s0 * B.CH + c];
-        P0 /= nx;
-        gains[s0] = 1.f;
-        for (int i = 1; i < I; ++i) {
-            double Pi = 0.0;
-            for (int c = 0; c < nch; ++c) Pi += B.pow_part[(int64_t)(s0 + i) * B.CH + c];
-            Pi /= nx;
-            if (!(Pi > 0.0)) {
-                atomicOr(B.err, kErrZeroPower);
-                gains[s0 + i] = 0.f;
-            } else {
-                gains[s0 + i] = (float)sqrt(P0 / Pi * pow(10.0, -(double)snr_db[s0 + i] / 10.0));
-            }
+            if (RSIM_STORE_OK(B, out + g.out[o] + m, out, 4 * g.out_n)) out[g.out[o] + m] = acc;
         }
     }
 }
@@ -315,52 +305,82 @@ extern "C" void rsim_plan_destroy(rsim_plan_t plan) {
 
 namespace {
 
-// Builds the partitioned plan: virtual source (i, p) of an utterance is source i delayed by
-// p * part_len samples, and its RIR to microphone j is taps [p * part_len, (p + 1) * part_len)
-// of h_ij (one zero tap if h_ij is shorter); part_len = N_max / 2, parts = ceil(max Nh / part_len)
-// per utterance.  Also builds the copy and sum tables that map the caller's buffers onto it.
+rsim_status plan_build(const rsim_plan_desc* d, int device, rsim_plan_t* out, rsim_plan_t borrow,
+                       int max_sources);
+
+// Builds the partitioned plan over the candidate utterances cand (those whose RIRs reach
+// beyond one block of N_max = 2^part_log): its utterance k is utterance cand[k]; virtual
+// source (i, q) is source i delayed by q * part_len samples, and its RIR to microphone j is
+// taps [q * part_len, (q + 1) * part_len) of h_ij (one zero tap where h_ij is shorter);
+// part_len = N_max / 2, ceil(longest RIR of the utterance / part_len) parts.  Every virtual
+// signal spans the utterance's output range (N_x, or the full N_x + max N_h - 1), so that
+// plan's "same" output is this plan's output, in either output mode.  Its RIRs carry no
+// cut-off of their own: the copy of a part holds the taps below the kept length L_ij of this
+// plan's cut-off and zeros from there on.  Also builds the copy and sum tables.
 rsim_status make_partitioned(rsim_plan_t p, const rsim_plan_desc* d, int device, const std::vector<int32_t>& src0,
                              const std::vector<int32_t>& rir0, const std::vector<int64_t>& xoff,
-                             const std::vector<int64_t>& roff, const std::vector<int32_t>& rlen, int part_log) {
-    const int U = d->num_utts, J = d->num_mics;
+                             const std::vector<int64_t>& roff, const std::vector<int32_t>& rlen,
+                             const std::vector<int64_t>& nyv, const std::vector<int64_t>& yoff, int part_log,
+                             const std::vector<int32_t>& cand) {
+    const int U = d->num_utts, J = d->num_mics, C = (int)cand.size();
+    const bool per_rir = d->gain_mode == 2;       // gains (and their gradients) per RIR
     const int64_t P = (int64_t)1 << (part_log - 1);
-    std::vector<int32_t> ns(U), parts(U), rl;
-    std::vector<int64_t> xs, hs_src, hs_dst, hs_copy, hs_tail, as_src;
-    std::vector<int64_t> xs_src, xs_lead, xs_copy, dh_src, dh_dst, dh_copy;
-    std::vector<int64_t> dx_out, dx_len, dx_t0{0}, dx_src, dx_tlen, da_out, da_len, da_t0{0}, da_src, da_tlen;
-    int64_t xv = 0, rv = 0, sv = 0;
-    for (int u = 0; u < U; ++u) {
+    std::vector<int32_t> ns(C), rl;
+    std::vector<int64_t> nxs(C);
+    // copy tables: x, RIR parts, gains, y (out) and grad_y (in), RIR-gradient parts
+    std::vector<int64_t> xs_src, xs_dst, xs_lead, xs_copy, xs_tail, xs_utt;
+    std::vector<int64_t> hs_src, hs_dst, hs_copy, hs_tail, hs_utt, hs_limr, hs_limo;
+    std::vector<int64_t> as_src, as_dst, as_utt;
+    std::vector<int64_t> ys_src, ys_dst, ys_copy, ys_utt;
+    // sum tables: dx (over the delayed copies), dalpha (over the parts)
+    std::vector<int64_t> dx_out, dx_len, dx_t0{0}, dx_src, dx_tlen, dx_utt;
+    std::vector<int64_t> da_out, da_len, da_t0{0}, da_src, da_tlen, da_utt;
+    int64_t xv = 0, rv = 0, sv = 0, yv = 0;       // virtual samples, RIR taps, sources, outputs
+    for (int k = 0; k < C; ++k) {
+        const int u = cand[k];
         const int I = d->num_sources[u];
-        const int64_t nx = d->num_samples[u];
+        const int64_t nx = d->num_samples[u], nv = nyv[u];
         int64_t nh = 1;
         for (int r = rir0[u]; r < rir0[u + 1]; ++r) nh = std::max<int64_t>(nh, rlen[r]);
         const int Pu = (int)((nh + P - 1) / P);
-        if ((int64_t)I * Pu > kMaxSources)
-            return fail(RSIM_E_UNSUPPORTED, "partitioned convolution needs sources x parts <= 16 per utterance");
-        ns[u] = I * Pu;
-        parts[u] = Pu;
+        if ((int64_t)I * Pu > kMaxPartSources)
+            return fail(RSIM_E_UNSUPPORTED, "partitioned convolution needs sources x parts <= 64 per utterance");
+        ns[k] = I * Pu;
+        nxs[k] = nv;
+        const int64_t v0 = (int64_t)rl.size();    // this utterance's first virtual RIR
         for (int i = 0; i < I; ++i) {
             const int64_t s = src0[u] + i;
             dx_out.push_back(xoff[s]);
             dx_len.push_back(nx);
-            da_out.push_back(s);
-            da_len.push_back(1);
+            dx_utt.push_back(k);
             for (int q = 0; q < Pu; ++q) {
-                const int64_t sv_q = sv + (int64_t)i * Pu + q;   // virtual source index
-                const int64_t xv_q = xv + ((int64_t)i * Pu + q) * nx;
-                const int64_t lead = std::min<int64_t>((int64_t)q * P, nx);
+                const int64_t vq = sv + (int64_t)i * Pu + q;             // virtual source
+                const int64_t xq = xv + ((int64_t)i * Pu + q) * nv;      // its samples
+                const int64_t lead = std::min<int64_t>((int64_t)q * P, nv);
+                const int64_t copy = std::min<int64_t>(nx, nv - lead);
                 xs_src.push_back(xoff[s]);
-                xs.push_back(xv_q);
+                xs_dst.push_back(xq);
                 xs_lead.push_back(lead);
-                xs_copy.push_back(nx - lead);
-                as_src.push_back(s);
-                dx_src.push_back(xv_q + lead);
-                dx_tlen.push_back(nx - lead);
-                da_src.push_back(sv_q);
-                da_tlen.push_back(1);
+                xs_copy.push_back(copy);
+                xs_tail.push_back(nv - lead - copy);
+                xs_utt.push_back(k);
+                dx_src.push_back(xq + lead);
+                dx_tlen.push_back(copy);
+                if (!per_rir) {
+                    as_src.push_back(s);
+                    as_dst.push_back(vq);
+                    as_utt.push_back(k);
+                    da_src.push_back(vq);
+                    da_tlen.push_back(1);
+                }
             }
             dx_t0.push_back((int64_t)dx_src.size());
-            da_t0.push_back((int64_t)da_src.size());
+            if (!per_rir) {
+                da_out.push_back(s);
+                da_len.push_back(1);
+                da_utt.push_back(k);
+                da_t0.push_back((int64_t)da_src.size());
+            }
         }
         // virtual RIRs in (virtual source, microphone) order
         for (int i = 0; i < I; ++i)
@@ -369,56 +389,104 @@ rsim_status make_partitioned(rsim_plan_t p, const rsim_plan_desc* d, int device,
                     const int64_t r = rir0[u] + (int64_t)i * J + j;
                     const int64_t valid = std::max<int64_t>(0, std::min<int64_t>(P, rlen[r] - (int64_t)q * P));
                     const int64_t len = std::max<int64_t>(valid, 1);
+                    const int64_t vr = (int64_t)rl.size();
                     rl.push_back((int32_t)len);
                     hs_src.push_back(roff[r] + (int64_t)q * P);
                     hs_dst.push_back(rv);
                     hs_copy.push_back(valid);
                     hs_tail.push_back(len - valid);
-                    dh_src.push_back(rv);
-                    dh_dst.push_back(roff[r] + (int64_t)q * P);
-                    dh_copy.push_back(valid);
+                    hs_utt.push_back(k);
+                    hs_limr.push_back(r);
+                    hs_limo.push_back((int64_t)q * P);
+                    if (per_rir) {
+                        as_src.push_back(r);
+                        as_dst.push_back(vr);
+                        as_utt.push_back(k);
+                    }
                     rv += len;
                 }
-        xv += (int64_t)I * Pu * nx;
+        if (per_rir) {
+            // dalpha_ij sums over the parts: virtual RIR (i, q, j) is the utterance's
+            // ((i Pu + q) J + j)-th
+            for (int i = 0; i < I; ++i)
+                for (int j = 0; j < J; ++j) {
+                    da_out.push_back(rir0[u] + (int64_t)i * J + j);
+                    da_len.push_back(1);
+                    da_utt.push_back(k);
+                    for (int q = 0; q < Pu; ++q) {
+                        da_src.push_back(v0 + ((int64_t)i * Pu + q) * J + j);
+                        da_tlen.push_back(1);
+                    }
+                    da_t0.push_back((int64_t)da_src.size());
+                }
+        }
+        // the output (J channels of nv samples) and grad_y, one segment each
+        ys_src.push_back(yv);
+        ys_dst.push_back(yoff[u]);
+        ys_copy.push_back((int64_t)J * nv);
+        ys_utt.push_back(k);
+        yv += (int64_t)J * nv;
+        xv += (int64_t)I * Pu * nv;
         sv += (int64_t)I * Pu;
     }
+    const int64_t nvr = (int64_t)rl.size();       // virtual RIRs
     rsim_plan_desc pd = *d;
+    pd.num_utts = C;
     pd.num_sources = ns.data();
+    pd.num_samples = nxs.data();
     pd.rir_len = rl.data();
-    pd.gain_mode = 1;
+    pd.eta_db = INFINITY;                         // the parts arrive cut
+    pd.gain_mode = per_rir ? 2 : 1;
     pd.output_mode = 0;
     pd.disable_graphs = 1;
     pd.snr_ref_mic = 0;
     pd.rooms = 0;
-    rsim_status st = rsim_plan(&pd, device, &p->part);
+    pd.long_rirs = 0;
+    rsim_status st = plan_build(&pd, device, &p->part, nullptr, kMaxPartSources);
     if (st != RSIM_OK) return fail(st, "partitioned plan: " + g_err);
-    // one allocation: tables, then the virtual buffers
-    std::vector<int64_t> zeros(std::max<size_t>({xs.size(), hs_src.size(), dh_src.size(), (size_t)1}), 0);
+    if (p->part->part) return fail(RSIM_E_UNSUPPORTED, "partitioned plan: parts beyond one block");
+    // one allocation: tables, the deferral flags and indices, then the virtual buffers
+    std::vector<int64_t> zeros(std::max<size_t>({xs_src.size(), hs_src.size(), as_src.size(), ys_src.size(),
+                                                 (size_t)1}), 0);
     std::vector<int64_t> ones_v(std::max<size_t>(as_src.size(), 1), 1);
-    std::vector<int64_t> seq(sv);
-    for (int64_t k = 0; k < sv; ++k) seq[k] = k;
+    std::vector<int64_t> didx(U, -1);
+    for (int k = 0; k < C; ++k) didx[cand[k]] = k;
     struct Arr { const std::vector<int64_t>* v; size_t n; const int64_t** dst; };
-    const size_t nS = xs.size(), nR = hs_src.size(), nO = dx_out.size();
+    const size_t nS = xs_src.size(), nR = hs_src.size(), nA = as_src.size(), nY = ys_src.size();
+    const size_t nO = dx_out.size(), nD = da_out.size();
+    const int64_t* defer_idx = nullptr;
     std::vector<Arr> arrs = {
-        {&xs_src, nS, &p->seg_x.src}, {&xs, nS, &p->seg_x.dst}, {&xs_lead, nS, &p->seg_x.lead},
-        {&xs_copy, nS, &p->seg_x.copy}, {&zeros, nS, &p->seg_x.tail},
+        {&xs_src, nS, &p->seg_x.src}, {&xs_dst, nS, &p->seg_x.dst}, {&xs_lead, nS, &p->seg_x.lead},
+        {&xs_copy, nS, &p->seg_x.copy}, {&xs_tail, nS, &p->seg_x.tail}, {&xs_utt, nS, &p->seg_x.utt},
         {&hs_src, nR, &p->seg_h.src}, {&hs_dst, nR, &p->seg_h.dst}, {&zeros, nR, &p->seg_h.lead},
-        {&hs_copy, nR, &p->seg_h.copy}, {&hs_tail, nR, &p->seg_h.tail},
-        {&as_src, nS, &p->seg_a.src}, {&seq, nS, &p->seg_a.dst}, {&zeros, nS, &p->seg_a.lead},
-        {&ones_v, nS, &p->seg_a.copy}, {&zeros, nS, &p->seg_a.tail},
-        {&dh_src, nR, &p->seg_dh.src}, {&dh_dst, nR, &p->seg_dh.dst}, {&zeros, nR, &p->seg_dh.lead},
-        {&dh_copy, nR, &p->seg_dh.copy}, {&zeros, nR, &p->seg_dh.tail},
+        {&hs_copy, nR, &p->seg_h.copy}, {&hs_tail, nR, &p->seg_h.tail}, {&hs_utt, nR, &p->seg_h.utt},
+        {&hs_limr, nR, &p->seg_h.lim_r}, {&hs_limo, nR, &p->seg_h.lim_off},
+        {&as_src, nA, &p->seg_a.src}, {&as_dst, nA, &p->seg_a.dst}, {&zeros, nA, &p->seg_a.lead},
+        {&ones_v, nA, &p->seg_a.copy}, {&zeros, nA, &p->seg_a.tail}, {&as_utt, nA, &p->seg_a.utt},
+        {&hs_dst, nR, &p->seg_dh.src}, {&hs_src, nR, &p->seg_dh.dst}, {&zeros, nR, &p->seg_dh.lead},
+        {&hs_copy, nR, &p->seg_dh.copy}, {&zeros, nR, &p->seg_dh.tail}, {&hs_utt, nR, &p->seg_dh.utt},
+        {&hs_limr, nR, &p->seg_dh.lim_r}, {&hs_limo, nR, &p->seg_dh.lim_off},
+        {&ys_src, nY, &p->seg_y.src}, {&ys_dst, nY, &p->seg_y.dst}, {&zeros, nY, &p->seg_y.lead},
+        {&ys_copy, nY, &p->seg_y.copy}, {&zeros, nY, &p->seg_y.tail}, {&ys_utt, nY, &p->seg_y.utt},
+        {&ys_dst, nY, &p->seg_gy.src}, {&ys_src, nY, &p->seg_gy.dst}, {&zeros, nY, &p->seg_gy.lead},
+        {&ys_copy, nY, &p->seg_gy.copy}, {&zeros, nY, &p->seg_gy.tail}, {&ys_utt, nY, &p->seg_gy.utt},
         {&dx_out, nO, &p->sum_dx.out}, {&dx_len, nO, &p->sum_dx.len}, {&dx_t0, nO + 1, &p->sum_dx.t0},
         {&dx_src, dx_src.size(), &p->sum_dx.src}, {&dx_tlen, dx_tlen.size(), &p->sum_dx.tlen},
-        {&da_out, nO, &p->sum_da.out}, {&da_len, nO, &p->sum_da.len}, {&da_t0, nO + 1, &p->sum_da.t0},
+        {&dx_utt, nO, &p->sum_dx.utt},
+        {&da_out, nD, &p->sum_da.out}, {&da_len, nD, &p->sum_da.len}, {&da_t0, nD + 1, &p->sum_da.t0},
         {&da_src, da_src.size(), &p->sum_da.src}, {&da_tlen, da_tlen.size(), &p->sum_da.tlen},
+        {&da_utt, nD, &p->sum_da.utt},
+        {&didx, (size_t)U, &defer_idx},
     };
     size_t total = 0;
     for (auto& a : arrs) total = align_up(total, 256) + sizeof(int64_t) * std::max<size_t>(a.n, 1);
+    const size_t d_off = align_up(total, 256);
+    total = d_off + std::max(C, 1);
     const size_t f_off = align_up(total, 256);
-    const int64_t fl[6] = {xv, rv, sv, xv, rv, sv};   // x, rir, gains, dx, dh, dalpha
+    const int64_t ng = per_rir ? nvr : sv;            // gains: per virtual RIR or virtual source
+    const int64_t fl[7] = {xv, rv, ng, yv, xv, rv, ng};    // x, RIR taps, gains, y, dx, dh, dalpha
     total = f_off;
-    for (int k = 0; k < 6; ++k) total = align_up(total, 256) + sizeof(float) * std::max<int64_t>(fl[k], 1);
+    for (int k = 0; k < 7; ++k) total = align_up(total, 256) + sizeof(float) * std::max<int64_t>(fl[k], 1);
     DeviceGuard guard(device);
     cudaError_t e = cudaMalloc(&p->part_mem, total);
     if (e != cudaSuccess) {
@@ -437,16 +505,38 @@ rsim_status make_partitioned(rsim_plan_t p, const rsim_plan_desc* d, int device,
         *a.dst = dst;
         off += sizeof(int64_t) * std::max<size_t>(a.n, 1);
     }
-    float** bufs[6] = {&p->part_x, &p->part_rir, &p->part_a, &p->part_dx, &p->part_dh, &p->part_da};
+    p->defer = (uint8_t*)((char*)p->part_mem + d_off);
+    e = cudaMemset(p->defer, 0, std::max(C, 1));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset (deferral flags)");
+    float** bufs[7] = {&p->part_x, &p->part_rir, &p->part_a, &p->part_y, &p->part_dx, &p->part_dh, &p->part_da};
     off = f_off;
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < 7; ++k) {
         off = align_up(off, 256);
         *bufs[k] = (float*)((char*)p->part_mem + off);
         off += sizeof(float) * std::max<int64_t>(fl[k], 1);
     }
-    p->seg_x.n = p->seg_a.n = (int64_t)nS;
+    p->seg_x.n = (int64_t)nS;
     p->seg_h.n = p->seg_dh.n = (int64_t)nR;
-    p->sum_dx.n = p->sum_da.n = (int64_t)nO;
+    p->seg_a.n = (int64_t)nA;
+    p->seg_y.n = p->seg_gy.n = (int64_t)nY;
+    p->sum_dx.n = (int64_t)nO;
+    p->sum_da.n = (int64_t)nD;
+    // destination extents (floats), for the bounds-checked build
+    p->seg_x.out_n = xv;
+    p->seg_h.out_n = rv;
+    p->seg_a.out_n = ng;
+    p->seg_y.out_n = yoff[U];
+    p->seg_gy.out_n = yv;
+    p->seg_dh.out_n = roff.back();
+    p->sum_dx.out_n = xoff.back();
+    p->sum_da.out_n = per_rir ? (int64_t)roff.size() - 1 : (int64_t)xoff.size() - 1;
+    p->part_utt = cand;
+    // the outer planner writes the flags the partitioned planner reads; gain mode 2's dalpha
+    // reads the RIR parts the forward was given
+    p->B.defer_idx = defer_idx;
+    p->B.defer = p->defer;
+    p->part->B.active = p->defer;
+    p->part->fwd_rir = p->part_rir;
     return RSIM_OK;
 }
 
@@ -456,7 +546,8 @@ namespace {
 // Builds a plan for description d.  With `borrow` non-NULL the plan takes no new
 // device memory, streams or events: its pieces must fit borrow's (same carving
 // order, each no larger), which are used at the same offsets (a reshape).
-rsim_status plan_build(const rsim_plan_desc* d, int device, rsim_plan_t* out, rsim_plan_t borrow) {
+rsim_status plan_build(const rsim_plan_desc* d, int device, rsim_plan_t* out, rsim_plan_t borrow,
+                       int max_sources) {
     if (!d || !out) return fail(RSIM_E_INVALID, "rsim_plan: NULL argument");
     *out = nullptr;
     const int U = d->num_utts, J = d->num_mics;
@@ -476,25 +567,28 @@ rsim_status plan_build(const rsim_plan_desc* d, int device, rsim_plan_t* out, rs
     if (d->output_mode != 0 && d->output_mode != 1) return fail(RSIM_E_INVALID, "output_mode must be 0 or 1");
     if (d->segment_len < 0 || d->bwd_segment_len < 0)
         return fail(RSIM_E_INVALID, "segment_len and bwd_segment_len must be >= 0");
-    // without a cut-off, an RIR longer than the largest allowed FFT size reaches (hop >= N/4:
-    // 3N/4 + 1 taps) goes through uniformly partitioned convolution
+    if (d->long_rirs != 0 && d->long_rirs != 1) return fail(RSIM_E_INVALID, "long_rirs must be 0 or 1");
+    // an utterance whose RIRs reach beyond one block of the largest allowed FFT size (hop >=
+    // N/4: 3N/4 + 1 taps) gets a partitioned path, without a cut-off or when asked for
     int part_log = kMinLog;
     for (int m = kMinLog; m <= kMaxLog; ++m)
         if ((mask >> m) & 1) part_log = m;
-    bool partitioned = false;
-    if (std::isinf(d->eta_db)) {
-        int64_t nh_all = 0, r_all = 0;
-        for (int u = 0; u < U; ++u) r_all += (int64_t)std::max(d->num_sources[u], 0) * J;
-        for (int64_t r = 0; r < r_all; ++r) nh_all = std::max<int64_t>(nh_all, d->rir_len[r]);
-        partitioned = nh_all > 3 * ((int64_t)1 << part_log) / 4 + 1;
+    const int64_t reach = 3 * ((int64_t)1 << part_log) / 4 + 1;
+    std::vector<int32_t> cand;
+    if (std::isinf(d->eta_db) || d->long_rirs) {
+        int64_t r = 0;
+        for (int u = 0; u < U; ++u) {
+            int64_t nh = 0;
+            const int64_t r1 = r + (int64_t)std::max(d->num_sources[u], 0) * J;
+            for (; r < r1; ++r) nh = std::max<int64_t>(nh, d->rir_len[r]);
+            if (nh > reach) cand.push_back(u);
+        }
     }
+    const bool partitioned = !cand.empty();
     if (d->rooms != 0 && d->rooms != 1) return fail(RSIM_E_INVALID, "rooms must be 0 or 1");
     if (d->rooms && (partitioned || d->gain_mode == 3))
         return fail(RSIM_E_UNSUPPORTED, "rooms = 1 needs gain_mode 0, 1 or 2 and every RIR within the "
                                         "largest FFT size's reach (no partitioned convolution)");
-    if (partitioned && (d->output_mode != 0 || d->gain_mode > 1))
-        return fail(RSIM_E_UNSUPPORTED, "RIRs longer than the largest FFT size reaches (partitioned "
-                                        "convolution) need output_mode 0 and gain_mode 0 or 1");
 
     std::vector<int32_t> src0(U + 1), rir0(U + 1), seg0(U + 1);
     std::vector<int64_t> yoff(U + 1), nyv(U);
@@ -511,7 +605,7 @@ rsim_status plan_build(const rsim_plan_desc* d, int device, rsim_plan_t* out, rs
     for (int u = 0; u < U; ++u) {
         const int I = d->num_sources[u];
         const int64_t nx = d->num_samples[u];
-        if (I < 1 || I > kMaxSources) return fail(RSIM_E_INVALID, "num_sources[u] must be in [1, 16]");
+        if (I < 1 || I > max_sources) return fail(RSIM_E_INVALID, "num_sources[u] must be in [1, 16]");
         if (nx < 1) return fail(RSIM_E_INVALID, "num_samples[u] must be >= 1");
         src0[u] = (int32_t)S;
         rir0[u] = (int32_t)R;
@@ -862,7 +956,8 @@ rsim_status plan_build(const rsim_plan_desc* d, int device, rsim_plan_t* out, rs
         return cuda_fail(e, "kernel attribute setup");
     }
     if (partitioned) {
-        const rsim_status ps = make_partitioned(p, d, device, src0, rir0, xoff, roff, rlen, part_log);
+        const rsim_status ps = make_partitioned(p, d, device, src0, rir0, xoff, roff, rlen, nyv, yoff, part_log,
+                                                cand);
         if (ps != RSIM_OK) {
             const std::string msg = g_err;
             rsim_plan_destroy(p);
@@ -901,7 +996,7 @@ rsim_status plan_build(const rsim_plan_desc* d, int device, rsim_plan_t* out, rs
 
 extern "C" rsim_status rsim_plan(const rsim_plan_desc* d, int device, rsim_plan_t* out) {
     g_err.clear();
-    return plan_build(d, device, out, nullptr);
+    return plan_build(d, device, out, nullptr, kMaxSources);
 }
 
 extern "C" rsim_status rsim_plan_reshape(rsim_plan_t p, const rsim_plan_desc* d) {
@@ -913,12 +1008,13 @@ extern "C" rsim_status rsim_plan_reshape(rsim_plan_t p, const rsim_plan_desc* d)
     const rsim_plan_desc& f = p->desc_fixed;
     if (d->num_mics != f.num_mics || d->eta_db != f.eta_db || d->fft_sizes_mask != f.fft_sizes_mask ||
         d->gain_mode != f.gain_mode || d->output_mode != f.output_mode || d->snr_ref_mic != f.snr_ref_mic ||
-        d->rooms != f.rooms || d->segment_len != f.segment_len || d->disable_graphs != f.disable_graphs)
+        d->rooms != f.rooms || d->segment_len != f.segment_len || d->disable_graphs != f.disable_graphs ||
+        d->long_rirs != f.long_rirs)
         return fail(RSIM_E_INVALID, "rsim_plan_reshape: only the batch shape may change (num_utts, "
                                     "num_sources, num_samples, rir_len, fft_cost)");
     DeviceGuard guard(p->device);
     rsim_plan_t np = nullptr;
-    const rsim_status st = plan_build(d, p->device, &np, p);
+    const rsim_status st = plan_build(d, p->device, &np, p, kMaxSources);
     if (st != RSIM_OK) return st;                // p is unchanged
     if (np->part || np->rev) {
         // the new shape needs a sub-plan: keep the old state
@@ -960,11 +1056,11 @@ extern "C" rsim_status rsim_plan_reshape(rsim_plan_t p, const rsim_plan_desc* d)
 
 namespace {
 
-void copy_segs(const rsim_plan_s::Segs& g, const float* in, float* out, cudaStream_t st) {
-    if (g.n > 0) k_copy_segs<<<(unsigned)std::min<int64_t>(g.n, 4096), 256, 0, st>>>(g, in, out);
+void copy_segs(rsim_plan_t p, const rsim_plan_s::Segs& g, const float* in, float* out, cudaStream_t st) {
+    if (g.n > 0) k_copy_segs<<<(unsigned)std::min<int64_t>(g.n, 4096), 256, 0, st>>>(p->B, g, in, out);
 }
-void sum_segs(const rsim_plan_s::Sums& g, const float* in, float* out, cudaStream_t st) {
-    if (g.n > 0) k_sum_segs<<<(unsigned)std::min<int64_t>(g.n, 4096), 256, 0, st>>>(g, in, out);
+void sum_segs(rsim_plan_t p, const rsim_plan_s::Sums& g, const float* in, float* out, cudaStream_t st) {
+    if (g.n > 0) k_sum_segs<<<(unsigned)std::min<int64_t>(g.n, 4096), 256, 0, st>>>(p->B, g, in, out);
 }
 
 // Room geometry of rsim_filter_mix_rooms: the RIRs are made on the device with
@@ -981,26 +1077,6 @@ cudaError_t enqueue_forward(rsim_plan_t p, cudaStream_t st, const float* x, cons
                             const float* snr_db, float* gains, float* y, int32_t* trunc_len,
                             float* energy_kept_frac, const RoomsCall* rooms = nullptr) {
     const DevBatch& B = p->B;
-    if (p->part) {
-        // partitioned: lengths (no cut-off) and gains here, the filtering on the plan over the
-        // virtual sources
-        launch_truncate(B, rir, p->factor, p->none, energy_kept_frac, p->grid_trunc, st);
-        if (p->gain_mode == 0) {
-            launch_power(B, x, p->grid_pow, st);
-            k_part_gains<<<(B.U + 255) / 256, 256, 0, st>>>(B, snr_db, gains);
-        }
-        copy_segs(p->seg_x, x, p->part_x, st);
-        copy_segs(p->seg_h, rir, p->part_rir, st);
-        copy_segs(p->seg_a, gains, p->part_a, st);
-        cudaError_t e = enqueue_forward(p->part, st, p->part_x, p->part_rir, nullptr, p->part_a, y, nullptr,
-                                        nullptr);
-        if (e != cudaSuccess) return e;
-        if (trunc_len) {
-            e = cudaMemcpyAsync(trunc_len, B.L, sizeof(int32_t) * B.R, cudaMemcpyDeviceToDevice, st);
-            if (e != cudaSuccess) return e;
-        }
-        return cudaGetLastError();
-    }
     // the cut-off: the scan of the caller's RIRs, or the RIRs made from room geometry
     // with the cut-off fused, whose kept taps then stand in for the caller's RIRs
     auto cut = [&](cudaStream_t s) {
@@ -1072,6 +1148,17 @@ cudaError_t enqueue_forward(rsim_plan_t p, cudaStream_t st, const float* x, cons
     stage_mark(p, 5, false, st);
     launch_fixup(B, y, p->tails, st);
     stage_mark(p, 5, true, st);
+    if (p->part) {
+        // the utterances the planner deferred: their sources delayed by whole parts, their
+        // cut RIRs in parts and their gains onto the partitioned plan, its output back
+        copy_segs(p, p->seg_x, x, p->part_x, st);
+        copy_segs(p, p->seg_h, rir, p->part_rir, st);
+        copy_segs(p, p->seg_a, gains, p->part_a, st);
+        cudaError_t e = enqueue_forward(p->part, st, p->part_x, p->part_rir, nullptr, p->part_a, p->part_y,
+                                        nullptr, nullptr);
+        if (e != cudaSuccess) return e;
+        copy_segs(p, p->seg_y, p->part_y, y, st);
+    }
     if (trunc_len) {
         cudaError_t e = cudaMemcpyAsync(trunc_len, B.L, sizeof(int32_t) * B.R, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return e;
@@ -1083,17 +1170,6 @@ cudaError_t enqueue_forward(rsim_plan_t p, cudaStream_t st, const float* x, cons
 cudaError_t enqueue_backward(rsim_plan_t p, cudaStream_t st, const float* grad_y, const float* x,
                              const float* gains, float* grad_x, float* grad_rir, float* grad_gains) {
     const DevBatch& B = p->B;
-    if (p->part) {
-        // the plan over the virtual sources, then its gradients folded back: dx_i sums the
-        // delayed copies, dh_ij gathers the parts, dalpha_i sums over the parts
-        cudaError_t e = enqueue_backward(p->part, st, grad_y, p->part_x, p->part_a, grad_x ? p->part_dx : nullptr,
-                                         p->part_dh, p->part_da);
-        if (e != cudaSuccess) return e;
-        if (grad_x) sum_segs(p->sum_dx, p->part_dx, grad_x, st);
-        copy_segs(p->seg_dh, p->part_dh, grad_rir, st);
-        sum_segs(p->sum_da, p->part_da, grad_gains, st);
-        return cudaGetLastError();
-    }
     const float* rir_gain = p->gain_mode == 2 ? gains : nullptr;
     const float* src_gains = p->gain_mode == 2 ? p->ones : gains;
     cudaError_t e = cudaMemsetAsync(p->Q.next + p->Q.idx(kListBwd, 0), 0, sizeof(int32_t) * kNumBuckets, st);
@@ -1107,6 +1183,18 @@ cudaError_t enqueue_backward(rsim_plan_t p, cudaStream_t st, const float* grad_y
     stage_mark(p, 7, false, st);
     launch_finalize(B, src_gains, rir_gain, p->fwd_rir, p->dhp, p->dap, grad_rir, grad_gains, st);
     stage_mark(p, 7, true, st);
+    if (p->part) {
+        // the deferred utterances: grad_y onto the partitioned plan, its gradients folded back
+        // over the finalizer's zeros (dx_i sums the delayed copies, dh_ij gathers the parts
+        // below the kept length, dalpha sums over the parts)
+        copy_segs(p, p->seg_gy, grad_y, p->part_y, st);
+        e = enqueue_backward(p->part, st, p->part_y, p->part_x, p->part_a, grad_x ? p->part_dx : nullptr,
+                             p->part_dh, p->part_da);
+        if (e != cudaSuccess) return e;
+        if (grad_x) sum_segs(p, p->sum_dx, p->part_dx, grad_x, st);
+        copy_segs(p, p->seg_dh, p->part_dh, grad_rir, st);
+        sum_segs(p, p->sum_da, p->part_da, grad_gains, st);
+    }
     return cudaGetLastError();
 }
 
@@ -1266,7 +1354,6 @@ extern "C" rsim_status rsim_plan_query(rsim_plan_t p, void* stream, int32_t* log
     if (!p) return fail(RSIM_E_INVALID, "NULL plan");
     if (!p->fwd_done) return fail(RSIM_E_STATE, "rsim_plan_query before rsim_filter_mix");
     DeviceGuard guard(p->device);
-    if (p->part) p = p->part;   // the FFT sizes and blocks of the partitioned filtering
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     const size_t n = sizeof(int32_t) * p->B.U;
@@ -1278,6 +1365,26 @@ extern "C" rsim_status rsim_plan_query(rsim_plan_t p, void* stream, int32_t* log
         return cuda_fail(e, "cudaMemcpy");
     if (num_blocks && (e = cudaMemcpy(num_blocks, p->B.nblk, n, cudaMemcpyDeviceToHost)) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpy");
+    if (p->part) {
+        // deferred utterances report the size, hop and blocks of their partitioned filtering
+        // (l_max stays the longest kept RIR)
+        const int C = (int)p->part_utt.size();
+        std::vector<uint8_t> dfr(C);
+        std::vector<int32_t> pl(C), ph(C), pb(C);
+        const size_t nc = sizeof(int32_t) * C;
+        if ((e = cudaMemcpy(dfr.data(), p->defer, C, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+            (e = cudaMemcpy(pl.data(), p->part->B.logN, nc, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+            (e = cudaMemcpy(ph.data(), p->part->B.hop, nc, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+            (e = cudaMemcpy(pb.data(), p->part->B.nblk, nc, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpy");
+        for (int k = 0; k < C; ++k) {
+            if (!dfr[k]) continue;
+            const int u = p->part_utt[k];
+            if (log2_n) log2_n[u] = pl[k];
+            if (hop) hop[u] = ph[k];
+            if (num_blocks) num_blocks[u] = pb[k];
+        }
+    }
     return RSIM_OK;
 }
 

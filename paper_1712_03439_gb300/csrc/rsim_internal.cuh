@@ -12,7 +12,10 @@ namespace rsim {
 constexpr int kMinLog = 11;
 constexpr int kMaxLog = 14;
 constexpr int kNumBuckets = kMaxLog - kMinLog + 1;
-constexpr int kMaxSources = 16;      // sources per utterance (bwd tile encoding)
+constexpr int kMaxSources = 16;      // sources per utterance (the public limit; the dalpha
+                                     // partials are strided by it)
+constexpr int kMaxPartSources = 64;  // virtual sources (source x part) per utterance of a
+                                     // partitioned plan
 constexpr int kJG = 2;               // microphones per group inside a tile
 constexpr int kPowerChunk = 32768;   // samples per partial-power CTA
 
@@ -80,6 +83,12 @@ struct DevBatch {
     int32_t test_withhold;   // test hook: the bulk copies are not issued, so the kernels'
                              // bounded waits run out (set from RSIM_TEST_WITHHOLD_BULK_COPY)
     int64_t NDHP;            // floats of the RIR-gradient partials (the planner fits the pieces in)
+    // utterances whose RIRs may reach beyond one block of the largest size (partitioned path)
+    const int64_t* defer_idx;   // [U] index of utterance u in the partitioned plan, -1 if it has
+                                // none (NULL: no utterance has one)
+    uint8_t* defer;             // [utterances of that plan] 1: the planner sent the utterance there
+    const uint8_t* active;      // in the partitioned plan: [U] 0 = the outer planner kept the
+                                // utterance (no work here); NULL: every utterance is active
 };
 
 struct Queues {

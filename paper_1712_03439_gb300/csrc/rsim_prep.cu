@@ -105,9 +105,10 @@ void launch_power(const DevBatch& B, const float* x, int grid, cudaStream_t st) 
 // N minimises the cost of Eq. 6 (ceiling block count, one hop shared by all
 // (i, j) of the utterance: hop = N - L_max + 1) weighted by the per-size cost
 // table; N must leave hop >= N/4 (a block's tail may then reach several
-// blocks ahead; the forward carries it).  Then per FFT size it writes the lists of
-// spectrum jobs (RIRs), forward tiles (segments) and backward tiles
-// (backward segment, source), in utterance order, and resets the queue cursors.
+// blocks ahead; the forward carries it).  An utterance no allowed N fits goes
+// to its partitioned path when it has one (no work here), else it is an error.
+// Then the backward partition of each size (below), and per FFT size the lists
+// of spectrum jobs (RIRs) and forward tiles (segments), in utterance order.
 constexpr int kPlanThreads = 1024;
 constexpr float kConsolidateShare = 0.1f;   // a size below this share of the work is a minority
 constexpr float kConsolidateSlack = 0.02f;  // ...and moves if that adds at most this share of the work
@@ -156,9 +157,11 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
         float cost[kNumBuckets];
         int best = 0;
         float best_c = 0.f;
+        // in a partitioned plan, an utterance the outer planner kept gets no work
+        const bool idle = B.active && !B.active[u];
         for (int m = kMinLog; m <= kMaxLog; ++m) {
             cost[m - kMinLog] = -1.f;                  // not allowed or not admissible
-            if (!((B.mask >> m) & 1)) continue;
+            if (idle || !((B.mask >> m) & 1)) continue;
             const int64_t N = 1LL << m;
             const int64_t hop = N - lmax + 1;
             if (4 * hop < N) continue;                 // hop >= N/4 keeps blocks useful
@@ -168,7 +171,10 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
             cost[m - kMinLog] = c;
             if (best == 0 || c < best_c) { best = m; best_c = c; }
         }
-        if (best == 0) atomicOr(B.err, kErrNoFftSize);
+        // no size fits the kept RIRs: the utterance's partitioned path takes it, if it has one
+        const int64_t di = B.defer_idx ? B.defer_idx[u] : -1;
+        if (di >= 0) B.defer[di] = best == 0 ? 1 : 0;
+        if (best == 0 && di < 0 && !idle) atomicOr(B.err, kErrNoFftSize);
         B.logN[u] = best;
         B.Lmax[u] = lmax;
         if (best) {
