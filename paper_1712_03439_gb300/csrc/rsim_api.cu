@@ -192,16 +192,19 @@ namespace {
 // segment o of a deferred utterance: lead[o] zeros, then copy[o] values from in + src[o]
 // (at most L[lim_r[o]] - lim_off[o] of them: a part of a cut RIR, or of its gradient; zeros
 // in place of the rest), then tail[o] zeros, written from out + dst[o]
-// (B: the outer plan, whose planner set the deferral flags and whose cut-off set L)
+// (B: the outer plan, whose planner set the deferral flags and whose cut-off set L).
+// The blocks of one grid row (blockIdx.y) take segments o = y, y + gridDim.y, ...; the
+// gridDim.x blocks of a row split each segment's values between them.
 __global__ void k_copy_segs(DevBatch B, rsim_plan_s::Segs g, const float* __restrict__ in, float* __restrict__ out) {
-    for (int64_t o = blockIdx.x; o < g.n; o += gridDim.x) {
+    const int64_t k0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, dk = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t o = blockIdx.y; o < g.n; o += gridDim.y) {
         if (!B.defer[g.utt[o]]) continue;
         float* d = out + g.dst[o];
         const float* s = in + g.src[o];
         const int64_t a = g.lead[o], n = a + g.copy[o] + g.tail[o];
         int64_t c = g.copy[o];
         if (g.lim_r) c = max((int64_t)0, min(c, (int64_t)B.L[g.lim_r[o]] - g.lim_off[o]));
-        for (int64_t k = threadIdx.x; k < n; k += blockDim.x)
+        for (int64_t k = k0; k < n; k += dk)
             if (RSIM_STORE_OK(B, d + k, out, 4 * g.out_n)) d[k] = (k >= a && k < a + c) ? s[k - a] : 0.f;
     }
 }
@@ -209,10 +212,11 @@ __global__ void k_copy_segs(DevBatch B, rsim_plan_s::Segs g, const float* __rest
 // output o of a deferred utterance, length len[o]: out[out[o] + m] = sum over terms q in
 // [t0[o], t0[o + 1]) of in[src[q] + m] for m < tlen[q] (terms added in order)
 __global__ void k_sum_segs(DevBatch B, rsim_plan_s::Sums g, const float* __restrict__ in, float* __restrict__ out) {
-    for (int64_t o = blockIdx.x; o < g.n; o += gridDim.x) {
+    const int64_t m0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, dm = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t o = blockIdx.y; o < g.n; o += gridDim.y) {
         if (!B.defer[g.utt[o]]) continue;
         const int64_t q0 = g.t0[o], q1 = g.t0[o + 1];
-        for (int64_t m = threadIdx.x; m < g.len[o]; m += blockDim.x) {
+        for (int64_t m = m0; m < g.len[o]; m += dm) {
             float acc = 0.f;
             for (int64_t q = q0; q < q1; ++q)
                 if (m < g.tlen[q]) acc += in[g.src[q] + m];
@@ -1056,11 +1060,18 @@ extern "C" rsim_status rsim_plan_reshape(rsim_plan_t p, const rsim_plan_desc* d)
 
 namespace {
 
+// grid: up to 4096 segment rows, and enough blocks per row to cover about 8 blocks per SM
+// in all (long segments, such as a deferred utterance's output, then spread over the GPU)
+dim3 segs_grid(rsim_plan_t p, int64_t n) {
+    const int64_t rows = std::min<int64_t>(n, 4096);
+    const int64_t cols = std::max<int64_t>(1, std::min<int64_t>(64, ((int64_t)p->sms * 8 + rows - 1) / rows));
+    return dim3((unsigned)cols, (unsigned)rows);
+}
 void copy_segs(rsim_plan_t p, const rsim_plan_s::Segs& g, const float* in, float* out, cudaStream_t st) {
-    if (g.n > 0) k_copy_segs<<<(unsigned)std::min<int64_t>(g.n, 4096), 256, 0, st>>>(p->B, g, in, out);
+    if (g.n > 0) k_copy_segs<<<segs_grid(p, g.n), 256, 0, st>>>(p->B, g, in, out);
 }
 void sum_segs(rsim_plan_t p, const rsim_plan_s::Sums& g, const float* in, float* out, cudaStream_t st) {
-    if (g.n > 0) k_sum_segs<<<(unsigned)std::min<int64_t>(g.n, 4096), 256, 0, st>>>(p->B, g, in, out);
+    if (g.n > 0) k_sum_segs<<<segs_grid(p, g.n), 256, 0, st>>>(p->B, g, in, out);
 }
 
 // Room geometry of rsim_filter_mix_rooms: the RIRs are made on the device with

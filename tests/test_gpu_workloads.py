@@ -9,7 +9,9 @@
   against the oracle's window forms, and the adjoint identities over the
   whole batch;
   without a cut-off (RIRs up to 19200 taps, beyond what one block of the
-  largest FFT size reaches) through the partitioned convolution.
+  largest FFT size reaches) through the partitioned convolution; and the same
+  shape at 30 dB with the full output, one utterance whose kept RIRs fit a block
+  beside one (RT60 2.0-2.4 s) whose kept RIRs do not.
 """
 import math
 
@@ -108,27 +110,31 @@ def test_differentiable_mix_64_utterances_autograd():
 
 
 # ---------------------------------------------------------------------------
+SEED_LONG = 171203439 + 40
+
+
 @pytest.fixture(scope="module")
 def long_batch():
     return synth.config_long(n_utts=2)
 
 
-@pytest.mark.parametrize("eta", [10.0, 20.0, 30.0, math.inf])
-def test_long_reverberant_multimic(long_batch, eta):
+def check_long(b, eta, output_mode=0, long_rirs=False):
+    """Forward + backward of a long-reverberation batch: lengths exact, adjoint
+    identities over the whole batch, outputs, dx and dh on sampled windows against
+    the oracle's window forms.  Returns the plan's query."""
     from paper_1712_03439_gb300 import Plan
-    b = long_batch
     J, S = b.num_mics, int(b.num_sources.sum())
-    assert J == 8 and np.all(b.num_sources == 4) and np.all(b.num_samples == 30 * synth.FS)
     gains = np.linspace(0.7, 1.3, S).astype(np.float32)
-    plan = Plan.for_batch(b, eta_db=eta, gain_mode=1)
+    plan = Plan.for_batch(b, eta_db=eta, gain_mode=1, output_mode=output_mode, long_rirs=long_rirs)
     x, rir, g = dev(b.x), dev(b.rir), dev(gains)
     y = torch.empty(plan.y_size, device="cuda")
     tl = torch.empty(plan.R, dtype=torch.int32, device="cuda")
     plan.filter_mix(x, rir, g, y, trunc_len=tl)
-    gy = synth.grad_like(71, b.y_size)
+    gy = synth.grad_like(71, plan.y_size)
     gx, gr, gg = torch.empty_like(x), torch.empty_like(rir), torch.empty_like(g)
     plan.filter_mix_backward(dev(gy), x, g, gx, gr, gg)
     plan.sync_status()
+    q = plan.query()
     L = oracle.truncate_batch(b, eta)["L"]
     np.testing.assert_array_equal(tl.cpu().numpy(), L.astype(np.int32))
     yv, gxv, grv, ggv = (t.cpu().numpy() for t in (y, gx, gr, gg))
@@ -143,20 +149,23 @@ def test_long_reverberant_multimic(long_batch, eta):
                       ("dalpha", np.dot(ggv.astype(np.float64), gains.astype(np.float64)))):
         assert abs(val - lhs) <= REL_L2 * abs(lhs), f"<{what}, .> vs <g, y>: {abs(val - lhs) / abs(lhs):.3e}"
     # sampled windows: the oracle computes those output (and dx) positions only
-    si, xo, yo, ri, ro = b.src_index(), b.x_offsets(), b.y_offsets(), b.rir_index(), b.rir_offsets()
+    n_out = synth.output_lengths(b, output_mode)
+    yo = np.concatenate([[0], np.cumsum(n_out * J)]).astype(np.int64)
+    si, xo, ri = b.src_index(), b.x_offsets(), b.rir_index()
     W = 1000
     for u in range(b.num_utts):
-        nx = int(b.num_samples[u])
+        nx, ny = int(b.num_samples[u]), int(n_out[u])
         I = int(b.num_sources[u])
         xs = np.stack([b.x[xo[s]:xo[s + 1]] for s in range(si[u], si[u + 1])])
         rirs = [b.rir[ro[r]:ro[r + 1]] for r in range(ri[u], ri[u + 1])]
         Lu = L[ri[u]:ri[u + 1]]
         a_u = gains[si[u]:si[u + 1]].astype(np.float64)
-        gu = gy[yo[u]:yo[u + 1]].reshape(J, nx)
-        for n0 in (0, 123457, nx - W):
+        gu = gy[yo[u]:yo[u + 1]].reshape(J, ny)
+        # (a window across the end of x only where the output runs past it)
+        for n0 in sorted({0, 123457, ny - W} | ({nx - W // 2} if ny > nx else set())):
             yw = oracle.mix_window(xs, rirs, Lu, a_u, n0, n0 + W)
             for j in range(J):
-                close_channel(yv[yo[u] + j * nx + n0:yo[u] + j * nx + n0 + W], yw[j], f"y u={u} j={j} n0={n0}")
+                close_channel(yv[yo[u] + j * ny + n0:yo[u] + j * ny + n0 + W], yw[j], f"y u={u} j={j} n0={n0}")
         for m0 in (0, 250001, nx - W):
             for i in range(I):
                 s = si[u] + i
@@ -165,10 +174,35 @@ def test_long_reverberant_multimic(long_batch, eta):
         # dh of sampled RIRs element by element on tap windows: the start, the middle,
         # the window across the cut-off (zero from L on) and the last taps
         WH = 256
-        for q in sorted({0, 5, 13, I * J - 1}):
-            r, i, j = ri[u] + q, q // J, q % J
+        for q_ in sorted({0, 5, 13, I * J - 1}):
+            r, i, j = ri[u] + q_, q_ // J, q_ % J
             nh, Lr = int(b.rir_len[r]), int(L[r])
             for k0 in sorted({0, Lr // 2, max(Lr - WH // 2, 0), max(nh - WH, 0)}):
                 k1 = min(k0 + WH, nh)
                 dhw = oracle.dh_window(xs[i], gu[j], Lr, a_u[i], k0, k1)
-                close_channel(grv[ro[r] + k0:ro[r] + k1], dhw, f"dh u={u} r={q} k0={k0}")
+                close_channel(grv[ro[r] + k0:ro[r] + k1], dhw, f"dh u={u} r={q_} k0={k0}")
+    return q
+
+
+@pytest.mark.parametrize("eta", [10.0, 20.0, 30.0, math.inf])
+def test_long_reverberant_multimic(long_batch, eta):
+    b = long_batch
+    assert b.num_mics == 8 and np.all(b.num_sources == 4) and np.all(b.num_samples == 30 * synth.FS)
+    check_long(b, eta)
+
+
+def test_long_reverberant_full_output_with_kept_rirs_beyond_one_block():
+    # the long-reverberation shape (30 s, 4 sources, 8-mic circle) at 30 dB: an utterance
+    # at RT60 1.2-1.4 s whose kept RIRs fit one block of N = 16384 beside one at 2.0-2.4 s
+    # whose kept RIRs do not (its partitioned path: up to 5 parts of 8192 taps), full output
+    mics = synth.circular_array(8, 0.05)
+    a = synth.make_batch(SEED_LONG, [30 * synth.FS], [4], mics, (1.2, 1.4))
+    c = synth.make_batch(SEED_LONG + 1, [30 * synth.FS], [4], mics, (2.0, 2.4))
+    b = synth.Batch(8, np.concatenate([a.num_sources, c.num_sources]), np.concatenate([a.num_samples, c.num_samples]),
+                    np.concatenate([a.rir_len, c.rir_len]), np.concatenate([a.x, c.x]),
+                    np.concatenate([a.rir, c.rir]), np.concatenate([a.snr_db, c.snr_db]))
+    L = oracle.truncate_batch(b, 30.0)["L"]
+    reach = 3 * 16384 // 4 + 1
+    assert L[:32].max() <= reach < L[32:].max()
+    q = check_long(b, 30.0, output_mode=1, long_rirs=True)
+    np.testing.assert_array_equal(q["hop"], [(1 << int(q["log2_n"][0])) - q["l_max"][0] + 1, 8193])
