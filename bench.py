@@ -50,14 +50,18 @@ def _peaks():
 # ---------------------------------------------------------------------------
 # algorithmic work (the minimum the method does at the chosen FFT sizes)
 # ---------------------------------------------------------------------------
-def algorithmic_work(batch, q, L):
+def algorithmic_work(batch, q, L, cache=False):
     """FLOPs and HBM bytes of the forward and backward OLA kernels.
 
     A real N-point transform counts 2.5 N log2 N flops, a complex
     multiply-add 8.  Forward per block: I + J transforms and I*J spectrum
     products; bytes: x read once, y written once.  Backward per block:
     2I + J transforms and 2*I*J products, plus one inverse per RIR for dh;
-    bytes: grad_y and x read once, grad_x written once, dh written once."""
+    bytes: grad_y and x read once, grad_x written once, dh written once.
+    With the spectrum cache (N <= 8192) each source block is transformed once
+    for the whole step: the forward also writes its half spectrum (N/4 bin
+    pairs of 16 bytes) and the backward reads it in place of x and does
+    I + J transforms per block."""
     ff = fb = bf = bb = 0.0
     ff5 = bf5 = 0.0           # the same with 5 N log2 N per transform (complex-FFT count)
     J = batch.num_mics
@@ -70,12 +74,15 @@ def algorithmic_work(batch, q, L):
         B = int(q["num_blocks"][u])
         tr = 2.5 * N * m
         mac = 8.0 * (N / 2 + 1)
+        cached = cache and m <= 13
+        nbw = (I + J) if cached else (2 * I + J)             # backward transforms per block
+        spec = B * I * 4.0 * N if cached else 0.0            # bytes of the kept spectra
         ff += B * ((I + J) * tr + I * J * mac)
-        fb += 4.0 * (I + J) * nx
-        bf += B * ((2 * I + J) * tr + 2 * I * J * mac) + I * J * tr
-        bb += 4.0 * (J + 2 * I) * nx + 4.0 * float(np.sum(L[ri[u]:ri[u + 1]]))
+        fb += 4.0 * (I + J) * nx + spec
+        bf += B * (nbw * tr + 2 * I * J * mac) + I * J * tr
+        bb += 4.0 * (J + I) * nx + (spec if cached else 4.0 * I * nx) + 4.0 * float(np.sum(L[ri[u]:ri[u + 1]]))
         ff5 += B * ((I + J) * 2 * tr + I * J * mac)
-        bf5 += B * ((2 * I + J) * 2 * tr + 2 * I * J * mac) + I * J * 2 * tr
+        bf5 += B * (nbw * 2 * tr + 2 * I * J * mac) + I * J * 2 * tr
     return dict(fwd_flops=ff, fwd_bytes=fb, bwd_flops=bf, bwd_bytes=bb, fwd_flops_5n=ff5, bwd_flops_5n=bf5)
 
 
@@ -351,7 +358,8 @@ def run_ours(args):
 
     b = synth.config_home()
     audio_s = b.audio_seconds()
-    plan = Plan.for_batch(b, eta_db=ETA_DB, gain_mode=0, device=dev.index)
+    plan = Plan.for_batch(b, eta_db=ETA_DB, gain_mode=0, device=dev.index,
+                          spectrum_cache=not getattr(args, "no_spectrum_cache", False))
     x = torch.from_numpy(b.x).to(dev)
     rir = torch.from_numpy(b.rir).to(dev)
     snr = torch.from_numpy(b.snr_db).to(dev)
@@ -503,19 +511,21 @@ def run_ours(args):
     # ---- roofline of the dominant kernel (from the live stage events)
     q = plan.query()
     L = tl.cpu().numpy()
-    work = algorithmic_work(b, q, L)
+    work = algorithmic_work(b, q, L, cache=plan.spectrum_cache)
     hbm, sm_mhz_max, peak_kind = _peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     p_fp32 = sms * 128 * 2 * sm_mhz_max * 1e6 / 1e12
     per = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in stages.items()}
     kern = "backward" if per["backward"] >= per["forward"] else "forward"
-    kname = {"forward": "k_forward", "backward": "k_backward"}[kern]
+    kname = {"forward": "k_forward", "backward": "k_backward_tm"}[kern]
     src = {"forward": "rsim_forward.cu", "backward": "rsim_backward.cu"}[kern]
+    klabel = {"forward": "k_forward<M>",
+              "backward": "k_backward_tm<M> (N <= 8192) and k_backward<8192> (N = 16384)"}[kern]
     n_sizes = plan.num_fft_sizes          # one launch per allowed FFT size
     w = "fwd" if kern == "forward" else "bwd"
     roof = roofline_entry(work[f"{w}_flops"], work[f"{w}_bytes"], per[kern], p_fp32, hbm, peak_kind,
                           _traffic_for(kname))
-    roof.update({"kernel": f"{kname}<M> ({src}), all FFT-size launches of one step",
+    roof.update({"kernel": f"{klabel} ({src}), all FFT-size launches of one step",
                  "stage_ms": per[kern], "launches_per_step": n_sizes,
                  "algorithmic_flops_per_step": work[f"{w}_flops"],
                  "algorithmic_bytes_per_step": work[f"{w}_bytes"],
@@ -552,6 +562,7 @@ def run_ours(args):
                    "audio_seconds_per_step": audio_s * world,
                    "step": "forward (cut-off, gains, FFT-size plan, RIR spectra, OLA filter-and-mix, "
                            "fix-up) + backward (grad x, grad RIR, grad gains), replayed as CUDA graphs",
+                   "spectrum_cache": plan.spectrum_cache,
                    "l2": "inputs larger than L2 (x is %.0f MB, grad_y %.0f MB)"
                          % (x.numel() * 4 / 1e6, gy.numel() * 4 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single GPU",
@@ -1047,6 +1058,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-spectrum-cache", action="store_true",
+                    help="home workload: the backward transforms every source block again instead of "
+                         "reading the forward's spectra")
     ap.add_argument("--only-step", action="store_true",
                     help="time only the K steps (no forward-only, end-to-end, plain or CPU legs); "
                          "for profiler runs")

@@ -48,6 +48,7 @@ class PlanDesc(ctypes.Structure):
         ("snr_ref_mic", ctypes.c_int32),
         ("rooms", ctypes.c_int32),
         ("long_rirs", ctypes.c_int32),
+        ("spectrum_cache", ctypes.c_int32),
     ]
 
 

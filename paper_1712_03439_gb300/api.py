@@ -39,7 +39,8 @@ class Plan:
 
     def __init__(self, num_sources, num_samples, rir_len, num_mics, eta_db=20.0,
                  fft_sizes=None, gain_mode=0, segment_len=0, bwd_segment_len=0, fft_cost=None,
-                 device=None, graphs=True, output_mode=0, snr_ref_mic=0, rooms=False, long_rirs=False):
+                 device=None, graphs=True, output_mode=0, snr_ref_mic=0, rooms=False, long_rirs=False,
+                 spectrum_cache=True):
         self._lib = _lib.load()
         self._handle = None
         self.num_sources = np.ascontiguousarray(num_sources, dtype=np.int32)
@@ -49,6 +50,7 @@ class Plan:
         self.gain_mode = int(gain_mode)
         self.output_mode = int(output_mode)
         self.eta_db = float(eta_db)
+        self.spectrum_cache = bool(spectrum_cache)
         mask = 0
         for n in (fft_sizes or []):
             m = int(round(math.log2(n)))
@@ -75,7 +77,7 @@ class Plan:
                            gain_mode=self.gain_mode, segment_len=int(segment_len),
                            bwd_segment_len=int(bwd_segment_len), disable_graphs=0 if graphs else 1,
                            output_mode=self.output_mode, snr_ref_mic=int(snr_ref_mic), rooms=1 if rooms else 0,
-                           long_rirs=1 if long_rirs else 0)
+                           long_rirs=1 if long_rirs else 0, spectrum_cache=1 if spectrum_cache else 0)
         h = ctypes.c_void_p()
         _lib.check(self._lib, self._lib.rsim_plan(ctypes.byref(self._desc()), self.device, ctypes.byref(h)))
         self._handle = h

@@ -572,6 +572,8 @@ rsim_status plan_build(const rsim_plan_desc* d, int device, rsim_plan_t* out, rs
     if (d->segment_len < 0 || d->bwd_segment_len < 0)
         return fail(RSIM_E_INVALID, "segment_len and bwd_segment_len must be >= 0");
     if (d->long_rirs != 0 && d->long_rirs != 1) return fail(RSIM_E_INVALID, "long_rirs must be 0 or 1");
+    if (d->spectrum_cache != 0 && d->spectrum_cache != 1)
+        return fail(RSIM_E_INVALID, "spectrum_cache must be 0 or 1");
     // an utterance whose RIRs reach beyond one block of the largest allowed FFT size (hop >=
     // N/4: 3N/4 + 1 taps) gets a partitioned path, without a cut-off or when asked for
     int part_log = kMinLog;
@@ -684,6 +686,7 @@ rsim_status plan_build(const rsim_plan_desc* d, int device, rsim_plan_t* out, rs
     std::vector<Piece> pieces;
     void* p_kept = nullptr;
     void* p_lpre = nullptr;
+    void *p_xsoff = nullptr, *p_xspec = nullptr;
     void *p_sord, *p_spre, *p_nstream, *p_ctasp, *p_ctab, *p_ctap, *p_piecedh, *p_sfirst, *p_slast;
     void *p_srcutt, *p_rirutt;
     void *p_nsrc, *p_nx, *p_ny, *p_src0, *p_rir0, *p_seg0, *p_segutt, *p_xoff, *p_yoff, *p_roff, *p_rlen,
@@ -768,6 +771,22 @@ rsim_status plan_build(const rsim_plan_desc* d, int device, rsim_plan_t* out, rs
     pieces.push_back({&p_melrow, sizeof(int64_t) * (U + 1)});
     pieces.push_back({&p_ones, sizeof(float) * std::max<int64_t>(S, 1)});
     if (d->rooms) pieces.push_back({&p_kept, sizeof(float) * std::max<int64_t>(roff[R], 1)});
+    // the forward's source spectra for the backward (sizes up to 8192): block b of a source
+    // takes 4N bytes and there are at most ceil(4 Nx / N) blocks (hop >= N/4), so at most
+    // 16 Nx + 4N bytes per source whatever N the planner picks
+    int cache_log = 0;
+    for (int m = kMinLog; m <= std::min(kMaxLog, 13); ++m)
+        if ((mask >> m) & 1) cache_log = m;
+    const bool cache = d->spectrum_cache && cache_log > 0;
+    std::vector<int64_t> xs_off(S + 1, 0);
+    if (cache) {
+        for (int u = 0; u < U; ++u)
+            for (int s = src0[u]; s < src0[u + 1]; ++s)
+                xs_off[s + 1] = xs_off[s] + (int64_t)align_up((size_t)(16 * d->num_samples[u] + (4LL << cache_log)),
+                                                              256);
+        pieces.push_back({&p_xsoff, sizeof(int64_t) * (S + 1)});
+        pieces.push_back({&p_xspec, (size_t)std::max<int64_t>(xs_off[S], 256)});
+    }
     // gain_mode 3: each source's RIR to the reference microphone, gathered, and the
     // reverberant sources (laid out like x)
     std::vector<int64_t> rev_src(S), rev_dst(S + 1, 0);
@@ -850,6 +869,7 @@ rsim_status plan_build(const rsim_plan_desc* d, int device, rsim_plan_t* out, rs
         {p_tuning, tuning.data(), sizeof(float) * 32},
         {p_ones, ones.data(), sizeof(float) * ones.size()},
     };
+    if (cache) ups.push_back({p_xsoff, xs_off.data(), sizeof(int64_t) * (S + 1)});
     if (d->gain_mode == 3) {
         ups.push_back({p_rsrc, rev_src.data(), sizeof(int64_t) * S});
         ups.push_back({p_rdst, rev_dst.data(), sizeof(int64_t) * (S + 1)});
@@ -879,6 +899,9 @@ rsim_status plan_build(const rsim_plan_desc* d, int device, rsim_plan_t* out, rs
     B.cta_sp = (int32_t*)p_ctasp; B.cta_b = (int32_t*)p_ctab; B.cta_p = (int32_t*)p_ctap;
     B.piece_dh = (int64_t*)p_piecedh; B.s_first = (int32_t*)p_sfirst; B.s_last = (int32_t*)p_slast;
     B.lpre = (int64_t*)p_lpre;
+    B.xspec = (float4*)p_xspec;
+    B.xspec_off = (const int64_t*)p_xsoff;
+    B.xspec_bytes = cache ? xs_off[S] : 0;
     // the device planner computes gains from the source powers in modes 0 and 3 (in mode 3
     // the powers are those of the reverberant sources)
     B.gain_mode = d->gain_mode == 3 ? 0 : d->gain_mode;
@@ -985,6 +1008,7 @@ rsim_status plan_build(const rsim_plan_desc* d, int device, rsim_plan_t* out, rs
         rd.disable_graphs = 1;
         rd.snr_ref_mic = 0;
         rd.rooms = 0;
+        rd.spectrum_cache = 0;                   // no backward runs on it
         const rsim_status rs = rsim_plan(&rd, device, &p->rev);
         if (rs != RSIM_OK) {
             const std::string msg = "reverberant-SNR plan: " + g_err;
@@ -1013,7 +1037,7 @@ extern "C" rsim_status rsim_plan_reshape(rsim_plan_t p, const rsim_plan_desc* d)
     if (d->num_mics != f.num_mics || d->eta_db != f.eta_db || d->fft_sizes_mask != f.fft_sizes_mask ||
         d->gain_mode != f.gain_mode || d->output_mode != f.output_mode || d->snr_ref_mic != f.snr_ref_mic ||
         d->rooms != f.rooms || d->segment_len != f.segment_len || d->disable_graphs != f.disable_graphs ||
-        d->long_rirs != f.long_rirs)
+        d->long_rirs != f.long_rirs || d->spectrum_cache != f.spectrum_cache)
         return fail(RSIM_E_INVALID, "rsim_plan_reshape: only the batch shape may change (num_utts, "
                                     "num_sources, num_samples, rir_len, fft_cost)");
     DeviceGuard guard(p->device);

@@ -373,7 +373,9 @@ struct BwdTmCfg {
     static_assert(IG >= 1 && IG <= kMaxSources, "source group");
 };
 
-template <int M, bool MG>
+// CACHED: the forward kept every block's source spectrum (B.xspec), which source steps read
+// instead of transforming the block
+template <int M, bool MG, bool CACHED>
 __global__ void __launch_bounds__(BwdTmCfg<M>::T, BwdTmCfg<M>::kMinBlocks)
 k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const float* __restrict__ x,
               const float* __restrict__ gains, const float2* __restrict__ Hc, float* __restrict__ dx,
@@ -432,6 +434,9 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
         ph ^= 1u << b;
     };
     bool h_pending = false;                      // a spectrum copy was issued and not yet waited for
+    // the forward kept every block's source spectrum: a source step stages it instead of
+    // the block and needs no forward transform
+    constexpr bool cached = CACHED;
     bool stop = false;                           // a wait ran out: the remaining pieces are skipped
     for_each_piece(B, bucket, blockIdx.x, [&](int pc, int, int u, int i0, int64_t b0, int64_t b1) {
         if (stop) return;
@@ -456,6 +461,10 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
                 if (k < jn) {
                     src = gy + B.yoff[u] + (int64_t)(j0 + k) * ny + p;
                     len = min((int64_t)(hop + lmax - 1), ny - p);
+                } else if (cached) {             // the forward's spectrum of the block
+                    src = reinterpret_cast<const float*>(reinterpret_cast<const char*>(B.xspec) +
+                                                         B.xspec_off[sb + k - jn]) + b * 2 * M;
+                    len = 2 * M;
                 } else {
                     src = x + B.xoff[sb + k - jn] + p;
                     len = min((int64_t)hop, nx - p);
@@ -472,6 +481,25 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
                     else if (b + 1 < b1) stage_step(sc ^ 1, b + 1, 0);
                 }
                 sc ^= 1;
+            };
+            // when step k is a source step its RIR spectra move into hs, once the readers of
+            // hs are done: without the cache at the start of step k (the previous source
+            // step's spectral products passed the barriers of its inverse transform; the
+            // copy lands while this step's forward transform runs), with it as early as the
+            // previous step allows (after its spectral products and a barrier, or at the
+            // end of a microphone step)
+            auto stage_h = [&](int k) {
+                if constexpr (L::kStageH) {
+                    if (k < jn || k >= nsteps || bad) return;
+                    h_pending = true;
+                    if (t == 0) {
+                        fence_proxy_async_smem();
+                        mbar_arrive_expect_tx(&mbar[2], (uint32_t)(jn * M * sizeof(float2)));
+                        for (int jj = 0; jj < jn; ++jj)
+                            bulk_copy_g2s(hs + jj * M, Hc + (int64_t)(rb + (i0 + k - jn) * J + j0 + jj) * B.MMAX,
+                                          (uint32_t)(M * sizeof(float2)), &mbar[2]);
+                    }
+                }
             };
             // zero this group's accumulators (no other thread reads this thread's columns)
             {
@@ -494,25 +522,32 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
 #pragma unroll 1
                 for (int k = 0; k < nsteps; ++k) {
                     float2 v[E], Z[E];
-                    if constexpr (L::kStageH) {
-                        // a source step: its RIR spectra move into hs while its forward
-                        // transform runs (the previous source's readers of hs passed the
-                        // barriers of its inverse transform)
-                        if (k >= jn && !bad) h_pending = true;
-                        if (k >= jn && t == 0 && !bad) {
-                            fence_proxy_async_smem();
-                            mbar_arrive_expect_tx(&mbar[2], (uint32_t)(jn * M * sizeof(float2)));
-                            for (int jj = 0; jj < jn; ++jj)
-                                bulk_copy_g2s(hs + jj * M, Hc + (int64_t)(rb + (i0 + k - jn) * J + j0 + jj) * B.MMAX,
-                                              (uint32_t)(M * sizeof(float2)), &mbar[2]);
-                        }
+                    if constexpr (!cached) {
+                        if (k >= jn) stage_h(k);
                     }
-                    next_input(v, b, k);
-                    if constexpr (kPaired) {
-                        rfft_paired<M, E, false>(Z, v, ex, tw, t, kt);
+                    if (cached && k >= jn) {
+                        // X_i from the stage (pair layout: pair kb = (X[kb], X[M - kb]))
+                        wait_bar(sc);
+                        const float4* sp = reinterpret_cast<const float4*>(stage(sc));
+#pragma unroll
+                        for (int q = 0; q < E / 2; ++q) {
+                            const float4 e4 = sp[kt + q * T];
+                            Z[2 * q] = make_float2(e4.x, e4.y);
+                            Z[2 * q + 1] = make_float2(e4.z, e4.w);
+                        }
+                        if (!bad) {
+                            if (k + 1 < nsteps) stage_step(sc ^ 1, b, k + 1);
+                            else if (b + 1 < b1) stage_step(sc ^ 1, b + 1, 0);
+                        }
+                        sc ^= 1;
                     } else {
-                        const float2* z = rfft_x<M, E, false>(v, ex, tw, t);
-                        split_forward<M, E>(Z, z, wsplit, t);
+                        next_input(v, b, k);
+                        if constexpr (kPaired) {
+                            rfft_paired<M, E, false>(Z, v, ex, tw, t, kt);
+                        } else {
+                            const float2* z = rfft_x<M, E, false>(v, ex, tw, t);
+                            split_forward<M, E>(Z, z, wsplit, t);
+                        }
                     }
                     if (k < jn) {
                         if (k == 0) {
@@ -522,6 +557,7 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
 #pragma unroll
                             for (int e = 0; e < E; ++e) G[1][e] = Z[e];
                         }
+                        if (cached) stage_h(k + 1);
                         continue;
                     }
                     const int i = k - jn;        // source of the tile; Z holds X_i
@@ -578,6 +614,14 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
                                 C[2 * q] = cadd(C[2 * q], cmulc(ha, ga));
                             }
                             C[2 * q + 1] = cadd(C[2 * q + 1], cmulc(hb, gb));
+                        }
+                    }
+                    if constexpr (L::kStageH) {
+                        // every thread is done with hs: the next source's spectra may come
+                        // in while this step's inverse transform and stores run
+                        if (cached && k + 1 < nsteps) {
+                            __syncthreads();
+                            stage_h(k + 1);
                         }
                     }
                     // <c, x_block> by Parseval on the half spectra (x_block is zero
@@ -763,7 +807,8 @@ static void backward_m(const DevBatch& B, const Queues& Q, int bucket, const flo
                        const float* gains, const float2* Hc, float* dx, float* dhp, float* dap,
                        Twiddles tw, int grid, cudaStream_t st) {
     if constexpr (M <= 4096) {
-        auto kern = B.J > kJG ? k_backward_tm<M, true> : k_backward_tm<M, false>;
+        auto kern = B.xspec ? (B.J > kJG ? k_backward_tm<M, true, true> : k_backward_tm<M, false, true>)
+                            : (B.J > kJG ? k_backward_tm<M, true, false> : k_backward_tm<M, false, false>);
         kern<<<grid, BwdTmCfg<M>::T, smem_backward_tm<M>(), st>>>(B, Q, bucket, g, x, gains, Hc, dx, dhp,
                                                                   dap, tw.get(BwdTmCfg<M>::E));
     } else {
@@ -823,10 +868,13 @@ static int occ_bb() {
 // (a CTA beyond that would wait in its allocation until another one exits)
 template <int M>
 static int occ_tm() {
-    const int a = occ_b(k_backward_tm<M, false>, BwdTmCfg<M>::T, smem_backward_tm<M>());
-    const int b = occ_b(k_backward_tm<M, true>, BwdTmCfg<M>::T, smem_backward_tm<M>());
-    const int c = 512 / BwdTmCfg<M>::kCols;
-    return a < b ? (a < c ? a : c) : (b < c ? b : c);
+    int n = 512 / BwdTmCfg<M>::kCols;
+    const int o[4] = {occ_b(k_backward_tm<M, false, false>, BwdTmCfg<M>::T, smem_backward_tm<M>()),
+                      occ_b(k_backward_tm<M, true, false>, BwdTmCfg<M>::T, smem_backward_tm<M>()),
+                      occ_b(k_backward_tm<M, false, true>, BwdTmCfg<M>::T, smem_backward_tm<M>()),
+                      occ_b(k_backward_tm<M, true, true>, BwdTmCfg<M>::T, smem_backward_tm<M>())};
+    for (int k = 0; k < 4; ++k) n = o[k] < n ? o[k] : n;
+    return n;
 }
 
 int occupancy_backward(int logN) {

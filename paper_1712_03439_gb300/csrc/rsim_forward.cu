@@ -188,11 +188,22 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
                     __syncthreads();
                     const float a = __ldg(gains + sb + i);
                     const float2* H0 = Hc + (int64_t)(rb + i * J + j0) * B.MMAX;
+                    // the block's spectrum, kept for the backward (first microphone group)
+                    float4* xsp = nullptr;
+                    if constexpr (M <= 4096) {
+                        if (B.xspec && j0 == 0)
+                            xsp = reinterpret_cast<float4*>(reinterpret_cast<char*>(B.xspec) + B.xspec_off[sb + i]) +
+                                  b * (M / 2);
+                    }
 #pragma unroll
                     for (int q = 0; q < E / 2; ++q) {
                         const int k = t + q * T;
                         float2 xa, xb;
                         split_pair<M>(sm, wsplit, k, xa, xb);
+                        // streaming store: read once, by the backward, so it should not evict
+                        // the RIR spectra this kernel keeps re-reading from L2
+                        if (xsp && RSIM_STORE_OK(B, xsp + k, B.xspec, B.xspec_bytes))
+                            __stcs(xsp + k, make_float4(xa.x, xa.y, xb.x, xb.y));
                         xa = cscale(xa, a);
                         xb = cscale(xb, a);
 #pragma unroll

@@ -89,6 +89,12 @@ struct DevBatch {
     uint8_t* defer;             // [utterances of that plan] 1: the planner sent the utterance there
     const uint8_t* active;      // in the partitioned plan: [U] 0 = the outer planner kept the
                                 // utterance (no work here); NULL: every utterance is active
+    // source half spectra of every block, written by the forward for the backward (N <= 8192)
+    float4* xspec;              // NULL: no cache.  Block b of source s: M/2 bin pairs from
+                                // (char*)xspec + xspec_off[s] + b * M/2 * 16 bytes, pair k
+                                // = (X[k], X[M - k]) (k = 0: (X[0], X[M]) packed, X[M/2])
+    const int64_t* xspec_off;   // [S + 1] byte offset of each source's slots
+    int64_t xspec_bytes;
 };
 
 struct Queues {

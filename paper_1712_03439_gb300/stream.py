@@ -142,8 +142,10 @@ class Streamer:
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.keep = keep_outputs
         self.class_plan = bool(class_plan)   # one shape-class plan, re-planned per batch
-        # one call per plan: launch eagerly rather than capture a graph that is never replayed
-        self.plan_kw = dict(graphs=False, **plan_kw)
+        # one call per plan: launch eagerly rather than capture a graph that is never replayed;
+        # no spectrum cache: its memory (up to 16 bytes per source sample) would shrink the
+        # batches the budget admits, and a batch here is small next to the copies around it
+        self.plan_kw = dict(dict(graphs=False, spectrum_cache=False), **plan_kw)
         self._pin = {}
 
     def _staging(self, name, n, dtype):

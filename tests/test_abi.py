@@ -43,7 +43,7 @@ def _desc(**kw):
                       segment_len=kw.pop("seg", 0), bwd_segment_len=kw.pop("bseg", 0),
                       fft_cost=None, disable_graphs=0, output_mode=kw.pop("om", 0),
                       snr_ref_mic=kw.pop("ref", 0), rooms=kw.pop("rooms", 0),
-                      long_rirs=kw.pop("long", 0))
+                      long_rirs=kw.pop("long", 0), spectrum_cache=kw.pop("cache", 0))
     return d, (ns, nx, rl)
 
 
@@ -72,6 +72,7 @@ def _desc(**kw):
     (dict(rooms=1, long=1, rl=[20000]), 2),
     (dict(long=2), 1),
     (dict(long=-1), 1),
+    (dict(cache=2), 1),
 ])
 def test_plan_rejects_bad_descriptions_on_the_host(lib, kw, status):
     d, keep = _desc(**kw)
