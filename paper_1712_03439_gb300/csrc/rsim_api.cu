@@ -943,7 +943,8 @@ rsim_status plan_build(const rsim_plan_desc* d, int device, rsim_plan_t* out, rs
         p->grid_bwd[b] = grid_bwd[b];
     }
     p->grid_trunc = (int)std::max<int64_t>(1, std::min<int64_t>(R, (int64_t)p->sms * 8));
-    p->grid_pow = (int)std::max<int64_t>(1, std::min<int64_t>(S * CH, (int64_t)p->sms * 8));
+    // one CTA per chunk (the scheduler balances them; chunks past an utterance's end exit)
+    p->grid_pow = (int)std::max<int64_t>(1, std::min<int64_t>(S * CH, (int64_t)1 << 20));
     p->use_graphs = d->disable_graphs == 0;
     p->desc_fixed = *d;
     p->desc_fixed.num_utts = 0;

@@ -71,7 +71,7 @@ k_power(DevBatch B, const float* __restrict__ x) {
         for (int64_t i = t; i < head; i += kPowThreads) acc(0, __ldg(p + i));
         for (int64_t i = tail0 + t; i < len; i += kPowThreads) acc(1, __ldg(p + i));
         const float4* p4 = reinterpret_cast<const float4*>(p + head);
-        constexpr int kU = 4;                    // float4 loads in flight per thread
+        constexpr int kU = 8;                    // float4 loads in flight per thread
         int64_t j = t;
         for (; j + (kU - 1) * kPowThreads < nvec; j += kU * kPowThreads) {
             float4 a[kU];
@@ -139,7 +139,10 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
                     atomicOr(B.err, kErrZeroPower);
                     gains[s0 + i] = 0.f;
                 } else {
-                    gains[s0 + i] = (float)sqrt(P0 / Pi * pow(10.0, -(double)snr_db[s0 + i] / 10.0));
+                    // the power ratio in FP64, 10^(-SNR/10) and the root in FP32: an FP64
+                    // pow per source would take most of this kernel (FP64 is slow here),
+                    // and FP32 keeps alpha within a few 1e-7 relative
+                    gains[s0 + i] = sqrtf((float)(P0 / Pi) * exp10f(-snr_db[s0 + i] / 10.f));
                 }
             }
         }
