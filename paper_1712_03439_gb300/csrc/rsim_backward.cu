@@ -517,51 +517,9 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
             for (int64_t b = b0; b < b1; ++b) {
                 const int64_t pos = b * hop;
                 float2 G[kJG][E];
-                // one loop body for every transform of the block (the transform code
-                // is emitted once)
-#pragma unroll 1
-                for (int k = 0; k < nsteps; ++k) {
-                    float2 v[E], Z[E];
-                    if constexpr (!cached) {
-                        if (k >= jn) stage_h(k);
-                    }
-                    if (cached && k >= jn) {
-                        // X_i from the stage (pair layout: pair kb = (X[kb], X[M - kb]))
-                        wait_bar(sc);
-                        const float4* sp = reinterpret_cast<const float4*>(stage(sc));
-#pragma unroll
-                        for (int q = 0; q < E / 2; ++q) {
-                            const float4 e4 = sp[kt + q * T];
-                            Z[2 * q] = make_float2(e4.x, e4.y);
-                            Z[2 * q + 1] = make_float2(e4.z, e4.w);
-                        }
-                        if (!bad) {
-                            if (k + 1 < nsteps) stage_step(sc ^ 1, b, k + 1);
-                            else if (b + 1 < b1) stage_step(sc ^ 1, b + 1, 0);
-                        }
-                        sc ^= 1;
-                    } else {
-                        next_input(v, b, k);
-                        if constexpr (kPaired) {
-                            rfft_paired<M, E, false>(Z, v, ex, tw, t, kt);
-                        } else {
-                            const float2* z = rfft_x<M, E, false>(v, ex, tw, t);
-                            split_forward<M, E>(Z, z, wsplit, t);
-                        }
-                    }
-                    if (k < jn) {
-                        if (k == 0) {
-#pragma unroll
-                            for (int e = 0; e < E; ++e) G[0][e] = Z[e];
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < E; ++e) G[1][e] = Z[e];
-                        }
-                        if (cached) stage_h(k + 1);
-                        continue;
-                    }
-                    const int i = k - jn;        // source of the tile; Z holds X_i
-                    // W_ij += conj(X_i) G_j
+                // a source step's work before its inverse transform: W_ij += conj(X_i) G_j
+                // (TMEM), C = sum_j conj(H_ij) G_j, and <c, x_block> by Parseval
+                auto src_pre = [&](int k, int i, const float2 (&Z)[E], float2 (&C)[E]) {
 #pragma unroll 1
                     for (int jj = 0; jj < jn; ++jj) {
                         float2 Wv[E];
@@ -580,8 +538,6 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
                         }
                         tmem_store<E>(wslot(i * kJG + jj), Wv);
                     }
-                    // C = sum_j conj(H_ij) G_j
-                    float2 C[E];
 #pragma unroll
                     for (int e = 0; e < E; ++e) C[e] = make_float2(0.f, 0.f);
                     if constexpr (L::kStageH) {
@@ -636,32 +592,118 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
                     }
 #pragma unroll
                     for (int q = 0; q < IG; ++q) da[q] += (q == i) ? p : 0.f;
-                    if constexpr (kPaired) irfft_paired<M, E>(v, C, ex, tw, t, kt);
-                    else irfft_x<M, E, false>(v, C, ex, tw, t);
-                    if (dx) {
-                        // samples [0, min(hop, Nx - pos)) of the block; the first microphone
-                        // group writes, later groups add; pairs go out as one 8-byte store
-                        const float a = __ldg(gains + sb + i);
-                        float* dst = dx + B.xoff[sb + i] + pos;
-                        const int ilim = (int)min((int64_t)hop, nx - pos);
-                        const bool pairs = ((reinterpret_cast<uintptr_t>(dst) & 7) == 0) && j0 == 0;
+                };
+                // dx = alpha c on samples [0, min(hop, Nx - pos)) of the block; the first
+                // microphone group writes, later groups add; pairs go out as one 8-byte store
+                auto dx_store = [&](int i, const float2 (&v)[E]) {
+                    if (!dx) return;
+                    const float a = __ldg(gains + sb + i);
+                    float* dst = dx + B.xoff[sb + i] + pos;
+                    const int ilim = (int)min((int64_t)hop, nx - pos);
+                    const bool pairs = ((reinterpret_cast<uintptr_t>(dst) & 7) == 0) && j0 == 0;
 #pragma unroll
-                        for (int q = 0; q < E; ++q) {
-                            const int n = 2 * (t + q * T);
-                            const float d0 = a * v[q].x, d1 = a * v[q].y;
-                            if (pairs && n + 1 < ilim) {
-                                if (RSIM_STORE_OK(B, dst + n + 1, dx, RSIM_X_BYTES(B)))
-                                    *reinterpret_cast<float2*>(dst + n) = make_float2(d0, d1);
-                            } else if constexpr (MG) {
-                                if (n < ilim && RSIM_STORE_OK(B, dst + n, dx, RSIM_X_BYTES(B)))
-                                    dst[n] = (j0 == 0) ? d0 : dst[n] + d0;
-                                if (n + 1 < ilim && RSIM_STORE_OK(B, dst + n + 1, dx, RSIM_X_BYTES(B)))
-                                    dst[n + 1] = (j0 == 0) ? d1 : dst[n + 1] + d1;
+                    for (int q = 0; q < E; ++q) {
+                        const int n = 2 * (t + q * T);
+                        const float d0 = a * v[q].x, d1 = a * v[q].y;
+                        if (pairs && n + 1 < ilim) {
+                            if (RSIM_STORE_OK(B, dst + n + 1, dx, RSIM_X_BYTES(B)))
+                                *reinterpret_cast<float2*>(dst + n) = make_float2(d0, d1);
+                        } else if constexpr (MG) {
+                            if (n < ilim && RSIM_STORE_OK(B, dst + n, dx, RSIM_X_BYTES(B)))
+                                dst[n] = (j0 == 0) ? d0 : dst[n] + d0;
+                            if (n + 1 < ilim && RSIM_STORE_OK(B, dst + n + 1, dx, RSIM_X_BYTES(B)))
+                                dst[n + 1] = (j0 == 0) ? d1 : dst[n + 1] + d1;
+                        } else {
+                            if (n < ilim && RSIM_STORE_OK(B, dst + n, dx, RSIM_X_BYTES(B))) dst[n] = d0;
+                            if (n + 1 < ilim && RSIM_STORE_OK(B, dst + n + 1, dx, RSIM_X_BYTES(B))) dst[n + 1] = d1;
+                        }
+                    }
+                };
+                auto keep_g = [&](int k, const float2 (&Z)[E]) {
+                    if (k == 0) {
+#pragma unroll
+                        for (int e = 0; e < E; ++e) G[0][e] = Z[e];
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < E; ++e) G[1][e] = Z[e];
+                    }
+                };
+                // X_i of a source step from the stage (pair kb = (X[kb], X[M - kb]))
+                auto take_x = [&](float2 (&Z)[E], int k) {
+                    wait_bar(sc);
+                    const float4* sp = reinterpret_cast<const float4*>(stage(sc));
+#pragma unroll
+                    for (int q = 0; q < E / 2; ++q) {
+                        const float4 e4 = sp[kt + q * T];
+                        Z[2 * q] = make_float2(e4.x, e4.y);
+                        Z[2 * q + 1] = make_float2(e4.z, e4.w);
+                    }
+                    if (!bad) {
+                        if (k + 1 < nsteps) stage_step(sc ^ 1, b, k + 1);
+                        else if (b + 1 < b1) stage_step(sc ^ 1, b + 1, 0);
+                    }
+                    sc ^= 1;
+                };
+                if constexpr (cached && kPaired) {
+                    // one transform per step, at one place: a microphone step's forward
+                    // (passes from butterfly t to butterfly kt, then the real split), a source
+                    // step's inverse (the unsplit of C, passes from kt to t, conjugate) --
+                    // the pass code is emitted once
+#pragma unroll 1
+                    for (int k = 0; k < nsteps; ++k) {
+                        const bool src = k >= jn;
+                        float2 v[E];
+                        if (src) {
+                            float2 Z[E], C[E];
+                            take_x(Z, k);
+                            src_pre(k, k - jn, Z, C);
+                            paired_unsplit<M, E>(v, C, tw, kt);
+                        } else {
+                            next_input(v, b, k);
+                        }
+                        fft_passes_sel<M, E, 0, 2>(v, ex, tw, t, src ? kt : t, src ? t : kt);
+                        if (!src) {
+                            float2 Z[E];
+                            paired_split<M, E>(Z, v, tw, kt);
+                            keep_g(k, Z);
+                            stage_h(k + 1);
+                            continue;
+                        }
+#pragma unroll
+                        for (int e = 0; e < E; ++e) v[e] = conjf2(v[e]);
+                        dx_store(k - jn, v);
+                    }
+                } else {
+                    // one loop body for every step of the block (the transform code is
+                    // emitted once per kind)
+#pragma unroll 1
+                    for (int k = 0; k < nsteps; ++k) {
+                        float2 v[E], Z[E];
+                        if constexpr (!cached) {
+                            if (k >= jn) stage_h(k);
+                        }
+                        if (cached && k >= jn) {
+                            take_x(Z, k);
+                        } else {
+                            next_input(v, b, k);
+                            if constexpr (kPaired) {
+                                rfft_paired<M, E, false>(Z, v, ex, tw, t, kt);
                             } else {
-                                if (n < ilim && RSIM_STORE_OK(B, dst + n, dx, RSIM_X_BYTES(B))) dst[n] = d0;
-                                if (n + 1 < ilim && RSIM_STORE_OK(B, dst + n + 1, dx, RSIM_X_BYTES(B))) dst[n + 1] = d1;
+                                const float2* z = rfft_x<M, E, false>(v, ex, tw, t);
+                                split_forward<M, E>(Z, z, wsplit, t);
                             }
                         }
+                        if (k < jn) {
+                            keep_g(k, Z);
+                            if (cached) stage_h(k + 1);
+                            continue;
+                        }
+                        const int i = k - jn;        // source of the tile; Z holds X_i
+                        float2 C[E];
+                        src_pre(k, i, Z, C);
+                        if constexpr (kPaired) irfft_paired<M, E>(v, C, ex, tw, t, kt);
+                        else irfft_x<M, E, false>(v, C, ex, tw, t);
+                        dx_store(i, v);
                     }
                 }
             }

@@ -754,12 +754,10 @@ __device__ __forceinline__ void paired_split_pair(const float2 (&v)[E], const fl
     xb = conjf2(csub(Ev, wO));
 }
 
-// Forward real FFT of strided registers v into paired layout P.
-template <int M, int E, bool WAIT, int NB>
-__device__ __forceinline__ void rfft_paired(float2 (&P)[E], float2 (&v)[E], Exch<NB>& ex,
-                                            const float2* __restrict__ tw, int t, int i) {
-    static_assert(PairedSplit<M, E>::ok, "paired split needs M = E^k");
-    fft_from_paired<M, E, 0, WAIT, NB>(v, ex, tw, t, i);
+// The real split after the forward passes: paired layout P from v.
+template <int M, int E>
+__device__ __forceinline__ void paired_split(float2 (&P)[E], const float2 (&v)[E], const float2* __restrict__ tw,
+                                             int i) {
     const float2* wsplit = tw + FftPlan<M, E>::OFF_SPLIT;
     float2 pw[E / 2];
     paired_swap<E>(pw, v);
@@ -767,12 +765,46 @@ __device__ __forceinline__ void rfft_paired(float2 (&P)[E], float2 (&v)[E], Exch
     for (int m = 0; m < E / 2; ++m) paired_split_pair<M, E>(v, pw, wsplit, i, m, P[2 * m], P[2 * m + 1]);
 }
 
+// Forward real FFT of strided registers v into paired layout P.
+template <int M, int E, bool WAIT, int NB>
+__device__ __forceinline__ void rfft_paired(float2 (&P)[E], float2 (&v)[E], Exch<NB>& ex,
+                                            const float2* __restrict__ tw, int t, int i) {
+    static_assert(PairedSplit<M, E>::ok, "paired split needs M = E^k");
+    fft_from_paired<M, E, 0, WAIT, NB>(v, ex, tw, t, i);
+    paired_split<M, E>(P, v, tw, i);
+}
+
+// Passes P .. NPASS-1 of the complex FFT of strided registers, pass 0 running
+// butterfly `first`, the last pass (and the exchange before it) butterfly
+// `last` and every other pass t: (t, i) is the forward of the paired layout
+// (as fft_from_paired), (i, t) the passes of the inverse (as irfft_paired) --
+// one code path for both where a kernel alternates between them.
+template <int M, int E, int P, int NB>
+__device__ __forceinline__ void fft_passes_sel(float2 (&v)[E], Exch<NB>& ex, const float2* __restrict__ tw, int t,
+                                               int first, int last) {
+    using Pl = FftPlan<M, E>;
+    constexpr int R = Pl::radix(P), LP = Pl::lp(P);
+    static_assert(Pl::NPASS >= 2, "a first and a last pass");
+    if constexpr (P == Pl::NPASS - 1) {
+        fft_pass<M, E, R, LP, true>(v, nullptr, tw + Pl::tw_off(P), last);
+    } else {
+        float2* b = ex.begin();
+        fft_pass<M, E, R, LP, false>(v, b, tw + Pl::tw_off(P), P == 0 ? first : t);
+        constexpr bool kLastExchange = P + 1 == Pl::NPASS - 1;
+        __syncthreads();
+        load_strided<M, E>(v, b, kLastExchange ? last : t);
+        ex.end();
+        fft_passes_sel<M, E, P + 1, NB>(v, ex, tw, t, first, last);
+    }
+}
+
 // Unnormalised inverse real FFT of a half spectrum in paired layout; on
 // return v[s] holds (y[2n], y[2n+1]) * 2M for n = t + s*T (as irfft_pairs).
-template <int M, int E, int NB>
-__device__ __forceinline__ void irfft_paired(float2 (&v)[E], const float2 (&P)[E], Exch<NB>& ex,
-                                             const float2* __restrict__ tw, int t, int i) {
-    static_assert(PairedSplit<M, E>::ok, "paired split needs M = E^k");
+// The inverse's preparation of a half spectrum P in paired layout: on return v
+// holds what the inverse's passes (pass 0 running butterfly i) transform.
+template <int M, int E>
+__device__ __forceinline__ void paired_unsplit(float2 (&v)[E], const float2 (&P)[E], const float2* __restrict__ tw,
+                                               int i) {
     constexpr int T = M / E;
     using Pl = FftPlan<M, E>;
     const float2* wsplit = tw + Pl::OFF_SPLIT;
@@ -809,6 +841,14 @@ __device__ __forceinline__ void irfft_paired(float2 (&v)[E], const float2 (&P)[E
 #pragma unroll
         for (int m = 0; m < E / 2; ++m) v[E - 1 - m] = got[m];
     }
+}
+
+template <int M, int E, int NB>
+__device__ __forceinline__ void irfft_paired(float2 (&v)[E], const float2 (&P)[E], Exch<NB>& ex,
+                                             const float2* __restrict__ tw, int t, int i) {
+    static_assert(PairedSplit<M, E>::ok, "paired split needs M = E^k");
+    using Pl = FftPlan<M, E>;
+    paired_unsplit<M, E>(v, P, tw, i);
     {
         float2* b = ex.begin();
         fft_pass<M, E, Pl::radix(0), 1, false>(v, b, tw, i);
