@@ -1126,9 +1126,10 @@ cudaError_t enqueue_forward(rsim_plan_t p, cudaStream_t st, const float* x, cons
     // per-(i, j) gains fold into the RIR spectra; the kernels then see unit source gains
     const float* rir_gain = p->gain_mode == 2 ? gains : nullptr;
     const float* src_gains = p->gain_mode == 2 ? p->ones : gains;
+    bool gains_aside = false;                    // the gains come from the side stream (ev_aux)
     if (p->gain_mode == 3) {
         // reverberant sources at the reference microphone (the auxiliary plan, unit gains),
-        // then their powers; the planner turns them into gains as for the dry signals
+        // then their powers, turned into gains as for the dry signals
         k_gather_rirs<<<(unsigned)std::min<int64_t>(std::max<int64_t>(B.S, 1), 4096), 256, 0, st>>>(
             B.S, p->rev_src_off, p->rev_dst_off, rir, p->rev_rir);
         cudaError_t e = enqueue_forward(p->rev, st, x, p->rev_rir, nullptr, p->ones, p->rev_y, nullptr, nullptr);
@@ -1138,15 +1139,19 @@ cudaError_t enqueue_forward(rsim_plan_t p, cudaStream_t st, const float* x, cons
         stage_mark(p, 0, true, st);
         stage_mark(p, 1, false, st);
         launch_power(B, p->rev_y, p->grid_pow, st);
+        launch_gains(B, snr_db, gains, st);
         stage_mark(p, 1, true, st);
     } else if (p->gain_mode == 0 && !p->timer.on) {
-        // source powers (reads x) run beside the RIR scan (reads rir)
+        // source powers (reads x) and the gains run beside the RIR scan (reads rir), the
+        // planner and the RIR spectra, which need only the cut-off; each size's forward
+        // waits for the gains (ev_aux) after its spectra
         cudaEventRecord(p->ev_fork, st);
         cudaStreamWaitEvent(p->aux, p->ev_fork, 0);
         launch_power(B, x, p->grid_pow, p->aux);
+        launch_gains(B, snr_db, gains, p->aux);
         cudaEventRecord(p->ev_aux, p->aux);
         cut(st);
-        cudaStreamWaitEvent(st, p->ev_aux, 0);
+        gains_aside = true;
     } else {
         stage_mark(p, 0, false, st);
         cut(st);
@@ -1154,17 +1159,19 @@ cudaError_t enqueue_forward(rsim_plan_t p, cudaStream_t st, const float* x, cons
         if (p->gain_mode == 0) {
             stage_mark(p, 1, false, st);
             launch_power(B, x, p->grid_pow, st);
+            launch_gains(B, snr_db, gains, st);
             stage_mark(p, 1, true, st);
         }
     }
     stage_mark(p, 2, false, st);
-    launch_plan(B, p->Q, snr_db, gains, st);
+    launch_plan(B, p->Q, st);
     stage_mark(p, 2, true, st);
     if (!p->timer.on) {
         // each FFT size's spectra then its OLA pass on that size's stream: a size's
         // forward waits only for its own spectra
         fan_out(p, st, [&](int m, cudaStream_t s) {
             launch_spectrum(m, B, p->Q, rir, rir_gain, p->Hc, p->tw[m - kMinLog], p->grid_spec[m - kMinLog], s);
+            if (gains_aside) cudaStreamWaitEvent(s, p->ev_aux, 0);
             launch_forward(m, B, p->Q, x, src_gains, p->Hc, y, p->tails, p->tw[m - kMinLog],
                            p->grid_fwd[m - kMinLog], s);
         });

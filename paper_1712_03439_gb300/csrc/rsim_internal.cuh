@@ -297,8 +297,8 @@ __device__ __forceinline__ bool store_ok(const DevBatch& B, const void* p, const
 void launch_truncate(const DevBatch& B, const float* rir, double factor, int none,
                      float* energy_kept_frac, int grid, cudaStream_t st);
 void launch_power(const DevBatch& B, const float* x, int grid, cudaStream_t st);
-void launch_plan(const DevBatch& B, const Queues& Q, const float* snr_db, float* gains,
-                 cudaStream_t st);
+void launch_gains(const DevBatch& B, const float* snr_db, float* gains, cudaStream_t st);
+void launch_plan(const DevBatch& B, const Queues& Q, cudaStream_t st);
 // Twiddle tables of one FFT size for 8 and 16 values per thread; every
 // tiled kernel picks the table of its own thread shape.
 struct Twiddles {

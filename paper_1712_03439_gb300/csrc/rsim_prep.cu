@@ -99,9 +99,47 @@ void launch_power(const DevBatch& B, const float* x, int grid, cudaStream_t st) 
 }
 
 // ---------------------------------------------------------------------------
+// K2a: gains from the source powers (gain modes 0 and 3): alpha_0 = 1,
+// alpha_i = sqrt(P_0 / P_i 10^(-SNR_i/10)), P the mean square over [0, Nx).
+// Apart from the planner: it needs the power scan, the planner only the cut-off,
+// so the planner and the RIR spectra need not wait for the scan.
+// ---------------------------------------------------------------------------
+__global__ void k_gains(DevBatch B, const float* __restrict__ snr_db, float* __restrict__ gains) {
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < B.U; u += gridDim.x * blockDim.x) {
+        const int s0 = B.src0[u], I = B.n_src[u];
+        const double nx = (double)B.n_x[u];
+        // chunks past this utterance's end are never written: sum only
+        // the ones that exist
+        const int nch = (int)((B.n_x[u] + kPowerChunk - 1) / kPowerChunk);
+        double P0 = 0.0;
+        for (int c = 0; c < nch; ++c) P0 += B.pow_part[(int64_t)s0 * B.CH + c];
+        P0 /= nx;
+        gains[s0] = 1.f;
+        for (int i = 1; i < I; ++i) {
+            double Pi = 0.0;
+            for (int c = 0; c < nch; ++c) Pi += B.pow_part[(int64_t)(s0 + i) * B.CH + c];
+            Pi /= nx;
+            if (!(Pi > 0.0)) {
+                atomicOr(B.err, kErrZeroPower);
+                gains[s0 + i] = 0.f;
+            } else {
+                // the power ratio in FP64, 10^(-SNR/10) and the root in FP32 (an FP64 pow
+                // per source is slow on this GPU's FP64 pipe; FP32 keeps alpha within a
+                // few 1e-7 relative)
+                gains[s0 + i] = sqrtf((float)(P0 / Pi) * exp10f(-snr_db[s0 + i] / 10.f));
+            }
+        }
+    }
+}
+
+void launch_gains(const DevBatch& B, const float* snr_db, float* gains, cudaStream_t st) {
+    k_gains<<<(B.U + 127) / 128, 128, 0, st>>>(B, snr_db, gains);
+}
+
+// ---------------------------------------------------------------------------
 // K2: planner (one CTA)
 // ---------------------------------------------------------------------------
-// Per utterance: gains from SNRs, L_max over its RIRs, and the FFT size N.
+// Per utterance: L_max over its RIRs and the FFT size N.
 // N minimises the cost of Eq. 6 (ceiling block count, one hop shared by all
 // (i, j) of the utterance: hop = N - L_max + 1) weighted by the per-size cost
 // table; N must leave hop >= N/4 (a block's tail may then reach several
@@ -115,38 +153,10 @@ constexpr float kConsolidateSlack = 0.02f;  // ...and moves if that adds at most
 
 
 __global__ void __launch_bounds__(kPlanThreads)
-k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict__ gains) {
+k_plan(DevBatch B, Queues Q) {
     __shared__ int sm[33];
     __shared__ long long pw_scratch[32];
     const int t = threadIdx.x;
-    // ---- gains (alpha_0 = 1, alpha_i = sqrt(P_0 / P_i 10^(-SNR_i/10)))
-    if (B.gain_mode == 0) {
-        for (int u = t; u < B.U; u += kPlanThreads) {
-            const int s0 = B.src0[u], I = B.n_src[u];
-            const double nx = (double)B.n_x[u];
-            // chunks past this utterance's end are never written: sum only
-            // the ones that exist
-            const int nch = (int)((B.n_x[u] + kPowerChunk - 1) / kPowerChunk);
-            double P0 = 0.0;
-            for (int c = 0; c < nch; ++c) P0 += B.pow_part[(int64_t)s0 * B.CH + c];
-            P0 /= nx;
-            gains[s0] = 1.f;
-            for (int i = 1; i < I; ++i) {
-                double Pi = 0.0;
-                for (int c = 0; c < nch; ++c) Pi += B.pow_part[(int64_t)(s0 + i) * B.CH + c];
-                Pi /= nx;
-                if (!(Pi > 0.0)) {
-                    atomicOr(B.err, kErrZeroPower);
-                    gains[s0 + i] = 0.f;
-                } else {
-                    // the power ratio in FP64, 10^(-SNR/10) and the root in FP32: an FP64
-                    // pow per source would take most of this kernel (FP64 is slow here),
-                    // and FP32 keeps alpha within a few 1e-7 relative
-                    gains[s0 + i] = sqrtf((float)(P0 / Pi) * exp10f(-snr_db[s0 + i] / 10.f));
-                }
-            }
-        }
-    }
     // ---- FFT size per utterance.  Every thread also tallies, per chosen size m,
     // the predicted work and, per other size d, how much dearer its utterances
     // would be at d (or that some cannot use d) -- for the consolidation below.
@@ -571,9 +581,8 @@ k_plan(DevBatch B, Queues Q, const float* __restrict__ snr_db, float* __restrict
     }
 }
 
-void launch_plan(const DevBatch& B, const Queues& Q, const float* snr_db, float* gains,
-                 cudaStream_t st) {
-    k_plan<<<1, kPlanThreads, 0, st>>>(B, Q, snr_db, gains);
+void launch_plan(const DevBatch& B, const Queues& Q, cudaStream_t st) {
+    k_plan<<<1, kPlanThreads, 0, st>>>(B, Q);
 }
 
 }  // namespace rsim
