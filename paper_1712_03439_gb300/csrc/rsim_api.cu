@@ -942,7 +942,8 @@ rsim_status plan_build(const rsim_plan_desc* d, int device, rsim_plan_t* out, rs
         p->grid_fwd[b] = grid_fwd[b];
         p->grid_bwd[b] = grid_bwd[b];
     }
-    p->grid_trunc = (int)std::max<int64_t>(1, std::min<int64_t>(R, (int64_t)p->sms * 8));
+    // one CTA per RIR (the scheduler balances their uneven lengths)
+    p->grid_trunc = (int)std::max<int64_t>(1, std::min<int64_t>(R, (int64_t)1 << 20));
     // one CTA per chunk (the scheduler balances them; chunks past an utterance's end exit)
     p->grid_pow = (int)std::max<int64_t>(1, std::min<int64_t>(S * CH, (int64_t)1 << 20));
     p->use_graphs = d->disable_graphs == 0;

@@ -221,34 +221,75 @@ struct CutScratch {
     double d[32];
 };
 
-template <typename Tap>
+// Eq. 7-9 for one RIR of n taps read through tap(i), by the CTA: L, and the kept
+// energy fraction if asked (in thread 0's *frac).  With KPER > 0 and n <= KPER * blockDim.x every thread
+// reads its taps once, all at once, into registers (both passes and the energy sums
+// then run there); otherwise each pass reads them again.  The decisions and the
+// order of every sum are the same either way.
+template <int KPER = 0, typename Tap>
 __device__ __forceinline__ int cut_rir(Tap tap, int n, double factor, int none, bool want_frac, float* frac,
                                        CutScratch& cs) {
     const int t = threadIdx.x, nt = blockDim.x;
+    constexpr int kC = KPER > 0 ? KPER : 1;
+    float c[kC];                                 // the thread's taps i = t + j * nt (in registers)
+    const bool inreg = KPER > 0 && n <= KPER * nt;
     float amax = 0.f;
+    if (inreg) {
+#pragma unroll
+        for (int j = 0; j < kC; ++j) {
+            const int i = t + j * nt;
+            c[j] = i < n ? tap(i) : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < kC; ++j) amax = fmaxf(amax, fabsf(c[j]));
+    } else {
 #pragma unroll 4
-    for (int i = t; i < n; i += nt) amax = fmaxf(amax, fabsf(tap(i)));
+        for (int i = t; i < n; i += nt) amax = fmaxf(amax, fabsf(tap(i)));
+    }
     amax = block_reduce(amax, OpMaxF(), cs.f, 0.f);
-    const double P = __dmul_rn((double)amax, (double)amax);   // exact
+    // the thresholds in FP64, once per CTA (FP64 is slow on this GPU: not in every thread)
+    if (t == 0) {
+        const double P0 = __dmul_rn((double)amax, (double)amax);   // exact
+        double pth0 = 0.0;
+        float lo = 0.f, hi = 0.f;
+        if (P0 != 0.0 && !none) {
+            pth0 = __dmul_rn(P0, factor);
+            const double st = sqrt(pth0);
+            lo = (float)(st * (1.0 - 1e-6));     // |h| < tlo  =>  h^2 < p_th
+            hi = (float)(st * (1.0 + 1e-6));     // |h| >= thi =>  h^2 >= p_th
+        }
+        cs.d[0] = P0;
+        cs.d[1] = pth0;
+        cs.f[0] = lo;
+        cs.f[1] = hi;
+    }
+    __syncthreads();
+    const double P = cs.d[0];
     int L;
     if (P == 0.0) {
         L = 1;
     } else if (none) {
         L = n;
     } else {
-        const double pth = __dmul_rn(P, factor);
-        const double st = sqrt(pth);
-        const float tlo = (float)(st * (1.0 - 1e-6));   // |h| < tlo  =>  h^2 < p_th
-        const float thi = (float)(st * (1.0 + 1e-6));   // |h| >= thi =>  h^2 >= p_th
+        const double pth = cs.d[1];
+        const float tlo = cs.f[0], thi = cs.f[1];
+        // Eq. 8's test of one tap (FP32 bounds settle the clear ones, FP64 the rest)
+        auto keep = [&](float a) {
+            if (a < tlo) return false;
+            if (a >= thi) return true;
+            return !(__dmul_rn((double)a, (double)a) < pth);
+        };
         int last = -1;
+        if (inreg) {
+#pragma unroll
+            for (int j = 0; j < kC; ++j) {
+                const int i = t + j * nt;
+                if (i < n && keep(fabsf(c[j]))) last = i;
+            }
+        } else {
 #pragma unroll 4
-        for (int i = t; i < n; i += nt) {
-            const float a = fabsf(tap(i));
-            bool keep;
-            if (a < tlo) keep = false;
-            else if (a >= thi) keep = true;
-            else keep = !(__dmul_rn((double)a, (double)a) < pth);
-            if (keep) last = i;
+            for (int i = t; i < n; i += nt)
+                if (keep(fabsf(tap(i)))) last = i;
         }
         last = block_reduce(last, OpMaxI(), cs.i, -1);
         L = last + 2;
@@ -256,15 +297,26 @@ __device__ __forceinline__ int cut_rir(Tap tap, int n, double factor, int none, 
     }
     if (want_frac) {
         float et = 0.f, ek = 0.f;
-        for (int i = t; i < n; i += nt) {
-            const float v = tap(i);
-            const float p = v * v;
-            et += p;
-            if (i < L) ek += p;
+        if (inreg) {
+#pragma unroll
+            for (int j = 0; j < kC; ++j) {
+                const int i = t + j * nt;
+                if (i >= n) break;
+                const float p = c[j] * c[j];
+                et += p;
+                if (i < L) ek += p;
+            }
+        } else {
+            for (int i = t; i < n; i += nt) {
+                const float v = tap(i);
+                const float p = v * v;
+                et += p;
+                if (i < L) ek += p;
+            }
         }
         const double dt = block_reduce((double)et, OpAddD(), cs.d, 0.0);
         const double dk = block_reduce((double)ek, OpAddD(), cs.d, 0.0);
-        *frac = dt > 0.0 ? (float)(dk / dt) : 1.f;
+        if (t == 0) *frac = dt > 0.0 ? (float)(dk / dt) : 1.f;
     }
     return L;
 }

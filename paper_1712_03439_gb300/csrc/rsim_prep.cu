@@ -11,8 +11,9 @@ namespace rsim {
 // K1: tail cut-off of every RIR (Eq. 7-9), one CTA per RIR (cut_rir)
 // ---------------------------------------------------------------------------
 constexpr int kTruncThreads = 256;
+constexpr int kTruncPer = 64;                    // taps per thread held in registers
 
-__global__ void __launch_bounds__(kTruncThreads)
+__global__ void __launch_bounds__(kTruncThreads, 2)
 k_truncate(DevBatch B, const float* __restrict__ rir, double factor, int none,
            float* __restrict__ ekf) {
     __shared__ CutScratch cs;
@@ -20,7 +21,9 @@ k_truncate(DevBatch B, const float* __restrict__ rir, double factor, int none,
         const float* h = rir + B.roff[r];
         const int n = B.rir_len[r];
         float frac;
-        const int L = cut_rir([&](int i) { return __ldg(h + i); }, n, factor, none, ekf != nullptr, &frac, cs);
+        // RIRs up to kTruncThreads * kTruncPer taps are read once, into registers
+        const int L = cut_rir<kTruncPer>([&](int i) { return __ldg(h + i); }, n, factor, none, ekf != nullptr,
+                                         &frac, cs);
         if (threadIdx.x == 0) {
             B.L[r] = L;
             if (ekf) ekf[r] = frac;
