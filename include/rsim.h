@@ -216,9 +216,9 @@ rsim_status rsim_plan_stage_times(rsim_plan_t plan, double *ms, int32_t *calls);
 int64_t rsim_plan_scratch_bytes(rsim_plan_t plan);
 
 /* Upper-bound plans: re-plans `plan` for another batch shape in place, without
- * new device memory, streams or events (SURVEY's shape classes; Sec. 1 draws
- * fresh rooms and utterances every epoch, so a training loop meets a new shape
- * on every batch).  A plan made for the largest batch of a class serves every
+ * new device memory, streams or events (a plan per shape class rather than
+ * per batch: Sec. 1 draws fresh rooms and utterances every epoch, so a training
+ * loop meets a new shape on every batch).  A plan made for the largest batch of a class serves every
  * batch whose scratch pieces each fit the class's: fewer or shorter
  * utterances, fewer sources, shorter RIRs.  Only num_utts, num_sources,
  * num_samples, rir_len and fft_cost may differ from the plan's description;
