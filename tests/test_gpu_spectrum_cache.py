@@ -69,3 +69,20 @@ def test_cached_spectra_with_a_partitioned_path():
     off = run(b, False, 0, None, True, eta=math.inf)
     for name, a, c in zip(("y", "gains", "dx", "dh", "dalpha"), on, off):
         np.testing.assert_array_equal(a, c, err_msg=name)
+
+
+def test_cache_memory_is_within_its_stated_bound():
+    # at most 16 bytes per source sample (plus one block of the largest cached size per
+    # source, rounded to 256 bytes): the plan's scratch grows by no more than that
+    from paper_1712_03439_gb300 import Plan
+    b = synth.make_batch(99, [900, 20011, 50000], [2, 3, 1], synth.linear_pair_array(), (0.1, 0.3))
+    on = Plan.for_batch(b, spectrum_cache=True)
+    off = Plan.for_batch(b, spectrum_cache=False)
+    S = int(b.num_sources.sum())
+    per_src = np.repeat(b.num_samples, b.num_sources)
+    bound = int(np.sum((16 * per_src + 4 * 8192 + 255) // 256 * 256)) + 8 * (S + 1) + 2 * 256
+    grown = on.scratch_bytes - off.scratch_bytes
+    assert 16 * per_src.sum() <= grown <= bound
+    on.close()
+    off.close()
+

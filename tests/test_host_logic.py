@@ -113,6 +113,26 @@ def test_algorithmic_work_counts_transforms_and_bytes():
     assert w["fwd_flops_5n"] > w["fwd_flops"]
 
 
+def test_algorithmic_work_with_the_spectrum_cache():
+    # each source block is transformed once for the step: the backward does I + J transforms
+    # per block at N <= 8192 and reads the kept spectra (4N bytes per source block) instead of
+    # x, which the forward writes; N = 16384 keeps the uncached count
+    bench = _bench()
+    b = synth.make_batch(3, [10000, 20000], [1, 2], synth.linear_pair_array(), (0.1, 0.1))
+    L = np.full(b.num_rirs, 500)
+    J = 2
+    tr = lambda m: 2.5 * (1 << m) * m
+    mac = lambda m: 8.0 * ((1 << m) / 2 + 1)
+    q = {"log2_n": np.array([13, 14]), "num_blocks": np.array([3, 2])}
+    plain = bench.algorithmic_work(b, q, L)
+    w = bench.algorithmic_work(b, q, L, cache=True)
+    assert w["fwd_flops"] == pytest.approx(plain["fwd_flops"])
+    spec = 3 * 1 * 4.0 * 8192
+    assert w["fwd_bytes"] == pytest.approx(plain["fwd_bytes"] + spec)
+    assert w["bwd_bytes"] == pytest.approx(plain["bwd_bytes"] - 4.0 * 1 * 10000 + spec)
+    assert plain["bwd_flops"] - w["bwd_flops"] == pytest.approx(3 * 1 * tr(13))
+
+
 def test_room_recipe_keeps_everything_inside_the_room():
     b = synth.config_stream(n_utts=40)
     geom, rir_len, rt60 = synth.room_geometry(5, b.num_sources, synth.linear_pair_array())
