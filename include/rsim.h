@@ -203,8 +203,9 @@ rsim_status rsim_plan_query(rsim_plan_t plan, void *stream, int32_t *log2_n, int
  * stream around each stage; rsim_plan_stage_times() synchronises the plan's
  * device, adds up the recorded durations (at most the last 64 calls) and
  * resets them.  Stages, in array order:
- *   0 truncation (Eq. 7-9)     1 source power       2 planner (N, queues, gains)
- *   3 RIR spectra              4 OLA forward        5 segment fix-up
+ *   0 truncation (Eq. 7-9)     1 source power and gains
+ *   2 planner (N, queues, backward partition)       3 RIR spectra
+ *   4 OLA forward              5 segment fix-up
  *   6 OLA backward             7 backward reduction
  * ms[8] receives milliseconds summed over calls, calls[8] the number of calls
  * summed (either may be NULL). */

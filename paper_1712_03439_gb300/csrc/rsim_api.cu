@@ -135,6 +135,8 @@ struct rsim_plan_s {
     cudaStream_t cap = nullptr;     // capture stream
     cudaStream_t aux = nullptr;     // side stream of the forward's first stage
     cudaEvent_t ev_aux = nullptr;
+    cudaEvent_t ev_plan = nullptr;  // the planner done (the backward partition waits for it)
+    cudaEvent_t ev_part = nullptr;  // the backward partition done (the forward's end waits for it)
     GraphCache gfwd, gbwd;
     // output samples per microphone of each utterance (host copy) and the row
     // offsets of the log-Mel features (device, written per call)
@@ -296,6 +298,8 @@ extern "C" void rsim_plan_destroy(rsim_plan_t plan) {
         if (plan->cap) cudaStreamDestroy(plan->cap);
         if (plan->aux) cudaStreamDestroy(plan->aux);
         if (plan->ev_aux) cudaEventDestroy(plan->ev_aux);
+        if (plan->ev_plan) cudaEventDestroy(plan->ev_plan);
+        if (plan->ev_part) cudaEventDestroy(plan->ev_part);
         if (plan->dmem) cudaFree(plan->dmem);
     }
     if (plan->rev) rsim_plan_destroy(plan->rev);
@@ -958,6 +962,8 @@ rsim_status plan_build(const rsim_plan_desc* d, int device, rsim_plan_t* out, rs
         p->cap = borrow->cap;
         p->aux = borrow->aux;
         p->ev_aux = borrow->ev_aux;
+        p->ev_plan = borrow->ev_plan;
+        p->ev_part = borrow->ev_part;
         p->ev_fork = borrow->ev_fork;
         for (int b = 0; b < kNumBuckets; ++b) {
             p->bs[b] = borrow->bs[b];
@@ -967,6 +973,8 @@ rsim_status plan_build(const rsim_plan_desc* d, int device, rsim_plan_t* out, rs
         e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_aux, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_plan, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_part, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
         for (int m = kMinLog; m <= kMaxLog && e == cudaSuccess; ++m) {
             if (!((mask >> m) & 1)) continue;
@@ -1050,7 +1058,7 @@ extern "C" rsim_status rsim_plan_reshape(rsim_plan_t p, const rsim_plan_desc* d)
         // the new shape needs a sub-plan: keep the old state
         np->dmem = nullptr;
         np->cap = np->aux = nullptr;
-        np->ev_aux = np->ev_fork = nullptr;
+        np->ev_aux = np->ev_plan = np->ev_part = np->ev_fork = nullptr;
         for (int b = 0; b < kNumBuckets; ++b) {
             np->bs[b] = nullptr;
             np->ev_join[b] = nullptr;
@@ -1063,7 +1071,7 @@ extern "C" rsim_status rsim_plan_reshape(rsim_plan_t p, const rsim_plan_desc* d)
     if (e != cudaSuccess) {
         np->dmem = nullptr;
         np->cap = np->aux = nullptr;
-        np->ev_aux = np->ev_fork = nullptr;
+        np->ev_aux = np->ev_plan = np->ev_part = np->ev_fork = nullptr;
         for (int b = 0; b < kNumBuckets; ++b) {
             np->bs[b] = nullptr;
             np->ev_join[b] = nullptr;
@@ -1075,7 +1083,7 @@ extern "C" rsim_status rsim_plan_reshape(rsim_plan_t p, const rsim_plan_desc* d)
     std::swap(*p, *np);
     np->dmem = nullptr;
     np->cap = np->aux = nullptr;
-    np->ev_aux = np->ev_fork = nullptr;
+    np->ev_aux = np->ev_plan = np->ev_part = np->ev_fork = nullptr;
     for (int b = 0; b < kNumBuckets; ++b) {
         np->bs[b] = nullptr;
         np->ev_join[b] = nullptr;
@@ -1166,6 +1174,16 @@ cudaError_t enqueue_forward(rsim_plan_t p, cudaStream_t st, const float* x, cons
     }
     stage_mark(p, 2, false, st);
     launch_plan(B, p->Q, st);
+    if (gains_aside) {
+        // the backward partition after the gains on the side stream: it overlaps the
+        // spectra and the forward, and the forward's end waits for it
+        cudaEventRecord(p->ev_plan, st);
+        cudaStreamWaitEvent(p->aux, p->ev_plan, 0);
+        launch_partition(B, p->aux);
+        cudaEventRecord(p->ev_part, p->aux);
+    } else {
+        launch_partition(B, st);
+    }
     stage_mark(p, 2, true, st);
     if (!p->timer.on) {
         // each FFT size's spectra then its OLA pass on that size's stream: a size's
@@ -1189,6 +1207,7 @@ cudaError_t enqueue_forward(rsim_plan_t p, cudaStream_t st, const float* x, cons
         });
         stage_mark(p, 4, true, st);
     }
+    if (gains_aside) cudaStreamWaitEvent(st, p->ev_part, 0);
     stage_mark(p, 5, false, st);
     launch_fixup(B, y, p->tails, st);
     stage_mark(p, 5, true, st);

@@ -351,6 +351,7 @@ void launch_truncate(const DevBatch& B, const float* rir, double factor, int non
 void launch_power(const DevBatch& B, const float* x, int grid, cudaStream_t st);
 void launch_gains(const DevBatch& B, const float* snr_db, float* gains, cudaStream_t st);
 void launch_plan(const DevBatch& B, const Queues& Q, cudaStream_t st);
+void launch_partition(const DevBatch& B, cudaStream_t st);
 // Twiddle tables of one FFT size for 8 and 16 values per thread; every
 // tiled kernel picks the table of its own thread shape.
 struct Twiddles {

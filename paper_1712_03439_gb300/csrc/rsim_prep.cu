@@ -107,36 +107,43 @@ void launch_power(const DevBatch& B, const float* x, int grid, cudaStream_t st) 
 // Apart from the planner: it needs the power scan, the planner only the cut-off,
 // so the planner and the RIR spectra need not wait for the scan.
 // ---------------------------------------------------------------------------
-__global__ void k_gains(DevBatch B, const float* __restrict__ snr_db, float* __restrict__ gains) {
-    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < B.U; u += gridDim.x * blockDim.x) {
+__global__ void __launch_bounds__(256) k_gains(DevBatch B, const float* __restrict__ snr_db,
+                                              float* __restrict__ gains) {
+    // one warp per utterance, one source per lane: each lane adds its source's chunk
+    // partials in chunk order (FP64), P_0 / P_i is the ratio of those sums (both over
+    // the utterance's Nx samples)
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < B.U; u += warps) {
         const int s0 = B.src0[u], I = B.n_src[u];
-        const double nx = (double)B.n_x[u];
-        // chunks past this utterance's end are never written: sum only
-        // the ones that exist
+        // chunks past this utterance's end are never written: sum only the ones that exist
         const int nch = (int)((B.n_x[u] + kPowerChunk - 1) / kPowerChunk);
-        double P0 = 0.0;
-        for (int c = 0; c < nch; ++c) P0 += B.pow_part[(int64_t)s0 * B.CH + c];
-        P0 /= nx;
-        gains[s0] = 1.f;
-        for (int i = 1; i < I; ++i) {
-            double Pi = 0.0;
-            for (int c = 0; c < nch; ++c) Pi += B.pow_part[(int64_t)(s0 + i) * B.CH + c];
-            Pi /= nx;
-            if (!(Pi > 0.0)) {
+        double S0 = 0.0;
+        for (int i0 = 0; i0 < I; i0 += 32) {
+            const int i = i0 + lane;
+            double Si = 0.0;
+            if (i < I)
+                for (int c = 0; c < nch; ++c) Si += B.pow_part[(int64_t)(s0 + i) * B.CH + c];
+            if (i0 == 0) S0 = __shfl_sync(0xffffffffu, Si, 0);
+            if (i >= I) continue;
+            if (i == 0) {
+                gains[s0] = 1.f;
+            } else if (!(Si > 0.0)) {
                 atomicOr(B.err, kErrZeroPower);
                 gains[s0 + i] = 0.f;
             } else {
                 // the power ratio in FP64, 10^(-SNR/10) and the root in FP32 (an FP64 pow
                 // per source is slow on this GPU's FP64 pipe; FP32 keeps alpha within a
                 // few 1e-7 relative)
-                gains[s0 + i] = sqrtf((float)(P0 / Pi) * exp10f(-snr_db[s0 + i] / 10.f));
+                gains[s0 + i] = sqrtf((float)(S0 / Si) * exp10f(-snr_db[s0 + i] / 10.f));
             }
         }
     }
 }
 
 void launch_gains(const DevBatch& B, const float* snr_db, float* gains, cudaStream_t st) {
-    k_gains<<<(B.U + 127) / 128, 128, 0, st>>>(B, snr_db, gains);
+    const int grid = (int)std::min<int64_t>(((int64_t)B.U * 32 + 255) / 256, 4096);
+    k_gains<<<grid > 0 ? grid : 1, 256, 0, st>>>(B, snr_db, gains);
 }
 
 // ---------------------------------------------------------------------------
@@ -148,8 +155,9 @@ void launch_gains(const DevBatch& B, const float* snr_db, float* gains, cudaStre
 // table; N must leave hop >= N/4 (a block's tail may then reach several
 // blocks ahead; the forward carries it).  An utterance no allowed N fits goes
 // to its partitioned path when it has one (no work here), else it is an error.
-// Then the backward partition of each size (below), and per FFT size the lists
-// of spectrum jobs (RIRs) and forward tiles (segments), in utterance order.
+// Then per FFT size the lists of spectrum jobs (RIRs) and forward tiles
+// (segments), in utterance order.  The backward partition of each size is
+// k_partition's (below).
 constexpr int kPlanThreads = 1024;
 constexpr float kConsolidateShare = 0.1f;   // a size below this share of the work is a minority
 constexpr float kConsolidateSlack = 0.02f;  // ...and moves if that adds at most this share of the work
@@ -158,7 +166,6 @@ constexpr float kConsolidateSlack = 0.02f;  // ...and moves if that adds at most
 __global__ void __launch_bounds__(kPlanThreads)
 k_plan(DevBatch B, Queues Q) {
     __shared__ int sm[33];
-    __shared__ long long pw_scratch[32];
     const int t = threadIdx.x;
     // ---- FFT size per utterance.  Every thread also tallies, per chosen size m,
     // the predicted work and, per other size d, how much dearer its utterances
@@ -257,6 +264,130 @@ k_plan(DevBatch B, Queues Q) {
         B.nblk[u] = m ? (int)((nx + hop - 1) / hop) : 0;
     }
     __syncthreads();
+    const int per = (B.U + kPlanThreads - 1) / kPlanThreads;
+    const int u0 = min(B.U, t * per), u1 = min(B.U, u0 + per);
+    const int lane = t & 31, wid = t >> 5;
+    // ---- work lists.  The forward's tiles go dearest first (cost: the tile's blocks x
+    // (I + J) transforms, in kFwdCls classes of equal width up to a bound on the dearest
+    // tile), so that the persistent CTAs end on cheap tiles (longest-processing-time
+    // first), which shortens the launch's ragged end: a shared-memory histogram of the
+    // (size, class) pairs, then each tile takes the next slot of its pair (the order
+    // within a class is that of the slot claims; results do not depend on it).  The
+    // spectrum lists: one contiguous chunk of utterances per thread, laid out by a
+    // block-wide exclusive scan of the per-thread counts.
+    constexpr int kFwdCls = 8;
+    // the tile's blocks in FP32 (only the order depends on them; the tiles' own block
+    // ranges are computed exactly where they are processed)
+    auto tile_cost = [&](int u, int g) {
+        const float r = (float)B.seg_len / (float)B.hop[u], nb = (float)B.nblk[u];
+        const float s = (float)(g - B.seg0[u]);
+        const float b0 = fminf(ceilf(s * r), nb), b1 = fminf(ceilf((s + 1.f) * r), nb);
+        return (int)(b1 - b0) * (B.n_src[u] + B.J);
+    };
+    int cmax = 0;                                // a tile holds at most ceil(seg_len / hop) + 1 blocks
+    for (int u = u0; u < u1; ++u)
+        if (B.logN[u] != 0)
+            cmax = max(cmax, (int)((B.seg_len + B.hop[u] - 1) / B.hop[u] + 1) * (B.n_src[u] + B.J));
+    cmax = block_reduce(cmax, OpMaxI(), sm, 0);
+    auto tile_cls = [&](int c) { return (int)((int64_t)(cmax - min(c, cmax)) * kFwdCls / (cmax + 1)); };
+    __shared__ int hist[kNumBuckets * kFwdCls];
+    if (t < kNumBuckets * kFwdCls) hist[t] = 0;
+    __syncthreads();
+    for (int u = u0; u < u1; ++u) {
+        const int m = B.logN[u];
+        if (m == 0) continue;
+        for (int g = B.seg0[u]; g < B.seg0[u + 1]; ++g)
+            atomicAdd(&hist[(m - kMinLog) * kFwdCls + tile_cls(tile_cost(u, g))], 1);
+    }
+    __syncthreads();
+    if (t < kNumBuckets) {                       // class c of size t starts after the dearer ones
+        int acc = 0;
+        for (int c = 0; c < kFwdCls; ++c) {
+            const int v = hist[t * kFwdCls + c];
+            hist[t * kFwdCls + c] = acc;
+            acc += v;
+        }
+        Q.count[Q.idx(kListFwd, t)] = acc;
+    }
+    __syncthreads();
+    for (int u = u0; u < u1; ++u) {
+        const int m = B.logN[u];
+        if (m == 0) continue;
+        int32_t* lf = Q.lst(kListFwd, m - kMinLog);
+        for (int g = B.seg0[u]; g < B.seg0[u + 1]; ++g)
+            lf[atomicAdd(&hist[(m - kMinLog) * kFwdCls + tile_cls(tile_cost(u, g))], 1)] = g;
+    }
+    int cnt[kNumBuckets];
+#pragma unroll
+    for (int q = 0; q < kNumBuckets; ++q) cnt[q] = 0;
+    for (int u = u0; u < u1; ++u) {
+        const int m = B.logN[u];
+        if (m == 0) continue;
+#pragma unroll
+        for (int q = 0; q < kNumBuckets; ++q)
+            if (q == m - kMinLog) cnt[q] += B.rir0[u + 1] - B.rir0[u];
+    }
+    __shared__ int wtot[kPlanThreads / 32][kNumBuckets];
+    __shared__ int ltot[kNumBuckets];
+    int off[kNumBuckets];
+    {
+#pragma unroll
+        for (int q = 0; q < kNumBuckets; ++q) {
+            int incl = cnt[q];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int n = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += n;
+            }
+            off[q] = incl - cnt[q];
+            if (lane == 31) wtot[wid][q] = incl;
+        }
+        __syncthreads();
+        if (t < kNumBuckets) {                   // exclusive scan of the warps' totals
+            int acc = 0;
+            for (int w = 0; w < kPlanThreads / 32; ++w) {
+                const int v = wtot[w][t];
+                wtot[w][t] = acc;
+                acc += v;
+            }
+            ltot[t] = acc;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kNumBuckets; ++q) off[q] += wtot[wid][q];
+    }
+    for (int u = u0; u < u1; ++u) {
+        const int m = B.logN[u];
+        if (m == 0) continue;
+        int32_t* ls = Q.lst(kListSpec, m - kMinLog);
+        int os = 0;
+#pragma unroll
+        for (int q = 0; q < kNumBuckets; ++q) {
+            if (q != m - kMinLog) continue;
+            os = off[q];
+            off[q] += B.rir0[u + 1] - B.rir0[u];
+        }
+        for (int r = B.rir0[u]; r < B.rir0[u + 1]; ++r) ls[os++] = r;
+    }
+    if (t < kNumBuckets) {
+        Q.count[Q.idx(kListSpec, t)] = ltot[t];
+        Q.count[Q.idx(kListBwd, t)] = 0;
+        Q.next[Q.idx(kListFwd, t)] = 0;
+        Q.next[Q.idx(kListBwd, t)] = 0;
+        Q.next[Q.idx(kListSpec, t)] = 0;
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// K2b: the backward partition (one CTA), from the sizes and block counts the
+// planner chose.  Only the backward and its finalizer read what it writes, so
+// it runs beside the spectra and the forward.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kPlanThreads)
+k_partition(DevBatch B) {
+    __shared__ long long pw_scratch[32];
+    const int t = threadIdx.x;
     const int per = (B.U + kPlanThreads - 1) / kPlanThreads;
     const int u0 = min(B.U, t * per), u1 = min(B.U, u0 + per);
     const int ngrp_j = (B.J + kJG - 1) / kJG;
@@ -511,81 +642,14 @@ k_plan(DevBatch B, Queues Q) {
             });
         }
     }
-    // ---- work lists of the forward and the spectra, one contiguous chunk of utterances
-    // per thread, laid out by one block-wide exclusive scan of the per-thread counts
-    constexpr int kNL = 2 * kNumBuckets;           // (list kind, size) pairs
-    int cnt[kNL];
-#pragma unroll
-    for (int q = 0; q < kNL; ++q) cnt[q] = 0;
-    for (int u = u0; u < u1; ++u) {
-        const int m = B.logN[u];
-        if (m == 0) continue;
-        const int b = m - kMinLog;
-#pragma unroll
-        for (int q = 0; q < kNumBuckets; ++q) {
-            if (q != b) continue;
-            cnt[q] += B.seg0[u + 1] - B.seg0[u];
-            cnt[kNumBuckets + q] += B.rir0[u + 1] - B.rir0[u];
-        }
-    }
-    __shared__ int wtot[kPlanThreads / 32][kNL];
-    __shared__ int ltot[kNL];
-    int off[kNL];
-    {
-#pragma unroll
-        for (int q = 0; q < kNL; ++q) {
-            int incl = cnt[q];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int n = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += n;
-            }
-            off[q] = incl - cnt[q];
-            if (lane == 31) wtot[wid][q] = incl;
-        }
-        __syncthreads();
-        if (t < kNL) {                            // exclusive scan of the warps' totals
-            int acc = 0;
-            for (int w = 0; w < kPlanThreads / 32; ++w) {
-                const int v = wtot[w][t];
-                wtot[w][t] = acc;
-                acc += v;
-            }
-            ltot[t] = acc;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < kNL; ++q) off[q] += wtot[wid][q];
-    }
-    for (int u = u0; u < u1; ++u) {
-        const int m = B.logN[u];
-        if (m == 0) continue;
-        const int b = m - kMinLog;
-        int32_t* lf = Q.lst(kListFwd, b);
-        int32_t* ls = Q.lst(kListSpec, b);
-        int of = 0, os = 0;
-#pragma unroll
-        for (int q = 0; q < kNumBuckets; ++q) {
-            if (q != b) continue;
-            of = off[q]; os = off[kNumBuckets + q];
-            off[q] += B.seg0[u + 1] - B.seg0[u];
-            off[kNumBuckets + q] += B.rir0[u + 1] - B.rir0[u];
-        }
-        for (int g = B.seg0[u]; g < B.seg0[u + 1]; ++g) lf[of++] = g;
-        for (int r = B.rir0[u]; r < B.rir0[u + 1]; ++r) ls[os++] = r;
-    }
-    if (t < kNumBuckets) {
-        Q.count[Q.idx(kListFwd, t)] = ltot[t];
-        Q.count[Q.idx(kListSpec, t)] = ltot[kNumBuckets + t];
-        Q.count[Q.idx(kListBwd, t)] = 0;
-        Q.next[Q.idx(kListFwd, t)] = 0;
-        Q.next[Q.idx(kListBwd, t)] = 0;
-        Q.next[Q.idx(kListSpec, t)] = 0;
-    }
 }
 
 void launch_plan(const DevBatch& B, const Queues& Q, cudaStream_t st) {
     k_plan<<<1, kPlanThreads, 0, st>>>(B, Q);
+}
+
+void launch_partition(const DevBatch& B, cudaStream_t st) {
+    k_partition<<<1, kPlanThreads, 0, st>>>(B);
 }
 
 }  // namespace rsim
