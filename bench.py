@@ -551,8 +551,8 @@ def run_ours(args):
                "sample": f"utterances 0-{n_cpu - 1} of the home-256 batch ({sub.audio_seconds():.1f} s of audio), "
                          f"forward + backward, FP64 direct convolution on {cores} threads, {dt:.1f} s wall"}
 
-    # truncate, power, plan, spectra, forward, fix-up | backward, finalize
-    kernels_per_step = (3 + 2 * n_sizes + 1) + (n_sizes + 1)
+    # truncate, power, gains, plan, backward partition, spectra, forward, fix-up | backward, finalize
+    kernels_per_step = (5 + 2 * n_sizes + 1) + (n_sizes + 1)
     line = {
         "metric": METRIC, "value": whole_job_rate(audio_s, world, ms), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "ms_per_step_median": ms_median,
