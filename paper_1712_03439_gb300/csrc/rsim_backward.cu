@@ -784,22 +784,23 @@ k_finalize(DevBatch B, const float* __restrict__ gains, const float* __restrict_
         const int sidx = B.src0[u] + i0;
         const int64_t local = B.lpre[r] - B.lpre[B.rir0[u] + i0 * B.J];
         const int p0 = B.s_first[sidx], p1 = B.s_last[sidx];
-        float acc[4];
+        constexpr int kFinU = 16;              // taps per thread in flight
+        float acc[kFinU];
         // taps of this thread: k = threadIdx.x + c * blockDim.x
         const int ntap_passes = (nh + kFinThreads - 1) / kFinThreads;
-        for (int c0 = 0; c0 < ntap_passes; c0 += 4) {
+        for (int c0 = 0; c0 < ntap_passes; c0 += kFinU) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[c] = 0.f;
+            for (int c = 0; c < kFinU; ++c) acc[c] = 0.f;
             for (int q = p0; q <= p1; ++q) {
                 const float* src = dhp + B.piece_dh[q] + local;
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
+                for (int c = 0; c < kFinU; ++c) {
                     const int k = threadIdx.x + (c0 + c) * kFinThreads;
                     if (k < Lr) acc[c] += src[k];
                 }
             }
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
+            for (int c = 0; c < kFinU; ++c) {
                 const int k = threadIdx.x + (c0 + c) * kFinThreads;
                 if (k < nh && RSIM_STORE_OK(B, out + k, grad_rir, RSIM_RIR_BYTES(B))) out[k] = k < Lr ? scale * acc[c] : 0.f;
                 if (h && k < Lr) dot = fmaf(h[k], acc[c], dot);

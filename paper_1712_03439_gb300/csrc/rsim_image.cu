@@ -169,7 +169,8 @@ constexpr int kCutThreads = 320;
 
 __global__ void __launch_bounds__(kCutThreads)
 k_image_cut(DevBatch B, const rsim_image_geom* __restrict__ geom, int32_t K, float fs, float c0, double factor,
-            int none, float* __restrict__ kept, float* __restrict__ full, float* __restrict__ ekf) {
+            float sqrt_factor, int none, float* __restrict__ kept, float* __restrict__ full,
+            float* __restrict__ ekf) {
     extern __shared__ __align__(16) float hwin[];
     __shared__ float2 tab[3][kImgMaxSide];
     __shared__ CutScratch cs;
@@ -191,7 +192,8 @@ k_image_cut(DevBatch B, const rsim_image_geom* __restrict__ geom, int32_t K, flo
             __syncthreads();
         }
         float frac = 1.f;
-        const int L = cut_rir([&](int i) { return hwin[i]; }, nh, factor, none, ekf != nullptr, &frac, cs);
+        const int L = cut_rir([&](int i) { return hwin[i]; }, nh, factor, sqrt_factor, none, ekf != nullptr, &frac,
+                              cs);
         for (int i = t; i < L; i += kCutThreads) kept[o0 + i] = hwin[i];
         if (full)
             for (int i = t; i < nh; i += kCutThreads) full[o0 + i] = hwin[i];
@@ -216,8 +218,8 @@ int image_cut_grid(int nh_max, int R, int sms) {
 
 void launch_image_cut(const DevBatch& B, const rsim_image_geom* geom, int K, float fs, float c0, double factor,
                       int none, int nh_max, float* kept, float* full, float* ekf, int grid, cudaStream_t st) {
-    k_image_cut<<<grid, kCutThreads, image_cut_smem(nh_max), st>>>(B, geom, K, fs, c0, factor, none, kept, full,
-                                                                   ekf);
+    k_image_cut<<<grid, kCutThreads, image_cut_smem(nh_max), st>>>(B, geom, K, fs, c0, factor,
+                                                                   (float)std::sqrt(factor), none, kept, full, ekf);
 }
 
 }  // namespace rsim

@@ -227,8 +227,8 @@ struct CutScratch {
 // then run there); otherwise each pass reads them again.  The decisions and the
 // order of every sum are the same either way.
 template <int KPER = 0, typename Tap>
-__device__ __forceinline__ int cut_rir(Tap tap, int n, double factor, int none, bool want_frac, float* frac,
-                                       CutScratch& cs) {
+__device__ __forceinline__ int cut_rir(Tap tap, int n, double factor, float sqrt_factor, int none, bool want_frac,
+                                       float* frac, CutScratch& cs) {
     const int t = threadIdx.x, nt = blockDim.x;
     constexpr int kC = KPER > 0 ? KPER : 1;
     float c[kC];                                 // the thread's taps i = t + j * nt (in registers)
@@ -247,32 +247,25 @@ __device__ __forceinline__ int cut_rir(Tap tap, int n, double factor, int none, 
         for (int i = t; i < n; i += nt) amax = fmaxf(amax, fabsf(tap(i)));
     }
     amax = block_reduce(amax, OpMaxF(), cs.f, 0.f);
-    // the thresholds in FP64, once per CTA (FP64 is slow on this GPU: not in every thread)
-    if (t == 0) {
-        const double P0 = __dmul_rn((double)amax, (double)amax);   // exact
-        double pth0 = 0.0;
-        float lo = 0.f, hi = 0.f;
-        if (P0 != 0.0 && !none) {
-            pth0 = __dmul_rn(P0, factor);
-            const double st = sqrt(pth0);
-            lo = (float)(st * (1.0 - 1e-6));     // |h| < tlo  =>  h^2 < p_th
-            hi = (float)(st * (1.0 + 1e-6));     // |h| >= thi =>  h^2 >= p_th
-        }
-        cs.d[0] = P0;
-        cs.d[1] = pth0;
-        cs.f[0] = lo;
-        cs.f[1] = hi;
-    }
-    __syncthreads();
-    const double P = cs.d[0];
+    // P = max h^2 (exact in FP64), p_th = P 10^(-eta/10) in FP64, and FP32 bounds
+    // around sqrt(p_th) = max |h| sqrt(factor) that settle the clear taps: with
+    // sqrt(factor) rounded to FP32 on the host, the bound's own rounding stays
+    // below 3e-7 relative, inside the 1e-6 margin.  Near the FP32 underflow range
+    // the bounds open up and every tap goes to the FP64 test.
+    const double P = __dmul_rn((double)amax, (double)amax);
     int L;
     if (P == 0.0) {
         L = 1;
     } else if (none) {
         L = n;
     } else {
-        const double pth = cs.d[1];
-        const float tlo = cs.f[0], thi = cs.f[1];
+        const double pth = __dmul_rn(P, factor);
+        float tlo = amax * sqrt_factor * (1.f - 1e-6f);   // |h| < tlo   =>  h^2 < p_th
+        float thi = amax * sqrt_factor * (1.f + 1e-6f);   // |h| >= thi  =>  h^2 >= p_th
+        if (!(tlo > 1e-30f)) {
+            tlo = 0.f;
+            thi = INFINITY;
+        }
         // Eq. 8's test of one tap (FP32 bounds settle the clear ones, FP64 the rest)
         auto keep = [&](float a) {
             if (a < tlo) return false;

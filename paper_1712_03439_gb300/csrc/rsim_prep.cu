@@ -14,7 +14,7 @@ constexpr int kTruncThreads = 256;
 constexpr int kTruncPer = 64;                    // taps per thread held in registers
 
 __global__ void __launch_bounds__(kTruncThreads, 2)
-k_truncate(DevBatch B, const float* __restrict__ rir, double factor, int none,
+k_truncate(DevBatch B, const float* __restrict__ rir, double factor, float sqrt_factor, int none,
            float* __restrict__ ekf) {
     __shared__ CutScratch cs;
     for (int r = blockIdx.x; r < B.R; r += gridDim.x) {
@@ -22,8 +22,8 @@ k_truncate(DevBatch B, const float* __restrict__ rir, double factor, int none,
         const int n = B.rir_len[r];
         float frac;
         // RIRs up to kTruncThreads * kTruncPer taps are read once, into registers
-        const int L = cut_rir<kTruncPer>([&](int i) { return __ldg(h + i); }, n, factor, none, ekf != nullptr,
-                                         &frac, cs);
+        const int L = cut_rir<kTruncPer>([&](int i) { return __ldg(h + i); }, n, factor, sqrt_factor, none,
+                                         ekf != nullptr, &frac, cs);
         if (threadIdx.x == 0) {
             B.L[r] = L;
             if (ekf) ekf[r] = frac;
@@ -34,7 +34,7 @@ k_truncate(DevBatch B, const float* __restrict__ rir, double factor, int none,
 
 void launch_truncate(const DevBatch& B, const float* rir, double factor, int none,
                      float* energy_kept_frac, int grid, cudaStream_t st) {
-    k_truncate<<<grid, kTruncThreads, 0, st>>>(B, rir, factor, none, energy_kept_frac);
+    k_truncate<<<grid, kTruncThreads, 0, st>>>(B, rir, factor, (float)sqrt(factor), none, energy_kept_frac);
 }
 
 // ---------------------------------------------------------------------------
