@@ -784,7 +784,7 @@ k_finalize(DevBatch B, const float* __restrict__ gains, const float* __restrict_
         const int sidx = B.src0[u] + i0;
         const int64_t local = B.lpre[r] - B.lpre[B.rir0[u] + i0 * B.J];
         const int p0 = B.s_first[sidx], p1 = B.s_last[sidx];
-        constexpr int kFinU = 16;              // taps per thread in flight
+        constexpr int kFinU = 4;               // taps per thread in flight (more cost occupancy)
         float acc[kFinU];
         // taps of this thread: k = threadIdx.x + c * blockDim.x
         const int ntap_passes = (nh + kFinThreads - 1) / kFinThreads;

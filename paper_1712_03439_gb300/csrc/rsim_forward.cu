@@ -288,6 +288,7 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 k_fixup(DevBatch B, float* __restrict__ y, const float* __restrict__ tails) {
+    const int j = blockIdx.y;                    // one microphone per grid row
     for (int g = blockIdx.x; g < B.NSEG; g += gridDim.x) {
         const int u = B.seg_utt[g];
         const int64_t s = g - B.seg0[u];
@@ -301,24 +302,22 @@ k_fixup(DevBatch B, float* __restrict__ y, const float* __restrict__ tails) {
         const int tail_len = B.Lmax[u] - 1;
         const int64_t ye = min(ny, B.n_x[u] + (int64_t)tail_len);
         const int lim = (int)min((int64_t)tail_len, ye - pos);
-        // four independent read-add-write rounds in flight per thread
-        constexpr int kU = 4;
-        for (int j = 0; j < B.J; ++j) {
-            const float* src = tails + ((int64_t)(g - 1) * B.J + j) * 2 * B.MMAX;
-            float* yj = y + B.yoff[u] + (int64_t)j * ny + pos;
-            for (int n0 = threadIdx.x; n0 < lim; n0 += kU * blockDim.x) {
-                float a[kU], c[kU];
+        // eight independent read-add-write rounds in flight per thread
+        constexpr int kU = 8;
+        const float* src = tails + ((int64_t)(g - 1) * B.J + j) * 2 * B.MMAX;
+        float* yj = y + B.yoff[u] + (int64_t)j * ny + pos;
+        for (int n0 = threadIdx.x; n0 < lim; n0 += kU * blockDim.x) {
+            float a[kU], c[kU];
 #pragma unroll
-                for (int k = 0; k < kU; ++k) {
-                    const int n = n0 + k * blockDim.x;
-                    a[k] = n < lim ? yj[n] : 0.f;
-                    c[k] = n < lim ? src[n] : 0.f;
-                }
+            for (int k = 0; k < kU; ++k) {
+                const int n = n0 + k * blockDim.x;
+                a[k] = n < lim ? yj[n] : 0.f;
+                c[k] = n < lim ? src[n] : 0.f;
+            }
 #pragma unroll
-                for (int k = 0; k < kU; ++k) {
-                    const int n = n0 + k * blockDim.x;
-                    if (n < lim && RSIM_STORE_OK(B, yj + n, y, RSIM_Y_BYTES(B))) yj[n] = a[k] + c[k];
-                }
+            for (int k = 0; k < kU; ++k) {
+                const int n = n0 + k * blockDim.x;
+                if (n < lim && RSIM_STORE_OK(B, yj + n, y, RSIM_Y_BYTES(B))) yj[n] = a[k] + c[k];
             }
         }
     }
@@ -375,7 +374,7 @@ void launch_forward(int logN, const DevBatch& B, const Queues& Q, const float* x
 void launch_fixup(const DevBatch& B, float* y, const float* tails, cudaStream_t st) {
     int grid = B.NSEG < 4096 ? B.NSEG : 4096;
     if (grid < 1) grid = 1;
-    k_fixup<<<grid, 256, 0, st>>>(B, y, tails);
+    k_fixup<<<dim3(grid, B.J > 0 ? B.J : 1), 256, 0, st>>>(B, y, tails);
 }
 
 int threads_for(int logN) { const int M = 1 << (logN - 1); return M / e_for(M); }

@@ -271,8 +271,9 @@ k_plan(DevBatch B, Queues Q) {
     // (I + J) transforms, in kFwdCls classes of equal width up to a bound on the dearest
     // tile), so that the persistent CTAs end on cheap tiles (longest-processing-time
     // first), which shortens the launch's ragged end: a shared-memory histogram of the
-    // (size, class) pairs, then each tile takes the next slot of its pair (the order
-    // within a class is that of the slot claims; results do not depend on it).  The
+    // (size, class) pairs, then each utterance takes the next run of slots of each of
+    // its pairs (the order of the runs within a class is that of the slot claims;
+    // results do not depend on it).  The
     // spectrum lists: one contiguous chunk of utterances per thread, laid out by a
     // block-wide exclusive scan of the per-thread counts.
     constexpr int kFwdCls = 8;
@@ -310,12 +311,32 @@ k_plan(DevBatch B, Queues Q) {
         Q.count[Q.idx(kListFwd, t)] = acc;
     }
     __syncthreads();
+    // each utterance claims its tiles of a class as one run of slots, so that an
+    // utterance's tiles stay together in the list (its RIR spectra then serve
+    // neighbouring CTAs from L2)
     for (int u = u0; u < u1; ++u) {
         const int m = B.logN[u];
         if (m == 0) continue;
+        int n[kFwdCls];
+#pragma unroll
+        for (int c = 0; c < kFwdCls; ++c) n[c] = 0;
+        for (int g = B.seg0[u]; g < B.seg0[u + 1]; ++g) {
+            const int c = tile_cls(tile_cost(u, g));
+#pragma unroll
+            for (int q = 0; q < kFwdCls; ++q) n[q] += q == c;
+        }
+#pragma unroll
+        for (int q = 0; q < kFwdCls; ++q)
+            if (n[q]) n[q] = atomicAdd(&hist[(m - kMinLog) * kFwdCls + q], n[q]);
         int32_t* lf = Q.lst(kListFwd, m - kMinLog);
-        for (int g = B.seg0[u]; g < B.seg0[u + 1]; ++g)
-            lf[atomicAdd(&hist[(m - kMinLog) * kFwdCls + tile_cls(tile_cost(u, g))], 1)] = g;
+        for (int g = B.seg0[u]; g < B.seg0[u + 1]; ++g) {
+            const int c = tile_cls(tile_cost(u, g));
+            int pos = 0;
+#pragma unroll
+            for (int q = 0; q < kFwdCls; ++q)
+                if (q == c) pos = n[q]++;
+            lf[pos] = g;
+        }
     }
     int cnt[kNumBuckets];
 #pragma unroll
