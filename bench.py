@@ -58,7 +58,7 @@ def algorithmic_work(batch, q, L, cache=False):
     products; bytes: x read once, y written once.  Backward per block:
     2I + J transforms and 2*I*J products, plus one inverse per RIR for dh;
     bytes: grad_y and x read once, grad_x written once, dh written once.
-    With the spectrum cache (N <= 8192) each source block is transformed once
+    With the spectrum cache each source block is transformed once
     for the whole step: the forward also writes its half spectrum (N/4 bin
     pairs of 16 bytes) and the backward reads it in place of x and does
     I + J transforms per block."""
@@ -74,7 +74,7 @@ def algorithmic_work(batch, q, L, cache=False):
         B = int(q["num_blocks"][u])
         tr = 2.5 * N * m
         mac = 8.0 * (N / 2 + 1)
-        cached = cache and m <= 13
+        cached = cache
         nbw = (I + J) if cached else (2 * I + J)             # backward transforms per block
         spec = B * I * 4.0 * N if cached else 0.0            # bytes of the kept spectra
         ff += B * ((I + J) * tr + I * J * mac)

@@ -105,10 +105,13 @@ typedef struct {
                                       cut-off those utterances always take the partitioned
                                       path, whatever this field says. */
     int32_t spectrum_cache;        /* 1: the forward keeps each block's source half spectrum
-                                      X_ib (FFT sizes up to 8192), which the backward reads
-                                      instead of transforming the block again -- the same
-                                      spectra, so the same results; the plan reserves at most
-                                      16 bytes per source sample for them; 0: no cache */
+                                      X_ib, which the backward reads instead of transforming
+                                      the block again: up to N = 8192 the same spectra, so
+                                      the same results; at N = 16384 the two kernels
+                                      transform with different thread shapes, so results
+                                      differ from those without the cache by FP32 rounding
+                                      only; the plan reserves at most 16 bytes per source
+                                      sample (plus one block) for them; 0: no cache */
 } rsim_plan_desc;
 
 /* Creates a plan for the given shapes on CUDA device `device`.  Validates the

@@ -775,11 +775,11 @@ rsim_status plan_build(const rsim_plan_desc* d, int device, rsim_plan_t* out, rs
     pieces.push_back({&p_melrow, sizeof(int64_t) * (U + 1)});
     pieces.push_back({&p_ones, sizeof(float) * std::max<int64_t>(S, 1)});
     if (d->rooms) pieces.push_back({&p_kept, sizeof(float) * std::max<int64_t>(roff[R], 1)});
-    // the forward's source spectra for the backward (sizes up to 8192): block b of a source
+    // the forward's source spectra for the backward (every size): block b of a source
     // takes 4N bytes and there are at most ceil(4 Nx / N) blocks (hop >= N/4), so at most
     // 16 Nx + 4N bytes per source whatever N the planner picks
     int cache_log = 0;
-    for (int m = kMinLog; m <= std::min(kMaxLog, 13); ++m)
+    for (int m = kMinLog; m <= kMaxLog; ++m)
         if ((mask >> m) & 1) cache_log = m;
     const bool cache = d->spectrum_cache && cache_log > 0;
     std::vector<int64_t> xs_off(S + 1, 0);

@@ -77,7 +77,10 @@ static_assert(kJG == 2, "the backward tile loop is written for microphone pairs"
 // MG: more microphones than one group (J > kJG): later groups add their dx to
 // the first group's.  Without it dx is only written, which keeps the
 // read-modify-write path out of the common kernel.
-template <int M, bool MG>
+// CACHED: the forward kept every block's source spectrum (B.xspec): the source
+// step of each microphone group stages it by one bulk copy instead of
+// transforming the block.
+template <int M, bool MG, bool CACHED>
 __global__ void __launch_bounds__(BwdCfg<M>::T, BwdCfg<M>::kMinBlocks)
 k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const float* __restrict__ x,
            const float* __restrict__ gains, const float2* __restrict__ Hc, float* __restrict__ dx,
@@ -87,6 +90,7 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
     constexpr int T = L::T;
     constexpr int NST = L::NST;
     constexpr bool kBulk = NST == 2;      // inputs staged by bulk copies completing on mbarriers
+    static_assert(!CACHED || kBulk, "the cached source spectra are staged by bulk copies");
     constexpr bool kPaired = PairedSplit<M, E>::ok;   // split in registers (paired layout)
     using Pl = FftPlan<M, E>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -145,8 +149,14 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
                 }
             };
             auto stage_x = [&](int k, int64_t b) {
-                const int64_t p = b * hop;
-                stage_in(k, xi + p, min((int64_t)hop, nx - p));
+                if constexpr (CACHED) {          // the forward's spectrum of the block (2M floats)
+                    stage_in(k, reinterpret_cast<const float*>(reinterpret_cast<const char*>(B.xspec) +
+                                                               B.xspec_off[sb + i]) + b * 2 * M,
+                             2 * M);
+                } else {
+                    const int64_t p = b * hop;
+                    stage_in(k, xi + p, min((int64_t)hop, nx - p));
+                }
             };
             auto stage_g = [&](int k, int64_t b, int j) {
                 const int64_t p = b * hop;
@@ -178,6 +188,26 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
                 }
                 if constexpr (!kBulk) cp_async_commit();
                 sc ^= (NST - 1);
+            };
+            // X of a block from the stage (pair k = (X[k], X[M - k])); queues microphone
+            // j0's window, then a barrier: every thread is done with the stage before a
+            // later step's copy refills it (a source step has no transform to provide one)
+            auto take_x = [&](float2 (&Xo)[E], int64_t b) {
+                if (!bad && !mbar_wait_bounded(&mbar[sc], (ph >> sc) & 1u)) {
+                    mbar_wait_bounded(&mbar[sc], (ph >> sc) & 1u, 100000000ull);
+                    bad = true;
+                }
+                ph ^= 1u << sc;
+                const float4* s4 = reinterpret_cast<const float4*>(stage(sc));
+#pragma unroll
+                for (int q = 0; q < E / 2; ++q) {
+                    const float4 e4 = s4[kt + q * T];
+                    Xo[2 * q] = make_float2(e4.x, e4.y);
+                    Xo[2 * q + 1] = make_float2(e4.z, e4.w);
+                }
+                if (!bad) stage_g(sc ^ 1, b, j0);
+                sc ^= 1;
+                __syncthreads();
             };
             float2 W[kJG][E];
 #pragma unroll
@@ -235,6 +265,12 @@ k_backward(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, const
 #pragma unroll 1
                 for (int sp = 0; sp <= kJG; ++sp) {
                     if (sp > jn) break;
+                    if constexpr (CACHED) {
+                        if (sp == 0) {
+                            take_x(X, b);
+                            continue;
+                        }
+                    }
                     next_input(v, b, sp < jn ? j0 + sp : -1);
                     if constexpr (kPaired) {
                         float2 G[E];
@@ -855,7 +891,8 @@ static void backward_m(const DevBatch& B, const Queues& Q, int bucket, const flo
         kern<<<grid, BwdTmCfg<M>::T, smem_backward_tm<M>(), st>>>(B, Q, bucket, g, x, gains, Hc, dx, dhp,
                                                                   dap, tw.get(BwdTmCfg<M>::E));
     } else {
-        auto kern = B.J > kJG ? k_backward<M, true> : k_backward<M, false>;
+        auto kern = B.xspec ? (B.J > kJG ? k_backward<M, true, true> : k_backward<M, false, true>)
+                            : (B.J > kJG ? k_backward<M, true, false> : k_backward<M, false, false>);
         kern<<<grid, BwdCfg<M>::T, smem_backward<M>(), st>>>(B, Q, bucket, g, x, gains, Hc, dx, dhp,
                                                                       dap, tw.get(BwdCfg<M>::E));
     }
@@ -903,9 +940,13 @@ static int occ_b(K kernel, int threads, int smem) {
 // both microphone-group variants share the launch shape; the smaller occupancy rules
 template <int M>
 static int occ_bb() {
-    const int a = occ_b(k_backward<M, false>, BwdCfg<M>::T, smem_backward<M>());
-    const int b = occ_b(k_backward<M, true>, BwdCfg<M>::T, smem_backward<M>());
-    return a < b ? a : b;
+    int o = occ_b(k_backward<M, false, false>, BwdCfg<M>::T, smem_backward<M>());
+    o = std::min(o, occ_b(k_backward<M, true, false>, BwdCfg<M>::T, smem_backward<M>()));
+    if constexpr (BwdCfg<M>::NST == 2) {
+        o = std::min(o, occ_b(k_backward<M, false, true>, BwdCfg<M>::T, smem_backward<M>()));
+        o = std::min(o, occ_b(k_backward<M, true, true>, BwdCfg<M>::T, smem_backward<M>()));
+    }
+    return o;
 }
 // the TMEM kernels: also no more CTAs per SM than the SM's 512 TMEM columns hold
 // (a CTA beyond that would wait in its allocation until another one exits)

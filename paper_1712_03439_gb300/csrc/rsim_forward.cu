@@ -190,7 +190,7 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
                     const float2* H0 = Hc + (int64_t)(rb + i * J + j0) * B.MMAX;
                     // the block's spectrum, kept for the backward (first microphone group)
                     float4* xsp = nullptr;
-                    if constexpr (M <= 4096) {
+                    {
                         if (B.xspec && j0 == 0)
                             xsp = reinterpret_cast<float4*>(reinterpret_cast<char*>(B.xspec) + B.xspec_off[sb + i]) +
                                   b * (M / 2);

@@ -115,8 +115,8 @@ def test_algorithmic_work_counts_transforms_and_bytes():
 
 def test_algorithmic_work_with_the_spectrum_cache():
     # each source block is transformed once for the step: the backward does I + J transforms
-    # per block at N <= 8192 and reads the kept spectra (4N bytes per source block) instead of
-    # x, which the forward writes; N = 16384 keeps the uncached count
+    # per block and reads the kept spectra (4N bytes per source block) instead of x, which
+    # the forward writes -- at every size
     bench = _bench()
     b = synth.make_batch(3, [10000, 20000], [1, 2], synth.linear_pair_array(), (0.1, 0.1))
     L = np.full(b.num_rirs, 500)
@@ -127,10 +127,10 @@ def test_algorithmic_work_with_the_spectrum_cache():
     plain = bench.algorithmic_work(b, q, L)
     w = bench.algorithmic_work(b, q, L, cache=True)
     assert w["fwd_flops"] == pytest.approx(plain["fwd_flops"])
-    spec = 3 * 1 * 4.0 * 8192
+    spec = 3 * 1 * 4.0 * 8192 + 2 * 2 * 4.0 * 16384
     assert w["fwd_bytes"] == pytest.approx(plain["fwd_bytes"] + spec)
-    assert w["bwd_bytes"] == pytest.approx(plain["bwd_bytes"] - 4.0 * 1 * 10000 + spec)
-    assert plain["bwd_flops"] - w["bwd_flops"] == pytest.approx(3 * 1 * tr(13))
+    assert w["bwd_bytes"] == pytest.approx(plain["bwd_bytes"] - 4.0 * (1 * 10000 + 2 * 20000) + spec)
+    assert plain["bwd_flops"] - w["bwd_flops"] == pytest.approx(3 * 1 * tr(13) + 2 * 2 * tr(14))
 
 
 def test_room_recipe_keeps_everything_inside_the_room():
