@@ -431,6 +431,11 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
     __shared__ double sd[32];
     __shared__ __align__(8) uint64_t mbar[3];      // two input stages, the RIR spectra
     __shared__ uint32_t tmem_base;
+    // the piece's per-source gains and offsets and its utterance's output offset, read once
+    // per piece (every step reads them: from global memory each read would sit on the step's path)
+    __shared__ float s_gain[IG];
+    __shared__ int64_t s_xoff[IG], s_xso[IG];
+    __shared__ int64_t s_yoff;
     const int t = threadIdx.x;
     if (chunk_empty(B, bucket, blockIdx.x)) return;   // before any TMEM is taken
     if (t < 32) {                                // warp 0 takes the CTA's TMEM columns
@@ -483,6 +488,13 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
         const int J = B.J;
         const int I = min(IG, B.n_src[u] - i0);
         const int sb = B.src0[u] + i0, rb = B.rir0[u];
+        __syncthreads();                         // the previous piece's readers are done
+        if (t < I) {
+            s_gain[t] = __ldg(gains + sb + t);
+            s_xoff[t] = B.xoff[sb + t];
+            s_xso[t] = cached ? B.xspec_off[sb + t] : 0;
+        }
+        if (t == 0) s_yoff = B.yoff[u];          // (read after the group's first barrier)
         float da[IG];                            // <c_i, x_i> over the run, per source
 #pragma unroll
         for (int q = 0; q < IG; ++q) da[q] = 0.f;
@@ -495,14 +507,14 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
                 const float* src;
                 int64_t len;
                 if (k < jn) {
-                    src = gy + B.yoff[u] + (int64_t)(j0 + k) * ny + p;
+                    src = gy + s_yoff + (int64_t)(j0 + k) * ny + p;
                     len = min((int64_t)(hop + lmax - 1), ny - p);
                 } else if (cached) {             // the forward's spectrum of the block
                     src = reinterpret_cast<const float*>(reinterpret_cast<const char*>(B.xspec) +
-                                                         B.xspec_off[sb + k - jn]) + b * 2 * M;
+                                                         s_xso[k - jn]) + b * 2 * M;
                     len = 2 * M;
                 } else {
-                    src = x + B.xoff[sb + k - jn] + p;
+                    src = x + s_xoff[k - jn] + p;
                     len = min((int64_t)hop, nx - p);
                 }
                 const int off = stage_real_bulk<M, E>(stage(kk), src, len, &mbar[kk], t, B.test_withhold != 0);
@@ -633,8 +645,8 @@ k_backward_tm(DevBatch B, Queues Q, int bucket, const float* __restrict__ gy, co
                 // microphone group writes, later groups add; pairs go out as one 8-byte store
                 auto dx_store = [&](int i, const float2 (&v)[E]) {
                     if (!dx) return;
-                    const float a = __ldg(gains + sb + i);
-                    float* dst = dx + B.xoff[sb + i] + pos;
+                    const float a = s_gain[i];
+                    float* dst = dx + s_xoff[i] + pos;
                     const int ilim = (int)min((int64_t)hop, nx - pos);
                     const bool pairs = ((reinterpret_cast<uintptr_t>(dst) & 7) == 0) && j0 == 0;
 #pragma unroll

@@ -102,6 +102,14 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
     float* tl_smem = reinterpret_cast<float*>(smem_raw + L::o_tl);
     __shared__ int slot;
     __shared__ __align__(8) uint64_t mbar;
+    // the tile's per-source gains and offsets and its utterance's output offset, read once
+    // per tile (every source step reads them: from global memory each read would sit on
+    // the step's path)
+    // (up to kMaxPartSources: a partitioned plan's utterances hold that many virtual sources)
+    constexpr int kSrc = kMaxPartSources > kMaxSources ? kMaxPartSources : kMaxSources;
+    __shared__ float f_gain[kSrc];
+    __shared__ int64_t f_xoff[kSrc], f_xso[kSrc];
+    __shared__ int64_t f_yoff;
     const int t = threadIdx.x;
     if (t == 0) {
         mbar_init(&mbar, 1);
@@ -135,6 +143,13 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
         if (b0 >= b1) continue;
         const int I = B.n_src[u], J = B.J;
         const int sb = B.src0[u], rb = B.rir0[u];
+        // (the previous tile ended on a barrier; these are read after the group's first one)
+        for (int q = t; q < I; q += T) {
+            f_gain[q] = __ldg(gains + sb + q);
+            f_xoff[q] = B.xoff[sb + q];
+            f_xso[q] = B.xspec ? B.xspec_off[sb + q] : 0;
+        }
+        if (t == 0) f_yoff = B.yoff[u];
         for (int j0 = 0; j0 < J; j0 += kJG) {
             const int jn = min(kJG, J - j0);
             // one bulk copy per source block into the stage (whole 16-byte chunks by
@@ -142,7 +157,7 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
             auto stage_x = [&](int64_t b, int i) {
                 if (bad) return;
                 const int64_t p = b * hop;
-                xoff = stage_real_bulk<M, E>(xs, x + B.xoff[sb + i] + p, min((int64_t)hop, nx - p), &mbar, t,
+                xoff = stage_real_bulk<M, E>(xs, x + f_xoff[i] + p, min((int64_t)hop, nx - p), &mbar, t,
                                              B.test_withhold != 0);
             };
             // carried tail of mic jj: shared memory, or this tile's slot of `tails`
@@ -186,13 +201,13 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
                     __syncthreads();
                     store_strided<M, E>(v, sm, t);
                     __syncthreads();
-                    const float a = __ldg(gains + sb + i);
+                    const float a = f_gain[i];
                     const float2* H0 = Hc + (int64_t)(rb + i * J + j0) * B.MMAX;
                     // the block's spectrum, kept for the backward (first microphone group)
                     float4* xsp = nullptr;
                     {
                         if (B.xspec && j0 == 0)
-                            xsp = reinterpret_cast<float4*>(reinterpret_cast<char*>(B.xspec) + B.xspec_off[sb + i]) +
+                            xsp = reinterpret_cast<float4*>(reinterpret_cast<char*>(B.xspec) + f_xso[i]) +
                                   b * (M / 2);
                     }
 #pragma unroll
@@ -226,7 +241,7 @@ k_forward(DevBatch B, Queues Q, int bucket, const float* __restrict__ x,
                     if (jj >= jn) break;
                     float2 v[E];
                     irfft_pairs<M, E>(v, Y[jj], sm, tw, t);
-                    float* yj = y + B.yoff[u] + (int64_t)(j0 + jj) * ny + pos;
+                    float* yj = y + f_yoff + (int64_t)(j0 + jj) * ny + pos;
                     float* tlj = tl(jj);
                     const int64_t lim = ye - pos;
                     // every sample n < N of the block adds the carried sum at n;
