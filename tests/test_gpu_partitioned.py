@@ -179,6 +179,14 @@ def test_small_largest_size_with_many_parts():
     run_and_check(b, 60.0, 1, 0, long_rirs=True, fft_sizes=[2048], seed=31)
 
 
+def test_the_largest_number_of_virtual_sources():
+    # 16 sources x 4 parts of 1024 taps (4000-tap RIRs, only N = 2048): the 64 virtual
+    # sources a partitioned plan's utterance may hold
+    b = synth.make_batch(47, [3000], [16], synth.linear_pair_array(), (0.25, 0.25))
+    assert int(b.rir_len.max()) == 4000
+    run_and_check(b, math.inf, 1, 0, fft_sizes=[2048], seed=33)
+
+
 def test_too_many_parts_is_unsupported():
     from paper_1712_03439_gb300 import Plan
     from paper_1712_03439_gb300._lib import RsimError
